@@ -1,0 +1,228 @@
+"""FP64 CPU oracle for the GLRM alternating proximal-gradient method.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
+of the benchmark use it to check and time the CUDA library.  It shares no code
+with that library and never imports it.
+
+The arithmetic lives in ``glrm_oracle.c`` (plain C, double precision, loops in
+index order); this module compiles it with gcc and marshals numpy arrays to it.
+Every function follows the passage of Udell et al., "Generalized Low Rank
+Models" (arXiv 1410.0342), cited in its docstring.
+
+The observed set is passed as coordinate triples (row, col, value) sorted by
+row then column; the oracle builds its own row and column lists from them.
+Factors are X (m x k) and Yt = Y^T (n x k), both row-major float64.
+
+Parity status of each function (the pins live in tests/test_oracle_*.py):
+  loss / dloss / decode / reg / prox   pinned (closed forms, brute force,
+                                       finite differences, Huber identity)
+  objective / gradient                 pinned (brute-force loops, finite
+                                       differences)
+  proxgrad                             pinned (qPCA closed form, Eckart-Young,
+                                       monotone objective, single-row brute force)
+  als                                  pinned (normal equations vs numpy.linalg,
+                                       qPCA closed form)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+LOSS_QUAD, LOSS_HUBER, LOSS_HINGE, LOSS_LOGISTIC, LOSS_ORDINAL = 0, 1, 2, 3, 4
+REG_ZERO, REG_QUAD, REG_L1, REG_NONNEG = 0, 1, 2, 3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "glrm_oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "libglrm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP) into oracle/lib/."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        d, i32, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+        p = ctypes.c_void_p
+        lib.oracle_loss.restype = d
+        lib.oracle_loss.argtypes = [i32, d, i32, d, d]
+        lib.oracle_dloss.restype = d
+        lib.oracle_dloss.argtypes = [i32, d, i32, d, d]
+        lib.oracle_decode.restype = d
+        lib.oracle_decode.argtypes = [i32, i32, d]
+        lib.oracle_reg.restype = d
+        lib.oracle_reg.argtypes = [i32, d, i32, p]
+        lib.oracle_prox.restype = None
+        lib.oracle_prox.argtypes = [i32, d, d, i32, p, p]
+        lib.oracle_objective.restype = d
+        lib.oracle_objective.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p,
+                                         i32, d, i32, d, p, p, i32]
+        lib.oracle_gradient.restype = i32
+        lib.oracle_gradient.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, p, p, i32]
+        lib.oracle_proxgrad.restype = i32
+        lib.oracle_proxgrad.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, i32, d, i32, d,
+                                        p, p, p, p, i32, p, p, i32]
+        lib.oracle_als.restype = i32
+        lib.oracle_als.argtypes = [i64, i64, i32, i64, p, p, p, d, p, p, i32, p, i32]
+        lib.oracle_num_threads.restype = i32
+        lib.oracle_num_threads.argtypes = [i32]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ----------------------------------------------------------------- entrywise
+
+def loss(kind: int, u: float, a: float, param: float = 1.0, levels: int = 0) -> float:
+    """L(u, a): eq. qpca, Huber (Sec. 4.3), hinge and logistic (Sec. 5.2), eq. ord-pca."""
+    return _load().oracle_loss(kind, param, levels, float(u), float(a))
+
+
+def dloss(kind: int, u: float, a: float, param: float = 1.0, levels: int = 0) -> float:
+    """dL/du, 0 at kinks (gradient form of Sec. 7.2)."""
+    return _load().oracle_dloss(kind, param, levels, float(u), float(a))
+
+
+def decode(kind: int, u: float, levels: int = 0) -> float:
+    """argmin_a L(u, a) over the loss's domain (Sec. 5.3)."""
+    return _load().oracle_decode(kind, levels, float(u))
+
+
+def reg(kind: int, w: float, x) -> float:
+    """r(x) for zero / gamma||x||^2 / lambda||x||_1 / nonnegativity indicator (Sec. 3)."""
+    x = _c(x, np.float64)
+    return _load().oracle_reg(kind, w, x.size, _ptr(x))
+
+
+def prox(kind: int, w: float, alpha: float, z) -> np.ndarray:
+    """prox_{alpha r}(z) (Sec. 7.2, definition of the proximal operator)."""
+    z = _c(z, np.float64)
+    out = np.empty_like(z)
+    _load().oracle_prox(kind, w, alpha, z.size, _ptr(z), _ptr(out))
+    return out
+
+
+# ------------------------------------------------------------------- problem
+
+class Problem:
+    """Data of one GLRM (eq. gpca): Omega as sorted (row, col, value) triples,
+    per-column losses and the row / column regularisers."""
+
+    def __init__(self, m, n, k, rows, cols, vals, loss_kind, loss_param, loss_levels,
+                 rx=(REG_ZERO, 0.0), ry=(REG_ZERO, 0.0)):
+        self.m, self.n, self.k = int(m), int(n), int(k)
+        self.rows = _c(rows, np.int32)
+        self.cols = _c(cols, np.int32)
+        self.vals = _c(vals, np.float64)
+        self.nnz = int(self.rows.size)
+        self.loss_kind = _c(np.broadcast_to(loss_kind, (self.n,)), np.int32)
+        self.loss_param = _c(np.broadcast_to(loss_param, (self.n,)), np.float64)
+        self.loss_levels = _c(np.broadcast_to(loss_levels, (self.n,)), np.int32)
+        self.rx = (int(rx[0]), float(rx[1]))
+        self.ry = (int(ry[0]), float(ry[1]))
+
+    @classmethod
+    def from_csr(cls, m, n, k, rowptr, colidx, vals, **kw):
+        rowptr = np.asarray(rowptr, dtype=np.int64)
+        rows = np.repeat(np.arange(m, dtype=np.int32), np.diff(rowptr))
+        return cls(m, n, k, rows, colidx, vals, **kw)
+
+    def row_counts(self) -> np.ndarray:
+        return np.bincount(self.rows, minlength=self.m).astype(np.int64)
+
+    def col_counts(self) -> np.ndarray:
+        return np.bincount(self.cols, minlength=self.n).astype(np.int64)
+
+    def initial_alphas(self):
+        """alpha_i = 1 / max(n_i, 1) and alpha_j = 1 / max(m_j, 1) (Sec. 7.2)."""
+        ax = 1.0 / np.maximum(self.row_counts(), 1).astype(np.float64)
+        ay = 1.0 / np.maximum(self.col_counts(), 1).astype(np.float64)
+        return ax, ay
+
+    def _common(self):
+        return (self.m, self.n, self.k, self.nnz, _ptr(self.rows), _ptr(self.cols),
+                _ptr(self.vals))
+
+    def _losses(self):
+        return (_ptr(self.loss_kind), _ptr(self.loss_param), _ptr(self.loss_levels))
+
+    def objective(self, X, Yt, nthreads: int = 0) -> float:
+        """sum_Omega L + sum_i r(x_i) + sum_j rt(y_j) (eq. gpca)."""
+        X = _c(X, np.float64)
+        Yt = _c(Yt, np.float64)
+        return _load().oracle_objective(*self._common(), *self._losses(), *self.rx, *self.ry,
+                                        _ptr(X), _ptr(Yt), nthreads)
+
+    def gradient(self, X, Yt, nthreads: int = 0):
+        """Loss part of the gradient: G_X = R Y^T and G_Y^T = R^T X over Omega (Sec. 7.2)."""
+        X = _c(X, np.float64)
+        Yt = _c(Yt, np.float64)
+        GX = np.empty_like(X)
+        GYt = np.empty_like(Yt)
+        rc = _load().oracle_gradient(*self._common(), *self._losses(), _ptr(X), _ptr(Yt),
+                                     _ptr(GX), _ptr(GYt), nthreads)
+        if rc:
+            raise ValueError(f"oracle_gradient failed ({rc})")
+        return GX, GYt
+
+    def proxgrad(self, X, Yt, nsweeps: int, alpha_x=None, alpha_y=None, nthreads: int = 0):
+        """Alternating proximal-gradient sweeps with the step-size safeguard
+        (Algorithm 2, Sec. 7.2).  Returns (X, Yt, alpha_x, alpha_y, history,
+        accepts) with history[t] the objective after sweep t and accepts[t] the
+        (rows, columns) accepted in sweep t."""
+        X = np.array(X, dtype=np.float64, order="C")
+        Yt = np.array(Yt, dtype=np.float64, order="C")
+        if alpha_x is None or alpha_y is None:
+            alpha_x, alpha_y = self.initial_alphas()
+        alpha_x = np.array(alpha_x, dtype=np.float64)
+        alpha_y = np.array(alpha_y, dtype=np.float64)
+        hist = np.empty(nsweeps, dtype=np.float64)
+        acc = np.empty(2 * nsweeps, dtype=np.int64)
+        rc = _load().oracle_proxgrad(*self._common(), *self._losses(), *self.rx, *self.ry,
+                                     _ptr(X), _ptr(Yt), _ptr(alpha_x), _ptr(alpha_y), nsweeps,
+                                     _ptr(hist), _ptr(acc), nthreads)
+        if rc:
+            raise ValueError(f"oracle_proxgrad failed ({rc})")
+        return X, Yt, alpha_x, alpha_y, hist, acc.reshape(nsweeps, 2)
+
+    def als(self, X, Yt, gamma: float, nsweeps: int, nthreads: int = 0):
+        """Alternating exact minimisation for quadratic loss + gamma||.||^2
+        (Algorithm 1; Sec. 2.4).  Returns (X, Yt, history)."""
+        X = np.array(X, dtype=np.float64, order="C")
+        Yt = np.array(Yt, dtype=np.float64, order="C")
+        hist = np.empty(nsweeps, dtype=np.float64)
+        rc = _load().oracle_als(*self._common(), gamma, _ptr(X), _ptr(Yt), nsweeps, _ptr(hist),
+                                nthreads)
+        if rc:
+            raise ValueError(f"oracle_als failed ({rc})")
+        return X, Yt, hist
+
+
+def num_threads(nthreads: int = 0) -> int:
+    """Threads the oracle's OpenMP loops use (after setting them, if > 0)."""
+    return _load().oracle_num_threads(nthreads)

@@ -1,0 +1,551 @@
+/*
+ * FP64 CPU oracle for the generalized low rank model (GLRM) fitting method of
+ * Udell, Horn, Zadeh and Boyd, "Generalized Low Rank Models" (arXiv 1410.0342).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA library is checked against.  It shares no code, header, table or helper
+ * with the CUDA library, and the product path never calls it: only the tests,
+ * the smoke check and the CPU-baseline leg of the benchmark load it.
+ *
+ * Problem (eq. gpca, Section 4; eq. apca, Section 5):
+ *     minimize  sum_{(i,j) in Omega} L_j(x_i . y_j, A_ij) + sum_i r(x_i) + sum_j rt(y_j)
+ * with X (m x k, rows x_i) and Y (k x n, columns y_j).  Y is held here as its
+ * transpose Yt (n x k, row j = y_j), both row-major.
+ *
+ * Everything is double precision, loops are plain and run in index order.
+ * OpenMP only spreads independent rows (X-step) or columns (Y-step) over
+ * threads, which the paper names as the natural parallelism of the method
+ * (Section 7.2, "Choosing a step size", last paragraph); every result is
+ * written to its own slot and every sum runs in a fixed order, so the output
+ * does not depend on the thread count.
+ *
+ * Readings of the paper taken where it is silent or inconsistent:
+ *  - quadratic loss is (u-a)^2 and the quadratic regulariser gamma*||x||^2
+ *    (eq. qpca, Section 2);
+ *  - Huber with threshold delta: 0.5 x^2 if |x| <= delta, else
+ *    delta*(|x| - delta/2); delta = 1 is the paper's function (Section 4.3);
+ *  - at a kink of the hinge / ordinal hinge a term's derivative is 0;
+ *  - Boolean data is coded -1/+1 and decodes to +1 when u >= 0;
+ *  - an ordinal decode tie goes to the smaller level;
+ *  - the step-size safeguard (Section 7.2) rejects a step that increases the
+ *    row (column) objective: the factor is kept and alpha shrinks by 0.7; a
+ *    step that does not increase it is kept and alpha grows by 1.05;
+ *  - alpha starts at 1/max(n_i, 1) (scale 1 divided by the observation count);
+ *  - the row objective uses the general regulariser r(x), which is +inf for
+ *    the nonnegativity indicator at an infeasible point.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { LOSS_QUAD = 0, LOSS_HUBER = 1, LOSS_HINGE = 2, LOSS_LOGISTIC = 3, LOSS_ORDINAL = 4 };
+enum { REG_ZERO = 0, REG_QUAD = 1, REG_L1 = 2, REG_NONNEG = 3 };
+
+static double pos(double v) { return v > 0.0 ? v : 0.0; }
+
+/* ---------------------------------------------------------------- losses */
+
+/* L(u, a).  Quadratic (eq. qpca), Huber (Section 4.3, "Huber PCA"), hinge
+ * (Section 5.2, "Boolean PCA"), logistic (Section 5.2, "Logistic PCA"),
+ * ordinal hinge (eq. ord-pca). */
+double oracle_loss(int kind, double param, int levels, double u, double a)
+{
+    switch (kind) {
+    case LOSS_QUAD:
+        return (u - a) * (u - a);
+    case LOSS_HUBER: {
+        double x = fabs(u - a), d = param;
+        return x <= d ? 0.5 * x * x : d * (x - 0.5 * d);
+    }
+    case LOSS_HINGE:
+        return pos(1.0 - a * u);
+    case LOSS_LOGISTIC: {
+        /* log(1 + exp(-a u)), evaluated without overflow */
+        double z = -a * u;
+        return z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
+    }
+    case LOSS_ORDINAL: {
+        double s = 0.0;
+        int lev = (int)a;
+        for (int ap = 1; ap <= lev - 1; ++ap) s += pos(1.0 - u + ap);
+        for (int ap = lev + 1; ap <= levels; ++ap) s += pos(1.0 + u - ap);
+        return s;
+    }
+    }
+    return NAN;
+}
+
+/* dL/du (a subgradient at kinks, taken as 0 there). */
+double oracle_dloss(int kind, double param, int levels, double u, double a)
+{
+    switch (kind) {
+    case LOSS_QUAD:
+        return 2.0 * (u - a);
+    case LOSS_HUBER: {
+        double x = u - a, d = param;
+        if (x > d) return d;
+        if (x < -d) return -d;
+        return x;
+    }
+    case LOSS_HINGE:
+        return (1.0 - a * u) > 0.0 ? -a : 0.0;
+    case LOSS_LOGISTIC:
+        /* d/du log(1+exp(-a u)) = -a / (1 + exp(a u)) */
+        return -a / (1.0 + exp(a * u));
+    case LOSS_ORDINAL: {
+        double s = 0.0;
+        int lev = (int)a;
+        for (int ap = 1; ap <= lev - 1; ++ap)
+            if (1.0 - u + ap > 0.0) s -= 1.0;
+        for (int ap = lev + 1; ap <= levels; ++ap)
+            if (1.0 + u - ap > 0.0) s += 1.0;
+        return s;
+    }
+    }
+    return NAN;
+}
+
+/* Imputation (Section 5.3): argmin over the loss's domain of L(u, a).
+ * Real-valued losses return u; Boolean losses return sign(u) with sign(0)=+1;
+ * the ordinal hinge is minimised by trying every level 1..d (ties to the
+ * smaller level). */
+double oracle_decode(int kind, int levels, double u)
+{
+    switch (kind) {
+    case LOSS_QUAD:
+    case LOSS_HUBER:
+        return u;
+    case LOSS_HINGE:
+    case LOSS_LOGISTIC:
+        return u >= 0.0 ? 1.0 : -1.0;
+    case LOSS_ORDINAL: {
+        int best = 1;
+        double bestv = oracle_loss(LOSS_ORDINAL, 0.0, levels, u, 1.0);
+        for (int a = 2; a <= levels; ++a) {
+            double v = oracle_loss(LOSS_ORDINAL, 0.0, levels, u, (double)a);
+            if (v < bestv) { bestv = v; best = a; }
+        }
+        return (double)best;
+    }
+    }
+    return NAN;
+}
+
+/* ----------------------------------------------------------- regularisers */
+
+/* r(x) for the quadratic (gamma ||x||^2, eq. qpca), l1 (lambda ||x||_1,
+ * Section 3.2 "Sparse PCA"), nonnegativity indicator (Section 3.2, "NNMF") and
+ * zero regularisers. */
+double oracle_reg(int kind, double w, int k, const double *x)
+{
+    double s = 0.0;
+    switch (kind) {
+    case REG_ZERO:
+        return 0.0;
+    case REG_QUAD:
+        for (int c = 0; c < k; ++c) s += x[c] * x[c];
+        return w * s;
+    case REG_L1:
+        for (int c = 0; c < k; ++c) s += fabs(x[c]);
+        return w * s;
+    case REG_NONNEG:
+        for (int c = 0; c < k; ++c)
+            if (x[c] < 0.0) return INFINITY;
+        return 0.0;
+    }
+    return NAN;
+}
+
+/* prox_{alpha r}(z) = argmin_x alpha r(x) + 0.5 ||x - z||^2 (Section 7.2,
+ * "Proximal gradient method").  All four regularisers are separable, so the
+ * minimiser is taken coordinate by coordinate:
+ *   quadratic:  alpha w x^2 + 0.5 (x-z)^2  ->  x = z / (1 + 2 alpha w)
+ *   l1:         alpha w |x| + 0.5 (x-z)^2  ->  soft threshold at alpha w
+ *   nonneg:     projection onto x >= 0     ->  max(z, 0)
+ *   zero:       x = z                                                    */
+void oracle_prox(int kind, double w, double alpha, int k, const double *z, double *out)
+{
+    for (int c = 0; c < k; ++c) {
+        double v = z[c];
+        switch (kind) {
+        case REG_ZERO:
+            out[c] = v;
+            break;
+        case REG_QUAD:
+            out[c] = v / (1.0 + 2.0 * alpha * w);
+            break;
+        case REG_L1: {
+            double t = alpha * w;
+            out[c] = v > t ? v - t : (v < -t ? v + t : 0.0);
+            break;
+        }
+        case REG_NONNEG:
+            out[c] = v > 0.0 ? v : 0.0;
+            break;
+        default:
+            out[c] = NAN;
+        }
+    }
+}
+
+/* ------------------------------------------------------------- Omega lists */
+
+/* The observed set is given as coordinate triples (row, col, value) sorted by
+ * row then column.  From it the oracle builds, by counting, its own list of
+ * the entries of every row (columns ascending) and of every column (rows
+ * ascending). */
+typedef struct {
+    int64_t m, n, nnz;
+    int64_t *rstart;  /* m+1 */
+    int32_t *rcol;    /* nnz, column of each entry of the row lists */
+    double *rval;
+    int64_t *cstart;  /* n+1 */
+    int32_t *crow;    /* nnz, row of each entry of the column lists */
+    double *cval;
+} omega_lists;
+
+static void lists_free(omega_lists *L)
+{
+    free(L->rstart); free(L->rcol); free(L->rval);
+    free(L->cstart); free(L->crow); free(L->cval);
+}
+
+static int lists_build(omega_lists *L, int64_t m, int64_t n, int64_t nnz,
+                       const int32_t *row, const int32_t *col, const double *val)
+{
+    L->m = m; L->n = n; L->nnz = nnz;
+    L->rstart = calloc((size_t)m + 1, sizeof(int64_t));
+    L->cstart = calloc((size_t)n + 1, sizeof(int64_t));
+    L->rcol = malloc(sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
+    L->rval = malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+    L->crow = malloc(sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
+    L->cval = malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+    if (!L->rstart || !L->cstart || !L->rcol || !L->rval || !L->crow || !L->cval) return -1;
+    for (int64_t e = 0; e < nnz; ++e) {
+        if (row[e] < 0 || row[e] >= m || col[e] < 0 || col[e] >= n) return -2;
+        L->rstart[row[e] + 1]++;
+        L->cstart[col[e] + 1]++;
+    }
+    for (int64_t i = 0; i < m; ++i) L->rstart[i + 1] += L->rstart[i];
+    for (int64_t j = 0; j < n; ++j) L->cstart[j + 1] += L->cstart[j];
+    int64_t *rfill = malloc(sizeof(int64_t) * (size_t)(m ? m : 1));
+    int64_t *cfill = malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    if (!rfill || !cfill) { free(rfill); free(cfill); return -1; }
+    memcpy(rfill, L->rstart, sizeof(int64_t) * (size_t)m);
+    memcpy(cfill, L->cstart, sizeof(int64_t) * (size_t)n);
+    /* entries arrive sorted by (row, col): the fills below keep each row's
+     * columns ascending and each column's rows ascending */
+    for (int64_t e = 0; e < nnz; ++e) {
+        int64_t p = rfill[row[e]]++;
+        L->rcol[p] = col[e];
+        L->rval[p] = val[e];
+        int64_t q = cfill[col[e]]++;
+        L->crow[q] = row[e];
+        L->cval[q] = val[e];
+    }
+    free(rfill); free(cfill);
+    return 0;
+}
+
+static double dot(int k, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int c = 0; c < k; ++c) s += a[c] * b[c];
+    return s;
+}
+
+/* Loss part of the objective of one factor vector v against the list of its
+ * observed entries: sum_e L(v . W[idx[e]], a[e]).  In the X-step v = x_i and
+ * W = Yt, and an entry's loss is that of its column idx[e]; in the Y-step
+ * v = y_j, W = X, and every entry uses column j's loss (fixed_col = j). */
+typedef struct {
+    const int32_t *kind;
+    const double *param;
+    const int32_t *levels;
+} loss_table;
+
+static double list_loss(int k, const double *v, const double *W, const int32_t *idx,
+                        const double *a, int64_t cnt, const loss_table *lt, int64_t fixed_col)
+{
+    double s = 0.0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        int64_t j = fixed_col >= 0 ? fixed_col : idx[e];
+        double u = dot(k, v, W + (int64_t)idx[e] * k);
+        s += oracle_loss(lt->kind[j], lt->param[j], lt->levels[j], u, a[e]);
+    }
+    return s;
+}
+
+/* One proximal-gradient update of v with the step-size safeguard
+ * (Section 7.2, "Proximal gradient method" and "Choosing a step size"):
+ *   g     = sum_e L'(v . w_e, a_e) w_e
+ *   v+    = prox_{alpha r}(v - alpha g)
+ *   keep v+ and alpha *= 1.05 if f(v+) <= f(v), else keep v and alpha *= 0.7,
+ * with f(v) = sum_e L(v . w_e, a_e) + r(v).
+ * Returns 1 when the step was accepted.  *fkept receives f of the kept vector. */
+static int update_vector(int k, double *v, double *alpha, const double *W, const int32_t *idx,
+                         const double *a, int64_t cnt, const loss_table *lt, int64_t fixed_col,
+                         int rkind, double rw, double *fkept, double *rkept)
+{
+    double g[k], z[k], vp[k];
+    for (int c = 0; c < k; ++c) g[c] = 0.0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        int64_t j = fixed_col >= 0 ? fixed_col : idx[e];
+        const double *w = W + (int64_t)idx[e] * k;
+        double u = dot(k, v, w);
+        double r = oracle_dloss(lt->kind[j], lt->param[j], lt->levels[j], u, a[e]);
+        for (int c = 0; c < k; ++c) g[c] += r * w[c];
+    }
+    for (int c = 0; c < k; ++c) z[c] = v[c] - (*alpha) * g[c];
+    oracle_prox(rkind, rw, *alpha, k, z, vp);
+    double r_old = oracle_reg(rkind, rw, k, v);
+    double r_new = oracle_reg(rkind, rw, k, vp);
+    double f_old = list_loss(k, v, W, idx, a, cnt, lt, fixed_col) + r_old;
+    double f_new = list_loss(k, vp, W, idx, a, cnt, lt, fixed_col) + r_new;
+    if (f_new <= f_old) {
+        for (int c = 0; c < k; ++c) v[c] = vp[c];
+        *alpha *= 1.05;
+        *fkept = f_new;
+        *rkept = r_new;
+        return 1;
+    }
+    *alpha *= 0.7;
+    *fkept = f_old;
+    *rkept = r_old;
+    return 0;
+}
+
+static int set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+/* Full objective (eq. gpca):  sum over Omega of L (rows ascending, then each
+ * row's columns ascending) + sum_i r(x_i) + sum_j rt(y_j). */
+static double objective_lists(const omega_lists *L, int k, const double *X, const double *Yt,
+                              const loss_table *lt, int rxk, double rxw, int ryk, double ryw)
+{
+    double *rowsum = malloc(sizeof(double) * (size_t)(L->m ? L->m : 1));
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (i = 0; i < L->m; ++i)
+        rowsum[i] = list_loss(k, X + i * k, Yt, L->rcol + L->rstart[i], L->rval + L->rstart[i],
+                              L->rstart[i + 1] - L->rstart[i], lt, -1);
+    double F = 0.0;
+    for (i = 0; i < L->m; ++i) F += rowsum[i];
+    for (i = 0; i < L->m; ++i) F += oracle_reg(rxk, rxw, k, X + i * k);
+    for (int64_t j = 0; j < L->n; ++j) F += oracle_reg(ryk, ryw, k, Yt + j * k);
+    free(rowsum);
+    return F;
+}
+
+double oracle_objective(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
+                        const int32_t *col, const double *val, const int32_t *lkind,
+                        const double *lparam, const int32_t *llevels, int rxk, double rxw,
+                        int ryk, double ryw, const double *X, const double *Yt, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    if (lists_build(&L, m, n, nnz, row, col, val)) { lists_free(&L); return NAN; }
+    set_threads(nthreads);
+    loss_table lt = { lkind, lparam, llevels };
+    double F = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw);
+    lists_free(&L);
+    return F;
+}
+
+/* Loss part of the gradient (Section 7.2, "Gradient method"):
+ *   GX[i] = sum_{j in Omega_i} L'_j(x_i . y_j, A_ij) y_j
+ *   GYt[j] = sum_{i in Omega_j} L'_j(x_i . y_j, A_ij) x_i               */
+int oracle_gradient(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
+                    const int32_t *col, const double *val, const int32_t *lkind,
+                    const double *lparam, const int32_t *llevels, const double *X,
+                    const double *Yt, double *GX, double *GYt, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    int rc = lists_build(&L, m, n, nnz, row, col, val);
+    if (rc) { lists_free(&L); return rc; }
+    set_threads(nthreads);
+    int64_t i, j;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (i = 0; i < m; ++i) {
+        double *g = GX + i * k;
+        for (int c = 0; c < k; ++c) g[c] = 0.0;
+        for (int64_t e = L.rstart[i]; e < L.rstart[i + 1]; ++e) {
+            int32_t jj = L.rcol[e];
+            double u = dot(k, X + i * k, Yt + (int64_t)jj * k);
+            double r = oracle_dloss(lkind[jj], lparam[jj], llevels[jj], u, L.rval[e]);
+            for (int c = 0; c < k; ++c) g[c] += r * Yt[(int64_t)jj * k + c];
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (j = 0; j < n; ++j) {
+        double *h = GYt + j * k;
+        for (int c = 0; c < k; ++c) h[c] = 0.0;
+        for (int64_t e = L.cstart[j]; e < L.cstart[j + 1]; ++e) {
+            int32_t ii = L.crow[e];
+            double u = dot(k, X + (int64_t)ii * k, Yt + j * k);
+            double r = oracle_dloss(lkind[j], lparam[j], llevels[j], u, L.cval[e]);
+            for (int c = 0; c < k; ++c) h[c] += r * X[(int64_t)ii * k + c];
+        }
+    }
+    lists_free(&L);
+    return 0;
+}
+
+/* Alternating proximal-gradient sweeps (Algorithm 2 with the proximal
+ * gradient update and the per-row/per-column step-size rule of Section 7.2).
+ * Sweep t updates every row x_i against Y^{t-1}, then every column y_j against
+ * the new X^t.  alpha_x (m) and alpha_y (n) carry the step sizes between
+ * calls; a caller starting a fit sets them to 1/max(n_i,1) and 1/max(m_j,1).
+ * history[t] receives the objective after sweep t; accepts[2t], accepts[2t+1]
+ * receive the number of accepted row and column steps of sweep t. */
+int oracle_proxgrad(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
+                    const int32_t *col, const double *val, const int32_t *lkind,
+                    const double *lparam, const int32_t *llevels, int rxk, double rxw, int ryk,
+                    double ryw, double *X, double *Yt, double *alpha_x, double *alpha_y,
+                    int nsweeps, double *history, int64_t *accepts, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    int rc = lists_build(&L, m, n, nnz, row, col, val);
+    if (rc) { lists_free(&L); return rc; }
+    set_threads(nthreads);
+    loss_table lt = { lkind, lparam, llevels };
+    double *fx = malloc(sizeof(double) * (size_t)(m ? m : 1));
+    double *rx = malloc(sizeof(double) * (size_t)(m ? m : 1));
+    double *fy = malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *ry = malloc(sizeof(double) * (size_t)(n ? n : 1));
+    int *ax = malloc(sizeof(int) * (size_t)(m ? m : 1));
+    int *ay = malloc(sizeof(int) * (size_t)(n ? n : 1));
+    for (int t = 0; t < nsweeps; ++t) {
+        int64_t i, j;
+#pragma omp parallel for schedule(dynamic, 64)
+        for (i = 0; i < m; ++i) {
+            int64_t b = L.rstart[i];
+            ax[i] = update_vector(k, X + i * k, alpha_x + i, Yt, L.rcol + b, L.rval + b,
+                                  L.rstart[i + 1] - b, &lt, -1, rxk, rxw, fx + i, rx + i);
+        }
+#pragma omp parallel for schedule(dynamic, 4)
+        for (j = 0; j < n; ++j) {
+            int64_t b = L.cstart[j];
+            ay[j] = update_vector(k, Yt + j * k, alpha_y + j, X, L.crow + b, L.cval + b,
+                                  L.cstart[j + 1] - b, &lt, j, ryk, ryw, fy + j, ry + j);
+        }
+        int64_t na = 0, nb = 0;
+        for (i = 0; i < m; ++i) na += ax[i];
+        for (j = 0; j < n; ++j) nb += ay[j];
+        if (accepts) { accepts[2 * t] = na; accepts[2 * t + 1] = nb; }
+        if (history)
+            history[t] = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw);
+    }
+    free(fx); free(rx); free(fy); free(ry); free(ax); free(ay);
+    lists_free(&L);
+    return 0;
+}
+
+/* Cholesky factorisation G = C C^T of a symmetric positive definite k x k
+ * matrix (lower triangle of C written over G), then the two triangular solves
+ * C w = b and C^T x = w.  Textbook column-by-column algorithm. */
+static int chol_solve(int k, double *G, double *b)
+{
+    for (int c = 0; c < k; ++c) {
+        double d = G[c * k + c];
+        for (int p = 0; p < c; ++p) d -= G[c * k + p] * G[c * k + p];
+        if (!(d > 0.0)) return -1;
+        d = sqrt(d);
+        G[c * k + c] = d;
+        for (int r = c + 1; r < k; ++r) {
+            double s = G[r * k + c];
+            for (int p = 0; p < c; ++p) s -= G[r * k + p] * G[c * k + p];
+            G[r * k + c] = s / d;
+        }
+    }
+    for (int r = 0; r < k; ++r) {
+        double s = b[r];
+        for (int p = 0; p < r; ++p) s -= G[r * k + p] * b[p];
+        b[r] = s / G[r * k + r];
+    }
+    for (int r = k - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int p = r + 1; p < k; ++p) s -= G[p * k + r] * b[p];
+        b[r] = s / G[r * k + r];
+    }
+    return 0;
+}
+
+/* Exact minimisation of sum_e (v . w_e - a_e)^2 + gamma ||v||^2 over v:
+ * (sum_e w_e w_e^T + gamma I) v = sum_e a_e w_e  (Section 2.4, "Parallelizing
+ * alternating minimization" and "Caching factorizations", with the Gram matrix
+ * restricted to the observed entries as in Section 2.5). */
+static int solve_vector(int k, double *v, const double *W, const int32_t *idx, const double *a,
+                        int64_t cnt, double gamma)
+{
+    double G[k * k], b[k];
+    for (int p = 0; p < k * k; ++p) G[p] = 0.0;
+    for (int c = 0; c < k; ++c) b[c] = 0.0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        const double *w = W + (int64_t)idx[e] * k;
+        for (int r = 0; r < k; ++r) {
+            b[r] += a[e] * w[r];
+            for (int c = 0; c < k; ++c) G[r * k + c] += w[r] * w[c];
+        }
+    }
+    for (int c = 0; c < k; ++c) G[c * k + c] += gamma;
+    if (chol_solve(k, G, b)) return -1;
+    for (int c = 0; c < k; ++c) v[c] = b[c];
+    return 0;
+}
+
+/* Alternating minimisation for quadratic loss and quadratic regularisation
+ * (Algorithm 1 with the closed-form row and column problems): every x_i is
+ * the exact minimiser against Y^{t-1}, then every y_j against X^t.
+ * history[t] receives the objective (quadratic loss, gamma ||.||^2 on both
+ * factors) after sweep t. */
+int oracle_als(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row, const int32_t *col,
+               const double *val, double gamma, double *X, double *Yt, int nsweeps,
+               double *history, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    int rc = lists_build(&L, m, n, nnz, row, col, val);
+    if (rc) { lists_free(&L); return rc; }
+    set_threads(nthreads);
+    int32_t *kind = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    double *param = malloc(sizeof(double) * (size_t)(n ? n : 1));
+    int32_t *lev = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    for (int64_t j = 0; j < n; ++j) { kind[j] = LOSS_QUAD; param[j] = 0.0; lev[j] = 0; }
+    loss_table lt = { kind, param, lev };
+    int bad = 0;
+    for (int t = 0; t < nsweeps && !bad; ++t) {
+        int64_t i, j;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+        for (i = 0; i < m; ++i) {
+            int64_t b = L.rstart[i];
+            bad |= solve_vector(k, X + i * k, Yt, L.rcol + b, L.rval + b, L.rstart[i + 1] - b, gamma) != 0;
+        }
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+        for (j = 0; j < n; ++j) {
+            int64_t b = L.cstart[j];
+            bad |= solve_vector(k, Yt + j * k, X, L.crow + b, L.cval + b, L.cstart[j + 1] - b, gamma) != 0;
+        }
+        if (history)
+            history[t] = objective_lists(&L, k, X, Yt, &lt, REG_QUAD, gamma, REG_QUAD, gamma);
+    }
+    free(kind); free(param); free(lev);
+    lists_free(&L);
+    return bad ? -3 : 0;
+}
+
+int oracle_num_threads(int nthreads) { return set_threads(nthreads); }

@@ -1,0 +1,276 @@
+"""Seeded synthetic GLRM workloads.
+
+This module only draws data: latent factors, observed sets, table values and
+initial factors.  It holds none of the fitting method's arithmetic and is the
+one piece of code that both the CUDA library's tests and the FP64 oracle's
+tests use, so that both sides see identical inputs.
+
+The shapes follow the paper's synthetic experiments (Udell et al., "Generalized
+Low Rank Models"): Gaussian low-rank tables with noise (Sec. 6.1 mixed data,
+Sec. 7.3 qPCA convergence), entries observed uniformly at random, Boolean data
+as signs of a noisy low-rank matrix (Sec. 6.1), and Spark's random sparse
+matrices with a fixed count of nonzeros per row (Sec. 9.3), scaled up.
+
+Every table is returned as ``Table``: Omega in CSR (rowptr, colidx, val) and
+CSC (colptr, rowidx, val) int32/float32 form plus per-column loss kinds,
+parameters and level counts, the regularisers and the initial factors.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+LOSS_QUAD, LOSS_HUBER, LOSS_HINGE, LOSS_LOGISTIC, LOSS_ORDINAL = 0, 1, 2, 3, 4
+REG_ZERO, REG_QUAD, REG_L1, REG_NONNEG = 0, 1, 2, 3
+
+BASE_SEED = 1410034200
+
+
+@dataclasses.dataclass
+class Table:
+    name: str
+    m: int
+    n: int
+    k: int
+    rowptr: np.ndarray      # int64 [m+1]
+    colidx: np.ndarray      # int32 [nnz]
+    val: np.ndarray         # float64 [nnz], CSR order
+    colptr: np.ndarray      # int64 [n+1]
+    rowidx: np.ndarray      # int32 [nnz]
+    cval: np.ndarray        # float64 [nnz], CSC order
+    loss_kind: np.ndarray   # int32 [n]
+    loss_param: np.ndarray  # float64 [n]
+    loss_levels: np.ndarray  # int32 [n]
+    rx: tuple
+    ry: tuple
+    X0: np.ndarray          # float64 [m, k] initial X
+    Yt0: np.ndarray         # float64 [n, k] initial Y^T
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.size)
+
+    def rows(self) -> np.ndarray:
+        """Row index of every entry in CSR order."""
+        return np.repeat(np.arange(self.m, dtype=np.int32), np.diff(self.rowptr))
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def csc_from_csr(m, n, rowptr, colidx, val):
+    """Reorder CSR entries by column (stable, so rows stay ascending)."""
+    order = np.argsort(colidx, kind="stable")
+    rows = np.repeat(np.arange(m, dtype=np.int32), np.diff(rowptr))
+    colptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(colidx, minlength=n), out=colptr[1:])
+    return colptr, rows[order].astype(np.int32), val[order]
+
+
+def omega_bernoulli(m: int, n: int, p: float, rng: np.random.Generator, block: int = 4096):
+    """Each cell observed independently with probability p; CSR with sorted columns."""
+    counts = np.empty(m, dtype=np.int64)
+    cols = []
+    for r0 in range(0, m, block):
+        r1 = min(m, r0 + block)
+        mask = rng.random((r1 - r0, n)) < p
+        counts[r0:r1] = mask.sum(axis=1)
+        cols.append(np.nonzero(mask)[1].astype(np.int32))
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    colidx = np.concatenate(cols) if cols else np.zeros(0, dtype=np.int32)
+    return rowptr, colidx
+
+
+def omega_fixed_per_row(m: int, n: int, r: int, rng: np.random.Generator, block: int = 65536):
+    """Exactly r distinct columns per row, each r-subset equally likely:
+    draw columns with replacement, keep the first r distinct in draw order."""
+    assert r <= n
+    draw = r + max(16, int(3 * np.sqrt(r * r * r / max(n, 1))) + 8)
+    rowptr = np.arange(m + 1, dtype=np.int64) * r
+    colidx = np.empty(m * r, dtype=np.int32)
+    for r0 in range(0, m, block):
+        r1 = min(m, r0 + block)
+        rows = r1 - r0
+        out = np.empty((rows, r), dtype=np.int32)
+        todo = np.arange(rows)
+        while todo.size:
+            d = rng.integers(0, n, size=(todo.size, draw), dtype=np.int64)
+            order = np.argsort(d, axis=1, kind="stable")
+            sd = np.take_along_axis(d, order, axis=1)
+            dup_sorted = np.zeros_like(sd, dtype=bool)
+            dup_sorted[:, 1:] = sd[:, 1:] == sd[:, :-1]
+            dup = np.empty_like(dup_sorted)
+            np.put_along_axis(dup, order, dup_sorted, axis=1)
+            keep = ~dup
+            ok = keep.sum(axis=1) >= r
+            good = todo[ok]
+            if good.size:
+                kk = keep[ok]
+                pos = np.cumsum(kk, axis=1)
+                sel = kk & (pos <= r)
+                vals = d[ok][sel].reshape(good.size, r)
+                out[good] = np.sort(vals, axis=1).astype(np.int32)
+            todo = todo[~ok]
+        colidx[r0 * r:r1 * r] = out.reshape(-1)
+    return rowptr, colidx
+
+
+def sampled_products(X0: np.ndarray, Y0t: np.ndarray, rowptr, colidx, chunk: int = 1 << 22):
+    """(X0 Y0)_ij for the observed entries in CSR order, to synthesise data."""
+    m = X0.shape[0]
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rowptr))
+    out = np.empty(colidx.size, dtype=np.float64)
+    for e0 in range(0, colidx.size, chunk):
+        e1 = min(colidx.size, e0 + chunk)
+        out[e0:e1] = np.einsum("ek,ek->e", X0[rows[e0:e1]], Y0t[colidx[e0:e1]])
+    return out
+
+
+def _finish(name, m, n, k, rowptr, colidx, val, kind, param, levels, rx, ry, rng, init_std=1.0):
+    colptr, rowidx, cval = csc_from_csr(m, n, rowptr, colidx, val)
+    X0 = rng.standard_normal((m, k)) * init_std
+    Yt0 = rng.standard_normal((n, k)) * init_std
+    return Table(name, m, n, k, rowptr, colidx.astype(np.int32), val.astype(np.float64),
+                 colptr, rowidx, cval.astype(np.float64),
+                 np.asarray(kind, dtype=np.int32), np.asarray(param, dtype=np.float64),
+                 np.asarray(levels, dtype=np.int32), rx, ry, X0, Yt0)
+
+
+# --------------------------------------------------------------- the tables
+
+def qpca_dense(m=200, n=100, k=5, gamma=0.1, noise=0.1, seed=BASE_SEED + 1, name="qpca_dense"):
+    """Fully observed A = X0 Y0 + N(0, noise^2), quadratic loss, gamma||.||^2
+    on both factors (the paper's qPCA experiment shape, Sec. 7.3)."""
+    rng = rng_for(seed)
+    X0 = rng.standard_normal((m, k))
+    Y0 = rng.standard_normal((k, n))
+    A = X0 @ Y0 + noise * rng.standard_normal((m, n))
+    rowptr = np.arange(m + 1, dtype=np.int64) * n
+    colidx = np.tile(np.arange(n, dtype=np.int32), m)
+    return _finish(name, m, n, k, rowptr, colidx, A.reshape(-1),
+                   np.full(n, LOSS_QUAD), np.zeros(n), np.zeros(n),
+                   (REG_QUAD, gamma), (REG_QUAD, gamma), rng)
+
+
+def mixed(m=100_000, n=1000, k=20, n_real=500, n_bool=300, levels=7, p_obs=0.6,
+          seed=BASE_SEED + 2, name="mixed", lam=0.01):
+    """Mixed-type table (Sec. 6.1 shape, scaled up): real columns with Huber
+    loss (Laplace(0, 0.5) noise, 1% of entries with noise x20), Boolean columns
+    sign(X0 Y0 + N(0, 0.5^2)) with hinge loss, ordinal columns binned at the
+    column's empirical septiles with the ordinal hinge; cells observed with
+    probability p_obs; l1 (lambda) on X, nonnegativity on Y."""
+    rng = rng_for(seed)
+    n_ord = n - n_real - n_bool
+    assert n_ord >= 0
+    X0 = rng.standard_normal((m, k))
+    Y0t = rng.standard_normal((n, k))
+    rowptr, colidx = omega_bernoulli(m, n, p_obs, rng)
+    u = sampled_products(X0, Y0t, rowptr, colidx)
+    val = np.empty_like(u)
+    real = colidx < n_real
+    boo = (colidx >= n_real) & (colidx < n_real + n_bool)
+    ordi = colidx >= n_real + n_bool
+    nr = int(real.sum())
+    noise = rng.laplace(0.0, 0.5, size=nr)
+    outl = rng.random(nr) < 0.01
+    noise[outl] *= 20.0
+    val[real] = u[real] + noise
+    z = u[boo] + 0.5 * rng.standard_normal(int(boo.sum()))
+    val[boo] = np.where(z >= 0.0, 1.0, -1.0)
+    if n_ord:
+        # septile edges of each ordinal column of X0 Y0 over all m rows
+        ocols = np.arange(n_real + n_bool, n)
+        edges = np.empty((n_ord, levels - 1))
+        qs = np.arange(1, levels) / levels
+        for c0 in range(0, n_ord, 64):
+            c1 = min(n_ord, c0 + 64)
+            full = X0 @ Y0t[ocols[c0:c1]].T
+            edges[c0:c1] = np.quantile(full, qs, axis=0).T
+        oc = colidx[ordi] - (n_real + n_bool)
+        uo = u[ordi]
+        lev = np.ones(uo.size)
+        for q in range(levels - 1):
+            lev += uo > edges[oc, q]
+        val[ordi] = lev
+    kind = np.concatenate([np.full(n_real, LOSS_HUBER), np.full(n_bool, LOSS_HINGE),
+                           np.full(n_ord, LOSS_ORDINAL)])
+    param = np.concatenate([np.full(n_real, 1.0), np.zeros(n_bool), np.zeros(n_ord)])
+    lv = np.concatenate([np.zeros(n_real), np.zeros(n_bool), np.full(n_ord, levels)])
+    return _finish(name, m, n, k, rowptr, colidx, val, kind, param, lv,
+                   (REG_L1, lam), (REG_NONNEG, 0.0), rng)
+
+
+def completion(m=1_000_000, n=20_000, k=64, per_row=200, gamma=0.05, noise=0.1,
+               seed=BASE_SEED + 3, name="completion"):
+    """Matrix completion: exactly per_row uniform columns per row,
+    A = X0 Y0 + N(0, noise^2) with X0, Y0 entries of variance 1/sqrt(k),
+    quadratic loss, gamma||.||^2 on both factors."""
+    rng = rng_for(seed)
+    sd = k ** -0.25
+    X0 = rng.standard_normal((m, k)) * sd
+    Y0t = rng.standard_normal((n, k)) * sd
+    rowptr, colidx = omega_fixed_per_row(m, n, per_row, rng)
+    val = sampled_products(X0, Y0t, rowptr, colidx) + noise * rng.standard_normal(colidx.size)
+    return _finish(name, m, n, k, rowptr, colidx, val, np.full(n, LOSS_QUAD), np.zeros(n),
+                   np.zeros(n), (REG_QUAD, gamma), (REG_QUAD, gamma), rng, init_std=sd)
+
+
+def logistic_bool(m=50_000, n=2000, k=32, p_obs=0.8, gamma=0.1, seed=BASE_SEED + 4,
+                  name="logistic"):
+    """Boolean table A_ij = +1 with probability sigma(x0_i . y0_j), else -1;
+    cells observed with probability p_obs; logistic loss, gamma||.||^2."""
+    rng = rng_for(seed)
+    X0 = rng.standard_normal((m, k))
+    Y0t = rng.standard_normal((n, k))
+    rowptr, colidx = omega_bernoulli(m, n, p_obs, rng)
+    u = sampled_products(X0, Y0t, rowptr, colidx)
+    prob = 1.0 / (1.0 + np.exp(-u))
+    val = np.where(rng.random(u.size) < prob, 1.0, -1.0)
+    return _finish(name, m, n, k, rowptr, colidx, val, np.full(n, LOSS_LOGISTIC), np.zeros(n),
+                   np.zeros(n), (REG_QUAD, gamma), (REG_QUAD, gamma), rng)
+
+
+def batch_instance(s: int, seed=BASE_SEED + 5, m_range=(50, 5000), n_range=(20, 500),
+                   ks=(4, 8, 16), p_obs=0.7, gamma=0.1, noise=0.2):
+    """Instance s of the batched workload: m, n uniform in their ranges, k
+    uniform over ks; even s quadratic loss, odd s Huber (delta = 1); A =
+    X0 Y0 + N(0, noise^2); cells observed with probability p_obs."""
+    rng = rng_for(seed + s)
+    m = int(rng.integers(m_range[0], m_range[1] + 1))
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    k = int(ks[int(rng.integers(0, len(ks)))])
+    X0 = rng.standard_normal((m, k))
+    Y0t = rng.standard_normal((n, k))
+    rowptr, colidx = omega_bernoulli(m, n, p_obs, rng)
+    val = sampled_products(X0, Y0t, rowptr, colidx) + noise * rng.standard_normal(colidx.size)
+    kind = LOSS_QUAD if s % 2 == 0 else LOSS_HUBER
+    return _finish(f"batch{s}", m, n, k, rowptr, colidx, val, np.full(n, kind),
+                   np.full(n, 1.0 if kind == LOSS_HUBER else 0.0), np.zeros(n),
+                   (REG_QUAD, gamma), (REG_QUAD, gamma), rng)
+
+
+def small_mixed(m=97, n=41, k=6, p_obs=0.55, seed=BASE_SEED + 20, rx=(REG_L1, 0.05),
+                ry=(REG_NONNEG, 0.0), levels=5):
+    """A small mixed table with every loss kind, for parity on ragged shapes."""
+    rng = rng_for(seed)
+    X0 = rng.standard_normal((m, k))
+    Y0t = rng.standard_normal((n, k))
+    rowptr, colidx = omega_bernoulli(m, n, p_obs, rng)
+    u = sampled_products(X0, Y0t, rowptr, colidx)
+    kinds = np.arange(n) % 5
+    val = np.empty_like(u)
+    ke = kinds[colidx]
+    val[ke == LOSS_QUAD] = u[ke == LOSS_QUAD] + 0.1 * rng.standard_normal(int((ke == 0).sum()))
+    sel = ke == LOSS_HUBER
+    val[sel] = u[sel] + rng.laplace(0.0, 0.5, int(sel.sum()))
+    for kk in (LOSS_HINGE, LOSS_LOGISTIC):
+        sel = ke == kk
+        val[sel] = np.where(u[sel] + 0.5 * rng.standard_normal(int(sel.sum())) >= 0, 1.0, -1.0)
+    sel = ke == LOSS_ORDINAL
+    val[sel] = np.clip(np.round(u[sel] / 2.0 + (levels + 1) / 2.0), 1, levels)
+    param = np.where(kinds == LOSS_HUBER, 1.0, 0.0)
+    lv = np.where(kinds == LOSS_ORDINAL, levels, 0)
+    return _finish("small_mixed", m, n, k, rowptr, colidx, val, kinds, param, lv, rx, ry, rng)

@@ -1,0 +1,213 @@
+"""Pins of the oracle's objective, gradient, proximal-gradient sweep and
+alternating-minimisation sweep against what the paper fixes: the quadratically
+regularised PCA closed form (eq. pca-reg-soln; Appendix A), Eckart-Young
+(Sec. 2.4), X^T X = Y Y^T at stationary points (Appendix A), the monotone
+objective the step-size safeguard guarantees (Sec. 7.2), finite-difference
+gradients and the l1 optimality conditions."""
+import numpy as np
+import pytest
+
+from paper_1410_0342_gb300 import workloads as W
+
+Q, HU, HI, LO, OR = 0, 1, 2, 3, 4
+RZ, RQ, RL1, RNN = 0, 1, 2, 3
+
+
+def _problem(o, t: W.Table, rx=None, ry=None):
+    return o.Problem.from_csr(t.m, t.n, t.k, t.rowptr, t.colidx, t.val, loss_kind=t.loss_kind,
+                              loss_param=t.loss_param, loss_levels=t.loss_levels,
+                              rx=rx or t.rx, ry=ry or t.ry)
+
+
+def qpca_optimum(A, k, gamma):
+    """min ||A - XY||_F^2 + gamma(||X||^2 + ||Y||^2) = ||A||^2 - sum_{i<=k} ((s_i - gamma)_+)^2."""
+    s = np.linalg.svd(A, compute_uv=False)
+    return float(np.sum(A * A) - np.sum(np.maximum(s[:k] - gamma, 0.0) ** 2))
+
+
+def test_objective_matches_matrix_form(oracle_mod):
+    """Fully observed quadratic problem: the entry sum equals the matrix form."""
+    o = oracle_mod
+    t = W.qpca_dense(m=23, n=17, k=3, seed=7)
+    p = _problem(o, t)
+    A = t.val.reshape(t.m, t.n)
+    X, Yt = t.X0, t.Yt0
+    ref = np.sum((A - X @ Yt.T) ** 2) + 0.1 * np.sum(X * X) + 0.1 * np.sum(Yt * Yt)
+    assert p.objective(X, Yt) == pytest.approx(ref, rel=1e-13)
+
+
+def test_objective_brute_force_mixed(oracle_mod):
+    """Every loss kind and regulariser, summed cell by cell over a dense mask."""
+    o = oracle_mod
+    t = W.small_mixed(m=13, n=11, k=3, seed=3, rx=(RL1, 0.2), ry=(RQ, 0.3))
+    p = _problem(o, t)
+    rows = t.rows()
+    X, Yt = t.X0, t.Yt0
+    tot = 0.0
+    for e in range(t.nnz):
+        i, j, a = rows[e], t.colidx[e], t.val[e]
+        u = float(X[i] @ Yt[j])
+        tot += o.loss(int(t.loss_kind[j]), u, a, float(t.loss_param[j]), int(t.loss_levels[j]))
+    tot += 0.2 * np.abs(X).sum() + 0.3 * np.sum(Yt * Yt)
+    assert p.objective(X, Yt) == pytest.approx(tot, rel=1e-12)
+
+
+def test_gradient_matches_finite_differences(oracle_mod):
+    """Loss part of the gradient against central differences of the loss part
+    of the objective (zero regularisers), away from kinks."""
+    o = oracle_mod
+    t = W.small_mixed(m=9, n=10, k=3, seed=5, rx=(RZ, 0.0), ry=(RZ, 0.0))
+    # drop the kinked losses' kinks by using smooth kinds only
+    kinds = np.array([Q, HU, LO, Q, HU, LO, Q, HU, LO, Q], dtype=np.int32)
+    rows = t.rows()
+    vals = t.val.copy()
+    for e in range(t.nnz):
+        if kinds[t.colidx[e]] == LO:
+            vals[e] = 1.0 if vals[e] > 0 else -1.0
+    p = o.Problem(t.m, t.n, t.k, rows, t.colidx, vals, kinds, np.full(t.n, 0.7), 0)
+    X, Yt = t.X0.copy(), t.Yt0.copy()
+    GX, GYt = p.gradient(X, Yt)
+    h = 1e-6
+    for i in range(t.m):
+        for c in range(t.k):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[i, c] += h
+            Xm[i, c] -= h
+            fd = (p.objective(Xp, Yt) - p.objective(Xm, Yt)) / (2 * h)
+            assert GX[i, c] == pytest.approx(fd, abs=2e-5, rel=1e-5)
+    for j in range(t.n):
+        for c in range(t.k):
+            Yp, Ym = Yt.copy(), Yt.copy()
+            Yp[j, c] += h
+            Ym[j, c] -= h
+            fd = (p.objective(X, Yp) - p.objective(X, Ym)) / (2 * h)
+            assert GYt[j, c] == pytest.approx(fd, abs=2e-5, rel=1e-5)
+
+
+def test_proxgrad_reaches_qpca_closed_form(oracle_mod):
+    """Sweeps on the 200x100, k=5, gamma=0.1 qPCA table reach the closed-form
+    optimum (unique local minimum, Appendix A) and X^T X = Y Y^T there."""
+    o = oracle_mod
+    t = W.qpca_dense()
+    p = _problem(o, t)
+    A = t.val.reshape(t.m, t.n)
+    fstar = qpca_optimum(A, t.k, 0.1)
+    X, Yt, ax, ay, hist, acc = p.proxgrad(t.X0, t.Yt0, 3000)
+    assert np.all(np.diff(hist) <= 1e-9 * np.abs(hist[1:]))
+    assert (hist[-1] - fstar) / fstar < 1e-8
+    np.testing.assert_allclose(X.T @ X, Yt.T @ Yt, atol=1e-4 * np.abs(X.T @ X).max())
+
+
+def test_proxgrad_eckart_young(oracle_mod):
+    """gamma = 0: the optimum is the truncated-SVD error sum_{i>k} s_i^2."""
+    o = oracle_mod
+    t = W.qpca_dense(m=40, n=30, k=3, seed=11)
+    p = _problem(o, t, rx=(RZ, 0.0), ry=(RZ, 0.0))
+    A = t.val.reshape(t.m, t.n)
+    s = np.linalg.svd(A, compute_uv=False)
+    ey = float(np.sum(s[t.k:] ** 2))
+    *_, hist, _ = p.proxgrad(t.X0, t.Yt0, 6000)
+    assert (hist[-1] - ey) / ey < 1e-6
+
+
+def test_proxgrad_monotone_mixed(oracle_mod):
+    """The safeguard rejects increasing steps, so the objective never rises
+    (Sec. 7.2); nonnegativity holds on Y after the first sweep."""
+    o = oracle_mod
+    t = W.small_mixed()
+    p = _problem(o, t)
+    X, Yt, ax, ay, hist, acc = p.proxgrad(t.X0, t.Yt0, 60)
+    assert np.all(np.isfinite(hist))
+    assert np.all(np.diff(hist) <= 1e-12 * np.abs(hist[1:]))
+    assert Yt.min() >= 0.0
+    assert acc[0, 1] == t.n  # first Y-step leaves an infinite objective: all accepted
+    # the returned objective is the objective of the returned factors
+    assert p.objective(X, Yt) == pytest.approx(hist[-1], rel=1e-13)
+
+
+def test_proxgrad_thread_count_invariant(oracle_mod):
+    o = oracle_mod
+    t = W.small_mixed(m=120, n=50, seed=9)
+    p = _problem(o, t)
+    r1 = p.proxgrad(t.X0, t.Yt0, 7, nthreads=1)
+    r4 = p.proxgrad(t.X0, t.Yt0, 7, nthreads=4)
+    for a, b in zip(r1, r4):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_proxgrad_step_rule_single_row(oracle_mod):
+    """A single fully observed row: the X-step of the first sweep can be
+    followed by hand (gradient, prox of gamma||x||^2, accept test, alpha
+    update), and the result must match the oracle's."""
+    o = oracle_mod
+    rng = np.random.default_rng(4)
+    k, n = 3, 6
+    Yt = rng.normal(size=(n, k))
+    a = rng.normal(size=n)
+    x = rng.normal(size=(1, k))
+    p = o.Problem(1, n, k, np.zeros(n, np.int32), np.arange(n, dtype=np.int32), a,
+                  np.full(n, Q), 0.0, 0, rx=(RQ, 0.2), ry=(RZ, 0.0))
+    # the expected X-step: g = sum 2(u - a) y_j; z = x - g/n; prox; accept test
+    alpha = 1.0 / n
+    u = Yt @ x[0]
+    g = (2 * (u - a)) @ Yt
+    xp = (x[0] - alpha * g) / (1 + 2 * alpha * 0.2)
+    fo = np.sum((u - a) ** 2) + 0.2 * x[0] @ x[0]
+    fn = np.sum((Yt @ xp - a) ** 2) + 0.2 * xp @ xp
+    X1, Yt1, ax, ay, hist, acc = p.proxgrad(x, Yt, 1)
+    if fn <= fo:
+        np.testing.assert_allclose(X1[0], xp, rtol=1e-13)
+        assert ax[0] == pytest.approx(alpha * 1.05)
+    else:
+        np.testing.assert_array_equal(X1[0], x[0])
+        assert ax[0] == pytest.approx(alpha * 0.7)
+
+
+def test_proxgrad_l1_optimality(oracle_mod):
+    """At convergence with l1 on X, every row meets 0 in g_i + lambda d|x_i|:
+    g_ic = -lambda sign(x_ic) where x_ic != 0 and |g_ic| <= lambda where 0."""
+    o = oracle_mod
+    t = W.qpca_dense(m=30, n=20, k=3, seed=13)
+    lam = 2.0
+    p = _problem(o, t, rx=(RL1, lam), ry=(RQ, 0.1))
+    X, Yt, *_ = p.proxgrad(t.X0, t.Yt0, 20000)
+    GX, _ = p.gradient(X, Yt)
+    nz = np.abs(X) > 1e-9
+    assert nz.any() and (~nz).any()
+    np.testing.assert_allclose(GX[nz], -lam * np.sign(X[nz]), atol=1e-4)
+    assert np.all(np.abs(GX[~nz]) <= lam + 1e-4)
+
+
+def test_als_normal_equations(oracle_mod):
+    """One ALS sweep: each x_i solves (sum y_j y_j^T + gamma I) x = sum a_ij y_j
+    (Sec. 2.4) with the old Y; each y_j then solves its equations with the new X."""
+    o = oracle_mod
+    t = W.small_mixed(m=15, n=12, k=4, seed=21, p_obs=0.6)
+    gamma = 0.3
+    rows = t.rows()
+    p = o.Problem(t.m, t.n, t.k, rows, t.colidx, t.val, np.full(t.n, Q), 0.0, 0,
+                  rx=(RQ, gamma), ry=(RQ, gamma))
+    X1, Yt1, hist = p.als(t.X0, t.Yt0, gamma, 1)
+    for i in range(t.m):
+        sel = rows == i
+        Yi = t.Yt0[t.colidx[sel]]
+        G = Yi.T @ Yi + gamma * np.eye(t.k)
+        np.testing.assert_allclose(X1[i], np.linalg.solve(G, Yi.T @ t.val[sel]), rtol=1e-10,
+                                   atol=1e-12)
+    for j in range(t.n):
+        sel = t.colidx == j
+        Xj = X1[rows[sel]]
+        G = Xj.T @ Xj + gamma * np.eye(t.k)
+        np.testing.assert_allclose(Yt1[j], np.linalg.solve(G, Xj.T @ t.val[sel]), rtol=1e-10,
+                                   atol=1e-12)
+
+
+def test_als_reaches_qpca_closed_form(oracle_mod):
+    o = oracle_mod
+    t = W.qpca_dense()
+    p = _problem(o, t)
+    A = t.val.reshape(t.m, t.n)
+    fstar = qpca_optimum(A, t.k, 0.1)
+    X, Yt, hist = p.als(t.X0, t.Yt0, 0.1, 5000)
+    assert np.all(np.diff(hist) <= 1e-10 * np.abs(hist[1:]))
+    assert (hist[-1] - fstar) / fstar < 1e-9
