@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput of the GLRM alternating proximal-gradient sweep on one GB300.
+
+A step is one full sweep (X-step over all rows, Y-step over all columns, FP64
+objective) of the mixed-type table: m = 100,000 rows, n = 1,000 columns,
+k = 20; 500 Huber, 300 hinge (Boolean) and 200 ordinal-hinge (7 levels)
+columns; 40% of cells missing at random (|Omega| ~ 6.0e7); l1 (0.01) on X,
+nonnegativity on Y; FP32.  The metric is observed entries per second per
+sweep.  The inputs (CSR + CSC, ~0.96 GB) are larger than L2, so no L2 flush
+is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) run independent replicas of the
+same fit; value is the entries all ranks processed over the slowest rank's
+time.  --impl reference times the FP64 CPU oracle (the correctness
+reference, not a tuned program) on a row sample of the same table.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1410_0342_gb300 import workloads as W  # noqa: E402
+
+METRIC = "observed entries/s per alternating prox-grad sweep"
+UNIT = "entries/s"
+WORKLOAD = "mixed-type table m=100000 n=1000 k=20 (500 Huber, 300 hinge, 200 ordinal d=7), " \
+           "40% missing, l1(0.01) on X, nonneg on Y, FP32"
+ORACLE_SAMPLE_ROWS = 10_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="glrm", choices=["glrm", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.file.read())) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4)
+                          if r[5 + q].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1410_0342_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if it
+    was taken from the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_digest") != source_digest():
+        return None
+    v = d.get("bytes_per_launch", {}).get(kernel)
+    return float(v) if v is not None else None
+
+
+def algorithmic_bytes(name: str, t: W.Table, k: int) -> float:
+    """Bytes a kernel must move at minimum per launch (FP32 values, int32
+    indices): each observed entry's index and value once, each factor row it
+    reads or writes once, and its per-chunk / per-segment partials."""
+    nnz, m, n = t.nnz, t.m, t.n
+    fb = 4 * k
+    x = name.endswith("_x")
+    nseg, other = (m, n) if x else (n, m)
+    nchunks = nnz / 1024 + nseg  # upper bound on chunks, partials are small
+    if name.startswith("pass_grad"):
+        return nnz * 8 + (nseg + other) * fb + nchunks * (fb + 8)
+    if name.startswith("pass_loss"):
+        return nnz * 8 + (nseg + other) * fb + nchunks * 8
+    if name.startswith("prox"):
+        return nchunks * (fb + 8) + nseg * (2 * fb + 4 + 24)
+    if name.startswith("decide"):
+        return nchunks * 8 + nseg * (2 * fb + 4 + 48)
+    return 0.0
+
+
+def table_rows(t: W.Table, rows: int) -> W.Table:
+    """The first `rows` rows of a table with all their entries (a sample of
+    the same workload for the CPU oracle)."""
+    e = int(t.rowptr[rows])
+    rowptr = t.rowptr[:rows + 1].copy()
+    colidx = t.colidx[:e]
+    val = t.val[:e]
+    colptr, rowidx, cval = W.csc_from_csr(rows, t.n, rowptr, colidx, val)
+    return W.Table(t.name + f"[:{rows}]", rows, t.n, t.k, rowptr, colidx, val, colptr, rowidx,
+                   cval, t.loss_kind, t.loss_param, t.loss_levels, t.rx, t.ry, t.X0[:rows],
+                   t.Yt0)
+
+
+def oracle_rate(t: W.Table, steps: int, warmup: int = 0):
+    """Entries/s of the oracle's sweep (with its objective) on table t."""
+    import oracle
+    oracle.build()
+    p = oracle.Problem.from_csr(t.m, t.n, t.k, t.rowptr, t.colidx, t.val,
+                                loss_kind=t.loss_kind, loss_param=t.loss_param,
+                                loss_levels=t.loss_levels, rx=t.rx, ry=t.ry)
+    X, Yt = t.X0.copy(), t.Yt0.copy()
+    ax, ay = p.initial_alphas()
+    if warmup:
+        X, Yt, ax, ay, _, _ = p.proxgrad(X, Yt, warmup, ax, ay)
+    t0 = time.perf_counter()
+    X, Yt, ax, ay, hist, _ = p.proxgrad(X, Yt, steps, ax, ay)
+    dt = time.perf_counter() - t0
+    return t.nnz * steps / dt, dt, oracle.num_threads()
+
+
+# ------------------------------------------------------------------- arms
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    t = W.mixed()
+    sample = table_rows(t, ORACLE_SAMPLE_ROWS)
+    rate, dt, cores = oracle_rate(sample, args.steps, args.warmup)
+    sample_desc = (f"first {ORACLE_SAMPLE_ROWS} rows of the table (all columns, "
+                   f"{sample.nnz} observed entries), {args.steps} sweeps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "CPU run"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_glrm(args, world, rank, local):
+    import torch
+    from paper_1410_0342_gb300 import build
+    build.build()
+    from paper_1410_0342_gb300 import glrm as G
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    t = W.mixed()
+    stream = torch.cuda.current_stream(dev)
+    g = G.GLRM.from_table(t, precision=G.GLRM_FP32, device=dev, stream=stream)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up
+    g.sweep(args.warmup, history=False)
+    torch.cuda.synchronize(dev)
+
+    # timed region: K sweeps, CUDA events on the library's stream, per-kernel
+    # events recorded by the library on the same stream
+    G.glrm_timing_enable(g.h, True)
+    launches0 = G.glrm_launch_count(g.h)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.sweep(args.steps, history=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    launches = G.glrm_launch_count(g.h) - launches0
+    kern = G.glrm_timing_read(g.h)
+    G.glrm_timing_enable(g.h, False)
+    hist = g.sweep(1, history=True)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * t.nnz * args.steps / (ms_max / 1000.0)
+
+    # dominant kernel and its roofline
+    peaks, peak_src = measured_peaks()
+    top = max(kern.items(), key=lambda kv: kv[1][0])
+    tname, (tms, tcount) = top
+    avg_s = tms / tcount / 1000.0
+    abytes = algorithmic_bytes(tname, t, t.k)
+    achieved = abytes / avg_s / 1e9
+    traffic = ncu_traffic(tname)
+    roofline = {"bound": "hbm", "kernel": tname, "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_s * 1e6,
+                "peak_source": peak_src,
+                "share_of_step": tms / ms}
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / ms}
+               for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+        hb = [pin(t.rowptr, np.int32), pin(t.colidx, np.int32), pin(t.val, np.float32),
+              pin(t.colptr, np.int32), pin(t.rowidx, np.int32), pin(t.cval, np.float32)]
+        hX, hY = pin(t.X0, np.float32), pin(t.Yt0, np.float32)
+        h2d = sum(x.numel() * x.element_size() for x in hb + [hX, hY])
+        out = np.empty(1, np.float64)
+        ge = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry,
+                    G.GLRM_FP32, dev, stream)
+
+        def e2e_step():
+            G.glrm_set_observed_host(ge.h, t.nnz, *[x.numpy() for x in hb])
+            G.glrm_set_factors_host(ge.h, hX.numpy(), hY.numpy())
+            G._check(G._lib.glrm_sweep(ge.h, 1, G._ptr(out)), ge.h)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt, world, dev)
+        e2e = {"value": world * t.nnz * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
+               "steps": args.e2e_steps,
+               "includes": "set_observed_host (H2D copy + device validation + chunk tables), "
+                           "set_factors_host, one sweep, objective D2H"}
+        ge.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = table_rows(t, ORACLE_SAMPLE_ROWS)
+        rate, dt, cores = oracle_rate(sample, 2, 0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {ORACLE_SAMPLE_ROWS} rows (all columns, {sample.nnz} entries), "
+                         f"2 sweeps with objective, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nnz": t.nnz, "m": t.m, "n": t.n, "k": t.k,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (CSR+CSC 0.96 GB); no flush"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "kernels": kernels,
+            "objective_after": float(hist[-1]),
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_glrm(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * glrm.h -- C ABI of libglrm, a GB300 (sm_103a) CUDA library for the
+ * alternating proximal-gradient fit of a generalized low rank model (GLRM),
+ * Udell, Horn, Zadeh, Boyd, "Generalized Low Rank Models" (arXiv 1410.0342).
+ *
+ * The model (eq. gpca, Section 4; eq. apca, Section 5):
+ *
+ *     minimize  sum_{(i,j) in Omega} L_j(x_i . y_j, A_ij)
+ *               + sum_i r(x_i) + sum_j rt(y_j)
+ *
+ * over X (m x k, row x_i) and Y (k x n, column y_j).  Throughout this ABI Y
+ * is passed and stored as its transpose Yt (n x k, row j = y_j), so that both
+ * factors are row-major with k contiguous values per row or column.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named *_dev are device pointers (cudaMalloc'd or equivalent),
+ *    pointers named *_host are host pointers; the caller owns both.  Device
+ *    pointers must be aligned to their element size; 16-byte alignment lets
+ *    the kernels use vector loads.
+ *  - Element type of values and factors: double for GLRM_FP64, float for
+ *    GLRM_FP32 and GLRM_BF16 (the BF16 form keeps FP32 master factors and
+ *    runs its factor products in bf16, see glrm_create).
+ *  - All work is enqueued on the stream given to glrm_create, in order.  An
+ *    entry point returns once its work is enqueued unless it says it
+ *    synchronises (it must when it hands a result back in host memory).
+ *  - Every entry point returns a glrm_status.  Nothing throws across the ABI.
+ *    On error, glrm_last_error(h) gives a message; the handle stays usable
+ *    unless the error is GLRM_ERR_CUDA from a failed kernel, after which the
+ *    CUDA context itself is in error.
+ *  - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef GLRM_H
+#define GLRM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct glrm_s *glrm_t;
+
+typedef enum {
+    GLRM_OK = 0,
+    GLRM_ERR_ARG = -1,       /* bad argument (null pointer, size, kind) */
+    GLRM_ERR_RANGE = -2,     /* a size beyond the library's limits */
+    GLRM_ERR_OMEGA = -3,     /* the observed set failed validation */
+    GLRM_ERR_NONFINITE = -4, /* NaN or Inf in data */
+    GLRM_ERR_CUDA = -5,      /* a CUDA runtime call failed */
+    GLRM_ERR_TIMEOUT = -6,   /* a device-side wait hit its iteration limit */
+    GLRM_ERR_STATE = -7,     /* call out of order (e.g. sweep before set_observed) */
+    GLRM_ERR_NOMEM = -8      /* device allocation failed */
+} glrm_status;
+
+/* Per-column loss L_j(u, a).
+ *   GLRM_LOSS_QUAD      (u - a)^2                                    eq. qpca, Sec. 2.1
+ *   GLRM_LOSS_HUBER     huber_delta(u - a), delta = param:
+ *                       0.5 x^2 if |x| <= delta, else delta (|x| - delta/2);
+ *                       delta = 1 is the paper's Huber function      Sec. 4.3
+ *   GLRM_LOSS_HINGE     (1 - a u)_+ with a in {-1, +1}                Sec. 5.2
+ *   GLRM_LOSS_LOGISTIC  log(1 + exp(-a u)) with a in {-1, +1}         Sec. 5.2
+ *   GLRM_LOSS_ORDINAL_HINGE
+ *                       sum_{a'<a} (1 - u + a')_+ + sum_{a'>a, a'<=d} (1 + u - a')_+
+ *                       with a in {1..d}, d = levels                 eq. ord-pca
+ * At a kink the derivative of the kinked term is taken as 0. */
+typedef enum {
+    GLRM_LOSS_QUAD = 0,
+    GLRM_LOSS_HUBER = 1,
+    GLRM_LOSS_HINGE = 2,
+    GLRM_LOSS_LOGISTIC = 3,
+    GLRM_LOSS_ORDINAL_HINGE = 4
+} glrm_loss_kind;
+
+/* Row / column regulariser r(x) with weight w.
+ *   GLRM_REG_ZERO    0
+ *   GLRM_REG_QUAD    w ||x||_2^2                      eq. qpca
+ *   GLRM_REG_L1      w ||x||_1                        Sec. 3.2, sparse PCA
+ *   GLRM_REG_NONNEG  indicator of x >= 0 (0 or +inf)   Sec. 3.2, NNMF
+ * Their proximal operators (Sec. 7.2) are z/(1+2 alpha w), soft
+ * thresholding at alpha w, max(z, 0) and the identity. */
+typedef enum {
+    GLRM_REG_ZERO = 0,
+    GLRM_REG_QUAD = 1,
+    GLRM_REG_L1 = 2,
+    GLRM_REG_NONNEG = 3
+} glrm_reg_kind;
+
+typedef enum { GLRM_FP64 = 0, GLRM_FP32 = 1, GLRM_BF16 = 2 } glrm_precision;
+
+typedef struct {
+    int32_t kind;   /* glrm_loss_kind */
+    float param;    /* Huber delta; ignored otherwise */
+    int32_t levels; /* ordinal level count d >= 2; ignored otherwise */
+} glrm_loss;
+
+/* Limits: 1 <= k <= 64; m, n >= 1; m, n, nnz < 2^31. */
+
+/* Create a model of m rows, n columns and rank k.
+ * col_loss_host: n loss descriptors, copied.  rx / ry: regulariser kind and
+ * weight for the rows of X and the columns of Y.  precision: glrm_precision.
+ * stream: a cudaStream_t (NULL = legacy default stream) on which every later
+ * call enqueues its work.  Allocates the factors (zero) and step sizes on the
+ * current CUDA device.  Section 4 (eq. gpca) defines the model. */
+int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss_host,
+                int32_t rx_kind, float rx_weight, int32_t ry_kind, float ry_weight,
+                int32_t precision, void *stream, glrm_t *out);
+
+/* Give the model its observed set Omega (Section 2.5; Section 5) in both
+ * orientations: CSR (rowptr m+1, colidx nnz, val nnz; row i's entries at
+ * rowptr[i]..rowptr[i+1]-1, columns strictly ascending) and CSC (colptr n+1,
+ * rowidx nnz, val nnz; rows strictly ascending).  Device pointers; values in
+ * the model's element type.  The library copies and re-tiles everything into
+ * buffers it owns (the caller may free its copies afterwards), validates it
+ * on the device -- pointer monotonicity, index range, no duplicate (i,j),
+ * CSR/CSC describing the same entries with bit-identical values, finite
+ * values -- and resets every step size to 1/max(count, 1) (Section 7.2,
+ * "Choosing a step size").  Synchronises (it reads back the validation
+ * result).  Returns GLRM_ERR_OMEGA or GLRM_ERR_NONFINITE when validation
+ * fails; the previous Omega is then gone and sweeps return GLRM_ERR_STATE. */
+int glrm_set_observed(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_dev,
+                      const int32_t *csr_colidx_dev, const void *csr_val_dev,
+                      const int32_t *csc_colptr_dev, const int32_t *csc_rowidx_dev,
+                      const void *csc_val_dev);
+
+/* Same as glrm_set_observed with host pointers: the library copies them to
+ * the device on its stream first (pinned host memory makes that faster). */
+int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host,
+                           const int32_t *csr_colidx_host, const void *csr_val_host,
+                           const int32_t *csc_colptr_host, const int32_t *csc_rowidx_host,
+                           const void *csc_val_host);
+
+/* Copy factors in: X_dev (m x k) and Yt_dev (n x k), row-major, element type
+ * of the model.  Either may be NULL to leave that factor unchanged.  Step
+ * sizes are not touched (glrm_reset_steps resets them). */
+int glrm_set_factors(glrm_t h, const void *X_dev, const void *Yt_dev);
+
+/* Copy factors out (same layout); either pointer may be NULL. */
+int glrm_get_factors(glrm_t h, void *X_dev, void *Yt_dev);
+
+/* Host-pointer variants of the two calls above; they synchronise. */
+int glrm_set_factors_host(glrm_t h, const void *X_host, const void *Yt_host);
+int glrm_get_factors_host(glrm_t h, void *X_host, void *Yt_host);
+
+/* Reset every row step size to 1/max(n_i, 1) and every column step size to
+ * 1/max(m_j, 1) (Section 7.2, "Choosing a step size", scale 1). */
+int glrm_reset_steps(glrm_t h);
+
+/* Run nsweeps alternating proximal-gradient sweeps (Algorithm 2 with the
+ * proximal gradient update and the step-size rule of Section 7.2).  One
+ * sweep updates every row x_i against the current Y, then every column y_j
+ * against the new X.  Each row (column) update computes
+ *     g = sum_{j in Omega_i} L_j'(x_i . y_j, A_ij) y_j,
+ *     x+ = prox_{alpha_i r}(x_i - alpha_i g),
+ * and keeps x+ (alpha_i *= 1.05) when its row objective
+ * sum_j L_j(x . y_j, A_ij) + r(x) is not larger than at x_i, else keeps x_i
+ * (alpha_i *= 0.7).  history_host, if not NULL, receives nsweeps doubles: the
+ * objective of eq. gpca after each sweep (an FP64 reduction); the call then
+ * synchronises.  With history_host NULL the call returns once enqueued. */
+int glrm_sweep(glrm_t h, int32_t nsweeps, double *history_host);
+
+/* Accepted row and column steps of the last sweep run (host, 2 values);
+ * synchronises. */
+int glrm_last_accepts(glrm_t h, int64_t *accepts_host);
+
+/* Objective of eq. gpca at the model's factors, reduced in FP64; written to
+ * out_host; synchronises. */
+int glrm_objective(glrm_t h, double *out_host);
+
+/* Objective of eq. gpca at caller factors X_dev (m x k), Yt_dev (n x k)
+ * (element type of the model), reduced in FP64 and written to the device
+ * double out_dev.  Does not synchronise.  This is the forward of the
+ * differentiable form. */
+int glrm_objective_at(glrm_t h, const void *X_dev, const void *Yt_dev, double *out_dev);
+
+/* Gradient of the objective at caller factors (Section 7.2, "Gradient
+ * method"): GX_dev[i] = sum_{j in Omega_i} L_j'(x_i . y_j, A_ij) y_j and
+ * GYt_dev[j] = sum_{i in Omega_j} L_j'(x_i . y_j, A_ij) x_i (m x k and n x k,
+ * element type of the model).  With include_reg != 0 the regulariser's
+ * gradient is added (2 w x for GLRM_REG_QUAD, w sign(x) for GLRM_REG_L1, 0 for
+ * GLRM_REG_ZERO; GLRM_REG_NONNEG is not differentiable and returns
+ * GLRM_ERR_ARG).  Residuals are recomputed from the factors, never stored.
+ * Does not synchronise.  This is the backward of the differentiable form. */
+int glrm_grad_at(glrm_t h, const void *X_dev, const void *Yt_dev, void *GX_dev,
+                 void *GYt_dev, int32_t include_reg);
+
+/* Imputation (Section 5.3): for the cnt pairs (rows_dev[e], cols_dev[e])
+ * write u = x_i . y_j (decode == 0) or the decoded value argmin_a L_j(u, a)
+ * (decode != 0): u for quadratic and Huber columns, +1 if u >= 0 else -1 for
+ * hinge and logistic columns, 1 + #{a in 1..d-1 : u > a + 1/2} for ordinal
+ * columns (the minimiser of the ordinal hinge, ties to the lower level).
+ * out_dev holds cnt values of the model's element type.  Indices out of range
+ * produce NaN.  Does not synchronise. */
+int glrm_predict(glrm_t h, int64_t cnt, const int32_t *rows_dev, const int32_t *cols_dev,
+                 void *out_dev, int32_t decode);
+
+/* Alternating minimisation for quadratic loss and quadratic regularisation
+ * (Algorithm 1; Section 2.4 "Alternating minimization" and "Caching
+ * factorizations", with each row's Gram matrix restricted to its observed
+ * entries, Section 2.5): every x_i becomes the solution of
+ * (sum_{j in Omega_i} y_j y_j^T + gamma I) x = sum_{j in Omega_i} A_ij y_j,
+ * then every y_j likewise against the new X.  The Gram matrices accumulate in
+ * the model's element type; the k x k Cholesky factorisation and the two
+ * triangular solves run in FP64.  Requires every column loss to be
+ * GLRM_LOSS_QUAD and rx, ry both GLRM_REG_QUAD with the same weight gamma
+ * (else GLRM_ERR_ARG).  history_host as in glrm_sweep. */
+int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history_host);
+
+/* Serialise the fit state (factors, step sizes, sweep counter) into buf_host.
+ * With buf_host NULL, *len receives the size needed.  Synchronises.
+ * glrm_set_state restores it into a handle of the same m, n, k, precision;
+ * continuing from a restored state is bitwise identical to not stopping. */
+int glrm_get_state(glrm_t h, void *buf_host, size_t *len);
+int glrm_set_state(glrm_t h, const void *buf_host, size_t len);
+
+/* Instrumentation (not part of the method).  glrm_timing_enable(h, 1)
+ * records a CUDA event on the handle's stream before every kernel the handle
+ * launches and after the last one, so each kernel's device time is measured
+ * on its own stream; glrm_timing_enable(h, 0) stops recording.  Enabling or
+ * disabling clears the totals.  glrm_timing_read synchronises and returns, for
+ * up to max_kernels kernel names (32-byte NUL-terminated slots in
+ * names_host), the total milliseconds and launch counts recorded so far;
+ * *count_host receives the number of names written.  glrm_launch_count gives
+ * the number of kernels the handle has enqueued since creation. */
+int glrm_timing_enable(glrm_t h, int32_t on);
+int glrm_timing_read(glrm_t h, int32_t max_kernels, char *names_host, double *ms_host,
+                     int64_t *launches_host, int32_t *count_host);
+int glrm_launch_count(glrm_t h, int64_t *count_host);
+
+/* Per-handle message for the last error (empty string when none). */
+const char *glrm_last_error(glrm_t h);
+
+/* Message for an error that happened before a handle existed. */
+const char *glrm_global_error(void);
+
+/* Free every device buffer of the handle (after synchronising its stream). */
+void glrm_destroy(glrm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLRM_H */

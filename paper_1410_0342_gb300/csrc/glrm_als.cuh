@@ -1,0 +1,177 @@
+// Alternating minimisation for quadratic loss with gamma ||.||^2 on both
+// factors (Algorithm 1 of Udell et al., with the row and column problems of
+// Section 2.4 solved exactly, the Gram matrices restricted to each row's or
+// column's observed entries as in Section 2.5).  A half-step solves, for
+// every segment s (row in the X-step, column in the Y-step),
+//     (sum_{e in s} w_e w_e^T + gamma I) f_s = sum_{e in s} a_e w_e.
+// Launch 1 (per chunk): partial Gram lower triangle and right-hand side in
+// the element type.  Launch 2 (per segment, one warp): sum of the partials in
+// a fixed order, then an FP64 Cholesky factorisation and two triangular
+// solves in shared memory.
+#pragma once
+
+#include "glrm_engine.cuh"
+
+namespace glrm {
+
+constexpr int kAlsWarps = 4;
+
+template <int K>
+struct Tri {
+    static constexpr int N = K * (K + 1) / 2;  // lower-triangle entries
+    static constexpr int P = N + K;            // + right-hand side
+    static constexpr int NP = (N + 31) / 32;   // per lane
+};
+
+// Row r and column c (c <= r) of lower-triangle entry p (row-major order).
+__device__ __forceinline__ void tri_rc(int p, int &r, int &c)
+{
+    r = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= p) ++r;
+    while (r * (r + 1) / 2 > p) --r;
+    c = p - r * (r + 1) / 2;
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(kAlsWarps * 32)
+als_gram_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ idx,
+                const T *__restrict__ val, const T *__restrict__ W, int k, T *__restrict__ part)
+{
+    using TR = Tri<K>;
+    __shared__ T wsh[kAlsWarps][32][K + 1];
+    __shared__ T ash[kAlsWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kAlsWarps + wid;
+    if (c >= nchunks) return;
+    const int4 ch = chunks[c];
+    int rq[TR::NP], cq[TR::NP];
+    T acc[TR::NP];
+#pragma unroll
+    for (int q = 0; q < TR::NP; ++q) {
+        const int p = lane + 32 * q;
+        tri_rc(p < TR::N ? p : 0, rq[q], cq[q]);
+        acc[q] = T(0);
+    }
+    T bacc = T(0);
+    for (int base = ch.y; base < ch.z; base += 32) {
+        const int e = base + lane;
+        if (e < ch.z) {
+            const int64_t j = __ldg(idx + e);
+            ash[wid][lane] = __ldg(val + e);
+#pragma unroll
+            for (int q = 0; q < K; ++q) wsh[wid][lane][q] = q < k ? __ldg(W + j * k + q) : T(0);
+        }
+        __syncwarp();
+        const int cnt = min(32, ch.z - base);
+        for (int t = 0; t < cnt; ++t) {
+#pragma unroll
+            for (int q = 0; q < TR::NP; ++q)
+                acc[q] = fma(wsh[wid][t][rq[q]], wsh[wid][t][cq[q]], acc[q]);
+            if (lane < K) bacc = fma(ash[wid][t], wsh[wid][t][lane], bacc);
+        }
+        __syncwarp();
+    }
+    T *out = part + c * TR::P;
+#pragma unroll
+    for (int q = 0; q < TR::NP; ++q)
+        if (lane + 32 * q < TR::N) out[lane + 32 * q] = acc[q];
+    if (lane < K) out[TR::N + lane] = bacc;
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(kAlsWarps * 32)
+als_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restrict__ part,
+                 int k, double gamma, T *__restrict__ F)
+{
+    using TR = Tri<K>;
+    __shared__ double G[kAlsWarps][K][K + 1];
+    __shared__ double b[kAlsWarps][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t s = (int64_t)blockIdx.x * kAlsWarps + wid;
+    if (s >= nseg) return;
+    const int cb = segchunk[s], ce = segchunk[s + 1];
+    for (int p = lane; p < TR::N; p += 32) {
+        int r, c;
+        tri_rc(p, r, c);
+        double v = 0.0;
+        for (int q = cb; q < ce; ++q) v += (double)part[(int64_t)q * TR::P + p];
+        if (r == c) v += gamma;
+        G[wid][r][c] = v;
+    }
+    if (lane < K) {
+        double v = 0.0;
+        for (int q = cb; q < ce; ++q) v += (double)part[(int64_t)q * TR::P + TR::N + lane];
+        b[wid][lane] = v;
+    }
+    __syncwarp();
+    // Cholesky G = C C^T, column by column (right-looking), lanes over rows.
+    for (int c = 0; c < k; ++c) {
+        if (lane == 0) G[wid][c][c] = sqrt(G[wid][c][c]);
+        __syncwarp();
+        const double d = G[wid][c][c];
+        for (int r = c + 1 + lane; r < k; r += 32) G[wid][r][c] /= d;
+        __syncwarp();
+        for (int r = c + 1 + lane; r < k; r += 32)
+            for (int q = c + 1; q <= r; ++q) G[wid][r][q] -= G[wid][r][c] * G[wid][q][c];
+        __syncwarp();
+    }
+    if (lane == 0) {
+        double *x = b[wid];
+        for (int r = 0; r < k; ++r) {  // C w = b
+            double v = x[r];
+            for (int p = 0; p < r; ++p) v -= G[wid][r][p] * x[p];
+            x[r] = v / G[wid][r][r];
+        }
+        for (int r = k - 1; r >= 0; --r) {  // C^T x = w
+            double v = x[r];
+            for (int p = r + 1; p < k; ++p) v -= G[wid][p][r] * x[p];
+            x[r] = v / G[wid][r][r];
+        }
+    }
+    __syncwarp();
+    if (lane < k) F[s * k + lane] = (T)b[wid][lane];
+}
+
+template <class T, int K>
+cudaError_t launch_als_half(glrm_s *h, bool xstep, float gamma)
+{
+    const Orient &o = xstep ? h->csr : h->csc;
+    T *F = (T *)(xstep ? h->X : h->Yt);
+    const T *W = (const T *)(xstep ? h->Yt : h->X);
+    const size_t need = (size_t)std::max<int64_t>(1, std::max(h->csr.nchunks, h->csc.nchunks)) *
+                        Tri<K>::P * sizeof(T);
+    if (h->s.als_bytes < need) {
+        if (h->s.als_part) cudaFree(h->s.als_part);
+        h->s.als_part = nullptr;
+        h->s.als_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->s.als_part, need);
+        if (e != cudaSuccess) return e;
+        h->s.als_bytes = need;
+    }
+    T *part = (T *)h->s.als_part;
+    h->launches += 1 + (o.nchunks ? 1 : 0);
+    tmark(h, xstep ? "als_gram_x" : "als_gram_y");
+    if (o.nchunks)
+        als_gram_kernel<T, K><<<blocks_for(o.nchunks, kAlsWarps), kAlsWarps * 32, 0, h->stream>>>(
+            o.nchunks, o.chunks, o.idx, (const T *)o.val, W, h->k, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tmark(h, xstep ? "als_solve_x" : "als_solve_y");
+    als_solve_kernel<T, K><<<blocks_for(o.nseg, kAlsWarps), kAlsWarps * 32, 0, h->stream>>>(
+        o.nseg, o.segchunk, part, h->k, (double)gamma, F);
+    tmark(h, nullptr);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Engine<T>::als_half(glrm_s *h, bool xstep, float gamma)
+{
+    const int k = h->k;
+    if (k <= 4) return launch_als_half<T, 4>(h, xstep, gamma);
+    if (k <= 8) return launch_als_half<T, 8>(h, xstep, gamma);
+    if (k <= 16) return launch_als_half<T, 16>(h, xstep, gamma);
+    if (k <= 32) return launch_als_half<T, 32>(h, xstep, gamma);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace glrm

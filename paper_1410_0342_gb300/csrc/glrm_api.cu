@@ -1,0 +1,666 @@
+// C ABI of libglrm (declared in include/glrm.h): handle life cycle, the
+// observed set's copy, validation and chunk tables, and the entry points
+// that enqueue the per-precision engines.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "glrm_handle.h"
+
+using namespace glrm;
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(glrm_s *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_error = msg;
+    return code;
+}
+
+int cuda_fail(glrm_s *h, cudaError_t e, const char *where)
+{
+    return fail(h, GLRM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+template <class P>
+void dfree(P *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_orient(Orient &o)
+{
+    dfree(o.ptr);
+    dfree(o.idx);
+    dfree(o.val);
+    dfree(o.chunks);
+    dfree(o.segchunk);
+    o.nchunks = 0;
+    o.maxlen = 0;
+}
+
+void free_scratch(Scratch &s)
+{
+    dfree(s.part_grad); dfree(s.part_loss); dfree(s.part_loss2); dfree(s.cand);
+    dfree(s.f_old); dfree(s.r_old); dfree(s.r_new);
+    dfree(s.kept_obj_x); dfree(s.kept_reg_x); dfree(s.kept_obj_y); dfree(s.kept_reg_y);
+    dfree(s.acc_x); dfree(s.acc_y); dfree(s.red_part); dfree(s.red_cnt);
+    dfree(s.hist); dfree(s.accepts); dfree(s.scalar); dfree(s.als_part);
+    s.hist_cap = 0;
+    s.als_bytes = 0;
+}
+
+bool prec_ok(int p) { return p == GLRM_FP64 || p == GLRM_FP32; }
+
+// The handle's device must be current for every call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+cudaError_t run_half(glrm_s *h, bool xstep) { return Engine<T>::half_step(h, xstep); }
+
+cudaError_t half_step(glrm_s *h, bool xstep)
+{
+    return h->prec == GLRM_FP64 ? run_half<double>(h, xstep) : run_half<float>(h, xstep);
+}
+
+cudaError_t reduce_sweep(glrm_s *h, double *slot)
+{
+    return h->prec == GLRM_FP64 ? Engine<double>::reduce_sweep(h, slot)
+                                : Engine<float>::reduce_sweep(h, slot);
+}
+
+// Chunk table of one orientation from its (host) pointer array.
+void build_chunks(const std::vector<int32_t> &ptr, std::vector<int4> &chunks,
+                  std::vector<int32_t> &segchunk, int32_t &maxlen)
+{
+    const int64_t nseg = (int64_t)ptr.size() - 1;
+    segchunk.resize(nseg + 1);
+    chunks.clear();
+    maxlen = 0;
+    for (int64_t s = 0; s < nseg; ++s) {
+        segchunk[s] = (int32_t)chunks.size();
+        const int32_t b = ptr[s], e = ptr[s + 1];
+        maxlen = std::max(maxlen, e - b);
+        for (int64_t c = b; c < e; c += kChunk)
+            chunks.push_back(make_int4((int)s, (int)c, (int)std::min<int64_t>(e, c + kChunk), 0));
+    }
+    segchunk[nseg] = (int32_t)chunks.size();
+}
+
+int alloc_scratch(glrm_s *h)
+{
+    Scratch &s = h->s;
+    free_scratch(s);
+    const size_t es = elem_size(h->prec);
+    const int64_t nch = std::max<int64_t>(1, std::max(h->csr.nchunks, h->csc.nchunks));
+    const int64_t mx = std::max(h->m, h->n);
+    CK(cudaMalloc(&s.part_grad, (size_t)nch * h->k * es));
+    CK(cudaMalloc(&s.part_loss, (size_t)nch * sizeof(double)));
+    CK(cudaMalloc(&s.part_loss2, (size_t)nch * sizeof(double)));
+    CK(cudaMalloc(&s.cand, (size_t)mx * h->k * es));
+    CK(cudaMalloc(&s.f_old, (size_t)mx * sizeof(double)));
+    CK(cudaMalloc(&s.r_old, (size_t)mx * sizeof(double)));
+    CK(cudaMalloc(&s.r_new, (size_t)mx * sizeof(double)));
+    CK(cudaMalloc(&s.kept_obj_x, (size_t)h->m * sizeof(double)));
+    CK(cudaMalloc(&s.kept_reg_x, (size_t)h->m * sizeof(double)));
+    CK(cudaMalloc(&s.kept_obj_y, (size_t)h->n * sizeof(double)));
+    CK(cudaMalloc(&s.kept_reg_y, (size_t)h->n * sizeof(double)));
+    CK(cudaMalloc(&s.acc_x, (size_t)h->m * sizeof(int32_t)));
+    CK(cudaMalloc(&s.acc_y, (size_t)h->n * sizeof(int32_t)));
+    CK(cudaMalloc(&s.red_part, kRedBlocks * sizeof(double)));
+    CK(cudaMalloc(&s.red_cnt, 2 * kRedBlocks * sizeof(long long)));
+    CK(cudaMalloc(&s.accepts, 2 * sizeof(long long)));
+    CK(cudaMalloc(&s.scalar, sizeof(double)));
+    CK(cudaMemsetAsync(s.accepts, 0, 2 * sizeof(long long), h->stream));
+    return GLRM_OK;
+}
+
+int ensure_hist(glrm_s *h, int n)
+{
+    if (h->s.hist_cap >= n) return GLRM_OK;
+    dfree(h->s.hist);
+    CK(cudaMalloc(&h->s.hist, (size_t)n * sizeof(double)));
+    h->s.hist_cap = n;
+    return GLRM_OK;
+}
+
+const char *flag_message(int f)
+{
+    if (f & 1) return "pointer array not monotone, not starting at 0 or not ending at nnz";
+    if (f & 2) return "index out of range";
+    if (f & 4) return "indices within a row/column not strictly ascending (unsorted or duplicate)";
+    if (f & 16) return "a CSC entry has no CSR counterpart";
+    if (f & 32) return "CSR and CSC values differ for the same entry";
+    return "invalid observed set";
+}
+
+int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *ci, const void *rv,
+                      const int32_t *cp, const int32_t *ri, const void *cv, cudaMemcpyKind kind)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    DeviceGuard dg(h->device);
+    if (nnz < 0 || nnz >= (int64_t)INT32_MAX) return fail(h, GLRM_ERR_RANGE, "nnz must be in [0, 2^31)");
+    if (!rp || !cp || (nnz > 0 && (!ci || !rv || !ri || !cv)))
+        return fail(h, GLRM_ERR_ARG, "null observed-set pointer");
+    h->have_omega = false;
+    free_orient(h->csr);
+    free_orient(h->csc);
+    const size_t es = elem_size(h->prec);
+    cudaStream_t st = h->stream;
+    Orient &R = h->csr, &C = h->csc;
+    R.nseg = h->m;
+    C.nseg = h->n;
+    h->nnz = nnz;
+    const size_t nz = (size_t)std::max<int64_t>(nnz, 1);
+    CK(cudaMalloc(&R.ptr, (size_t)(h->m + 1) * sizeof(int32_t)));
+    CK(cudaMalloc(&C.ptr, (size_t)(h->n + 1) * sizeof(int32_t)));
+    CK(cudaMalloc(&R.idx, nz * sizeof(int32_t)));
+    CK(cudaMalloc(&C.idx, nz * sizeof(int32_t)));
+    CK(cudaMalloc(&R.val, nz * es));
+    CK(cudaMalloc(&C.val, nz * es));
+    CK(cudaMemcpyAsync(R.ptr, rp, (size_t)(h->m + 1) * sizeof(int32_t), kind, st));
+    CK(cudaMemcpyAsync(C.ptr, cp, (size_t)(h->n + 1) * sizeof(int32_t), kind, st));
+    if (nnz > 0) {
+        CK(cudaMemcpyAsync(R.idx, ci, (size_t)nnz * sizeof(int32_t), kind, st));
+        CK(cudaMemcpyAsync(C.idx, ri, (size_t)nnz * sizeof(int32_t), kind, st));
+        CK(cudaMemcpyAsync(R.val, rv, (size_t)nnz * es, kind, st));
+        CK(cudaMemcpyAsync(C.val, cv, (size_t)nnz * es, kind, st));
+    }
+    // validation: pointers first (the index checks rely on them)
+    int *flag = nullptr;
+    CK(cudaMalloc(&flag, sizeof(int)));
+    int hflag = 0;
+    auto check = [&](void) -> int {
+        cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "validation");
+        return GLRM_OK;
+    };
+    int rc = GLRM_OK;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_validate_ptr(R.ptr, h->m, nnz, flag, st);
+    if (e == cudaSuccess) e = launch_validate_ptr(C.ptr, h->n, nnz, flag, st);
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_ptr");
+    if (rc == GLRM_OK) rc = check();
+    if (rc == GLRM_OK && hflag == 0) {
+        e = launch_validate_idx(R.ptr, R.idx, R.val, h->prec, h->m, h->n, flag, st);
+        if (e == cudaSuccess) e = launch_validate_idx(C.ptr, C.idx, C.val, h->prec, h->n, h->m, flag, st);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
+        if (rc == GLRM_OK) rc = check();
+    }
+    if (rc == GLRM_OK && hflag == 0) {
+        e = launch_validate_cross(R, C, h->prec, flag, st);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_cross");
+        if (rc == GLRM_OK) rc = check();
+    }
+    cudaFree(flag);
+    if (rc != GLRM_OK) return rc;
+    if (hflag) {
+        const int code = (hflag & 8) && !(hflag & ~8) ? GLRM_ERR_NONFINITE : GLRM_ERR_OMEGA;
+        free_orient(R);
+        free_orient(C);
+        return fail(h, code, (hflag & 8) && !(hflag & ~8) ? "non-finite value in the observed set"
+                                                        : flag_message(hflag));
+    }
+    // chunk tables (host-built from the validated pointer arrays)
+    for (Orient *o : {&R, &C}) {
+        std::vector<int32_t> ptr(o->nseg + 1);
+        CK(cudaMemcpy(ptr.data(), o->ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        std::vector<int4> chunks;
+        std::vector<int32_t> segchunk;
+        build_chunks(ptr, chunks, segchunk, o->maxlen);
+        o->nchunks = (int64_t)chunks.size();
+        CK(cudaMalloc(&o->chunks, std::max<size_t>(1, chunks.size()) * sizeof(int4)));
+        CK(cudaMalloc(&o->segchunk, segchunk.size() * sizeof(int32_t)));
+        if (!chunks.empty())
+            CK(cudaMemcpy(o->chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(o->segchunk, segchunk.data(), segchunk.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+    }
+    rc = alloc_scratch(h);
+    if (rc != GLRM_OK) return rc;
+    h->have_omega = true;
+    e = h->prec == GLRM_FP64 ? Engine<double>::reset_steps(h) : Engine<float>::reset_steps(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reset_steps");
+    CK(cudaStreamSynchronize(st));
+    h->err.clear();
+    return GLRM_OK;
+}
+
+}  // namespace
+
+namespace glrm {
+size_t elem_size(int prec) { return prec == GLRM_FP64 ? sizeof(double) : sizeof(float); }
+
+void tmark(glrm_s *h, const char *name)
+{
+    Timer &t = h->timer;
+    if (!t.on) return;
+    const size_t i = t.marks.size();
+    if (i >= t.pool.size()) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return;
+        t.pool.push_back(ev);
+    }
+    if (cudaEventRecord(t.pool[i], h->stream) != cudaSuccess) return;
+    t.marks.emplace_back(name, i);
+}
+}  // namespace glrm
+
+namespace {
+
+// Fold the recorded marks into per-kernel totals (synchronises).
+int timer_collect(glrm_s *h)
+{
+    Timer &t = h->timer;
+    if (t.marks.empty()) return GLRM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t q = 0; q + 1 < t.marks.size(); ++q) {
+        if (!t.marks[q].first) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, t.pool[t.marks[q].second], t.pool[t.marks[q + 1].second]));
+        auto &a = t.acc[t.marks[q].first];
+        a.first += ms;
+        a.second += 1;
+    }
+    t.marks.clear();
+    return GLRM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *glrm_global_error(void) { return g_error.c_str(); }
+
+const char *glrm_last_error(glrm_t h) { return h ? h->err.c_str() : g_error.c_str(); }
+
+int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss, int32_t rx_kind,
+                float rx_weight, int32_t ry_kind, float ry_weight, int32_t precision, void *stream,
+                glrm_t *out)
+{
+    g_error.clear();
+    if (!out) return fail(nullptr, GLRM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (m < 1 || n < 1 || m >= INT32_MAX || n >= INT32_MAX)
+        return fail(nullptr, GLRM_ERR_RANGE, "m and n must be in [1, 2^31)");
+    if (k < 1 || k > kMaxK) return fail(nullptr, GLRM_ERR_RANGE, "k must be in [1, 64]");
+    if (!prec_ok(precision)) return fail(nullptr, GLRM_ERR_ARG, "unsupported precision");
+    if (!col_loss) return fail(nullptr, GLRM_ERR_ARG, "col_loss is null");
+    for (int r : {rx_kind, ry_kind})
+        if (r < kRegZero || r > kRegNonneg) return fail(nullptr, GLRM_ERR_ARG, "bad regulariser kind");
+    if (!(rx_weight >= 0.f) || !(ry_weight >= 0.f) || !isfinite(rx_weight) || !isfinite(ry_weight))
+        return fail(nullptr, GLRM_ERR_ARG, "regulariser weights must be finite and >= 0");
+    std::vector<LossSpec> spec((size_t)n);
+    for (int64_t j = 0; j < n; ++j) {
+        const glrm_loss &L = col_loss[j];
+        if (L.kind < kLossQuad || L.kind > kLossOrdinal)
+            return fail(nullptr, GLRM_ERR_ARG, "bad loss kind in column " + std::to_string(j));
+        if (L.kind == kLossHuber && !(L.param > 0.f && isfinite(L.param)))
+            return fail(nullptr, GLRM_ERR_ARG, "Huber threshold must be > 0 (column " + std::to_string(j) + ")");
+        if (L.kind == kLossOrdinal && (L.levels < 2 || L.levels > 1024))
+            return fail(nullptr, GLRM_ERR_ARG, "ordinal levels must be in [2, 1024] (column " + std::to_string(j) + ")");
+        spec[j] = LossSpec{L.kind, L.kind == kLossOrdinal ? L.levels : 0,
+                           L.kind == kLossHuber ? L.param : 0.f, 0.f};
+    }
+    glrm_s *h = new (std::nothrow) glrm_s;
+    if (!h) return fail(nullptr, GLRM_ERR_NOMEM, "host allocation failed");
+    h->m = m;
+    h->n = n;
+    h->k = k;
+    h->prec = precision;
+    h->stream = (cudaStream_t)stream;
+    h->loss_host = spec;
+    h->rx_kind = rx_kind;
+    h->ry_kind = ry_kind;
+    h->rx_w = rx_weight;
+    h->ry_w = ry_weight;
+    cudaError_t e = cudaGetDevice(&h->device);
+    const size_t es = elem_size(precision);
+    if (e == cudaSuccess) e = cudaMalloc(&h->loss_dev, (size_t)n * sizeof(LossSpec));
+    if (e == cudaSuccess) e = cudaMalloc(&h->X, (size_t)m * k * es);
+    if (e == cudaSuccess) e = cudaMalloc(&h->Yt, (size_t)n * k * es);
+    if (e == cudaSuccess) e = cudaMalloc(&h->alpha_x, (size_t)m * es);
+    if (e == cudaSuccess) e = cudaMalloc(&h->alpha_y, (size_t)n * es);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->loss_dev, spec.data(), (size_t)n * sizeof(LossSpec),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->X, 0, (size_t)m * k * es, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Yt, 0, (size_t)n * k * es, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("glrm_create: ") + cudaGetErrorString(e);
+        glrm_destroy(h);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? GLRM_ERR_NOMEM : GLRM_ERR_CUDA, msg);
+    }
+    *out = h;
+    return GLRM_OK;
+}
+
+int glrm_set_observed(glrm_t h, int64_t nnz, const int32_t *rp, const int32_t *ci, const void *rv,
+                      const int32_t *cp, const int32_t *ri, const void *cv)
+{
+    return set_observed_impl(h, nnz, rp, ci, rv, cp, ri, cv, cudaMemcpyDeviceToDevice);
+}
+
+int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                           const void *rv, const int32_t *cp, const int32_t *ri, const void *cv)
+{
+    return set_observed_impl(h, nnz, rp, ci, rv, cp, ri, cv, cudaMemcpyHostToDevice);
+}
+
+static int copy_factors(glrm_t h, void *X, void *Yt, const void *Xs, const void *Yts, cudaMemcpyKind kind,
+                        bool sync)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    DeviceGuard dg(h->device);
+    const size_t es = elem_size(h->prec);
+    if (X && Xs) CK(cudaMemcpyAsync(X, Xs, (size_t)h->m * h->k * es, kind, h->stream));
+    if (Yt && Yts) CK(cudaMemcpyAsync(Yt, Yts, (size_t)h->n * h->k * es, kind, h->stream));
+    if (sync) CK(cudaStreamSynchronize(h->stream));
+    return GLRM_OK;
+}
+
+int glrm_set_factors(glrm_t h, const void *X, const void *Yt)
+{
+    return h ? copy_factors(h, h->X, h->Yt, X, Yt, cudaMemcpyDeviceToDevice, false)
+             : fail(nullptr, GLRM_ERR_ARG, "null handle");
+}
+
+int glrm_get_factors(glrm_t h, void *X, void *Yt)
+{
+    return h ? copy_factors(h, X, Yt, X ? h->X : nullptr, Yt ? h->Yt : nullptr,
+                            cudaMemcpyDeviceToDevice, false)
+             : fail(nullptr, GLRM_ERR_ARG, "null handle");
+}
+
+int glrm_set_factors_host(glrm_t h, const void *X, const void *Yt)
+{
+    return h ? copy_factors(h, h->X, h->Yt, X, Yt, cudaMemcpyHostToDevice, true)
+             : fail(nullptr, GLRM_ERR_ARG, "null handle");
+}
+
+int glrm_get_factors_host(glrm_t h, void *X, void *Yt)
+{
+    return h ? copy_factors(h, X, Yt, X ? h->X : nullptr, Yt ? h->Yt : nullptr,
+                            cudaMemcpyDeviceToHost, true)
+             : fail(nullptr, GLRM_ERR_ARG, "null handle");
+}
+
+int glrm_reset_steps(glrm_t h)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    DeviceGuard dg(h->device);
+    cudaError_t e = h->prec == GLRM_FP64 ? Engine<double>::reset_steps(h) : Engine<float>::reset_steps(h);
+    return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "reset_steps");
+}
+
+int glrm_sweep(glrm_t h, int32_t nsweeps, double *history)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_sweep before glrm_set_observed");
+    if (nsweeps < 0) return fail(h, GLRM_ERR_ARG, "nsweeps < 0");
+    if (nsweeps == 0) return GLRM_OK;
+    DeviceGuard dg(h->device);
+    int rc = ensure_hist(h, nsweeps);
+    if (rc != GLRM_OK) return rc;
+    for (int t = 0; t < nsweeps; ++t) {
+        cudaError_t e = half_step(h, true);
+        if (e == cudaSuccess) e = half_step(h, false);
+        if (e == cudaSuccess) e = reduce_sweep(h, h->s.hist + t);
+        if (e != cudaSuccess) return cuda_fail(h, e, "glrm_sweep");
+        h->sweeps_done++;
+    }
+    if (history) {
+        CK(cudaMemcpyAsync(history, h->s.hist, (size_t)nsweeps * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return GLRM_OK;
+}
+
+int glrm_last_accepts(glrm_t h, int64_t *acc)
+{
+    if (!h || !acc) return fail(h, GLRM_ERR_ARG, "null argument");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    DeviceGuard dg(h->device);
+    long long tmp[2];
+    CK(cudaMemcpyAsync(tmp, h->s.accepts, sizeof tmp, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    acc[0] = tmp[0];
+    acc[1] = tmp[1];
+    return GLRM_OK;
+}
+
+int glrm_objective_at(glrm_t h, const void *X, const void *Yt, double *out)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!X || !Yt || !out) return fail(h, GLRM_ERR_ARG, "null pointer");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    DeviceGuard dg(h->device);
+    cudaError_t e = h->prec == GLRM_FP64
+                        ? Engine<double>::objective_at(h, (const double *)X, (const double *)Yt, out)
+                        : Engine<float>::objective_at(h, (const float *)X, (const float *)Yt, out);
+    return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_objective_at");
+}
+
+int glrm_objective(glrm_t h, double *out)
+{
+    if (!h || !out) return fail(h, GLRM_ERR_ARG, "null argument");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    int rc = glrm_objective_at(h, h->X, h->Yt, h->s.scalar);
+    if (rc != GLRM_OK) return rc;
+    DeviceGuard dg(h->device);
+    CK(cudaMemcpyAsync(out, h->s.scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GLRM_OK;
+}
+
+int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, int32_t include_reg)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!X || !Yt || !GX || !GYt) return fail(h, GLRM_ERR_ARG, "null pointer");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    if (include_reg && (h->rx_kind == kRegNonneg || h->ry_kind == kRegNonneg))
+        return fail(h, GLRM_ERR_ARG, "the nonnegativity indicator has no gradient");
+    DeviceGuard dg(h->device);
+    cudaError_t e = h->prec == GLRM_FP64
+                        ? Engine<double>::grad_at(h, (const double *)X, (const double *)Yt,
+                                                  (double *)GX, (double *)GYt, include_reg != 0)
+                        : Engine<float>::grad_at(h, (const float *)X, (const float *)Yt, (float *)GX,
+                                                 (float *)GYt, include_reg != 0);
+    return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_grad_at");
+}
+
+int glrm_predict(glrm_t h, int64_t cnt, const int32_t *rows, const int32_t *cols, void *out,
+                 int32_t decode)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (cnt < 0 || (cnt > 0 && (!rows || !cols || !out))) return fail(h, GLRM_ERR_ARG, "bad arguments");
+    DeviceGuard dg(h->device);
+    cudaError_t e = h->prec == GLRM_FP64
+                        ? Engine<double>::predict(h, cnt, rows, cols, (double *)out, decode != 0)
+                        : Engine<float>::predict(h, cnt, rows, cols, (float *)out, decode != 0);
+    return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_predict");
+}
+
+int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_als_sweep before glrm_set_observed");
+    if (nsweeps < 0) return fail(h, GLRM_ERR_ARG, "nsweeps < 0");
+    if (h->rx_kind != kRegQuad || h->ry_kind != kRegQuad || h->rx_w != h->ry_w || !(h->rx_w > 0.f))
+        return fail(h, GLRM_ERR_ARG,
+                    "ALS needs quadratic regularisers of equal weight gamma > 0 on X and Y");
+    if (h->k > 32) return fail(h, GLRM_ERR_RANGE, "ALS supports k <= 32");
+    for (const LossSpec &L : h->loss_host)
+        if (L.kind != kLossQuad) return fail(h, GLRM_ERR_ARG, "ALS needs quadratic loss in every column");
+    if (nsweeps == 0) return GLRM_OK;
+    DeviceGuard dg(h->device);
+    int rc = ensure_hist(h, nsweeps);
+    if (rc != GLRM_OK) return rc;
+    for (int t = 0; t < nsweeps; ++t) {
+        cudaError_t e = h->prec == GLRM_FP64 ? Engine<double>::als_half(h, true, h->rx_w)
+                                             : Engine<float>::als_half(h, true, h->rx_w);
+        if (e == cudaSuccess)
+            e = h->prec == GLRM_FP64 ? Engine<double>::als_half(h, false, h->ry_w)
+                                     : Engine<float>::als_half(h, false, h->ry_w);
+        if (e == cudaSuccess)
+            e = h->prec == GLRM_FP64
+                    ? Engine<double>::objective_at(h, (const double *)h->X, (const double *)h->Yt, h->s.hist + t)
+                    : Engine<float>::objective_at(h, (const float *)h->X, (const float *)h->Yt, h->s.hist + t);
+        if (e != cudaSuccess) return cuda_fail(h, e, "glrm_als_sweep");
+        h->sweeps_done++;
+    }
+    if (history) {
+        CK(cudaMemcpyAsync(history, h->s.hist, (size_t)nsweeps * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return GLRM_OK;
+}
+
+// State layout: 8 int64 header words {magic, version, m, n, k, prec, sweeps, 0}
+// then X, Yt, alpha_x, alpha_y in the model's element type.
+static const int64_t kStateMagic = 0x4d524c47;  // "GLRM"
+
+int glrm_get_state(glrm_t h, void *buf, size_t *len)
+{
+    if (!h || !len) return fail(h, GLRM_ERR_ARG, "null argument");
+    const size_t es = elem_size(h->prec);
+    const size_t need = 8 * sizeof(int64_t) + es * (size_t)((h->m + h->n) * h->k + h->m + h->n);
+    if (!buf) {
+        *len = need;
+        return GLRM_OK;
+    }
+    if (*len < need) return fail(h, GLRM_ERR_ARG, "state buffer too small");
+    DeviceGuard dg(h->device);
+    int64_t hdr[8] = {kStateMagic, 1, h->m, h->n, h->k, h->prec, h->sweeps_done, 0};
+    char *p = (char *)buf;
+    memcpy(p, hdr, sizeof hdr);
+    p += sizeof hdr;
+    CK(cudaMemcpyAsync(p, h->X, es * h->m * h->k, cudaMemcpyDeviceToHost, h->stream));
+    p += es * h->m * h->k;
+    CK(cudaMemcpyAsync(p, h->Yt, es * h->n * h->k, cudaMemcpyDeviceToHost, h->stream));
+    p += es * h->n * h->k;
+    CK(cudaMemcpyAsync(p, h->alpha_x, es * h->m, cudaMemcpyDeviceToHost, h->stream));
+    p += es * h->m;
+    CK(cudaMemcpyAsync(p, h->alpha_y, es * h->n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *len = need;
+    return GLRM_OK;
+}
+
+int glrm_set_state(glrm_t h, const void *buf, size_t len)
+{
+    if (!h || !buf) return fail(h, GLRM_ERR_ARG, "null argument");
+    const size_t es = elem_size(h->prec);
+    const size_t need = 8 * sizeof(int64_t) + es * (size_t)((h->m + h->n) * h->k + h->m + h->n);
+    if (len < need) return fail(h, GLRM_ERR_ARG, "state buffer too small");
+    int64_t hdr[8];
+    memcpy(hdr, buf, sizeof hdr);
+    if (hdr[0] != kStateMagic || hdr[1] != 1 || hdr[2] != h->m || hdr[3] != h->n || hdr[4] != h->k ||
+        hdr[5] != h->prec)
+        return fail(h, GLRM_ERR_ARG, "state does not match this model");
+    DeviceGuard dg(h->device);
+    const char *p = (const char *)buf + sizeof hdr;
+    CK(cudaMemcpyAsync(h->X, p, es * h->m * h->k, cudaMemcpyHostToDevice, h->stream));
+    p += es * h->m * h->k;
+    CK(cudaMemcpyAsync(h->Yt, p, es * h->n * h->k, cudaMemcpyHostToDevice, h->stream));
+    p += es * h->n * h->k;
+    CK(cudaMemcpyAsync(h->alpha_x, p, es * h->m, cudaMemcpyHostToDevice, h->stream));
+    p += es * h->m;
+    CK(cudaMemcpyAsync(h->alpha_y, p, es * h->n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->sweeps_done = hdr[6];
+    return GLRM_OK;
+}
+
+int glrm_timing_enable(glrm_t h, int32_t on)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    DeviceGuard dg(h->device);
+    int rc = timer_collect(h);
+    if (rc != GLRM_OK) return rc;
+    h->timer.acc.clear();
+    h->timer.on = on != 0;
+    return GLRM_OK;
+}
+
+int glrm_timing_read(glrm_t h, int32_t max_kernels, char *names_host, double *ms_host,
+                     int64_t *launches_host, int32_t *count_host)
+{
+    if (!h || !count_host) return fail(h, GLRM_ERR_ARG, "null argument");
+    DeviceGuard dg(h->device);
+    int rc = timer_collect(h);
+    if (rc != GLRM_OK) return rc;
+    int q = 0;
+    for (const auto &kv : h->timer.acc) {
+        if (q >= max_kernels) break;
+        if (names_host) {
+            strncpy(names_host + 32 * q, kv.first.c_str(), 31);
+            names_host[32 * q + 31] = 0;
+        }
+        if (ms_host) ms_host[q] = kv.second.first;
+        if (launches_host) launches_host[q] = kv.second.second;
+        ++q;
+    }
+    *count_host = q;
+    return GLRM_OK;
+}
+
+int glrm_launch_count(glrm_t h, int64_t *count_host)
+{
+    if (!h || !count_host) return fail(h, GLRM_ERR_ARG, "null argument");
+    *count_host = h->launches;
+    return GLRM_OK;
+}
+
+void glrm_destroy(glrm_t h)
+{
+    if (!h) return;
+    {
+        DeviceGuard dg(h->device);
+        cudaStreamSynchronize(h->stream);
+        for (cudaEvent_t ev : h->timer.pool) cudaEventDestroy(ev);
+        free_orient(h->csr);
+        free_orient(h->csc);
+        free_scratch(h->s);
+        dfree(h->loss_dev);
+        dfree(h->X);
+        dfree(h->Yt);
+        dfree(h->alpha_x);
+        dfree(h->alpha_y);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+// Device-side pieces of the GLRM sweep: per-entry losses and derivatives,
+// per-coordinate proximal operators and regulariser values, factor-row
+// loaders and warp reductions.  Section references are to Udell et al.,
+// "Generalized Low Rank Models" (arXiv 1410.0342).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace glrm {
+
+constexpr int kLossQuad = 0, kLossHuber = 1, kLossHinge = 2, kLossLogistic = 3, kLossOrdinal = 4;
+constexpr int kRegZero = 0, kRegQuad = 1, kRegL1 = 2, kRegNonneg = 3;
+
+// One column's loss, 16 bytes so that a lane loads it with one instruction.
+struct __align__(16) LossSpec {
+    int32_t kind;
+    int32_t levels;
+    float param;
+    float pad;
+};
+
+__device__ __forceinline__ float xexp(float x) { return expf(x); }
+__device__ __forceinline__ double xexp(double x) { return exp(x); }
+__device__ __forceinline__ float xlog1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double xlog1p(double x) { return log1p(x); }
+template <class T> __device__ __forceinline__ T xinf();
+template <> __device__ __forceinline__ float xinf<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double xinf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+// L(u, a) into *L and dL/du as the return value (a subgradient with the
+// kinked term's derivative taken as 0 at its kink).
+//   quadratic (u-a)^2                                      eq. qpca
+//   Huber with threshold delta = param                     Sec. 4.3
+//   hinge (1 - a u)_+                                      Sec. 5.2
+//   logistic log(1 + exp(-a u)), overflow-free form        Sec. 5.2
+//   ordinal hinge over levels 1..d                         eq. ord-pca
+template <class T>
+__device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
+{
+    switch (s.kind) {
+    case kLossQuad: {
+        T r = u - a;
+        L = r * r;
+        return T(2) * r;
+    }
+    case kLossHuber: {
+        T x = u - a, d = T(s.param), ax = fabs(x);
+        if (ax <= d) {
+            L = T(0.5) * x * x;
+            return x;
+        }
+        L = d * (ax - T(0.5) * d);
+        return x > T(0) ? d : -d;
+    }
+    case kLossHinge: {
+        T z = T(1) - a * u;
+        if (z > T(0)) {
+            L = z;
+            return -a;
+        }
+        L = T(0);
+        return T(0);
+    }
+    case kLossLogistic: {
+        // z = -a u; log(1 + e^z) = max(z, 0) + log1p(e^{-|z|});
+        // derivative -a sigma(z) with sigma evaluated on the stable side.
+        T z = -a * u, e = xexp(-fabs(z));
+        L = fmax(z, T(0)) + xlog1p(e);
+        T sg = z >= T(0) ? T(1) / (T(1) + e) : e / (T(1) + e);
+        return -a * sg;
+    }
+    default: {
+        const int lev = (int)a;
+        T Ls = T(0), d = T(0);
+        for (int ap = 1; ap < lev; ++ap) {
+            T t = T(1) - u + T(ap);
+            if (t > T(0)) { Ls += t; d -= T(1); }
+        }
+        for (int ap = lev + 1; ap <= s.levels; ++ap) {
+            T t = T(1) + u - T(ap);
+            if (t > T(0)) { Ls += t; d += T(1); }
+        }
+        L = Ls;
+        return d;
+    }
+    }
+}
+
+// argmin_a L(u, a) (Sec. 5.3).  For the ordinal hinge,
+// L(u, a+1) - L(u, a) = (1 + a - u)_+ - (u - a)_+ is <= 0 exactly when
+// u >= a + 1/2, so the minimiser is 1 + #{a in 1..d-1 : u > a + 1/2} with
+// ties at u = a + 1/2 going to the lower level; the comparisons are exact in
+// any precision.
+template <class T>
+__device__ __forceinline__ T decode_value(const LossSpec &s, T u)
+{
+    switch (s.kind) {
+    case kLossHinge:
+    case kLossLogistic:
+        return u >= T(0) ? T(1) : T(-1);
+    case kLossOrdinal: {
+        int lev = 1;
+        for (int a = 1; a < s.levels; ++a) lev += (u > T(a) + T(0.5)) ? 1 : 0;
+        return T(lev);
+    }
+    default:
+        return u;
+    }
+}
+
+// prox_{alpha r} of one coordinate (every regulariser here is separable):
+// z/(1 + 2 alpha w), soft threshold at alpha w, max(z, 0), identity.
+template <class T>
+__device__ __forceinline__ T prox1(int kind, T w, T alpha, T z)
+{
+    switch (kind) {
+    case kRegQuad:
+        return z / (T(1) + T(2) * alpha * w);
+    case kRegL1: {
+        T t = alpha * w;
+        return z > t ? z - t : (z < -t ? z + t : T(0));
+    }
+    case kRegNonneg:
+        return z > T(0) ? z : T(0);
+    default:
+        return z;
+    }
+}
+
+// One coordinate's share of r(x): w x^2, w |x|, 0 or +inf (infeasible), 0.
+template <class T>
+__device__ __forceinline__ double reg1(int kind, T w, T x)
+{
+    switch (kind) {
+    case kRegQuad:
+        return (double)w * (double)x * (double)x;
+    case kRegL1:
+        return (double)w * fabs((double)x);
+    case kRegNonneg:
+        return x < T(0) ? xinf<double>() : 0.0;
+    default:
+        return 0.0;
+    }
+}
+
+// One coordinate of the regulariser's gradient: 2 w x, w sign(x), 0.
+template <class T>
+__device__ __forceinline__ T reg_grad1(int kind, T w, T x)
+{
+    switch (kind) {
+    case kRegQuad:
+        return T(2) * w * x;
+    case kRegL1:
+        return x > T(0) ? w : (x < T(0) ? -w : T(0));
+    default:
+        return T(0);
+    }
+}
+
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ int shfl_xor(int v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+    return v;
+}
+
+// Load coordinates c0 .. c0+S-1 of a factor row (row-major, k values).
+// VEC: the caller guarantees k == the padded width, so the slice is in range,
+// and 16-byte alignment, so the slice loads as float4 / double2 vectors.
+// Otherwise coordinates at or beyond k read as 0.
+template <class T, int S, bool VEC>
+__device__ __forceinline__ void load_slice(T (&v)[S], const T *__restrict__ row, int c0, int k)
+{
+    if constexpr (VEC && sizeof(T) == 4) {
+        static_assert(S % 4 == 0, "float slice must be a multiple of 4");
+        const float4 *p = reinterpret_cast<const float4 *>(row + c0);
+#pragma unroll
+        for (int q = 0; q < S / 4; ++q) {
+            float4 t = __ldg(p + q);
+            v[4 * q + 0] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    } else if constexpr (VEC && sizeof(T) == 8) {
+        static_assert(S % 2 == 0, "double slice must be a multiple of 2");
+        const double2 *p = reinterpret_cast<const double2 *>(row + c0);
+#pragma unroll
+        for (int q = 0; q < S / 2; ++q) {
+            double2 t = __ldg(p + q);
+            v[2 * q + 0] = t.x;
+            v[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) v[s] = (c0 + s < k) ? __ldg(row + c0 + s) : T(0);
+    }
+}
+
+}  // namespace glrm

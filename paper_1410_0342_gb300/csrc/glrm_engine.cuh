@@ -1,0 +1,467 @@
+// Kernels of the alternating proximal-gradient sweep (Algorithm 2 with the
+// proximal gradient update and the step-size rule of Section 7.2 of Udell et
+// al., "Generalized Low Rank Models") and of the objective, gradient and
+// imputation, templated on the element type T and the padded rank K.
+//
+// A half-step updates the factor F of every segment (row x_i of X in the
+// X-step over CSR, column y_j of Y in the Y-step over CSC) against the other
+// factor W, in four launches:
+//   pass_kernel<GRAD=1>  per chunk: u = f . w_idx, L'(u, a), partial gradient
+//                        sum L' w and partial loss sum L
+//   prox_kernel          per segment: g = sum of partials, f+ = prox(f - alpha g),
+//                        f_old = loss + r(f), r(f+)
+//   pass_kernel<GRAD=0>  per chunk: partial loss at f+
+//   decide_kernel        per segment: keep f+ (alpha *= 1.05) if
+//                        f_new <= f_old, else keep f (alpha *= 0.7)
+// Chunks hold at most kChunk entries, so long columns spread over many warps.
+// All reductions run in a fixed order: results are bitwise reproducible.
+#pragma once
+
+#include "glrm_handle.h"
+
+namespace glrm {
+
+constexpr int kWarpsPerBlock = 8;
+
+template <int K>
+struct Lanes {
+    // G lanes share one entry, each holding S = K / G coordinates.
+    static constexpr int G = K > 32 ? 4 : 1;
+    static constexpr int S = K / G;
+    static constexpr int PER = 32 / G;  // entries per warp iteration
+};
+
+template <class T, int K, bool XSTEP, bool VEC, bool GRAD>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ idx,
+            const T *__restrict__ val, const T *__restrict__ F, const T *__restrict__ W, int k,
+            const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
+            double *__restrict__ part_loss)
+{
+    using LN = Lanes<K>;
+    constexpr int G = LN::G, S = LN::S, PER = LN::PER;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= nchunks) return;  // the whole warp leaves together
+    const int gl = lane % G, grp = lane / G, c0 = gl * S;
+    const int4 ch = chunks[c];
+    T f[S], g[S];
+    load_slice<T, S, VEC>(f, F + (int64_t)ch.x * k, c0, k);
+#pragma unroll
+    for (int s = 0; s < S; ++s) g[s] = T(0);
+    T lsum = T(0);
+    LossSpec sp;
+    if constexpr (!XSTEP) sp = loss[ch.x];
+    for (int base = ch.y; base < ch.z; base += PER) {
+        const int e = base + grp;
+        const bool ok = e < ch.z;
+        int j = 0;
+        T a = T(0);
+        T w[S];
+        if (ok) {
+            j = __ldg(idx + e);
+            a = __ldg(val + e);
+            load_slice<T, S, VEC>(w, W + (int64_t)j * k, c0, k);
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) w[s] = T(0);
+        }
+        T u = T(0);
+#pragma unroll
+        for (int s = 0; s < S; ++s) u = fma(f[s], w[s], u);
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) u += shfl_xor(u, o);
+        if (ok) {
+            if constexpr (XSTEP) sp = loss[j];
+            T L;
+            T d = loss_deriv<T>(sp, u, a, L);
+            if constexpr (GRAD) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) g[s] = fma(d, w[s], g[s]);
+            }
+            if (gl == 0) lsum += L;
+        }
+    }
+    if constexpr (GRAD) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) g[s] += shfl_xor(g[s], o);
+        }
+        if (grp == 0) {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                if (c0 + s < k) part_grad[c * k + c0 + s] = g[s];
+        }
+    }
+    const double ls = warp_sum((double)lsum);
+    if (lane == 0) part_loss[c] = ls;
+}
+
+// Sum of a segment's chunk partials, lanes strided then a butterfly: fixed order.
+__device__ __forceinline__ double seg_loss_sum(const double *__restrict__ part, int c_beg, int c_end,
+                                               int lane)
+{
+    double v = 0.0;
+    for (int c = c_beg + lane; c < c_end; c += 32) v += part[c];
+    return warp_sum(v);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+prox_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restrict__ part_grad,
+            const double *__restrict__ part_loss, const T *__restrict__ F,
+            const T *__restrict__ alpha, int k, int rkind, T rw, T *__restrict__ cand,
+            double *__restrict__ f_old, double *__restrict__ r_old, double *__restrict__ r_new)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (s >= nseg) return;
+    const int cb = segchunk[s], ce = segchunk[s + 1];
+    const T al = alpha[s];
+    double ro = 0.0, rn = 0.0;
+    for (int c = lane; c < k; c += 32) {
+        T g = T(0);
+        for (int q = cb; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
+        const T x = F[s * k + c];
+        const T xp = prox1<T>(rkind, rw, al, x - al * g);
+        cand[s * k + c] = xp;
+        ro += reg1<T>(rkind, rw, x);
+        rn += reg1<T>(rkind, rw, xp);
+    }
+    ro = warp_sum(ro);
+    rn = warp_sum(rn);
+    const double ls = seg_loss_sum(part_loss, cb, ce, lane);
+    if (lane == 0) {
+        f_old[s] = ls + ro;
+        r_old[s] = ro;
+        r_new[s] = rn;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+decide_kernel(int64_t nseg, const int32_t *__restrict__ segchunk,
+              const double *__restrict__ part_loss_new, const double *__restrict__ f_old,
+              const double *__restrict__ r_old, const double *__restrict__ r_new,
+              const T *__restrict__ cand, T *__restrict__ F, T *__restrict__ alpha, int k,
+              double *__restrict__ kept_obj, double *__restrict__ kept_reg,
+              int32_t *__restrict__ accepted)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (s >= nseg) return;
+    const double fn = seg_loss_sum(part_loss_new, segchunk[s], segchunk[s + 1], lane) + r_new[s];
+    const double fo = f_old[s];
+    const bool acc = fn <= fo;
+    if (acc)
+        for (int c = lane; c < k; c += 32) F[s * k + c] = cand[s * k + c];
+    if (lane == 0) {
+        alpha[s] = alpha[s] * (acc ? T(1.05) : T(0.7));
+        kept_obj[s] = acc ? fn : fo;
+        kept_reg[s] = acc ? r_new[s] : r_old[s];
+        accepted[s] = acc ? 1 : 0;
+    }
+}
+
+// Deterministic two-level sums.  Stage 1: block b sums a fixed contiguous
+// range of each source; stage 2: one block sums the kRedBlocks partials.
+template <class T>
+__global__ void __launch_bounds__(256)
+reduce_stage1(const double *__restrict__ a, int64_t na, const double *__restrict__ b, int64_t nb,
+              const T *__restrict__ X, int64_t m, int rxk, T rxw, const T *__restrict__ Yt,
+              int64_t n, int ryk, T ryw, int k, const int32_t *__restrict__ ca, int64_t nca,
+              const int32_t *__restrict__ cb, int64_t ncb, double *__restrict__ part,
+              long long *__restrict__ cnt)
+{
+    __shared__ double sh[256];
+    __shared__ long long shc[2][256];
+    double v = 0.0;
+    long long c1 = 0, c2 = 0;
+    auto range = [&](int64_t len, int64_t &lo, int64_t &hi) {
+        const int64_t per = (len + gridDim.x - 1) / gridDim.x;
+        lo = per * blockIdx.x;
+        hi = lo + per < len ? lo + per : len;
+    };
+    int64_t lo, hi;
+    if (a) { range(na, lo, hi); for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += a[i]; }
+    if (b) { range(nb, lo, hi); for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += b[i]; }
+    if (X) {
+        range(m * k, lo, hi);
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += reg1<T>(rxk, rxw, X[i]);
+    }
+    if (Yt) {
+        range(n * k, lo, hi);
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += reg1<T>(ryk, ryw, Yt[i]);
+    }
+    if (ca) { range(nca, lo, hi); for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c1 += ca[i]; }
+    if (cb) { range(ncb, lo, hi); for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c2 += cb[i]; }
+    sh[threadIdx.x] = v;
+    shc[0][threadIdx.x] = c1;
+    shc[1][threadIdx.x] = c2;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+            shc[0][threadIdx.x] += shc[0][threadIdx.x + o];
+            shc[1][threadIdx.x] += shc[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sh[0];
+        cnt[2 * blockIdx.x] = shc[0][0];
+        cnt[2 * blockIdx.x + 1] = shc[1][0];
+    }
+}
+
+static __global__ void __launch_bounds__(256)
+reduce_stage2(const double *__restrict__ part, const long long *__restrict__ cnt, int nparts,
+              double *__restrict__ out, long long *__restrict__ cnt_out)
+{
+    __shared__ double sh[256];
+    __shared__ long long shc[2][256];
+    double v = 0.0;
+    long long c1 = 0, c2 = 0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        v += part[i];
+        c1 += cnt[2 * i];
+        c2 += cnt[2 * i + 1];
+    }
+    sh[threadIdx.x] = v;
+    shc[0][threadIdx.x] = c1;
+    shc[1][threadIdx.x] = c2;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+            shc[0][threadIdx.x] += shc[0][threadIdx.x + o];
+            shc[1][threadIdx.x] += shc[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (out) *out = sh[0];
+        if (cnt_out) {
+            cnt_out[0] = shc[0][0];
+            cnt_out[1] = shc[1][0];
+        }
+    }
+}
+
+// Gradient of each segment: sum of its chunk partials (+ the regulariser's
+// gradient), one warp per segment, lanes over coordinates.
+template <class T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+seg_grad_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restrict__ part_grad,
+                const T *__restrict__ F, int k, int rkind, T rw, bool reg, T *__restrict__ G)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (s >= nseg) return;
+    const int cb = segchunk[s], ce = segchunk[s + 1];
+    for (int c = lane; c < k; c += 32) {
+        T g = T(0);
+        for (int q = cb; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
+        if (reg) g += reg_grad1<T>(rkind, rw, F[s * k + c]);
+        G[s * k + c] = g;
+    }
+}
+
+template <class T>
+__global__ void predict_kernel(int64_t cnt, const int32_t *__restrict__ rows,
+                               const int32_t *__restrict__ cols, const T *__restrict__ X,
+                               const T *__restrict__ Yt, int64_t m, int64_t n, int k,
+                               const LossSpec *__restrict__ loss, bool decode, T *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cnt) return;
+    const int32_t i = rows[e], j = cols[e];
+    if (i < 0 || i >= m || j < 0 || j >= n) {
+        out[e] = T(NAN);
+        return;
+    }
+    T u = T(0);
+    for (int c = 0; c < k; ++c) u = fma(X[(int64_t)i * k + c], Yt[(int64_t)j * k + c], u);
+    out[e] = decode ? decode_value<T>(loss[j], u) : u;
+}
+
+template <class T>
+__global__ void reset_alpha_kernel(const int32_t *__restrict__ ptr, int64_t nseg, T *__restrict__ alpha)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const int len = ptr[s + 1] - ptr[s];
+    alpha[s] = T(1) / T(len > 1 ? len : 1);
+}
+
+// ------------------------------------------------------------------ launchers
+
+inline unsigned blocks_for(int64_t items, int per_block)
+{
+    return (unsigned)((items + per_block - 1) / per_block);
+}
+
+template <class T, int K, bool XSTEP, bool GRAD>
+cudaError_t launch_pass(const Orient &o, const T *F, const T *W, int k, const LossSpec *loss,
+                        T *part_grad, double *part_loss, cudaStream_t st)
+{
+    if (o.nchunks == 0) return cudaSuccess;
+    const bool vec = (k == K) && ((reinterpret_cast<uintptr_t>(F) | reinterpret_cast<uintptr_t>(W)) % 16 == 0);
+    const unsigned nb = blocks_for(o.nchunks, kWarpsPerBlock);
+    if (vec)
+        pass_kernel<T, K, XSTEP, true, GRAD><<<nb, kWarpsPerBlock * 32, 0, st>>>(
+            o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+    else
+        pass_kernel<T, K, XSTEP, false, GRAD><<<nb, kWarpsPerBlock * 32, 0, st>>>(
+            o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+    return cudaGetLastError();
+}
+
+// Dispatch a runtime k to the smallest padded width K >= k.
+template <class T, bool XSTEP, bool GRAD>
+cudaError_t dispatch_pass(const Orient &o, const T *F, const T *W, int k, const LossSpec *loss,
+                          T *part_grad, double *part_loss, cudaStream_t st)
+{
+#define GLRM_PASS_CASE(KK) \
+    if (k <= KK) return launch_pass<T, KK, XSTEP, GRAD>(o, F, W, k, loss, part_grad, part_loss, st);
+    GLRM_PASS_CASE(4)
+    GLRM_PASS_CASE(8)
+    GLRM_PASS_CASE(12)
+    GLRM_PASS_CASE(16)
+    GLRM_PASS_CASE(20)
+    GLRM_PASS_CASE(24)
+    GLRM_PASS_CASE(32)
+    GLRM_PASS_CASE(48)
+    GLRM_PASS_CASE(64)
+#undef GLRM_PASS_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <class T>
+cudaError_t Engine<T>::half_step(glrm_s *h, bool xstep)
+{
+    const Orient &o = xstep ? h->csr : h->csc;
+    T *F = (T *)(xstep ? h->X : h->Yt);
+    const T *W = (const T *)(xstep ? h->Yt : h->X);
+    T *alpha = (T *)(xstep ? h->alpha_x : h->alpha_y);
+    const int rk = xstep ? h->rx_kind : h->ry_kind;
+    const T rw = (T)(xstep ? h->rx_w : h->ry_w);
+    Scratch &s = h->s;
+    cudaStream_t st = h->stream;
+    const int k = h->k;
+    const int pass_launches = o.nchunks ? 1 : 0;
+    cudaError_t e;
+    tmark(h, xstep ? "pass_grad_x" : "pass_grad_y");
+    e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st)
+              : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st);
+    if (e != cudaSuccess) return e;
+    const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
+    tmark(h, xstep ? "prox_x" : "prox_y");
+    prox_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const T *)s.part_grad,
+                                                       s.part_loss, F, alpha, k, rk, rw, (T *)s.cand,
+                                                       s.f_old, s.r_old, s.r_new);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tmark(h, xstep ? "pass_loss_x" : "pass_loss_y");
+    e = xstep ? dispatch_pass<T, true, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st)
+              : dispatch_pass<T, false, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st);
+    if (e != cudaSuccess) return e;
+    tmark(h, xstep ? "decide_x" : "decide_y");
+    decide_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
+        o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const T *)s.cand, F, alpha, k,
+        xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y,
+        xstep ? s.acc_x : s.acc_y);
+    tmark(h, nullptr);
+    h->launches += 2 + 2 * pass_launches;
+    return cudaGetLastError();
+}
+
+// Objective after a sweep: the Y-step's kept column objectives hold every
+// loss term plus rt(y_j); add the X-step's kept r(x_i).
+template <class T>
+cudaError_t Engine<T>::reduce_sweep(glrm_s *h, double *hist_slot)
+{
+    Scratch &s = h->s;
+    tmark(h, "reduce_stage1");
+    reduce_stage1<T><<<kRedBlocks, 256, 0, h->stream>>>(
+        s.kept_obj_y, h->n, s.kept_reg_x, h->m, nullptr, 0, 0, T(0), nullptr, 0, 0, T(0), h->k,
+        s.acc_x, h->m, s.acc_y, h->n, s.red_part, s.red_cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tmark(h, "reduce_stage2");
+    reduce_stage2<<<1, 256, 0, h->stream>>>(s.red_part, s.red_cnt, kRedBlocks, hist_slot, s.accepts);
+    tmark(h, nullptr);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Engine<T>::objective_at(glrm_s *h, const T *X, const T *Yt, double *out)
+{
+    Scratch &s = h->s;
+    tmark(h, "objective_pass");
+    cudaError_t e = dispatch_pass<T, true, false>(h->csr, X, Yt, h->k, h->loss_dev, nullptr,
+                                                  s.part_loss, h->stream);
+    if (e != cudaSuccess) return e;
+    tmark(h, "reduce_stage1");
+    reduce_stage1<T><<<kRedBlocks, 256, 0, h->stream>>>(
+        s.part_loss, h->csr.nchunks, nullptr, 0, X, h->m, h->rx_kind, (T)h->rx_w, Yt, h->n,
+        h->ry_kind, (T)h->ry_w, h->k, nullptr, 0, nullptr, 0, s.red_part, s.red_cnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tmark(h, "reduce_stage2");
+    reduce_stage2<<<1, 256, 0, h->stream>>>(s.red_part, s.red_cnt, kRedBlocks, out, nullptr);
+    tmark(h, nullptr);
+    h->launches += 2 + (h->csr.nchunks ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt, bool reg)
+{
+    Scratch &s = h->s;
+    tmark(h, "grad_pass_x");
+    cudaError_t e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev,
+                                                 (T *)s.part_grad, s.part_loss, h->stream);
+    if (e != cudaSuccess) return e;
+    tmark(h, "grad_seg_x");
+    seg_grad_kernel<T><<<blocks_for(h->m, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
+        h->m, h->csr.segchunk, (const T *)s.part_grad, X, h->k, h->rx_kind, (T)h->rx_w, reg, GX);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tmark(h, "grad_pass_y");
+    e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
+                                      s.part_loss, h->stream);
+    if (e != cudaSuccess) return e;
+    tmark(h, "grad_seg_y");
+    seg_grad_kernel<T><<<blocks_for(h->n, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
+        h->n, h->csc.segchunk, (const T *)s.part_grad, Yt, h->k, h->ry_kind, (T)h->ry_w, reg, GYt);
+    tmark(h, nullptr);
+    h->launches += 2 + (h->csr.nchunks ? 1 : 0) + (h->csc.nchunks ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Engine<T>::predict(glrm_s *h, int64_t cnt, const int32_t *rows, const int32_t *cols,
+                               T *out, bool decode)
+{
+    if (cnt == 0) return cudaSuccess;
+    h->launches += 1;
+    predict_kernel<T><<<blocks_for(cnt, 256), 256, 0, h->stream>>>(
+        cnt, rows, cols, (const T *)h->X, (const T *)h->Yt, h->m, h->n, h->k, h->loss_dev, decode,
+        out);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Engine<T>::reset_steps(glrm_s *h)
+{
+    h->launches += 2;
+    reset_alpha_kernel<T><<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->csr.ptr, h->m,
+                                                                       (T *)h->alpha_x);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reset_alpha_kernel<T><<<blocks_for(h->n, 256), 256, 0, h->stream>>>(h->csc.ptr, h->n,
+                                                                       (T *)h->alpha_y);
+    return cudaGetLastError();
+}
+
+}  // namespace glrm

@@ -1,0 +1,6 @@
+// FP32 instantiation of the sweep, objective, gradient, imputation and ALS
+// engines (compiled as its own translation unit so the precisions build in
+// parallel).
+#include "glrm_als.cuh"
+
+template struct glrm::Engine<float>;

@@ -1,0 +1,121 @@
+// Host-side state behind a glrm_t handle and the per-precision engine
+// interface.  Everything here is internal to libglrm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "glrm.h"
+#include "glrm_device.cuh"
+
+namespace glrm {
+
+// Entries of one segment (a row in CSR, a column in CSC) are cut into chunks
+// of at most kChunk entries; one warp processes one chunk.
+constexpr int kChunk = 1024;
+constexpr int kMaxK = 64;
+
+// One orientation of Omega: CSR (segments = rows, used by the X-step) or CSC
+// (segments = columns, used by the Y-step).
+struct Orient {
+    int64_t nseg = 0;
+    int32_t *ptr = nullptr;       // nseg + 1
+    int32_t *idx = nullptr;       // nnz: column (CSR) or row (CSC) of each entry
+    void *val = nullptr;          // nnz values, element type of the model
+    int4 *chunks = nullptr;       // {segment, begin, end, 0}
+    int32_t *segchunk = nullptr;  // nseg + 1: first chunk of each segment
+    int64_t nchunks = 0;
+    int32_t maxlen = 0;
+};
+
+struct Scratch {
+    void *part_grad = nullptr;     // max chunks x k, element type
+    double *part_loss = nullptr;   // max chunks
+    double *part_loss2 = nullptr;  // max chunks
+    void *cand = nullptr;          // max(m, n) x k candidate factors
+    double *f_old = nullptr, *r_old = nullptr, *r_new = nullptr;  // max(m, n)
+    double *kept_obj_x = nullptr, *kept_reg_x = nullptr;         // m
+    double *kept_obj_y = nullptr, *kept_reg_y = nullptr;         // n
+    int32_t *acc_x = nullptr, *acc_y = nullptr;                  // m, n
+    double *red_part = nullptr;     // kRedBlocks partial sums
+    long long *red_cnt = nullptr;   // kRedBlocks x 2 partial counts
+    double *hist = nullptr;         // hist_cap objective history
+    long long *accepts = nullptr;   // 2
+    double *scalar = nullptr;       // 1
+    int hist_cap = 0;
+    void *als_part = nullptr;       // ALS per-chunk Gram partials
+    size_t als_bytes = 0;
+};
+
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+
+// Optional per-launch timing: an event is recorded before every kernel launch
+// (tagged with the kernel's name) and after the last one, so consecutive
+// events on the handle's stream bracket exactly one kernel.
+struct Timer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<const char *, size_t>> marks;  // name (null = stop), event
+    std::map<std::string, std::pair<double, long long>> acc;  // ms, launches
+};
+
+}  // namespace glrm
+
+struct glrm_s {
+    int64_t m = 0, n = 0;
+    int k = 0;
+    int prec = GLRM_FP32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<glrm::LossSpec> loss_host;
+    glrm::LossSpec *loss_dev = nullptr;
+    int rx_kind = 0, ry_kind = 0;
+    float rx_w = 0.f, ry_w = 0.f;
+    void *X = nullptr, *Yt = nullptr;          // factors
+    void *alpha_x = nullptr, *alpha_y = nullptr;  // step sizes, element type
+    bool have_omega = false;
+    int64_t nnz = 0;
+    glrm::Orient csr, csc;
+    glrm::Scratch s;
+    glrm::Timer timer;
+    long long launches = 0;  // kernels enqueued since creation
+    int64_t sweeps_done = 0;
+    std::string err;
+};
+
+namespace glrm {
+
+size_t elem_size(int prec);
+
+// Record a timing mark before the launch of kernel `name` (null closes the
+// last interval).  No-op unless timing is enabled.
+void tmark(glrm_s *h, const char *name);
+
+// Per-precision launchers, instantiated for float and double in their own
+// translation units.  Each returns a cudaError_t of the launches.
+template <class T>
+struct Engine {
+    static cudaError_t half_step(glrm_s *h, bool xstep);
+    static cudaError_t reduce_sweep(glrm_s *h, double *hist_slot);
+    static cudaError_t objective_at(glrm_s *h, const T *X, const T *Yt, double *out);
+    static cudaError_t grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt, bool reg);
+    static cudaError_t predict(glrm_s *h, int64_t cnt, const int32_t *rows, const int32_t *cols,
+                               T *out, bool decode);
+    static cudaError_t reset_steps(glrm_s *h);
+    static cudaError_t als_half(glrm_s *h, bool xstep, float gamma);
+};
+
+// Validation of one orientation, writes bit flags into *flag (device int).
+cudaError_t launch_validate_ptr(const int32_t *ptr, int64_t nseg, int64_t nnz, int *flag,
+                                cudaStream_t st);
+cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const void *val,
+                                int prec, int64_t nseg, int64_t other, int *flag,
+                                cudaStream_t st);
+cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
+                                  cudaStream_t st);
+
+}  // namespace glrm

@@ -1,0 +1,329 @@
+"""Python binding of libglrm (C ABI in include/glrm.h).
+
+Argument marshalling only: every function here passes pointers and sizes to
+the CUDA library of the same name; all arithmetic runs in its kernels.  Device
+buffers are torch CUDA tensors; PyTorch supplies memory and the stream.  If
+the library is missing the import of this module fails loudly: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+GLRM_OK = 0
+GLRM_ERR_ARG, GLRM_ERR_RANGE, GLRM_ERR_OMEGA, GLRM_ERR_NONFINITE = -1, -2, -3, -4
+GLRM_ERR_CUDA, GLRM_ERR_TIMEOUT, GLRM_ERR_STATE, GLRM_ERR_NOMEM = -5, -6, -7, -8
+GLRM_LOSS_QUAD, GLRM_LOSS_HUBER, GLRM_LOSS_HINGE, GLRM_LOSS_LOGISTIC, GLRM_LOSS_ORDINAL_HINGE = range(5)
+GLRM_REG_ZERO, GLRM_REG_QUAD, GLRM_REG_L1, GLRM_REG_NONNEG = range(4)
+GLRM_FP64, GLRM_FP32, GLRM_BF16 = 0, 1, 2
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libglrm.so")
+
+
+class GLRMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libglrm error {code}: {msg}")
+        self.code = code
+
+
+class glrm_loss(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("param", ctypes.c_float), ("levels", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libglrm.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    p, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "glrm_create": [i64, i64, i32, p, i32, f32, i32, f32, i32, p, p],
+        "glrm_set_observed": [p, i64, p, p, p, p, p, p],
+        "glrm_set_observed_host": [p, i64, p, p, p, p, p, p],
+        "glrm_set_factors": [p, p, p],
+        "glrm_get_factors": [p, p, p],
+        "glrm_set_factors_host": [p, p, p],
+        "glrm_get_factors_host": [p, p, p],
+        "glrm_reset_steps": [p],
+        "glrm_sweep": [p, i32, p],
+        "glrm_last_accepts": [p, p],
+        "glrm_objective": [p, p],
+        "glrm_objective_at": [p, p, p, p],
+        "glrm_grad_at": [p, p, p, p, p, i32],
+        "glrm_predict": [p, i64, p, p, p, i32],
+        "glrm_als_sweep": [p, i32, p],
+        "glrm_get_state": [p, p, p],
+        "glrm_set_state": [p, p, ctypes.c_size_t],
+        "glrm_timing_enable": [p, i32],
+        "glrm_timing_read": [p, i32, p, p, p, p],
+        "glrm_launch_count": [p, p],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.glrm_last_error.argtypes = [p]
+    lib.glrm_last_error.restype = ctypes.c_char_p
+    lib.glrm_global_error.argtypes = []
+    lib.glrm_global_error.restype = ctypes.c_char_p
+    lib.glrm_destroy.argtypes = [p]
+    lib.glrm_destroy.restype = None
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    """The loaded ctypes library (for tests that check exported symbols)."""
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return t
+
+
+def _check(rc: int, h=None):
+    if rc != GLRM_OK:
+        msg = (_lib.glrm_last_error(h) if h else _lib.glrm_global_error()) or b""
+        raise GLRMError(rc, msg.decode(errors="replace"))
+
+
+def dtype_of(precision: int) -> torch.dtype:
+    return torch.float64 if precision == GLRM_FP64 else torch.float32
+
+
+# ------------------------------------------------------- same-name wrappers
+
+def glrm_create(m, n, k, col_loss, rx, ry, precision=GLRM_FP32, stream=None):
+    """col_loss: sequence of (kind, param, levels) per column, or arrays
+    (kind[n], param[n], levels[n]).  rx, ry: (kind, weight).  stream: a
+    torch.cuda.Stream (default: the current stream)."""
+    if isinstance(col_loss, tuple) and len(col_loss) == 3 and hasattr(col_loss[0], "__len__"):
+        kinds, params, levels = (np.asarray(a) for a in col_loss)
+    else:
+        arr = np.asarray(col_loss, dtype=np.float64).reshape(-1, 3)
+        kinds, params, levels = arr[:, 0], arr[:, 1], arr[:, 2]
+    losses = (glrm_loss * n)()
+    for j in range(n):
+        losses[j] = glrm_loss(int(kinds[j]), float(params[j]), int(levels[j]))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p()
+    _check(_lib.glrm_create(m, n, k, ctypes.cast(losses, ctypes.c_void_p), int(rx[0]),
+                            float(rx[1]), int(ry[0]), float(ry[1]), precision,
+                            ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+    return h
+
+
+def glrm_set_observed(h, nnz, csr_rowptr, csr_colidx, csr_val, csc_colptr, csc_rowidx, csc_val):
+    _check(_lib.glrm_set_observed(h, nnz, _ptr(csr_rowptr), _ptr(csr_colidx), _ptr(csr_val),
+                                  _ptr(csc_colptr), _ptr(csc_rowidx), _ptr(csc_val)), h)
+
+
+def glrm_set_observed_host(h, nnz, csr_rowptr, csr_colidx, csr_val, csc_colptr, csc_rowidx,
+                           csc_val):
+    _check(_lib.glrm_set_observed_host(h, nnz, _ptr(csr_rowptr), _ptr(csr_colidx),
+                                       _ptr(csr_val), _ptr(csc_colptr), _ptr(csc_rowidx),
+                                       _ptr(csc_val)), h)
+
+
+def glrm_set_factors(h, X, Yt):
+    _check(_lib.glrm_set_factors(h, _ptr(X), _ptr(Yt)), h)
+
+
+def glrm_get_factors(h, X, Yt):
+    _check(_lib.glrm_get_factors(h, _ptr(X), _ptr(Yt)), h)
+
+
+def glrm_set_factors_host(h, X, Yt):
+    _check(_lib.glrm_set_factors_host(h, _ptr(X), _ptr(Yt)), h)
+
+
+def glrm_get_factors_host(h, X, Yt):
+    _check(_lib.glrm_get_factors_host(h, _ptr(X), _ptr(Yt)), h)
+
+
+def glrm_reset_steps(h):
+    _check(_lib.glrm_reset_steps(h), h)
+
+
+def glrm_sweep(h, nsweeps, history=True):
+    """Returns the per-sweep objective (numpy float64) when history is True."""
+    if history:
+        out = np.empty(nsweeps, dtype=np.float64)
+        _check(_lib.glrm_sweep(h, nsweeps, _ptr(out)), h)
+        return out
+    _check(_lib.glrm_sweep(h, nsweeps, None), h)
+    return None
+
+
+def glrm_last_accepts(h):
+    out = np.zeros(2, dtype=np.int64)
+    _check(_lib.glrm_last_accepts(h, _ptr(out)), h)
+    return out
+
+
+def glrm_objective(h) -> float:
+    out = np.zeros(1, dtype=np.float64)
+    _check(_lib.glrm_objective(h, _ptr(out)), h)
+    return float(out[0])
+
+
+def glrm_objective_at(h, X, Yt, out):
+    _check(_lib.glrm_objective_at(h, _ptr(X), _ptr(Yt), _ptr(out)), h)
+
+
+def glrm_grad_at(h, X, Yt, GX, GYt, include_reg=True):
+    _check(_lib.glrm_grad_at(h, _ptr(X), _ptr(Yt), _ptr(GX), _ptr(GYt), int(bool(include_reg))), h)
+
+
+def glrm_predict(h, rows, cols, out, decode=True):
+    _check(_lib.glrm_predict(h, int(rows.numel()), _ptr(rows), _ptr(cols), _ptr(out),
+                             int(bool(decode))), h)
+
+
+def glrm_als_sweep(h, nsweeps, history=True):
+    if history:
+        out = np.empty(nsweeps, dtype=np.float64)
+        _check(_lib.glrm_als_sweep(h, nsweeps, _ptr(out)), h)
+        return out
+    _check(_lib.glrm_als_sweep(h, nsweeps, None), h)
+    return None
+
+
+def glrm_get_state(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(_lib.glrm_get_state(h, None, ctypes.byref(n)), h)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.glrm_get_state(h, buf, ctypes.byref(n)), h)
+    return buf.raw[:n.value]
+
+
+def glrm_set_state(h, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(_lib.glrm_set_state(h, buf, len(state)), h)
+
+
+def glrm_timing_enable(h, on=True):
+    _check(_lib.glrm_timing_enable(h, int(bool(on))), h)
+
+
+def glrm_timing_read(h, max_kernels=64):
+    """{kernel name: (total ms, launches)} recorded since timing was enabled."""
+    names = ctypes.create_string_buffer(32 * max_kernels)
+    ms = np.zeros(max_kernels, np.float64)
+    cnt = np.zeros(max_kernels, np.int64)
+    q = ctypes.c_int32(0)
+    _check(_lib.glrm_timing_read(h, max_kernels, names, _ptr(ms), _ptr(cnt), ctypes.byref(q)), h)
+    out = {}
+    for i in range(q.value):
+        nm = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[i]), int(cnt[i]))
+    return out
+
+
+def glrm_launch_count(h) -> int:
+    out = ctypes.c_int64(0)
+    _check(_lib.glrm_launch_count(h, ctypes.byref(out)), h)
+    return int(out.value)
+
+
+def glrm_destroy(h):
+    if h:
+        _lib.glrm_destroy(h)
+
+
+# ----------------------------------------------------------- convenience
+
+class GLRM:
+    """Owns one handle.  ``table`` is anything with the fields of
+    workloads.Table (m, n, k, CSR/CSC arrays, per-column losses, rx, ry)."""
+
+    def __init__(self, m, n, k, col_loss, rx, ry, precision=GLRM_FP32, device=None,
+                 stream=None):
+        self.m, self.n, self.k, self.precision = int(m), int(n), int(k), precision
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        self.dtype = dtype_of(precision)
+        with torch.cuda.device(self.device):
+            self.h = glrm_create(self.m, self.n, self.k, col_loss, rx, ry, precision, stream)
+
+    @classmethod
+    def from_table(cls, t, precision=GLRM_FP32, device=None, stream=None, factors=True):
+        g = cls(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry,
+                precision, device, stream)
+        g.set_observed_table(t)
+        if factors:
+            g.set_factors(torch.as_tensor(t.X0, dtype=g.dtype, device=g.device),
+                          torch.as_tensor(t.Yt0, dtype=g.dtype, device=g.device))
+        return g
+
+    def set_observed_table(self, t):
+        dev, dt = self.device, self.dtype
+        i32 = torch.int32
+        arrs = [torch.as_tensor(np.asarray(t.rowptr), dtype=i32, device=dev),
+                torch.as_tensor(np.asarray(t.colidx), dtype=i32, device=dev),
+                torch.as_tensor(np.asarray(t.val), dtype=dt, device=dev),
+                torch.as_tensor(np.asarray(t.colptr), dtype=i32, device=dev),
+                torch.as_tensor(np.asarray(t.rowidx), dtype=i32, device=dev),
+                torch.as_tensor(np.asarray(t.cval), dtype=dt, device=dev)]
+        with torch.cuda.device(self.device):
+            glrm_set_observed(self.h, int(t.colidx.size), *arrs)
+
+    def set_factors(self, X, Yt):
+        glrm_set_factors(self.h, X.contiguous() if X is not None else None,
+                         Yt.contiguous() if Yt is not None else None)
+
+    def factors(self):
+        X = torch.empty(self.m, self.k, dtype=self.dtype, device=self.device)
+        Yt = torch.empty(self.n, self.k, dtype=self.dtype, device=self.device)
+        glrm_get_factors(self.h, X, Yt)
+        return X, Yt
+
+    def sweep(self, nsweeps, history=True):
+        return glrm_sweep(self.h, nsweeps, history)
+
+    def als_sweep(self, nsweeps, history=True):
+        return glrm_als_sweep(self.h, nsweeps, history)
+
+    def objective(self):
+        return glrm_objective(self.h)
+
+    def accepts(self):
+        return glrm_last_accepts(self.h)
+
+    def predict(self, rows, cols, decode=True):
+        out = torch.empty(rows.numel(), dtype=self.dtype, device=self.device)
+        glrm_predict(self.h, rows.to(torch.int32).contiguous(), cols.to(torch.int32).contiguous(),
+                     out, decode)
+        return out
+
+    def state(self) -> bytes:
+        return glrm_get_state(self.h)
+
+    def load_state(self, s: bytes):
+        glrm_set_state(self.h, s)
+
+    def close(self):
+        if self.h:
+            glrm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,260 @@
+"""GPU parity of the proximal-gradient sweep, objective, gradient, imputation
+and ALS against the FP64 oracle, on the same seeded inputs.
+
+Tolerances: objectives after a fixed number of sweeps within 1e-4 relative
+on the FP32 path (1e-9 on the FP64 path); gradients within 1e-5 relative
+(norm-wise) on FP32; Omega handling and decoded Boolean / ordinal values
+bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1410_0342_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+Q, HU, HI, LO, OR = 0, 1, 2, 3, 4
+RZ, RQ, RL1, RNN = 0, 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1410_0342_gb300 import build
+    build.build()
+    from paper_1410_0342_gb300 import glrm
+    return glrm
+
+
+def oracle_problem(o, t, rx=None, ry=None):
+    return o.Problem.from_csr(t.m, t.n, t.k, t.rowptr, t.colidx, t.val, loss_kind=t.loss_kind,
+                              loss_param=t.loss_param, loss_levels=t.loss_levels,
+                              rx=rx or t.rx, ry=ry or t.ry)
+
+
+def relerr(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+def test_fp64_qpca_matches_oracle(G, oracle_mod):
+    t = W.qpca_dense()
+    g = G.GLRM.from_table(t, precision=G.GLRM_FP64)
+    hist = g.sweep(100)
+    acc = g.accepts()
+    X, Yt, ax, ay, ohist, oacc = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 100)
+    assert relerr(hist, ohist).max() < 1e-9
+    assert tuple(acc) == tuple(oacc[-1])
+    Xg, Ytg = g.factors()
+    np.testing.assert_allclose(Xg.cpu().numpy(), X, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(Ytg.cpu().numpy(), Yt, rtol=1e-7, atol=1e-9)
+
+
+def test_fp64_reaches_qpca_closed_form(G):
+    t = W.qpca_dense()
+    g = G.GLRM.from_table(t, precision=G.GLRM_FP64)
+    hist = g.sweep(3000)
+    A = t.val.reshape(t.m, t.n)
+    s = np.linalg.svd(A, compute_uv=False)
+    fstar = float(np.sum(A * A) - np.sum(np.maximum(s[:t.k] - 0.1, 0) ** 2))
+    assert (hist[-1] - fstar) / fstar < 1e-8
+
+
+@pytest.mark.parametrize("k", [6, 8, 19, 20, 33, 50, 64])
+def test_fp32_mixed_matches_oracle(G, oracle_mod, k):
+    t = W.small_mixed(m=211, n=57, k=k, seed=100 + k)
+    g = G.GLRM.from_table(t)
+    hist = g.sweep(25)
+    *_, ohist, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 25)
+    assert np.all(np.isfinite(hist))
+    assert relerr(hist, ohist).max() < 1e-4
+
+
+def test_fp32_multichunk_segments(G, oracle_mod):
+    """Columns of ~1500 entries (two chunks and a ragged tail) and rows with
+    zero entries."""
+    t = W.small_mixed(m=3001, n=130, k=20, p_obs=0.5, seed=31, rx=(RQ, 0.1), ry=(RL1, 0.02))
+    rowptr = t.rowptr.copy()
+    # empty rows 0, 17 and the last; empty column 5
+    keep = np.ones(t.nnz, bool)
+    rows = t.rows()
+    keep &= ~np.isin(rows, [0, 17, t.m - 1])
+    keep &= t.colidx != 5
+    t2 = _subset(t, keep)
+    g = G.GLRM.from_table(t2)
+    hist = g.sweep(20)
+    *_, ohist, oacc = oracle_problem(oracle_mod, t2).proxgrad(t2.X0, t2.Yt0, 20)
+    assert relerr(hist, ohist).max() < 1e-4
+
+
+def _subset(t, keep):
+    rows = t.rows()[keep]
+    cols = t.colidx[keep]
+    vals = t.val[keep]
+    rowptr = np.zeros(t.m + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=t.m), out=rowptr[1:])
+    colptr, rowidx, cval = W.csc_from_csr(t.m, t.n, rowptr, cols, vals)
+    return W.Table(t.name, t.m, t.n, t.k, rowptr, cols, vals, colptr, rowidx, cval,
+                   t.loss_kind, t.loss_param, t.loss_levels, t.rx, t.ry, t.X0, t.Yt0)
+
+
+def test_objective_and_gradient_match_oracle(G, oracle_mod):
+    t = W.small_mixed(m=1500, n=90, k=20, seed=41, rx=(RQ, 0.1), ry=(RL1, 0.05))
+    g = G.GLRM.from_table(t)
+    X = torch.as_tensor(t.X0, dtype=torch.float32, device="cuda")
+    Yt = torch.as_tensor(t.Yt0, dtype=torch.float32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.glrm_objective_at(g.h, X, Yt, out)
+    p = oracle_problem(oracle_mod, t)
+    # the oracle evaluates at the same float32-rounded factors
+    Xd, Yd = X.double().cpu().numpy(), Yt.double().cpu().numpy()
+    assert relerr(out.item(), p.objective(Xd, Yd)) < 1e-5
+    GX = torch.empty_like(X)
+    GY = torch.empty_like(Yt)
+    G.glrm_grad_at(g.h, X, Yt, GX, GY, include_reg=False)
+    oGX, oGY = p.gradient(Xd, Yd)
+    for a, b in ((GX, oGX), (GY, oGY)):
+        a = a.double().cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
+    G.glrm_grad_at(g.h, X, Yt, GX, GY, include_reg=True)
+    rgx = oGX + 2 * 0.1 * Xd
+    rgy = oGY + 0.05 * np.sign(Yd)
+    assert np.linalg.norm(GX.double().cpu().numpy() - rgx) / np.linalg.norm(rgx) < 1e-5
+    assert np.linalg.norm(GY.double().cpu().numpy() - rgy) / np.linalg.norm(rgy) < 1e-5
+
+
+def test_decode_bit_exact(G, oracle_mod):
+    """Decoded values equal the oracle's decode of the same u, including the
+    half-integer ties of the ordinal hinge and u = 0 for Boolean columns."""
+    t = W.small_mixed(m=300, n=60, k=6, seed=51)
+    g = G.GLRM.from_table(t)
+    g.sweep(5)
+    rng = np.random.default_rng(0)
+    rows = torch.as_tensor(rng.integers(0, t.m, 20000), dtype=torch.int32, device="cuda")
+    cols = torch.as_tensor(rng.integers(0, t.n, 20000), dtype=torch.int32, device="cuda")
+    u = g.predict(rows, cols, decode=False).cpu().numpy()
+    dec = g.predict(rows, cols, decode=True).cpu().numpy()
+    c = cols.cpu().numpy()
+    for e in range(u.size):
+        j = c[e]
+        ref = oracle_mod.decode(int(t.loss_kind[j]), float(u[e]), int(t.loss_levels[j]))
+        assert dec[e] == np.float32(ref), (e, j, u[e], dec[e], ref)
+    # exact ties through a handle whose factors produce chosen u values
+    k = 1
+    n = 8
+    us = np.array([0.0, -0.0, 1.5, 2.5, 3.5, 6.5, 2.4999998, 2.5000002], np.float32)
+    kinds = np.array([HI, LO, OR, OR, OR, OR, OR, OR])
+    gg = G.GLRM(1, n, k, (kinds, np.zeros(n), np.where(kinds == OR, 7, 0)), (RZ, 0.0), (RZ, 0.0))
+    tt = W.Table("ties", 1, n, k, np.array([0, n]), np.arange(n, dtype=np.int32),
+                 np.where(kinds == OR, 1.0, 1.0), np.arange(n + 1), np.zeros(n, np.int32),
+                 np.ones(n), kinds, np.zeros(n), np.where(kinds == OR, 7, 0), (RZ, 0.0),
+                 (RZ, 0.0), np.ones((1, 1)), us.reshape(n, 1).astype(np.float64))
+    gg.set_observed_table(tt)
+    gg.set_factors(torch.ones(1, 1, device="cuda"), torch.as_tensor(us.reshape(n, 1), device="cuda"))
+    r = torch.zeros(n, dtype=torch.int32, device="cuda")
+    cc = torch.arange(n, dtype=torch.int32, device="cuda")
+    d = gg.predict(r, cc).cpu().numpy()
+    for j in range(n):
+        ref = oracle_mod.decode(int(kinds[j]), float(us[j]), 7)
+        assert d[j] == np.float32(ref), (j, us[j], d[j], ref)
+
+
+def test_deterministic_and_resumable(G):
+    t = W.small_mixed(m=800, n=70, k=12, seed=61)
+    g1 = G.GLRM.from_table(t)
+    h1 = g1.sweep(10)
+    g2 = G.GLRM.from_table(t)
+    h2a = g2.sweep(4)
+    st = g2.state()
+    g3 = G.GLRM.from_table(t, factors=False)
+    g3.load_state(st)
+    h3 = g3.sweep(6)
+    np.testing.assert_array_equal(h1, np.concatenate([h2a, h3]))
+    X1, Y1 = g1.factors()
+    X3, Y3 = g3.factors()
+    assert torch.equal(X1, X3) and torch.equal(Y1, Y3)
+
+
+def test_als_matches_oracle(G, oracle_mod):
+    t = W.qpca_dense()
+    g = G.GLRM.from_table(t, precision=G.GLRM_FP64)
+    hist = g.als_sweep(30)
+    X, Yt, ohist = oracle_problem(oracle_mod, t).als(t.X0, t.Yt0, 0.1, 30)
+    assert relerr(hist, ohist).max() < 1e-9
+    # missing data, FP32 Gram accumulation, k = 16
+    t2 = W.batch_instance(0, m_range=(400, 400), n_range=(120, 120), ks=(16,))
+    g2 = G.GLRM.from_table(t2)
+    h2 = g2.als_sweep(10)
+    *_, oh2 = oracle_problem(oracle_mod, t2).als(t2.X0, t2.Yt0, 0.1, 10)
+    assert relerr(h2, oh2).max() < 1e-4
+
+
+def test_als_rejects_non_quadratic(G):
+    t = W.small_mixed(m=50, n=20, k=4)
+    g = G.GLRM.from_table(t)
+    with pytest.raises(G.GLRMError) as e:
+        g.als_sweep(1)
+    assert e.value.code == G.GLRM_ERR_ARG
+
+
+def _omega_tensors(t, dt=torch.float32):
+    i32 = torch.int32
+    return [torch.as_tensor(t.rowptr, dtype=i32, device="cuda"),
+            torch.as_tensor(t.colidx, dtype=i32, device="cuda"),
+            torch.as_tensor(t.val, dtype=dt, device="cuda"),
+            torch.as_tensor(t.colptr, dtype=i32, device="cuda"),
+            torch.as_tensor(t.rowidx, dtype=i32, device="cuda"),
+            torch.as_tensor(t.cval, dtype=dt, device="cuda")]
+
+
+@pytest.mark.parametrize("fault", ["ptr", "range", "dup", "unsorted", "cross", "value", "nan"])
+def test_observed_set_validation(G, fault):
+    t = W.small_mixed(m=40, n=15, k=4, seed=71)
+    g = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry)
+    a = _omega_tensors(t)
+    if fault == "ptr":
+        a[0][3] = a[0][4] + 1
+    elif fault == "range":
+        a[1][5] = t.n
+    elif fault == "dup":
+        r = int(np.argmax(np.diff(t.rowptr) >= 2))
+        a[1][int(t.rowptr[r]) + 1] = a[1][int(t.rowptr[r])]
+    elif fault == "unsorted":
+        r = int(np.argmax(np.diff(t.rowptr) >= 2))
+        b = int(t.rowptr[r])
+        a[1][b], a[1][b + 1] = a[1][b + 1].clone(), a[1][b].clone()
+    elif fault == "cross":
+        a[4][0] = (a[4][0] + 1) % t.m
+    elif fault == "value":
+        a[5][3] += 1.0
+    elif fault == "nan":
+        a[2][2] = float("nan")
+    with pytest.raises(G.GLRMError) as e:
+        G.glrm_set_observed(g.h, t.nnz, *a)
+    expect = G.GLRM_ERR_NONFINITE if fault == "nan" else G.GLRM_ERR_OMEGA
+    assert e.value.code == expect
+    with pytest.raises(G.GLRMError) as e:
+        g.sweep(1)
+    assert e.value.code == G.GLRM_ERR_STATE
+    # a valid set afterwards works
+    G.glrm_set_observed(g.h, t.nnz, *_omega_tensors(t))
+    assert np.isfinite(g.sweep(1)).all()
+
+
+def test_host_entry_points(G, oracle_mod):
+    t = W.small_mixed(m=120, n=40, k=5, seed=81)
+    g = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry)
+    G.glrm_set_observed_host(g.h, t.nnz, t.rowptr.astype(np.int32), t.colidx,
+                             t.val.astype(np.float32), t.colptr.astype(np.int32), t.rowidx,
+                             t.cval.astype(np.float32))
+    G.glrm_set_factors_host(g.h, t.X0.astype(np.float32), t.Yt0.astype(np.float32))
+    hist = g.sweep(10)
+    *_, ohist, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 10)
+    assert relerr(hist, ohist).max() < 1e-4
+    X = np.empty((t.m, t.k), np.float32)
+    Y = np.empty((t.n, t.k), np.float32)
+    G.glrm_get_factors_host(g.h, X, Y)
+    Xd, Yd = g.factors()
+    np.testing.assert_array_equal(X, Xd.cpu().numpy())
+    np.testing.assert_array_equal(Y, Yd.cpu().numpy())
