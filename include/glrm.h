@@ -90,20 +90,21 @@ typedef enum { GLRM_FP64 = 0, GLRM_FP32 = 1, GLRM_BF16 = 2 } glrm_precision;
 
 typedef struct {
     int32_t kind;   /* glrm_loss_kind */
-    float param;    /* Huber delta; ignored otherwise */
     int32_t levels; /* ordinal level count d >= 2; ignored otherwise */
+    double param;   /* Huber delta; ignored otherwise */
 } glrm_loss;
 
 /* Limits: 1 <= k <= 64; m, n >= 1; m, n, nnz < 2^31. */
 
 /* Create a model of m rows, n columns and rank k.
  * col_loss_host: n loss descriptors, copied.  rx / ry: regulariser kind and
- * weight for the rows of X and the columns of Y.  precision: glrm_precision.
+ * weight for the rows of X and the columns of Y (used in the model's element
+ * type, so FP64 models see the weights exactly).  precision: glrm_precision.
  * stream: a cudaStream_t (NULL = legacy default stream) on which every later
  * call enqueues its work.  Allocates the factors (zero) and step sizes on the
  * current CUDA device.  Section 4 (eq. gpca) defines the model. */
 int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss_host,
-                int32_t rx_kind, float rx_weight, int32_t ry_kind, float ry_weight,
+                int32_t rx_kind, double rx_weight, int32_t ry_kind, double ry_weight,
                 int32_t precision, void *stream, glrm_t *out);
 
 /* Give the model its observed set Omega (Section 2.5; Section 5) in both

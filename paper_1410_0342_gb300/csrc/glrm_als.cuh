@@ -133,7 +133,7 @@ als_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__
 }
 
 template <class T, int K>
-cudaError_t launch_als_half(glrm_s *h, bool xstep, float gamma)
+cudaError_t launch_als_half(glrm_s *h, bool xstep, double gamma)
 {
     const Orient &o = xstep ? h->csr : h->csc;
     T *F = (T *)(xstep ? h->X : h->Yt);
@@ -158,13 +158,13 @@ cudaError_t launch_als_half(glrm_s *h, bool xstep, float gamma)
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "als_solve_x" : "als_solve_y");
     als_solve_kernel<T, K><<<blocks_for(o.nseg, kAlsWarps), kAlsWarps * 32, 0, h->stream>>>(
-        o.nseg, o.segchunk, part, h->k, (double)gamma, F);
+        o.nseg, o.segchunk, part, h->k, gamma, F);
     tmark(h, nullptr);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t Engine<T>::als_half(glrm_s *h, bool xstep, float gamma)
+cudaError_t Engine<T>::als_half(glrm_s *h, bool xstep, double gamma)
 {
     const int k = h->k;
     if (k <= 4) return launch_als_half<T, 4>(h, xstep, gamma);

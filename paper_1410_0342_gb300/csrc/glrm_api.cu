@@ -303,7 +303,7 @@ const char *glrm_global_error(void) { return g_error.c_str(); }
 const char *glrm_last_error(glrm_t h) { return h ? h->err.c_str() : g_error.c_str(); }
 
 int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss, int32_t rx_kind,
-                float rx_weight, int32_t ry_kind, float ry_weight, int32_t precision, void *stream,
+                double rx_weight, int32_t ry_kind, double ry_weight, int32_t precision, void *stream,
                 glrm_t *out)
 {
     g_error.clear();
@@ -316,19 +316,19 @@ int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss, int3
     if (!col_loss) return fail(nullptr, GLRM_ERR_ARG, "col_loss is null");
     for (int r : {rx_kind, ry_kind})
         if (r < kRegZero || r > kRegNonneg) return fail(nullptr, GLRM_ERR_ARG, "bad regulariser kind");
-    if (!(rx_weight >= 0.f) || !(ry_weight >= 0.f) || !isfinite(rx_weight) || !isfinite(ry_weight))
+    if (!(rx_weight >= 0.0) || !(ry_weight >= 0.0) || !isfinite(rx_weight) || !isfinite(ry_weight))
         return fail(nullptr, GLRM_ERR_ARG, "regulariser weights must be finite and >= 0");
     std::vector<LossSpec> spec((size_t)n);
     for (int64_t j = 0; j < n; ++j) {
         const glrm_loss &L = col_loss[j];
         if (L.kind < kLossQuad || L.kind > kLossOrdinal)
             return fail(nullptr, GLRM_ERR_ARG, "bad loss kind in column " + std::to_string(j));
-        if (L.kind == kLossHuber && !(L.param > 0.f && isfinite(L.param)))
+        if (L.kind == kLossHuber && !(L.param > 0.0 && isfinite(L.param)))
             return fail(nullptr, GLRM_ERR_ARG, "Huber threshold must be > 0 (column " + std::to_string(j) + ")");
         if (L.kind == kLossOrdinal && (L.levels < 2 || L.levels > 1024))
             return fail(nullptr, GLRM_ERR_ARG, "ordinal levels must be in [2, 1024] (column " + std::to_string(j) + ")");
         spec[j] = LossSpec{L.kind, L.kind == kLossOrdinal ? L.levels : 0,
-                           L.kind == kLossHuber ? L.param : 0.f, 0.f};
+                           L.kind == kLossHuber ? L.param : 0.0};
     }
     glrm_s *h = new (std::nothrow) glrm_s;
     if (!h) return fail(nullptr, GLRM_ERR_NOMEM, "host allocation failed");
@@ -517,7 +517,7 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_als_sweep before glrm_set_observed");
     if (nsweeps < 0) return fail(h, GLRM_ERR_ARG, "nsweeps < 0");
-    if (h->rx_kind != kRegQuad || h->ry_kind != kRegQuad || h->rx_w != h->ry_w || !(h->rx_w > 0.f))
+    if (h->rx_kind != kRegQuad || h->ry_kind != kRegQuad || h->rx_w != h->ry_w || !(h->rx_w > 0.0))
         return fail(h, GLRM_ERR_ARG,
                     "ALS needs quadratic regularisers of equal weight gamma > 0 on X and Y");
     if (h->k > 32) return fail(h, GLRM_ERR_RANGE, "ALS supports k <= 32");

@@ -18,8 +18,7 @@ constexpr int kRegZero = 0, kRegQuad = 1, kRegL1 = 2, kRegNonneg = 3;
 struct __align__(16) LossSpec {
     int32_t kind;
     int32_t levels;
-    float param;
-    float pad;
+    double param;
 };
 
 __device__ __forceinline__ float xexp(float x) { return expf(x); }

@@ -74,7 +74,7 @@ struct glrm_s {
     std::vector<glrm::LossSpec> loss_host;
     glrm::LossSpec *loss_dev = nullptr;
     int rx_kind = 0, ry_kind = 0;
-    float rx_w = 0.f, ry_w = 0.f;
+    double rx_w = 0.0, ry_w = 0.0;
     void *X = nullptr, *Yt = nullptr;          // factors
     void *alpha_x = nullptr, *alpha_y = nullptr;  // step sizes, element type
     bool have_omega = false;
@@ -106,7 +106,7 @@ struct Engine {
     static cudaError_t predict(glrm_s *h, int64_t cnt, const int32_t *rows, const int32_t *cols,
                                T *out, bool decode);
     static cudaError_t reset_steps(glrm_s *h);
-    static cudaError_t als_half(glrm_s *h, bool xstep, float gamma);
+    static cudaError_t als_half(glrm_s *h, bool xstep, double gamma);
 };
 
 // Validation of one orientation, writes bit flags into *flag (device int).

@@ -31,16 +31,16 @@ class GLRMError(RuntimeError):
 
 
 class glrm_loss(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("param", ctypes.c_float), ("levels", ctypes.c_int32)]
+    _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32), ("param", ctypes.c_double)]
 
 
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libglrm.so not built ({_LIB_PATH}); run __graft_entry__.build()")
     lib = ctypes.CDLL(_LIB_PATH)
-    p, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    p, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     sig = {
-        "glrm_create": [i64, i64, i32, p, i32, f32, i32, f32, i32, p, p],
+        "glrm_create": [i64, i64, i32, p, i32, f64, i32, f64, i32, p, p],
         "glrm_set_observed": [p, i64, p, p, p, p, p, p],
         "glrm_set_observed_host": [p, i64, p, p, p, p, p, p],
         "glrm_set_factors": [p, p, p],
@@ -119,7 +119,7 @@ def glrm_create(m, n, k, col_loss, rx, ry, precision=GLRM_FP32, stream=None):
         kinds, params, levels = arr[:, 0], arr[:, 1], arr[:, 2]
     losses = (glrm_loss * n)()
     for j in range(n):
-        losses[j] = glrm_loss(int(kinds[j]), float(params[j]), int(levels[j]))
+        losses[j] = glrm_loss(int(kinds[j]), int(levels[j]), float(params[j]))
     if stream is None:
         stream = torch.cuda.current_stream()
     h = ctypes.c_void_p()

@@ -41,15 +41,15 @@ def test_every_declared_symbol_is_exported(lib):
 
 def _create(lib, m, n, k, losses, rx=(0, 0.0), ry=(0, 0.0), prec=1):
     class L(ctypes.Structure):
-        _fields_ = [("kind", ctypes.c_int32), ("param", ctypes.c_float),
-                    ("levels", ctypes.c_int32)]
-    arr = (L * max(1, len(losses)))(*[L(*x) for x in losses])
+        _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32),
+                    ("param", ctypes.c_double)]
+    arr = (L * max(1, len(losses)))(*[L(x[0], x[2], x[1]) for x in losses])
     h = ctypes.c_void_p()
     lib.glrm_create.restype = ctypes.c_int
     lib.glrm_global_error.restype = ctypes.c_char_p
     rc = lib.glrm_create(ctypes.c_int64(m), ctypes.c_int64(n), ctypes.c_int32(k), arr,
-                         ctypes.c_int32(rx[0]), ctypes.c_float(rx[1]), ctypes.c_int32(ry[0]),
-                         ctypes.c_float(ry[1]), ctypes.c_int32(prec), None, ctypes.byref(h))
+                         ctypes.c_int32(rx[0]), ctypes.c_double(rx[1]), ctypes.c_int32(ry[0]),
+                         ctypes.c_double(ry[1]), ctypes.c_int32(prec), None, ctypes.byref(h))
     return rc, lib.glrm_global_error().decode()
 
 
