@@ -214,6 +214,30 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history_host);
 int glrm_get_state(glrm_t h, void *buf_host, size_t *len);
 int glrm_set_state(glrm_t h, const void *buf_host, size_t len);
 
+/* Kernel path of each half-step (a tuning knob; results agree to rounding).
+ *   GLRM_PATH_CHUNKED  entries cut into chunks of <= 1024, one warp each; the
+ *                      other factor read from global memory (any k, any size)
+ *   GLRM_PATH_FUSED    the whole other factor staged in each CTA's shared
+ *                      memory by a TMA bulk copy; one warp runs a row's (column's)
+ *                      gradient, prox, re-evaluation and decision in one kernel
+ *   GLRM_PATH_BLOCKED  the other factor staged panel by panel (TMA); per
+ *                      (panel, segment) partials summed over panels in a fixed
+ *                      order
+ * GLRM_PATH_AUTO picks fused when the other factor fits, else blocked when a
+ * (panel, segment) run holds >= 64 entries on average, else chunked.  The
+ * staged paths need k <= 32.  glrm_set_path(h, xstep_path, ystep_path) may be
+ * called before or after glrm_set_observed; an infeasible request returns
+ * GLRM_ERR_ARG and restores GLRM_PATH_AUTO.  glrm_get_path writes the paths in
+ * use (2 values, never AUTO) after glrm_set_observed. */
+typedef enum {
+    GLRM_PATH_AUTO = 0,
+    GLRM_PATH_CHUNKED = 1,
+    GLRM_PATH_FUSED = 2,
+    GLRM_PATH_BLOCKED = 3
+} glrm_path;
+int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path);
+int glrm_get_path(glrm_t h, int32_t *paths_host);
+
 /* Instrumentation (not part of the method).  glrm_timing_enable(h, 1)
  * records a CUDA event on the handle's stream before every kernel the handle
  * launches and after the last one, so each kernel's device time is measured

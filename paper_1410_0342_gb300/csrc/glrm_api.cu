@@ -51,8 +51,12 @@ void free_orient(Orient &o)
     dfree(o.val);
     dfree(o.chunks);
     dfree(o.segchunk);
+    dfree(o.runptr);
     o.nchunks = 0;
     o.maxlen = 0;
+    o.mode = kModeChunked;
+    o.R = o.nb = o.ngroups = o.grid = 0;
+    o.smem_bytes = 0;
 }
 
 void free_scratch(Scratch &s)
@@ -61,7 +65,7 @@ void free_scratch(Scratch &s)
     dfree(s.f_old); dfree(s.r_old); dfree(s.r_new);
     dfree(s.kept_obj_x); dfree(s.kept_reg_x); dfree(s.kept_obj_y); dfree(s.kept_reg_y);
     dfree(s.acc_x); dfree(s.acc_y); dfree(s.red_part); dfree(s.red_cnt);
-    dfree(s.hist); dfree(s.accepts); dfree(s.scalar); dfree(s.als_part);
+    dfree(s.hist); dfree(s.accepts); dfree(s.scalar); dfree(s.als_part); dfree(s.err);
     s.hist_cap = 0;
     s.als_bytes = 0;
 }
@@ -87,7 +91,77 @@ cudaError_t run_half(glrm_s *h, bool xstep) { return Engine<T>::half_step(h, xst
 
 cudaError_t half_step(glrm_s *h, bool xstep)
 {
+    const Orient &o = xstep ? h->csr : h->csc;
+    if (o.mode != kModeChunked)
+        return h->prec == GLRM_FP64 ? Engine<double>::tiled_half_step(h, xstep)
+                                    : Engine<float>::tiled_half_step(h, xstep);
     return h->prec == GLRM_FP64 ? run_half<double>(h, xstep) : run_half<float>(h, xstep);
+}
+
+// Padded width the staged kernels use for k (0: not supported there).
+int tiled_width(int k)
+{
+    for (int K : {4, 8, 12, 16, 20, 24, 32})
+        if (k <= K) return K;
+    return 0;
+}
+
+// Pick fused / blocked / chunked for one orientation: fused when the whole
+// other factor (plus, for the X-step, its loss table) fits in one CTA's shared
+// memory; blocked when panels of it do and a (panel, segment) run holds 64
+// entries or more on average; chunked otherwise.
+int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
+{
+    int dev = h->device, optin = 0, sms = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    dfree(o.runptr);
+    const int K = tiled_width(h->k);
+    o.mode = kModeChunked;
+    if (force == GLRM_PATH_CHUNKED) return GLRM_OK;
+    if (K == 0 || h->nnz == 0) {
+        if (force == GLRM_PATH_AUTO) return GLRM_OK;
+        return fail(h, GLRM_ERR_ARG, "the staged paths need 1 <= k <= 32 and a non-empty Omega");
+    }
+    const size_t es = elem_size(h->prec);
+    const int64_t nother = xstep ? h->n : h->m;
+    const size_t per_row = (size_t)K * es + (xstep ? sizeof(LossSpec) : 0);
+    const size_t budget = (size_t)optin - 1024;
+    const size_t fused = (((size_t)nother * K * es + 15) & ~(size_t)15) +
+                         (xstep ? (size_t)nother * sizeof(LossSpec) : 0);
+    const bool fused_ok = fused <= budget;
+    if (force == GLRM_PATH_FUSED && !fused_ok)
+        return fail(h, GLRM_ERR_ARG, "fused path: the other factor does not fit in shared memory");
+    if (force == GLRM_PATH_FUSED || (force == GLRM_PATH_AUTO && fused_ok && o.maxlen <= 8192)) {
+        o.mode = kModeFused;
+        o.smem_bytes = fused;
+        const int64_t want = (o.nseg + 15) / 16;
+        o.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms));
+        return GLRM_OK;
+    }
+    int R = (int)std::min<size_t>((budget / per_row) & ~(size_t)31, (size_t)1 << 20);
+    if (force == GLRM_PATH_BLOCKED && R > 32) {
+        // forced: at least two panels when the factor allows, so the partial
+        // reduction over panels is exercised
+        const int64_t half = ((nother + 1) / 2 + 31) & ~(int64_t)31;
+        R = (int)std::max<int64_t>(32, std::min<int64_t>(R, half));
+    }
+    if (R < 32) {
+        if (force == GLRM_PATH_AUTO) return GLRM_OK;
+        return fail(h, GLRM_ERR_ARG, "blocked path: shared memory too small");
+    }
+    const int nb = (int)((nother + R - 1) / R);
+    const double avg_run = (double)h->nnz / ((double)nb * (double)o.nseg);
+    if (force == GLRM_PATH_AUTO && avg_run < 64.0) return GLRM_OK;
+    o.mode = kModeBlocked;
+    o.R = R;
+    o.nb = nb;
+    o.grid = sms;
+    o.ngroups = (int)std::max<int64_t>(1, std::min<int64_t>(o.nseg, (4LL * sms + nb - 1) / nb));
+    o.smem_bytes = (((size_t)R * K * es + 15) & ~(size_t)15) + (xstep ? (size_t)R * sizeof(LossSpec) : 0);
+    CK(cudaMalloc(&o.runptr, (size_t)(nb + 1) * o.nseg * sizeof(int32_t)));
+    CK(launch_build_runptr(o, h->stream));
+    return GLRM_OK;
 }
 
 cudaError_t reduce_sweep(glrm_s *h, double *slot)
@@ -114,14 +188,22 @@ void build_chunks(const std::vector<int32_t> &ptr, std::vector<int4> &chunks,
     segchunk[nseg] = (int32_t)chunks.size();
 }
 
+// Number of partial slots an orientation's passes write (chunks, or
+// panels x segments when blocked).
+int64_t partial_slots(const Orient &o)
+{
+    return o.mode == kModeBlocked ? (int64_t)o.nb * o.nseg : o.nchunks;
+}
+
 int alloc_scratch(glrm_s *h)
 {
     Scratch &s = h->s;
     free_scratch(s);
     const size_t es = elem_size(h->prec);
-    const int64_t nch = std::max<int64_t>(1, std::max(h->csr.nchunks, h->csc.nchunks));
+    const int64_t nch = std::max<int64_t>(1, std::max(partial_slots(h->csr), partial_slots(h->csc)));
+    const int Kt = std::max(h->k, tiled_width(h->k));
     const int64_t mx = std::max(h->m, h->n);
-    CK(cudaMalloc(&s.part_grad, (size_t)nch * h->k * es));
+    CK(cudaMalloc(&s.part_grad, (size_t)nch * Kt * es));
     CK(cudaMalloc(&s.part_loss, (size_t)nch * sizeof(double)));
     CK(cudaMalloc(&s.part_loss2, (size_t)nch * sizeof(double)));
     CK(cudaMalloc(&s.cand, (size_t)mx * h->k * es));
@@ -138,7 +220,9 @@ int alloc_scratch(glrm_s *h)
     CK(cudaMalloc(&s.red_cnt, 2 * kRedBlocks * sizeof(long long)));
     CK(cudaMalloc(&s.accepts, 2 * sizeof(long long)));
     CK(cudaMalloc(&s.scalar, sizeof(double)));
+    CK(cudaMalloc(&s.err, sizeof(int)));
     CK(cudaMemsetAsync(s.accepts, 0, 2 * sizeof(long long), h->stream));
+    CK(cudaMemsetAsync(s.err, 0, sizeof(int), h->stream));
     return GLRM_OK;
 }
 
@@ -244,7 +328,9 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         CK(cudaMemcpy(o->segchunk, segchunk.data(), segchunk.size() * sizeof(int32_t),
                       cudaMemcpyHostToDevice));
     }
-    rc = alloc_scratch(h);
+    rc = choose_mode(h, R, true, h->path_x);
+    if (rc == GLRM_OK) rc = choose_mode(h, C, false, h->path_y);
+    if (rc == GLRM_OK) rc = alloc_scratch(h);
     if (rc != GLRM_OK) return rc;
     h->have_omega = true;
     e = h->prec == GLRM_FP64 ? Engine<double>::reset_steps(h) : Engine<float>::reset_steps(h);
@@ -442,7 +528,14 @@ int glrm_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (history) {
         CK(cudaMemcpyAsync(history, h->s.hist, (size_t)nsweeps * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
+        int flag = 0;
+        CK(cudaMemcpyAsync(&flag, h->s.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+        if (flag) {
+            cudaMemsetAsync(h->s.err, 0, sizeof(int), h->stream);
+            return fail(h, GLRM_ERR_TIMEOUT, "a staged copy into shared memory did not complete "
+                                             "within its wait limit; results of this call are invalid");
+        }
     }
     return GLRM_OK;
 }
@@ -601,6 +694,48 @@ int glrm_set_state(glrm_t h, const void *buf, size_t len)
     CK(cudaMemcpyAsync(h->alpha_y, p, es * h->n, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->sweeps_done = hdr[6];
+    return GLRM_OK;
+}
+
+int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    for (int p : {xstep_path, ystep_path})
+        if (p < GLRM_PATH_AUTO || p > GLRM_PATH_BLOCKED) return fail(h, GLRM_ERR_ARG, "bad path");
+    h->path_x = xstep_path;
+    h->path_y = ystep_path;
+    if (!h->have_omega) return GLRM_OK;
+    DeviceGuard dg(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    int rc = choose_mode(h, h->csr, true, h->path_x);
+    if (rc == GLRM_OK) rc = choose_mode(h, h->csc, false, h->path_y);
+    if (rc == GLRM_OK) {
+        // keep the fit state; only scratch depends on the paths
+        const int hist_cap = h->s.hist_cap;
+        rc = alloc_scratch(h);
+        if (rc == GLRM_OK && hist_cap) rc = ensure_hist(h, hist_cap);
+    }
+    if (rc != GLRM_OK) {
+        h->path_x = h->path_y = GLRM_PATH_AUTO;
+        choose_mode(h, h->csr, true, GLRM_PATH_AUTO);
+        choose_mode(h, h->csc, false, GLRM_PATH_AUTO);
+        alloc_scratch(h);
+        return rc;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return GLRM_OK;
+}
+
+int glrm_get_path(glrm_t h, int32_t *paths_host)
+{
+    if (!h || !paths_host) return fail(h, GLRM_ERR_ARG, "null argument");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    auto code = [](int mode) {
+        return mode == kModeFused ? GLRM_PATH_FUSED
+                                  : (mode == kModeBlocked ? GLRM_PATH_BLOCKED : GLRM_PATH_CHUNKED);
+    };
+    paths_host[0] = code(h->csr.mode);
+    paths_host[1] = code(h->csc.mode);
     return GLRM_OK;
 }
 

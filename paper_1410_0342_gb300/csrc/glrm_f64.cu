@@ -2,5 +2,6 @@
 // engines (compiled as its own translation unit so the precisions build in
 // parallel).
 #include "glrm_als.cuh"
+#include "glrm_tiled.cuh"
 
 template struct glrm::Engine<double>;

@@ -19,6 +19,13 @@ namespace glrm {
 constexpr int kChunk = 1024;
 constexpr int kMaxK = 64;
 
+// How a half-step runs over one orientation (chosen at set-up):
+// chunked: entries cut into chunks, the other factor gathered from global
+//          memory (L1/L2); any size.
+// fused:   the whole other factor staged in shared memory per CTA; one kernel.
+// blocked: the other factor staged panel by panel; partials per (panel, segment).
+constexpr int kModeChunked = 0, kModeFused = 1, kModeBlocked = 2;
+
 // One orientation of Omega: CSR (segments = rows, used by the X-step) or CSC
 // (segments = columns, used by the Y-step).
 struct Orient {
@@ -30,6 +37,11 @@ struct Orient {
     int32_t *segchunk = nullptr;  // nseg + 1: first chunk of each segment
     int64_t nchunks = 0;
     int32_t maxlen = 0;
+    int mode = kModeChunked;
+    int R = 0, nb = 0, ngroups = 0;  // blocked: panel rows, panels, segment groups
+    int32_t *runptr = nullptr;       // blocked: (nb + 1) x nseg run starts
+    int grid = 0;                    // fused / blocked: CTAs per launch
+    size_t smem_bytes = 0;           // fused / blocked: dynamic shared memory
 };
 
 struct Scratch {
@@ -49,6 +61,7 @@ struct Scratch {
     int hist_cap = 0;
     void *als_part = nullptr;       // ALS per-chunk Gram partials
     size_t als_bytes = 0;
+    int *err = nullptr;             // device flag: a bounded wait expired
 };
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
@@ -84,6 +97,7 @@ struct glrm_s {
     glrm::Timer timer;
     long long launches = 0;  // kernels enqueued since creation
     int64_t sweeps_done = 0;
+    int path_x = GLRM_PATH_AUTO, path_y = GLRM_PATH_AUTO;
     std::string err;
 };
 
@@ -107,6 +121,7 @@ struct Engine {
                                T *out, bool decode);
     static cudaError_t reset_steps(glrm_s *h);
     static cudaError_t als_half(glrm_s *h, bool xstep, double gamma);
+    static cudaError_t tiled_half_step(glrm_s *h, bool xstep);
 };
 
 // Validation of one orientation, writes bit flags into *flag (device int).
@@ -117,5 +132,6 @@ cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const vo
                                 cudaStream_t st);
 cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
                                   cudaStream_t st);
+cudaError_t launch_build_runptr(const Orient &o, cudaStream_t st);
 
 }  // namespace glrm

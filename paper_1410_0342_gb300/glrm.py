@@ -20,6 +20,7 @@ GLRM_ERR_CUDA, GLRM_ERR_TIMEOUT, GLRM_ERR_STATE, GLRM_ERR_NOMEM = -5, -6, -7, -8
 GLRM_LOSS_QUAD, GLRM_LOSS_HUBER, GLRM_LOSS_HINGE, GLRM_LOSS_LOGISTIC, GLRM_LOSS_ORDINAL_HINGE = range(5)
 GLRM_REG_ZERO, GLRM_REG_QUAD, GLRM_REG_L1, GLRM_REG_NONNEG = range(4)
 GLRM_FP64, GLRM_FP32, GLRM_BF16 = 0, 1, 2
+GLRM_PATH_AUTO, GLRM_PATH_CHUNKED, GLRM_PATH_FUSED, GLRM_PATH_BLOCKED = 0, 1, 2, 3
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libglrm.so")
 
@@ -60,6 +61,8 @@ def _load():
         "glrm_timing_enable": [p, i32],
         "glrm_timing_read": [p, i32, p, p, p, p],
         "glrm_launch_count": [p, p],
+        "glrm_set_path": [p, i32, i32],
+        "glrm_get_path": [p, p],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -216,6 +219,16 @@ def glrm_get_state(h) -> bytes:
 def glrm_set_state(h, state: bytes):
     buf = ctypes.create_string_buffer(state, len(state))
     _check(_lib.glrm_set_state(h, buf, len(state)), h)
+
+
+def glrm_set_path(h, xstep_path, ystep_path):
+    _check(_lib.glrm_set_path(h, int(xstep_path), int(ystep_path)), h)
+
+
+def glrm_get_path(h):
+    out = np.zeros(2, np.int32)
+    _check(_lib.glrm_get_path(h, _ptr(out)), h)
+    return int(out[0]), int(out[1])
 
 
 def glrm_timing_enable(h, on=True):
