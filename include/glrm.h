@@ -223,7 +223,16 @@ int glrm_set_state(glrm_t h, const void *buf_host, size_t len);
  *   GLRM_PATH_BLOCKED  the other factor staged panel by panel (TMA); per
  *                      (panel, segment) partials summed over panels in a fixed
  *                      order
- * GLRM_PATH_AUTO picks fused when the other factor fits, else blocked when a
+ *   GLRM_PATH_MASKED   segments in tiles of 32, one per lane; a warp walks the
+ *                      union of its tile's other-indices in order, loading each
+ *                      other-factor row once as a broadcast from shared memory
+ *                      (whole factor, or panel by panel); values re-ordered at
+ *                      set-up and streamed by TMA
+ *   GLRM_PATH_MASKED_PANELS  the masked path with at least two panels even when
+ *                      the factor would fit whole (glrm_get_path reports it for
+ *                      any masked path that runs panel by panel)
+ * GLRM_PATH_AUTO picks masked when a tile's pairs average >= 8 observed lanes
+ * (dense tables), else fused when the other factor fits, else blocked when a
  * (panel, segment) run holds >= 64 entries on average, else chunked.  The
  * staged paths need k <= 32.  glrm_set_path(h, xstep_path, ystep_path) may be
  * called before or after glrm_set_observed; an infeasible request returns
@@ -233,7 +242,9 @@ typedef enum {
     GLRM_PATH_AUTO = 0,
     GLRM_PATH_CHUNKED = 1,
     GLRM_PATH_FUSED = 2,
-    GLRM_PATH_BLOCKED = 3
+    GLRM_PATH_BLOCKED = 3,
+    GLRM_PATH_MASKED = 4,
+    GLRM_PATH_MASKED_PANELS = 5
 } glrm_path;
 int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path);
 int glrm_get_path(glrm_t h, int32_t *paths_host);

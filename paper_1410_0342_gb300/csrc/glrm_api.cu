@@ -52,6 +52,13 @@ void free_orient(Orient &o)
     dfree(o.chunks);
     dfree(o.segchunk);
     dfree(o.runptr);
+    dfree(o.tptr);
+    dfree(o.tidx);
+    dfree(o.tmask);
+    dfree(o.tval);
+    dfree(o.tpan);
+    dfree(o.tvpan);
+    o.npairs = 0;
     o.nchunks = 0;
     o.maxlen = 0;
     o.mode = kModeChunked;
@@ -92,6 +99,9 @@ cudaError_t run_half(glrm_s *h, bool xstep) { return Engine<T>::half_step(h, xst
 cudaError_t half_step(glrm_s *h, bool xstep)
 {
     const Orient &o = xstep ? h->csr : h->csc;
+    if (o.mode == kModeMasked)
+        return h->prec == GLRM_FP64 ? Engine<double>::masked_half_step(h, xstep)
+                                    : Engine<float>::masked_half_step(h, xstep);
     if (o.mode != kModeChunked)
         return h->prec == GLRM_FP64 ? Engine<double>::tiled_half_step(h, xstep)
                                     : Engine<float>::tiled_half_step(h, xstep);
@@ -110,12 +120,89 @@ int tiled_width(int k)
 // other factor (plus, for the X-step, its loss table) fits in one CTA's shared
 // memory; blocked when panels of it do and a (panel, segment) run holds 64
 // entries or more on average; chunked otherwise.
+// Masked tiles: count each tile's pairs, and build the layout when forced or
+// when a pair averages >= 8 observed lanes.
+int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, size_t budget)
+{
+    const size_t es = elem_size(h->prec);
+    const int64_t nother = xstep ? h->n : h->m;
+    const int64_t ntiles = (o.nseg + 31) / 32;
+    CK(cudaMalloc(&o.tptr, (size_t)(ntiles + 1) * sizeof(int32_t)));
+    CK(launch_mt_count(o, o.tptr, h->stream));
+    std::vector<int32_t> cnt((size_t)ntiles);
+    CK(cudaMemcpyAsync(cnt.data(), o.tptr, (size_t)ntiles * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<int32_t> off((size_t)ntiles + 1);
+    int64_t tot = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        off[t] = (int32_t)tot;
+        tot += cnt[t];
+    }
+    off[ntiles] = (int32_t)tot;
+    const double lanes = tot ? (double)h->nnz / (double)tot : 0.0;
+    if (force == GLRM_PATH_AUTO && lanes < 8.0) {
+        dfree(o.tptr);
+        return GLRM_OK;
+    }
+    const size_t ring = (size_t)kStreamWarps * kRingSlotsHost * kRingBytes;
+    if (ring + 64 * ((size_t)K * es + 16) > budget) {
+        dfree(o.tptr);
+        return force == GLRM_PATH_AUTO ? GLRM_OK : fail(h, GLRM_ERR_ARG, "masked path: shared memory too small");
+    }
+    const size_t panel_all = ((((size_t)nother * K * es) + 15) & ~(size_t)15) +
+                             (xstep ? (size_t)nother * sizeof(LossSpec) : 0);
+    const int64_t ngroups = (ntiles + kStreamWarps - 1) / kStreamWarps;
+    int64_t R, nb;
+    if (panel_all + ring <= budget && force != GLRM_PATH_MASKED_PANELS) {
+        R = nother;
+        nb = 1;
+    } else {
+        const int64_t per_row = (int64_t)K * es + (xstep ? (int64_t)sizeof(LossSpec) : 0);
+        const int64_t Rmax = (((int64_t)budget - (int64_t)ring) / per_row) & ~(int64_t)31;
+        const int64_t nb_target = std::max<int64_t>(2, (4LL * sms + ngroups - 1) / ngroups);
+        R = ((nother + nb_target - 1) / nb_target + 31) & ~(int64_t)31;
+        R = std::max<int64_t>(32, std::min<int64_t>(R, Rmax));
+        nb = (nother + R - 1) / R;
+    }
+    o.R = (int)R;
+    o.nb = (int)nb;
+    o.ngroups = (int)ngroups;
+    o.npairs = tot;
+    CK(cudaMemcpyAsync(o.tptr, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMalloc(&o.tidx, (size_t)std::max<int64_t>(tot, 1) * sizeof(int32_t)));
+    CK(cudaMalloc(&o.tmask, (size_t)std::max<int64_t>(tot, 1) * sizeof(uint32_t)));
+    CK(cudaMalloc(&o.tval, ((size_t)h->nnz + kPad) * es));
+    CK(cudaMemsetAsync(o.tval, 0, ((size_t)h->nnz + kPad) * es, h->stream));
+    CK(cudaMalloc(&o.tpan, (size_t)ntiles * (nb + 1) * sizeof(int32_t)));
+    CK(cudaMalloc(&o.tvpan, (size_t)ntiles * (nb + 1) * sizeof(int32_t)));
+    CK(launch_mt_build(o, h->prec, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    o.mode = kModeMasked;
+    if (nb == 1) {
+        o.smem_bytes = panel_all + ring;
+        o.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)sms));
+    } else {
+        o.smem_bytes = ((((size_t)R * K * es) + 15) & ~(size_t)15) +
+                       (xstep ? (size_t)R * sizeof(LossSpec) : 0) + ring;
+        o.grid = sms;
+    }
+    return GLRM_OK;
+}
+
 int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
 {
     int dev = h->device, optin = 0, sms = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     dfree(o.runptr);
+    dfree(o.tptr);
+    dfree(o.tidx);
+    dfree(o.tmask);
+    dfree(o.tval);
+    dfree(o.tpan);
+    dfree(o.tvpan);
     const int K = tiled_width(h->k);
     o.mode = kModeChunked;
     if (force == GLRM_PATH_CHUNKED) return GLRM_OK;
@@ -127,24 +214,39 @@ int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
     const int64_t nother = xstep ? h->n : h->m;
     const size_t per_row = (size_t)K * es + (xstep ? sizeof(LossSpec) : 0);
     const size_t budget = (size_t)optin - 1024;
-    const size_t fused = (((size_t)nother * K * es + 15) & ~(size_t)15) +
-                         (xstep ? (size_t)nother * sizeof(LossSpec) : 0);
-    const bool fused_ok = fused <= budget;
+    if (force == GLRM_PATH_AUTO || force == GLRM_PATH_MASKED || force == GLRM_PATH_MASKED_PANELS) {
+        int rc = plan_masked(h, o, xstep, force, K, sms, budget);
+        if (rc != GLRM_OK || o.mode == kModeMasked || force != GLRM_PATH_AUTO) return rc;
+    }
+    // per warp: two staging buffers of `cap` (index, value) pairs
+    const size_t per_cap = (size_t)kStreamWarps * 2 * (sizeof(int32_t) + es);
+    const size_t panel_all = ((((size_t)nother * K * es) + 15) & ~(size_t)15) +
+                             (xstep ? (size_t)nother * sizeof(LossSpec) : 0);
+    const int cap_fused =
+        panel_all < budget ? (int)std::min<size_t>(1024, ((budget - panel_all) / per_cap) & ~(size_t)3) : 0;
+    const bool fused_ok = cap_fused >= 64;
     if (force == GLRM_PATH_FUSED && !fused_ok)
         return fail(h, GLRM_ERR_ARG, "fused path: the other factor does not fit in shared memory");
     if (force == GLRM_PATH_FUSED || (force == GLRM_PATH_AUTO && fused_ok && o.maxlen <= 8192)) {
         o.mode = kModeFused;
-        o.smem_bytes = fused;
-        const int64_t want = (o.nseg + 15) / 16;
+        o.cap = cap_fused;
+        o.smem_bytes = panel_all + per_cap * cap_fused;
+        const int64_t want = (o.nseg + kStreamWarps - 1) / kStreamWarps;
         o.grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms));
         return GLRM_OK;
     }
-    int R = (int)std::min<size_t>((budget / per_row) & ~(size_t)31, (size_t)1 << 20);
-    if (force == GLRM_PATH_BLOCKED && R > 32) {
+    // blocked: 1024-entry buffers, panels from what is left, runs kept under
+    // about 80% of a buffer on average
+    const int cap = 1024;
+    const double density = (double)h->nnz / ((double)o.nseg * (double)nother);
+    const size_t left = budget > per_cap * cap ? budget - per_cap * cap : 0;
+    int64_t R = (int64_t)std::min<double>((double)(left / per_row), 0.8 * cap / std::max(density, 1e-12));
+    R &= ~(int64_t)31;
+    if (force == GLRM_PATH_BLOCKED && R >= 32) {
         // forced: at least two panels when the factor allows, so the partial
         // reduction over panels is exercised
         const int64_t half = ((nother + 1) / 2 + 31) & ~(int64_t)31;
-        R = (int)std::max<int64_t>(32, std::min<int64_t>(R, half));
+        R = std::max<int64_t>(32, std::min<int64_t>(R, half));
     }
     if (R < 32) {
         if (force == GLRM_PATH_AUTO) return GLRM_OK;
@@ -154,11 +256,13 @@ int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
     const double avg_run = (double)h->nnz / ((double)nb * (double)o.nseg);
     if (force == GLRM_PATH_AUTO && avg_run < 64.0) return GLRM_OK;
     o.mode = kModeBlocked;
-    o.R = R;
+    o.R = (int)R;
     o.nb = nb;
+    o.cap = cap;
     o.grid = sms;
     o.ngroups = (int)std::max<int64_t>(1, std::min<int64_t>(o.nseg, (4LL * sms + nb - 1) / nb));
-    o.smem_bytes = (((size_t)R * K * es + 15) & ~(size_t)15) + (xstep ? (size_t)R * sizeof(LossSpec) : 0);
+    o.smem_bytes = (((size_t)R * K * es + 15) & ~(size_t)15) + (xstep ? (size_t)R * sizeof(LossSpec) : 0) +
+                   per_cap * cap;
     CK(cudaMalloc(&o.runptr, (size_t)(nb + 1) * o.nseg * sizeof(int32_t)));
     CK(launch_build_runptr(o, h->stream));
     return GLRM_OK;
@@ -192,7 +296,7 @@ void build_chunks(const std::vector<int32_t> &ptr, std::vector<int4> &chunks,
 // panels x segments when blocked).
 int64_t partial_slots(const Orient &o)
 {
-    return o.mode == kModeBlocked ? (int64_t)o.nb * o.nseg : o.nchunks;
+    return (o.mode == kModeBlocked || o.mode == kModeMasked) ? (int64_t)o.nb * o.nseg : o.nchunks;
 }
 
 int alloc_scratch(glrm_s *h)
@@ -262,13 +366,19 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     R.nseg = h->m;
     C.nseg = h->n;
     h->nnz = nnz;
-    const size_t nz = (size_t)std::max<int64_t>(nnz, 1);
+    // kPad extra zeroed entries let the staged kernels copy 16-byte aligned
+    // supersets of any entry range.
+    const size_t nz = (size_t)nnz + kPad;
     CK(cudaMalloc(&R.ptr, (size_t)(h->m + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&C.ptr, (size_t)(h->n + 1) * sizeof(int32_t)));
     CK(cudaMalloc(&R.idx, nz * sizeof(int32_t)));
     CK(cudaMalloc(&C.idx, nz * sizeof(int32_t)));
     CK(cudaMalloc(&R.val, nz * es));
     CK(cudaMalloc(&C.val, nz * es));
+    CK(cudaMemsetAsync(R.idx, 0, nz * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(C.idx, 0, nz * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(R.val, 0, nz * es, st));
+    CK(cudaMemsetAsync(C.val, 0, nz * es, st));
     CK(cudaMemcpyAsync(R.ptr, rp, (size_t)(h->m + 1) * sizeof(int32_t), kind, st));
     CK(cudaMemcpyAsync(C.ptr, cp, (size_t)(h->n + 1) * sizeof(int32_t), kind, st));
     if (nnz > 0) {
@@ -701,7 +811,7 @@ int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     for (int p : {xstep_path, ystep_path})
-        if (p < GLRM_PATH_AUTO || p > GLRM_PATH_BLOCKED) return fail(h, GLRM_ERR_ARG, "bad path");
+        if (p < GLRM_PATH_AUTO || p > GLRM_PATH_MASKED_PANELS) return fail(h, GLRM_ERR_ARG, "bad path");
     h->path_x = xstep_path;
     h->path_y = ystep_path;
     if (!h->have_omega) return GLRM_OK;
@@ -730,12 +840,13 @@ int glrm_get_path(glrm_t h, int32_t *paths_host)
 {
     if (!h || !paths_host) return fail(h, GLRM_ERR_ARG, "null argument");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
-    auto code = [](int mode) {
-        return mode == kModeFused ? GLRM_PATH_FUSED
-                                  : (mode == kModeBlocked ? GLRM_PATH_BLOCKED : GLRM_PATH_CHUNKED);
+    auto code = [](const Orient &o) {
+        if (o.mode == kModeMasked) return o.nb == 1 ? GLRM_PATH_MASKED : GLRM_PATH_MASKED_PANELS;
+        return o.mode == kModeFused ? GLRM_PATH_FUSED
+                                    : (o.mode == kModeBlocked ? GLRM_PATH_BLOCKED : GLRM_PATH_CHUNKED);
     };
-    paths_host[0] = code(h->csr.mode);
-    paths_host[1] = code(h->csc.mode);
+    paths_host[0] = code(h->csr);
+    paths_host[1] = code(h->csc);
     return GLRM_OK;
 }
 

@@ -3,5 +3,6 @@
 // parallel).
 #include "glrm_als.cuh"
 #include "glrm_tiled.cuh"
+#include "glrm_masked.cuh"
 
 template struct glrm::Engine<double>;

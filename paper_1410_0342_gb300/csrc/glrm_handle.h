@@ -18,13 +18,19 @@ namespace glrm {
 // of at most kChunk entries; one warp processes one chunk.
 constexpr int kChunk = 1024;
 constexpr int kMaxK = 64;
+constexpr int kPad = 8;  // zeroed entries after the last one in library copies of Omega
+constexpr int kStreamWarps = 8;  // warps per CTA of the staged (fused / blocked / masked) kernels
+constexpr int kRingSlotsHost = 4;  // value-stream ring slots per warp (masked kernels)
+constexpr int kRingBytes = 2048;   // bytes per ring slot
 
 // How a half-step runs over one orientation (chosen at set-up):
 // chunked: entries cut into chunks, the other factor gathered from global
 //          memory (L1/L2); any size.
 // fused:   the whole other factor staged in shared memory per CTA; one kernel.
 // blocked: the other factor staged panel by panel; partials per (panel, segment).
-constexpr int kModeChunked = 0, kModeFused = 1, kModeBlocked = 2;
+// masked:  segments in tiles of 32 (lane = segment), the tile's union of
+//          other-indices walked in order with one broadcast load per index.
+constexpr int kModeChunked = 0, kModeFused = 1, kModeBlocked = 2, kModeMasked = 3;
 
 // One orientation of Omega: CSR (segments = rows, used by the X-step) or CSC
 // (segments = columns, used by the Y-step).
@@ -41,7 +47,16 @@ struct Orient {
     int R = 0, nb = 0, ngroups = 0;  // blocked: panel rows, panels, segment groups
     int32_t *runptr = nullptr;       // blocked: (nb + 1) x nseg run starts
     int grid = 0;                    // fused / blocked: CTAs per launch
-    size_t smem_bytes = 0;           // fused / blocked: dynamic shared memory
+    int cap = 0;                     // fused / blocked: entries per staging buffer
+    size_t smem_bytes = 0;           // fused / blocked / masked: dynamic shared memory
+    // masked tiles (nb panels of R other-indices; nb == 1: fused kernel)
+    int64_t npairs = 0;
+    int32_t *tptr = nullptr;   // ntiles + 1: first pair of each tile
+    int32_t *tidx = nullptr;   // npairs: other-index of each pair
+    uint32_t *tmask = nullptr; // npairs: lanes holding it
+    void *tval = nullptr;      // nnz + kPad values in (tile, index, lane) order
+    int32_t *tpan = nullptr;   // ntiles x (nb + 1): first pair of each panel
+    int32_t *tvpan = nullptr;  // ntiles x (nb + 1): first value of each panel
 };
 
 struct Scratch {
@@ -122,6 +137,7 @@ struct Engine {
     static cudaError_t reset_steps(glrm_s *h);
     static cudaError_t als_half(glrm_s *h, bool xstep, double gamma);
     static cudaError_t tiled_half_step(glrm_s *h, bool xstep);
+    static cudaError_t masked_half_step(glrm_s *h, bool xstep);
 };
 
 // Validation of one orientation, writes bit flags into *flag (device int).
@@ -133,5 +149,7 @@ cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const vo
 cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
                                   cudaStream_t st);
 cudaError_t launch_build_runptr(const Orient &o, cudaStream_t st);
+cudaError_t launch_mt_count(const Orient &o, int32_t *cnt, cudaStream_t st);
+cudaError_t launch_mt_build(const Orient &o, int prec, cudaStream_t st);
 
 }  // namespace glrm

@@ -25,7 +25,6 @@
 
 namespace glrm {
 
-constexpr int kTileWarps = 16;
 constexpr long kWaitLimit = 1L << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -263,52 +262,195 @@ __device__ __forceinline__ double reg_of(const Vec<T, K> &v, int k, int rk, T rw
     return r;
 }
 
+// ------------------------------------------------- per-warp entry streams
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One warp's two staging buffers for the (index, value) lists of its
+// segments: while it works on one segment from buffer `cur`, a TMA bulk copy
+// fills buffer cur^1 with the next segment's entries.  A range is copied as
+// its 16-byte aligned superset [lo, hi) (the library pads its copies of Omega
+// with kPad zero entries), so entry q sits at position q - lo.  Ranges longer
+// than `cap` are not staged and are read from global memory instead.
+template <class T>
+struct EntryStream {
+    // two buffers, kept in scalar members so that runtime selection stays in
+    // registers
+    int32_t *ib0, *ib1;
+    T *vb0, *vb1;
+    uint64_t *bar0, *bar1;
+    unsigned ph0, ph1;
+    int lo0, lo1;
+    bool st0, st1;
+    int cap;
+
+    __device__ __forceinline__ void init(unsigned char *base, uint64_t *bars, int cap_)
+    {
+        cap = cap_;
+        const size_t one = (size_t)cap * (sizeof(int32_t) + sizeof(T));
+        ib0 = reinterpret_cast<int32_t *>(base);
+        vb0 = reinterpret_cast<T *>(base + (size_t)cap * sizeof(int32_t));
+        ib1 = reinterpret_cast<int32_t *>(base + one);
+        vb1 = reinterpret_cast<T *>(base + one + (size_t)cap * sizeof(int32_t));
+        bar0 = bars;
+        bar1 = bars + 1;
+        ph0 = ph1 = 0;
+        lo0 = lo1 = 0;
+        st0 = st1 = false;
+    }
+    __device__ __forceinline__ bool staged(int q) const { return q ? st1 : st0; }
+    __device__ __forceinline__ const int32_t *ibase(int q) const { return q ? ib1 - lo1 : ib0 - lo0; }
+    __device__ __forceinline__ const T *vbase(int q) const { return q ? vb1 - lo1 : vb0 - lo0; }
+
+    // Whole warp calls; lane 0 issues.  Every issue completes one phase of
+    // the buffer's barrier (with the copy, or at once when not staged).
+    __device__ __forceinline__ void issue(int q, int b, int e, const int32_t *__restrict__ idx,
+                                          const T *__restrict__ val)
+    {
+        const int l = b & ~3, hi = (e + 3) & ~3, n = hi - l;
+        const bool stg = n > 0 && n <= cap;
+        if (q) { lo1 = l; st1 = stg; } else { lo0 = l; st0 = stg; }
+        int32_t *ib = q ? ib1 : ib0;
+        T *vb = q ? vb1 : vb0;
+        uint64_t *bar = q ? bar1 : bar0;
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+            fence_proxy_async();
+            if (stg) {
+                mbar_expect_tx(bar, (unsigned)(n * (sizeof(int32_t) + sizeof(T))));
+                bulk_g2s(ib, idx + l, (unsigned)(n * sizeof(int32_t)), bar);
+                bulk_g2s(vb, val + l, (unsigned)(n * sizeof(T)), bar);
+            } else {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+            }
+        }
+    }
+
+    // Wait for buffer q (bounded); false if the copy did not land in time.
+    __device__ __forceinline__ bool wait(int q)
+    {
+        uint64_t *bar = q ? bar1 : bar0;
+        const unsigned ph = q ? ph1 : ph0;
+        bool ok = mbar_wait_bounded(bar, ph);
+        if (!ok) ok = mbar_wait_bounded(bar, ph);
+        if (q) ph1 ^= 1u; else ph0 ^= 1u;
+        return ok;
+    }
+};
+
+// Pass over one segment's entries [b, e): u = f . w_j for the other-factor row
+// j (panel-local, from shared memory), loss and derivative; with GRAD the
+// gradient sum L' w_j accumulates in g.  Entries come from the staging buffer
+// (SM) or from global memory.
+template <class T, int K, bool XSTEP, bool GRAD, bool SM>
+__device__ __forceinline__ T seg_pass(const Vec<T, K> &f, Vec<T, K> &g, int b, int e, int jbase,
+                                      const int32_t *__restrict__ ip, const T *__restrict__ vp,
+                                      const T *__restrict__ Ws, const LossSpec *__restrict__ Ls,
+                                      const LossSpec &segspec)
+{
+    const int lane = threadIdx.x & 31;
+    T lsum = T(0);
+    LossSpec sp = segspec;
+    for (int q = b + lane; q < e; q += 32) {
+        int j;
+        T a;
+        if constexpr (SM) {
+            j = ip[q];
+            a = vp[q];
+        } else {
+            j = __ldg(ip + q);
+            a = __ldg(vp + q);
+        }
+        j -= jbase;
+        Vec<T, K> w;
+        w.load(Ws + (int64_t)j * K);
+        const T u = f.dot(w);
+        if constexpr (XSTEP) sp = Ls[j];
+        T L;
+        const T d = loss_deriv<T>(sp, u, a, L);
+        if constexpr (GRAD) g.axpy(d, w);
+        lsum += L;
+    }
+    return lsum;
+}
+
+template <class T, int K, bool XSTEP, bool GRAD>
+__device__ __forceinline__ T seg_pass_any(const EntryStream<T> &st, int q, const Vec<T, K> &f,
+                                          Vec<T, K> &g, int b, int e, int jbase,
+                                          const int32_t *__restrict__ idx, const T *__restrict__ val,
+                                          const T *Ws, const LossSpec *Ls, const LossSpec &segspec)
+{
+    if (st.staged(q))
+        return seg_pass<T, K, XSTEP, GRAD, true>(f, g, b, e, jbase, st.ibase(q), st.vbase(q), Ws,
+                                                 Ls, segspec);
+    return seg_pass<T, K, XSTEP, GRAD, false>(f, g, b, e, jbase, idx, val, Ws, Ls, segspec);
+}
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Bytes of one warp's pair of staging buffers.
+template <class T>
+__host__ __device__ __forceinline__ size_t stream_bytes(int cap)
+{
+    return 2 * (size_t)cap * (sizeof(int32_t) + sizeof(T));
+}
+
 // ----------------------------------------------------------- fused kernel
 
-// Dynamic shared memory: the other factor (nother x K) then, for the X-step,
-// the loss table of the other index (nother x LossSpec).
+// Dynamic shared memory: the other factor (nother x K), for the X-step its
+// loss table (nother LossSpecs), then kStreamWarps pairs of staging buffers.
 template <class T, int K, bool XSTEP>
-__global__ void __launch_bounds__(kTileWarps * 32)
+__global__ void __launch_bounds__(kStreamWarps * 32, 1)
 fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                   const T *__restrict__ val, T *__restrict__ F, const T *__restrict__ W,
                   int64_t nother, int k, T *__restrict__ alpha, const LossSpec *__restrict__ loss,
                   int rk, T rw, double *__restrict__ kept_obj, double *__restrict__ kept_reg,
-                  int32_t *__restrict__ accepted, int *__restrict__ err)
+                  int32_t *__restrict__ accepted, int *__restrict__ err, int cap)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bar_panel;
+    __shared__ uint64_t bar_seg[kStreamWarps][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T *Ws = reinterpret_cast<T *>(dsm);
-    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + (((size_t)nother * K * sizeof(T) + 15) & ~(size_t)15));
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    size_t off = align16((size_t)nother * K * sizeof(T));
+    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
+    if constexpr (XSTEP) off += (size_t)nother * sizeof(LossSpec);
+    EntryStream<T> st;
+    st.init(dsm + off + (size_t)wid * stream_bytes<T>(cap), &bar_seg[wid][0], cap);
+    if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
+    if (lane == 0) {
+        mbar_init(&bar_seg[wid][0], 1);
+        mbar_init(&bar_seg[wid][1], 1);
+    }
     __syncthreads();
     if constexpr (XSTEP) {
         for (int64_t q = threadIdx.x; q < nother; q += blockDim.x) Ls[q] = loss[q];
     }
-    if (!stage_panel<T>(Ws, W, 0, (int)nother, k, K, &bar, 0, err)) return;
+    if (!stage_panel<T>(Ws, W, 0, (int)nother, k, K, &bar_panel, 0, err)) return;
 
-    const int lane = threadIdx.x & 31;
-    const int64_t wstride = (int64_t)gridDim.x * kTileWarps;
-    for (int64_t s = (int64_t)blockIdx.x * kTileWarps + (threadIdx.x >> 5); s < nseg; s += wstride) {
+    const int64_t wstride = (int64_t)gridDim.x * kStreamWarps;
+    int64_t s = (int64_t)blockIdx.x * kStreamWarps + wid;
+    int cur = 0;
+    if (s < nseg) st.issue(0, ptr[s], ptr[s + 1], idx, val);
+    for (; s < nseg; s += wstride) {
+        const int64_t nx = s + wstride;
+        if (nx < nseg) st.issue(cur ^ 1, ptr[nx], ptr[nx + 1], idx, val);
+        if (!st.wait(cur)) {
+            if (lane == 0) atomicOr(err, 1);
+            if (nx < nseg) st.wait(cur ^ 1);
+            return;
+        }
         const int b = ptr[s], e = ptr[s + 1];
         Vec<T, K> f, g;
         f.load_masked(F + s * k, k);
         g.zero();
         LossSpec sp;
         if constexpr (!XSTEP) sp = loss[s];
-        T lsum = T(0);
         // pass 1: gradient and loss at the current factor
-        for (int q = b + lane; q < e; q += 32) {
-            const int j = __ldg(idx + q);
-            const T a = __ldg(val + q);
-            Vec<T, K> w;
-            w.load(Ws + (int64_t)j * K);
-            const T u = f.dot(w);
-            if constexpr (XSTEP) sp = Ls[j];
-            T L;
-            const T d = loss_deriv<T>(sp, u, a, L);
-            g.axpy(d, w);
-            lsum += L;
-        }
+        const T lsum = seg_pass_any<T, K, XSTEP, true>(st, cur, f, g, b, e, 0, idx, val, Ws, Ls, sp);
         g.warp_allsum();
         const double lold = warp_sum((double)lsum);
         const T al = alpha[s];
@@ -329,18 +471,8 @@ fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *
             fp.load_masked(tmp, K);
         }
         // pass 2: loss at the candidate
-        T lsum2 = T(0);
-        for (int q = b + lane; q < e; q += 32) {
-            const int j = __ldg(idx + q);
-            const T a = __ldg(val + q);
-            Vec<T, K> w;
-            w.load(Ws + (int64_t)j * K);
-            const T u = fp.dot(w);
-            if constexpr (XSTEP) sp = Ls[j];
-            T L;
-            loss_deriv<T>(sp, u, a, L);
-            lsum2 += L;
-        }
+        Vec<T, K> unused;
+        const T lsum2 = seg_pass_any<T, K, XSTEP, false>(st, cur, fp, unused, b, e, 0, idx, val, Ws, Ls, sp);
         const double fnew = warp_sum((double)lsum2) + rnew;
         const double fold = lold + rold;
         const bool acc = fnew <= fold;
@@ -355,6 +487,7 @@ fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *
             kept_reg[s] = acc ? rnew : rold;
             accepted[s] = acc ? 1 : 0;
         }
+        cur ^= 1;
     }
 }
 
@@ -381,24 +514,34 @@ static __global__ void build_runptr_kernel(int64_t nseg, int nb, int R, const in
 
 // One work unit = (panel b, segments [s0, s1)).  GRAD: partial gradient and
 // loss at F; else loss only at F (the candidate).  Partials at (b*nseg + s).
+// Each warp streams its runs through its staging buffers.
 template <class T, int K, bool XSTEP, bool GRAD>
-__global__ void __launch_bounds__(kTileWarps * 32)
+__global__ void __launch_bounds__(kStreamWarps * 32, 1)
 blocked_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
                     const int32_t *__restrict__ runptr, const int32_t *__restrict__ idx,
                     const T *__restrict__ val, const T *__restrict__ F, const T *__restrict__ W,
                     int k, const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
-                    double *__restrict__ part_loss, int *__restrict__ err)
+                    double *__restrict__ part_loss, int *__restrict__ err, int cap)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ uint64_t bar;
-    T *Ws = reinterpret_cast<T *>(dsm);
-    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + (((size_t)R * K * sizeof(T) + 15) & ~(size_t)15));
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
+    __shared__ uint64_t bar_panel;
+    __shared__ uint64_t bar_seg[kStreamWarps][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T *Ws = reinterpret_cast<T *>(dsm);
+    size_t off = align16((size_t)R * K * sizeof(T));
+    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
+    if constexpr (XSTEP) off += (size_t)R * sizeof(LossSpec);
+    EntryStream<T> st;
+    st.init(dsm + off + (size_t)wid * stream_bytes<T>(cap), &bar_seg[wid][0], cap);
+    if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
+    if (lane == 0) {
+        mbar_init(&bar_seg[wid][0], 1);
+        mbar_init(&bar_seg[wid][1], 1);
+    }
+    __syncthreads();
     const int64_t seg_per = (nseg + ngroups - 1) / ngroups;
     const int64_t nunits = (int64_t)nb * ngroups;
-    unsigned phase = 0;
+    unsigned pphase = 0;
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
         const int b = (int)(u / ngroups);
         const int64_t grp = u % ngroups;
@@ -408,11 +551,28 @@ blocked_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
         if constexpr (XSTEP) {
             for (int q = threadIdx.x; q < rows; q += blockDim.x) Ls[q] = loss[r0 + q];
         }
-        if (!stage_panel<T>(Ws, W, r0, rows, k, K, &bar, phase, err)) return;
-        phase ^= 1u;
+        if (!stage_panel<T>(Ws, W, r0, rows, k, K, &bar_panel, pphase, err)) return;
+        pphase ^= 1u;
         const int64_t s0 = grp * seg_per;
         const int64_t s1 = s0 + seg_per < nseg ? s0 + seg_per : nseg;
-        for (int64_t s = s0 + wid; s < s1; s += kTileWarps) {
+        int64_t s = s0 + wid;
+        int cur = 0;
+        bool bad = false;
+        if (s < s1) {
+            const int64_t slot = (int64_t)b * nseg + s;
+            st.issue(0, runptr[slot], runptr[slot + nseg], idx, val);
+        }
+        for (; s < s1; s += kStreamWarps) {
+            const int64_t nx = s + kStreamWarps;
+            if (nx < s1) {
+                const int64_t ns = (int64_t)b * nseg + nx;
+                st.issue(cur ^ 1, runptr[ns], runptr[ns + nseg], idx, val);
+            }
+            if (!st.wait(cur)) {
+                if (nx < s1) st.wait(cur ^ 1);
+                bad = true;
+                break;
+            }
             const int64_t slot = (int64_t)b * nseg + s;
             const int qb = runptr[slot], qe = runptr[slot + nseg];
             Vec<T, K> f, g;
@@ -420,19 +580,8 @@ blocked_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
             g.zero();
             LossSpec sp;
             if constexpr (!XSTEP) sp = loss[s];
-            T lsum = T(0);
-            for (int q = qb + lane; q < qe; q += 32) {
-                const int jl = __ldg(idx + q) - (int)r0;
-                const T a = __ldg(val + q);
-                Vec<T, K> w;
-                w.load(Ws + (int64_t)jl * K);
-                const T uu = f.dot(w);
-                if constexpr (XSTEP) sp = Ls[jl];
-                T L;
-                const T d = loss_deriv<T>(sp, uu, a, L);
-                if constexpr (GRAD) g.axpy(d, w);
-                lsum += L;
-            }
+            const T lsum = seg_pass_any<T, K, XSTEP, GRAD>(st, cur, f, g, qb, qe, (int)r0, idx, val,
+                                                          Ws, Ls, sp);
             const double ls = warp_sum((double)lsum);
             if constexpr (GRAD) {
                 g.warp_allsum();
@@ -441,6 +590,11 @@ blocked_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
                     if (lane == (c & 31)) part_grad[slot * K + c] = g.get(c);
             }
             if (lane == 0) part_loss[slot] = ls;
+            cur ^= 1;
+        }
+        if (__syncthreads_or(bad)) {
+            if (threadIdx.x == 0) atomicOr(err, 1);
+            return;
         }
     }
 }
@@ -524,9 +678,9 @@ cudaError_t launch_fused(glrm_s *h, const Orient &o, T *F, const T *W, int64_t n
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)o.smem_bytes);
     if (e != cudaSuccess) return e;
-    kern<<<o.grid, kTileWarps * 32, o.smem_bytes, h->stream>>>(
+    kern<<<o.grid, kStreamWarps * 32, o.smem_bytes, h->stream>>>(
         o.nseg, o.ptr, o.idx, (const T *)o.val, F, W, nother, h->k, alpha, h->loss_dev, rk, rw,
-        kept_obj, kept_reg, acc, h->s.err);
+        kept_obj, kept_reg, acc, h->s.err, o.cap);
     return cudaGetLastError();
 }
 
@@ -538,9 +692,9 @@ cudaError_t launch_blocked_pass(glrm_s *h, const Orient &o, const T *F, const T 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)o.smem_bytes);
     if (e != cudaSuccess) return e;
-    kern<<<o.grid, kTileWarps * 32, o.smem_bytes, h->stream>>>(
+    kern<<<o.grid, kStreamWarps * 32, o.smem_bytes, h->stream>>>(
         o.nseg, o.nb, o.R, o.ngroups, nother, o.runptr, o.idx, (const T *)o.val, F, W, h->k,
-        h->loss_dev, part_grad, part_loss, h->s.err);
+        h->loss_dev, part_grad, part_loss, h->s.err, o.cap);
     return cudaGetLastError();
 }
 

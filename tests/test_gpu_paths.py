@@ -1,6 +1,6 @@
-"""The three kernel paths of a half-step (chunked, fused, blocked) against
-the FP64 oracle on the same tables, and the automatic choice on shapes that
-select each of them."""
+"""The kernel paths of a half-step (chunked, fused, blocked, masked tiles
+with the whole other factor or panel by panel) against the FP64 oracle on the
+same tables, and the automatic choice on shapes that select each of them."""
 import numpy as np
 import pytest
 import torch
@@ -28,7 +28,7 @@ def oracle_hist(o, t, nsweeps):
     return p.proxgrad(t.X0, t.Yt0, nsweeps)
 
 
-PATHS = [(1, 1), (2, 2), (3, 3), (2, 3), (3, 1), (1, 2)]
+PATHS = [(1, 1), (2, 2), (3, 3), (2, 3), (3, 1), (1, 2), (4, 4), (5, 5), (4, 1), (1, 5), (5, 4)]
 
 
 @pytest.mark.parametrize("paths", PATHS)
@@ -44,7 +44,7 @@ def test_paths_match_oracle_fp32(G, oracle_mod, paths, k):
     assert rel.max() < 1e-4, rel
 
 
-@pytest.mark.parametrize("paths", [(1, 1), (2, 2), (3, 3)])
+@pytest.mark.parametrize("paths", [(1, 1), (2, 2), (3, 3), (4, 4), (5, 5)])
 def test_paths_match_oracle_fp64(G, oracle_mod, paths):
     t = W.qpca_dense(m=300, n=140, k=6, seed=5)
     g = G.GLRM.from_table(t, precision=G.GLRM_FP64)
@@ -64,17 +64,17 @@ def test_path_switch_keeps_state(G):
     g2 = G.GLRM.from_table(t)
     G.glrm_set_path(g2.h, 1, 1)
     h2a = g2.sweep(4)
-    G.glrm_set_path(g2.h, 2, 3)
+    G.glrm_set_path(g2.h, 4, 5)
     h2b = g2.sweep(4)
     h2 = np.concatenate([h2a, h2b])
     assert (np.abs(h1 - h2) / np.abs(h1)).max() < 1e-5
 
 
 def test_auto_path_choice(G):
-    # Y^T small: fused X-step; X large and dense: blocked Y-step
+    # dense: masked tiles; Y^T fits whole, X only panel by panel
     t = W.small_mixed(m=6000, n=64, k=16, p_obs=0.7, seed=3)
     g = G.GLRM.from_table(t)
-    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_FUSED, G.GLRM_PATH_BLOCKED)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_MASKED, G.GLRM_PATH_MASKED_PANELS)
     # sparse with a large X: chunked Y-step
     t2 = W.small_mixed(m=60000, n=3000, k=8, p_obs=0.002, seed=4)
     g2 = G.GLRM.from_table(t2)
