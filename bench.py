@@ -39,7 +39,7 @@ from paper_1410_0342_gb300 import workloads as W  # noqa: E402
 
 METRIC = "observed entries/s per alternating prox-grad sweep"
 UNIT = "entries/s"
-WORKLOAD = "mixed-type table m=100000 n=1000 k=20 (500 Huber, 300 hinge, 200 ordinal d=7), " \
+WORKLOAD = "mixed-type table m={m} n=1000 k=20 (500 Huber, 300 hinge, 200 ordinal d=7), " \
            "40% missing, l1(0.01) on X, nonneg on Y, FP32"
 ORACLE_SAMPLE_ROWS = 10_000
 
@@ -52,7 +52,14 @@ def parse():
     ap.add_argument("--impl", default="glrm", choices=["glrm", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=100_000,
+                    help="rows of the mixed table (smaller for profiling runs)")
+    ap.add_argument("--path", default="auto",
+                    help="kernel paths 'X,Y' (auto, chunked, fused, blocked, masked, panels)")
     return ap.parse_args()
+
+
+PATH_CODES = {"auto": 0, "chunked": 1, "fused": 2, "blocked": 3, "masked": 4, "panels": 5}
 
 
 # ---------------------------------------------------------------- helpers
@@ -215,7 +222,7 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "CPU run"},
+        "config": {"workload": WORKLOAD.format(m=t.m), "l2": "CPU run"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -235,9 +242,13 @@ def run_glrm(args, world, rank, local):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    t = W.mixed()
+    t = W.mixed(m=args.rows)
     stream = torch.cuda.current_stream(dev)
     g = G.GLRM.from_table(t, precision=G.GLRM_FP32, device=dev, stream=stream)
+    if args.path != "auto":
+        px, py = (PATH_CODES[v] for v in args.path.split(","))
+        G.glrm_set_path(g.h, px, py)
+    paths = G.glrm_get_path(g.h)
     torch.cuda.synchronize(dev)
 
     def barrier():
@@ -340,7 +351,8 @@ def run_glrm(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nnz": t.nnz, "m": t.m, "n": t.n, "k": t.k,
+            "config": {"workload": WORKLOAD.format(m=t.m), "nnz": t.nnz, "m": t.m, "n": t.n, "k": t.k,
+                       "paths": {"x": paths[0], "y": paths[1]},
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (CSR+CSC 0.96 GB); no flush"},
             "roofline": roofline,

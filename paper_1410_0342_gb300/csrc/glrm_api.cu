@@ -145,14 +145,14 @@ int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, siz
         dfree(o.tptr);
         return GLRM_OK;
     }
-    const size_t ring = (size_t)kStreamWarps * kRingSlotsHost * kRingBytes;
+    const size_t ring = (size_t)kMaskedWarps * kRingSlotsHost * kRingBytes;
     if (ring + 64 * ((size_t)K * es + 16) > budget) {
         dfree(o.tptr);
         return force == GLRM_PATH_AUTO ? GLRM_OK : fail(h, GLRM_ERR_ARG, "masked path: shared memory too small");
     }
     const size_t panel_all = ((((size_t)nother * K * es) + 15) & ~(size_t)15) +
                              (xstep ? (size_t)nother * sizeof(LossSpec) : 0);
-    const int64_t ngroups = (ntiles + kStreamWarps - 1) / kStreamWarps;
+    const int64_t ngroups = (ntiles + kMaskedWarps - 1) / kMaskedWarps;
     int64_t R, nb;
     if (panel_all + ring <= budget && force != GLRM_PATH_MASKED_PANELS) {
         R = nother;
@@ -346,6 +346,7 @@ const char *flag_message(int f)
     if (f & 4) return "indices within a row/column not strictly ascending (unsorted or duplicate)";
     if (f & 16) return "a CSC entry has no CSR counterpart";
     if (f & 32) return "CSR and CSC values differ for the same entry";
+    if (f & 64) return "a value outside its column loss's domain (Boolean: -1 or +1; ordinal: integer in 1..d)";
     return "invalid observed set";
 }
 
@@ -411,6 +412,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     }
     if (rc == GLRM_OK && hflag == 0) {
         e = launch_validate_cross(R, C, h->prec, flag, st);
+        if (e == cudaSuccess) e = launch_validate_domain(C, h->prec, h->loss_dev, flag, st);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_cross");
         if (rc == GLRM_OK) rc = check();
     }

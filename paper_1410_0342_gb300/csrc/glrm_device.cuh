@@ -72,7 +72,7 @@ __device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
         return -a * sg;
     }
     default: {
-        const int lev = (int)a;
+        const int lev = min(max((int)a, 1), s.levels);  // a is validated to 1..d at set-up
         T Ls = T(0), d = T(0);
         for (int ap = 1; ap < lev; ++ap) {
             T t = T(1) - u + T(ap);

@@ -20,8 +20,9 @@ constexpr int kChunk = 1024;
 constexpr int kMaxK = 64;
 constexpr int kPad = 8;  // zeroed entries after the last one in library copies of Omega
 constexpr int kStreamWarps = 8;  // warps per CTA of the staged (fused / blocked / masked) kernels
-constexpr int kRingSlotsHost = 4;  // value-stream ring slots per warp (masked kernels)
-constexpr int kRingBytes = 2048;   // bytes per ring slot
+constexpr int kMaskedWarps = 16;   // warps per CTA of the masked-tile kernels
+constexpr int kRingSlotsHost = 8;  // value-stream ring slots per warp (masked kernels)
+constexpr int kRingBytes = 1024;   // bytes per ring slot
 
 // How a half-step runs over one orientation (chosen at set-up):
 // chunked: entries cut into chunks, the other factor gathered from global
@@ -148,6 +149,8 @@ cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const vo
                                 cudaStream_t st);
 cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
                                   cudaStream_t st);
+cudaError_t launch_validate_domain(const Orient &csc, int prec, const LossSpec *loss, int *flag,
+                                   cudaStream_t st);
 cudaError_t launch_build_runptr(const Orient &o, cudaStream_t st);
 cudaError_t launch_mt_count(const Orient &o, int32_t *cnt, cudaStream_t st);
 cudaError_t launch_mt_build(const Orient &o, int prec, cudaStream_t st);

@@ -121,18 +121,23 @@ __global__ void mt_emit_kernel(int64_t nseg, const int32_t *__restrict__ ptr,
 // ------------------------------------------------------------ value stream
 
 // Sequential reader of a contiguous range of values through a ring of
-// kRingSlots chunks of C values in shared memory, filled by TMA bulk copies
-// (one mbarrier per slot).  Positions must be read in non-decreasing order.
-template <class T, int C>
-struct ValStream {
+// kRingSlots chunks of C values in shared memory (one mbarrier per slot),
+// filled by TMA bulk copies.  Offsets are relative to the 16-byte aligned
+// start of the range; since the ring holds a power-of-two number of values and
+// chunk q lives in slot q mod kRingSlots, offset o sits at ring[o mod size].
+template <class T>
+struct Ring {
+    static constexpr int C = kRingBytes / (int)sizeof(T);  // values per chunk
+    static constexpr int N = C * kRingSlots;                // values in the ring
+    static_assert((N & (N - 1)) == 0, "ring size must be a power of two");
     T *buf;
     uint64_t *bars;
     const T *src;
-    int64_t base;      // 16-byte aligned start of the range
-    int64_t hi;        // end of the range rounded up to 16 bytes
-    int64_t nchunks;   // chunks covering [base, hi)
-    int64_t issued, ready, freed;
-    unsigned phases;   // one parity bit per slot
+    uint32_t hi;       // aligned end of the range (offset)
+    uint32_t issued;   // offsets < issued have been requested
+    uint32_t ready;    // offsets < ready have landed
+    uint32_t freed;    // offsets < freed may be overwritten
+    unsigned phases;   // parity bit per slot
     bool ok;
 
     __device__ __forceinline__ void init(T *b, uint64_t *br)
@@ -140,104 +145,141 @@ struct ValStream {
         buf = b;
         bars = br;
         phases = 0;
-        issued = ready = freed = nchunks = 0;
+        issued = ready = freed = hi = 0;
         ok = true;
     }
 
     __device__ __forceinline__ void issue_one()
     {
-        const int slot = (int)(issued % kRingSlots);
-        const int64_t c0 = base + issued * C;
-        const int64_t n = min((int64_t)C, hi - c0);
+        const int slot = (int)((issued / C) % kRingSlots);
+        const uint32_t n = min((uint32_t)C, hi - issued);
         __syncwarp();
         if ((threadIdx.x & 31) == 0) {
             fence_proxy_async();
-            mbar_expect_tx(bars + slot, (unsigned)(n * sizeof(T)));
-            bulk_g2s(buf + (size_t)slot * C, src + c0, (unsigned)(n * sizeof(T)), bars + slot);
+            mbar_expect_tx(bars + slot, n * (unsigned)sizeof(T));
+            bulk_g2s(buf + (size_t)slot * C, src + issued, n * (unsigned)sizeof(T), bars + slot);
         }
-        ++issued;
+        issued += C;
     }
 
-    // Start reading [start, end) of src (a previous range must be finished).
-    __device__ __forceinline__ void begin(const T *s, int64_t start, int64_t end)
+    // Start reading global values [start, end); returns the offset of start.
+    __device__ __forceinline__ uint32_t begin(const T *s, int64_t start, int64_t end)
     {
-        src = s;
-        base = start & ~(int64_t)3;
-        hi = (end + 3) & ~(int64_t)3;
-        nchunks = end > start ? (hi - base + C - 1) / C : 0;
+        const int64_t base = start & ~(int64_t)3;
+        src = s + base;
+        hi = end > start ? (uint32_t)(((end + 3) & ~(int64_t)3) - base) : 0u;
         issued = ready = freed = 0;
-        while (issued < nchunks && issued < kRingSlots) issue_one();
+        while (issued < hi && issued < (uint32_t)N) issue_one();
+        return (uint32_t)(start - base);
     }
 
-    // Make positions < vend readable.
-    __device__ __forceinline__ void ensure(int64_t vend)
+    // Make offsets < e readable (bounded waits).
+    __device__ __forceinline__ void ensure(uint32_t e)
     {
-        while (ready < nchunks && base + ready * C < vend) {
-            const int slot = (int)(ready % kRingSlots);
+        while (ready < e && ready < hi) {
+            const int slot = (int)((ready / C) % kRingSlots);
             bool w = mbar_wait_bounded(bars + slot, (phases >> slot) & 1u);
             if (!w) w = mbar_wait_bounded(bars + slot, (phases >> slot) & 1u);
             ok = ok && w;
             phases ^= 1u << slot;
-            ++ready;
+            ready += C;
         }
     }
 
-    // Positions < v are consumed: recycle their chunks.
-    __device__ __forceinline__ void release(int64_t v)
+    // Offsets < c are consumed: recycle their chunks for the next requests.
+    __device__ __forceinline__ void release(uint32_t c)
     {
-        while (freed < ready && base + (freed + 1) * C <= v) {
-            ++freed;
-            if (issued < nchunks) issue_one();
+        while (freed + C <= c && freed + C <= ready) {
+            freed += C;
+            if (issued < hi) issue_one();
         }
     }
 
-    __device__ __forceinline__ T at(int64_t pos) const
-    {
-        const int64_t c = (pos - base) / C;
-        return buf[(size_t)(c % kRingSlots) * C + (pos - base - c * C)];
-    }
+    __device__ __forceinline__ T at(uint32_t o) const { return buf[o & (uint32_t)(N - 1)]; }
 
-    // Drain: wait for every issued chunk (bounded) so no copy targets the
-    // ring after the range is abandoned.
+    // Wait for every requested chunk so that no copy targets the ring after
+    // the range is left.
     __device__ __forceinline__ void drain()
     {
         while (ready < issued) {
-            const int slot = (int)(ready % kRingSlots);
+            const int slot = (int)((ready / C) % kRingSlots);
             bool w = mbar_wait_bounded(bars + slot, (phases >> slot) & 1u);
             ok = ok && w;
             phases ^= 1u << slot;
-            ++ready;
+            ready += C;
         }
         freed = ready;
     }
 };
 
-template <class T>
-struct RingChunk {
-    static constexpr int C = kRingBytes / (int)sizeof(T);
-};
+// Loss and derivative with the kind fixed at compile time when KIND >= 0.
+template <class T, int KIND>
+__device__ __forceinline__ T loss_k(const LossSpec &s, T u, T a, T &L)
+{
+    if constexpr (KIND < 0) {
+        return loss_deriv<T>(s, u, a, L);
+    } else {
+        LossSpec q = s;
+        q.kind = KIND;
+        return loss_deriv<T>(q, u, a, L);
+    }
+}
 
-// One pass of a warp over pairs [pb, pe) of a tile whose values start at
-// vstart; jbase is the first other-index of the panel in shared memory.
-template <class T, int K, bool XSTEP, bool GRAD>
-__device__ __forceinline__ T mt_pass(ValStream<T, RingChunk<T>::C> &vs, const Vec<T, K> &f,
-                                     Vec<T, K> &g, int pb, int pe, int64_t vstart, int jbase,
-                                     const int32_t *__restrict__ tidx,
-                                     const uint32_t *__restrict__ tmask, const T *__restrict__ tval,
-                                     int64_t vend, const T *Ws, const LossSpec *Ls,
-                                     const LossSpec &segspec)
+// Process `cnt` pairs of a batch (indices / masks in lane q of myj / mym).
+// Every lane runs the same instructions; lanes outside a pair's mask get zero
+// weight, so nothing diverges.
+template <class T, int K, bool XSTEP, bool GRAD, int KIND>
+__device__ __forceinline__ void mt_batch(int cnt, int myj, uint32_t mym, uint32_t &voff,
+                                         const Ring<T> &rg, const T *Ws, int jbase,
+                                         const LossSpec *Ls, const LossSpec &segspec,
+                                         const Vec<T, K> &f, Vec<T, K> &g, T &lsum)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll 2
+    for (int q = 0; q < cnt; ++q) {
+        const int j = __shfl_sync(0xffffffffu, myj, q);
+        const uint32_t m = __shfl_sync(0xffffffffu, mym, q);
+        const bool act = (m >> lane) & 1u;
+        // lanes outside the mask take a = 1 (inside every loss's domain)
+        const T a = act ? rg.at(voff + __popc(m & lt)) : T(1);
+        Vec<T, K> w;
+        w.load(Ws + (int64_t)(j - jbase) * K);
+        const T u = f.dot(w);
+        T L;
+        T d;
+        if constexpr (XSTEP) d = loss_k<T, KIND>(Ls[j - jbase], u, a, L);
+        else d = loss_k<T, KIND>(segspec, u, a, L);
+        d = act ? d : T(0);
+        lsum += act ? L : T(0);
+        if constexpr (GRAD) g.axpy(d, w);
+        voff += __popc(m);
+    }
+}
+
+// One pass of a warp over pairs [pb, pe) of a tile whose values are global
+// positions [vstart, vend); jbase: first other-index held in shared memory.
+template <class T, int K, bool XSTEP, bool GRAD>
+__device__ __forceinline__ T mt_pass(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K> &g, int pb, int pe,
+                                     int64_t vstart, int64_t vend, int jbase,
+                                     const int32_t *__restrict__ tidx,
+                                     const uint32_t *__restrict__ tmask, const T *__restrict__ tval,
+                                     const T *Ws, const LossSpec *Ls, const LossSpec &segspec)
+{
+    const int lane = threadIdx.x & 31;
     T lsum = T(0);
-    LossSpec sp = segspec;
-    vs.begin(tval, vstart, vend);
-    int64_t vpos = vstart;
+    uint32_t voff = rg.begin(tval, vstart, vend);
     int nj = 0;
     uint32_t nm = 0;
     if (pb + lane < pe) {
         nj = __ldg(tidx + pb + lane);
         nm = __ldg(tmask + pb + lane);
+    }
+    // Y-step: the tile's loss kind is fixed when all its segments share it
+    int segkind = -1;
+    if constexpr (!XSTEP) {
+        if (__all_sync(0xffffffffu, segspec.kind == __shfl_sync(0xffffffffu, segspec.kind, 0)))
+            segkind = segspec.kind;
     }
     for (int c0 = pb; c0 < pe; c0 += 32) {
         const int myj = nj;
@@ -247,27 +289,35 @@ __device__ __forceinline__ T mt_pass(ValStream<T, RingChunk<T>::C> &vs, const Ve
             nj = __ldg(tidx + c0 + 32 + lane);
             nm = __ldg(tmask + c0 + 32 + lane);
         }
-        for (int q = 0; q < cnt; ++q) {
-            const int j = __shfl_sync(0xffffffffu, myj, q);
-            const uint32_t m = __shfl_sync(0xffffffffu, mym, q);
-            const int pc = __popc(m);
-            vs.ensure(vpos + pc);
-            Vec<T, K> w;
-            w.load(Ws + (int64_t)(j - jbase) * K);
-            if constexpr (XSTEP) sp = Ls[j - jbase];
-            if ((m >> lane) & 1u) {
-                const T a = vs.at(vpos + __popc(m & lt));
-                const T u = f.dot(w);
-                T L;
-                const T d = loss_deriv<T>(sp, u, a, L);
-                if constexpr (GRAD) g.axpy(d, w);
-                lsum += L;
-            }
-            vpos += pc;
-            vs.release(vpos);
+        const uint32_t total = __reduce_add_sync(0xffffffffu, (unsigned)__popc(mym));
+        rg.ensure(voff + total);
+        int kind = segkind;
+        if constexpr (XSTEP) {
+            const int kj = Ls[(lane < cnt ? myj : __shfl_sync(0xffffffffu, myj, 0)) - jbase].kind;
+            kind = __all_sync(0xffffffffu, kj == __shfl_sync(0xffffffffu, kj, 0)) ? kj : -1;
         }
+        switch (kind) {
+        case kLossQuad:
+            mt_batch<T, K, XSTEP, GRAD, kLossQuad>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            break;
+        case kLossHuber:
+            mt_batch<T, K, XSTEP, GRAD, kLossHuber>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            break;
+        case kLossHinge:
+            mt_batch<T, K, XSTEP, GRAD, kLossHinge>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            break;
+        case kLossLogistic:
+            mt_batch<T, K, XSTEP, GRAD, kLossLogistic>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            break;
+        case kLossOrdinal:
+            mt_batch<T, K, XSTEP, GRAD, kLossOrdinal>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            break;
+        default:
+            mt_batch<T, K, XSTEP, GRAD, -1>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+        }
+        rg.release(voff);
     }
-    vs.drain();
+    rg.drain();
     return lsum;
 }
 
@@ -275,7 +325,7 @@ __device__ __forceinline__ T mt_pass(ValStream<T, RingChunk<T>::C> &vs, const Ve
 // loss table) in shared memory; one warp per tile runs gradient, prox,
 // re-evaluation and decision for its 32 segments.
 template <class T, int K, bool XSTEP>
-__global__ void __launch_bounds__(kStreamWarps * 32, 1)
+__global__ void __launch_bounds__(kMaskedWarps * 32, 1)
 mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *__restrict__ tvpan,
                 const int32_t *__restrict__ tidx, const uint32_t *__restrict__ tmask,
                 const T *__restrict__ tval, T *__restrict__ F, const T *__restrict__ W,
@@ -283,16 +333,15 @@ mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *_
                 int rk, T rw, double *__restrict__ kept_obj, double *__restrict__ kept_reg,
                 int32_t *__restrict__ accepted, int *__restrict__ err)
 {
-    constexpr int C = RingChunk<T>::C;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ uint64_t bar_panel;
-    __shared__ uint64_t bar_ring[kStreamWarps][kRingSlots];
+    __shared__ uint64_t bar_ring[kMaskedWarps][kRingSlots];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T *Ws = reinterpret_cast<T *>(dsm);
     size_t off = align16((size_t)nother * K * sizeof(T));
     LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
     if constexpr (XSTEP) off += (size_t)nother * sizeof(LossSpec);
-    T *ring = reinterpret_cast<T *>(dsm + off) + (size_t)wid * kRingSlots * C;
+    T *ring = reinterpret_cast<T *>(dsm + off) + (size_t)wid * Ring<T>::N;
     if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
     if (lane < kRingSlots) mbar_init(&bar_ring[wid][lane], 1);
     __syncthreads();
@@ -300,11 +349,11 @@ mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *_
         for (int64_t q = threadIdx.x; q < nother; q += blockDim.x) Ls[q] = loss[q];
     }
     if (!stage_panel<T>(Ws, W, 0, (int)nother, k, K, &bar_panel, 0, err)) return;
-    ValStream<T, C> vs;
+    Ring<T> vs;
     vs.init(ring, &bar_ring[wid][0]);
     const int64_t ntiles = (nseg + 31) / 32;
-    for (int64_t t = (int64_t)blockIdx.x * kStreamWarps + wid; t < ntiles;
-         t += (int64_t)gridDim.x * kStreamWarps) {
+    for (int64_t t = (int64_t)blockIdx.x * kMaskedWarps + wid; t < ntiles;
+         t += (int64_t)gridDim.x * kMaskedWarps) {
         const int64_t s = t * 32 + lane;
         const bool live = s < nseg;
         const int pb = tpan[2 * t], pe = tpan[2 * t + 1];
@@ -317,7 +366,7 @@ mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *_
         if constexpr (!XSTEP) {
             if (live) sp = loss[s];
         }
-        const T l1 = mt_pass<T, K, XSTEP, true>(vs, f, g, pb, pe, vb, 0, tidx, tmask, tval, ve, Ws,
+        const T l1 = mt_pass<T, K, XSTEP, true>(vs, f, g, pb, pe, vb, ve, 0, tidx, tmask, tval, Ws,
                                                 Ls, sp);
         const T al = live ? alpha[s] : T(0);
         Vec<T, K> fp;
@@ -337,8 +386,8 @@ mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *_
             fp.load_masked(tmp, K);
         }
         Vec<T, K> unused;
-        const T l2 = mt_pass<T, K, XSTEP, false>(vs, fp, unused, pb, pe, vb, 0, tidx, tmask, tval,
-                                                 ve, Ws, Ls, sp);
+        const T l2 = mt_pass<T, K, XSTEP, false>(vs, fp, unused, pb, pe, vb, ve, 0, tidx, tmask,
+                                                 tval, Ws, Ls, sp);
         if (!vs.ok) {
             if (lane == 0) atomicOr(err, 1);
             return;
@@ -364,7 +413,7 @@ mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *_
 // CTA stages the panel, each warp reduces its tiles' pairs in that panel into
 // per-(panel, segment) partials (GRAD: gradient and loss at F; else loss).
 template <class T, int K, bool XSTEP, bool GRAD>
-__global__ void __launch_bounds__(kStreamWarps * 32, 1)
+__global__ void __launch_bounds__(kMaskedWarps * 32, 1)
 mt_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
                const int32_t *__restrict__ tpan, const int32_t *__restrict__ tvpan,
                const int32_t *__restrict__ tidx, const uint32_t *__restrict__ tmask,
@@ -372,20 +421,19 @@ mt_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
                const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
                double *__restrict__ part_loss, int *__restrict__ err)
 {
-    constexpr int C = RingChunk<T>::C;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ uint64_t bar_panel;
-    __shared__ uint64_t bar_ring[kStreamWarps][kRingSlots];
+    __shared__ uint64_t bar_ring[kMaskedWarps][kRingSlots];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T *Ws = reinterpret_cast<T *>(dsm);
     size_t off = align16((size_t)R * K * sizeof(T));
     LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
     if constexpr (XSTEP) off += (size_t)R * sizeof(LossSpec);
-    T *ring = reinterpret_cast<T *>(dsm + off) + (size_t)wid * kRingSlots * C;
+    T *ring = reinterpret_cast<T *>(dsm + off) + (size_t)wid * Ring<T>::N;
     if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
     if (lane < kRingSlots) mbar_init(&bar_ring[wid][lane], 1);
     __syncthreads();
-    ValStream<T, C> vs;
+    Ring<T> vs;
     vs.init(ring, &bar_ring[wid][0]);
     const int64_t ntiles = (nseg + 31) / 32;
     const int64_t tiles_per = (ntiles + ngroups - 1) / ngroups;
@@ -404,7 +452,7 @@ mt_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
         pphase ^= 1u;
         const int64_t t0 = grp * tiles_per;
         const int64_t t1 = t0 + tiles_per < ntiles ? t0 + tiles_per : ntiles;
-        for (int64_t t = t0 + wid; t < t1; t += kStreamWarps) {
+        for (int64_t t = t0 + wid; t < t1; t += kMaskedWarps) {
             const int64_t s = t * 32 + lane;
             const bool live = s < nseg;
             const int64_t pi = t * (nb + 1) + b;
@@ -418,8 +466,8 @@ mt_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
             if constexpr (!XSTEP) {
                 if (live) sp = loss[s];
             }
-            const T l = mt_pass<T, K, XSTEP, GRAD>(vs, f, g, pb, pe, vb, (int)r0, tidx, tmask, tval,
-                                                   ve, Ws, Ls, sp);
+            const T l = mt_pass<T, K, XSTEP, GRAD>(vs, f, g, pb, pe, vb, ve, (int)r0, tidx, tmask,
+                                                   tval, Ws, Ls, sp);
             if (live) {
                 const int64_t slot = (int64_t)b * nseg + s;
                 if constexpr (GRAD) {
@@ -458,7 +506,7 @@ cudaError_t mt_half_K(glrm_s *h)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_bytes);
         if (e != cudaSuccess) return e;
         tmark(h, XSTEP ? "masked_fused_x" : "masked_fused_y");
-        kern<<<o.grid, kStreamWarps * 32, o.smem_bytes, h->stream>>>(
+        kern<<<o.grid, kMaskedWarps * 32, o.smem_bytes, h->stream>>>(
             o.nseg, o.tpan, o.tvpan, o.tidx, o.tmask, (const T *)o.tval, F, W, nother, h->k, alpha,
             h->loss_dev, rk, rw, kobj, kreg, acc, h->s.err);
         tmark(h, nullptr);
@@ -474,7 +522,7 @@ cudaError_t mt_half_K(glrm_s *h)
                                   (int)o.smem_bytes)) != cudaSuccess)
         return e;
     tmark(h, XSTEP ? "masked_grad_x" : "masked_grad_y");
-    pass_g<<<o.grid, kStreamWarps * 32, o.smem_bytes, h->stream>>>(
+    pass_g<<<o.grid, kMaskedWarps * 32, o.smem_bytes, h->stream>>>(
         o.nseg, o.nb, o.R, o.ngroups, nother, o.tpan, o.tvpan, o.tidx, o.tmask, (const T *)o.tval,
         F, W, h->k, h->loss_dev, (T *)s.part_grad, s.part_loss, h->s.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -485,7 +533,7 @@ cudaError_t mt_half_K(glrm_s *h)
         s.f_old, s.r_old, s.r_new);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, XSTEP ? "masked_loss_x" : "masked_loss_y");
-    pass_l<<<o.grid, kStreamWarps * 32, o.smem_bytes, h->stream>>>(
+    pass_l<<<o.grid, kMaskedWarps * 32, o.smem_bytes, h->stream>>>(
         o.nseg, o.nb, o.R, o.ngroups, nother, o.tpan, o.tvpan, o.tidx, o.tmask, (const T *)o.tval,
         (const T *)s.cand, W, h->k, h->loss_dev, nullptr, s.part_loss2, h->s.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

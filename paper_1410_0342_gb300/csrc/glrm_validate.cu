@@ -74,7 +74,40 @@ __global__ void validate_cross_kernel(const int32_t *__restrict__ colptr,
     if (lane == 0 && f) atomicOr(flag, f);
 }
 
+// One warp per column: values inside the column loss's domain (Boolean
+// losses: -1 or +1; ordinal hinge: an integer in 1..d).
+template <class T>
+__global__ void validate_domain_kernel(const int32_t *__restrict__ colptr, const T *__restrict__ cval,
+                                       int64_t n, const LossSpec *__restrict__ loss, int *flag)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const LossSpec sp = loss[j];
+    int f = 0;
+    for (int q = colptr[j] + lane; q < colptr[j + 1]; q += 32) {
+        const T a = cval[q];
+        if ((sp.kind == kLossHinge || sp.kind == kLossLogistic) && !(a == T(1) || a == T(-1))) f |= 64;
+        if (sp.kind == kLossOrdinal && !(a >= T(1) && a <= T(sp.levels) && a == (T)(int)a)) f |= 64;
+    }
+    for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0 && f) atomicOr(flag, f);
+}
+
 }  // namespace
+
+cudaError_t launch_validate_domain(const Orient &csc, int prec, const LossSpec *loss, int *flag,
+                                   cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((csc.nseg + 7) / 8);
+    if (prec == GLRM_FP64)
+        validate_domain_kernel<double><<<nb, 256, 0, st>>>(csc.ptr, (const double *)csc.val, csc.nseg,
+                                                           loss, flag);
+    else
+        validate_domain_kernel<float><<<nb, 256, 0, st>>>(csc.ptr, (const float *)csc.val, csc.nseg,
+                                                          loss, flag);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_validate_ptr(const int32_t *ptr, int64_t nseg, int64_t nnz, int *flag,
                                 cudaStream_t st)

@@ -37,7 +37,10 @@ def test_paths_match_oracle_fp32(G, oracle_mod, paths, k):
     t = W.small_mixed(m=1303, n=150, k=k, p_obs=0.5, seed=200 + k)
     g = G.GLRM.from_table(t)
     G.glrm_set_path(g.h, *paths)
-    assert G.glrm_get_path(g.h) == paths
+    got = G.glrm_get_path(g.h)
+    for want, have in zip(paths, got):
+        # a masked request runs panel by panel when the factor does not fit whole
+        assert have == want or (want == G.GLRM_PATH_MASKED and have == G.GLRM_PATH_MASKED_PANELS)
     hist = g.sweep(15)
     X, Yt, ax, ay, ohist, oacc = oracle_hist(oracle_mod, t, 15)
     rel = np.abs(hist - ohist) / np.abs(ohist)

@@ -208,7 +208,8 @@ def _omega_tensors(t, dt=torch.float32):
             torch.as_tensor(t.cval, dtype=dt, device="cuda")]
 
 
-@pytest.mark.parametrize("fault", ["ptr", "range", "dup", "unsorted", "cross", "value", "nan"])
+@pytest.mark.parametrize("fault", ["ptr", "range", "dup", "unsorted", "cross", "value", "nan",
+                                   "domain"])
 def test_observed_set_validation(G, fault):
     t = W.small_mixed(m=40, n=15, k=4, seed=71)
     g = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry)
@@ -230,6 +231,14 @@ def test_observed_set_validation(G, fault):
         a[5][3] += 1.0
     elif fault == "nan":
         a[2][2] = float("nan")
+    elif fault == "domain":
+        # an ordinal column (kind 4 every fifth column) gets level 0 in both orientations
+        j = 4
+        q = int(t.colptr[j])
+        i = int(t.rowidx[q])
+        e = int(t.rowptr[i]) + int(np.searchsorted(t.colidx[t.rowptr[i]:t.rowptr[i + 1]], j))
+        a[2][e] = 0.0
+        a[5][q] = 0.0
     with pytest.raises(G.GLRMError) as e:
         G.glrm_set_observed(g.h, t.nnz, *a)
     expect = G.GLRM_ERR_NONFINITE if fault == "nan" else G.GLRM_ERR_OMEGA
