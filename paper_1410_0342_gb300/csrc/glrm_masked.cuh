@@ -180,7 +180,7 @@ struct Ring {
             const int slot = (int)((ready / C) % kRingSlots);
             bool w = mbar_wait_bounded(bars + slot, (phases >> slot) & 1u);
             if (!w) w = mbar_wait_bounded(bars + slot, (phases >> slot) & 1u);
-            ok = ok && w;
+            ok = __all_sync(0xffffffffu, ok && w);  // warp-uniform verdict
             phases ^= 1u << slot;
             ready += C;
         }
@@ -204,7 +204,7 @@ struct Ring {
         while (ready < issued) {
             const int slot = (int)((ready / C) % kRingSlots);
             bool w = mbar_wait_bounded(bars + slot, (phases >> slot) & 1u);
-            ok = ok && w;
+            ok = __all_sync(0xffffffffu, ok && w);
             phases ^= 1u << slot;
             ready += C;
         }
@@ -278,8 +278,8 @@ __device__ __forceinline__ T mt_pass(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K> 
     // Y-step: the tile's loss kind is fixed when all its segments share it
     int segkind = -1;
     if constexpr (!XSTEP) {
-        if (__all_sync(0xffffffffu, segspec.kind == __shfl_sync(0xffffffffu, segspec.kind, 0)))
-            segkind = segspec.kind;
+        const int k0 = __shfl_sync(0xffffffffu, segspec.kind, 0);
+        if (__all_sync(0xffffffffu, segspec.kind == k0)) segkind = segspec.kind;
     }
     for (int c0 = pb; c0 < pe; c0 += 32) {
         const int myj = nj;
@@ -293,8 +293,11 @@ __device__ __forceinline__ T mt_pass(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K> 
         rg.ensure(voff + total);
         int kind = segkind;
         if constexpr (XSTEP) {
-            const int kj = Ls[(lane < cnt ? myj : __shfl_sync(0xffffffffu, myj, 0)) - jbase].kind;
-            kind = __all_sync(0xffffffffu, kj == __shfl_sync(0xffffffffu, kj, 0)) ? kj : -1;
+            // every lane shuffles (full mask), then lanes past the batch reuse pair 0
+            const int j0 = __shfl_sync(0xffffffffu, myj, 0);
+            const int kj = Ls[(lane < cnt ? myj : j0) - jbase].kind;
+            const int k0 = __shfl_sync(0xffffffffu, kj, 0);
+            kind = __all_sync(0xffffffffu, kj == k0) ? kj : -1;
         }
         switch (kind) {
         case kLossQuad:

@@ -337,7 +337,7 @@ struct EntryStream {
         bool ok = mbar_wait_bounded(bar, ph);
         if (!ok) ok = mbar_wait_bounded(bar, ph);
         if (q) ph1 ^= 1u; else ph0 ^= 1u;
-        return ok;
+        return __all_sync(0xffffffffu, ok);  // warp-uniform verdict
     }
 };
 
