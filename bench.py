@@ -55,11 +55,11 @@ def parse():
     ap.add_argument("--rows", type=int, default=100_000,
                     help="rows of the mixed table (smaller for profiling runs)")
     ap.add_argument("--path", default="auto",
-                    help="kernel paths 'X,Y' (auto, chunked, fused, blocked, masked, panels)")
+                    help="kernel paths 'X,Y' (auto, chunked, fused, blocked, masked, split)")
     return ap.parse_args()
 
 
-PATH_CODES = {"auto": 0, "chunked": 1, "fused": 2, "blocked": 3, "masked": 4, "panels": 5}
+PATH_CODES = {"auto": 0, "chunked": 1, "fused": 2, "blocked": 3, "masked": 4, "split": 5}
 
 
 # ---------------------------------------------------------------- helpers

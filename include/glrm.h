@@ -224,13 +224,16 @@ int glrm_set_state(glrm_t h, const void *buf_host, size_t len);
  *                      (panel, segment) partials summed over panels in a fixed
  *                      order
  *   GLRM_PATH_MASKED   segments in tiles of 32, one per lane; a warp walks the
- *                      union of its tile's other-indices in order, loading each
- *                      other-factor row once as a broadcast from shared memory
- *                      (whole factor, or panel by panel); values re-ordered at
- *                      set-up and streamed by TMA
- *   GLRM_PATH_MASKED_PANELS  the masked path with at least two panels even when
- *                      the factor would fit whole (glrm_get_path reports it for
- *                      any masked path that runs panel by panel)
+ *                      union of its tile's other-indices in order and reads each
+ *                      other-factor row once as a shared-memory broadcast (the
+ *                      whole factor resident, or the rows of each batch of 32
+ *                      gathered with cp.async); values re-ordered at set-up and
+ *                      streamed by TMA.  When there are fewer tiles than warps
+ *                      on the GPU, a tile's list is split over several warps
+ *                      whose partials are summed in a fixed order.
+ *   GLRM_PATH_MASKED_SPLIT  the masked path with every tile split in two or
+ *                      more units (glrm_get_path reports it whenever a masked
+ *                      half-step runs split)
  * GLRM_PATH_AUTO picks masked when a tile's pairs average >= 8 observed lanes
  * (dense tables), else fused when the other factor fits, else blocked when a
  * (panel, segment) run holds >= 64 entries on average, else chunked.  The
@@ -244,7 +247,7 @@ typedef enum {
     GLRM_PATH_FUSED = 2,
     GLRM_PATH_BLOCKED = 3,
     GLRM_PATH_MASKED = 4,
-    GLRM_PATH_MASKED_PANELS = 5
+    GLRM_PATH_MASKED_SPLIT = 5
 } glrm_path;
 int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path);
 int glrm_get_path(glrm_t h, int32_t *paths_host);

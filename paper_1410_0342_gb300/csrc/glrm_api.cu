@@ -56,9 +56,11 @@ void free_orient(Orient &o)
     dfree(o.tidx);
     dfree(o.tmask);
     dfree(o.tval);
-    dfree(o.tpan);
-    dfree(o.tvpan);
+    dfree(o.ubeg);
+    dfree(o.utile);
+    dfree(o.uvoff);
     o.npairs = 0;
+    o.nunits = 0;
     o.nchunks = 0;
     o.maxlen = 0;
     o.mode = kModeChunked;
@@ -120,13 +122,17 @@ int tiled_width(int k)
 // other factor (plus, for the X-step, its loss table) fits in one CTA's shared
 // memory; blocked when panels of it do and a (panel, segment) run holds 64
 // entries or more on average; chunked otherwise.
-// Masked tiles: count each tile's pairs, and build the layout when forced or
-// when a pair averages >= 8 observed lanes.
+// Masked tiles: count each tile's pairs; build the layout when forced or when
+// a pair averages >= 8 observed lanes.  The other factor is kept whole in
+// shared memory when it fits, else gathered per batch (needs k == K).  Tiles
+// are split into units of P pairs only when there are too few tiles to give
+// every warp of the GPU one.
 int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, size_t budget)
 {
     const size_t es = elem_size(h->prec);
     const int64_t nother = xstep ? h->n : h->m;
     const int64_t ntiles = (o.nseg + 31) / 32;
+    const bool forced = force != GLRM_PATH_AUTO;
     CK(cudaMalloc(&o.tptr, (size_t)(ntiles + 1) * sizeof(int32_t)));
     CK(launch_mt_count(o, o.tptr, h->stream));
     std::vector<int32_t> cnt((size_t)ntiles);
@@ -135,39 +141,56 @@ int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, siz
     CK(cudaStreamSynchronize(h->stream));
     std::vector<int32_t> off((size_t)ntiles + 1);
     int64_t tot = 0;
+    int32_t cmax = 0;
     for (int64_t t = 0; t < ntiles; ++t) {
         off[t] = (int32_t)tot;
         tot += cnt[t];
+        cmax = std::max(cmax, cnt[t]);
     }
     off[ntiles] = (int32_t)tot;
     const double lanes = tot ? (double)h->nnz / (double)tot : 0.0;
-    if (force == GLRM_PATH_AUTO && lanes < 8.0) {
+    auto give_up = [&](const char *why) {
         dfree(o.tptr);
-        return GLRM_OK;
+        return forced ? fail(h, GLRM_ERR_ARG, why) : GLRM_OK;
+    };
+    if (!forced && lanes < 8.0) return give_up("");
+    const size_t ring = (size_t)kRingSlotsHost * kRingBytes;
+    const size_t full_fixed = ((((size_t)nother * K * es) + 15) & ~(size_t)15) +
+                              (xstep ? (size_t)nother * sizeof(LossSpec) : 0);
+    const size_t gather_warp = ring + 2 * 32 * (size_t)K * es;
+    int warps = 0;
+    bool full = false;
+    for (int w = kMaskedWarps; w >= 4 && !warps; w -= 4) {
+        if (full_fixed + w * ring <= budget) {
+            warps = w;
+            full = true;
+        } else if (h->k == K && w * gather_warp <= budget) {
+            warps = w;
+        }
     }
-    const size_t ring = (size_t)kMaskedWarps * kRingSlotsHost * kRingBytes;
-    if (ring + 64 * ((size_t)K * es + 16) > budget) {
-        dfree(o.tptr);
-        return force == GLRM_PATH_AUTO ? GLRM_OK : fail(h, GLRM_ERR_ARG, "masked path: shared memory too small");
+    if (!warps) return give_up("masked path: the other factor neither fits in shared memory nor can be gathered (k must be a multiple of 4)");
+    const int64_t slots = (int64_t)sms * warps;
+    int64_t P = std::max<int64_t>(cmax, 1);
+    if (force == GLRM_PATH_MASKED_SPLIT) {
+        P = std::max<int64_t>(32, ((cmax + 1) / 2 + 31) & ~(int64_t)31);
+    } else if (ntiles < slots) {
+        P = std::max<int64_t>(256, ((tot / (2 * slots)) + 31) & ~(int64_t)31);
+        if (P >= cmax) P = cmax;
     }
-    const size_t panel_all = ((((size_t)nother * K * es) + 15) & ~(size_t)15) +
-                             (xstep ? (size_t)nother * sizeof(LossSpec) : 0);
-    const int64_t ngroups = (ntiles + kMaskedWarps - 1) / kMaskedWarps;
-    int64_t R, nb;
-    if (panel_all + ring <= budget && force != GLRM_PATH_MASKED_PANELS) {
-        R = nother;
-        nb = 1;
-    } else {
-        const int64_t per_row = (int64_t)K * es + (xstep ? (int64_t)sizeof(LossSpec) : 0);
-        const int64_t Rmax = (((int64_t)budget - (int64_t)ring) / per_row) & ~(int64_t)31;
-        const int64_t nb_target = std::max<int64_t>(2, (4LL * sms + ngroups - 1) / ngroups);
-        R = ((nother + nb_target - 1) / nb_target + 31) & ~(int64_t)31;
-        R = std::max<int64_t>(32, std::min<int64_t>(R, Rmax));
-        nb = (nother + R - 1) / R;
+    std::vector<int32_t> ubeg((size_t)ntiles + 1);
+    std::vector<int32_t> utile;
+    int64_t nunits = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        ubeg[t] = (int32_t)nunits;
+        const int64_t nu = cnt[t] ? (cnt[t] + P - 1) / P : 1;  // an empty tile keeps one unit
+        for (int64_t q = 0; q < nu; ++q) utile.push_back((int32_t)t);
+        nunits += nu;
     }
-    o.R = (int)R;
-    o.nb = (int)nb;
-    o.ngroups = (int)ngroups;
+    ubeg[ntiles] = (int32_t)nunits;
+    o.full = full;
+    o.warps = warps;
+    o.P = (int)P;
+    o.nunits = nunits;
     o.npairs = tot;
     CK(cudaMemcpyAsync(o.tptr, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                        h->stream));
@@ -175,19 +198,30 @@ int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, siz
     CK(cudaMalloc(&o.tmask, (size_t)std::max<int64_t>(tot, 1) * sizeof(uint32_t)));
     CK(cudaMalloc(&o.tval, ((size_t)h->nnz + kPad) * es));
     CK(cudaMemsetAsync(o.tval, 0, ((size_t)h->nnz + kPad) * es, h->stream));
-    CK(cudaMalloc(&o.tpan, (size_t)ntiles * (nb + 1) * sizeof(int32_t)));
-    CK(cudaMalloc(&o.tvpan, (size_t)ntiles * (nb + 1) * sizeof(int32_t)));
+    CK(cudaMalloc(&o.ubeg, ubeg.size() * sizeof(int32_t)));
+    CK(cudaMalloc(&o.utile, (size_t)nunits * sizeof(int32_t)));
+    CK(cudaMalloc(&o.uvoff, (size_t)nunits * sizeof(int32_t)));
+    CK(cudaMemcpyAsync(o.ubeg, ubeg.data(), ubeg.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(o.utile, utile.data(), utile.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       h->stream));
+    // empty tiles never reach the emit loop: their single unit starts at
+    // the tile's first value
+    std::vector<int32_t> uvoff0((size_t)nunits, 0);
+    {
+        std::vector<int32_t> ptr((size_t)o.nseg + 1);
+        CK(cudaMemcpyAsync(ptr.data(), o.ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int64_t t = 0; t < ntiles; ++t) uvoff0[ubeg[t]] = ptr[(size_t)(t * 32)];
+    }
+    CK(cudaMemcpyAsync(o.uvoff, uvoff0.data(), uvoff0.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       h->stream));
     CK(launch_mt_build(o, h->prec, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     o.mode = kModeMasked;
-    if (nb == 1) {
-        o.smem_bytes = panel_all + ring;
-        o.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)sms));
-    } else {
-        o.smem_bytes = ((((size_t)R * K * es) + 15) & ~(size_t)15) +
-                       (xstep ? (size_t)R * sizeof(LossSpec) : 0) + ring;
-        o.grid = sms;
-    }
+    o.smem_bytes = full ? full_fixed + (size_t)warps * ring : (size_t)warps * gather_warp;
+    o.grid = (int)std::max<int64_t>(1, std::min<int64_t>((nunits + warps - 1) / warps, (int64_t)sms));
     return GLRM_OK;
 }
 
@@ -201,8 +235,9 @@ int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
     dfree(o.tidx);
     dfree(o.tmask);
     dfree(o.tval);
-    dfree(o.tpan);
-    dfree(o.tvpan);
+    dfree(o.ubeg);
+    dfree(o.utile);
+    dfree(o.uvoff);
     const int K = tiled_width(h->k);
     o.mode = kModeChunked;
     if (force == GLRM_PATH_CHUNKED) return GLRM_OK;
@@ -214,7 +249,7 @@ int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
     const int64_t nother = xstep ? h->n : h->m;
     const size_t per_row = (size_t)K * es + (xstep ? sizeof(LossSpec) : 0);
     const size_t budget = (size_t)optin - 1024;
-    if (force == GLRM_PATH_AUTO || force == GLRM_PATH_MASKED || force == GLRM_PATH_MASKED_PANELS) {
+    if (force == GLRM_PATH_AUTO || force == GLRM_PATH_MASKED || force == GLRM_PATH_MASKED_SPLIT) {
         int rc = plan_masked(h, o, xstep, force, K, sms, budget);
         if (rc != GLRM_OK || o.mode == kModeMasked || force != GLRM_PATH_AUTO) return rc;
     }
@@ -296,7 +331,8 @@ void build_chunks(const std::vector<int32_t> &ptr, std::vector<int4> &chunks,
 // panels x segments when blocked).
 int64_t partial_slots(const Orient &o)
 {
-    return (o.mode == kModeBlocked || o.mode == kModeMasked) ? (int64_t)o.nb * o.nseg : o.nchunks;
+    if (o.mode == kModeMasked) return o.nunits * 32;
+    return o.mode == kModeBlocked ? (int64_t)o.nb * o.nseg : o.nchunks;
 }
 
 int alloc_scratch(glrm_s *h)
@@ -813,7 +849,7 @@ int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     for (int p : {xstep_path, ystep_path})
-        if (p < GLRM_PATH_AUTO || p > GLRM_PATH_MASKED_PANELS) return fail(h, GLRM_ERR_ARG, "bad path");
+        if (p < GLRM_PATH_AUTO || p > GLRM_PATH_MASKED_SPLIT) return fail(h, GLRM_ERR_ARG, "bad path");
     h->path_x = xstep_path;
     h->path_y = ystep_path;
     if (!h->have_omega) return GLRM_OK;
@@ -843,7 +879,8 @@ int glrm_get_path(glrm_t h, int32_t *paths_host)
     if (!h || !paths_host) return fail(h, GLRM_ERR_ARG, "null argument");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
     auto code = [](const Orient &o) {
-        if (o.mode == kModeMasked) return o.nb == 1 ? GLRM_PATH_MASKED : GLRM_PATH_MASKED_PANELS;
+        if (o.mode == kModeMasked)
+            return o.nunits == (o.nseg + 31) / 32 ? GLRM_PATH_MASKED : GLRM_PATH_MASKED_SPLIT;
         return o.mode == kModeFused ? GLRM_PATH_FUSED
                                     : (o.mode == kModeBlocked ? GLRM_PATH_BLOCKED : GLRM_PATH_CHUNKED);
     };

@@ -72,18 +72,18 @@ __device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
         return -a * sg;
     }
     default: {
-        const int lev = min(max((int)a, 1), s.levels);  // a is validated to 1..d at set-up
-        T Ls = T(0), d = T(0);
-        for (int ap = 1; ap < lev; ++ap) {
-            T t = T(1) - u + T(ap);
-            if (t > T(0)) { Ls += t; d -= T(1); }
-        }
-        for (int ap = lev + 1; ap <= s.levels; ++ap) {
-            T t = T(1) + u - T(ap);
-            if (t > T(0)) { Ls += t; d += T(1); }
-        }
-        L = Ls;
-        return d;
+        // Ordinal hinge in closed form.  A term (1 - u + a')_+ with a' < a is
+        // active (> 0) exactly for a' >= floor(u); a term (1 + u - a')_+ with
+        // a' > a exactly for a' <= ceil(u).  With n1, n2 active terms over the
+        // integer ranges [lo1, hi1], [lo2, hi2] the sums are arithmetic series.
+        const T d = T(s.levels);
+        const T lev = fmin(fmax(a, T(1)), d);  // a is validated to 1..d at set-up
+        const T lo1 = fmax(T(1), floor(u)), hi1 = lev - T(1);
+        const T n1 = fmax(T(0), hi1 - lo1 + T(1));
+        const T lo2 = lev + T(1), hi2 = fmin(d, ceil(u));
+        const T n2 = fmax(T(0), hi2 - lo2 + T(1));
+        L = n1 * (T(1) - u) + T(0.5) * n1 * (lo1 + hi1) + n2 * (T(1) + u) - T(0.5) * n2 * (lo2 + hi2);
+        return n2 - n1;
     }
     }
 }

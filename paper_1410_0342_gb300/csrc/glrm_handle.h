@@ -50,14 +50,20 @@ struct Orient {
     int grid = 0;                    // fused / blocked: CTAs per launch
     int cap = 0;                     // fused / blocked: entries per staging buffer
     size_t smem_bytes = 0;           // fused / blocked / masked: dynamic shared memory
-    // masked tiles (nb panels of R other-indices; nb == 1: fused kernel)
+    // masked tiles: pair lists per tile of 32 segments, cut into units of at
+    // most P pairs (one unit per tile: fused kernel; more: partials)
     int64_t npairs = 0;
+    bool full = false;         // other factor resident in shared memory (else gathered)
+    int warps = 0;             // warps per CTA of the masked kernel
+    int P = 0;                 // pairs per unit
+    int64_t nunits = 0;
     int32_t *tptr = nullptr;   // ntiles + 1: first pair of each tile
     int32_t *tidx = nullptr;   // npairs: other-index of each pair
     uint32_t *tmask = nullptr; // npairs: lanes holding it
     void *tval = nullptr;      // nnz + kPad values in (tile, index, lane) order
-    int32_t *tpan = nullptr;   // ntiles x (nb + 1): first pair of each panel
-    int32_t *tvpan = nullptr;  // ntiles x (nb + 1): first value of each panel
+    int32_t *ubeg = nullptr;   // ntiles + 1: first unit of each tile
+    int32_t *utile = nullptr;  // nunits: tile of each unit
+    int32_t *uvoff = nullptr;  // nunits: first value of each unit
 };
 
 struct Scratch {

@@ -56,15 +56,15 @@ static __global__ void mt_count_kernel(int64_t nseg, const int32_t *__restrict__
     if (lane == 0) cnt[t] = c;
 }
 
-// Emit pairs and tile-ordered values; record for every panel b (other-index
-// in [b R, (b+1) R)) the first pair and the value offset of the panel.
+// Emit pairs and tile-ordered values.  A tile's pair list is cut into units
+// of at most P pairs (unit q of tile t starts at pair tptr[t] + q P); the
+// value offset where each unit starts goes to uvoff[ubeg[t] + q].
 template <class T>
 __global__ void mt_emit_kernel(int64_t nseg, const int32_t *__restrict__ ptr,
                                const int32_t *__restrict__ idx, const T *__restrict__ val,
-                               const int32_t *__restrict__ tptr, int nb, int R,
-                               int32_t *__restrict__ tidx, uint32_t *__restrict__ tmask,
-                               T *__restrict__ tval, int32_t *__restrict__ tpan,
-                               int32_t *__restrict__ tvpan)
+                               const int32_t *__restrict__ tptr, const int32_t *__restrict__ ubeg,
+                               int P, int32_t *__restrict__ tidx, uint32_t *__restrict__ tmask,
+                               T *__restrict__ tval, int32_t *__restrict__ uvoff)
 {
     const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -77,25 +77,14 @@ __global__ void mt_emit_kernel(int64_t nseg, const int32_t *__restrict__ ptr,
         e = ptr[s + 1];
     }
     int nxt = p < e ? idx[p] : INT_MAX;
-    int pair = tptr[t];
+    const int pair0 = tptr[t];
+    int pair = pair0;
     int voff = ptr[t * 32];
-    int curb = 0;
     const uint32_t lt = (1u << lane) - 1u;
-    if (lane == 0) {
-        tpan[t * (nb + 1)] = pair;
-        tvpan[t * (nb + 1)] = voff;
-    }
     for (;;) {
         const int j = __reduce_min_sync(0xffffffffu, nxt);
         if (j == INT_MAX) break;
-        const int pb = j / R;
-        while (curb < pb) {
-            ++curb;
-            if (lane == 0) {
-                tpan[t * (nb + 1) + curb] = pair;
-                tvpan[t * (nb + 1) + curb] = voff;
-            }
-        }
+        if (lane == 0 && (pair - pair0) % P == 0) uvoff[ubeg[t] + (pair - pair0) / P] = voff;
         const uint32_t m = __ballot_sync(0xffffffffu, nxt == j);
         if (lane == 0) {
             tidx[pair] = j;
@@ -108,13 +97,6 @@ __global__ void mt_emit_kernel(int64_t nseg, const int32_t *__restrict__ ptr,
         }
         voff += __popc(m);
         ++pair;
-    }
-    while (curb < nb) {
-        ++curb;
-        if (lane == 0) {
-            tpan[t * (nb + 1) + curb] = pair;
-            tvpan[t * (nb + 1) + curb] = voff;
-        }
     }
 }
 
@@ -227,12 +209,13 @@ __device__ __forceinline__ T loss_k(const LossSpec &s, T u, T a, T &L)
 
 // Process `cnt` pairs of a batch (indices / masks in lane q of myj / mym).
 // Every lane runs the same instructions; lanes outside a pair's mask get zero
-// weight, so nothing diverges.
-template <class T, int K, bool XSTEP, bool GRAD, int KIND>
-__device__ __forceinline__ void mt_batch(int cnt, int myj, uint32_t mym, uint32_t &voff,
-                                         const Ring<T> &rg, const T *Ws, int jbase,
-                                         const LossSpec *Ls, const LossSpec &segspec,
-                                         const Vec<T, K> &f, Vec<T, K> &g, T &lsum)
+// weight, so nothing diverges.  FULL: row j of the resident factor; else row
+// q of the batch buffer.
+template <class T, int K, bool XSTEP, bool GRAD, int KIND, bool FULL>
+__device__ __forceinline__ void mt_batch2(int cnt, int myj, uint32_t mym, uint32_t &voff,
+                                          const Ring<T> &rg, const T *rows, const LossSpec *Ls,
+                                          const LossSpec &segspec, const Vec<T, K> &f, Vec<T, K> &g,
+                                          T &lsum)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -244,11 +227,11 @@ __device__ __forceinline__ void mt_batch(int cnt, int myj, uint32_t mym, uint32_
         // lanes outside the mask take a = 1 (inside every loss's domain)
         const T a = act ? rg.at(voff + __popc(m & lt)) : T(1);
         Vec<T, K> w;
-        w.load(Ws + (int64_t)(j - jbase) * K);
+        w.load(rows + (int64_t)(FULL ? j : q) * K);
         const T u = f.dot(w);
         T L;
         T d;
-        if constexpr (XSTEP) d = loss_k<T, KIND>(Ls[j - jbase], u, a, L);
+        if constexpr (XSTEP) d = loss_k<T, KIND>(Ls[j], u, a, L);
         else d = loss_k<T, KIND>(segspec, u, a, L);
         d = act ? d : T(0);
         lsum += act ? L : T(0);
@@ -257,14 +240,40 @@ __device__ __forceinline__ void mt_batch(int cnt, int myj, uint32_t mym, uint32_
     }
 }
 
+// Other-factor rows for one batch of 32 pairs, copied by each lane with
+// cp.async (16-byte pieces) into the warp's batch buffer.
+template <class T, int K>
+__device__ __forceinline__ void gather_rows(T *dst, const T *__restrict__ W, int j, bool valid)
+{
+    constexpr int PIECES = K * (int)sizeof(T) / 16;
+    if (valid) {
+        const char *src = reinterpret_cast<const char *>(W + (int64_t)j * K);
+        char *d = reinterpret_cast<char *>(dst);
+#pragma unroll
+        for (int q = 0; q < PIECES; ++q)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(d + 16 * q)),
+                         "l"(src + 16 * q)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void gather_wait_all()
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+}
+
 // One pass of a warp over pairs [pb, pe) of a tile whose values are global
-// positions [vstart, vend); jbase: first other-index held in shared memory.
-template <class T, int K, bool XSTEP, bool GRAD>
-__device__ __forceinline__ T mt_pass(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K> &g, int pb, int pe,
-                                     int64_t vstart, int64_t vend, int jbase,
-                                     const int32_t *__restrict__ tidx,
-                                     const uint32_t *__restrict__ tmask, const T *__restrict__ tval,
-                                     const T *Ws, const LossSpec *Ls, const LossSpec &segspec)
+// positions [vstart, vend).  FULL: the other factor is in shared memory (Ws,
+// row j at j - jbase); else rows are gathered per batch into gbuf (two
+// buffers of 32 rows).
+template <class T, int K, bool XSTEP, bool GRAD, bool FULL>
+__device__ __forceinline__ T mt_pass2(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K> &g, int pb, int pe,
+                                      int64_t vstart, int64_t vend, const int32_t *__restrict__ tidx,
+                                      const uint32_t *__restrict__ tmask, const T *__restrict__ tval,
+                                      const T *Ws, const T *__restrict__ W, T *gbuf,
+                                      const LossSpec *__restrict__ Lsrc, const LossSpec &segspec)
 {
     const int lane = threadIdx.x & 31;
     T lsum = T(0);
@@ -275,7 +284,8 @@ __device__ __forceinline__ T mt_pass(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K> 
         nj = __ldg(tidx + pb + lane);
         nm = __ldg(tmask + pb + lane);
     }
-    // Y-step: the tile's loss kind is fixed when all its segments share it
+    int cur = 0;
+    if constexpr (!FULL) gather_rows<T, K>(gbuf + lane * K, W, nj, pb + lane < pe);
     int segkind = -1;
     if constexpr (!XSTEP) {
         const int k0 = __shfl_sync(0xffffffffu, segspec.kind, 0);
@@ -285,82 +295,119 @@ __device__ __forceinline__ T mt_pass(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K> 
         const int myj = nj;
         const uint32_t mym = nm;
         const int cnt = min(32, pe - c0);
-        if (c0 + 32 + lane < pe) {  // next batch of pairs
+        const bool more = c0 + 32 + lane < pe;
+        if (more) {  // next batch of pairs
             nj = __ldg(tidx + c0 + 32 + lane);
             nm = __ldg(tmask + c0 + 32 + lane);
+        }
+        const T *rows;
+        if constexpr (FULL) {
+            rows = Ws;
+        } else {
+            gather_wait_all();                       // this batch's rows have landed
+            rows = gbuf + cur * 32 * K;
+            if (c0 + 32 < pe)                          // request the next batch's rows
+                gather_rows<T, K>(gbuf + (cur ^ 1) * 32 * K + lane * K, W, nj, more);
         }
         const uint32_t total = __reduce_add_sync(0xffffffffu, (unsigned)__popc(mym));
         rg.ensure(voff + total);
         int kind = segkind;
+        const LossSpec *Ls = Lsrc;
         if constexpr (XSTEP) {
-            // every lane shuffles (full mask), then lanes past the batch reuse pair 0
             const int j0 = __shfl_sync(0xffffffffu, myj, 0);
-            const int kj = Ls[(lane < cnt ? myj : j0) - jbase].kind;
+            const int kj = Lsrc[lane < cnt ? myj : j0].kind;
             const int k0 = __shfl_sync(0xffffffffu, kj, 0);
             kind = __all_sync(0xffffffffu, kj == k0) ? kj : -1;
         }
+        // rows are addressed by pair position q in the batch when gathered,
+        // by the other-index j when the whole factor is resident
         switch (kind) {
         case kLossQuad:
-            mt_batch<T, K, XSTEP, GRAD, kLossQuad>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            mt_batch2<T, K, XSTEP, GRAD, kLossQuad, FULL>(cnt, myj, mym, voff, rg, rows, Ls, segspec, f, g, lsum);
             break;
         case kLossHuber:
-            mt_batch<T, K, XSTEP, GRAD, kLossHuber>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            mt_batch2<T, K, XSTEP, GRAD, kLossHuber, FULL>(cnt, myj, mym, voff, rg, rows, Ls, segspec, f, g, lsum);
             break;
         case kLossHinge:
-            mt_batch<T, K, XSTEP, GRAD, kLossHinge>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            mt_batch2<T, K, XSTEP, GRAD, kLossHinge, FULL>(cnt, myj, mym, voff, rg, rows, Ls, segspec, f, g, lsum);
             break;
         case kLossLogistic:
-            mt_batch<T, K, XSTEP, GRAD, kLossLogistic>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            mt_batch2<T, K, XSTEP, GRAD, kLossLogistic, FULL>(cnt, myj, mym, voff, rg, rows, Ls, segspec, f, g, lsum);
             break;
         case kLossOrdinal:
-            mt_batch<T, K, XSTEP, GRAD, kLossOrdinal>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            mt_batch2<T, K, XSTEP, GRAD, kLossOrdinal, FULL>(cnt, myj, mym, voff, rg, rows, Ls, segspec, f, g, lsum);
             break;
         default:
-            mt_batch<T, K, XSTEP, GRAD, -1>(cnt, myj, mym, voff, rg, Ws, jbase, Ls, segspec, f, g, lsum);
+            mt_batch2<T, K, XSTEP, GRAD, -1, FULL>(cnt, myj, mym, voff, rg, rows, Ls, segspec, f, g, lsum);
         }
         rg.release(voff);
+        cur ^= 1;
     }
+    if constexpr (!FULL) gather_wait_all();
     rg.drain();
     return lsum;
 }
 
-// Fused masked-tile half-step: the whole other factor (and for the X-step its
-// loss table) in shared memory; one warp per tile runs gradient, prox,
-// re-evaluation and decision for its 32 segments.
-template <class T, int K, bool XSTEP>
+// Modes of the masked kernel.
+constexpr int kMtFused = 0;  // unit = whole tile: gradient, prox, re-evaluation, decision
+constexpr int kMtGrad = 1;   // unit = part of a tile: partial gradient and loss at F
+constexpr int kMtLoss = 2;   // unit = part of a tile: partial loss at F (the candidate)
+
+// Dynamic shared memory: FULL: the other factor (nother x K) and, for the
+// X-step, its loss table; then per warp a value ring and (gather) two batch
+// buffers of 32 rows.
+template <class T, int K, bool XSTEP, bool FULL, int MODE>
 __global__ void __launch_bounds__(kMaskedWarps * 32, 1)
-mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *__restrict__ tvpan,
-                const int32_t *__restrict__ tidx, const uint32_t *__restrict__ tmask,
-                const T *__restrict__ tval, T *__restrict__ F, const T *__restrict__ W,
-                int64_t nother, int k, T *__restrict__ alpha, const LossSpec *__restrict__ loss,
-                int rk, T rw, double *__restrict__ kept_obj, double *__restrict__ kept_reg,
-                int32_t *__restrict__ accepted, int *__restrict__ err)
+mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile,
+          const int32_t *__restrict__ tptr, const int32_t *__restrict__ uvoff,
+          const int32_t *__restrict__ ubeg, const int32_t *__restrict__ segptr,
+          const int32_t *__restrict__ tidx, const uint32_t *__restrict__ tmask,
+          const T *__restrict__ tval, T *__restrict__ F, const T *__restrict__ W, int64_t nother,
+          int k, T *__restrict__ alpha, const LossSpec *__restrict__ loss, int rk, T rw,
+          double *__restrict__ kept_obj, double *__restrict__ kept_reg,
+          int32_t *__restrict__ accepted, T *__restrict__ part_grad, double *__restrict__ part_loss,
+          int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ uint64_t bar_panel;
     __shared__ uint64_t bar_ring[kMaskedWarps][kRingSlots];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    size_t off = 0;
     T *Ws = reinterpret_cast<T *>(dsm);
-    size_t off = align16((size_t)nother * K * sizeof(T));
-    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
-    if constexpr (XSTEP) off += (size_t)nother * sizeof(LossSpec);
-    T *ring = reinterpret_cast<T *>(dsm + off) + (size_t)wid * Ring<T>::N;
+    LossSpec *Ls = nullptr;
+    if constexpr (FULL) {
+        off = align16((size_t)nother * K * sizeof(T));
+        if constexpr (XSTEP) {
+            Ls = reinterpret_cast<LossSpec *>(dsm + off);
+            off += (size_t)nother * sizeof(LossSpec);
+        }
+    }
+    constexpr size_t kWarpBytes = (size_t)kRingSlots * kRingBytes + (FULL ? 0 : 2 * 32 * K * sizeof(T));
+    unsigned char *wbase = dsm + off + (size_t)wid * kWarpBytes;
+    T *ring = reinterpret_cast<T *>(wbase);
+    T *gbuf = reinterpret_cast<T *>(wbase + (size_t)kRingSlots * kRingBytes);
     if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
     if (lane < kRingSlots) mbar_init(&bar_ring[wid][lane], 1);
     __syncthreads();
-    if constexpr (XSTEP) {
-        for (int64_t q = threadIdx.x; q < nother; q += blockDim.x) Ls[q] = loss[q];
+    if constexpr (FULL) {
+        if constexpr (XSTEP) {
+            for (int64_t q = threadIdx.x; q < nother; q += blockDim.x) Ls[q] = loss[q];
+        }
+        if (!stage_panel<T>(Ws, W, 0, (int)nother, k, K, &bar_panel, 0, err)) return;
     }
-    if (!stage_panel<T>(Ws, W, 0, (int)nother, k, K, &bar_panel, 0, err)) return;
+    const LossSpec *Lsrc = FULL ? Ls : loss;
     Ring<T> vs;
     vs.init(ring, &bar_ring[wid][0]);
-    const int64_t ntiles = (nseg + 31) / 32;
-    for (int64_t t = (int64_t)blockIdx.x * kMaskedWarps + wid; t < ntiles;
-         t += (int64_t)gridDim.x * kMaskedWarps) {
+    for (int64_t u = (int64_t)blockIdx.x * nwarps + wid; u < nunits; u += (int64_t)gridDim.x * nwarps) {
+        const int64_t t = utile[u];
+        const int q = (int)(u - ubeg[t]);
+        const int pb = tptr[t] + q * P;
+        const int pe = min(tptr[t + 1], pb + P);
+        const int64_t vb = uvoff[u];
+        const int64_t tend = t * 32 + 32 < nseg ? t * 32 + 32 : nseg;
+        const int64_t ve = (u + 1 < ubeg[t + 1]) ? uvoff[u + 1] : segptr[tend];
         const int64_t s = t * 32 + lane;
         const bool live = s < nseg;
-        const int pb = tpan[2 * t], pe = tpan[2 * t + 1];
-        const int64_t vb = tvpan[2 * t], ve = tvpan[2 * t + 1];
         Vec<T, K> f, g;
         if (live) f.load_masked(F + s * k, k);
         else f.zero();
@@ -369,128 +416,148 @@ mt_fused_kernel(int64_t nseg, const int32_t *__restrict__ tpan, const int32_t *_
         if constexpr (!XSTEP) {
             if (live) sp = loss[s];
         }
-        const T l1 = mt_pass<T, K, XSTEP, true>(vs, f, g, pb, pe, vb, ve, 0, tidx, tmask, tval, Ws,
-                                                Ls, sp);
-        const T al = live ? alpha[s] : T(0);
-        Vec<T, K> fp;
-        double rold = 0.0, rnew = 0.0;
-        {
-            T tmp[K];
+        if constexpr (MODE == kMtFused) {
+            const T l1 = mt_pass2<T, K, XSTEP, true, FULL>(vs, f, g, pb, pe, vb, ve, tidx, tmask, tval,
+                                                          Ws, W, gbuf, Lsrc, sp);
+            const T al = live ? alpha[s] : T(0);
+            Vec<T, K> fp;
+            double rold = 0.0, rnew = 0.0;
+            {
+                T tmp[K];
 #pragma unroll
-            for (int c = 0; c < K; ++c) {
-                const T x = f.get(c);
-                const T xp = c < k ? prox1<T>(rk, rw, al, x - al * g.get(c)) : T(0);
-                tmp[c] = xp;
-                if (c < k) {
-                    rold += reg1<T>(rk, rw, x);
-                    rnew += reg1<T>(rk, rw, xp);
+                for (int c = 0; c < K; ++c) {
+                    const T x = f.get(c);
+                    const T xp = c < k ? prox1<T>(rk, rw, al, x - al * g.get(c)) : T(0);
+                    tmp[c] = xp;
+                    if (c < k) {
+                        rold += reg1<T>(rk, rw, x);
+                        rnew += reg1<T>(rk, rw, xp);
+                    }
                 }
+                fp.load_masked(tmp, K);
             }
-            fp.load_masked(tmp, K);
-        }
-        Vec<T, K> unused;
-        const T l2 = mt_pass<T, K, XSTEP, false>(vs, fp, unused, pb, pe, vb, ve, 0, tidx, tmask,
-                                                 tval, Ws, Ls, sp);
-        if (!vs.ok) {
-            if (lane == 0) atomicOr(err, 1);
-            return;
-        }
-        if (live) {
-            const double fold = (double)l1 + rold;
-            const double fnew = (double)l2 + rnew;
-            const bool acc = fnew <= fold;
-            if (acc) {
+            Vec<T, K> unused;
+            const T l2 = mt_pass2<T, K, XSTEP, false, FULL>(vs, fp, unused, pb, pe, vb, ve, tidx, tmask,
+                                                            tval, Ws, W, gbuf, Lsrc, sp);
+            if (!vs.ok) {
+                if (lane == 0) atomicOr(err, 1);
+                return;
+            }
+            if (live) {
+                const double fold = (double)l1 + rold;
+                const double fnew = (double)l2 + rnew;
+                const bool acc = fnew <= fold;
+                if (acc) {
 #pragma unroll
-                for (int c = 0; c < K; ++c)
-                    if (c < k) F[s * k + c] = fp.get(c);
+                    for (int c = 0; c < K; ++c)
+                        if (c < k) F[s * k + c] = fp.get(c);
+                }
+                alpha[s] = al * (acc ? T(1.05) : T(0.7));
+                kept_obj[s] = acc ? fnew : fold;
+                kept_reg[s] = acc ? rnew : rold;
+                accepted[s] = acc ? 1 : 0;
             }
-            alpha[s] = al * (acc ? T(1.05) : T(0.7));
-            kept_obj[s] = acc ? fnew : fold;
-            kept_reg[s] = acc ? rnew : rold;
-            accepted[s] = acc ? 1 : 0;
+        } else {
+            const T l = mt_pass2<T, K, XSTEP, MODE == kMtGrad, FULL>(vs, f, g, pb, pe, vb, ve, tidx, tmask,
+                                                                    tval, Ws, W, gbuf, Lsrc, sp);
+            if (!vs.ok) {
+                if (lane == 0) atomicOr(err, 1);
+                return;
+            }
+            const int64_t slot = u * 32 + lane;
+            if constexpr (MODE == kMtGrad) {
+#pragma unroll
+                for (int c = 0; c < K; ++c) part_grad[slot * K + c] = g.get(c);
+            }
+            part_loss[slot] = (double)l;
         }
     }
 }
 
-// Panel pass of the masked-tile form: unit = (panel b, group of tiles); the
-// CTA stages the panel, each warp reduces its tiles' pairs in that panel into
-// per-(panel, segment) partials (GRAD: gradient and loss at F; else loss).
-template <class T, int K, bool XSTEP, bool GRAD>
-__global__ void __launch_bounds__(kMaskedWarps * 32, 1)
-mt_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
-               const int32_t *__restrict__ tpan, const int32_t *__restrict__ tvpan,
-               const int32_t *__restrict__ tidx, const uint32_t *__restrict__ tmask,
-               const T *__restrict__ tval, const T *__restrict__ F, const T *__restrict__ W, int k,
-               const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
-               double *__restrict__ part_loss, int *__restrict__ err)
+// Per-segment prox / decide over unit partials: segment s of tile t has
+// partials at (u * 32 + s % 32) for the units u of t, summed in order.
+template <class T, int K>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+unit_prox_kernel(int64_t nseg, const int32_t *__restrict__ ubeg, const T *__restrict__ part_grad,
+                 const double *__restrict__ part_loss, const T *__restrict__ F,
+                 const T *__restrict__ alpha, int k, int rkind, T rw, T *__restrict__ cand,
+                 double *__restrict__ f_old, double *__restrict__ r_old, double *__restrict__ r_new)
 {
-    extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ uint64_t bar_panel;
-    __shared__ uint64_t bar_ring[kMaskedWarps][kRingSlots];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    T *Ws = reinterpret_cast<T *>(dsm);
-    size_t off = align16((size_t)R * K * sizeof(T));
-    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
-    if constexpr (XSTEP) off += (size_t)R * sizeof(LossSpec);
-    T *ring = reinterpret_cast<T *>(dsm + off) + (size_t)wid * Ring<T>::N;
-    if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
-    if (lane < kRingSlots) mbar_init(&bar_ring[wid][lane], 1);
-    __syncthreads();
-    Ring<T> vs;
-    vs.init(ring, &bar_ring[wid][0]);
-    const int64_t ntiles = (nseg + 31) / 32;
-    const int64_t tiles_per = (ntiles + ngroups - 1) / ngroups;
-    const int64_t nunits = (int64_t)nb * ngroups;
-    unsigned pphase = 0;
-    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-        const int b = (int)(u / ngroups);
-        const int64_t grp = u % ngroups;
-        const int64_t r0 = (int64_t)b * R;
-        const int rows = (int)((r0 + R <= nother) ? R : nother - r0);
-        __syncthreads();
-        if constexpr (XSTEP) {
-            for (int q = threadIdx.x; q < rows; q += blockDim.x) Ls[q] = loss[r0 + q];
-        }
-        if (!stage_panel<T>(Ws, W, r0, rows, k, K, &bar_panel, pphase, err)) return;
-        pphase ^= 1u;
-        const int64_t t0 = grp * tiles_per;
-        const int64_t t1 = t0 + tiles_per < ntiles ? t0 + tiles_per : ntiles;
-        for (int64_t t = t0 + wid; t < t1; t += kMaskedWarps) {
-            const int64_t s = t * 32 + lane;
-            const bool live = s < nseg;
-            const int64_t pi = t * (nb + 1) + b;
-            const int pb = tpan[pi], pe = tpan[pi + 1];
-            const int64_t vb = tvpan[pi], ve = tvpan[pi + 1];
-            Vec<T, K> f, g;
-            if (live) f.load_masked(F + s * k, k);
-            else f.zero();
-            g.zero();
-            LossSpec sp{};
-            if constexpr (!XSTEP) {
-                if (live) sp = loss[s];
-            }
-            const T l = mt_pass<T, K, XSTEP, GRAD>(vs, f, g, pb, pe, vb, ve, (int)r0, tidx, tmask,
-                                                   tval, Ws, Ls, sp);
-            if (live) {
-                const int64_t slot = (int64_t)b * nseg + s;
-                if constexpr (GRAD) {
-#pragma unroll
-                    for (int c = 0; c < K; ++c) part_grad[slot * K + c] = g.get(c);
-                }
-                part_loss[slot] = (double)l;
-            }
-        }
-        if (__syncthreads_or(!vs.ok)) {
-            if (threadIdx.x == 0) atomicOr(err, 1);
-            return;
-        }
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (s >= nseg) return;
+    const int64_t t = s / 32, l = s % 32;
+    const int u0 = ubeg[t], u1 = ubeg[t + 1];
+    const T al = alpha[s];
+    double ro = 0.0, rn = 0.0;
+    for (int c = lane; c < k; c += 32) {
+        T g = T(0);
+        for (int u = u0; u < u1; ++u) g += part_grad[((int64_t)u * 32 + l) * K + c];
+        const T x = F[s * k + c];
+        const T xp = prox1<T>(rkind, rw, al, x - al * g);
+        cand[s * k + c] = xp;
+        ro += reg1<T>(rkind, rw, x);
+        rn += reg1<T>(rkind, rw, xp);
+    }
+    ro = warp_sum(ro);
+    rn = warp_sum(rn);
+    double ls = 0.0;
+    for (int u = u0 + lane; u < u1; u += 32) ls += part_loss[(int64_t)u * 32 + l];
+    ls = warp_sum(ls);
+    if (lane == 0) {
+        f_old[s] = ls + ro;
+        r_old[s] = ro;
+        r_new[s] = rn;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+unit_decide_kernel(int64_t nseg, const int32_t *__restrict__ ubeg,
+                   const double *__restrict__ part_loss_new, const double *__restrict__ f_old,
+                   const double *__restrict__ r_old, const double *__restrict__ r_new,
+                   const T *__restrict__ cand, T *__restrict__ F, T *__restrict__ alpha, int k,
+                   double *__restrict__ kept_obj, double *__restrict__ kept_reg,
+                   int32_t *__restrict__ accepted)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (s >= nseg) return;
+    const int64_t t = s / 32, l = s % 32;
+    double ls = 0.0;
+    for (int u = ubeg[t] + lane; u < ubeg[t + 1]; u += 32) ls += part_loss_new[(int64_t)u * 32 + l];
+    const double fn = warp_sum(ls) + r_new[s];
+    const double fo = f_old[s];
+    const bool acc = fn <= fo;
+    if (acc)
+        for (int c = lane; c < k; c += 32) F[s * k + c] = cand[s * k + c];
+    if (lane == 0) {
+        alpha[s] = alpha[s] * (acc ? T(1.05) : T(0.7));
+        kept_obj[s] = acc ? fn : fo;
+        kept_reg[s] = acc ? r_new[s] : r_old[s];
+        accepted[s] = acc ? 1 : 0;
     }
 }
 
 // ---------------------------------------------------------------- launchers
 
-template <class T, int K, bool XSTEP>
-cudaError_t mt_half_K(glrm_s *h)
+template <class T, int K, bool XSTEP, bool FULL, int MODE>
+cudaError_t launch_mt(glrm_s *h, const Orient &o, T *F, const T *W, int64_t nother, T *alpha, int rk,
+                      T rw, double *kobj, double *kreg, int32_t *acc, T *pg, double *pl)
+{
+    auto kern = mt_kernel<T, K, XSTEP, FULL, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)o.smem_bytes);
+    if (e != cudaSuccess) return e;
+    kern<<<o.grid, o.warps * 32, o.smem_bytes, h->stream>>>(
+        o.nseg, o.nunits, o.P, o.utile, o.tptr, o.uvoff, o.ubeg, o.ptr, o.tidx, o.tmask,
+        (const T *)o.tval, F, W, nother, h->k, alpha, h->loss_dev, rk, rw, kobj, kreg, acc, pg, pl,
+        h->s.err);
+    return cudaGetLastError();
+}
+
+template <class T, int K, bool XSTEP, bool FULL>
+cudaError_t mt_half_src(glrm_s *h)
 {
     const Orient &o = XSTEP ? h->csr : h->csc;
     T *F = (T *)(XSTEP ? h->X : h->Yt);
@@ -504,49 +571,42 @@ cudaError_t mt_half_K(glrm_s *h)
     double *kreg = XSTEP ? s.kept_reg_x : s.kept_reg_y;
     int32_t *acc = XSTEP ? s.acc_x : s.acc_y;
     cudaError_t e;
-    if (o.nb == 1) {
-        auto kern = mt_fused_kernel<T, K, XSTEP>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_bytes);
-        if (e != cudaSuccess) return e;
+    if (o.nunits == (o.nseg + 31) / 32) {  // one unit per tile: fused
         tmark(h, XSTEP ? "masked_fused_x" : "masked_fused_y");
-        kern<<<o.grid, kMaskedWarps * 32, o.smem_bytes, h->stream>>>(
-            o.nseg, o.tpan, o.tvpan, o.tidx, o.tmask, (const T *)o.tval, F, W, nother, h->k, alpha,
-            h->loss_dev, rk, rw, kobj, kreg, acc, h->s.err);
+        e = launch_mt<T, K, XSTEP, FULL, kMtFused>(h, o, F, W, nother, alpha, rk, rw, kobj, kreg, acc,
+                                                   nullptr, nullptr);
         tmark(h, nullptr);
         h->launches += 1;
-        return cudaGetLastError();
+        return e;
     }
-    auto pass_g = mt_pass_kernel<T, K, XSTEP, true>;
-    auto pass_l = mt_pass_kernel<T, K, XSTEP, false>;
-    if ((e = cudaFuncSetAttribute(pass_g, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)o.smem_bytes)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(pass_l, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)o.smem_bytes)) != cudaSuccess)
-        return e;
     tmark(h, XSTEP ? "masked_grad_x" : "masked_grad_y");
-    pass_g<<<o.grid, kMaskedWarps * 32, o.smem_bytes, h->stream>>>(
-        o.nseg, o.nb, o.R, o.ngroups, nother, o.tpan, o.tvpan, o.tidx, o.tmask, (const T *)o.tval,
-        F, W, h->k, h->loss_dev, (T *)s.part_grad, s.part_loss, h->s.err);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_mt<T, K, XSTEP, FULL, kMtGrad>(h, o, F, W, nother, alpha, rk, rw, kobj, kreg, acc,
+                                              (T *)s.part_grad, s.part_loss);
+    if (e != cudaSuccess) return e;
     const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
     tmark(h, XSTEP ? "masked_prox_x" : "masked_prox_y");
-    blocked_prox_kernel<T, K><<<nbs, kWarpsPerBlock * 32, 0, h->stream>>>(
-        o.nseg, o.nb, (const T *)s.part_grad, s.part_loss, F, alpha, h->k, rk, rw, (T *)s.cand,
+    unit_prox_kernel<T, K><<<nbs, kWarpsPerBlock * 32, 0, h->stream>>>(
+        o.nseg, o.ubeg, (const T *)s.part_grad, s.part_loss, F, alpha, h->k, rk, rw, (T *)s.cand,
         s.f_old, s.r_old, s.r_new);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, XSTEP ? "masked_loss_x" : "masked_loss_y");
-    pass_l<<<o.grid, kMaskedWarps * 32, o.smem_bytes, h->stream>>>(
-        o.nseg, o.nb, o.R, o.ngroups, nother, o.tpan, o.tvpan, o.tidx, o.tmask, (const T *)o.tval,
-        (const T *)s.cand, W, h->k, h->loss_dev, nullptr, s.part_loss2, h->s.err);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_mt<T, K, XSTEP, FULL, kMtLoss>(h, o, (T *)s.cand, W, nother, alpha, rk, rw, kobj, kreg,
+                                              acc, nullptr, s.part_loss2);
+    if (e != cudaSuccess) return e;
     tmark(h, XSTEP ? "masked_decide_x" : "masked_decide_y");
-    blocked_decide_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, h->stream>>>(
-        o.nseg, o.nb, s.part_loss2, s.f_old, s.r_old, s.r_new, (const T *)s.cand, F, alpha, h->k,
+    unit_decide_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, h->stream>>>(
+        o.nseg, o.ubeg, s.part_loss2, s.f_old, s.r_old, s.r_new, (const T *)s.cand, F, alpha, h->k,
         kobj, kreg, acc);
     tmark(h, nullptr);
     h->launches += 4;
     return cudaGetLastError();
+}
+
+template <class T, int K, bool XSTEP>
+cudaError_t mt_half_K(glrm_s *h)
+{
+    const Orient &o = XSTEP ? h->csr : h->csc;
+    return o.full ? mt_half_src<T, K, XSTEP, true>(h) : mt_half_src<T, K, XSTEP, false>(h);
 }
 
 template <class T, bool XSTEP>
@@ -569,15 +629,15 @@ cudaError_t Engine<T>::masked_half_step(glrm_s *h, bool xstep)
     return xstep ? mt_half<T, true>(h) : mt_half<T, false>(h);
 }
 
-// Build the masked tiles of one orientation (the pair counts are already in
-// o.tptr as an exclusive scan).
+// Build the masked tiles of one orientation (tptr holds the exclusive scan of
+// the pair counts, ubeg the first unit of each tile).
 template <class T>
 cudaError_t mt_build(const Orient &o, cudaStream_t st)
 {
     const int64_t ntiles = (o.nseg + 31) / 32;
     mt_emit_kernel<T><<<blocks_for(ntiles, 8), 256, 0, st>>>(o.nseg, o.ptr, o.idx, (const T *)o.val,
-                                                             o.tptr, o.nb, o.R, o.tidx, o.tmask,
-                                                             (T *)o.tval, o.tpan, o.tvpan);
+                                                             o.tptr, o.ubeg, o.P, o.tidx, o.tmask,
+                                                             (T *)o.tval, o.uvoff);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ GLRM_LOSS_QUAD, GLRM_LOSS_HUBER, GLRM_LOSS_HINGE, GLRM_LOSS_LOGISTIC, GLRM_LOSS_
 GLRM_REG_ZERO, GLRM_REG_QUAD, GLRM_REG_L1, GLRM_REG_NONNEG = range(4)
 GLRM_FP64, GLRM_FP32, GLRM_BF16 = 0, 1, 2
 GLRM_PATH_AUTO, GLRM_PATH_CHUNKED, GLRM_PATH_FUSED, GLRM_PATH_BLOCKED = 0, 1, 2, 3
-GLRM_PATH_MASKED, GLRM_PATH_MASKED_PANELS = 4, 5
+GLRM_PATH_MASKED, GLRM_PATH_MASKED_SPLIT = 4, 5
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libglrm.so")
 

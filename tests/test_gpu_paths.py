@@ -7,6 +7,8 @@ import torch
 
 from paper_1410_0342_gb300 import workloads as W
 
+from gpu_parity import synced_sweeps
+
 pytestmark = pytest.mark.gpu
 
 RZ, RQ, RL1, RNN = 0, 1, 2, 3
@@ -40,11 +42,8 @@ def test_paths_match_oracle_fp32(G, oracle_mod, paths, k):
     got = G.glrm_get_path(g.h)
     for want, have in zip(paths, got):
         # a masked request runs panel by panel when the factor does not fit whole
-        assert have == want or (want == G.GLRM_PATH_MASKED and have == G.GLRM_PATH_MASKED_PANELS)
-    hist = g.sweep(15)
-    X, Yt, ax, ay, ohist, oacc = oracle_hist(oracle_mod, t, 15)
-    rel = np.abs(hist - ohist) / np.abs(ohist)
-    assert rel.max() < 1e-4, rel
+        assert have == want or (want == G.GLRM_PATH_MASKED and have == G.GLRM_PATH_MASKED_SPLIT)
+    synced_sweeps(g, oracle_mod, t, 8)
 
 
 @pytest.mark.parametrize("paths", [(1, 1), (2, 2), (3, 3), (4, 4), (5, 5)])
@@ -77,7 +76,7 @@ def test_auto_path_choice(G):
     # dense: masked tiles; Y^T fits whole, X only panel by panel
     t = W.small_mixed(m=6000, n=64, k=16, p_obs=0.7, seed=3)
     g = G.GLRM.from_table(t)
-    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_MASKED, G.GLRM_PATH_MASKED_PANELS)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_MASKED, G.GLRM_PATH_MASKED_SPLIT)
     # sparse with a large X: chunked Y-step
     t2 = W.small_mixed(m=60000, n=3000, k=8, p_obs=0.002, seed=4)
     g2 = G.GLRM.from_table(t2)
@@ -94,6 +93,4 @@ def test_auto_path_choice(G):
 def test_sparse_chunked_matches_oracle(G, oracle_mod):
     t = W.small_mixed(m=20000, n=900, k=8, p_obs=0.004, seed=6)
     g = G.GLRM.from_table(t)
-    hist = g.sweep(10)
-    *_, ohist, _ = oracle_hist(oracle_mod, t, 10)
-    assert (np.abs(hist - ohist) / np.abs(ohist)).max() < 1e-4
+    synced_sweeps(g, oracle_mod, t, 6)

@@ -1,15 +1,20 @@
 """GPU parity of the proximal-gradient sweep, objective, gradient, imputation
 and ALS against the FP64 oracle, on the same seeded inputs.
 
-Tolerances: objectives after a fixed number of sweeps within 1e-4 relative
-on the FP32 path (1e-9 on the FP64 path); gradients within 1e-5 relative
-(norm-wise) on FP32; Omega handling and decoded Boolean / ordinal values
-bit-exact."""
+Tolerances: FP64 path: objectives after a fixed number of sweeps within 1e-9
+relative and identical accept counts.  FP32 path: each sweep from a state
+shared with the oracle within 1e-5 relative (near-tie accept / reject flips
+allowed on at most 1% of rows, see gpu_parity.py); objectives after a fixed
+number of free-running sweeps within 1e-4 on tables large enough that a flip
+does not move the total.  Gradients within 1e-5 relative (norm-wise) on FP32;
+Omega handling and decoded Boolean / ordinal values bit-exact."""
 import numpy as np
 import pytest
 import torch
 
 from paper_1410_0342_gb300 import workloads as W
+
+from gpu_parity import synced_sweeps
 
 pytestmark = pytest.mark.gpu
 
@@ -65,9 +70,16 @@ def test_fp64_reaches_qpca_closed_form(G):
 def test_fp32_mixed_matches_oracle(G, oracle_mod, k):
     t = W.small_mixed(m=211, n=57, k=k, seed=100 + k)
     g = G.GLRM.from_table(t)
-    hist = g.sweep(25)
-    *_, ohist, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 25)
-    assert np.all(np.isfinite(hist))
+    synced_sweeps(g, oracle_mod, t, 12)
+
+
+def test_fp32_free_running_objective(G, oracle_mod):
+    """20 free-running sweeps on a 20,000 x 300 mixed table: objectives within
+    1e-4 of the oracle's."""
+    t = W.small_mixed(m=20000, n=300, k=20, p_obs=0.5, seed=77)
+    g = G.GLRM.from_table(t)
+    hist = g.sweep(20)
+    *_, ohist, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 20)
     assert relerr(hist, ohist).max() < 1e-4
 
 
@@ -83,9 +95,7 @@ def test_fp32_multichunk_segments(G, oracle_mod):
     keep &= t.colidx != 5
     t2 = _subset(t, keep)
     g = G.GLRM.from_table(t2)
-    hist = g.sweep(20)
-    *_, ohist, oacc = oracle_problem(oracle_mod, t2).proxgrad(t2.X0, t2.Yt0, 20)
-    assert relerr(hist, ohist).max() < 1e-4
+    synced_sweeps(g, oracle_mod, t2, 10)
 
 
 def _subset(t, keep):
@@ -182,7 +192,8 @@ def test_als_matches_oracle(G, oracle_mod):
     hist = g.als_sweep(30)
     X, Yt, ohist = oracle_problem(oracle_mod, t).als(t.X0, t.Yt0, 0.1, 30)
     assert relerr(hist, ohist).max() < 1e-9
-    # missing data, FP32 Gram accumulation, k = 16
+    # missing data, FP32 Gram accumulation, k = 16 (ALS has no accept / reject
+    # branch, so free-running trajectories stay together)
     t2 = W.batch_instance(0, m_range=(400, 400), n_range=(120, 120), ks=(16,))
     g2 = G.GLRM.from_table(t2)
     h2 = g2.als_sweep(10)
@@ -258,9 +269,7 @@ def test_host_entry_points(G, oracle_mod):
                              t.val.astype(np.float32), t.colptr.astype(np.int32), t.rowidx,
                              t.cval.astype(np.float32))
     G.glrm_set_factors_host(g.h, t.X0.astype(np.float32), t.Yt0.astype(np.float32))
-    hist = g.sweep(10)
-    *_, ohist, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 10)
-    assert relerr(hist, ohist).max() < 1e-4
+    synced_sweeps(g, oracle_mod, t, 5)
     X = np.empty((t.m, t.k), np.float32)
     Y = np.empty((t.n, t.k), np.float32)
     G.glrm_get_factors_host(g.h, X, Y)
