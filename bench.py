@@ -159,21 +159,34 @@ def ncu_traffic(kernel: str):
 
 def algorithmic_bytes(name: str, t: W.Table, k: int) -> float:
     """Bytes a kernel must move at minimum per launch (FP32 values, int32
-    indices): each observed entry's index and value once, each factor row it
-    reads or writes once, and its per-chunk / per-segment partials."""
+    indices): every observed entry's index and value once, every factor row it
+    reads once and every row it writes once.  A fused half-step reads the
+    entries once and both factors, and writes the updated factor and step
+    sizes; a gradient or loss pass reads the entries and both factors; prox /
+    decide kernels touch per-segment state only."""
     nnz, m, n = t.nnz, t.m, t.n
     fb = 4 * k
     x = name.endswith("_x")
     nseg, other = (m, n) if x else (n, m)
-    nchunks = nnz / 1024 + nseg  # upper bound on chunks, partials are small
-    if name.startswith("pass_grad"):
-        return nnz * 8 + (nseg + other) * fb + nchunks * (fb + 8)
-    if name.startswith("pass_loss"):
-        return nnz * 8 + (nseg + other) * fb + nchunks * 8
-    if name.startswith("prox"):
-        return nchunks * (fb + 8) + nseg * (2 * fb + 4 + 24)
-    if name.startswith("decide"):
-        return nchunks * 8 + nseg * (2 * fb + 4 + 48)
+    if "fused" in name:
+        return nnz * 8 + (nseg + other) * fb + nseg * (fb + 4)
+    if "grad" in name or "loss" in name:
+        return nnz * 8 + (nseg + other) * fb
+    if "prox" in name or "decide" in name:
+        return nseg * (2 * fb + 4)
+    return 0.0
+
+
+def algorithmic_flops(name: str, t: W.Table, k: int) -> float:
+    """FP32 multiply-adds x 2 the method needs per launch: per observed entry
+    a dot product (2k), the gradient update (2k) and, after the prox, the
+    re-evaluating dot product (2k)."""
+    if "fused" in name:
+        return t.nnz * 6.0 * k
+    if "grad" in name:
+        return t.nnz * 4.0 * k
+    if "loss" in name:
+        return t.nnz * 2.0 * k
     return 0.0
 
 
@@ -293,12 +306,18 @@ def run_glrm(args, world, rank, local):
     abytes = algorithmic_bytes(tname, t, t.k)
     achieved = abytes / avg_s / 1e9
     traffic = ncu_traffic(tname)
+    # the FP32 pipe: 152 SMs x 128 lanes x 2 flop per FMA x the sampled SM clock
+    clk_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+    aflops = algorithmic_flops(tname, t, t.k)
     roofline = {"bound": "hbm", "kernel": tname, "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_s * 1e6,
-                "peak_source": peak_src,
-                "share_of_step": tms / ms}
+                "peak_source": peak_src, "share_of_step": tms / ms,
+                "alu": {"achieved_tflops": aflops / avg_s / 1e12, "peak_tflops": fp32_peak,
+                        "frac": aflops / avg_s / 1e12 / fp32_peak,
+                        "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled SM clock"}}
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / ms}
                for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
 

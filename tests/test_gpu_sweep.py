@@ -74,9 +74,11 @@ def test_fp32_mixed_matches_oracle(G, oracle_mod, k):
 
 
 def test_fp32_free_running_objective(G, oracle_mod):
-    """20 free-running sweeps on a 20,000 x 300 mixed table: objectives within
-    1e-4 of the oracle's."""
-    t = W.small_mixed(m=20000, n=300, k=20, p_obs=0.5, seed=77)
+    """20 free-running sweeps of quadratic-loss matrix completion (20,000 x
+    400, 40 entries per row, k = 16): objectives within 1e-4 of the oracle's.
+    (With piecewise-linear losses the FP32 and FP64 trajectories part after
+    near-tie flips; those tables are checked sweep by sweep instead.)"""
+    t = W.completion(m=20000, n=400, k=16, per_row=40, seed=78)
     g = G.GLRM.from_table(t)
     hist = g.sweep(20)
     *_, ohist, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 20)
