@@ -266,6 +266,35 @@ int glrm_timing_read(glrm_t h, int32_t max_kernels, char *names_host, double *ms
                      int64_t *launches_host, int32_t *count_host);
 int glrm_launch_count(glrm_t h, int64_t *count_host);
 
+/* Objective without any device allocation, for callers that cannot call
+ * cudaMalloc where they need it: code recording into a CUDA graph capture (an
+ * allocation inside a capture is not allowed), hosts whose device memory all
+ * belongs to their own pool, loops that must not touch the allocator.  The
+ * paper has no counterpart: this is the value glrm_objective_at computes
+ * (FP32 model, per-row loss sums plus regularisers, reduced in FP64), for
+ * caller-owned data and without a handle.
+ *
+ * Inputs (device pointers, caller-owned): CSR rowptr (m+1), colidx, val (FP32)
+ * of Omega; col_loss_dev: n glrm_loss descriptors in device memory, 16-byte
+ * aligned; factors X_dev (m x k) and Yt_dev (n x k), FP32 row-major.  Output:
+ * the objective in the device double out_dev.  Work is enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream); the call does not
+ * synchronise.  A column index outside [0, n) turns the result into NaN.
+ *
+ * Scratch: a file-scope device array of GLRM_NOALLOC_MAX_TERMS doubles
+ * (8 MiB) inside the library, held by every GPU that loads the library until
+ * the process exits; m + n must not exceed GLRM_NOALLOC_MAX_TERMS
+ * (GLRM_ERR_RANGE otherwise, nothing launched).  The first call on a device
+ * looks up the array's device address on that device, so make that first call
+ * outside any stream capture.  Every call overwrites the slots it uses; calls
+ * that overlap on the GPU share the array and race.  Limits: 1 <= k <= 64. */
+#define GLRM_NOALLOC_MAX_TERMS (1 << 20)
+int glrm_objective_noalloc(int64_t m, int64_t n, int32_t k, const int32_t *csr_rowptr_dev,
+                           const int32_t *csr_colidx_dev, const float *csr_val_dev,
+                           const glrm_loss *col_loss_dev, int32_t rx_kind, double rx_weight,
+                           int32_t ry_kind, double ry_weight, const float *X_dev,
+                           const float *Yt_dev, double *out_dev, void *stream);
+
 /* Per-handle message for the last error (empty string when none). */
 const char *glrm_last_error(glrm_t h);
 

@@ -64,6 +64,7 @@ def _load():
         "glrm_launch_count": [p, p],
         "glrm_set_path": [p, i32, i32],
         "glrm_get_path": [p, p],
+        "glrm_objective_noalloc": [i64, i64, i32, p, p, p, p, i32, f64, i32, f64, p, p, p, p],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -254,6 +255,18 @@ def glrm_launch_count(h) -> int:
     out = ctypes.c_int64(0)
     _check(_lib.glrm_launch_count(h, ctypes.byref(out)), h)
     return int(out.value)
+
+
+def glrm_objective_noalloc(m, n, k, csr_rowptr, csr_colidx, csr_val, col_loss_dev, rx, ry, X, Yt,
+                           out, stream=None):
+    """Objective without device allocation (see include/glrm.h); every
+    argument is a CUDA tensor, col_loss_dev the raw bytes of n glrm_loss."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib.glrm_objective_noalloc(m, n, k, _ptr(csr_rowptr), _ptr(csr_colidx), _ptr(csr_val),
+                                       _ptr(col_loss_dev), int(rx[0]), float(rx[1]), int(ry[0]),
+                                       float(ry[1]), _ptr(X), _ptr(Yt), _ptr(out),
+                                       ctypes.c_void_p(stream.cuda_stream)))
 
 
 def glrm_destroy(h):
