@@ -180,10 +180,12 @@ int glrm_objective_at(glrm_t h, const void *X_dev, const void *Yt_dev, double *o
  * element type of the model).  With include_reg != 0 the regulariser's
  * gradient is added (2 w x for GLRM_REG_QUAD, w sign(x) for GLRM_REG_L1, 0 for
  * GLRM_REG_ZERO; GLRM_REG_NONNEG is not differentiable and returns
- * GLRM_ERR_ARG).  Residuals are recomputed from the factors, never stored.
- * Does not synchronise.  This is the backward of the differentiable form. */
+ * GLRM_ERR_ARG).  scale_dev, if not NULL, points to a device double that
+ * multiplies both gradients (the incoming derivative of a backward pass).
+ * Residuals are recomputed from the factors, never stored.  Does not
+ * synchronise.  This is the backward of the differentiable form. */
 int glrm_grad_at(glrm_t h, const void *X_dev, const void *Yt_dev, void *GX_dev,
-                 void *GYt_dev, int32_t include_reg);
+                 void *GYt_dev, int32_t include_reg, const double *scale_dev);
 
 /* Imputation (Section 5.3): for the cnt pairs (rows_dev[e], cols_dev[e])
  * write u = x_i . y_j (decode == 0) or the decoded value argmin_a L_j(u, a)

@@ -725,7 +725,8 @@ int glrm_objective(glrm_t h, double *out)
     return GLRM_OK;
 }
 
-int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, int32_t include_reg)
+int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, int32_t include_reg,
+                 const double *scale)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (!X || !Yt || !GX || !GYt) return fail(h, GLRM_ERR_ARG, "null pointer");
@@ -735,9 +736,9 @@ int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, i
     DeviceGuard dg(h->device);
     cudaError_t e = h->prec == GLRM_FP64
                         ? Engine<double>::grad_at(h, (const double *)X, (const double *)Yt,
-                                                  (double *)GX, (double *)GYt, include_reg != 0)
+                                                  (double *)GX, (double *)GYt, include_reg != 0, scale)
                         : Engine<float>::grad_at(h, (const float *)X, (const float *)Yt, (float *)GX,
-                                                 (float *)GYt, include_reg != 0);
+                                                 (float *)GYt, include_reg != 0, scale);
     return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_grad_at");
 }
 

@@ -254,17 +254,19 @@ reduce_stage2(const double *__restrict__ part, const long long *__restrict__ cnt
 template <class T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 seg_grad_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restrict__ part_grad,
-                const T *__restrict__ F, int k, int rkind, T rw, bool reg, T *__restrict__ G)
+                const T *__restrict__ F, int k, int rkind, T rw, bool reg,
+                const double *__restrict__ scale, T *__restrict__ G)
 {
     const int lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (s >= nseg) return;
     const int cb = segchunk[s], ce = segchunk[s + 1];
+    const T sc = scale ? (T)*scale : T(1);
     for (int c = lane; c < k; c += 32) {
         T g = T(0);
         for (int q = cb; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
         if (reg) g += reg_grad1<T>(rkind, rw, F[s * k + c]);
-        G[s * k + c] = g;
+        G[s * k + c] = sc * g;
     }
 }
 
@@ -416,7 +418,8 @@ cudaError_t Engine<T>::objective_at(glrm_s *h, const T *X, const T *Yt, double *
 }
 
 template <class T>
-cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt, bool reg)
+cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt, bool reg,
+                               const double *scale)
 {
     Scratch &s = h->s;
     tmark(h, "grad_pass_x");
@@ -425,7 +428,7 @@ cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt
     if (e != cudaSuccess) return e;
     tmark(h, "grad_seg_x");
     seg_grad_kernel<T><<<blocks_for(h->m, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->m, h->csr.segchunk, (const T *)s.part_grad, X, h->k, h->rx_kind, (T)h->rx_w, reg, GX);
+        h->m, h->csr.segchunk, (const T *)s.part_grad, X, h->k, h->rx_kind, (T)h->rx_w, reg, scale, GX);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, "grad_pass_y");
     e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
@@ -433,7 +436,7 @@ cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt
     if (e != cudaSuccess) return e;
     tmark(h, "grad_seg_y");
     seg_grad_kernel<T><<<blocks_for(h->n, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->n, h->csc.segchunk, (const T *)s.part_grad, Yt, h->k, h->ry_kind, (T)h->ry_w, reg, GYt);
+        h->n, h->csc.segchunk, (const T *)s.part_grad, Yt, h->k, h->ry_kind, (T)h->ry_w, reg, scale, GYt);
     tmark(h, nullptr);
     h->launches += 2 + (h->csr.nchunks ? 1 : 0) + (h->csc.nchunks ? 1 : 0);
     return cudaGetLastError();

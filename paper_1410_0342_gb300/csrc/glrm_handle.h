@@ -138,7 +138,8 @@ struct Engine {
     static cudaError_t half_step(glrm_s *h, bool xstep);
     static cudaError_t reduce_sweep(glrm_s *h, double *hist_slot);
     static cudaError_t objective_at(glrm_s *h, const T *X, const T *Yt, double *out);
-    static cudaError_t grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt, bool reg);
+    static cudaError_t grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt, bool reg,
+                               const double *scale);
     static cudaError_t predict(glrm_s *h, int64_t cnt, const int32_t *rows, const int32_t *cols,
                                T *out, bool decode);
     static cudaError_t reset_steps(glrm_s *h);

@@ -54,7 +54,7 @@ def _load():
         "glrm_last_accepts": [p, p],
         "glrm_objective": [p, p],
         "glrm_objective_at": [p, p, p, p],
-        "glrm_grad_at": [p, p, p, p, p, i32],
+        "glrm_grad_at": [p, p, p, p, p, i32, p],
         "glrm_predict": [p, i64, p, p, p, i32],
         "glrm_als_sweep": [p, i32, p],
         "glrm_get_state": [p, p, p],
@@ -192,8 +192,10 @@ def glrm_objective_at(h, X, Yt, out):
     _check(_lib.glrm_objective_at(h, _ptr(X), _ptr(Yt), _ptr(out)), h)
 
 
-def glrm_grad_at(h, X, Yt, GX, GYt, include_reg=True):
-    _check(_lib.glrm_grad_at(h, _ptr(X), _ptr(Yt), _ptr(GX), _ptr(GYt), int(bool(include_reg))), h)
+def glrm_grad_at(h, X, Yt, GX, GYt, include_reg=True, scale=None):
+    """scale: optional CUDA float64 tensor (one element) multiplying both gradients."""
+    _check(_lib.glrm_grad_at(h, _ptr(X), _ptr(Yt), _ptr(GX), _ptr(GYt), int(bool(include_reg)),
+                             _ptr(scale)), h)
 
 
 def glrm_predict(h, rows, cols, out, decode=True):
