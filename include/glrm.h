@@ -254,6 +254,63 @@ typedef enum {
 int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path);
 int glrm_get_path(glrm_t h, int32_t *paths_host);
 
+/* ------------------------------------------------------------ batched form
+ * Many independent models of uneven size fitted together.  Each instance is a
+ * model of eq. gpca with one loss for all its columns and its own
+ * regularisers, fitted either by the proximal-gradient sweep with the
+ * step-size rule (Algorithm 2, Section 7.2) or, for quadratic loss with
+ * gamma ||.||^2 on both factors, by alternating minimisation (Algorithm 1 with
+ * the row / column problems of Section 2.4 solved exactly: Gram matrix of the
+ * observed entries in FP32, k x k Cholesky factorisation and solves in FP64).
+ * A sweep of the batch runs every instance's X-step in one launch, every
+ * Y-step in a second and the per-instance objectives in a third; with
+ * GLRM_BATCH_GRAPH the nsweeps sweeps are captured once into a CUDA graph and
+ * replayed with one graph launch.  k must be 4, 8 or 16 (FP32). */
+typedef struct glrm_batch_s *glrm_batch_t;
+enum { GLRM_BATCH_PROXGRAD = 0, GLRM_BATCH_ALS = 1 };
+/* sweep modes: graph replay, plain launches on the stream, and one launch per
+ * instance and half-step (for comparison) */
+enum { GLRM_BATCH_GRAPH = 0, GLRM_BATCH_STREAM = 1, GLRM_BATCH_PER_INSTANCE = 2 };
+typedef struct {
+    int64_t m, n;   /* rows, columns */
+    int32_t k;      /* 4, 8 or 16 */
+    int32_t method; /* GLRM_BATCH_PROXGRAD or GLRM_BATCH_ALS */
+    glrm_loss loss; /* loss of every column of the instance */
+    int32_t rx_kind, ry_kind;
+    double rx_weight, ry_weight;
+    int64_t nnz;    /* observed entries */
+} glrm_batch_instance;
+
+/* Instances are laid out one after another: instance s's CSR pointers (m_s+1
+ * values, starting at 0) follow instance s-1's, its entries (nnz_s indices and
+ * values, indices local to the instance) follow s-1's, likewise for CSC.
+ * Device pointers, copied; validated on the device (as glrm_set_observed).
+ * Factors start at zero (glrm_batch_set_factors); X is the concatenation of
+ * every instance's m_s x k_s row-major X, Yt likewise.  Step sizes start at
+ * 1/max(count, 1).  Synchronises.  On error *out may still hold a handle to
+ * pass to glrm_batch_destroy. */
+int glrm_batch_create(int32_t count, const glrm_batch_instance *inst_host, const int32_t *rowptr_dev,
+                      const int32_t *colidx_dev, const float *val_dev, const int32_t *colptr_dev,
+                      const int32_t *rowidx_dev, const float *cval_dev, void *stream,
+                      glrm_batch_t *out);
+int glrm_batch_set_factors(glrm_batch_t b, const float *X_dev, const float *Yt_dev);
+int glrm_batch_get_factors(glrm_batch_t b, float *X_dev, float *Yt_dev);
+/* step sizes: one float per row of every instance (ax), per column (ay) */
+int glrm_batch_set_steps(glrm_batch_t b, const float *ax_dev, const float *ay_dev);
+int glrm_batch_get_steps(glrm_batch_t b, float *ax_dev, float *ay_dev);
+/* nsweeps sweeps of every instance; objectives_host, if not NULL, receives
+ * nsweeps x count doubles (sweep-major), the objective of each instance after
+ * each sweep, and the call synchronises. */
+int glrm_batch_sweep(glrm_batch_t b, int32_t nsweeps, double *objectives_host, int32_t mode);
+/* Autotuner: for every bucket of instances (k, method, entries per row or
+ * column class) and each half-step, times the half-step kernel on that
+ * bucket's instances with 1, 2, 4 and 8 rows (columns) per work item and keeps
+ * the fastest; the fit state is saved and restored around the timing runs.
+ * tiles_x / tiles_y (32 values each, nullable) receive the table. */
+int glrm_batch_autotune(glrm_batch_t b, int32_t reps, int32_t *tiles_x_host, int32_t *tiles_y_host);
+const char *glrm_batch_last_error(glrm_batch_t b);
+void glrm_batch_destroy(glrm_batch_t b);
+
 /* Instrumentation (not part of the method).  glrm_timing_enable(h, 1)
  * records a CUDA event on the handle's stream before every kernel the handle
  * launches and after the last one, so each kernel's device time is measured

@@ -65,6 +65,13 @@ def _load():
         "glrm_set_path": [p, i32, i32],
         "glrm_get_path": [p, p],
         "glrm_objective_noalloc": [i64, i64, i32, p, p, p, p, i32, f64, i32, f64, p, p, p, p],
+        "glrm_batch_create": [i32, p, p, p, p, p, p, p, p, p],
+        "glrm_batch_set_factors": [p, p, p],
+        "glrm_batch_get_factors": [p, p, p],
+        "glrm_batch_set_steps": [p, p, p],
+        "glrm_batch_get_steps": [p, p, p],
+        "glrm_batch_sweep": [p, i32, p, i32],
+        "glrm_batch_autotune": [p, i32, p, p],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -76,6 +83,10 @@ def _load():
     lib.glrm_global_error.restype = ctypes.c_char_p
     lib.glrm_destroy.argtypes = [p]
     lib.glrm_destroy.restype = None
+    lib.glrm_batch_last_error.argtypes = [p]
+    lib.glrm_batch_last_error.restype = ctypes.c_char_p
+    lib.glrm_batch_destroy.argtypes = [p]
+    lib.glrm_batch_destroy.restype = None
     return lib
 
 
@@ -274,6 +285,98 @@ def glrm_objective_noalloc(m, n, k, csr_rowptr, csr_colidx, csr_val, col_loss_de
 def glrm_destroy(h):
     if h:
         _lib.glrm_destroy(h)
+
+
+# ------------------------------------------------------------ batched form
+
+GLRM_BATCH_PROXGRAD, GLRM_BATCH_ALS = 0, 1
+GLRM_BATCH_GRAPH, GLRM_BATCH_STREAM, GLRM_BATCH_PER_INSTANCE = 0, 1, 2
+
+
+class glrm_batch_instance(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("method", ctypes.c_int32), ("loss", glrm_loss), ("rx_kind", ctypes.c_int32),
+                ("ry_kind", ctypes.c_int32), ("rx_weight", ctypes.c_double),
+                ("ry_weight", ctypes.c_double), ("nnz", ctypes.c_int64)]
+
+
+def _bcheck(rc, b=None):
+    if rc != GLRM_OK:
+        msg = _lib.glrm_batch_last_error(b) or b""
+        raise GLRMError(rc, msg.decode(errors="replace"))
+
+
+class Batch:
+    """A glrm_batch_t over a workloads.Batch (device tensors)."""
+
+    def __init__(self, wb, methods, rx=(GLRM_REG_QUAD, 0.1), ry=(GLRM_REG_QUAD, 0.1),
+                 huber_delta=1.0, stream=None):
+        self.count = wb.count
+        arr = (glrm_batch_instance * self.count)()
+        for s in range(self.count):
+            kind = int(wb.kind[s])
+            arr[s] = glrm_batch_instance(int(wb.m[s]), int(wb.n[s]), int(wb.k[s]), int(methods[s]),
+                                         glrm_loss(kind, 0, huber_delta if kind == 1 else 0.0),
+                                         int(rx[0]), int(ry[0]), float(rx[1]), float(ry[1]),
+                                         int(wb.nnz[s]))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.wb = wb
+        self.b = ctypes.c_void_p()
+        rc = _lib.glrm_batch_create(self.count, ctypes.cast(arr, ctypes.c_void_p), _ptr(wb.rowptr),
+                                    _ptr(wb.colidx), _ptr(wb.val), _ptr(wb.colptr), _ptr(wb.rowidx),
+                                    _ptr(wb.cval), ctypes.c_void_p(stream.cuda_stream),
+                                    ctypes.byref(self.b))
+        if rc != GLRM_OK:
+            msg = (_lib.glrm_batch_last_error(self.b) if self.b else _lib.glrm_batch_last_error(None)) or b""
+            if self.b:
+                _lib.glrm_batch_destroy(self.b)
+                self.b = None
+            raise GLRMError(rc, msg.decode(errors="replace"))
+        _bcheck(_lib.glrm_batch_set_factors(self.b, _ptr(wb.X0), _ptr(wb.Yt0)), self.b)
+
+    def sweep(self, nsweeps, mode=GLRM_BATCH_GRAPH, history=True):
+        if history:
+            out = np.empty((nsweeps, self.count), np.float64)
+            _bcheck(_lib.glrm_batch_sweep(self.b, nsweeps, _ptr(out), mode), self.b)
+            return out
+        _bcheck(_lib.glrm_batch_sweep(self.b, nsweeps, None, mode), self.b)
+        return None
+
+    def factors(self):
+        X = torch.empty_like(self.wb.X0)
+        Yt = torch.empty_like(self.wb.Yt0)
+        _bcheck(_lib.glrm_batch_get_factors(self.b, _ptr(X), _ptr(Yt)), self.b)
+        return X, Yt
+
+    def set_factors(self, X, Yt):
+        _bcheck(_lib.glrm_batch_set_factors(self.b, _ptr(X), _ptr(Yt)), self.b)
+
+    def steps(self):
+        ax = torch.empty(int(self.wb.m.sum()), dtype=torch.float32, device=self.wb.X0.device)
+        ay = torch.empty(int(self.wb.n.sum()), dtype=torch.float32, device=self.wb.X0.device)
+        _bcheck(_lib.glrm_batch_get_steps(self.b, _ptr(ax), _ptr(ay)), self.b)
+        return ax, ay
+
+    def set_steps(self, ax, ay):
+        _bcheck(_lib.glrm_batch_set_steps(self.b, _ptr(ax), _ptr(ay)), self.b)
+
+    def autotune(self, reps=3):
+        tx = np.zeros(32, np.int32)
+        ty = np.zeros(32, np.int32)
+        _bcheck(_lib.glrm_batch_autotune(self.b, reps, _ptr(tx), _ptr(ty)), self.b)
+        return tx, ty
+
+    def close(self):
+        if self.b:
+            _lib.glrm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------- convenience

@@ -274,3 +274,79 @@ def small_mixed(m=97, n=41, k=6, p_obs=0.55, seed=BASE_SEED + 20, rx=(REG_L1, 0.
     param = np.where(kinds == LOSS_HUBER, 1.0, 0.0)
     lv = np.where(kinds == LOSS_ORDINAL, levels, 0)
     return _finish("small_mixed", m, n, k, rowptr, colidx, val, kinds, param, lv, rx, ry, rng)
+
+
+# ------------------------------------------------------------ batched tables
+
+@dataclasses.dataclass
+class Batch:
+    """Concatenated instances: per-instance sizes and losses, CSR / CSC arrays
+    with instance-local indices, initial factors (torch tensors on `device`)."""
+    m: np.ndarray          # int64 [count]
+    n: np.ndarray          # int64 [count]
+    k: np.ndarray          # int32 [count]
+    kind: np.ndarray       # int32 [count] loss of every column of the instance
+    nnz: np.ndarray        # int64 [count]
+    rowptr: object         # int32 [sum(m+1)], instance-local entry offsets
+    colidx: object         # int32 [sum nnz]
+    val: object            # float32 [sum nnz]
+    colptr: object         # int32 [sum(n+1)]
+    rowidx: object         # int32 [sum nnz]
+    cval: object           # float32 [sum nnz]
+    X0: object             # float32 [sum m*k]
+    Yt0: object            # float32 [sum n*k]
+
+    @property
+    def count(self) -> int:
+        return int(self.m.size)
+
+
+def batch_instance_torch(s: int, device, seed=BASE_SEED + 5, m_range=(50, 5000),
+                         n_range=(20, 500), ks=(4, 8, 16), p_obs=0.7, noise=0.2):
+    """Instance s of the batched workload drawn with torch generators on
+    `device` (sizes from a CPU generator, data from a device generator, both
+    seeded with seed + s): m, n uniform in their ranges, k uniform over ks;
+    even s quadratic loss, odd s Huber; A = X0 Y0 + N(0, noise^2); cells
+    observed with probability p_obs.  Returns host-side metadata and device
+    tensors (CSR, CSC, initial factors)."""
+    import torch
+    cg = torch.Generator().manual_seed(seed + s)
+    m = int(torch.randint(m_range[0], m_range[1] + 1, (1,), generator=cg))
+    n = int(torch.randint(n_range[0], n_range[1] + 1, (1,), generator=cg))
+    k = int(ks[int(torch.randint(0, len(ks), (1,), generator=cg))])
+    dg = torch.Generator(device=device).manual_seed(seed + s)
+    kw = dict(generator=dg, device=device)
+    X0 = torch.randn(m, k, **kw)
+    Y0t = torch.randn(n, k, **kw)
+    mask = torch.rand(m, n, **kw) < p_obs
+    A = X0 @ Y0t.T + noise * torch.randn(m, n, **kw)
+    rc = mask.nonzero()
+    rows, cols = rc[:, 0], rc[:, 1]
+    rowptr = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    rowptr[1:] = torch.cumsum(torch.bincount(rows, minlength=m), 0)
+    cr = mask.T.nonzero()
+    colptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    colptr[1:] = torch.cumsum(torch.bincount(cr[:, 0], minlength=n), 0)
+    Xi = torch.randn(m, k, **kw)
+    Yi = torch.randn(n, k, **kw)
+    return dict(m=m, n=n, k=k, kind=LOSS_QUAD if s % 2 == 0 else LOSS_HUBER,
+                rowptr=rowptr.to(torch.int32), colidx=cols.to(torch.int32),
+                val=A[rows, cols].float(), colptr=colptr.to(torch.int32),
+                rowidx=cr[:, 1].to(torch.int32), cval=A[cr[:, 1], cr[:, 0]].float(),
+                X0=Xi.float(), Yt0=Yi.float())
+
+
+def batch_torch(count=4096, device="cuda", **kw) -> Batch:
+    """The batched workload: `count` instances from batch_instance_torch,
+    concatenated."""
+    import torch
+    parts = [batch_instance_torch(s, device, **kw) for s in range(count)]
+    cat = lambda key: torch.cat([p[key].reshape(-1) for p in parts])
+    return Batch(m=np.array([p["m"] for p in parts], np.int64),
+                 n=np.array([p["n"] for p in parts], np.int64),
+                 k=np.array([p["k"] for p in parts], np.int32),
+                 kind=np.array([p["kind"] for p in parts], np.int32),
+                 nnz=np.array([int(p["colidx"].numel()) for p in parts], np.int64),
+                 rowptr=cat("rowptr"), colidx=cat("colidx"), val=cat("val"),
+                 colptr=cat("colptr"), rowidx=cat("rowidx"), cval=cat("cval"),
+                 X0=cat("X0"), Yt0=cat("Yt0"))
