@@ -56,6 +56,9 @@ def parse():
                     help="rows of the mixed table (smaller for profiling runs)")
     ap.add_argument("--path", default="auto",
                     help="kernel paths 'X,Y' (auto, chunked, fused, blocked, masked, split)")
+    ap.add_argument("--form", default="sweep", choices=["sweep", "batched", "autograd", "completion"],
+                    help="sweep: the benchmark line; the others measure the batched, differentiable "
+                         "and matrix-completion forms on their own workloads")
     return ap.parse_args()
 
 
@@ -389,9 +392,92 @@ def run_glrm(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def _events(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_form(args):
+    """Measurements of the other forms, one JSON line each (single GPU)."""
+    import torch
+    from paper_1410_0342_gb300 import build
+    build.build()
+    from paper_1410_0342_gb300 import glrm as G
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream(dev)
+    line = {"form": args.form, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
+    if args.form == "batched":
+        t0 = time.time()
+        wb = W.batch_torch(4096, device=dev)
+        gen_s = time.time() - t0
+        meth = [G.GLRM_BATCH_ALS if s % 2 == 0 else G.GLRM_BATCH_PROXGRAD for s in range(wb.count)]
+        B = G.Batch(wb, meth, stream=st)
+        tx, ty = B.autotune(reps=2)
+        nnz = int(wb.nnz.sum())
+        B.sweep(args.steps, G.GLRM_BATCH_GRAPH, history=False)  # capture + warm-up
+        for _ in range(max(0, args.warmup - 1)):
+            B.sweep(args.steps, G.GLRM_BATCH_GRAPH, history=False)
+        ms_graph = _events(torch, st, lambda: B.sweep(args.steps, G.GLRM_BATCH_GRAPH, history=False))
+        ms_stream = _events(torch, st, lambda: B.sweep(args.steps, G.GLRM_BATCH_STREAM, history=False))
+        ms_inst = _events(torch, st, lambda: B.sweep(args.steps, G.GLRM_BATCH_PER_INSTANCE, history=False))
+        line.update({
+            "metric": METRIC, "unit": UNIT, "value": nnz * args.steps / (ms_graph / 1e3),
+            "config": {"workload": "4096 instances, m~U[50,5000], n~U[20,500], k in {4,8,16}, even "
+                                   "quadratic (ALS, FP64 Cholesky), odd Huber (prox-grad), 30% missing, "
+                                   "gamma=0.1, FP32", "nnz": nnz, "generate_s": gen_s},
+            "ms_per_sweep": {"graph": ms_graph / args.steps, "stream": ms_stream / args.steps,
+                             "per_instance_launches": ms_inst / args.steps},
+            "speedup_vs_per_instance": ms_inst / ms_graph,
+            "tiles_x": tx.tolist(), "tiles_y": ty.tolist()})
+    elif args.form == "autograd":
+        from paper_1410_0342_gb300 import autograd as AG
+        t = W.logistic_bool()
+        g = G.GLRM.from_table(t, factors=False, stream=st)
+        X = torch.as_tensor(t.X0, dtype=torch.float32, device=dev).requires_grad_()
+        Yt = torch.as_tensor(t.Yt0, dtype=torch.float32, device=dev).requires_grad_()
+
+        def step():
+            X.grad = None
+            Yt.grad = None
+            AG.glrm_objective(X, Yt, g).backward()
+
+        for _ in range(args.warmup):
+            step()
+        ms = _events(torch, st, lambda: [step() for _ in range(args.steps)])
+        line.update({"metric": "observed entries/s per forward+backward", "unit": UNIT,
+                     "value": t.nnz * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "config": {"workload": "logistic Boolean table m=50000 n=2000 k=32, 20% "
+                                            "missing, gamma=0.1, FP32", "nnz": t.nnz}})
+    else:
+        t = W.completion()
+        g = G.GLRM.from_table(t, stream=st)
+        paths = G.glrm_get_path(g.h)
+        g.sweep(args.warmup, history=False)
+        G.glrm_timing_enable(g.h, True)
+        ms = _events(torch, st, lambda: g.sweep(args.steps, history=False))
+        kern = G.glrm_timing_read(g.h)
+        line.update({"metric": METRIC, "unit": UNIT, "value": t.nnz * args.steps / (ms / 1e3),
+                     "ms_per_step": ms / args.steps, "dtype": "f32",
+                     "config": {"workload": "matrix completion m=1e6 n=20000 k=64, 200 entries "
+                                            "per row, quadratic loss, gamma=0.05, FP32",
+                                "nnz": t.nnz, "paths": paths},
+                     "kernels": {k: v[0] / v[1] for k, v in kern.items()}})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.form != "sweep":
+        if rank == 0:
+            run_form(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
