@@ -305,8 +305,10 @@ int glrm_batch_sweep(glrm_batch_t b, int32_t nsweeps, double *objectives_host, i
 /* Autotuner: for every bucket of instances (k, method, entries per row or
  * column class) and each half-step, times the half-step kernel on that
  * bucket's instances with 1, 2, 4 and 8 rows (columns) per work item and keeps
- * the fastest; the fit state is saved and restored around the timing runs.
- * tiles_x / tiles_y (32 values each, nullable) receive the table. */
+ * the fastest, then times the whole half-step with the work items ordered by
+ * decreasing work or grouped by instance and keeps the faster order; the fit
+ * state is saved and restored around the timing runs.  tiles_x / tiles_y (32
+ * values each, nullable) receive the table. */
 int glrm_batch_autotune(glrm_batch_t b, int32_t reps, int32_t *tiles_x_host, int32_t *tiles_y_host);
 const char *glrm_batch_last_error(glrm_batch_t b);
 void glrm_batch_destroy(glrm_batch_t b);

@@ -104,31 +104,14 @@ als_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__
         b[wid][lane] = v;
     }
     __syncwarp();
-    // Cholesky G = C C^T, column by column (right-looking), lanes over rows.
-    for (int c = 0; c < k; ++c) {
-        if (lane == 0) G[wid][c][c] = sqrt(G[wid][c][c]);
-        __syncwarp();
-        const double d = G[wid][c][c];
-        for (int r = c + 1 + lane; r < k; r += 32) G[wid][r][c] /= d;
-        __syncwarp();
-        for (int r = c + 1 + lane; r < k; r += 32)
-            for (int q = c + 1; q <= r; ++q) G[wid][r][q] -= G[wid][r][c] * G[wid][q][c];
-        __syncwarp();
-    }
-    if (lane == 0) {
-        double *x = b[wid];
-        for (int r = 0; r < k; ++r) {  // C w = b
-            double v = x[r];
-            for (int p = 0; p < r; ++p) v -= G[wid][r][p] * x[p];
-            x[r] = v / G[wid][r][r];
-        }
-        for (int r = k - 1; r >= 0; --r) {  // C^T x = w
-            double v = x[r];
-            for (int p = r + 1; p < k; ++p) v -= G[wid][p][r] * x[p];
-            x[r] = v / G[wid][r][r];
-        }
+    // unused rows / columns beyond k become identity rows of a K x K system
+    for (int c = k + lane; c < K; c += 32) {
+        for (int q = 0; q < c; ++q) G[wid][c][q] = 0.0;
+        G[wid][c][c] = 1.0;
+        b[wid][c] = 0.0;
     }
     __syncwarp();
+    warp_cholesky_solve<K, K + 1>(G[wid], b[wid]);
     if (lane < k) F[s * k + lane] = (T)b[wid][lane];
 }
 

@@ -69,6 +69,7 @@ struct glrm_batch_s {
     int64_t nitems_x = 0, nitems_y = 0;
     std::vector<int64_t> inst_items_x, inst_items_y;  // first item of each instance (unbatched mode)
     int32_t tile_x[kBucketCount], tile_y[kBucketCount];
+    int order_x = 0, order_y = 0;  // 0: items by decreasing work; 1: grouped by instance
     int grid = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_sweeps = 0;
@@ -255,29 +256,7 @@ __device__ void als_segment(const Seg &g, double gamma, int64_t s, AlsSmem &sm, 
         if (lane + 32 * q < N) sm.G[rq[q]][cq[q]] = (double)acc[q] + (rq[q] == cq[q] ? gamma : 0.0);
     if (lane < K) sm.rhs[lane] = (double)bacc;
     __syncwarp();
-    for (int c = 0; c < K; ++c) {
-        if (lane == 0) sm.G[c][c] = sqrt(sm.G[c][c]);
-        __syncwarp();
-        const double d = sm.G[c][c];
-        for (int r = c + 1 + lane; r < K; r += 32) sm.G[r][c] /= d;
-        __syncwarp();
-        for (int r = c + 1 + lane; r < K; r += 32)
-            for (int q = c + 1; q <= r; ++q) sm.G[r][q] -= sm.G[r][c] * sm.G[q][c];
-        __syncwarp();
-    }
-    if (lane == 0) {
-        for (int r = 0; r < K; ++r) {
-            double v = sm.rhs[r];
-            for (int p = 0; p < r; ++p) v -= sm.G[r][p] * sm.rhs[p];
-            sm.rhs[r] = v / sm.G[r][r];
-        }
-        for (int r = K - 1; r >= 0; --r) {
-            double v = sm.rhs[r];
-            for (int p = r + 1; p < K; ++p) v -= sm.G[p][r] * sm.rhs[p];
-            sm.rhs[r] = v / sm.G[r][r];
-        }
-    }
-    __syncwarp();
+    warp_cholesky_solve<K, kBK + 1>(sm.G, sm.rhs);
     float f[K];
     double reg = 0.0;
 #pragma unroll
@@ -473,9 +452,11 @@ int bucket(const BInst &I, int64_t nnz, bool xstep)
 }
 
 // Items of one orientation: each instance's segments in ranges of the tile
-// size of its bucket, ordered by decreasing estimated work.
+// size of its bucket, ordered by decreasing estimated work (order 0) or
+// instance by instance (order 1: warps running at the same time then share an
+// instance's factors in L2).
 void build_items(const glrm_batch_s *b, bool xstep, const int32_t *tiles, const std::vector<int> *only,
-                 std::vector<int4> &items, std::vector<int64_t> *first)
+                 std::vector<int4> &items, std::vector<int64_t> *first, int order = 0)
 {
     struct W {
         int4 it;
@@ -496,7 +477,8 @@ void build_items(const glrm_batch_s *b, bool xstep, const int32_t *tiles, const 
             all.push_back(W{make_int4(s, (int)a, (int)z, 0), w});
         }
     }
-    std::stable_sort(all.begin(), all.end(), [](const W &x, const W &y) { return x.cost > y.cost; });
+    if (order == 0)
+        std::stable_sort(all.begin(), all.end(), [](const W &x, const W &y) { return x.cost > y.cost; });
     items.clear();
     for (const W &w : all) items.push_back(w.it);
     if (first) {
@@ -510,8 +492,8 @@ void build_items(const glrm_batch_s *b, bool xstep, const int32_t *tiles, const 
 int upload_items(glrm_batch_s *b)
 {
     std::vector<int4> ix, iy;
-    build_items(b, true, b->tile_x, nullptr, ix, nullptr);
-    build_items(b, false, b->tile_y, nullptr, iy, nullptr);
+    build_items(b, true, b->tile_x, nullptr, ix, nullptr, b->order_x);
+    build_items(b, false, b->tile_y, nullptr, iy, nullptr, b->order_y);
     bfree(b->items_x);
     bfree(b->items_y);
     BCK(cudaMalloc(&b->items_x, std::max<size_t>(1, ix.size()) * sizeof(int4)));
@@ -875,6 +857,30 @@ int glrm_batch_autotune(glrm_batch_t b, int32_t reps, int32_t *tiles_x, int32_t 
                 }
             }
             table[kv.first] = best;
+        }
+        // item order over the whole half-step with the chosen tiles
+        float best_ms = 1e30f;
+        for (int order = 0; order < 2 && rc == GLRM_OK; ++order) {
+            std::vector<int4> items;
+            build_items(b, xstep, table, nullptr, items, nullptr, order);
+            int4 *d = nullptr;
+            if (cudaMalloc(&d, std::max<size_t>(1, items.size()) * sizeof(int4)) != cudaSuccess) {
+                rc = bfail(b, GLRM_ERR_NOMEM, "autotune items");
+                break;
+            }
+            cudaMemcpy(d, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+            launch_half(b, xstep, d, (int64_t)items.size(), st);
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps; ++r) launch_half(b, xstep, d, (int64_t)items.size(), st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaFree(d);
+            if (ms < best_ms) {
+                best_ms = ms;
+                (xstep ? b->order_x : b->order_y) = order;
+            }
         }
     }
     cudaEventDestroy(e0);

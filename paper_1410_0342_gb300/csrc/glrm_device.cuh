@@ -159,6 +159,58 @@ __device__ __forceinline__ T reg_grad1(int kind, T w, T x)
     }
 }
 
+// 1/sqrt(d) in FP64 for d > 0 (and within float range): a float estimate
+// from rsqrtf refined by two Newton-Raphson steps y <- y (3 - d y^2) / 2 for
+// the root of 1/y^2 - d (each step squares the relative error: ~1e-7 ->
+// ~1e-14 -> below FP64 rounding).  Saves the FP64 division and square root,
+// which are slow on this GPU.
+__device__ __forceinline__ double rsqrt_fp64(double d)
+{
+    double y = (double)rsqrtf((float)d);
+    y = y * (1.5 - 0.5 * d * y * y);
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+}
+
+// Solve (C C^T) x = b in place for an SPD matrix G (row-major, leading
+// dimension LD, lower triangle used; overwritten by C) and right-hand side b
+// (overwritten by x), one warp, K <= 32.  Column by column: lane 0 takes the
+// pivot's reciprocal square root, lanes below it scale and update; the two
+// triangular solves are column-oriented too, so every step is one pass of the
+// warp.  FP64 throughout.
+template <int K, int LD>
+__device__ __forceinline__ void warp_cholesky_solve(double (*G)[LD], double *b)
+{
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < K; ++c) {
+        if (lane == 0) {
+            const double r = rsqrt_fp64(G[c][c]);
+            G[c][c] = r;  // the pivot slot keeps 1/C[c][c] from here on
+        }
+        __syncwarp();
+        const double r = G[c][c];
+        if (lane > c && lane < K) G[lane][c] *= r;
+        __syncwarp();
+        if (lane > c && lane < K)
+            for (int q = c + 1; q <= lane; ++q) G[lane][q] -= G[lane][c] * G[q][c];
+        __syncwarp();
+    }
+    // C w = b: w[c] = b[c] / C[c][c], then b[r] -= C[r][c] w[c] for r > c
+    for (int c = 0; c < K; ++c) {
+        if (lane == 0) b[c] *= G[c][c];
+        __syncwarp();
+        if (lane > c && lane < K) b[lane] -= G[lane][c] * b[c];
+        __syncwarp();
+    }
+    // C^T x = w: x[c] = w[c] / C[c][c], then b[r] -= C[c][r] x[c] for r < c
+    for (int c = K - 1; c >= 0; --c) {
+        if (lane == 0) b[c] *= G[c][c];
+        __syncwarp();
+        if (lane < c) b[lane] -= G[c][lane] * b[c];
+        __syncwarp();
+    }
+}
+
 __device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ int shfl_xor(int v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
