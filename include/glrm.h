@@ -18,8 +18,12 @@
  *    pointers must be aligned to their element size; 16-byte alignment lets
  *    the kernels use vector loads.
  *  - Element type of values and factors: double for GLRM_FP64, float for
- *    GLRM_FP32 and GLRM_BF16 (the BF16 form keeps FP32 master factors and
- *    runs its factor products in bf16, see glrm_create).
+ *    GLRM_FP32 and GLRM_BF16.  The BF16 form keeps FP32 factors; its gradient
+ *    passes read BF16 copies of the other factor (products accumulated in
+ *    FP32, loss derivatives in FP32), and every candidate is re-evaluated with
+ *    the FP32 factors before the accept / reject test, so the objective it
+ *    reports and every accepted step are exact to FP32.  glrm_grad_at of a
+ *    BF16 model reads BF16 copies of both factors.
  *  - All work is enqueued on the stream given to glrm_create, in order.  An
  *    entry point returns once its work is enqueued unless it says it
  *    synchronises (it must when it hands a result back in host memory).

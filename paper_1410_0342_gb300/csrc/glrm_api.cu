@@ -75,11 +75,12 @@ void free_scratch(Scratch &s)
     dfree(s.kept_obj_x); dfree(s.kept_reg_x); dfree(s.kept_obj_y); dfree(s.kept_reg_y);
     dfree(s.acc_x); dfree(s.acc_y); dfree(s.red_part); dfree(s.red_cnt);
     dfree(s.hist); dfree(s.accepts); dfree(s.scalar); dfree(s.als_part); dfree(s.err);
+    dfree(s.x_bf16); dfree(s.yt_bf16);
     s.hist_cap = 0;
     s.als_bytes = 0;
 }
 
-bool prec_ok(int p) { return p == GLRM_FP64 || p == GLRM_FP32; }
+bool prec_ok(int p) { return p == GLRM_FP64 || p == GLRM_FP32 || p == GLRM_BF16; }
 
 // The handle's device must be current for every call.
 struct DeviceGuard {
@@ -241,6 +242,10 @@ int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
     const int K = tiled_width(h->k);
     o.mode = kModeChunked;
     if (force == GLRM_PATH_CHUNKED) return GLRM_OK;
+    if (h->prec == GLRM_BF16) {  // the BF16 form runs on the chunked path
+        if (force == GLRM_PATH_AUTO) return GLRM_OK;
+        return fail(h, GLRM_ERR_ARG, "the BF16 form runs on the chunked path only");
+    }
     if (K == 0 || h->nnz == 0) {
         if (force == GLRM_PATH_AUTO) return GLRM_OK;
         return fail(h, GLRM_ERR_ARG, "the staged paths need 1 <= k <= 32 and a non-empty Omega");
@@ -361,6 +366,10 @@ int alloc_scratch(glrm_s *h)
     CK(cudaMalloc(&s.accepts, 2 * sizeof(long long)));
     CK(cudaMalloc(&s.scalar, sizeof(double)));
     CK(cudaMalloc(&s.err, sizeof(int)));
+    if (h->prec == GLRM_BF16) {
+        CK(cudaMalloc(&s.x_bf16, (size_t)h->m * h->k * sizeof(__nv_bfloat16)));
+        CK(cudaMalloc(&s.yt_bf16, (size_t)h->n * h->k * sizeof(__nv_bfloat16)));
+    }
     CK(cudaMemsetAsync(s.accepts, 0, 2 * sizeof(long long), h->stream));
     CK(cudaMemsetAsync(s.err, 0, sizeof(int), h->stream));
     return GLRM_OK;

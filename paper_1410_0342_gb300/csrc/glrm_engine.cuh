@@ -17,6 +17,8 @@
 // All reductions run in a fixed order: results are bitwise reproducible.
 #pragma once
 
+#include <type_traits>
+
 #include "glrm_handle.h"
 
 namespace glrm {
@@ -31,10 +33,42 @@ struct Lanes {
     static constexpr int PER = 32 / G;  // entries per warp iteration
 };
 
-template <class T, int K, bool XSTEP, bool VEC, bool GRAD>
+// Coordinates c0 .. c0+S-1 of a BF16 row (the BF16 copy of the other factor
+// in the BF16 form), widened to FP32.
+template <int S, bool VEC>
+__device__ __forceinline__ void load_slice_bf16(float (&v)[S], const __nv_bfloat16 *__restrict__ row,
+                                                int c0, int k)
+{
+    if constexpr (VEC) {
+        static_assert(S % 8 == 0, "bf16 slice must be a multiple of 8");
+        const uint4 *p = reinterpret_cast<const uint4 *>(row + c0);
+#pragma unroll
+        for (int q = 0; q < S / 8; ++q) {
+            const uint4 t = __ldg(p + q);
+            const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                v[8 * q + 2 * h] = __uint_as_float(w[h] << 16);
+                v[8 * q + 2 * h + 1] = __uint_as_float(w[h] & 0xffff0000u);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) v[s] = (c0 + s < k) ? __bfloat162float(row[c0 + s]) : 0.f;
+    }
+}
+
+template <class T, int S, bool VEC, class WT>
+__device__ __forceinline__ void load_w(T (&v)[S], const WT *__restrict__ row, int c0, int k)
+{
+    if constexpr (std::is_same<WT, __nv_bfloat16>::value) load_slice_bf16<S, VEC>(v, row, c0, k);
+    else load_slice<T, S, VEC>(v, row, c0, k);
+}
+
+template <class T, int K, bool XSTEP, bool VEC, bool GRAD, class WT = T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ idx,
-            const T *__restrict__ val, const T *__restrict__ F, const T *__restrict__ W, int k,
+            const T *__restrict__ val, const T *__restrict__ F, const WT *__restrict__ W, int k,
             const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
             double *__restrict__ part_loss)
 {
@@ -61,7 +95,7 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
         if (ok) {
             j = __ldg(idx + e);
             a = __ldg(val + e);
-            load_slice<T, S, VEC>(w, W + (int64_t)j * k, c0, k);
+            load_w<T, S, VEC, WT>(w, W + (int64_t)j * k, c0, k);
         } else {
 #pragma unroll
             for (int s = 0; s < S; ++s) w[s] = T(0);
@@ -96,6 +130,13 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
     }
     const double ls = warp_sum((double)lsum);
     if (lane == 0) part_loss[c] = ls;
+}
+
+// Round FP32 values to BF16 (round to nearest even).
+static __global__ void to_bf16_kernel(const float *__restrict__ src, int64_t n, __nv_bfloat16 *__restrict__ dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
 }
 
 // Sum of a segment's chunk partials, lanes strided then a butterfly: fixed order.
@@ -304,29 +345,37 @@ inline unsigned blocks_for(int64_t items, int per_block)
     return (unsigned)((items + per_block - 1) / per_block);
 }
 
-template <class T, int K, bool XSTEP, bool GRAD>
-cudaError_t launch_pass(const Orient &o, const T *F, const T *W, int k, const LossSpec *loss,
+template <class T, int K, bool XSTEP, bool GRAD, class WT>
+cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
                         T *part_grad, double *part_loss, cudaStream_t st)
 {
     if (o.nchunks == 0) return cudaSuccess;
-    const bool vec = (k == K) && ((reinterpret_cast<uintptr_t>(F) | reinterpret_cast<uintptr_t>(W)) % 16 == 0);
+    // the BF16 copy is read 8 values at a time, so its vector path needs k % 8 == 0
+    constexpr int kVecMult = std::is_same<WT, __nv_bfloat16>::value ? 8 : 1;
+    const bool vec = (k == K) && (Lanes<K>::S % kVecMult == 0) &&
+                     ((reinterpret_cast<uintptr_t>(F) | reinterpret_cast<uintptr_t>(W)) % 16 == 0);
     const unsigned nb = blocks_for(o.nchunks, kWarpsPerBlock);
-    if (vec)
-        pass_kernel<T, K, XSTEP, true, GRAD><<<nb, kWarpsPerBlock * 32, 0, st>>>(
+    if constexpr (std::is_same<WT, __nv_bfloat16>::value && Lanes<K>::S % 8 != 0) {
+        pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
             o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
-    else
-        pass_kernel<T, K, XSTEP, false, GRAD><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-            o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+    } else {
+        if (vec)
+            pass_kernel<T, K, XSTEP, true, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
+                o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+        else
+            pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
+                o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+    }
     return cudaGetLastError();
 }
 
 // Dispatch a runtime k to the smallest padded width K >= k.
-template <class T, bool XSTEP, bool GRAD>
-cudaError_t dispatch_pass(const Orient &o, const T *F, const T *W, int k, const LossSpec *loss,
+template <class T, bool XSTEP, bool GRAD, class WT = T>
+cudaError_t dispatch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
                           T *part_grad, double *part_loss, cudaStream_t st)
 {
 #define GLRM_PASS_CASE(KK) \
-    if (k <= KK) return launch_pass<T, KK, XSTEP, GRAD>(o, F, W, k, loss, part_grad, part_loss, st);
+    if (k <= KK) return launch_pass<T, KK, XSTEP, GRAD, WT>(o, F, W, k, loss, part_grad, part_loss, st);
     GLRM_PASS_CASE(4)
     GLRM_PASS_CASE(8)
     GLRM_PASS_CASE(12)
@@ -354,10 +403,29 @@ cudaError_t Engine<T>::half_step(glrm_s *h, bool xstep)
     const int k = h->k;
     const int pass_launches = o.nchunks ? 1 : 0;
     cudaError_t e;
-    tmark(h, xstep ? "pass_grad_x" : "pass_grad_y");
-    e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st)
-              : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st);
-    if (e != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->prec == GLRM_BF16) {
+            // BF16 form: the gradient pass reads a BF16 copy of the other factor
+            const int64_t nother = xstep ? h->n : h->m;
+            __nv_bfloat16 *Wb = xstep ? s.yt_bf16 : s.x_bf16;
+            tmark(h, xstep ? "to_bf16_y" : "to_bf16_x");
+            to_bf16_kernel<<<blocks_for(nother * k, 256), 256, 0, st>>>((const float *)W, nother * k, Wb);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            h->launches += 1;
+            tmark(h, xstep ? "pass_grad_x_bf16" : "pass_grad_y_bf16");
+            e = xstep ? dispatch_pass<T, true, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (T *)s.part_grad,
+                                                                    s.part_loss, st)
+                      : dispatch_pass<T, false, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (T *)s.part_grad,
+                                                                     s.part_loss, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (h->prec != GLRM_BF16) {
+        tmark(h, xstep ? "pass_grad_x" : "pass_grad_y");
+        e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st)
+                  : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st);
+        if (e != cudaSuccess) return e;
+    }
     const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
     prox_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const T *)s.part_grad,
@@ -422,17 +490,47 @@ cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt
                                const double *scale)
 {
     Scratch &s = h->s;
+    cudaError_t e;
+    bool bf16 = false;
+    if constexpr (std::is_same<T, float>::value) bf16 = h->prec == GLRM_BF16;
+    if (bf16) {
+        // BF16 form: both gradient passes read BF16 copies of the factors
+        to_bf16_kernel<<<blocks_for(h->n * h->k, 256), 256, 0, h->stream>>>((const float *)Yt, h->n * h->k,
+                                                                           s.yt_bf16);
+        to_bf16_kernel<<<blocks_for(h->m * h->k, 256), 256, 0, h->stream>>>((const float *)X, h->m * h->k,
+                                                                           s.x_bf16);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        h->launches += 2;
+    }
     tmark(h, "grad_pass_x");
-    cudaError_t e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev,
-                                                 (T *)s.part_grad, s.part_loss, h->stream);
+    if constexpr (std::is_same<T, float>::value) {
+        if (bf16)
+            e = dispatch_pass<T, true, true, __nv_bfloat16>(h->csr, X, s.yt_bf16, h->k, h->loss_dev,
+                                                            (T *)s.part_grad, s.part_loss, h->stream);
+        else
+            e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev, (T *)s.part_grad,
+                                             s.part_loss, h->stream);
+    } else {
+        e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev, (T *)s.part_grad, s.part_loss,
+                                         h->stream);
+    }
     if (e != cudaSuccess) return e;
     tmark(h, "grad_seg_x");
     seg_grad_kernel<T><<<blocks_for(h->m, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
         h->m, h->csr.segchunk, (const T *)s.part_grad, X, h->k, h->rx_kind, (T)h->rx_w, reg, scale, GX);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, "grad_pass_y");
-    e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
-                                      s.part_loss, h->stream);
+    if constexpr (std::is_same<T, float>::value) {
+        if (bf16)
+            e = dispatch_pass<T, false, true, __nv_bfloat16>(h->csc, Yt, s.x_bf16, h->k, h->loss_dev,
+                                                             (T *)s.part_grad, s.part_loss, h->stream);
+        else
+            e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
+                                              s.part_loss, h->stream);
+    } else {
+        e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
+                                          s.part_loss, h->stream);
+    }
     if (e != cudaSuccess) return e;
     tmark(h, "grad_seg_y");
     seg_grad_kernel<T><<<blocks_for(h->n, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(

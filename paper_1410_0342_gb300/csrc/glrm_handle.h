@@ -84,6 +84,8 @@ struct Scratch {
     void *als_part = nullptr;       // ALS per-chunk Gram partials
     size_t als_bytes = 0;
     int *err = nullptr;             // device flag: a bounded wait expired
+    __nv_bfloat16 *x_bf16 = nullptr;   // BF16 form: BF16 copies of the factors
+    __nv_bfloat16 *yt_bf16 = nullptr;
 };
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs

@@ -1,0 +1,64 @@
+"""The BF16 form: gradient passes on BF16 copies of the factors with FP32
+accumulation and FP32 loss derivatives; candidates re-evaluated in FP32
+before the accept / reject test.  Checked against the FP64 oracle (gradient
+within 2e-2) and against the plain FP32 sweep (objective accuracy)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1410_0342_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1410_0342_gb300 import build
+    build.build()
+    from paper_1410_0342_gb300 import glrm
+    return glrm
+
+
+def oracle_problem(o, t):
+    return o.Problem.from_csr(t.m, t.n, t.k, t.rowptr, t.colidx, t.val, loss_kind=t.loss_kind,
+                              loss_param=t.loss_param, loss_levels=t.loss_levels, rx=t.rx, ry=t.ry)
+
+
+@pytest.mark.parametrize("k", [16, 64])
+def test_bf16_gradient_within_2e2(G, oracle_mod, k):
+    t = W.completion(m=8000, n=600, k=k, per_row=60, seed=60 + k)
+    g = G.GLRM.from_table(t, precision=G.GLRM_BF16)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_CHUNKED, G.GLRM_PATH_CHUNKED)
+    X = torch.as_tensor(t.X0, dtype=torch.float32, device="cuda")
+    Yt = torch.as_tensor(t.Yt0, dtype=torch.float32, device="cuda")
+    GX = torch.empty_like(X)
+    GY = torch.empty_like(Yt)
+    G.glrm_grad_at(g.h, X, Yt, GX, GY, include_reg=False)
+    p = oracle_problem(oracle_mod, t)
+    oGX, oGY = p.gradient(X.double().cpu().numpy(), Yt.double().cpu().numpy())
+    for a, b in ((GX, oGX), (GY, oGY)):
+        rel = np.linalg.norm(a.double().cpu().numpy() - b) / np.linalg.norm(b)
+        assert rel < 2e-2, rel
+        assert rel > 1e-7  # it really ran on BF16 copies
+
+
+def test_bf16_sweep_matches_fp32_objective(G, oracle_mod):
+    """Same table, same start: the BF16 form's objective after 20 sweeps is
+    within 1e-3 of the FP32 form's and of the oracle's; every reported value
+    is the FP32 objective of the accepted factors and never increases."""
+    t = W.completion(m=20000, n=400, k=64, per_row=40, seed=79)
+    gb = G.GLRM.from_table(t, precision=G.GLRM_BF16)
+    gf = G.GLRM.from_table(t, precision=G.GLRM_FP32)
+    hb = gb.sweep(20)
+    hf = gf.sweep(20)
+    *_, oh, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 20)
+    assert np.all(np.diff(hb) <= 1e-7 * np.abs(hb[1:]))
+    assert abs(hb[-1] - hf[-1]) / hf[-1] < 1e-3, (hb[-1], hf[-1])
+    assert abs(hb[-1] - oh[-1]) / oh[-1] < 1e-3, (hb[-1], oh[-1])
+    # the reported objective is the FP32 objective of the factors it kept
+    X, Yt = gb.factors()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.glrm_objective_at(gb.h, X, Yt, out)
+    assert abs(out.item() - hb[-1]) / hb[-1] < 1e-6
