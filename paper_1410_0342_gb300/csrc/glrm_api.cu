@@ -52,6 +52,7 @@ void free_orient(Orient &o)
     dfree(o.chunks);
     dfree(o.segchunk);
     dfree(o.runptr);
+    dfree(o.perm);
     dfree(o.tptr);
     dfree(o.tidx);
     dfree(o.tmask);
@@ -75,7 +76,8 @@ void free_scratch(Scratch &s)
     dfree(s.kept_obj_x); dfree(s.kept_reg_x); dfree(s.kept_obj_y); dfree(s.kept_reg_y);
     dfree(s.acc_x); dfree(s.acc_y); dfree(s.red_part); dfree(s.red_cnt);
     dfree(s.hist); dfree(s.accepts); dfree(s.scalar); dfree(s.als_part); dfree(s.err);
-    dfree(s.x_bf16); dfree(s.yt_bf16);
+    dfree(s.x_bf16); dfree(s.yt_bf16); dfree(s.u_csr); dfree(s.u_csc); dfree(s.u_new);
+    s.u_sweeps = -1;
     s.hist_cap = 0;
     s.als_bytes = 0;
 }
@@ -369,6 +371,17 @@ int alloc_scratch(glrm_s *h)
     if (h->prec == GLRM_BF16) {
         CK(cudaMalloc(&s.x_bf16, (size_t)h->m * h->k * sizeof(__nv_bfloat16)));
         CK(cudaMalloc(&s.yt_bf16, (size_t)h->n * h->k * sizeof(__nv_bfloat16)));
+        const size_t nz = (size_t)std::max<int64_t>(h->nnz, 1);
+        CK(cudaMalloc(&s.u_csr, nz * sizeof(float)));
+        CK(cudaMalloc(&s.u_csc, nz * sizeof(float)));
+        CK(cudaMalloc(&s.u_new, nz * sizeof(float)));
+        s.u_sweeps = -1;
+        if (h->csr.perm == nullptr && h->nnz > 0) {
+            CK(cudaMalloc(&h->csr.perm, nz * sizeof(int32_t)));
+            CK(cudaMalloc(&h->csc.perm, nz * sizeof(int32_t)));
+            CK(launch_perm(h->csr, h->csc, h->stream));
+            CK(launch_perm(h->csc, h->csr, h->stream));
+        }
     }
     CK(cudaMemsetAsync(s.accepts, 0, 2 * sizeof(long long), h->stream));
     CK(cudaMemsetAsync(s.err, 0, sizeof(int), h->stream));
@@ -633,6 +646,7 @@ static int copy_factors(glrm_t h, void *X, void *Yt, const void *Xs, const void 
 
 int glrm_set_factors(glrm_t h, const void *X, const void *Yt)
 {
+    if (h) h->s.u_sweeps = -1;
     return h ? copy_factors(h, h->X, h->Yt, X, Yt, cudaMemcpyDeviceToDevice, false)
              : fail(nullptr, GLRM_ERR_ARG, "null handle");
 }
@@ -646,6 +660,7 @@ int glrm_get_factors(glrm_t h, void *X, void *Yt)
 
 int glrm_set_factors_host(glrm_t h, const void *X, const void *Yt)
 {
+    if (h) h->s.u_sweeps = -1;
     return h ? copy_factors(h, h->X, h->Yt, X, Yt, cudaMemcpyHostToDevice, true)
              : fail(nullptr, GLRM_ERR_ARG, "null handle");
 }
@@ -778,6 +793,7 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     DeviceGuard dg(h->device);
     int rc = ensure_hist(h, nsweeps);
     if (rc != GLRM_OK) return rc;
+    h->s.u_sweeps = -1;
     for (int t = 0; t < nsweeps; ++t) {
         cudaError_t e = h->prec == GLRM_FP64 ? Engine<double>::als_half(h, true, h->rx_w)
                                              : Engine<float>::als_half(h, true, h->rx_w);
@@ -843,6 +859,7 @@ int glrm_set_state(glrm_t h, const void *buf, size_t len)
         return fail(h, GLRM_ERR_ARG, "state does not match this model");
     DeviceGuard dg(h->device);
     const char *p = (const char *)buf + sizeof hdr;
+    h->s.u_sweeps = -1;
     CK(cudaMemcpyAsync(h->X, p, es * h->m * h->k, cudaMemcpyHostToDevice, h->stream));
     p += es * h->m * h->k;
     CK(cudaMemcpyAsync(h->Yt, p, es * h->n * h->k, cudaMemcpyHostToDevice, h->stream));

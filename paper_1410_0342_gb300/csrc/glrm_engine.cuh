@@ -404,28 +404,12 @@ cudaError_t Engine<T>::half_step(glrm_s *h, bool xstep)
     const int pass_launches = o.nchunks ? 1 : 0;
     cudaError_t e;
     if constexpr (std::is_same<T, float>::value) {
-        if (h->prec == GLRM_BF16) {
-            // BF16 form: the gradient pass reads a BF16 copy of the other factor
-            const int64_t nother = xstep ? h->n : h->m;
-            __nv_bfloat16 *Wb = xstep ? s.yt_bf16 : s.x_bf16;
-            tmark(h, xstep ? "to_bf16_y" : "to_bf16_x");
-            to_bf16_kernel<<<blocks_for(nother * k, 256), 256, 0, st>>>((const float *)W, nother * k, Wb);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            h->launches += 1;
-            tmark(h, xstep ? "pass_grad_x_bf16" : "pass_grad_y_bf16");
-            e = xstep ? dispatch_pass<T, true, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (T *)s.part_grad,
-                                                                    s.part_loss, st)
-                      : dispatch_pass<T, false, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (T *)s.part_grad,
-                                                                     s.part_loss, st);
-            if (e != cudaSuccess) return e;
-        }
+        if (h->prec == GLRM_BF16) return bf16_half_step_entry(h, xstep);
     }
-    if (h->prec != GLRM_BF16) {
-        tmark(h, xstep ? "pass_grad_x" : "pass_grad_y");
-        e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st)
-                  : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st);
-        if (e != cudaSuccess) return e;
-    }
+    tmark(h, xstep ? "pass_grad_x" : "pass_grad_y");
+    e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st)
+              : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st);
+    if (e != cudaSuccess) return e;
     const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
     prox_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const T *)s.part_grad,

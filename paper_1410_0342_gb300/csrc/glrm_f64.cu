@@ -6,3 +6,7 @@
 #include "glrm_masked.cuh"
 
 template struct glrm::Engine<double>;
+
+namespace glrm {
+// the BF16 form exists for FP32 models only (glrm_f32.cu)
+}  // namespace glrm

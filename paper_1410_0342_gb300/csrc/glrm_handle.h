@@ -47,6 +47,7 @@ struct Orient {
     int mode = kModeChunked;
     int R = 0, nb = 0, ngroups = 0;  // blocked: panel rows, panels, segment groups
     int32_t *runptr = nullptr;       // blocked: (nb + 1) x nseg run starts
+    int32_t *perm = nullptr;         // BF16 form: position of each entry in the other order
     int grid = 0;                    // fused / blocked: CTAs per launch
     int cap = 0;                     // fused / blocked: entries per staging buffer
     size_t smem_bytes = 0;           // fused / blocked / masked: dynamic shared memory
@@ -86,6 +87,9 @@ struct Scratch {
     int *err = nullptr;             // device flag: a bounded wait expired
     __nv_bfloat16 *x_bf16 = nullptr;   // BF16 form: BF16 copies of the factors
     __nv_bfloat16 *yt_bf16 = nullptr;
+    float *u_csr = nullptr, *u_csc = nullptr;  // BF16 form: exact products per entry, both orders
+    float *u_new = nullptr;                    // BF16 form: re-evaluated products
+    int u_sweeps = -1;                         // sweeps since the last exact refresh (-1: stale)
 };
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
@@ -158,6 +162,8 @@ cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const vo
                                 cudaStream_t st);
 cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
                                   cudaStream_t st);
+cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep);
+cudaError_t launch_perm(const Orient &o, const Orient &other, cudaStream_t st);
 cudaError_t launch_validate_domain(const Orient &csc, int prec, const LossSpec *loss, int *flag,
                                    cudaStream_t st);
 cudaError_t launch_build_runptr(const Orient &o, cudaStream_t st);
