@@ -18,12 +18,15 @@
  *    pointers must be aligned to their element size; 16-byte alignment lets
  *    the kernels use vector loads.
  *  - Element type of values and factors: double for GLRM_FP64, float for
- *    GLRM_FP32 and GLRM_BF16.  The BF16 form keeps FP32 factors; its gradient
- *    passes read BF16 copies of the other factor (products accumulated in
- *    FP32, loss derivatives in FP32), and every candidate is re-evaluated with
- *    the FP32 factors before the accept / reject test, so the objective it
- *    reports and every accepted step are exact to FP32.  glrm_grad_at of a
- *    BF16 model reads BF16 copies of both factors.
+ *    GLRM_FP32 and GLRM_BF16.  The BF16 form keeps FP32 factors and an FP32
+ *    product u = x_i . y_j per observed entry; its passes gather BF16 copies
+ *    of the other factor (FP32 accumulation), take residuals from u, and
+ *    re-evaluate a candidate as u + (new - old) . y^ (y^ the BF16 row), so
+ *    only the step's contribution is rounded.  u is recomputed exactly from
+ *    the FP32 factors every 8 sweeps; in between, the objectives a sweep
+ *    reports differ from the FP32 objective of the factors by that rounding
+ *    (a few parts in 1e6 on a converging fit).  glrm_grad_at of a BF16
+ *    model reads BF16 copies of both factors.
  *  - All work is enqueued on the stream given to glrm_create, in order.  An
  *    entry point returns once its work is enqueued unless it says it
  *    synchronises (it must when it hands a result back in host memory).
@@ -316,6 +319,16 @@ int glrm_batch_sweep(glrm_batch_t b, int32_t nsweeps, double *objectives_host, i
 int glrm_batch_autotune(glrm_batch_t b, int32_t reps, int32_t *tiles_x_host, int32_t *tiles_y_host);
 const char *glrm_batch_last_error(glrm_batch_t b);
 void glrm_batch_destroy(glrm_batch_t b);
+
+/* Tensor-core building block of the dense form: D = A B^T on the
+ * fifth-generation tensor cores (tcgen05.mma, BF16 operands staged in shared
+ * memory, FP32 accumulator in tensor memory).  A: M x K, B: N x K, both
+ * row-major BF16 (raw 16-bit words); D: M x N row-major FP32.  Device
+ * pointers; M a multiple of 128, N of 64, K of 16 with K <= 128
+ * (GLRM_ERR_RANGE otherwise).  Synchronises; GLRM_ERR_TIMEOUT if a wait for
+ * the tensor core hit its limit. */
+int glrm_tc_gemm_bf16(const void *A_dev, const void *B_dev, float *D_dev, int32_t M, int32_t N,
+                      int32_t K, void *stream);
 
 /* Instrumentation (not part of the method).  glrm_timing_enable(h, 1)
  * records a CUDA event on the handle's stream before every kernel the handle

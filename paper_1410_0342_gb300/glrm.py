@@ -72,6 +72,7 @@ def _load():
         "glrm_batch_get_steps": [p, p, p],
         "glrm_batch_sweep": [p, i32, p, i32],
         "glrm_batch_autotune": [p, i32, p, p],
+        "glrm_tc_gemm_bf16": [p, p, p, i32, i32, i32, p],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -280,6 +281,17 @@ def glrm_objective_noalloc(m, n, k, csr_rowptr, csr_colidx, csr_val, col_loss_de
                                        _ptr(col_loss_dev), int(rx[0]), float(rx[1]), int(ry[0]),
                                        float(ry[1]), _ptr(X), _ptr(Yt), _ptr(out),
                                        ctypes.c_void_p(stream.cuda_stream)))
+
+
+def glrm_tc_gemm_bf16(A, B, D, stream=None):
+    """D = A B^T on the tensor cores; A (M x K) and B (N x K) bf16 CUDA tensors,
+    D (M x N) float32."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    M, K = A.shape
+    N = B.shape[0]
+    _check(_lib.glrm_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(D), M, N, K,
+                                  ctypes.c_void_p(stream.cuda_stream)))
 
 
 def glrm_destroy(h):
