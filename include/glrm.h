@@ -138,6 +138,25 @@ int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host
                            const int32_t *csc_colptr_host, const int32_t *csc_rowidx_host,
                            const void *csc_val_host);
 
+/* Give the model a fully observed table instead: Omega = every (i, j), the
+ * data matrix of Section 2 with nothing missing.  A: m x n, row-major with
+ * leading dimension lda >= n (elements), FP32 (GLRM_FP32 models only;
+ * GLRM_ERR_ARG otherwise; GLRM_ERR_RANGE when k > 64).  The library copies A
+ * into rows padded to a multiple of 4 floats, validates it like an observed
+ * set (finite values, each column's values in its loss's domain) and resets
+ * the step sizes to 1/n (rows) and 1/m (columns).  Sweeps, objectives and
+ * gradients then run the dense form on the tensor cores: U = X Y, the loss
+ * derivatives R and R Y^T, X^T R (the contractions of Section 7.2's
+ * gradient) by tcgen05 MMAs on BF16 splits, FP32 accumulation: U from a
+ * three-part split x = hi + mid + lo and six products (error about 2^-25 of
+ * sum_c |x_c y_c|, FP32 quality), the gradient contractions from two-part
+ * splits and three products (about 2^-16 relative); everything else in FP32.  glrm_als_sweep and
+ * glrm_set_path return GLRM_ERR_STATE on a dense table; glrm_get_path reports
+ * GLRM_PATH_DENSE.  Synchronises.  A later glrm_set_observed replaces the
+ * table. */
+int glrm_set_dense(glrm_t h, const void *A_dev, int64_t lda);
+int glrm_set_dense_host(glrm_t h, const void *A_host, int64_t lda);
+
 /* Copy factors in: X_dev (m x k) and Yt_dev (n x k), row-major, element type
  * of the model.  Either may be NULL to leave that factor unchanged.  Step
  * sizes are not touched (glrm_reset_steps resets them). */
@@ -256,7 +275,8 @@ typedef enum {
     GLRM_PATH_FUSED = 2,
     GLRM_PATH_BLOCKED = 3,
     GLRM_PATH_MASKED = 4,
-    GLRM_PATH_MASKED_SPLIT = 5
+    GLRM_PATH_MASKED_SPLIT = 5,
+    GLRM_PATH_DENSE = 6 /* reported for a dense table (glrm_set_dense) */
 } glrm_path;
 int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path);
 int glrm_get_path(glrm_t h, int32_t *paths_host);

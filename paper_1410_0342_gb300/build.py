@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj, r.stderr
 
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, len(srcs), os.cpu_count() or 1))) as ex:
         results = list(ex.map(compile_one, srcs))
     if verbose:
         for _, err in results:

@@ -103,6 +103,7 @@ cudaError_t run_half(glrm_s *h, bool xstep) { return Engine<T>::half_step(h, xst
 
 cudaError_t half_step(glrm_s *h, bool xstep)
 {
+    if (h->dn.on) return dense_half_step(h, xstep);
     const Orient &o = xstep ? h->csr : h->csc;
     if (o.mode == kModeMasked)
         return h->prec == GLRM_FP64 ? Engine<double>::masked_half_step(h, xstep)
@@ -419,6 +420,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     h->have_omega = false;
     free_orient(h->csr);
     free_orient(h->csc);
+    dense_free(h);
     const size_t es = elem_size(h->prec);
     cudaStream_t st = h->stream;
     Orient &R = h->csr, &C = h->csc;
@@ -508,6 +510,70 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     CK(cudaStreamSynchronize(st));
     h->err.clear();
     return GLRM_OK;
+}
+
+// Fully observed table: Omega = every (i, j).  A copy with rows padded to a
+// multiple of 4 floats (16-byte aligned rows for the bulk copies), validated
+// like an observed set (finite, inside each column loss's domain).
+int set_dense_impl(glrm_s *h, const void *A, int64_t lda, cudaMemcpyKind kind)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!A) return fail(h, GLRM_ERR_ARG, "null table");
+    if (h->prec != GLRM_FP32) return fail(h, GLRM_ERR_ARG, "the dense form runs on GLRM_FP32 models");
+    if (lda < h->n) return fail(h, GLRM_ERR_ARG, "lda < n");
+    if (!dense_supported(h->k)) return fail(h, GLRM_ERR_RANGE, "the dense form supports k <= 64");
+    DeviceGuard dg(h->device);
+    h->have_omega = false;
+    free_orient(h->csr);
+    free_orient(h->csc);
+    dense_free(h);
+    cudaStream_t st = h->stream;
+    Dense &d = h->dn;
+    d.lda = (h->n + 3) / 4 * 4;
+    const size_t bytes = (size_t)h->m * d.lda * sizeof(float);
+    CK(cudaMalloc(&d.A, std::max<size_t>(bytes, 16)));
+    if (d.lda != h->n) CK(cudaMemsetAsync(d.A, 0, bytes, st));
+    CK(cudaMemcpy2DAsync(d.A, (size_t)d.lda * sizeof(float), A, (size_t)lda * sizeof(float),
+                         (size_t)h->n * sizeof(float), (size_t)h->m, kind, st));
+    int *flag = nullptr;
+    CK(cudaMalloc(&flag, sizeof(int)));
+    int hflag = 0;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_dense_validate(d.A, d.lda, h->m, h->n, h->loss_dev, flag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(flag);
+    if (e != cudaSuccess) {
+        dense_free(h);
+        return cuda_fail(h, e, "dense validation");
+    }
+    if (hflag) {
+        dense_free(h);
+        return fail(h, (hflag & 8) ? GLRM_ERR_NONFINITE : GLRM_ERR_OMEGA,
+                    (hflag & 8) ? "non-finite value in the table" : flag_message(hflag));
+    }
+    h->nnz = h->m * h->n;
+    e = dense_prepare(h);
+    if (e != cudaSuccess) {
+        dense_free(h);
+        free_orient(h->csr);
+        free_orient(h->csc);
+        return cuda_fail(h, e, "dense_prepare");
+    }
+    d.on = true;
+    int rc = alloc_scratch(h);
+    if (rc != GLRM_OK) return rc;
+    h->have_omega = true;
+    if ((e = dense_reset_steps(h)) != cudaSuccess) return cuda_fail(h, e, "reset_steps");
+    CK(cudaStreamSynchronize(st));
+    h->err.clear();
+    return GLRM_OK;
+}
+
+cudaError_t reset_steps_any(glrm_s *h)
+{
+    if (h->dn.on) return dense_reset_steps(h);
+    return h->prec == GLRM_FP64 ? Engine<double>::reset_steps(h) : Engine<float>::reset_steps(h);
 }
 
 }  // namespace
@@ -632,6 +698,16 @@ int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *rp, const int32
     return set_observed_impl(h, nnz, rp, ci, rv, cp, ri, cv, cudaMemcpyHostToDevice);
 }
 
+int glrm_set_dense(glrm_t h, const void *A, int64_t lda)
+{
+    return set_dense_impl(h, A, lda, cudaMemcpyDeviceToDevice);
+}
+
+int glrm_set_dense_host(glrm_t h, const void *A, int64_t lda)
+{
+    return set_dense_impl(h, A, lda, cudaMemcpyHostToDevice);
+}
+
 static int copy_factors(glrm_t h, void *X, void *Yt, const void *Xs, const void *Yts, cudaMemcpyKind kind,
                         bool sync)
 {
@@ -677,7 +753,7 @@ int glrm_reset_steps(glrm_t h)
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->prec == GLRM_FP64 ? Engine<double>::reset_steps(h) : Engine<float>::reset_steps(h);
+    cudaError_t e = reset_steps_any(h);
     return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "reset_steps");
 }
 
@@ -731,7 +807,8 @@ int glrm_objective_at(glrm_t h, const void *X, const void *Yt, double *out)
     if (!X || !Yt || !out) return fail(h, GLRM_ERR_ARG, "null pointer");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->prec == GLRM_FP64
+    cudaError_t e = h->dn.on ? dense_objective_at(h, (const float *)X, (const float *)Yt, out)
+                    : h->prec == GLRM_FP64
                         ? Engine<double>::objective_at(h, (const double *)X, (const double *)Yt, out)
                         : Engine<float>::objective_at(h, (const float *)X, (const float *)Yt, out);
     return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_objective_at");
@@ -758,7 +835,9 @@ int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, i
     if (include_reg && (h->rx_kind == kRegNonneg || h->ry_kind == kRegNonneg))
         return fail(h, GLRM_ERR_ARG, "the nonnegativity indicator has no gradient");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->prec == GLRM_FP64
+    cudaError_t e = h->dn.on ? dense_grad_at(h, (const float *)X, (const float *)Yt, (float *)GX, (float *)GYt,
+                                             include_reg != 0, scale)
+                    : h->prec == GLRM_FP64
                         ? Engine<double>::grad_at(h, (const double *)X, (const double *)Yt,
                                                   (double *)GX, (double *)GYt, include_reg != 0, scale)
                         : Engine<float>::grad_at(h, (const float *)X, (const float *)Yt, (float *)GX,
@@ -783,6 +862,7 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_als_sweep before glrm_set_observed");
     if (nsweeps < 0) return fail(h, GLRM_ERR_ARG, "nsweeps < 0");
+    if (h->dn.on) return fail(h, GLRM_ERR_STATE, "ALS runs on an observed set, not on a dense table");
     if (h->rx_kind != kRegQuad || h->ry_kind != kRegQuad || h->rx_w != h->ry_w || !(h->rx_w > 0.0))
         return fail(h, GLRM_ERR_ARG,
                     "ALS needs quadratic regularisers of equal weight gamma > 0 on X and Y");
@@ -877,6 +957,7 @@ int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path)
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     for (int p : {xstep_path, ystep_path})
         if (p < GLRM_PATH_AUTO || p > GLRM_PATH_MASKED_SPLIT) return fail(h, GLRM_ERR_ARG, "bad path");
+    if (h->dn.on) return fail(h, GLRM_ERR_STATE, "a dense table has one path");
     h->path_x = xstep_path;
     h->path_y = ystep_path;
     if (!h->have_omega) return GLRM_OK;
@@ -905,6 +986,10 @@ int glrm_get_path(glrm_t h, int32_t *paths_host)
 {
     if (!h || !paths_host) return fail(h, GLRM_ERR_ARG, "null argument");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    if (h->dn.on) {
+        paths_host[0] = paths_host[1] = GLRM_PATH_DENSE;
+        return GLRM_OK;
+    }
     auto code = [](const Orient &o) {
         if (o.mode == kModeMasked)
             return o.nunits == (o.nseg + 31) / 32 ? GLRM_PATH_MASKED : GLRM_PATH_MASKED_SPLIT;
@@ -965,6 +1050,7 @@ void glrm_destroy(glrm_t h)
         for (cudaEvent_t ev : h->timer.pool) cudaEventDestroy(ev);
         free_orient(h->csr);
         free_orient(h->csc);
+        dense_free(h);
         free_scratch(h->s);
         dfree(h->loss_dev);
         dfree(h->X);

@@ -1,0 +1,818 @@
+// Dense, fully observed form of the alternating proximal-gradient sweep
+// (Algorithm 2 of Udell et al., "Generalized Low Rank Models", with Omega =
+// every (i, j)) on the fifth-generation tensor cores.
+//
+// Naming: in a half-step the "own" factor F is the one being updated (X in
+// the X-step, Y in the Y-step) and the "other" factor W is held fixed.  Each
+// half-step is five launches:
+//   pack   W split into BF16 parts x = hi + mid + lo (+ at most 2^-26 |x|) in
+//          the tensor core's canonical K-major shared-memory layout: all three
+//          parts with K = k (B operand of GEMM1), hi and mid per 64-row chunk
+//          with K = the chunk rows (B operand of GEMM2);
+//   grad   per 128 own rows and a range of 64-wide chunks of the other
+//          dimension: U = F W^T (GEMM1: the six BF16 products of the split
+//          whose order is at least 2^-18, FP32 accumulation in tensor memory),
+//          L(U, A) and its derivative R against the A tile (staged by tensor
+//          TMA), R split hi + mid into tensor memory, G += R W (GEMM2: three
+//          products, R read from tensor memory);
+//   prox   f+ = prox(f - alpha g) per row / column (shared with the sparse form);
+//   loss   the candidate's losses (GEMM1 and L only);
+//   decide accept when the objective did not increase (shared with the
+//          sparse form).
+// Products U: the dropped terms (mid.lo, lo.mid, lo.lo) and the split
+// remainders are about 2^-25 of sum_c |f_c w_c|, below FP32's own rounding of
+// a k-term dot product, so losses and the accept / reject test see FP32
+// quality values.  Gradients: R and W split in two, three products, about
+// 2^-16 relative.
+//
+// Pipeline of one CTA (thread 0 issues every copy and MMA; 16 warps run the
+// per-entry work): GEMM1 runs two chunks ahead into a double-buffered
+// accumulator, so the tensor core computes U of chunk q + 1 while the warps
+// evaluate the losses of chunk q; W's GEMM1 parts are triple-buffered, its
+// GEMM2 parts and the A tiles double- (or more) buffered.
+#include <cuda.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "glrm_tc.cuh"
+
+namespace glrm {
+
+constexpr int kDnNT = 64;        // chunk of the other dimension (UMMA N of GEMM1, K of GEMM2)
+constexpr int kDnRows = 128;     // own rows per CTA (UMMA M)
+constexpr int kDnWarps = 16;     // warp w: TMEM lanes 32 (w % 4) .. + 31, chunk columns 16 (w / 4) .. + 15
+constexpr int kDnThreads = kDnWarps * 32;
+constexpr int kDnTmem = 256;     // TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), R at [192, 256)
+constexpr int kDnColG = 128, kDnColR = 192;
+constexpr int kDnMaxStages = 4;
+
+// Column loss with its parameters in FP32 (kind as int bits, Huber
+// threshold, ordinal level count, unused).
+using LossF = float4;
+
+struct DenseArgs {
+    int64_t nown, nother;
+    int k;
+    const float *F;           // own factor, nown x k
+    const __nv_bfloat16 *pk;  // other factor, K-major over k: parts hi, mid, lo (each pack_part)
+    const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid
+    int64_t pack_part;        // elements per part
+    const LossF *lossf;       // n column losses
+    const int32_t *gkind;     // per 16-column group: the kind shared by its columns, else -1
+    int parts, nA;
+    int64_t nchunks, per_part;  // chunks of the other dimension, chunks per part
+    float *part_grad;           // (nown * parts) x k
+    double *part_loss;          // nown * parts
+    int *err;
+};
+
+// Dynamic shared memory of one CTA: the A stages first (1024-byte aligned for
+// the swizzled boxes; 1024 bytes of slack align the base), then the own
+// factor's three parts, three stages of W's three GEMM1 parts, two stages of
+// W's two GEMM2 parts and three stages of the loss table.
+template <bool XSTEP, bool GRAD, int KP>
+struct DnSmem {
+    static constexpr size_t own = (size_t)kDnRows * KP * 2;  // one BF16 part
+    static constexpr size_t pk = (size_t)kDnNT * KP * 2;
+    static constexpr size_t pt = GRAD ? (size_t)KP * kDnNT * 2 : 0;
+    static constexpr size_t ls = XSTEP ? (size_t)kDnNT * sizeof(LossF) : 0;
+    static constexpr size_t a = (size_t)kDnNT * kDnRows * 4;  // 32 KB A tile
+    static constexpr size_t fixed = 3 * own + 9 * pk + 4 * pt + 3 * ls;
+    static size_t bytes(int nA) { return 1024 + fixed + (size_t)nA * a; }
+};
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v)
+{
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// 2-D tiled TMA load of one box into shared memory, completion on the mbarrier.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// x = hi + mid + lo in BF16 (each remainder exact in FP32).
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 &hi, __nv_bfloat16 &mid, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(hi);
+    mid = __float2bfloat16_rn(r1);
+    lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
+// One MMA with A read from tensor memory: D[taddr] (+)= A[a_taddr] B^T.
+__device__ __forceinline__ void umma_bf16_ta(uint32_t taddr, uint32_t a_taddr, uint64_t bdesc, uint32_t idesc,
+                                             bool accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(taddr),
+        "r"(a_taddr), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+        : "memory");
+}
+
+// Eight 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Losses and derivatives of 16 entries of one loss kind (KIND < 0: each
+// entry's own kind).  X-step: the entries are 16 columns (per-column
+// parameters in lf); Y-step: one column (parameters of `own`).  Entries
+// outside the table (bit clear in `valid`) give 0.
+template <int KIND, bool XSTEP>
+__device__ __forceinline__ void dn_losses(const float (&u)[16], const float (&a)[16], const LossF *lf, LossF own,
+                                          uint32_t valid, float (&rr)[16], float &lsum)
+{
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        const LossF sp = XSTEP ? lf[w] : own;
+        float L, d;
+        if constexpr (KIND >= 0)
+            d = loss_deriv_k<KIND, float>(u[w], a[w], sp.y, sp.z, L);
+        else
+            d = loss_deriv_kind<float>(__float_as_int(sp.x), u[w], a[w], sp.y, sp.z, L);
+        const bool v = (valid >> w) & 1u;
+        lsum += v ? L : 0.f;
+        rr[w] = v ? d : 0.f;
+    }
+}
+
+// One pass over a (128 own rows) x (range of chunks) block.  GRAD: partial
+// gradient rows and partial losses; otherwise partial losses only.
+// A tiles: X-step, two boxes of 32 columns x 128 own rows with the 128-byte
+// swizzle (16-byte unit u of row r at u ^ (r % 8): conflict-free row reads);
+// Y-step, one box of 128 own columns x 64 rows, unswizzled.
+template <bool XSTEP, bool GRAD, int KP>
+__global__ void __launch_bounds__(kDnThreads, 1)
+dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
+{
+    using SM = DnSmem<XSTEP, GRAD, KP>;
+    extern __shared__ __align__(1024) unsigned char dsm_dense[];
+    __shared__ uint64_t barA[kDnMaxStages], barP[3], barT[2], barG1[2], barG2;
+    __shared__ uint32_t tslot;
+    __shared__ double red[4][kDnRows];
+    unsigned char *base = dsm_dense + ((1024 - (smem_u32(dsm_dense) & 1023)) & 1023);
+    unsigned char *ast = base;                                   // A stage s at ast + s * a
+    unsigned char *fx = base + (size_t)p.nA * SM::a;             // fixed buffers
+    __nv_bfloat16 *own = reinterpret_cast<__nv_bfloat16 *>(fx);  // parts hi, mid, lo
+    unsigned char *pkst = fx + 3 * SM::own;                      // pk stage s at pkst + s * 3 pk
+    unsigned char *ptst = pkst + 9 * SM::pk;                     // pt stage s at ptst + s * 2 pt
+    unsigned char *lsst = ptst + 4 * SM::pt;                     // loss table stage s at lsst + s * ls
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, grp = warp >> 2;
+    const int orow = quarter * 32 + lane;
+    const int64_t o0 = (int64_t)blockIdx.x * kDnRows;
+    const int part = blockIdx.y;
+    const int64_t qb = (int64_t)part * p.per_part;
+    const int64_t qe = qb + p.per_part < p.nchunks ? qb + p.per_part : p.nchunks;
+    const int nq = (int)(qe - qb);
+    const int nA = p.nA;
+    const bool own_ok = o0 + orow < p.nown;
+    const int nown_t = (int)(p.nown - o0 < kDnRows ? p.nown - o0 : kDnRows);
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const int tb = grp * 16;  // this warp's columns of a chunk
+
+    if (warp == 0) tmem_alloc(&tslot, kDnTmem);
+    if (tid == 0) {
+        for (int s = 0; s < kDnMaxStages; ++s) mbar_init(&barA[s], 1);
+        for (int s = 0; s < 3; ++s) mbar_init(&barP[s], 1);
+        mbar_init(&barT[0], 1);
+        mbar_init(&barT[1], 1);
+        mbar_init(&barG1[0], 1);
+        mbar_init(&barG1[1], 1);
+        mbar_init(&barG2, 1);
+    }
+    // own rows, split in three, K-major core-matrix layout
+    for (int q = tid; q < kDnRows * KP; q += kDnThreads) {
+        const int r = q / KP, c = q - r * KP;
+        const float v = (r < nown_t && c < p.k) ? p.F[(o0 + r) * p.k + c] : 0.f;
+        __nv_bfloat16 hi, mid, lo;
+        split3(v, hi, mid, lo);
+        const int64_t ix = core_index(r, c, KP);
+        own[ix] = hi;
+        own[kDnRows * KP + ix] = mid;
+        own[2 * kDnRows * KP + ix] = lo;
+    }
+    // Y-step: this thread's column loss, and whether the warp shares one kind
+    LossF myspec = make_float4(__int_as_float(kLossQuad), 0.f, 0.f, 0.f);
+    if (!XSTEP && own_ok) myspec = p.lossf[o0 + orow];
+    int wkind = -1;
+    if constexpr (!XSTEP) {
+        const int kd = __float_as_int(myspec.x);
+        const int k0 = __shfl_sync(0xffffffffu, kd, 0);
+        wkind = __all_sync(0xffffffffu, kd == k0) ? k0 : -1;
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tslot;
+
+    // thread 0 issues every copy and MMA
+    int p_issued = 0, a_issued = 0, t_issued = 0, g1_issued = 0, g2_issued = 0;
+    bool ok0 = true;  // thread 0: every wait of its own succeeded
+    auto issue_pack = [&](int64_t q) {  // GEMM1's W parts (+ X-step column losses), stage q % 3
+        const int s = (int)((q - qb) % 3);
+        unsigned char *st = pkst + s * 3 * SM::pk;
+        const int64_t t0 = q * kDnNT;
+        const int nv = (int)(p.nother - t0 < kDnNT ? p.nother - t0 : kDnNT);
+        const unsigned bytes = (unsigned)(3 * SM::pk + (XSTEP ? nv * sizeof(LossF) : 0));
+        mbar_expect_tx(&barP[s], bytes);
+#pragma unroll
+        for (int w = 0; w < 3; ++w)
+            bulk_g2s(st + w * SM::pk, p.pk + w * p.pack_part + t0 * KP, (unsigned)SM::pk, &barP[s]);
+        if constexpr (XSTEP)
+            bulk_g2s(lsst + s * SM::ls, p.lossf + t0, (unsigned)(nv * sizeof(LossF)), &barP[s]);
+        ++p_issued;
+    };
+    auto issue_pt = [&](int64_t q) {  // GEMM2's W parts, stage q % 2
+        const int s = (int)((q - qb) & 1);
+        unsigned char *st = ptst + s * 2 * SM::pt;
+        mbar_expect_tx(&barT[s], (unsigned)(2 * SM::pt));
+        bulk_g2s(st, p.pt + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
+        bulk_g2s(st + SM::pt, p.pt + p.pack_part + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
+        ++t_issued;
+    };
+    auto issue_a = [&](int64_t q) {  // the A tile, stage q % nA (out-of-range rows / columns read as 0)
+        const int s = (int)((q - qb) % nA);
+        unsigned char *dst = ast + s * SM::a;
+        const int t0 = (int)(q * kDnNT);
+        mbar_expect_tx(&barA[s], (unsigned)SM::a);
+        if constexpr (XSTEP) {
+            tma_load_2d(dst, &amap, t0, (int)o0, &barA[s]);
+            tma_load_2d(dst + SM::a / 2, &amap, t0 + 32, (int)o0, &barA[s]);
+        } else {
+            tma_load_2d(dst, &amap, (int)o0, t0, &barA[s]);
+        }
+        ++a_issued;
+    };
+    // GEMM1 of chunk q into accumulator buffer (q - qb) % 2, once its W parts are in
+    auto issue_gemm1 = [&](int64_t q) {
+        const int c = (int)(q - qb);
+        const int s = c % 3, b = c & 1;
+        if (!ok0 || !mbar_wait_bounded(&barP[s], (unsigned)(c / 3) & 1u)) {
+            ok0 = false;
+            return;
+        }
+        tc_fence_after();
+        const uint32_t idesc = umma_idesc_bf16(kDnRows, kDnNT);
+        const __nv_bfloat16 *w = reinterpret_cast<const __nv_bfloat16 *>(pkst + s * 3 * SM::pk);
+        constexpr uint32_t sbo = KP * 16;
+        constexpr int own_part = kDnRows * KP, w_part = kDnNT * KP;
+        // (own part, W part), smallest products first; hi . hi last
+        const int pa[6] = {1, 0, 2, 0, 1, 0};
+        const int pb[6] = {1, 2, 0, 1, 0, 0};
+#pragma unroll
+        for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+            for (int ks = 0; ks < KP / 16; ++ks)
+                umma_bf16(taddr + (uint32_t)(b * kDnNT), umma_desc(own + pa[pr] * own_part + ks * 128, 128, sbo),
+                          umma_desc(w + pb[pr] * w_part + ks * 128, 128, sbo), idesc, pr > 0 || ks > 0);
+        umma_commit(&barG1[b]);
+        ++g1_issued;
+    };
+    // GEMM2 of chunk q: G += R W, R from tensor memory
+    auto issue_gemm2 = [&](int64_t q) {
+        const int c = (int)(q - qb);
+        const int s = c & 1;
+        if (!ok0 || !mbar_wait_bounded(&barT[s], (unsigned)(c >> 1) & 1u)) {
+            ok0 = false;
+            return;
+        }
+        tc_fence_after();
+        const uint32_t idesc = umma_idesc_bf16(kDnRows, KP);
+        constexpr uint32_t sbo = kDnNT * 16;
+        constexpr int tpart = KP * kDnNT;
+        const __nv_bfloat16 *wt = reinterpret_cast<const __nv_bfloat16 *>(ptst + s * 2 * SM::pt);
+        // (R part, W part): mid.hi, hi.mid, hi.hi; a K = 16 step of R is 8 columns
+        const int pa[3] = {1, 0, 0};
+        const int pb[3] = {0, 1, 0};
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+            for (int ks = 0; ks < kDnNT / 16; ++ks)
+                umma_bf16_ta(taddr + kDnColG, taddr + (uint32_t)(kDnColR + pa[pr] * 32 + ks * 8),
+                             umma_desc(wt + pb[pr] * tpart + ks * 128, 128, sbo), idesc, c > 0 || pr > 0 || ks > 0);
+        umma_commit(&barG2);
+        ++g2_issued;
+    };
+    if (tid == 0) {
+        for (int s = 0; s < nA && s < nq; ++s) issue_a(qb + s);
+        for (int s = 0; s < 3 && s < nq; ++s) issue_pack(qb + s);
+        if (GRAD) {
+            issue_pt(qb);
+            if (nq > 1) issue_pt(qb + 1);
+        }
+        issue_gemm1(qb);
+        if (nq > 1) issue_gemm1(qb + 1);
+    }
+
+    bool ok = true;
+    bool fail = false;
+    double lacc = 0.0;
+    for (int it = 0; it < nq; ++it) {
+        const int64_t q = qb + it;
+        const int b = it & 1;
+        const int sA = it % nA;
+        ok = ok && mbar_wait_bounded(&barG1[b], (unsigned)(it >> 1) & 1u);
+        if (XSTEP) ok = ok && mbar_wait_bounded(&barP[it % 3], (unsigned)(it / 3) & 1u);  // loss table
+        ok = ok && mbar_wait_bounded(&barA[sA], (unsigned)(it / nA) & 1u);
+        tc_fence_after();
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld / st below are warp-collective
+        float lsum = 0.f;
+        float rr[16];
+        if (ok) {
+            const unsigned char *as = ast + sA * SM::a;
+            const int64_t t0 = q * kDnNT;
+            float u[16], a[16];
+            tmem_ld16(taddr + lane_base + (uint32_t)(b * kDnNT + tb), u);
+            if constexpr (XSTEP) {
+                // box tb / 32, row orow: 16-byte units (tb % 32) / 4 .. + 3, swizzled
+                const unsigned char *row = as + (tb >> 5) * (SM::a / 2) + orow * 128;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float4 v =
+                        *reinterpret_cast<const float4 *>(row + ((((tb & 31) >> 2) + w) ^ (orow & 7)) * 16);
+                    a[4 * w] = v.x;
+                    a[4 * w + 1] = v.y;
+                    a[4 * w + 2] = v.z;
+                    a[4 * w + 3] = v.w;
+                }
+            } else {
+                const float *af = reinterpret_cast<const float *>(as);
+#pragma unroll
+                for (int w = 0; w < 16; ++w) a[w] = af[(tb + w) * kDnRows + orow];
+            }
+            const int64_t nv = p.nother - t0 - tb;  // valid columns from tb on
+            const uint32_t valid = !own_ok ? 0u : (nv >= 16 ? 0xffffu : (nv <= 0 ? 0u : (1u << nv) - 1u));
+            const LossF *lf = reinterpret_cast<const LossF *>(lsst + (it % 3) * SM::ls) + tb;
+            const int kind = XSTEP ? __ldg(p.gkind + ((t0 + tb) >> 4)) : wkind;
+            switch (kind) {
+            case kLossQuad: dn_losses<kLossQuad, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+            case kLossHuber: dn_losses<kLossHuber, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+            case kLossHinge: dn_losses<kLossHinge, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+            case kLossLogistic: dn_losses<kLossLogistic, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+            case kLossOrdinal: dn_losses<kLossOrdinal, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+            default: dn_losses<-1, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+            }
+        }
+        lacc += (double)lsum;
+        if constexpr (GRAD) {
+            // R of the previous chunk is no longer read once its GEMM2 is done
+            if (it > 0) ok = ok && mbar_wait_bounded(&barG2, (unsigned)(it - 1) & 1u);
+            tc_fence_after();
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                uint32_t hi[8], mi[8];
+#pragma unroll
+                for (int w = 0; w < 16; w += 2) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[w], rr[w + 1]);
+                    const float2 hf = __bfloat1622float2(h2);
+                    hi[w / 2] = bf2_bits(h2);
+                    mi[w / 2] = bf2_bits(__floats2bfloat162_rn(rr[w] - hf.x, rr[w + 1] - hf.y));
+                }
+                tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + tb / 2), hi);
+                tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + 32 + tb / 2), mi);
+                tmem_wait_st();
+            }
+        }
+        tc_fence_before();
+        fail = __syncthreads_or(!ok) != 0;
+        tc_fence_after();
+        if (fail) break;
+        if (tid == 0) {
+            // A stage sA is consumed: it takes chunk q + nA
+            if (it + nA < nq) issue_a(q + nA);
+            if (GRAD) {
+                issue_gemm2(q);
+                if (it + 1 < nq && it >= 1) issue_pt(q + 1);
+            }
+            // accumulator buffer b is consumed: GEMM1 of chunk q + 2 goes there
+            if (it + 2 < nq) issue_gemm1(q + 2);
+            // W stage of chunk q (GEMM1 done) takes chunk q + 3
+            if (it + 3 < nq) issue_pack(q + 3);
+        }
+    }
+    if (GRAD && !fail) {
+        ok = ok && mbar_wait_bounded(&barG2, (unsigned)(nq - 1) & 1u);
+        tc_fence_after();
+    }
+    if (tid == 0) ok = ok && ok0;
+    fail = __syncthreads_or(!ok) != 0;
+    if (!fail) {
+        red[grp][orow] = lacc;
+        if (GRAD && grp == 0) {
+            float *g = p.part_grad + ((o0 + orow) * p.parts + part) * p.k;
+#pragma unroll
+            for (int bb = 0; bb < KP / 16; ++bb) {
+                float v[16];
+                tmem_ld16(taddr + lane_base + (uint32_t)(kDnColG + 16 * bb), v);
+                if (own_ok) {
+#pragma unroll
+                    for (int w = 0; w < 16; ++w)
+                        if (16 * bb + w < p.k) g[16 * bb + w] = v[w];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!fail && grp == 0 && own_ok)
+        p.part_loss[(o0 + orow) * p.parts + part] = red[0][orow] + red[1][orow] + red[2][orow] + red[3][orow];
+    if (fail && tid == 0) {
+        atomicOr(p.err, 1);
+        // wait (bounded) for the last copy into each stage and the last MMA
+        // batches: every earlier one completed before a later one was issued
+        for (int c = p_issued - 3 > 0 ? p_issued - 3 : 0; c < p_issued; ++c)
+            mbar_wait_bounded(&barP[c % 3], (unsigned)(c / 3) & 1u);
+        for (int c = a_issued - nA > 0 ? a_issued - nA : 0; c < a_issued; ++c)
+            mbar_wait_bounded(&barA[c % nA], (unsigned)(c / nA) & 1u);
+        for (int c = t_issued - 2 > 0 ? t_issued - 2 : 0; c < t_issued; ++c)
+            mbar_wait_bounded(&barT[c & 1], (unsigned)(c >> 1) & 1u);
+        for (int c = g1_issued - 2 > 0 ? g1_issued - 2 : 0; c < g1_issued; ++c)
+            mbar_wait_bounded(&barG1[c & 1], (unsigned)(c >> 1) & 1u);
+        if (g2_issued > 0) mbar_wait_bounded(&barG2, (unsigned)(g2_issued - 1) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(taddr, kDnTmem);
+    }
+}
+
+// The other factor W (rows x k, FP32) split x = hi + mid + lo into both packed
+// layouts: K-major over k (row r, coordinate c of part w at
+// w pk_part + core_index(r, c, KP)), all three parts; and, per chunk of kDnNT
+// rows, K-major over the chunk rows (chunk q, element (c, t) of part w at
+// w pt_part + q KP kDnNT + core_index(c, t, kDnNT)), parts hi and mid.  Rows
+// from `rows` to rows_pad and coordinates from k to KP are zero.
+static __global__ void dense_pack_kernel(const float *__restrict__ W, int64_t rows, int k, int KP,
+                                         int64_t rows_pad, int64_t part, __nv_bfloat16 *__restrict__ pk,
+                                         __nv_bfloat16 *__restrict__ pt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows_pad * KP) return;
+    const int64_t r = i / KP;
+    const int c = (int)(i - r * KP);
+    const float v = (r < rows && c < k) ? W[r * k + c] : 0.f;
+    __nv_bfloat16 hi, mid, lo;
+    split3(v, hi, mid, lo);
+    const int64_t ik = core_index(r, c, KP);
+    pk[ik] = hi;
+    pk[part + ik] = mid;
+    pk[2 * part + ik] = lo;
+    const int64_t q = r / kDnNT;
+    const int t = (int)(r - q * kDnNT);
+    const int64_t it = q * KP * kDnNT + core_index(c, t, kDnNT);
+    pt[it] = hi;
+    pt[part + it] = mid;
+}
+
+// Values outside a column loss's domain (flag 64) or not finite (flag 8).
+static __global__ void dense_validate_kernel(const float *__restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                             const LossSpec *__restrict__ loss, int *__restrict__ flag)
+{
+    int f = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m * n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n, j = i - r * n;
+        const float a = A[r * lda + j];
+        if (!isfinite(a)) {
+            f |= 8;
+            continue;
+        }
+        const LossSpec s = loss[j];
+        if ((s.kind == kLossHinge || s.kind == kLossLogistic) && a != 1.f && a != -1.f) f |= 64;
+        if (s.kind == kLossOrdinal && (a != floorf(a) || a < 1.f || a > (float)s.levels)) f |= 64;
+    }
+    if (f) atomicOr(flag, f);
+}
+
+static __global__ void dense_alpha_kernel(float *__restrict__ alpha, int64_t nseg, float value)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nseg) alpha[s] = value;
+}
+
+static __global__ void dense_segchunk_kernel(int32_t *__restrict__ sc, int64_t nseg, int parts)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s <= nseg) sc[s] = (int32_t)(s * parts);
+}
+
+namespace {
+
+int dense_width(int k)
+{
+    for (int K : {16, 32, 48, 64})
+        if (k <= K) return K;
+    return 0;
+}
+
+template <bool XSTEP, bool GRAD, int KP>
+cudaError_t launch_dense_kp(glrm_s *h, const DenseArgs &a, int nA, unsigned tiles)
+{
+    const size_t smem = DnSmem<XSTEP, GRAD, KP>::bytes(nA);
+    cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(XSTEP ? h->dn.tmap_x : h->dn.tmap_y);
+    dense_pass_kernel<XSTEP, GRAD, KP>
+        <<<dim3(tiles, (unsigned)a.parts), kDnThreads, smem, h->stream>>>(a, *map);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+// A stages that fit next to the fixed buffers and the kernel's static shared
+// memory (at most kDnMaxStages; fewer than 2 is refused by the caller).
+template <bool XSTEP, bool GRAD, int KP>
+int stages_kp(int optin)
+{
+    using SM = DnSmem<XSTEP, GRAD, KP>;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, dense_pass_kernel<XSTEP, GRAD, KP>) != cudaSuccess) return 0;
+    if ((size_t)optin < fa.sharedSizeBytes) return 0;
+    const size_t room = (size_t)optin - fa.sharedSizeBytes;
+    if (room < SM::bytes(0)) return 0;
+    const int n = (int)((room - SM::bytes(0)) / SM::a);
+    return n < kDnMaxStages ? n : kDnMaxStages;
+}
+
+template <bool XSTEP, bool GRAD>
+cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *part_loss)
+{
+    const Dense &d = h->dn;
+    DenseArgs a;
+    a.nown = XSTEP ? h->m : h->n;
+    a.nother = XSTEP ? h->n : h->m;
+    a.k = h->k;
+    a.F = F;
+    a.pk = d.pk;
+    a.pt = d.pt;
+    a.pack_part = d.pack_part;
+    a.lossf = d.lossf;
+    a.gkind = d.gkind;
+    a.parts = XSTEP ? d.parts_x : d.parts_y;
+    a.nchunks = (a.nother + kDnNT - 1) / kDnNT;
+    a.per_part = XSTEP ? d.per_part_x : d.per_part_y;
+    a.part_grad = part_grad;
+    a.part_loss = part_loss;
+    a.err = h->s.err;
+    const unsigned tiles = (unsigned)((a.nown + kDnRows - 1) / kDnRows);
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (e != cudaSuccess) return e;
+#define GLRM_DENSE_CASE(KK)                                                   \
+    if (d.KP == KK) {                                                         \
+        a.nA = stages_kp<XSTEP, GRAD, KK>(optin);                             \
+        if (a.nA < 2) return cudaErrorInvalidConfiguration;                   \
+        return launch_dense_kp<XSTEP, GRAD, KK>(h, a, a.nA, tiles);           \
+    }
+    GLRM_DENSE_CASE(16)
+    GLRM_DENSE_CASE(32)
+    GLRM_DENSE_CASE(48)
+    GLRM_DENSE_CASE(64)
+#undef GLRM_DENSE_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dense_pack(glrm_s *h, const float *W, int64_t rows)
+{
+    const Dense &d = h->dn;
+    const int64_t rows_pad = (rows + kDnRows - 1) / kDnRows * kDnRows;
+    const int64_t total = rows_pad * d.KP;
+    tmark(h, "dense_pack");
+    dense_pack_kernel<<<(unsigned)((total + 255) / 256), 256, 0, h->stream>>>(W, rows, h->k, d.KP, rows_pad,
+                                                                              d.pack_part, d.pk, d.pt);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+// Parts of the other dimension per own tile: about four CTAs per SM in all,
+// no part empty.
+void choose_parts(int64_t nown, int64_t nother, int sms, int &parts, int64_t &per_part)
+{
+    const int64_t tiles = (nown + kDnRows - 1) / kDnRows;
+    const int64_t nch = std::max<int64_t>(1, (nother + kDnNT - 1) / kDnNT);
+    int64_t want = (4LL * sms + tiles - 1) / tiles;
+    want = std::max<int64_t>(1, std::min<int64_t>(want, nch));
+    per_part = (nch + want - 1) / want;
+    parts = (int)((nch + per_part - 1) / per_part);
+}
+
+}  // namespace
+
+bool dense_supported(int k) { return dense_width(k) != 0; }
+
+void dense_free(glrm_s *h)
+{
+    Dense &d = h->dn;
+    for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf, (void *)d.gkind})
+        if (p) cudaFree(p);
+    d = Dense();
+}
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps of A (FP32, dims n x m, row pitch lda): X-step boxes of 32
+// columns x 128 rows with the 128-byte swizzle, Y-step boxes of 128 columns x
+// 64 rows.  Out-of-range elements load as zero.
+cudaError_t encode_maps(glrm_s *h)
+{
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeTiled>(fn);
+    }
+    Dense &d = h->dn;
+    const cuuint64_t dims[2] = {(cuuint64_t)h->n, (cuuint64_t)h->m};
+    const cuuint64_t strides[1] = {(cuuint64_t)d.lda * sizeof(float)};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint32_t box_x[2] = {32, (cuuint32_t)kDnRows};
+    const cuuint32_t box_y[2] = {(cuuint32_t)kDnRows, (cuuint32_t)kDnNT};
+    CUresult r = encode(reinterpret_cast<CUtensorMap *>(d.tmap_x), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.A, dims,
+                        strides, box_x, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    r = encode(reinterpret_cast<CUtensorMap *>(d.tmap_y), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.A, dims, strides,
+               box_y, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// Packs, part split and the segment -> partial-slot tables the shared prox
+// and decide kernels read (segment s owns slots s * parts .. s * parts + parts).
+cudaError_t dense_prepare(glrm_s *h)
+{
+    Dense &d = h->dn;
+    d.KP = dense_width(h->k);
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    choose_parts(h->m, h->n, sms, d.parts_x, d.per_part_x);
+    choose_parts(h->n, h->m, sms, d.parts_y, d.per_part_y);
+    const int64_t rows_pad = (std::max(h->m, h->n) + kDnRows - 1) / kDnRows * kDnRows;
+    d.pack_part = rows_pad * d.KP;
+    if ((e = cudaMalloc(&d.pk, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.pt, 2 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
+    if ((e = encode_maps(h)) != cudaSuccess) return e;
+    // column losses in FP32, and the kind each 16-column group shares (-1:
+    // mixed; groups past n count as quadratic)
+    std::vector<float4> lf(h->n);
+    for (int64_t j = 0; j < h->n; ++j) {
+        const LossSpec &L = h->loss_host[j];
+        int32_t kb = L.kind;
+        float kf;
+        memcpy(&kf, &kb, sizeof kf);
+        lf[j] = make_float4(kf, (float)L.param, (float)L.levels, 0.f);
+    }
+    const int64_t ngroups = (h->n + kDnNT - 1) / kDnNT * (kDnNT / 16);
+    std::vector<int32_t> gk(ngroups, kLossQuad);
+    for (int64_t g = 0; g * 16 < h->n; ++g) {
+        int32_t kd = h->loss_host[g * 16].kind;
+        for (int64_t j = g * 16; j < std::min<int64_t>(h->n, g * 16 + 16); ++j)
+            if (h->loss_host[j].kind != kd) kd = -1;
+        gk[g] = kd;
+    }
+    if ((e = cudaMalloc(&d.lossf, (size_t)h->n * sizeof(float4))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.gkind, (size_t)ngroups * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(d.lossf, lf.data(), lf.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(d.gkind, gk.data(), gk.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    Orient &R = h->csr, &C = h->csc;
+    R.nseg = h->m;
+    C.nseg = h->n;
+    R.nchunks = h->m * d.parts_x;  // partial slots, for the scratch sizes
+    C.nchunks = h->n * d.parts_y;
+    if ((e = cudaMalloc(&R.segchunk, (size_t)(h->m + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&C.segchunk, (size_t)(h->n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+    dense_segchunk_kernel<<<(unsigned)((h->m + 256) / 256), 256, 0, h->stream>>>(R.segchunk, h->m, d.parts_x);
+    dense_segchunk_kernel<<<(unsigned)((h->n + 256) / 256), 256, 0, h->stream>>>(C.segchunk, h->n, d.parts_y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_validate(const float *A, int64_t lda, int64_t m, int64_t n, const LossSpec *loss,
+                                  int *flag, cudaStream_t st)
+{
+    const int64_t total = m * n;
+    const unsigned nb = (unsigned)std::min<int64_t>(4096, std::max<int64_t>(1, (total + 255) / 256));
+    dense_validate_kernel<<<nb, 256, 0, st>>>(A, lda, m, n, loss, flag);
+    return cudaGetLastError();
+}
+
+// alpha = 1 / max(n_i, 1): every row has n observed entries, every column m.
+cudaError_t dense_reset_steps(glrm_s *h)
+{
+    dense_alpha_kernel<<<(unsigned)((h->m + 255) / 256), 256, 0, h->stream>>>(
+        (float *)h->alpha_x, h->m, 1.f / (float)std::max<int64_t>(h->n, 1));
+    dense_alpha_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(
+        (float *)h->alpha_y, h->n, 1.f / (float)std::max<int64_t>(h->m, 1));
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t dense_half_step(glrm_s *h, bool xstep)
+{
+    const Orient &o = xstep ? h->csr : h->csc;
+    float *F = (float *)(xstep ? h->X : h->Yt);
+    const float *W = (const float *)(xstep ? h->Yt : h->X);
+    float *alpha = (float *)(xstep ? h->alpha_x : h->alpha_y);
+    const int rk = xstep ? h->rx_kind : h->ry_kind;
+    const float rw = (float)(xstep ? h->rx_w : h->ry_w);
+    Scratch &s = h->s;
+    cudaStream_t st = h->stream;
+    cudaError_t e = dense_pack(h, W, xstep ? h->n : h->m);
+    if (e != cudaSuccess) return e;
+    tmark(h, xstep ? "dense_grad_x" : "dense_grad_y");
+    e = xstep ? launch_dense<true, true>(h, F, (float *)s.part_grad, s.part_loss)
+              : launch_dense<false, true>(h, F, (float *)s.part_grad, s.part_loss);
+    if (e != cudaSuccess) return e;
+    const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
+    tmark(h, xstep ? "prox_x" : "prox_y");
+    prox_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const float *)s.part_grad,
+                                                           s.part_loss, F, alpha, h->k, rk, rw,
+                                                           (float *)s.cand, s.f_old, s.r_old, s.r_new);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tmark(h, xstep ? "dense_loss_x" : "dense_loss_y");
+    e = xstep ? launch_dense<true, false>(h, (const float *)s.cand, nullptr, s.part_loss2)
+              : launch_dense<false, false>(h, (const float *)s.cand, nullptr, s.part_loss2);
+    if (e != cudaSuccess) return e;
+    tmark(h, xstep ? "decide_x" : "decide_y");
+    decide_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
+        o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F, alpha, h->k,
+        xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y, xstep ? s.acc_x : s.acc_y);
+    tmark(h, nullptr);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, double *out)
+{
+    Scratch &s = h->s;
+    cudaError_t e = dense_pack(h, Yt, h->n);
+    if (e != cudaSuccess) return e;
+    tmark(h, "dense_objective");
+    if ((e = launch_dense<true, false>(h, X, nullptr, s.part_loss)) != cudaSuccess) return e;
+    tmark(h, "reduce_stage1");
+    reduce_stage1<float><<<kRedBlocks, 256, 0, h->stream>>>(
+        s.part_loss, h->m * h->dn.parts_x, nullptr, 0, X, h->m, h->rx_kind, (float)h->rx_w, Yt, h->n,
+        h->ry_kind, (float)h->ry_w, h->k, nullptr, 0, nullptr, 0, s.red_part, s.red_cnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tmark(h, "reduce_stage2");
+    reduce_stage2<<<1, 256, 0, h->stream>>>(s.red_part, s.red_cnt, kRedBlocks, out, nullptr);
+    tmark(h, nullptr);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t dense_grad_at(glrm_s *h, const float *X, const float *Yt, float *GX, float *GYt, bool reg,
+                          const double *scale)
+{
+    Scratch &s = h->s;
+    cudaError_t e = dense_pack(h, Yt, h->n);
+    if (e != cudaSuccess) return e;
+    tmark(h, "dense_grad_x");
+    if ((e = launch_dense<true, true>(h, X, (float *)s.part_grad, s.part_loss)) != cudaSuccess) return e;
+    tmark(h, "grad_seg_x");
+    seg_grad_kernel<float><<<blocks_for(h->m, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
+        h->m, h->csr.segchunk, (const float *)s.part_grad, X, h->k, h->rx_kind, (float)h->rx_w, reg, scale, GX);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = dense_pack(h, X, h->m)) != cudaSuccess) return e;
+    tmark(h, "dense_grad_y");
+    if ((e = launch_dense<false, true>(h, Yt, (float *)s.part_grad, s.part_loss)) != cudaSuccess) return e;
+    tmark(h, "grad_seg_y");
+    seg_grad_kernel<float><<<blocks_for(h->n, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
+        h->n, h->csc.segchunk, (const float *)s.part_grad, Yt, h->k, h->ry_kind, (float)h->ry_w, reg, scale,
+        GYt);
+    tmark(h, nullptr);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace glrm

@@ -36,25 +36,24 @@ template <> __device__ __forceinline__ double xinf<double>() { return __longlong
 //   hinge (1 - a u)_+                                      Sec. 5.2
 //   logistic log(1 + exp(-a u)), overflow-free form        Sec. 5.2
 //   ordinal hinge over levels 1..d                         eq. ord-pca
-template <class T>
-__device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
+// loss_deriv_k: one kind, its parameters already in T (param: the Huber
+// threshold; levels: the ordinal level count; others ignore them).
+template <int KIND, class T>
+__device__ __forceinline__ T loss_deriv_k(T u, T a, T param, T levels, T &L)
 {
-    switch (s.kind) {
-    case kLossQuad: {
+    if constexpr (KIND == kLossQuad) {
         T r = u - a;
         L = r * r;
         return T(2) * r;
-    }
-    case kLossHuber: {
-        T x = u - a, d = T(s.param), ax = fabs(x);
+    } else if constexpr (KIND == kLossHuber) {
+        T x = u - a, d = param, ax = fabs(x);
         if (ax <= d) {
             L = T(0.5) * x * x;
             return x;
         }
         L = d * (ax - T(0.5) * d);
         return x > T(0) ? d : -d;
-    }
-    case kLossHinge: {
+    } else if constexpr (KIND == kLossHinge) {
         T z = T(1) - a * u;
         if (z > T(0)) {
             L = z;
@@ -62,21 +61,19 @@ __device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
         }
         L = T(0);
         return T(0);
-    }
-    case kLossLogistic: {
+    } else if constexpr (KIND == kLossLogistic) {
         // z = -a u; log(1 + e^z) = max(z, 0) + log1p(e^{-|z|});
         // derivative -a sigma(z) with sigma evaluated on the stable side.
         T z = -a * u, e = xexp(-fabs(z));
         L = fmax(z, T(0)) + xlog1p(e);
         T sg = z >= T(0) ? T(1) / (T(1) + e) : e / (T(1) + e);
         return -a * sg;
-    }
-    default: {
+    } else {
         // Ordinal hinge in closed form.  A term (1 - u + a')_+ with a' < a is
         // active (> 0) exactly for a' >= floor(u); a term (1 + u - a')_+ with
         // a' > a exactly for a' <= ceil(u).  With n1, n2 active terms over the
         // integer ranges [lo1, hi1], [lo2, hi2] the sums are arithmetic series.
-        const T d = T(s.levels);
+        const T d = levels;
         const T lev = fmin(fmax(a, T(1)), d);  // a is validated to 1..d at set-up
         const T lo1 = fmax(T(1), floor(u)), hi1 = lev - T(1);
         const T n1 = fmax(T(0), hi1 - lo1 + T(1));
@@ -85,7 +82,25 @@ __device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
         L = n1 * (T(1) - u) + T(0.5) * n1 * (lo1 + hi1) + n2 * (T(1) + u) - T(0.5) * n2 * (lo2 + hi2);
         return n2 - n1;
     }
+}
+
+// L(u, a) into *L and dL/du as the return value, for a runtime kind.
+template <class T>
+__device__ __forceinline__ T loss_deriv_kind(int kind, T u, T a, T param, T levels, T &L)
+{
+    switch (kind) {
+    case kLossQuad: return loss_deriv_k<kLossQuad, T>(u, a, param, levels, L);
+    case kLossHuber: return loss_deriv_k<kLossHuber, T>(u, a, param, levels, L);
+    case kLossHinge: return loss_deriv_k<kLossHinge, T>(u, a, param, levels, L);
+    case kLossLogistic: return loss_deriv_k<kLossLogistic, T>(u, a, param, levels, L);
+    default: return loss_deriv_k<kLossOrdinal, T>(u, a, param, levels, L);
     }
+}
+
+template <class T>
+__device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
+{
+    return loss_deriv_kind<T>(s.kind, u, a, T(s.param), T(s.levels), L);
 }
 
 // argmin_a L(u, a) (Sec. 5.3).  For the ordinal hinge,

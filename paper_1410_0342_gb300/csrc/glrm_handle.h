@@ -94,6 +94,23 @@ struct Scratch {
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 
+// Dense (fully observed) table and the tensor-core form's buffers.
+struct Dense {
+    bool on = false;
+    float *A = nullptr;  // m x lda, lda = n rounded up to 4, padding zero
+    int64_t lda = 0;
+    int KP = 0;  // k padded to a multiple of 16
+    int parts_x = 1, parts_y = 1;         // partial slots per row / column
+    int64_t per_part_x = 0, per_part_y = 0;  // 64-wide chunks per part
+    __nv_bfloat16 *pk = nullptr;  // packed other factor, K-major over k (parts hi, mid, lo)
+    __nv_bfloat16 *pt = nullptr;  // packed other factor, K-major over chunk rows (parts hi, mid)
+    int64_t pack_part = 0;        // elements per part
+    float4 *lossf = nullptr;      // n column losses in FP32 {kind bits, param, levels, 0}
+    int32_t *gkind = nullptr;     // per 16-column group: the shared kind, or -1
+    alignas(64) unsigned char tmap_x[128] = {};  // CUtensorMap of A, X-step boxes
+    alignas(64) unsigned char tmap_y[128] = {};  // CUtensorMap of A, Y-step boxes
+};
+
 // Optional per-launch timing: an event is recorded before every kernel launch
 // (tagged with the kernel's name) and after the last one, so consecutive
 // events on the handle's stream bracket exactly one kernel.
@@ -122,6 +139,7 @@ struct glrm_s {
     int64_t nnz = 0;
     glrm::Orient csr, csc;
     glrm::Scratch s;
+    glrm::Dense dn;
     glrm::Timer timer;
     long long launches = 0;  // kernels enqueued since creation
     int64_t sweeps_done = 0;
@@ -166,6 +184,17 @@ cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep);
 cudaError_t launch_perm(const Orient &o, const Orient &other, cudaStream_t st);
 cudaError_t launch_validate_domain(const Orient &csc, int prec, const LossSpec *loss, int *flag,
                                    cudaStream_t st);
+// Dense, fully observed form (tensor cores, FP32 models).
+bool dense_supported(int k);
+void dense_free(glrm_s *h);
+cudaError_t dense_prepare(glrm_s *h);
+cudaError_t launch_dense_validate(const float *A, int64_t lda, int64_t m, int64_t n, const LossSpec *loss,
+                                  int *flag, cudaStream_t st);
+cudaError_t dense_reset_steps(glrm_s *h);
+cudaError_t dense_half_step(glrm_s *h, bool xstep);
+cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, double *out);
+cudaError_t dense_grad_at(glrm_s *h, const float *X, const float *Yt, float *GX, float *GYt, bool reg,
+                          const double *scale);
 cudaError_t launch_build_runptr(const Orient &o, cudaStream_t st);
 cudaError_t launch_mt_count(const Orient &o, int32_t *cnt, cudaStream_t st);
 cudaError_t launch_mt_build(const Orient &o, int prec, cudaStream_t st);

@@ -90,7 +90,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ int core_index(int r, int c, int K)
+__host__ __device__ __forceinline__ int64_t core_index(int64_t r, int c, int K)
 {
     return ((r >> 3) * (K >> 3) + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
 }
@@ -103,7 +103,7 @@ __device__ __forceinline__ int core_index(int r, int c, int K)
 constexpr int kTcMaxK = 128;
 constexpr int kTcNT = 64;
 
-__global__ void __launch_bounds__(128, 1)
+static __global__ void __launch_bounds__(128, 1)
 tc_gemm_bf16_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
                     float *__restrict__ D, int M, int N, int K, int *__restrict__ err)
 {

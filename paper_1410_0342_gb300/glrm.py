@@ -21,7 +21,7 @@ GLRM_LOSS_QUAD, GLRM_LOSS_HUBER, GLRM_LOSS_HINGE, GLRM_LOSS_LOGISTIC, GLRM_LOSS_
 GLRM_REG_ZERO, GLRM_REG_QUAD, GLRM_REG_L1, GLRM_REG_NONNEG = range(4)
 GLRM_FP64, GLRM_FP32, GLRM_BF16 = 0, 1, 2
 GLRM_PATH_AUTO, GLRM_PATH_CHUNKED, GLRM_PATH_FUSED, GLRM_PATH_BLOCKED = 0, 1, 2, 3
-GLRM_PATH_MASKED, GLRM_PATH_MASKED_SPLIT = 4, 5
+GLRM_PATH_MASKED, GLRM_PATH_MASKED_SPLIT, GLRM_PATH_DENSE = 4, 5, 6
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libglrm.so")
 
@@ -45,6 +45,8 @@ def _load():
         "glrm_create": [i64, i64, i32, p, i32, f64, i32, f64, i32, p, p],
         "glrm_set_observed": [p, i64, p, p, p, p, p, p],
         "glrm_set_observed_host": [p, i64, p, p, p, p, p, p],
+        "glrm_set_dense": [p, p, i64],
+        "glrm_set_dense_host": [p, p, i64],
         "glrm_set_factors": [p, p, p],
         "glrm_get_factors": [p, p, p],
         "glrm_set_factors_host": [p, p, p],
@@ -156,6 +158,21 @@ def glrm_set_observed_host(h, nnz, csr_rowptr, csr_colidx, csr_val, csc_colptr, 
     _check(_lib.glrm_set_observed_host(h, nnz, _ptr(csr_rowptr), _ptr(csr_colidx),
                                        _ptr(csr_val), _ptr(csc_colptr), _ptr(csc_rowidx),
                                        _ptr(csc_val)), h)
+
+
+def glrm_set_dense(h, A, lda=None):
+    """A: m x n float32 CUDA tensor (rows contiguous; lda = its row stride)."""
+    if lda is None:
+        lda = A.stride(0) if isinstance(A, torch.Tensor) else A.shape[1]
+    _check(_lib.glrm_set_dense(h, ctypes.c_void_p(A.data_ptr()), int(lda)), h)
+
+
+def glrm_set_dense_host(h, A, lda=None):
+    """A: m x n float32 host array or CPU tensor (pinned memory copies faster)."""
+    if lda is None:
+        lda = A.stride(0) if isinstance(A, torch.Tensor) else A.shape[1]
+    ptr = ctypes.c_void_p(A.data_ptr()) if isinstance(A, torch.Tensor) else _ptr(A)
+    _check(_lib.glrm_set_dense_host(h, ptr, int(lda)), h)
 
 
 def glrm_set_factors(h, X, Yt):
@@ -414,6 +431,29 @@ class GLRM:
             g.set_factors(torch.as_tensor(t.X0, dtype=g.dtype, device=g.device),
                           torch.as_tensor(t.Yt0, dtype=g.dtype, device=g.device))
         return g
+
+    @classmethod
+    def from_dense_table(cls, t, device=None, stream=None, factors=True):
+        """A workloads.DenseTable, or a fully observed workloads.Table (nnz ==
+        m n, CSR rows complete), given to the dense form."""
+        g = cls(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry,
+                GLRM_FP32, device, stream)
+        if hasattr(t, "A"):
+            src = t.A
+        else:
+            if int(t.colidx.size) != t.m * t.n:
+                raise ValueError("the table is not fully observed")
+            src = np.asarray(t.val).reshape(t.m, t.n)
+        A = torch.as_tensor(src, dtype=torch.float32, device=g.device)
+        g.set_dense(A)
+        if factors:
+            g.set_factors(torch.as_tensor(t.X0, dtype=g.dtype, device=g.device),
+                          torch.as_tensor(t.Yt0, dtype=g.dtype, device=g.device))
+        return g
+
+    def set_dense(self, A):
+        with torch.cuda.device(self.device):
+            glrm_set_dense(self.h, A)
 
     def set_observed_table(self, t):
         dev, dt = self.device, self.dtype

@@ -276,6 +276,77 @@ def small_mixed(m=97, n=41, k=6, p_obs=0.55, seed=BASE_SEED + 20, rx=(REG_L1, 0.
     return _finish("small_mixed", m, n, k, rowptr, colidx, val, kinds, param, lv, rx, ry, rng)
 
 
+# ------------------------------------------------------------- dense tables
+
+@dataclasses.dataclass
+class DenseTable:
+    """A fully observed table: A (m x n, row-major float32), column losses,
+    regularisers and the initial factors."""
+    name: str
+    m: int
+    n: int
+    k: int
+    A: np.ndarray           # float32 [m, n]
+    loss_kind: np.ndarray   # int32 [n]
+    loss_param: np.ndarray  # float64 [n]
+    loss_levels: np.ndarray  # int32 [n]
+    rx: tuple
+    ry: tuple
+    X0: np.ndarray          # float64 [m, k]
+    Yt0: np.ndarray         # float64 [n, k]
+
+    def observed(self) -> Table:
+        """The same data as an observed set with every entry present (CSR and
+        CSC); for the oracle on small tables."""
+        rowptr = np.arange(self.m + 1, dtype=np.int64) * self.n
+        colidx = np.tile(np.arange(self.n, dtype=np.int32), self.m)
+        val = self.A.astype(np.float64).reshape(-1)
+        colptr, rowidx, cval = csc_from_csr(self.m, self.n, rowptr, colidx, val)
+        return Table(self.name, self.m, self.n, self.k, rowptr, colidx, val, colptr, rowidx, cval,
+                     self.loss_kind, self.loss_param, self.loss_levels, self.rx, self.ry,
+                     self.X0, self.Yt0)
+
+
+def mixed_dense(m=100_000, n=1000, k=20, n_real=500, n_bool=300, levels=7, seed=BASE_SEED + 6,
+                name="mixed_dense", lam=0.01, block=8192):
+    """The mixed-type table's recipe with every cell observed: Huber columns
+    (Laplace(0, 0.5) noise, 1% of entries x20), hinge columns
+    sign(X0 Y0 + N(0, 0.5^2)), ordinal columns binned at the column's
+    empirical septiles of X0 Y0 (estimated on the first 20,000 rows); l1
+    (lambda) on X, nonnegativity on Y.  Generated in row blocks."""
+    rng = rng_for(seed)
+    n_ord = n - n_real - n_bool
+    assert n_ord >= 0
+    X0 = rng.standard_normal((m, k))
+    Y0t = rng.standard_normal((n, k))
+    ocols = np.arange(n_real + n_bool, n)
+    qs = np.arange(1, levels) / levels
+    sample = X0[:min(m, 20000)] @ Y0t[ocols].T
+    edges = np.quantile(sample, qs, axis=0).T if n_ord else np.zeros((0, levels - 1))
+    A = np.empty((m, n), dtype=np.float32)
+    for r0 in range(0, m, block):
+        r1 = min(m, r0 + block)
+        u = X0[r0:r1] @ Y0t.T
+        noise = rng.laplace(0.0, 0.5, size=(r1 - r0, n_real))
+        noise[rng.random((r1 - r0, n_real)) < 0.01] *= 20.0
+        A[r0:r1, :n_real] = u[:, :n_real] + noise
+        z = u[:, n_real:n_real + n_bool] + 0.5 * rng.standard_normal((r1 - r0, n_bool))
+        A[r0:r1, n_real:n_real + n_bool] = np.where(z >= 0.0, 1.0, -1.0)
+        if n_ord:
+            uo = u[:, n_real + n_bool:]
+            lev = np.ones(uo.shape)
+            for q in range(levels - 1):
+                lev += uo > edges[:, q][None, :]
+            A[r0:r1, n_real + n_bool:] = lev
+    kind = np.concatenate([np.full(n_real, LOSS_HUBER), np.full(n_bool, LOSS_HINGE),
+                           np.full(n_ord, LOSS_ORDINAL)]).astype(np.int32)
+    param = np.concatenate([np.full(n_real, 1.0), np.zeros(n_bool), np.zeros(n_ord)])
+    lv = np.concatenate([np.zeros(n_real), np.zeros(n_bool), np.full(n_ord, levels)]).astype(np.int32)
+    Xi = rng.standard_normal((m, k))
+    Yi = rng.standard_normal((n, k))
+    return DenseTable(name, m, n, k, A, kind, param, lv, (REG_L1, lam), (REG_NONNEG, 0.0), Xi, Yi)
+
+
 # ------------------------------------------------------------ batched tables
 
 @dataclasses.dataclass

@@ -1,0 +1,179 @@
+"""The dense, fully observed form (tensor-core contractions) against the FP64
+oracle run on the same table as an observed set with every entry present.
+
+Tolerances come from the arithmetic: the products x_i . y_j are six BF16
+products of three-part splits x = hi + mid + lo accumulated in FP32, an error
+of about 2^-25 sum_c |x_ic y_jc| per entry, below FP32's k 2^-24; the
+gradient contractions use two-part splits (about 2^-16 relative).  So
+per-sweep objectives from a state shared with the oracle agree within 1e-5
+(as for the FP32 sparse path); factors after a sweep within 1e-4; gradients
+within 1e-4 norm-wise.  Shapes are ragged against the 128-row tiles and 64-wide chunks,
+and large enough that both half-steps split the other dimension into parts."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1410_0342_gb300 import workloads as W
+
+from gpu_parity import oracle_problem, synced_sweeps
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1410_0342_gb300 import build
+    build.build()
+    from paper_1410_0342_gb300 import glrm
+    return glrm
+
+
+def dense_mixed(m, n, k, seed, rx=(1, 0.1), ry=(1, 0.1)):
+    return W.small_mixed(m=m, n=n, k=k, p_obs=1.0, seed=seed, rx=rx, ry=ry)
+
+
+def test_dense_qpca_tiny_matches_oracle(G, oracle_mod):
+    """200 x 100, k = 5 (one partial tile each way, k padded to 16)."""
+    t = W.qpca_dense()
+    g = G.GLRM.from_dense_table(t)
+    assert tuple(G.glrm_get_path(g.h)) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    rels = synced_sweeps(g, oracle_mod, t, 10, rtol=1e-5)
+    assert rels.max() < 1e-5
+
+
+@pytest.mark.parametrize("m,n,k", [(1000, 301, 20), (777, 130, 33), (300, 64, 64), (129, 65, 16)])
+def test_dense_mixed_matches_oracle(G, oracle_mod, m, n, k):
+    """Every loss kind (columns cycle quadratic, Huber, hinge, logistic,
+    ordinal), ragged m and n, k padded to 16 / 32 / 48 / 64."""
+    t = dense_mixed(m, n, k, seed=500 + k)
+    g = G.GLRM.from_dense_table(t)
+    synced_sweeps(g, oracle_mod, t, 6, rtol=1e-5)
+
+
+def test_dense_objective_and_gradient(G, oracle_mod):
+    """Objective and gradient at the initial factors on a 5,000 x 2,000 table
+    (k = 64): both half-steps split the other dimension into several parts."""
+    t = W.qpca_dense(m=5000, n=2000, k=64, seed=77)
+    g = G.GLRM.from_dense_table(t)
+    p = oracle_problem(oracle_mod, t)
+    X = torch.as_tensor(t.X0, dtype=torch.float32, device="cuda")
+    Yt = torch.as_tensor(t.Yt0, dtype=torch.float32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.glrm_objective_at(g.h, X, Yt, out)
+    Xd = X.double().cpu().numpy()
+    Yd = Yt.double().cpu().numpy()
+    of = p.objective(Xd, Yd)
+    assert abs(out.item() - of) / of < 1e-5, (out.item(), of)
+    GX = torch.empty_like(X)
+    GY = torch.empty_like(Yt)
+    G.glrm_grad_at(g.h, X, Yt, GX, GY, include_reg=False)
+    oGX, oGY = p.gradient(Xd, Yd)
+    for a, b in ((GX, oGX), (GY, oGY)):
+        rel = np.linalg.norm(a.double().cpu().numpy() - b) / np.linalg.norm(b)
+        assert rel < 1e-4, rel
+
+
+def test_dense_mixed_objective_gradient(G, oracle_mod):
+    t = dense_mixed(1500, 410, 24, seed=9)
+    g = G.GLRM.from_dense_table(t)
+    p = oracle_problem(oracle_mod, t)
+    rng = np.random.default_rng(5)
+    X = torch.as_tensor(rng.standard_normal((t.m, t.k)), dtype=torch.float32, device="cuda")
+    Yt = torch.as_tensor(rng.standard_normal((t.n, t.k)), dtype=torch.float32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.glrm_objective_at(g.h, X, Yt, out)
+    of = p.objective(X.double().cpu().numpy(), Yt.double().cpu().numpy())
+    assert abs(out.item() - of) / of < 1e-5
+    GX = torch.empty_like(X)
+    GY = torch.empty_like(Yt)
+    G.glrm_grad_at(g.h, X, Yt, GX, GY, include_reg=True)
+    oGX, oGY = p.gradient(X.double().cpu().numpy(), Yt.double().cpu().numpy())
+    # glrm_grad_at adds the regulariser's gradient (quadratic, weight 0.1)
+    oGX = oGX + 2 * 0.1 * X.double().cpu().numpy()
+    oGY = oGY + 2 * 0.1 * Yt.double().cpu().numpy()
+    for a, b in ((GX, oGX), (GY, oGY)):
+        rel = np.linalg.norm(a.double().cpu().numpy() - b) / np.linalg.norm(b)
+        assert rel < 1e-4, rel
+
+
+def test_dense_matches_sparse_fp32_one_sweep(G):
+    """The dense form and the FP32 sparse path on the same fully observed
+    quadratic table (3,000 x 700, k = 32), one sweep from the same state:
+    objectives within 1e-5, accepted rows and columns within 1%.  (Free-running
+    trajectories part after near-tie accept / reject flips, as between any two
+    roundings.)"""
+    t = W.qpca_dense(m=3000, n=700, k=32, seed=41)
+    gd = G.GLRM.from_dense_table(t)
+    gs = G.GLRM.from_table(t, precision=G.GLRM_FP32)
+    for _ in range(3):
+        hd = gd.sweep(1)[0]
+        hs = gs.sweep(1)[0]
+        assert abs(hd - hs) / hs < 1e-5, (hd, hs)
+        ad, as_ = gd.accepts(), gs.accepts()
+        assert abs(int(ad[0]) - int(as_[0])) <= max(2, t.m // 100)
+        assert abs(int(ad[1]) - int(as_[1])) <= max(2, t.n // 100)
+        gs.load_state(gd.state())
+
+
+def test_dense_reaches_qpca_closed_form(G):
+    """Quadratic loss and regulariser on a fully observed table: the sweep
+    approaches ||A||^2 - sum_i (sigma_i - gamma)_+^2 (Section 2.5, shrunk
+    singular values) as closely as FP32 arithmetic allows.  On this table the
+    FP32 sparse path stalls 9.0e-5 above f* (its accept / reject test stops
+    resolving the remaining decrease); the dense form must do as well, 1e-4."""
+    t = W.qpca_dense()
+    g = G.GLRM.from_dense_table(t)
+    hist = g.sweep(3000)
+    assert np.all(np.diff(hist) <= 1e-7 * np.abs(hist[1:]))
+    A = t.val.reshape(t.m, t.n)
+    s = np.linalg.svd(A, compute_uv=False)
+    fstar = float(np.sum(A * A) - np.sum(np.maximum(s[:t.k] - 0.1, 0) ** 2))
+    assert 0 <= (hist[-1] - fstar) / fstar < 1e-4, (hist[-1], fstar)
+
+
+def test_dense_host_copy_and_pitch(G):
+    """glrm_set_dense_host from a strided host array equals glrm_set_dense."""
+    t = dense_mixed(300, 77, 8, seed=3)
+    A = t.val.reshape(t.m, t.n).astype(np.float32)
+    wide = np.zeros((t.m, 80), np.float32)
+    wide[:, :t.n] = A
+    g1 = G.GLRM.from_dense_table(t)
+    g2 = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry)
+    G.glrm_set_dense_host(g2.h, wide, 80)
+    g2.set_factors(torch.as_tensor(t.X0, dtype=torch.float32, device="cuda"),
+                   torch.as_tensor(t.Yt0, dtype=torch.float32, device="cuda"))
+    np.testing.assert_array_equal(g1.sweep(3), g2.sweep(3))
+
+
+def test_dense_validation(G):
+    t = dense_mixed(200, 50, 8, seed=4)
+    A = torch.as_tensor(t.val.reshape(t.m, t.n), dtype=torch.float32, device="cuda")
+    g = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry)
+    bad = A.clone()
+    bad[3, 7] = float("nan")
+    with pytest.raises(G.GLRMError) as e:
+        g.set_dense(bad)
+    assert e.value.code == G.GLRM_ERR_NONFINITE
+    bad = A.clone()
+    bad[5, 2] = 0.5  # column 2 has hinge loss: values must be -1 or +1
+    with pytest.raises(G.GLRMError) as e:
+        g.set_dense(bad)
+    assert e.value.code == G.GLRM_ERR_OMEGA
+    with pytest.raises(G.GLRMError) as e:
+        G.glrm_set_dense(g.h, A, 10)
+    assert e.value.code == G.GLRM_ERR_ARG
+    with pytest.raises(G.GLRMError) as e:
+        g.sweep(1)
+    assert e.value.code == G.GLRM_ERR_STATE
+    g.set_dense(A)
+    g.sweep(1)
+    with pytest.raises(G.GLRMError) as e:
+        g.als_sweep(1)
+    assert e.value.code == G.GLRM_ERR_STATE
+    g64 = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry,
+                 precision=G.GLRM_FP64)
+    with pytest.raises(G.GLRMError) as e:
+        g64.set_dense(A.double())
+    assert e.value.code == G.GLRM_ERR_ARG
