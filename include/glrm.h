@@ -344,8 +344,9 @@ void glrm_batch_destroy(glrm_batch_t b);
  * fifth-generation tensor cores (tcgen05.mma, BF16 operands staged in shared
  * memory, FP32 accumulator in tensor memory).  A: M x K, B: N x K, both
  * row-major BF16 (raw 16-bit words); D: M x N row-major FP32.  Device
- * pointers; M a multiple of 128, N of 64, K of 16 with K <= 128
- * (GLRM_ERR_RANGE otherwise).  Synchronises; GLRM_ERR_TIMEOUT if a wait for
+ * pointers; M a multiple of 128, N of 64, K one of 16, 32, 64, 128 (the
+ * operands are staged in the 32-, 64- or 128-byte swizzled layouts the dense
+ * form uses; GLRM_ERR_RANGE otherwise).  Synchronises; GLRM_ERR_TIMEOUT if a wait for
  * the tensor core hit its limit. */
 int glrm_tc_gemm_bf16(const void *A_dev, const void *B_dev, float *D_dev, int32_t M, int32_t N,
                       int32_t K, void *stream);

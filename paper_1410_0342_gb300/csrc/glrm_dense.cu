@@ -43,8 +43,8 @@ namespace glrm {
 
 constexpr int kDnNT = 64;        // chunk of the other dimension (UMMA N of GEMM1, K of GEMM2)
 constexpr int kDnRows = 128;     // own rows per CTA (UMMA M)
-constexpr int kDnWarps = 16;     // warp w: TMEM lanes 32 (w % 4) .. + 31, chunk columns 16 (w / 4) .. + 15
-constexpr int kDnThreads = kDnWarps * 32;
+constexpr int kDnWarps = 16;     // evaluating warp w: TMEM lanes 32 (w % 4) .. + 31, chunk columns 16 (w / 4) .. + 15
+constexpr int kDnThreads = (kDnWarps + 1) * 32;  // + the producer warp
 constexpr int kDnTmem = 256;     // TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), R at [192, 256)
 constexpr int kDnColG = 128, kDnColR = 192;
 constexpr int kDnMaxStages = 4;
@@ -60,8 +60,7 @@ struct DenseArgs {
     const __nv_bfloat16 *pk;  // other factor, K-major over k: parts hi, mid, lo (each pack_part)
     const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid
     int64_t pack_part;        // elements per part
-    const LossF *lossf;       // n column losses
-    const int32_t *gkind;     // per 16-column group: the kind shared by its columns, else -1
+    const LossF *lossf;       // n column losses; w: the kind of the column's 16-column group, else -1
     int parts, nA;
     int64_t nchunks, per_part;  // chunks of the other dimension, chunks per part
     float *part_grad;           // (nown * parts) x k
@@ -129,22 +128,58 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Losses and derivatives of 16 entries of one loss kind (KIND < 0: each
-// entry's own kind).  X-step: the entries are 16 columns (per-column
-// parameters in lf); Y-step: one column (parameters of `own`).  Entries
-// outside the table (bit clear in `valid`) give 0.
-template <int KIND, bool XSTEP>
-__device__ __forceinline__ void dn_losses(const float (&u)[16], const float (&a)[16], const LossF *lf, LossF own,
-                                          uint32_t valid, float (&rr)[16], float &lsum)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Losses and derivatives of 16 entries that all lie inside the table and
+// share one loss kind with parameters prm (Huber threshold) and lev (ordinal
+// level count).  Quadratic entries run two at a time in packed FP32.
+template <int KIND>
+__device__ __forceinline__ void dn_block(const float (&u)[16], const float (&a)[16], float prm, float lev,
+                                         float (&rr)[16], float &lsum)
+{
+    if constexpr (KIND == kLossQuad) {
+        const unsigned long long m1 = pk2(-1.f, -1.f);
+        unsigned long long acc = pk2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < 16; w += 2) {
+            const unsigned long long r = ffma2(pk2(a[w], a[w + 1]), m1, pk2(u[w], u[w + 1]));  // u - a
+            acc = ffma2(r, r, acc);
+            upk2(fadd2(r, r), rr[w], rr[w + 1]);
+        }
+        float l0, l1;
+        upk2(acc, l0, l1);
+        lsum += l0 + l1;
+    } else {
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+            float L;
+            rr[w] = loss_deriv_k<KIND, float>(u[w], a[w], prm, lev, L);
+            lsum += L;
+        }
+    }
+}
+
+// Any mix of kinds, entries outside the table (bit clear in `valid`) give 0.
+// X-step: the entries are 16 columns (losses in lf); Y-step: one column (own).
+template <bool XSTEP>
+__device__ __forceinline__ void dn_block_any(const float (&u)[16], const float (&a)[16], const LossF *lf,
+                                             LossF own, uint32_t valid, float (&rr)[16], float &lsum)
 {
 #pragma unroll
     for (int w = 0; w < 16; ++w) {
         const LossF sp = XSTEP ? lf[w] : own;
-        float L, d;
-        if constexpr (KIND >= 0)
-            d = loss_deriv_k<KIND, float>(u[w], a[w], sp.y, sp.z, L);
-        else
-            d = loss_deriv_kind<float>(__float_as_int(sp.x), u[w], a[w], sp.y, sp.z, L);
+        float L;
+        const float d = loss_deriv_kind<float>(__float_as_int(sp.x), u[w], a[w], sp.y, sp.z, L);
         const bool v = (valid >> w) & 1u;
         lsum += v ? L : 0.f;
         rr[w] = v ? d : 0.f;
@@ -156,13 +191,22 @@ __device__ __forceinline__ void dn_losses(const float (&u)[16], const float (&a)
 // A tiles: X-step, two boxes of 32 columns x 128 own rows with the 128-byte
 // swizzle (16-byte unit u of row r at u ^ (r % 8): conflict-free row reads);
 // Y-step, one box of 128 own columns x 64 rows, unswizzled.
+// Warps 0 .. 15 evaluate the entries; warp 16 (lane 0) issues every copy and
+// MMA.  It learns from barU[c % 2] (one arrival per evaluating warp) that U of
+// chunk c has been read out of tensor memory, and issues GEMM1 of chunk c + 2
+// into that buffer at once; from barE[c % 4] that the entries of chunk c are
+// done (A stage read, R written), and issues the next copies and GEMM2.  The
+// evaluating warps never wait for each other inside the loop.  A warp can
+// start chunk c only after every warp has read U of chunk c - 2, so after
+// every warp has finished chunk c - 3: four barE barriers keep the arrivals
+// of different chunks apart.
 template <bool XSTEP, bool GRAD, int KP>
 __global__ void __launch_bounds__(kDnThreads, 1)
 dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 {
     using SM = DnSmem<XSTEP, GRAD, KP>;
     extern __shared__ __align__(1024) unsigned char dsm_dense[];
-    __shared__ uint64_t barA[kDnMaxStages], barP[3], barT[2], barG1[2], barG2;
+    __shared__ uint64_t barA[kDnMaxStages], barP[3], barL[3], barT[2], barG1[2], barG2, barU[2], barE[4];
     __shared__ uint32_t tslot;
     __shared__ double red[4][kDnRows];
     unsigned char *base = dsm_dense + ((1024 - (smem_u32(dsm_dense) & 1023)) & 1023);
@@ -174,7 +218,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     unsigned char *lsst = ptst + 4 * SM::pt;                     // loss table stage s at lsst + s * ls
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, grp = warp >> 2;
+    const int quarter = warp & 3, grp = (warp >> 2) & 3;
     const int orow = quarter * 32 + lane;
     const int64_t o0 = (int64_t)blockIdx.x * kDnRows;
     const int part = blockIdx.y;
@@ -182,7 +226,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     const int64_t qe = qb + p.per_part < p.nchunks ? qb + p.per_part : p.nchunks;
     const int nq = (int)(qe - qb);
     const int nA = p.nA;
-    const bool own_ok = o0 + orow < p.nown;
+    const bool producer = warp == kDnWarps;
+    const bool own_ok = !producer && o0 + orow < p.nown;
     const int nown_t = (int)(p.nown - o0 < kDnRows ? p.nown - o0 : kDnRows);
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const int tb = grp * 16;  // this warp's columns of a chunk
@@ -191,22 +236,36 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     if (tid == 0) {
         for (int s = 0; s < kDnMaxStages; ++s) mbar_init(&barA[s], 1);
         for (int s = 0; s < 3; ++s) mbar_init(&barP[s], 1);
+        for (int s = 0; s < 3; ++s) mbar_init(&barL[s], 1);
         mbar_init(&barT[0], 1);
         mbar_init(&barT[1], 1);
         mbar_init(&barG1[0], 1);
         mbar_init(&barG1[1], 1);
         mbar_init(&barG2, 1);
+        mbar_init(&barU[0], kDnWarps);
+        mbar_init(&barU[1], kDnWarps);
+        for (int s = 0; s < 4; ++s) mbar_init(&barE[s], kDnWarps);
     }
-    // own rows, split in three, K-major core-matrix layout
-    for (int q = tid; q < kDnRows * KP; q += kDnThreads) {
-        const int r = q / KP, c = q - r * KP;
-        const float v = (r < nown_t && c < p.k) ? p.F[(o0 + r) * p.k + c] : 0.f;
-        __nv_bfloat16 hi, mid, lo;
-        split3(v, hi, mid, lo);
-        const int64_t ix = core_index(r, c, KP);
-        own[ix] = hi;
-        own[kDnRows * KP + ix] = mid;
-        own[2 * kDnRows * KP + ix] = lo;
+    // own rows split in three, K-major core-matrix layout: one thread per
+    // (row, 8 coordinates), 16-byte stores
+    for (int q = tid; q < kDnRows * (KP / 8); q += kDnThreads) {
+        const int r = q / (KP / 8), c0 = (q - r * (KP / 8)) * 8;
+        uint32_t hv[4], mv[4], lv[4];
+#pragma unroll
+        for (int w = 0; w < 8; w += 2) {
+            const float v0 = (r < nown_t && c0 + w < p.k) ? p.F[(o0 + r) * p.k + c0 + w] : 0.f;
+            const float v1 = (r < nown_t && c0 + w + 1 < p.k) ? p.F[(o0 + r) * p.k + c0 + w + 1] : 0.f;
+            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+            split3(v0, h0, m0, l0);
+            split3(v1, h1, m1, l1);
+            hv[w / 2] = bf2_bits(__halves2bfloat162(h0, h1));
+            mv[w / 2] = bf2_bits(__halves2bfloat162(m0, m1));
+            lv[w / 2] = bf2_bits(__halves2bfloat162(l0, l1));
+        }
+        unsigned char *ob = reinterpret_cast<unsigned char *>(own) + sw_off(r, c0, 2 * KP);
+        *reinterpret_cast<uint4 *>(ob) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4 *>(ob + SM::own) = make_uint4(mv[0], mv[1], mv[2], mv[3]);
+        *reinterpret_cast<uint4 *>(ob + 2 * SM::own) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
     }
     // Y-step: this thread's column loss, and whether the warp shares one kind
     LossF myspec = make_float4(__int_as_float(kLossQuad), 0.f, 0.f, 0.f);
@@ -223,199 +282,244 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     tc_fence_after();
     const uint32_t taddr = tslot;
 
-    // thread 0 issues every copy and MMA
-    int p_issued = 0, a_issued = 0, t_issued = 0, g1_issued = 0, g2_issued = 0;
-    bool ok0 = true;  // thread 0: every wait of its own succeeded
-    auto issue_pack = [&](int64_t q) {  // GEMM1's W parts (+ X-step column losses), stage q % 3
-        const int s = (int)((q - qb) % 3);
-        unsigned char *st = pkst + s * 3 * SM::pk;
-        const int64_t t0 = q * kDnNT;
-        const int nv = (int)(p.nother - t0 < kDnNT ? p.nother - t0 : kDnNT);
-        const unsigned bytes = (unsigned)(3 * SM::pk + (XSTEP ? nv * sizeof(LossF) : 0));
-        mbar_expect_tx(&barP[s], bytes);
-#pragma unroll
-        for (int w = 0; w < 3; ++w)
-            bulk_g2s(st + w * SM::pk, p.pk + w * p.pack_part + t0 * KP, (unsigned)SM::pk, &barP[s]);
-        if constexpr (XSTEP)
-            bulk_g2s(lsst + s * SM::ls, p.lossf + t0, (unsigned)(nv * sizeof(LossF)), &barP[s]);
-        ++p_issued;
-    };
-    auto issue_pt = [&](int64_t q) {  // GEMM2's W parts, stage q % 2
-        const int s = (int)((q - qb) & 1);
-        unsigned char *st = ptst + s * 2 * SM::pt;
-        mbar_expect_tx(&barT[s], (unsigned)(2 * SM::pt));
-        bulk_g2s(st, p.pt + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
-        bulk_g2s(st + SM::pt, p.pt + p.pack_part + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
-        ++t_issued;
-    };
-    auto issue_a = [&](int64_t q) {  // the A tile, stage q % nA (out-of-range rows / columns read as 0)
-        const int s = (int)((q - qb) % nA);
-        unsigned char *dst = ast + s * SM::a;
-        const int t0 = (int)(q * kDnNT);
-        mbar_expect_tx(&barA[s], (unsigned)SM::a);
-        if constexpr (XSTEP) {
-            tma_load_2d(dst, &amap, t0, (int)o0, &barA[s]);
-            tma_load_2d(dst + SM::a / 2, &amap, t0 + 32, (int)o0, &barA[s]);
-        } else {
-            tma_load_2d(dst, &amap, (int)o0, t0, &barA[s]);
-        }
-        ++a_issued;
-    };
-    // GEMM1 of chunk q into accumulator buffer (q - qb) % 2, once its W parts are in
-    auto issue_gemm1 = [&](int64_t q) {
-        const int c = (int)(q - qb);
-        const int s = c % 3, b = c & 1;
-        if (!ok0 || !mbar_wait_bounded(&barP[s], (unsigned)(c / 3) & 1u)) {
-            ok0 = false;
-            return;
-        }
-        tc_fence_after();
-        const uint32_t idesc = umma_idesc_bf16(kDnRows, kDnNT);
-        const __nv_bfloat16 *w = reinterpret_cast<const __nv_bfloat16 *>(pkst + s * 3 * SM::pk);
-        constexpr uint32_t sbo = KP * 16;
-        constexpr int own_part = kDnRows * KP, w_part = kDnNT * KP;
-        // (own part, W part), smallest products first; hi . hi last
-        const int pa[6] = {1, 0, 2, 0, 1, 0};
-        const int pb[6] = {1, 2, 0, 1, 0, 0};
-#pragma unroll
-        for (int pr = 0; pr < 6; ++pr)
-#pragma unroll
-            for (int ks = 0; ks < KP / 16; ++ks)
-                umma_bf16(taddr + (uint32_t)(b * kDnNT), umma_desc(own + pa[pr] * own_part + ks * 128, 128, sbo),
-                          umma_desc(w + pb[pr] * w_part + ks * 128, 128, sbo), idesc, pr > 0 || ks > 0);
-        umma_commit(&barG1[b]);
-        ++g1_issued;
-    };
-    // GEMM2 of chunk q: G += R W, R from tensor memory
-    auto issue_gemm2 = [&](int64_t q) {
-        const int c = (int)(q - qb);
-        const int s = c & 1;
-        if (!ok0 || !mbar_wait_bounded(&barT[s], (unsigned)(c >> 1) & 1u)) {
-            ok0 = false;
-            return;
-        }
-        tc_fence_after();
-        const uint32_t idesc = umma_idesc_bf16(kDnRows, KP);
-        constexpr uint32_t sbo = kDnNT * 16;
-        constexpr int tpart = KP * kDnNT;
-        const __nv_bfloat16 *wt = reinterpret_cast<const __nv_bfloat16 *>(ptst + s * 2 * SM::pt);
-        // (R part, W part): mid.hi, hi.mid, hi.hi; a K = 16 step of R is 8 columns
-        const int pa[3] = {1, 0, 0};
-        const int pb[3] = {0, 1, 0};
-#pragma unroll
-        for (int pr = 0; pr < 3; ++pr)
-#pragma unroll
-            for (int ks = 0; ks < kDnNT / 16; ++ks)
-                umma_bf16_ta(taddr + kDnColG, taddr + (uint32_t)(kDnColR + pa[pr] * 32 + ks * 8),
-                             umma_desc(wt + pb[pr] * tpart + ks * 128, 128, sbo), idesc, c > 0 || pr > 0 || ks > 0);
-        umma_commit(&barG2);
-        ++g2_issued;
-    };
-    if (tid == 0) {
-        for (int s = 0; s < nA && s < nq; ++s) issue_a(qb + s);
-        for (int s = 0; s < 3 && s < nq; ++s) issue_pack(qb + s);
-        if (GRAD) {
-            issue_pt(qb);
-            if (nq > 1) issue_pt(qb + 1);
-        }
-        issue_gemm1(qb);
-        if (nq > 1) issue_gemm1(qb + 1);
-    }
-
     bool ok = true;
-    bool fail = false;
-    double lacc = 0.0;
-    for (int it = 0; it < nq; ++it) {
-        const int64_t q = qb + it;
-        const int b = it & 1;
-        const int sA = it % nA;
-        ok = ok && mbar_wait_bounded(&barG1[b], (unsigned)(it >> 1) & 1u);
-        if (XSTEP) ok = ok && mbar_wait_bounded(&barP[it % 3], (unsigned)(it / 3) & 1u);  // loss table
-        ok = ok && mbar_wait_bounded(&barA[sA], (unsigned)(it / nA) & 1u);
-        tc_fence_after();
-        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld / st below are warp-collective
-        float lsum = 0.f;
-        float rr[16];
-        if (ok) {
-            const unsigned char *as = ast + sA * SM::a;
-            const int64_t t0 = q * kDnNT;
-            float u[16], a[16];
-            tmem_ld16(taddr + lane_base + (uint32_t)(b * kDnNT + tb), u);
-            if constexpr (XSTEP) {
-                // box tb / 32, row orow: 16-byte units (tb % 32) / 4 .. + 3, swizzled
-                const unsigned char *row = as + (tb >> 5) * (SM::a / 2) + orow * 128;
+    float lacc = 0.f, lcomp = 0.f;
+    // producer bookkeeping (warp kDnWarps, lane 0)
+    int p_issued = 0, a_issued = 0, t_issued = 0, l_issued = 0, g1_issued = 0, g2_issued = 0;
+    if (producer) {
+        if (lane == 0) {
+            auto issue_pack = [&](int64_t q) {  // GEMM1's W parts, stage q % 3
+                const int s = (int)((q - qb) % 3);
+                unsigned char *st = pkst + s * 3 * SM::pk;
+                const int64_t t0 = q * kDnNT;
+                mbar_expect_tx(&barP[s], (unsigned)(3 * SM::pk));
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const float4 v =
-                        *reinterpret_cast<const float4 *>(row + ((((tb & 31) >> 2) + w) ^ (orow & 7)) * 16);
-                    a[4 * w] = v.x;
-                    a[4 * w + 1] = v.y;
-                    a[4 * w + 2] = v.z;
-                    a[4 * w + 3] = v.w;
+                for (int w = 0; w < 3; ++w)
+                    bulk_g2s(st + w * SM::pk, p.pk + w * p.pack_part + t0 * KP, (unsigned)SM::pk, &barP[s]);
+                ++p_issued;
+            };
+            auto issue_ls = [&](int64_t q) {  // X-step: the chunk's column losses, stage q % 3
+                const int s = (int)((q - qb) % 3);
+                const int64_t t0 = q * kDnNT;
+                const int nv = (int)(p.nother - t0 < kDnNT ? p.nother - t0 : kDnNT);
+                mbar_expect_tx(&barL[s], (unsigned)(nv * sizeof(LossF)));
+                bulk_g2s(lsst + s * SM::ls, p.lossf + t0, (unsigned)(nv * sizeof(LossF)), &barL[s]);
+                ++l_issued;
+            };
+            auto issue_pt = [&](int64_t q) {  // GEMM2's W parts, stage q % 2
+                const int s = (int)((q - qb) & 1);
+                unsigned char *st = ptst + s * 2 * SM::pt;
+                mbar_expect_tx(&barT[s], (unsigned)(2 * SM::pt));
+                bulk_g2s(st, p.pt + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
+                bulk_g2s(st + SM::pt, p.pt + p.pack_part + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
+                ++t_issued;
+            };
+            auto issue_a = [&](int64_t q) {  // the A tile, stage q % nA (out-of-range elements read as 0)
+                const int s = (int)((q - qb) % nA);
+                unsigned char *dst = ast + s * SM::a;
+                const int t0 = (int)(q * kDnNT);
+                mbar_expect_tx(&barA[s], (unsigned)SM::a);
+                if constexpr (XSTEP) {
+                    tma_load_2d(dst, &amap, t0, (int)o0, &barA[s]);
+                    tma_load_2d(dst + SM::a / 2, &amap, t0 + 32, (int)o0, &barA[s]);
+                } else {
+                    tma_load_2d(dst, &amap, (int)o0, t0, &barA[s]);
                 }
-            } else {
-                const float *af = reinterpret_cast<const float *>(as);
+                ++a_issued;
+            };
+            // GEMM1 of chunk q into accumulator buffer (q - qb) % 2, once its W parts are in
+            auto issue_gemm1 = [&](int64_t q) -> bool {
+                const int c = (int)(q - qb);
+                const int s = c % 3, b = c & 1;
+                if (!mbar_wait_bounded(&barP[s], (unsigned)(c / 3) & 1u)) return false;
+                tc_fence_after();
+                const uint32_t idesc = umma_idesc_bf16(kDnRows, kDnNT);
+                const unsigned char *w = pkst + s * 3 * SM::pk;
+                const unsigned char *ow = reinterpret_cast<const unsigned char *>(own);
+                constexpr uint32_t RB = 2 * KP;  // bytes per operand row; a K step of 16 is 32 bytes
+                // (own part, W part), smallest products first; hi . hi last
+                const int pa[6] = {1, 0, 2, 0, 1, 0};
+                const int pb[6] = {1, 2, 0, 1, 0, 0};
 #pragma unroll
-                for (int w = 0; w < 16; ++w) a[w] = af[(tb + w) * kDnRows + orow];
+                for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+                    for (int ks = 0; ks < KP / 16; ++ks)
+                        umma_bf16(taddr + (uint32_t)(b * kDnNT), umma_desc_sw(ow + pa[pr] * SM::own + ks * 32, RB),
+                                  umma_desc_sw(w + pb[pr] * SM::pk + ks * 32, RB), idesc, pr > 0 || ks > 0);
+                umma_commit(&barG1[b]);
+                ++g1_issued;
+                return true;
+            };
+            // GEMM2 of chunk q: G += R W, R from tensor memory
+            auto issue_gemm2 = [&](int64_t q) -> bool {
+                const int c = (int)(q - qb);
+                const int s = c & 1;
+                if (!mbar_wait_bounded(&barT[s], (unsigned)(c >> 1) & 1u)) return false;
+                tc_fence_after();
+                const uint32_t idesc = umma_idesc_bf16(kDnRows, KP);
+                const unsigned char *wt = ptst + s * 2 * SM::pt;
+                // (R part, W part): mid.hi, hi.mid, hi.hi; a K = 16 step of R is 8 columns
+                const int pa[3] = {1, 0, 0};
+                const int pb[3] = {0, 1, 0};
+#pragma unroll
+                for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+                    for (int ks = 0; ks < kDnNT / 16; ++ks)
+                        umma_bf16_ta(taddr + kDnColG, taddr + (uint32_t)(kDnColR + pa[pr] * 32 + ks * 8),
+                                     umma_desc_sw(wt + pb[pr] * SM::pt + ks * 32, 2 * kDnNT), idesc,
+                                     c > 0 || pr > 0 || ks > 0);
+                umma_commit(&barG2);
+                ++g2_issued;
+                return true;
+            };
+            for (int s = 0; s < nA && s < nq; ++s) issue_a(qb + s);
+            for (int s = 0; s < 3 && s < nq; ++s) issue_pack(qb + s);
+            if (XSTEP)
+                for (int s = 0; s < 3 && s < nq; ++s) issue_ls(qb + s);
+            if (GRAD) {
+                issue_pt(qb);
+                if (nq > 1) issue_pt(qb + 1);
             }
-            const int64_t nv = p.nother - t0 - tb;  // valid columns from tb on
-            const uint32_t valid = !own_ok ? 0u : (nv >= 16 ? 0xffffu : (nv <= 0 ? 0u : (1u << nv) - 1u));
-            const LossF *lf = reinterpret_cast<const LossF *>(lsst + (it % 3) * SM::ls) + tb;
-            const int kind = XSTEP ? __ldg(p.gkind + ((t0 + tb) >> 4)) : wkind;
-            switch (kind) {
-            case kLossQuad: dn_losses<kLossQuad, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
-            case kLossHuber: dn_losses<kLossHuber, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
-            case kLossHinge: dn_losses<kLossHinge, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
-            case kLossLogistic: dn_losses<kLossLogistic, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
-            case kLossOrdinal: dn_losses<kLossOrdinal, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
-            default: dn_losses<-1, XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+            ok = issue_gemm1(qb);
+            if (ok && nq > 1) ok = issue_gemm1(qb + 1);
+            for (int it = 0; ok && it < nq; ++it) {
+                const int64_t q = qb + it;
+                // U of chunk q has been read (so GEMM1 of q is done): its accumulator
+                // buffer takes chunk q + 2, its W stage chunk q + 3
+                if (!mbar_wait_bounded(&barU[it & 1], (unsigned)(it >> 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (it + 3 < nq) issue_pack(q + 3);
+                if (it + 2 < nq && !issue_gemm1(q + 2)) {
+                    ok = false;
+                    break;
+                }
+                // the entries of chunk q are done: its A stage, loss-table stage and
+                // (GEMM2 of q - 1 having completed before) R are free
+                if (!mbar_wait_bounded(&barE[it & 3], (unsigned)(it >> 2) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (it + nA < nq) issue_a(q + nA);
+                if (XSTEP && it + 3 < nq) issue_ls(q + 3);
+                if (GRAD) {
+                    if (it >= 1 && it + 1 < nq) issue_pt(q + 1);  // GEMM2 of q - 1 (its stage) is done
+                    if (!issue_gemm2(q)) {
+                        ok = false;
+                        break;
+                    }
+                }
             }
         }
-        lacc += (double)lsum;
-        if constexpr (GRAD) {
-            // R of the previous chunk is no longer read once its GEMM2 is done
-            if (it > 0) ok = ok && mbar_wait_bounded(&barG2, (unsigned)(it - 1) & 1u);
+    } else {
+        for (int it = 0; it < nq; ++it) {
+            const int64_t q = qb + it;
+            const int b = it & 1;
+            const int sA = it % nA;
+            ok = ok && mbar_wait_bounded(&barG1[b], (unsigned)(it >> 1) & 1u);
+            if (XSTEP) ok = ok && mbar_wait_bounded(&barL[it % 3], (unsigned)(it / 3) & 1u);  // loss table
+            ok = ok && mbar_wait_bounded(&barA[sA], (unsigned)(it / nA) & 1u);
             tc_fence_after();
-            ok = __all_sync(0xffffffffu, ok);
-            if (ok) {
+            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld / st below are warp-collective
+            if (!ok) break;
+            float lsum = 0.f;
+            float rr[16];
+            {
+                const unsigned char *as = ast + sA * SM::a;
+                const int64_t t0 = q * kDnNT;
+                float u[16], a[16];
+                tmem_ld16(taddr + lane_base + (uint32_t)(b * kDnNT + tb), u);
+                // U of this chunk is in registers: its buffer may take the next GEMM1
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&barU[b]);
+                if constexpr (XSTEP) {
+                    // box tb / 32, row orow: 16-byte units (tb % 32) / 4 .. + 3, swizzled
+                    const unsigned char *row = as + (tb >> 5) * (SM::a / 2) + orow * 128;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const float4 v =
+                            *reinterpret_cast<const float4 *>(row + ((((tb & 31) >> 2) + w) ^ (orow & 7)) * 16);
+                        a[4 * w] = v.x;
+                        a[4 * w + 1] = v.y;
+                        a[4 * w + 2] = v.z;
+                        a[4 * w + 3] = v.w;
+                    }
+                } else {
+                    const float *af = reinterpret_cast<const float *>(as);
+#pragma unroll
+                    for (int w = 0; w < 16; ++w) a[w] = af[(tb + w) * kDnRows + orow];
+                }
+                const int64_t nv = p.nother - t0 - tb;  // valid columns from tb on
+                const uint32_t valid = !own_ok ? 0u : (nv >= 16 ? 0xffffu : (nv <= 0 ? 0u : (1u << nv) - 1u));
+                const LossF *lf = reinterpret_cast<const LossF *>(lsst + (it % 3) * SM::ls) + tb;
+                // the kind (and parameters) the 16 entries share, -1 if they do not:
+                // X-step, kept in the w of each column's loss; Y-step, the warp's columns
+                int kind = wkind;
+                float prm = myspec.y, lev = myspec.z;
+                if constexpr (XSTEP) {
+                    const LossF l0 = lf[0];
+                    kind = nv > 0 ? __float_as_int(l0.w) : -1;
+                    prm = l0.y;
+                    lev = l0.z;
+                }
+                if (__all_sync(0xffffffffu, valid == 0xffffu)) {
+                    switch (kind) {
+                    case kLossQuad: dn_block<kLossQuad>(u, a, prm, lev, rr, lsum); break;
+                    case kLossHuber: dn_block<kLossHuber>(u, a, prm, lev, rr, lsum); break;
+                    case kLossHinge: dn_block<kLossHinge>(u, a, prm, lev, rr, lsum); break;
+                    case kLossLogistic: dn_block<kLossLogistic>(u, a, prm, lev, rr, lsum); break;
+                    case kLossOrdinal: dn_block<kLossOrdinal>(u, a, prm, lev, rr, lsum); break;
+                    default: dn_block_any<XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
+                    }
+                } else {
+                    dn_block_any<XSTEP>(u, a, lf, myspec, valid, rr, lsum);
+                }
+            }
+            // compensated FP32 running sum of the chunk sums
+            {
+                const float y = lsum - lcomp;
+                const float t = lacc + y;
+                lcomp = (t - lacc) - y;
+                lacc = t;
+            }
+            if constexpr (GRAD) {
+                // R of the previous chunk is no longer read once its GEMM2 is done
+                if (it > 0) ok = mbar_wait_bounded(&barG2, (unsigned)(it - 1) & 1u);
+                tc_fence_after();
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
                 uint32_t hi[8], mi[8];
+                const unsigned long long m1 = pk2(-1.f, -1.f);
 #pragma unroll
                 for (int w = 0; w < 16; w += 2) {
                     const __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[w], rr[w + 1]);
                     const float2 hf = __bfloat1622float2(h2);
+                    float m0, m1v;
+                    upk2(ffma2(pk2(hf.x, hf.y), m1, pk2(rr[w], rr[w + 1])), m0, m1v);  // r - hi, exact
                     hi[w / 2] = bf2_bits(h2);
-                    mi[w / 2] = bf2_bits(__floats2bfloat162_rn(rr[w] - hf.x, rr[w + 1] - hf.y));
+                    mi[w / 2] = bf2_bits(__floats2bfloat162_rn(m0, m1v));
                 }
                 tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + tb / 2), hi);
                 tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + 32 + tb / 2), mi);
                 tmem_wait_st();
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&barE[it & 3]);
         }
-        tc_fence_before();
-        fail = __syncthreads_or(!ok) != 0;
-        tc_fence_after();
-        if (fail) break;
-        if (tid == 0) {
-            // A stage sA is consumed: it takes chunk q + nA
-            if (it + nA < nq) issue_a(q + nA);
-            if (GRAD) {
-                issue_gemm2(q);
-                if (it + 1 < nq && it >= 1) issue_pt(q + 1);
-            }
-            // accumulator buffer b is consumed: GEMM1 of chunk q + 2 goes there
-            if (it + 2 < nq) issue_gemm1(q + 2);
-            // W stage of chunk q (GEMM1 done) takes chunk q + 3
-            if (it + 3 < nq) issue_pack(q + 3);
+        if (GRAD && ok) {
+            ok = mbar_wait_bounded(&barG2, (unsigned)(nq - 1) & 1u);
+            tc_fence_after();
+            ok = __all_sync(0xffffffffu, ok);
         }
     }
-    if (GRAD && !fail) {
-        ok = ok && mbar_wait_bounded(&barG2, (unsigned)(nq - 1) & 1u);
-        tc_fence_after();
-    }
-    if (tid == 0) ok = ok && ok0;
-    fail = __syncthreads_or(!ok) != 0;
-    if (!fail) {
-        red[grp][orow] = lacc;
+    const bool fail = __syncthreads_or(!ok) != 0;
+    if (!fail && !producer) {
+        red[grp][orow] = (double)lacc - (double)lcomp;
         if (GRAD && grp == 0) {
             float *g = p.part_grad + ((o0 + orow) * p.parts + part) * p.k;
 #pragma unroll
@@ -431,14 +535,16 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
         }
     }
     __syncthreads();
-    if (!fail && grp == 0 && own_ok)
+    if (!fail && !producer && grp == 0 && own_ok)
         p.part_loss[(o0 + orow) * p.parts + part] = red[0][orow] + red[1][orow] + red[2][orow] + red[3][orow];
-    if (fail && tid == 0) {
+    if (fail && producer && lane == 0) {
         atomicOr(p.err, 1);
         // wait (bounded) for the last copy into each stage and the last MMA
         // batches: every earlier one completed before a later one was issued
         for (int c = p_issued - 3 > 0 ? p_issued - 3 : 0; c < p_issued; ++c)
             mbar_wait_bounded(&barP[c % 3], (unsigned)(c / 3) & 1u);
+        for (int c = l_issued - 3 > 0 ? l_issued - 3 : 0; c < l_issued; ++c)
+            mbar_wait_bounded(&barL[c % 3], (unsigned)(c / 3) & 1u);
         for (int c = a_issued - nA > 0 ? a_issued - nA : 0; c < a_issued; ++c)
             mbar_wait_bounded(&barA[c % nA], (unsigned)(c / nA) & 1u);
         for (int c = t_issued - 2 > 0 ? t_issued - 2 : 0; c < t_issued; ++c)
@@ -456,10 +562,10 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 }
 
 // The other factor W (rows x k, FP32) split x = hi + mid + lo into both packed
-// layouts: K-major over k (row r, coordinate c of part w at
-// w pk_part + core_index(r, c, KP)), all three parts; and, per chunk of kDnNT
-// rows, K-major over the chunk rows (chunk q, element (c, t) of part w at
-// w pt_part + q KP kDnNT + core_index(c, t, kDnNT)), parts hi and mid.  Rows
+// layouts, swizzled K-major (sw_off): over k (row r, coordinate c of part w at
+// byte w part 2 + sw_off(r, c, 2 KP)), all three parts; and, per chunk of
+// kDnNT rows, over the chunk rows (chunk q, element (c, t) of part w at byte
+// w part 2 + q KP kDnNT 2 + sw_off(c, t, 2 kDnNT)), parts hi and mid.  Rows
 // from `rows` to rows_pad and coordinates from k to KP are zero.
 static __global__ void dense_pack_kernel(const float *__restrict__ W, int64_t rows, int k, int KP,
                                          int64_t rows_pad, int64_t part, __nv_bfloat16 *__restrict__ pk,
@@ -472,13 +578,15 @@ static __global__ void dense_pack_kernel(const float *__restrict__ W, int64_t ro
     const float v = (r < rows && c < k) ? W[r * k + c] : 0.f;
     __nv_bfloat16 hi, mid, lo;
     split3(v, hi, mid, lo);
-    const int64_t ik = core_index(r, c, KP);
+    // 8-row groups are contiguous, so the swizzle of a global row is that of
+    // its row within any 64-row chunk
+    const int64_t ik = (r >> 3) * 8 * KP + sw_off((uint32_t)(r & 7), (uint32_t)c, 2 * KP) / 2;
     pk[ik] = hi;
     pk[part + ik] = mid;
     pk[2 * part + ik] = lo;
     const int64_t q = r / kDnNT;
     const int t = (int)(r - q * kDnNT);
-    const int64_t it = q * KP * kDnNT + core_index(c, t, kDnNT);
+    const int64_t it = q * KP * kDnNT + sw_off((uint32_t)c, (uint32_t)t, 2 * kDnNT) / 2;
     pt[it] = hi;
     pt[part + it] = mid;
 }
@@ -519,7 +627,7 @@ namespace {
 
 int dense_width(int k)
 {
-    for (int K : {16, 32, 48, 64})
+    for (int K : {16, 32, 64})
         if (k <= K) return K;
     return 0;
 }
@@ -566,7 +674,6 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     a.pt = d.pt;
     a.pack_part = d.pack_part;
     a.lossf = d.lossf;
-    a.gkind = d.gkind;
     a.parts = XSTEP ? d.parts_x : d.parts_y;
     a.nchunks = (a.nother + kDnNT - 1) / kDnNT;
     a.per_part = XSTEP ? d.per_part_x : d.per_part_y;
@@ -585,7 +692,6 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     }
     GLRM_DENSE_CASE(16)
     GLRM_DENSE_CASE(32)
-    GLRM_DENSE_CASE(48)
     GLRM_DENSE_CASE(64)
 #undef GLRM_DENSE_CASE
     return cudaErrorInvalidValue;
@@ -622,7 +728,7 @@ bool dense_supported(int k) { return dense_width(k) != 0; }
 void dense_free(glrm_s *h)
 {
     Dense &d = h->dn;
-    for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf, (void *)d.gkind})
+    for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf})
         if (p) cudaFree(p);
     d = Dense();
 }
@@ -681,8 +787,8 @@ cudaError_t dense_prepare(glrm_s *h)
     if ((e = cudaMalloc(&d.pk, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&d.pt, 2 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
     if ((e = encode_maps(h)) != cudaSuccess) return e;
-    // column losses in FP32, and the kind each 16-column group shares (-1:
-    // mixed; groups past n count as quadratic)
+    // column losses in FP32, each with the kind its 16-column group shares
+    // (-1: mixed)
     std::vector<float4> lf(h->n);
     for (int64_t j = 0; j < h->n; ++j) {
         const LossSpec &L = h->loss_host[j];
@@ -694,17 +800,22 @@ cudaError_t dense_prepare(glrm_s *h)
     const int64_t ngroups = (h->n + kDnNT - 1) / kDnNT * (kDnNT / 16);
     std::vector<int32_t> gk(ngroups, kLossQuad);
     for (int64_t g = 0; g * 16 < h->n; ++g) {
-        int32_t kd = h->loss_host[g * 16].kind;
-        for (int64_t j = g * 16; j < std::min<int64_t>(h->n, g * 16 + 16); ++j)
-            if (h->loss_host[j].kind != kd) kd = -1;
+        const LossSpec &L0 = h->loss_host[g * 16];
+        int32_t kd = L0.kind;
+        for (int64_t j = g * 16; j < std::min<int64_t>(h->n, g * 16 + 16); ++j) {
+            const LossSpec &L = h->loss_host[j];
+            if (L.kind != L0.kind || (float)L.param != (float)L0.param || L.levels != L0.levels) kd = -1;
+        }
         gk[g] = kd;
     }
+    for (int64_t j = 0; j < h->n; ++j) {
+        const int32_t kd = gk[j / 16];
+        memcpy(&lf[j].w, &kd, sizeof kd);
+    }
     if ((e = cudaMalloc(&d.lossf, (size_t)h->n * sizeof(float4))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&d.gkind, (size_t)ngroups * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(d.lossf, lf.data(), lf.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
-    if ((e = cudaMemcpy(d.gkind, gk.data(), gk.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
+
     Orient &R = h->csr, &C = h->csc;
     R.nseg = h->m;
     C.nseg = h->n;

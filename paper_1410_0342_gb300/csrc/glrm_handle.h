@@ -105,8 +105,7 @@ struct Dense {
     __nv_bfloat16 *pk = nullptr;  // packed other factor, K-major over k (parts hi, mid, lo)
     __nv_bfloat16 *pt = nullptr;  // packed other factor, K-major over chunk rows (parts hi, mid)
     int64_t pack_part = 0;        // elements per part
-    float4 *lossf = nullptr;      // n column losses in FP32 {kind bits, param, levels, 0}
-    int32_t *gkind = nullptr;     // per 16-column group: the shared kind, or -1
+    float4 *lossf = nullptr;      // n column losses in FP32 {kind bits, param, levels, group kind bits}
     alignas(64) unsigned char tmap_x[128] = {};  // CUtensorMap of A, X-step boxes
     alignas(64) unsigned char tmap_y[128] = {};  // CUtensorMap of A, Y-step boxes
 };

@@ -10,14 +10,14 @@ extern "C" int glrm_tc_gemm_bf16(const void *A_dev, const void *B_dev, float *D_
 {
     using namespace glrm;
     if (!A_dev || !B_dev || !D_dev) return GLRM_ERR_ARG;
-    if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % kTcNT || K % 16 || K > kTcMaxK) return GLRM_ERR_RANGE;
+    if (M <= 0 || N <= 0 || M % 128 || N % kTcNT || (K != 16 && K != 32 && K != 64 && K != 128)) return GLRM_ERR_RANGE;
     cudaStream_t st = (cudaStream_t)stream;
     int *err = nullptr;
     if (cudaGetSymbolAddress((void **)&err, g_tc_err) != cudaSuccess) return GLRM_ERR_CUDA;
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return GLRM_ERR_CUDA;
     // at least 57 KB of dynamic shared memory: at most 4 CTAs per SM, whose
-    // 4 x 64 TMEM columns always fit in the SM's 512
-    const size_t smem = std::max<size_t>((size_t)(128 + kTcNT) * kTcMaxK * 2, 57 * 1024);
+    // 4 x 64 TMEM columns always fit in the SM's 512 (1 KB slack aligns the base)
+    const size_t smem = std::max<size_t>((size_t)(128 + kTcNT) * kTcMaxK * 2 + 1024, 57 * 1024);
     if (cudaFuncSetAttribute(tc_gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return GLRM_ERR_CUDA;

@@ -95,11 +95,37 @@ __host__ __device__ __forceinline__ int64_t core_index(int64_t r, int c, int K)
     return ((r >> 3) * (K >> 3) + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
 }
 
+// Swizzled K-major operand layouts.  Rows of RB = 32, 64 or 128 bytes (16,
+// 32 or 64 BF16 values along K), 8-row groups of 8 RB bytes; inside a group
+// the 16-byte unit u of row r sits at u ^ (r % 8 >> (3 - log2(RB / 16)))
+// (the 32-, 64- and 128-byte swizzles: address bits 4.. are XORed with bits
+// 7..).  Every operand buffer starts on a 1024-byte boundary.
+__host__ __device__ constexpr uint32_t sw_off(uint32_t r, uint32_t c, uint32_t RB)
+{
+    const uint32_t off = r * RB + c * 2;
+    return off ^ (((off >> 7) & (RB / 16 - 1)) << 4);
+}
+
+// Layout-type field of the descriptor for rows of RB bytes.
+__host__ __device__ constexpr uint64_t sw_type(uint32_t RB)
+{
+    return RB == 128 ? 2ull : (RB == 64 ? 4ull : 6ull);
+}
+
+// Descriptor of a swizzled K-major operand at smem (the K offset of an MMA
+// inside a row is added to the start address): stride between 8-row groups
+// 8 RB, leading offset unused (1).
+__device__ __forceinline__ uint64_t umma_desc_sw(const void *smem, uint32_t RB)
+{
+    const uint64_t a = (uint64_t)((smem_u32(smem) >> 4) & 0x3FFF);
+    return a | (1ull << 16) | ((uint64_t)(((8 * RB) >> 4) & 0x3FFF) << 32) | (1ull << 46) | (sw_type(RB) << 61);
+}
+
 // D (M x N, row-major FP32) = A (M x K, row-major BF16) B^T (B: N x K,
 // row-major BF16).  One CTA of 128 threads per 128 x NT tile; M a multiple of
-// 128, N of NT, K of 16 and at most kTcMaxK.  The dynamic shared memory
-// (above half an SM's) keeps one CTA per SM so the TMEM allocation always
-// finds its columns.
+// 128, N of NT, K of 16 and at most kTcMaxK.  Operands in the swizzled K-major
+// layout with RB = 2K bytes per row for K <= 64, or (K = 128) two 64-wide
+// column blocks of 128-byte rows.
 constexpr int kTcMaxK = 128;
 constexpr int kTcNT = 64;
 
@@ -107,20 +133,25 @@ static __global__ void __launch_bounds__(128, 1)
 tc_gemm_bf16_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
                     float *__restrict__ D, int M, int N, int K, int *__restrict__ err)
 {
-    extern __shared__ __align__(128) unsigned char dsm[];
+    extern __shared__ __align__(1024) unsigned char dsm_tc[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tslot;
-    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(dsm);
-    __nv_bfloat16 *Bs = As + 128 * kTcMaxK;
+    unsigned char *base = dsm_tc + ((1024 - (smem_u32(dsm_tc) & 1023)) & 1023);
+    const int KB = K < 64 ? K : 64;           // K values per column block
+    const uint32_t RB = (uint32_t)KB * 2;     // bytes per row
+    const int nblk = K / KB;
+    unsigned char *As = base;                 // block j at As + j * 128 RB
+    unsigned char *Bs = base + (size_t)nblk * 128 * RB;  // block j at Bs + j * NT RB
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 128, n0 = (int64_t)blockIdx.y * kTcNT;
     for (int q = tid; q < 128 * K; q += 128) {
         const int r = q / K, c = q % K;
-        As[core_index(r, c, K)] = A[(r0 + r) * K + c];
+        *reinterpret_cast<__nv_bfloat16 *>(As + (c / KB) * 128 * RB + sw_off(r, c % KB, RB)) = A[(r0 + r) * K + c];
     }
     for (int q = tid; q < kTcNT * K; q += 128) {
         const int r = q / K, c = q % K;
-        Bs[core_index(r, c, K)] = B[(n0 + r) * K + c];
+        *reinterpret_cast<__nv_bfloat16 *>(Bs + (c / KB) * kTcNT * RB + sw_off(r, c % KB, RB)) =
+            B[(n0 + r) * K + c];
     }
     if (tid == 0) mbar_init(&bar, 1);
     if (warp == 0) tmem_alloc(&tslot, kTcNT);
@@ -132,8 +163,9 @@ tc_gemm_bf16_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__
     if (tid == 0) {
         const uint32_t idesc = umma_idesc_bf16(128, kTcNT);
         for (int ks = 0; ks < K / 16; ++ks) {
-            const uint64_t ad = umma_desc(As + ks * 16 * 8, 128, (uint32_t)(K * 16));
-            const uint64_t bd = umma_desc(Bs + ks * 16 * 8, 128, (uint32_t)(K * 16));
+            const int j = ks * 16 / KB, kk = ks * 16 % KB;
+            const uint64_t ad = umma_desc_sw(As + j * 128 * RB + kk * 2, RB);
+            const uint64_t bd = umma_desc_sw(Bs + j * kTcNT * RB + kk * 2, RB);
             umma_bf16(taddr, ad, bd, idesc, ks > 0);
         }
         umma_commit(&bar);

@@ -308,12 +308,13 @@ class DenseTable:
 
 
 def mixed_dense(m=100_000, n=1000, k=20, n_real=500, n_bool=300, levels=7, seed=BASE_SEED + 6,
-                name="mixed_dense", lam=0.01, block=8192):
+                name="mixed_dense", lam=0.01, block=8192, rx=None, ry=None):
     """The mixed-type table's recipe with every cell observed: Huber columns
     (Laplace(0, 0.5) noise, 1% of entries x20), hinge columns
     sign(X0 Y0 + N(0, 0.5^2)), ordinal columns binned at the column's
     empirical septiles of X0 Y0 (estimated on the first 20,000 rows); l1
-    (lambda) on X, nonnegativity on Y.  Generated in row blocks."""
+    (lambda) on X, nonnegativity on Y unless rx / ry say otherwise.  Generated
+    in row blocks."""
     rng = rng_for(seed)
     n_ord = n - n_real - n_bool
     assert n_ord >= 0
@@ -344,7 +345,7 @@ def mixed_dense(m=100_000, n=1000, k=20, n_real=500, n_bool=300, levels=7, seed=
     lv = np.concatenate([np.zeros(n_real), np.zeros(n_bool), np.full(n_ord, levels)]).astype(np.int32)
     Xi = rng.standard_normal((m, k))
     Yi = rng.standard_normal((n, k))
-    return DenseTable(name, m, n, k, A, kind, param, lv, (REG_L1, lam), (REG_NONNEG, 0.0), Xi, Yi)
+    return DenseTable(name, m, n, k, A, kind, param, lv, rx or (REG_L1, lam), ry or (REG_NONNEG, 0.0), Xi, Yi)
 
 
 # ------------------------------------------------------------ batched tables

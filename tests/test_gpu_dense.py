@@ -46,7 +46,7 @@ def test_dense_qpca_tiny_matches_oracle(G, oracle_mod):
 @pytest.mark.parametrize("m,n,k", [(1000, 301, 20), (777, 130, 33), (300, 64, 64), (129, 65, 16)])
 def test_dense_mixed_matches_oracle(G, oracle_mod, m, n, k):
     """Every loss kind (columns cycle quadratic, Huber, hinge, logistic,
-    ordinal), ragged m and n, k padded to 16 / 32 / 48 / 64."""
+    ordinal), ragged m and n, k padded to 16 / 32 / 64."""
     t = dense_mixed(m, n, k, seed=500 + k)
     g = G.GLRM.from_dense_table(t)
     synced_sweeps(g, oracle_mod, t, 6, rtol=1e-5)
@@ -73,6 +73,31 @@ def test_dense_objective_and_gradient(G, oracle_mod):
     for a, b in ((GX, oGX), (GY, oGY)):
         rel = np.linalg.norm(a.double().cpu().numpy() - b) / np.linalg.norm(b)
         assert rel < 1e-4, rel
+
+
+@pytest.mark.parametrize("k", [20, 64])
+def test_dense_long_loops_match_oracle(G, oracle_mod, k):
+    """20,000 x 2,000 mixed table: each CTA walks 8 or more 64-wide chunks, so
+    every staging ring and completion barrier wraps several times.  Objective
+    and gradient at random factors, then two synced sweeps."""
+    t = W.mixed_dense(m=20000, n=2000, k=k, n_real=1000, n_bool=600, seed=600 + k,
+                      rx=(2, 0.01), ry=(1, 0.1)).observed()
+    g = G.GLRM.from_dense_table(t)
+    p = oracle_problem(oracle_mod, t)
+    X = torch.as_tensor(t.X0, dtype=torch.float32, device="cuda")
+    Yt = torch.as_tensor(t.Yt0, dtype=torch.float32, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.glrm_objective_at(g.h, X, Yt, out)
+    of = p.objective(X.double().cpu().numpy(), Yt.double().cpu().numpy())
+    assert abs(out.item() - of) / of < 1e-5, (out.item(), of)
+    GX = torch.empty_like(X)
+    GY = torch.empty_like(Yt)
+    G.glrm_grad_at(g.h, X, Yt, GX, GY, include_reg=False)
+    oGX, oGY = p.gradient(X.double().cpu().numpy(), Yt.double().cpu().numpy())
+    for a, b in ((GX, oGX), (GY, oGY)):
+        rel = np.linalg.norm(a.double().cpu().numpy() - b) / np.linalg.norm(b)
+        assert rel < 1e-4, rel
+    synced_sweeps(g, oracle_mod, t, 2, rtol=1e-5)
 
 
 def test_dense_mixed_objective_gradient(G, oracle_mod):
