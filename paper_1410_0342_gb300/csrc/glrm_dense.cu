@@ -44,9 +44,11 @@ namespace glrm {
 constexpr int kDnNT = 64;        // chunk of the other dimension (UMMA N of GEMM1, K of GEMM2)
 constexpr int kDnRows = 128;     // own rows per CTA (UMMA M)
 constexpr int kDnWarps = 16;     // evaluating warp w: TMEM lanes 32 (w % 4) .. + 31, chunk columns 16 (w / 4) .. + 15
-constexpr int kDnThreads = (kDnWarps + 1) * 32;  // + the producer warp
-constexpr int kDnTmem = 256;     // TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), R at [192, 256)
-constexpr int kDnColG = 128, kDnColR = 192;
+constexpr int kDnThreads = (kDnWarps + 2) * 32;  // + the MMA warp and the copy warp
+// TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), R (hi, mid)
+// at [192, 256), the own rows (hi, mid, lo; KP / 2 columns each) from 256
+constexpr int kDnTmem = 512;
+constexpr int kDnColG = 128, kDnColR = 192, kDnColOwn = 256;
 constexpr int kDnMaxStages = 4;
 
 // Column loss with its parameters in FP32 (kind as int bits, Huber
@@ -69,17 +71,16 @@ struct DenseArgs {
 };
 
 // Dynamic shared memory of one CTA: the A stages first (1024-byte aligned for
-// the swizzled boxes; 1024 bytes of slack align the base), then the own
-// factor's three parts, three stages of W's three GEMM1 parts, two stages of
-// W's two GEMM2 parts and three stages of the loss table.
+// the swizzled boxes; 1024 bytes of slack align the base), then three stages
+// of W's three GEMM1 parts, two stages of W's two GEMM2 parts and three
+// stages of the loss table (every operand buffer on a 1024-byte boundary).
 template <bool XSTEP, bool GRAD, int KP>
 struct DnSmem {
-    static constexpr size_t own = (size_t)kDnRows * KP * 2;  // one BF16 part
     static constexpr size_t pk = (size_t)kDnNT * KP * 2;
     static constexpr size_t pt = GRAD ? (size_t)KP * kDnNT * 2 : 0;
     static constexpr size_t ls = XSTEP ? (size_t)kDnNT * sizeof(LossF) : 0;
     static constexpr size_t a = (size_t)kDnNT * kDnRows * 4;  // 32 KB A tile
-    static constexpr size_t fixed = 3 * own + 9 * pk + 4 * pt + 3 * ls;
+    static constexpr size_t fixed = 9 * pk + 4 * pt + 3 * ls;
     static size_t bytes(int nA) { return 1024 + fixed + (size_t)nA * a; }
 };
 
@@ -191,15 +192,19 @@ __device__ __forceinline__ void dn_block_any(const float (&u)[16], const float (
 // A tiles: X-step, two boxes of 32 columns x 128 own rows with the 128-byte
 // swizzle (16-byte unit u of row r at u ^ (r % 8): conflict-free row reads);
 // Y-step, one box of 128 own columns x 64 rows, unswizzled.
-// Warps 0 .. 15 evaluate the entries; warp 16 (lane 0) issues every copy and
-// MMA.  It learns from barU[c % 2] (one arrival per evaluating warp) that U of
-// chunk c has been read out of tensor memory, and issues GEMM1 of chunk c + 2
-// into that buffer at once; from barE[c % 4] that the entries of chunk c are
-// done (A stage read, R written), and issues the next copies and GEMM2.  The
-// evaluating warps never wait for each other inside the loop.  A warp can
-// start chunk c only after every warp has read U of chunk c - 2, so after
-// every warp has finished chunk c - 3: four barE barriers keep the arrivals
-// of different chunks apart.
+// Warps 0 .. 15 evaluate the entries; lane 0 of warp 16 issues the MMAs (and
+// the copies of W's GEMM1 parts), lane 0 of warp 17 the other copies.  The
+// MMA warp learns from barU[c % 2] (one arrival per evaluating warp) that U of
+// chunk c has been read out of tensor memory and issues GEMM1 of chunk c + 2
+// into that buffer at once; both learn from barE[c % 4] that the entries of
+// chunk c are done (A stage read, R written): the copy warp refills the
+// stages, the MMA warp issues GEMM2.  The evaluating warps never wait for each
+// other inside the loop.  A warp can start chunk c only after every warp has
+// read U of chunk c - 2, so after every warp has finished chunk c - 3: four
+// barE barriers keep the arrivals of different chunks apart, and neither
+// producer warp can fall two phases behind a barrier it waits on (the copy
+// warp issues the A tile every chunk c needs after the wait for chunk c - 4
+// at the latest; the MMA warp issues GEMM1 of c after its wait for c - 2).
 template <bool XSTEP, bool GRAD, int KP>
 __global__ void __launch_bounds__(kDnThreads, 1)
 dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
@@ -212,8 +217,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     unsigned char *base = dsm_dense + ((1024 - (smem_u32(dsm_dense) & 1023)) & 1023);
     unsigned char *ast = base;                                   // A stage s at ast + s * a
     unsigned char *fx = base + (size_t)p.nA * SM::a;             // fixed buffers
-    __nv_bfloat16 *own = reinterpret_cast<__nv_bfloat16 *>(fx);  // parts hi, mid, lo
-    unsigned char *pkst = fx + 3 * SM::own;                      // pk stage s at pkst + s * 3 pk
+    unsigned char *pkst = fx;                                    // pk stage s at pkst + s * 3 pk
     unsigned char *ptst = pkst + 9 * SM::pk;                     // pt stage s at ptst + s * 2 pt
     unsigned char *lsst = ptst + 4 * SM::pt;                     // loss table stage s at lsst + s * ls
 
@@ -226,7 +230,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     const int64_t qe = qb + p.per_part < p.nchunks ? qb + p.per_part : p.nchunks;
     const int nq = (int)(qe - qb);
     const int nA = p.nA;
-    const bool producer = warp == kDnWarps;
+    const bool producer = warp >= kDnWarps;  // kDnWarps: MMA warp, kDnWarps + 1: copy warp
     const bool own_ok = !producer && o0 + orow < p.nown;
     const int nown_t = (int)(p.nown - o0 < kDnRows ? p.nown - o0 : kDnRows);
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
@@ -246,27 +250,6 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
         mbar_init(&barU[1], kDnWarps);
         for (int s = 0; s < 4; ++s) mbar_init(&barE[s], kDnWarps);
     }
-    // own rows split in three, K-major core-matrix layout: one thread per
-    // (row, 8 coordinates), 16-byte stores
-    for (int q = tid; q < kDnRows * (KP / 8); q += kDnThreads) {
-        const int r = q / (KP / 8), c0 = (q - r * (KP / 8)) * 8;
-        uint32_t hv[4], mv[4], lv[4];
-#pragma unroll
-        for (int w = 0; w < 8; w += 2) {
-            const float v0 = (r < nown_t && c0 + w < p.k) ? p.F[(o0 + r) * p.k + c0 + w] : 0.f;
-            const float v1 = (r < nown_t && c0 + w + 1 < p.k) ? p.F[(o0 + r) * p.k + c0 + w + 1] : 0.f;
-            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-            split3(v0, h0, m0, l0);
-            split3(v1, h1, m1, l1);
-            hv[w / 2] = bf2_bits(__halves2bfloat162(h0, h1));
-            mv[w / 2] = bf2_bits(__halves2bfloat162(m0, m1));
-            lv[w / 2] = bf2_bits(__halves2bfloat162(l0, l1));
-        }
-        unsigned char *ob = reinterpret_cast<unsigned char *>(own) + sw_off(r, c0, 2 * KP);
-        *reinterpret_cast<uint4 *>(ob) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<uint4 *>(ob + SM::own) = make_uint4(mv[0], mv[1], mv[2], mv[3]);
-        *reinterpret_cast<uint4 *>(ob + 2 * SM::own) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-    }
     // Y-step: this thread's column loss, and whether the warp shares one kind
     LossF myspec = make_float4(__int_as_float(kLossQuad), 0.f, 0.f, 0.f);
     if (!XSTEP && own_ok) myspec = p.lossf[o0 + orow];
@@ -276,11 +259,36 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
         const int k0 = __shfl_sync(0xffffffffu, kd, 0);
         wkind = __all_sync(0xffffffffu, kd == k0) ? k0 : -1;
     }
-    fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = tslot;
+    // own rows split in three into tensor memory (GEMM1's A operand, two BF16
+    // values per column along k): warps 0 .. 3, one row per thread
+    if (grp == 0 && !producer) {
+#pragma unroll
+        for (int c0 = 0; c0 < KP; c0 += 16) {
+            uint32_t hv[8], mv[8], lv[8];
+#pragma unroll
+            for (int w = 0; w < 16; w += 2) {
+                const float v0 = (orow < nown_t && c0 + w < p.k) ? p.F[(o0 + orow) * p.k + c0 + w] : 0.f;
+                const float v1 = (orow < nown_t && c0 + w + 1 < p.k) ? p.F[(o0 + orow) * p.k + c0 + w + 1] : 0.f;
+                __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+                split3(v0, h0, m0, l0);
+                split3(v1, h1, m1, l1);
+                hv[w / 2] = bf2_bits(__halves2bfloat162(h0, h1));
+                mv[w / 2] = bf2_bits(__halves2bfloat162(m0, m1));
+                lv[w / 2] = bf2_bits(__halves2bfloat162(l0, l1));
+            }
+            tmem_st8(taddr + lane_base + (uint32_t)(kDnColOwn + c0 / 2), hv);
+            tmem_st8(taddr + lane_base + (uint32_t)(kDnColOwn + KP / 2 + c0 / 2), mv);
+            tmem_st8(taddr + lane_base + (uint32_t)(kDnColOwn + KP + c0 / 2), lv);
+        }
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     bool ok = true;
     float lacc = 0.f, lcomp = 0.f;
@@ -335,8 +343,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 tc_fence_after();
                 const uint32_t idesc = umma_idesc_bf16(kDnRows, kDnNT);
                 const unsigned char *w = pkst + s * 3 * SM::pk;
-                const unsigned char *ow = reinterpret_cast<const unsigned char *>(own);
-                constexpr uint32_t RB = 2 * KP;  // bytes per operand row; a K step of 16 is 32 bytes
+                constexpr uint32_t RB = 2 * KP;  // bytes per W row; a K step of 16 is 32 bytes, 8 own columns
                 // (own part, W part), smallest products first; hi . hi last
                 const int pa[6] = {1, 0, 2, 0, 1, 0};
                 const int pb[6] = {1, 2, 0, 1, 0, 0};
@@ -344,8 +351,9 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
                     for (int ks = 0; ks < KP / 16; ++ks)
-                        umma_bf16(taddr + (uint32_t)(b * kDnNT), umma_desc_sw(ow + pa[pr] * SM::own + ks * 32, RB),
-                                  umma_desc_sw(w + pb[pr] * SM::pk + ks * 32, RB), idesc, pr > 0 || ks > 0);
+                        umma_bf16_ta(taddr + (uint32_t)(b * kDnNT),
+                                     taddr + (uint32_t)(kDnColOwn + pa[pr] * (KP / 2) + ks * 8),
+                                     umma_desc_sw(w + pb[pr] * SM::pk + ks * 32, RB), idesc, pr > 0 || ks > 0);
                 umma_commit(&barG1[b]);
                 ++g1_issued;
                 return true;
@@ -372,45 +380,59 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 ++g2_issued;
                 return true;
             };
-            for (int s = 0; s < nA && s < nq; ++s) issue_a(qb + s);
-            for (int s = 0; s < 3 && s < nq; ++s) issue_pack(qb + s);
-            if (XSTEP)
-                for (int s = 0; s < 3 && s < nq; ++s) issue_ls(qb + s);
-            if (GRAD) {
-                issue_pt(qb);
-                if (nq > 1) issue_pt(qb + 1);
-            }
-            ok = issue_gemm1(qb);
-            if (ok && nq > 1) ok = issue_gemm1(qb + 1);
-            for (int it = 0; ok && it < nq; ++it) {
-                const int64_t q = qb + it;
-                // U of chunk q has been read (so GEMM1 of q is done): its accumulator
-                // buffer takes chunk q + 2, its W stage chunk q + 3
-                if (!mbar_wait_bounded(&barU[it & 1], (unsigned)(it >> 1) & 1u)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                if (it + 3 < nq) issue_pack(q + 3);
-                if (it + 2 < nq && !issue_gemm1(q + 2)) {
-                    ok = false;
-                    break;
-                }
-                // the entries of chunk q are done: its A stage, loss-table stage and
-                // (GEMM2 of q - 1 having completed before) R are free
-                if (!mbar_wait_bounded(&barE[it & 3], (unsigned)(it >> 2) & 1u)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                if (it + nA < nq) issue_a(q + nA);
-                if (XSTEP && it + 3 < nq) issue_ls(q + 3);
-                if (GRAD) {
-                    if (it >= 1 && it + 1 < nq) issue_pt(q + 1);  // GEMM2 of q - 1 (its stage) is done
-                    if (!issue_gemm2(q)) {
+            if (warp == kDnWarps) {
+                // MMA warp: W's GEMM1 parts, GEMM1 and GEMM2
+                for (int s = 0; s < 3 && s < nq; ++s) issue_pack(qb + s);
+                ok = issue_gemm1(qb);
+                if (ok && nq > 1) ok = issue_gemm1(qb + 1);
+                for (int it = 0; ok && it < nq; ++it) {
+                    const int64_t q = qb + it;
+                    // U of chunk q has been read (so GEMM1 of q is done): its
+                    // accumulator buffer takes chunk q + 2, its W stage chunk q + 3
+                    if (!mbar_wait_bounded(&barU[it & 1], (unsigned)(it >> 1) & 1u)) {
                         ok = false;
                         break;
                     }
+                    tc_fence_after();
+                    if (it + 3 < nq) issue_pack(q + 3);
+                    if (it + 2 < nq && !issue_gemm1(q + 2)) {
+                        ok = false;
+                        break;
+                    }
+                    if (GRAD) {
+                        // R of chunk q is written
+                        if (!mbar_wait_bounded(&barE[it & 3], (unsigned)(it >> 2) & 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        if (!issue_gemm2(q)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            } else {
+                // copy warp: A tiles, loss tables and W's GEMM2 parts
+                for (int s = 0; s < nA && s < nq; ++s) issue_a(qb + s);
+                if (XSTEP)
+                    for (int s = 0; s < 3 && s < nq; ++s) issue_ls(qb + s);
+                if (GRAD) {
+                    issue_pt(qb);
+                    if (nq > 1) issue_pt(qb + 1);
+                }
+                for (int it = 0; it < nq; ++it) {
+                    const int64_t q = qb + it;
+                    // the entries of chunk q are done: its A stage, loss-table stage
+                    // and (GEMM2 of q - 1 having completed before) the GEMM2 stage of
+                    // q - 1 are free
+                    if (!mbar_wait_bounded(&barE[it & 3], (unsigned)(it >> 2) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    if (it + nA < nq) issue_a(q + nA);
+                    if (XSTEP && it + 3 < nq) issue_ls(q + 3);
+                    if (GRAD && it >= 1 && it + 1 < nq) issue_pt(q + 1);
                 }
             }
         }
@@ -537,7 +559,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     __syncthreads();
     if (!fail && !producer && grp == 0 && own_ok)
         p.part_loss[(o0 + orow) * p.parts + part] = red[0][orow] + red[1][orow] + red[2][orow] + red[3][orow];
-    if (fail && producer && lane == 0) {
+    if (fail && producer && lane == 0) {  // each producer warp drains what it issued
         atomicOr(p.err, 1);
         // wait (bounded) for the last copy into each stage and the last MMA
         // batches: every earlier one completed before a later one was issued
