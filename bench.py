@@ -56,9 +56,11 @@ def parse():
                     help="rows of the mixed table (smaller for profiling runs)")
     ap.add_argument("--path", default="auto",
                     help="kernel paths 'X,Y' (auto, chunked, fused, blocked, masked, split)")
-    ap.add_argument("--form", default="sweep", choices=["sweep", "batched", "autograd", "completion"],
-                    help="sweep: the benchmark line; the others measure the batched, differentiable "
-                         "and matrix-completion forms on their own workloads")
+    ap.add_argument("--form", default="sweep",
+                    choices=["sweep", "batched", "autograd", "completion", "dense"],
+                    help="sweep: the benchmark line; the others measure the batched, differentiable, "
+                         "matrix-completion and dense (fully observed, tensor-core) forms on their own "
+                         "workloads")
     return ap.parse_args()
 
 
@@ -454,6 +456,37 @@ def run_form(args):
                      "value": t.nnz * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
                      "config": {"workload": "logistic Boolean table m=50000 n=2000 k=32, 20% "
                                             "missing, gamma=0.1, FP32", "nnz": t.nnz}})
+    elif args.form == "dense":
+        t = W.mixed_dense()
+        g = G.GLRM.from_dense_table(t, stream=st)
+        g.sweep(args.warmup, history=False)
+        G.glrm_timing_enable(g.h, True)
+        ms = _events(torch, st, lambda: g.sweep(args.steps, history=False))
+        kern = G.glrm_timing_read(g.h)
+        G.glrm_timing_enable(g.h, False)
+        per = {k: v[0] / v[1] for k, v in kern.items()}
+        nent = t.m * t.n
+        # dominant kernel: the X-step gradient pass; algorithmic bytes = A once
+        # (4 m n) + both factors (4 (m + n) k) + the partial gradients (4 m k)
+        top = max((k for k in per if k.startswith("dense_")), key=lambda k: per[k])
+        bytes_pass = 4.0 * nent + 4.0 * (t.m + t.n) * t.k + (4.0 * t.m * t.k if "grad" in top else 0.0)
+        flops_pass = (4.0 if "grad" in top else 2.0) * nent * t.k
+        peaks, source = measured_peaks()
+        hbm = peaks.get("hbm_gbs")
+        tc = peaks.get("bf16_tflops")
+        ach = bytes_pass / (per[top] / 1e3) / 1e9
+        line.update({
+            "metric": METRIC, "unit": UNIT, "value": nent * args.steps / (ms / 1e3),
+            "ms_per_step": ms / args.steps, "dtype": "fp32 (bf16 three-way split products, fp32 accumulation)",
+            "config": {"workload": "mixed-type table, fully observed: m=100000 n=1000 k=20 (500 Huber, "
+                                   "300 hinge, 200 ordinal d=7), l1(0.01) on X, nonneg on Y",
+                       "entries": nent, "inputs_vs_L2": "A is 400 MB > L2"},
+            "kernels_ms": per,
+            "roofline": {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm if hbm else None, "peak_source": source,
+                         "tensor_tflops": flops_pass / (per[top] / 1e3) / 1e12,
+                         "tensor_frac_of_bf16": (flops_pass / (per[top] / 1e3) / 1e12) / tc if tc else None}})
+        g.close()
     else:
         t = W.completion()
         res = {}
