@@ -147,10 +147,9 @@ int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host
  * the step sizes to 1/n (rows) and 1/m (columns).  Sweeps, objectives and
  * gradients then run the dense form on the tensor cores: U = X Y, the loss
  * derivatives R and R Y^T, X^T R (the contractions of Section 7.2's
- * gradient) by tcgen05 MMAs on BF16 splits, FP32 accumulation: U from a
- * three-part split x = hi + mid + lo and six products (error about 2^-25 of
- * sum_c |x_c y_c|, FP32 quality), the gradient contractions from two-part
- * splits and three products (about 2^-16 relative); everything else in FP32.  glrm_als_sweep and
+ * gradient) by tcgen05 MMAs on BF16 splits, FP32 accumulation: every value
+ * split in three, x = hi + mid + lo, and six products summed (error about
+ * 2^-25 of sum_c |x_c y_c|, FP32 quality); everything else in FP32.  glrm_als_sweep and
  * glrm_set_path return GLRM_ERR_STATE on a dense table; glrm_get_path reports
  * GLRM_PATH_DENSE.  Synchronises.  A later glrm_set_observed replaces the
  * table. */

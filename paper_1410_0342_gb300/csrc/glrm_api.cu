@@ -348,7 +348,8 @@ int alloc_scratch(glrm_s *h)
     Scratch &s = h->s;
     free_scratch(s);
     const size_t es = elem_size(h->prec);
-    const int64_t nch = std::max<int64_t>(1, std::max(partial_slots(h->csr), partial_slots(h->csc)));
+    int64_t nch = std::max<int64_t>(1, std::max(partial_slots(h->csr), partial_slots(h->csc)));
+    if (h->dn.on) nch = std::max<int64_t>(nch, h->dn.slots);
     const int Kt = std::max(h->k, tiled_width(h->k));
     const int64_t mx = std::max(h->m, h->n);
     CK(cudaMalloc(&s.part_grad, (size_t)nch * Kt * es));
@@ -407,6 +408,57 @@ const char *flag_message(int f)
     if (f & 32) return "CSR and CSC values differ for the same entry";
     if (f & 64) return "a value outside its column loss's domain (Boolean: -1 or +1; ordinal: integer in 1..d)";
     return "invalid observed set";
+}
+
+// Density from which an FP32 observed set is stored densely (NaN marking the
+// missing cells) and swept by the tensor-core form: the dense passes cost
+// about 13 ps per cell against about 30 ps per observed entry for the masked
+// sparse path (mixed table, k = 20, measured on GB300).
+constexpr double kDenseAutoDensity = 0.4;
+
+// Set up the kernel paths of an observed set (CSR / CSC and their chunk tables
+// already built): the dense form, or a sparse path per half-step.
+int configure_paths(glrm_s *h)
+{
+    const bool force_dense = h->path_x == GLRM_PATH_DENSE || h->path_y == GLRM_PATH_DENSE;
+    bool dense = false;
+    if (force_dense) {
+        if (h->path_x != GLRM_PATH_DENSE && h->path_y != GLRM_PATH_DENSE)
+            return fail(h, GLRM_ERR_ARG, "bad path");
+        if ((h->path_x != GLRM_PATH_DENSE && h->path_x != GLRM_PATH_AUTO) ||
+            (h->path_y != GLRM_PATH_DENSE && h->path_y != GLRM_PATH_AUTO))
+            return fail(h, GLRM_ERR_ARG, "the dense path runs both half-steps");
+        if (h->prec != GLRM_FP32 || !dense_supported(h->k))
+            return fail(h, GLRM_ERR_ARG, "the dense path needs an FP32 model with k <= 64");
+        dense = true;
+    } else if (h->path_x == GLRM_PATH_AUTO && h->path_y == GLRM_PATH_AUTO && h->prec == GLRM_FP32 &&
+               dense_supported(h->k) && (double)h->nnz >= kDenseAutoDensity * (double)h->m * (double)h->n) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        dense = (double)h->m * (double)((h->n + 3) / 4 * 4) * 4.0 <= 0.5 * (double)free_b;
+    }
+    dense_free(h);
+    if (!dense) {
+        int rc = choose_mode(h, h->csr, true, h->path_x);
+        if (rc == GLRM_OK) rc = choose_mode(h, h->csc, false, h->path_y);
+        return rc;
+    }
+    // the chunk tables stay (ALS runs on them); the tile layouts go
+    int rc = choose_mode(h, h->csr, true, GLRM_PATH_CHUNKED);
+    if (rc == GLRM_OK) rc = choose_mode(h, h->csc, false, GLRM_PATH_CHUNKED);
+    if (rc != GLRM_OK) return rc;
+    Dense &d = h->dn;
+    d.lda = (h->n + 3) / 4 * 4;
+    CK(cudaMalloc(&d.A, std::max<size_t>((size_t)h->m * d.lda * sizeof(float), 16)));
+    cudaError_t e = launch_dense_scatter(h);
+    if (e == cudaSuccess) e = dense_prepare(h);
+    if (e != cudaSuccess) {
+        dense_free(h);
+        return cuda_fail(h, e, "dense set-up");
+    }
+    d.missing = true;
+    d.on = true;
+    return GLRM_OK;
 }
 
 int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *ci, const void *rv,
@@ -500,8 +552,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         CK(cudaMemcpy(o->segchunk, segchunk.data(), segchunk.size() * sizeof(int32_t),
                       cudaMemcpyHostToDevice));
     }
-    rc = choose_mode(h, R, true, h->path_x);
-    if (rc == GLRM_OK) rc = choose_mode(h, C, false, h->path_y);
+    rc = configure_paths(h);
     if (rc == GLRM_OK) rc = alloc_scratch(h);
     if (rc != GLRM_OK) return rc;
     h->have_omega = true;
@@ -553,13 +604,14 @@ int set_dense_impl(glrm_s *h, const void *A, int64_t lda, cudaMemcpyKind kind)
                     (hflag & 8) ? "non-finite value in the table" : flag_message(hflag));
     }
     h->nnz = h->m * h->n;
+    h->csr.nseg = h->m;
+    h->csc.nseg = h->n;
     e = dense_prepare(h);
     if (e != cudaSuccess) {
         dense_free(h);
-        free_orient(h->csr);
-        free_orient(h->csc);
         return cuda_fail(h, e, "dense_prepare");
     }
+    d.missing = false;
     d.on = true;
     int rc = alloc_scratch(h);
     if (rc != GLRM_OK) return rc;
@@ -572,7 +624,7 @@ int set_dense_impl(glrm_s *h, const void *A, int64_t lda, cudaMemcpyKind kind)
 
 cudaError_t reset_steps_any(glrm_s *h)
 {
-    if (h->dn.on) return dense_reset_steps(h);
+    if (h->dn.on && !h->dn.missing) return dense_reset_steps(h);
     return h->prec == GLRM_FP64 ? Engine<double>::reset_steps(h) : Engine<float>::reset_steps(h);
 }
 
@@ -862,7 +914,8 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_als_sweep before glrm_set_observed");
     if (nsweeps < 0) return fail(h, GLRM_ERR_ARG, "nsweeps < 0");
-    if (h->dn.on) return fail(h, GLRM_ERR_STATE, "ALS runs on an observed set, not on a dense table");
+    if (h->dn.on && !h->dn.missing)
+        return fail(h, GLRM_ERR_STATE, "ALS runs on an observed set, not on a dense table");
     if (h->rx_kind != kRegQuad || h->ry_kind != kRegQuad || h->rx_w != h->ry_w || !(h->rx_w > 0.0))
         return fail(h, GLRM_ERR_ARG,
                     "ALS needs quadratic regularisers of equal weight gamma > 0 on X and Y");
@@ -956,15 +1009,19 @@ int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     for (int p : {xstep_path, ystep_path})
-        if (p < GLRM_PATH_AUTO || p > GLRM_PATH_MASKED_SPLIT) return fail(h, GLRM_ERR_ARG, "bad path");
-    if (h->dn.on) return fail(h, GLRM_ERR_STATE, "a dense table has one path");
+        if (p < GLRM_PATH_AUTO || p > GLRM_PATH_DENSE) return fail(h, GLRM_ERR_ARG, "bad path");
+    if (h->dn.on && !h->dn.missing) {
+        for (int p : {xstep_path, ystep_path})
+            if (p != GLRM_PATH_AUTO && p != GLRM_PATH_DENSE)
+                return fail(h, GLRM_ERR_STATE, "a fully observed table (glrm_set_dense) has the dense path only");
+        return GLRM_OK;
+    }
     h->path_x = xstep_path;
     h->path_y = ystep_path;
     if (!h->have_omega) return GLRM_OK;
     DeviceGuard dg(h->device);
     CK(cudaStreamSynchronize(h->stream));
-    int rc = choose_mode(h, h->csr, true, h->path_x);
-    if (rc == GLRM_OK) rc = choose_mode(h, h->csc, false, h->path_y);
+    int rc = configure_paths(h);
     if (rc == GLRM_OK) {
         // keep the fit state; only scratch depends on the paths
         const int hist_cap = h->s.hist_cap;
@@ -973,8 +1030,7 @@ int glrm_set_path(glrm_t h, int32_t xstep_path, int32_t ystep_path)
     }
     if (rc != GLRM_OK) {
         h->path_x = h->path_y = GLRM_PATH_AUTO;
-        choose_mode(h, h->csr, true, GLRM_PATH_AUTO);
-        choose_mode(h, h->csc, false, GLRM_PATH_AUTO);
+        configure_paths(h);
         alloc_scratch(h);
         return rc;
     }

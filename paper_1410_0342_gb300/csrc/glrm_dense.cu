@@ -6,30 +6,31 @@
 // the X-step, Y in the Y-step) and the "other" factor W is held fixed.  Each
 // half-step is five launches:
 //   pack   W split into BF16 parts x = hi + mid + lo (+ at most 2^-26 |x|) in
-//          the tensor core's canonical K-major shared-memory layout: all three
-//          parts with K = k (B operand of GEMM1), hi and mid per 64-row chunk
-//          with K = the chunk rows (B operand of GEMM2);
+//          the tensor core's swizzled K-major shared-memory layouts: with K = k
+//          (B operand of GEMM1) and, per 64-row chunk, with K = the chunk rows
+//          (B operand of GEMM2);
 //   grad   per 128 own rows and a range of 64-wide chunks of the other
-//          dimension: U = F W^T (GEMM1: the six BF16 products of the split
-//          whose order is at least 2^-18, FP32 accumulation in tensor memory),
-//          L(U, A) and its derivative R against the A tile (staged by tensor
-//          TMA), R split hi + mid into tensor memory, G += R W (GEMM2: three
-//          products, R read from tensor memory);
+//          dimension: U = F W^T (GEMM1), L(U, A) and its derivative R against
+//          the A tile (staged by tensor TMA; a NaN cell is a missing entry and
+//          contributes nothing), R split in three into tensor memory, G += R W
+//          (GEMM2);
 //   prox   f+ = prox(f - alpha g) per row / column (shared with the sparse form);
 //   loss   the candidate's losses (GEMM1 and L only);
 //   decide accept when the objective did not increase (shared with the
 //          sparse form).
-// Products U: the dropped terms (mid.lo, lo.mid, lo.lo) and the split
-// remainders are about 2^-25 of sum_c |f_c w_c|, below FP32's own rounding of
-// a k-term dot product, so losses and the accept / reject test see FP32
-// quality values.  Gradients: R and W split in two, three products, about
-// 2^-16 relative.
+// Both GEMMs sum the six BF16 products of the splits whose order is at least
+// 2^-18 (hi.hi, hi.mid, mid.hi, mid.mid, hi.lo, lo.hi) in FP32 in tensor
+// memory; the dropped terms (mid.lo, lo.mid, lo.lo) and the split remainders
+// are about 2^-25 of sum |f_c w_c|, below FP32's own rounding of a k-term
+// dot product, so losses, the accept / reject test and the gradients see FP32
+// quality values.
 //
-// Pipeline of one CTA (thread 0 issues every copy and MMA; 16 warps run the
-// per-entry work): GEMM1 runs two chunks ahead into a double-buffered
-// accumulator, so the tensor core computes U of chunk q + 1 while the warps
-// evaluate the losses of chunk q; W's GEMM1 parts are triple-buffered, its
-// GEMM2 parts and the A tiles double- (or more) buffered.
+// Pipeline of one CTA (one lane each of three producer warps issues the
+// GEMM1 MMAs, the copies and the GEMM2 MMAs; 16 warps run the per-entry
+// work): GEMM1 runs two chunks ahead into a double-buffered accumulator, so
+// the tensor core computes U of chunk q + 1 while the warps evaluate the
+// losses of chunk q; W's GEMM1 parts are triple-buffered, its GEMM2 parts and
+// the A tiles double- (or more) buffered.
 #include <cuda.h>
 
 #include <string.h>
@@ -44,11 +45,12 @@ namespace glrm {
 constexpr int kDnNT = 64;        // chunk of the other dimension (UMMA N of GEMM1, K of GEMM2)
 constexpr int kDnRows = 128;     // own rows per CTA (UMMA M)
 constexpr int kDnWarps = 16;     // evaluating warp w: TMEM lanes 32 (w % 4) .. + 31, chunk columns 16 (w / 4) .. + 15
-constexpr int kDnThreads = (kDnWarps + 2) * 32;  // + the MMA warp and the copy warp
-// TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), R (hi, mid)
-// at [192, 256), the own rows (hi, mid, lo; KP / 2 columns each) from 256
+constexpr int kDnThreads = (kDnWarps + 3) * 32;  // + the GEMM1 warp, the copy warp, the GEMM2 warp
+// TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), R (hi, mid,
+// lo; 32 columns each) at [192, 288), the own rows (hi, mid, lo; KP / 2
+// columns each) from 288
 constexpr int kDnTmem = 512;
-constexpr int kDnColG = 128, kDnColR = 192, kDnColOwn = 256;
+constexpr int kDnColG = 128, kDnColR = 192, kDnColOwn = 288;
 constexpr int kDnMaxStages = 4;
 
 // Column loss with its parameters in FP32 (kind as int bits, Huber
@@ -80,7 +82,7 @@ struct DnSmem {
     static constexpr size_t pt = GRAD ? (size_t)KP * kDnNT * 2 : 0;
     static constexpr size_t ls = XSTEP ? (size_t)kDnNT * sizeof(LossF) : 0;
     static constexpr size_t a = (size_t)kDnNT * kDnRows * 4;  // 32 KB A tile
-    static constexpr size_t fixed = 9 * pk + 4 * pt + 3 * ls;
+    static constexpr size_t fixed = 9 * pk + 6 * pt + 3 * ls;
     static size_t bytes(int nA) { return 1024 + fixed + (size_t)nA * a; }
 };
 
@@ -143,12 +145,22 @@ __device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsign
 
 // Losses and derivatives of 16 entries that all lie inside the table and
 // share one loss kind with parameters prm (Huber threshold) and lev (ordinal
-// level count).  Quadratic entries run two at a time in packed FP32.
-template <int KIND>
+// level count).  Quadratic entries run two at a time in packed FP32.  MISS:
+// a NaN value marks a missing entry, which contributes nothing.
+template <int KIND, bool MISS>
 __device__ __forceinline__ void dn_block(const float (&u)[16], const float (&a)[16], float prm, float lev,
                                          float (&rr)[16], float &lsum)
 {
-    if constexpr (KIND == kLossQuad) {
+    if constexpr (MISS) {
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+            const bool v = a[w] == a[w];
+            float L;
+            const float d = loss_deriv_k<KIND, float>(u[w], v ? a[w] : 0.f, prm, lev, L);
+            lsum += v ? L : 0.f;
+            rr[w] = v ? d : 0.f;
+        }
+    } else if constexpr (KIND == kLossQuad) {
         const unsigned long long m1 = pk2(-1.f, -1.f);
         unsigned long long acc = pk2(0.f, 0.f);
 #pragma unroll
@@ -170,7 +182,8 @@ __device__ __forceinline__ void dn_block(const float (&u)[16], const float (&a)[
     }
 }
 
-// Any mix of kinds, entries outside the table (bit clear in `valid`) give 0.
+// Any mix of kinds; entries outside the table (bit clear in `valid`) and
+// missing entries (NaN) give 0.
 // X-step: the entries are 16 columns (losses in lf); Y-step: one column (own).
 template <bool XSTEP>
 __device__ __forceinline__ void dn_block_any(const float (&u)[16], const float (&a)[16], const LossF *lf,
@@ -181,7 +194,7 @@ __device__ __forceinline__ void dn_block_any(const float (&u)[16], const float (
         const LossF sp = XSTEP ? lf[w] : own;
         float L;
         const float d = loss_deriv_kind<float>(__float_as_int(sp.x), u[w], a[w], sp.y, sp.z, L);
-        const bool v = (valid >> w) & 1u;
+        const bool v = ((valid >> w) & 1u) && a[w] == a[w];
         lsum += v ? L : 0.f;
         rr[w] = v ? d : 0.f;
     }
@@ -205,7 +218,7 @@ __device__ __forceinline__ void dn_block_any(const float (&u)[16], const float (
 // producer warp can fall two phases behind a barrier it waits on (the copy
 // warp issues the A tile every chunk c needs after the wait for chunk c - 4
 // at the latest; the MMA warp issues GEMM1 of c after its wait for c - 2).
-template <bool XSTEP, bool GRAD, int KP>
+template <bool XSTEP, bool GRAD, int KP, bool MISS>
 __global__ void __launch_bounds__(kDnThreads, 1)
 dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 {
@@ -218,8 +231,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     unsigned char *ast = base;                                   // A stage s at ast + s * a
     unsigned char *fx = base + (size_t)p.nA * SM::a;             // fixed buffers
     unsigned char *pkst = fx;                                    // pk stage s at pkst + s * 3 pk
-    unsigned char *ptst = pkst + 9 * SM::pk;                     // pt stage s at ptst + s * 2 pt
-    unsigned char *lsst = ptst + 4 * SM::pt;                     // loss table stage s at lsst + s * ls
+    unsigned char *ptst = pkst + 9 * SM::pk;                     // pt stage s at ptst + s * 3 pt
+    unsigned char *lsst = ptst + 6 * SM::pt;                     // loss table stage s at lsst + s * ls
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, grp = (warp >> 2) & 3;
@@ -230,7 +243,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     const int64_t qe = qb + p.per_part < p.nchunks ? qb + p.per_part : p.nchunks;
     const int nq = (int)(qe - qb);
     const int nA = p.nA;
-    const bool producer = warp >= kDnWarps;  // kDnWarps: MMA warp, kDnWarps + 1: copy warp
+    // kDnWarps: GEMM1 warp, kDnWarps + 1: copy warp, kDnWarps + 2: GEMM2 warp
+    const bool producer = warp >= kDnWarps;
     const bool own_ok = !producer && o0 + orow < p.nown;
     const int nown_t = (int)(p.nown - o0 < kDnRows ? p.nown - o0 : kDnRows);
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
@@ -316,10 +330,11 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
             };
             auto issue_pt = [&](int64_t q) {  // GEMM2's W parts, stage q % 2
                 const int s = (int)((q - qb) & 1);
-                unsigned char *st = ptst + s * 2 * SM::pt;
-                mbar_expect_tx(&barT[s], (unsigned)(2 * SM::pt));
-                bulk_g2s(st, p.pt + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
-                bulk_g2s(st + SM::pt, p.pt + p.pack_part + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
+                unsigned char *st = ptst + s * 3 * SM::pt;
+                mbar_expect_tx(&barT[s], (unsigned)(3 * SM::pt));
+#pragma unroll
+                for (int w = 0; w < 3; ++w)
+                    bulk_g2s(st + w * SM::pt, p.pt + w * p.pack_part + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
                 ++t_issued;
             };
             auto issue_a = [&](int64_t q) {  // the A tile, stage q % nA (out-of-range elements read as 0)
@@ -365,12 +380,12 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 if (!mbar_wait_bounded(&barT[s], (unsigned)(c >> 1) & 1u)) return false;
                 tc_fence_after();
                 const uint32_t idesc = umma_idesc_bf16(kDnRows, KP);
-                const unsigned char *wt = ptst + s * 2 * SM::pt;
-                // (R part, W part): mid.hi, hi.mid, hi.hi; a K = 16 step of R is 8 columns
-                const int pa[3] = {1, 0, 0};
-                const int pb[3] = {0, 1, 0};
+                const unsigned char *wt = ptst + s * 3 * SM::pt;
+                // (R part, W part), smallest products first; a K = 16 step of R is 8 columns
+                const int pa[6] = {1, 0, 2, 0, 1, 0};
+                const int pb[6] = {1, 2, 0, 1, 0, 0};
 #pragma unroll
-                for (int pr = 0; pr < 3; ++pr)
+                for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
                     for (int ks = 0; ks < kDnNT / 16; ++ks)
                         umma_bf16_ta(taddr + kDnColG, taddr + (uint32_t)(kDnColR + pa[pr] * 32 + ks * 8),
@@ -381,7 +396,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 return true;
             };
             if (warp == kDnWarps) {
-                // MMA warp: W's GEMM1 parts, GEMM1 and GEMM2
+                // GEMM1 warp: W's GEMM1 parts and GEMM1
                 for (int s = 0; s < 3 && s < nq; ++s) issue_pack(qb + s);
                 ok = issue_gemm1(qb);
                 if (ok && nq > 1) ok = issue_gemm1(qb + 1);
@@ -399,17 +414,18 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                         ok = false;
                         break;
                     }
-                    if (GRAD) {
-                        // R of chunk q is written
-                        if (!mbar_wait_bounded(&barE[it & 3], (unsigned)(it >> 2) & 1u)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        if (!issue_gemm2(q)) {
-                            ok = false;
-                            break;
-                        }
+                }
+            } else if (warp == kDnWarps + 2) {
+                // GEMM2 warp (gradient passes): G += R W once R of chunk q is written
+                for (int it = 0; GRAD && it < nq; ++it) {
+                    if (!mbar_wait_bounded(&barE[it & 3], (unsigned)(it >> 2) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (!issue_gemm2(qb + it)) {
+                        ok = false;
+                        break;
                     }
                 }
             } else {
@@ -490,11 +506,11 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 }
                 if (__all_sync(0xffffffffu, valid == 0xffffu)) {
                     switch (kind) {
-                    case kLossQuad: dn_block<kLossQuad>(u, a, prm, lev, rr, lsum); break;
-                    case kLossHuber: dn_block<kLossHuber>(u, a, prm, lev, rr, lsum); break;
-                    case kLossHinge: dn_block<kLossHinge>(u, a, prm, lev, rr, lsum); break;
-                    case kLossLogistic: dn_block<kLossLogistic>(u, a, prm, lev, rr, lsum); break;
-                    case kLossOrdinal: dn_block<kLossOrdinal>(u, a, prm, lev, rr, lsum); break;
+                    case kLossQuad: dn_block<kLossQuad, MISS>(u, a, prm, lev, rr, lsum); break;
+                    case kLossHuber: dn_block<kLossHuber, MISS>(u, a, prm, lev, rr, lsum); break;
+                    case kLossHinge: dn_block<kLossHinge, MISS>(u, a, prm, lev, rr, lsum); break;
+                    case kLossLogistic: dn_block<kLossLogistic, MISS>(u, a, prm, lev, rr, lsum); break;
+                    case kLossOrdinal: dn_block<kLossOrdinal, MISS>(u, a, prm, lev, rr, lsum); break;
                     default: dn_block_any<XSTEP>(u, a, lf, myspec, valid, rr, lsum); break;
                     }
                 } else {
@@ -514,19 +530,27 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 tc_fence_after();
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
-                uint32_t hi[8], mi[8];
+                uint32_t hi[8], mi[8], lo[8];
                 const unsigned long long m1 = pk2(-1.f, -1.f);
 #pragma unroll
                 for (int w = 0; w < 16; w += 2) {
+                    // r = hi + mid + lo, each remainder exact in FP32
                     const __nv_bfloat162 h2 = __floats2bfloat162_rn(rr[w], rr[w + 1]);
                     const float2 hf = __bfloat1622float2(h2);
-                    float m0, m1v;
-                    upk2(ffma2(pk2(hf.x, hf.y), m1, pk2(rr[w], rr[w + 1])), m0, m1v);  // r - hi, exact
+                    const unsigned long long r1 = ffma2(pk2(hf.x, hf.y), m1, pk2(rr[w], rr[w + 1]));
+                    float a0, a1;
+                    upk2(r1, a0, a1);
+                    const __nv_bfloat162 m2 = __floats2bfloat162_rn(a0, a1);
+                    const float2 mf = __bfloat1622float2(m2);
+                    float b0, b1;
+                    upk2(ffma2(pk2(mf.x, mf.y), m1, r1), b0, b1);
                     hi[w / 2] = bf2_bits(h2);
-                    mi[w / 2] = bf2_bits(__floats2bfloat162_rn(m0, m1v));
+                    mi[w / 2] = bf2_bits(m2);
+                    lo[w / 2] = bf2_bits(__floats2bfloat162_rn(b0, b1));
                 }
                 tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + tb / 2), hi);
                 tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + 32 + tb / 2), mi);
+                tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + 64 + tb / 2), lo);
                 tmem_wait_st();
             }
             tc_fence_before();
@@ -587,7 +611,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 // layouts, swizzled K-major (sw_off): over k (row r, coordinate c of part w at
 // byte w part 2 + sw_off(r, c, 2 KP)), all three parts; and, per chunk of
 // kDnNT rows, over the chunk rows (chunk q, element (c, t) of part w at byte
-// w part 2 + q KP kDnNT 2 + sw_off(c, t, 2 kDnNT)), parts hi and mid.  Rows
+// w part 2 + q KP kDnNT 2 + sw_off(c, t, 2 kDnNT)), all three parts.  Rows
 // from `rows` to rows_pad and coordinates from k to KP are zero.
 static __global__ void dense_pack_kernel(const float *__restrict__ W, int64_t rows, int k, int KP,
                                          int64_t rows_pad, int64_t part, __nv_bfloat16 *__restrict__ pk,
@@ -611,6 +635,7 @@ static __global__ void dense_pack_kernel(const float *__restrict__ W, int64_t ro
     const int64_t it = q * KP * kDnNT + sw_off((uint32_t)c, (uint32_t)t, 2 * kDnNT) / 2;
     pt[it] = hi;
     pt[part + it] = mid;
+    pt[2 * part + it] = lo;
 }
 
 // Values outside a column loss's domain (flag 64) or not finite (flag 8).
@@ -631,6 +656,16 @@ static __global__ void dense_validate_kernel(const float *__restrict__ A, int64_
         if (s.kind == kLossOrdinal && (a != floorf(a) || a < 1.f || a > (float)s.levels)) f |= 64;
     }
     if (f) atomicOr(flag, f);
+}
+
+// Omega's values (CSR) into a dense table that holds NaN everywhere else.
+static __global__ void dense_scatter_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                            const float *__restrict__ val, int64_t m, int64_t lda,
+                                            float *__restrict__ A)
+{
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= m) return;
+    for (int e = rowptr[i] + (threadIdx.x & 31); e < rowptr[i + 1]; e += 32) A[i * lda + colidx[e]] = val[e];
 }
 
 static __global__ void dense_alpha_kernel(float *__restrict__ alpha, int64_t nseg, float value)
@@ -654,15 +689,15 @@ int dense_width(int k)
     return 0;
 }
 
-template <bool XSTEP, bool GRAD, int KP>
+template <bool XSTEP, bool GRAD, int KP, bool MISS>
 cudaError_t launch_dense_kp(glrm_s *h, const DenseArgs &a, int nA, unsigned tiles)
 {
     const size_t smem = DnSmem<XSTEP, GRAD, KP>::bytes(nA);
-    cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP>,
+    cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP, MISS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(XSTEP ? h->dn.tmap_x : h->dn.tmap_y);
-    dense_pass_kernel<XSTEP, GRAD, KP>
+    dense_pass_kernel<XSTEP, GRAD, KP, MISS>
         <<<dim3(tiles, (unsigned)a.parts), kDnThreads, smem, h->stream>>>(a, *map);
     h->launches += 1;
     return cudaGetLastError();
@@ -670,12 +705,12 @@ cudaError_t launch_dense_kp(glrm_s *h, const DenseArgs &a, int nA, unsigned tile
 
 // A stages that fit next to the fixed buffers and the kernel's static shared
 // memory (at most kDnMaxStages; fewer than 2 is refused by the caller).
-template <bool XSTEP, bool GRAD, int KP>
+template <bool XSTEP, bool GRAD, int KP, bool MISS>
 int stages_kp(int optin)
 {
     using SM = DnSmem<XSTEP, GRAD, KP>;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dense_pass_kernel<XSTEP, GRAD, KP>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, dense_pass_kernel<XSTEP, GRAD, KP, MISS>) != cudaSuccess) return 0;
     if ((size_t)optin < fa.sharedSizeBytes) return 0;
     const size_t room = (size_t)optin - fa.sharedSizeBytes;
     if (room < SM::bytes(0)) return 0;
@@ -706,11 +741,16 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     if (e != cudaSuccess) return e;
-#define GLRM_DENSE_CASE(KK)                                                   \
-    if (d.KP == KK) {                                                         \
-        a.nA = stages_kp<XSTEP, GRAD, KK>(optin);                             \
-        if (a.nA < 2) return cudaErrorInvalidConfiguration;                   \
-        return launch_dense_kp<XSTEP, GRAD, KK>(h, a, a.nA, tiles);           \
+#define GLRM_DENSE_CASE(KK)                                                        \
+    if (d.KP == KK) {                                                              \
+        if (d.missing) {                                                           \
+            a.nA = stages_kp<XSTEP, GRAD, KK, true>(optin);                        \
+            if (a.nA < 2) return cudaErrorInvalidConfiguration;                    \
+            return launch_dense_kp<XSTEP, GRAD, KK, true>(h, a, a.nA, tiles);      \
+        }                                                                          \
+        a.nA = stages_kp<XSTEP, GRAD, KK, false>(optin);                           \
+        if (a.nA < 2) return cudaErrorInvalidConfiguration;                        \
+        return launch_dense_kp<XSTEP, GRAD, KK, false>(h, a, a.nA, tiles);         \
     }
     GLRM_DENSE_CASE(16)
     GLRM_DENSE_CASE(32)
@@ -750,7 +790,8 @@ bool dense_supported(int k) { return dense_width(k) != 0; }
 void dense_free(glrm_s *h)
 {
     Dense &d = h->dn;
-    for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf})
+    for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf, (void *)d.segchunk_x,
+                    (void *)d.segchunk_y})
         if (p) cudaFree(p);
     d = Dense();
 }
@@ -807,7 +848,7 @@ cudaError_t dense_prepare(glrm_s *h)
     const int64_t rows_pad = (std::max(h->m, h->n) + kDnRows - 1) / kDnRows * kDnRows;
     d.pack_part = rows_pad * d.KP;
     if ((e = cudaMalloc(&d.pk, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&d.pt, 2 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.pt, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
     if ((e = encode_maps(h)) != cudaSuccess) return e;
     // column losses in FP32, each with the kind its 16-column group shares
     // (-1: mixed)
@@ -838,15 +879,23 @@ cudaError_t dense_prepare(glrm_s *h)
     if ((e = cudaMemcpy(d.lossf, lf.data(), lf.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
 
-    Orient &R = h->csr, &C = h->csc;
-    R.nseg = h->m;
-    C.nseg = h->n;
-    R.nchunks = h->m * d.parts_x;  // partial slots, for the scratch sizes
-    C.nchunks = h->n * d.parts_y;
-    if ((e = cudaMalloc(&R.segchunk, (size_t)(h->m + 1) * sizeof(int32_t))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&C.segchunk, (size_t)(h->n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
-    dense_segchunk_kernel<<<(unsigned)((h->m + 256) / 256), 256, 0, h->stream>>>(R.segchunk, h->m, d.parts_x);
-    dense_segchunk_kernel<<<(unsigned)((h->n + 256) / 256), 256, 0, h->stream>>>(C.segchunk, h->n, d.parts_y);
+    d.slots = std::max(h->m * d.parts_x, h->n * d.parts_y);
+    if ((e = cudaMalloc(&d.segchunk_x, (size_t)(h->m + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.segchunk_y, (size_t)(h->n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+    dense_segchunk_kernel<<<(unsigned)((h->m + 256) / 256), 256, 0, h->stream>>>(d.segchunk_x, h->m, d.parts_x);
+    dense_segchunk_kernel<<<(unsigned)((h->n + 256) / 256), 256, 0, h->stream>>>(d.segchunk_y, h->n, d.parts_y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_scatter(glrm_s *h)
+{
+    const Dense &d = h->dn;
+    cudaError_t e = cudaMemsetAsync(d.A, 0xFF, (size_t)h->m * d.lda * sizeof(float), h->stream);  // NaN
+    if (e != cudaSuccess) return e;
+    if (h->nnz == 0) return cudaSuccess;
+    dense_scatter_kernel<<<(unsigned)((h->m + 7) / 8), 256, 0, h->stream>>>(h->csr.ptr, h->csr.idx,
+                                                                          (const float *)h->csr.val, h->m, d.lda, d.A);
+    h->launches += 1;
     return cudaGetLastError();
 }
 
@@ -872,7 +921,8 @@ cudaError_t dense_reset_steps(glrm_s *h)
 
 cudaError_t dense_half_step(glrm_s *h, bool xstep)
 {
-    const Orient &o = xstep ? h->csr : h->csc;
+    const int64_t nseg = xstep ? h->m : h->n;
+    const int32_t *segchunk = xstep ? h->dn.segchunk_x : h->dn.segchunk_y;
     float *F = (float *)(xstep ? h->X : h->Yt);
     const float *W = (const float *)(xstep ? h->Yt : h->X);
     float *alpha = (float *)(xstep ? h->alpha_x : h->alpha_y);
@@ -886,9 +936,9 @@ cudaError_t dense_half_step(glrm_s *h, bool xstep)
     e = xstep ? launch_dense<true, true>(h, F, (float *)s.part_grad, s.part_loss)
               : launch_dense<false, true>(h, F, (float *)s.part_grad, s.part_loss);
     if (e != cudaSuccess) return e;
-    const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
+    const unsigned nbs = blocks_for(nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
-    prox_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const float *)s.part_grad,
+    prox_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(nseg, segchunk, (const float *)s.part_grad,
                                                            s.part_loss, F, alpha, h->k, rk, rw,
                                                            (float *)s.cand, s.f_old, s.r_old, s.r_new);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -898,7 +948,7 @@ cudaError_t dense_half_step(glrm_s *h, bool xstep)
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "decide_x" : "decide_y");
     decide_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
-        o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F, alpha, h->k,
+        nseg, segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F, alpha, h->k,
         xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y, xstep ? s.acc_x : s.acc_y);
     tmark(h, nullptr);
     h->launches += 2;
@@ -934,14 +984,14 @@ cudaError_t dense_grad_at(glrm_s *h, const float *X, const float *Yt, float *GX,
     if ((e = launch_dense<true, true>(h, X, (float *)s.part_grad, s.part_loss)) != cudaSuccess) return e;
     tmark(h, "grad_seg_x");
     seg_grad_kernel<float><<<blocks_for(h->m, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->m, h->csr.segchunk, (const float *)s.part_grad, X, h->k, h->rx_kind, (float)h->rx_w, reg, scale, GX);
+        h->m, h->dn.segchunk_x, (const float *)s.part_grad, X, h->k, h->rx_kind, (float)h->rx_w, reg, scale, GX);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = dense_pack(h, X, h->m)) != cudaSuccess) return e;
     tmark(h, "dense_grad_y");
     if ((e = launch_dense<false, true>(h, Yt, (float *)s.part_grad, s.part_loss)) != cudaSuccess) return e;
     tmark(h, "grad_seg_y");
     seg_grad_kernel<float><<<blocks_for(h->n, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->n, h->csc.segchunk, (const float *)s.part_grad, Yt, h->k, h->ry_kind, (float)h->ry_w, reg, scale,
+        h->n, h->dn.segchunk_y, (const float *)s.part_grad, Yt, h->k, h->ry_kind, (float)h->ry_w, reg, scale,
         GYt);
     tmark(h, nullptr);
     h->launches += 2;

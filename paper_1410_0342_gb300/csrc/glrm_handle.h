@@ -97,7 +97,8 @@ constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 // Dense (fully observed) table and the tensor-core form's buffers.
 struct Dense {
     bool on = false;
-    float *A = nullptr;  // m x lda, lda = n rounded up to 4, padding zero
+    bool missing = false;  // A holds NaN at cells outside Omega (a sparse table stored densely)
+    float *A = nullptr;    // m x lda, lda = n rounded up to 4, padding zero
     int64_t lda = 0;
     int KP = 0;  // k padded to a multiple of 16
     int parts_x = 1, parts_y = 1;         // partial slots per row / column
@@ -105,6 +106,8 @@ struct Dense {
     __nv_bfloat16 *pk = nullptr;  // packed other factor, K-major over k (parts hi, mid, lo)
     __nv_bfloat16 *pt = nullptr;  // packed other factor, K-major over chunk rows (parts hi, mid)
     int64_t pack_part = 0;        // elements per part
+    int32_t *segchunk_x = nullptr, *segchunk_y = nullptr;  // segment -> first partial slot (s * parts)
+    int64_t slots = 0;                                     // partial slots of the larger half-step
     float4 *lossf = nullptr;      // n column losses in FP32 {kind bits, param, levels, group kind bits}
     alignas(64) unsigned char tmap_x[128] = {};  // CUtensorMap of A, X-step boxes
     alignas(64) unsigned char tmap_y[128] = {};  // CUtensorMap of A, Y-step boxes
@@ -189,6 +192,7 @@ void dense_free(glrm_s *h);
 cudaError_t dense_prepare(glrm_s *h);
 cudaError_t launch_dense_validate(const float *A, int64_t lda, int64_t m, int64_t n, const LossSpec *loss,
                                   int *flag, cudaStream_t st);
+cudaError_t launch_dense_scatter(glrm_s *h);
 cudaError_t dense_reset_steps(glrm_s *h);
 cudaError_t dense_half_step(glrm_s *h, bool xstep);
 cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, double *out);

@@ -10,6 +10,8 @@ import struct
 
 import numpy as np
 
+from paper_1410_0342_gb300 import workloads as W
+
 
 def decode_state(buf: bytes, m: int, n: int, k: int, dtype=np.float32):
     """(X, Yt, alpha_x, alpha_y, sweeps) from a glrm_get_state buffer."""
@@ -57,3 +59,15 @@ def synced_sweeps(g, o, t, nsweeps, rtol=1e-5, max_flip_frac=0.01):
         bad = (np.abs(Xg - Xo).max(axis=1) / scale) > 1e-4
         assert bad.mean() <= max_flip_frac + 2.0 / len(bad), bad.sum()
     return np.array(rels)
+
+
+def subset_table(t, keep):
+    """The table restricted to the entries where keep (a CSR-order mask) is set."""
+    rows = t.rows()[keep]
+    cols = t.colidx[keep]
+    vals = t.val[keep]
+    rowptr = np.zeros(t.m + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=t.m), out=rowptr[1:])
+    colptr, rowidx, cval = W.csc_from_csr(t.m, t.n, rowptr, cols, vals)
+    return W.Table(t.name, t.m, t.n, t.k, rowptr, cols, vals, colptr, rowidx, cval,
+                   t.loss_kind, t.loss_param, t.loss_levels, t.rx, t.ry, t.X0, t.Yt0)

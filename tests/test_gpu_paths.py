@@ -7,7 +7,7 @@ import torch
 
 from paper_1410_0342_gb300 import workloads as W
 
-from gpu_parity import synced_sweeps
+from gpu_parity import subset_table, synced_sweeps
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +62,7 @@ def test_path_switch_keeps_state(G):
     """Switching paths mid-fit continues the same fit (same factors and steps)."""
     t = W.small_mixed(m=900, n=80, k=12, seed=9)
     g1 = G.GLRM.from_table(t)
+    G.glrm_set_path(g1.h, G.GLRM_PATH_MASKED, G.GLRM_PATH_MASKED_SPLIT)
     h1 = g1.sweep(8)
     g2 = G.GLRM.from_table(t)
     G.glrm_set_path(g2.h, 1, 1)
@@ -73,10 +74,16 @@ def test_path_switch_keeps_state(G):
 
 
 def test_auto_path_choice(G):
-    # dense: masked tiles; Y^T fits whole, X only panel by panel
+    # 70% observed: stored densely, tensor-core form (FP32); FP64 stays sparse
     t = W.small_mixed(m=6000, n=64, k=16, p_obs=0.7, seed=3)
     g = G.GLRM.from_table(t)
-    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_MASKED, G.GLRM_PATH_MASKED_SPLIT)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    g64 = G.GLRM.from_table(t, precision=G.GLRM_FP64)
+    assert G.glrm_get_path(g64.h) == (G.GLRM_PATH_MASKED, G.GLRM_PATH_MASKED_SPLIT)
+    # 33% observed: masked tiles; Y^T fits whole, X only panel by panel
+    t1 = W.small_mixed(m=6000, n=64, k=16, p_obs=0.33, seed=3)
+    g1 = G.GLRM.from_table(t1)
+    assert G.glrm_get_path(g1.h) == (G.GLRM_PATH_MASKED, G.GLRM_PATH_MASKED_SPLIT)
     # sparse with a large X: chunked Y-step
     t2 = W.small_mixed(m=60000, n=3000, k=8, p_obs=0.002, seed=4)
     g2 = G.GLRM.from_table(t2)
@@ -94,3 +101,41 @@ def test_sparse_chunked_matches_oracle(G, oracle_mod):
     t = W.small_mixed(m=20000, n=900, k=8, p_obs=0.004, seed=6)
     g = G.GLRM.from_table(t)
     synced_sweeps(g, oracle_mod, t, 6)
+
+
+@pytest.mark.parametrize("p_obs,k", [(0.55, 12), (0.45, 33), (0.9, 5)])
+def test_dense_path_with_missing_cells(G, oracle_mod, p_obs, k):
+    """An observed set stored densely (NaN at the missing cells): synced
+    sweeps against the oracle, including empty rows and columns."""
+    t = W.small_mixed(m=1501, n=130, k=k, p_obs=p_obs, seed=300 + k)
+    keep = ~np.isin(t.rows(), [0, 17, t.m - 1]) & (t.colidx != 5)
+    t = subset_table(t, keep)
+    g = G.GLRM.from_table(t)
+    G.glrm_set_path(g.h, G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    synced_sweeps(g, oracle_mod, t, 6)
+
+
+def test_dense_path_switch_and_als(G, oracle_mod):
+    """Switching between the dense and the sparse paths keeps the fit; ALS
+    still runs on an observed set stored densely."""
+    t = W.small_mixed(m=800, n=60, k=6, p_obs=0.6, seed=21, rx=(RQ, 0.1), ry=(RQ, 0.1))
+    g = G.GLRM.from_table(t)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    synced_sweeps(g, oracle_mod, t, 2)
+    G.glrm_set_path(g.h, G.GLRM_PATH_CHUNKED, G.GLRM_PATH_MASKED)
+    synced_sweeps(g, oracle_mod, t, 2)
+    G.glrm_set_path(g.h, G.GLRM_PATH_AUTO, G.GLRM_PATH_AUTO)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    synced_sweeps(g, oracle_mod, t, 2)
+    q = W.qpca_dense(m=300, n=90, k=4, seed=22)
+    gq = G.GLRM.from_table(q)
+    assert G.glrm_get_path(gq.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    X0, Y0 = gq.factors()
+    hist = gq.als_sweep(30)
+    p = oracle_mod.Problem.from_csr(q.m, q.n, q.k, q.rowptr, q.colidx, q.val, loss_kind=q.loss_kind,
+                                    loss_param=q.loss_param, loss_levels=q.loss_levels, rx=q.rx, ry=q.ry)
+    *_, ohist = p.als(X0.double().cpu().numpy(), Y0.double().cpu().numpy(), 0.1, 30)
+    assert (np.abs(hist - ohist) / ohist).max() < 1e-4
+    with pytest.raises(G.GLRMError):
+        G.glrm_set_path(gq.h, G.GLRM_PATH_DENSE, G.GLRM_PATH_CHUNKED)
