@@ -173,6 +173,10 @@ def algorithmic_bytes(name: str, t: W.Table, k: int) -> float:
     fb = 4 * k
     x = name.endswith("_x")
     nseg, other = (m, n) if x else (n, m)
+    if name.startswith("dense_grad") or name.startswith("dense_loss"):
+        # the dense form reads every cell of the table once (4 m n bytes, a
+        # missing cell is a NaN), both factors, and writes per-row partials
+        return 4.0 * m * n + (nseg + other) * fb + (nseg * fb if "grad" in name else 0)
     if "fused" in name:
         return nnz * 8 + (nseg + other) * fb + nseg * (fb + 4)
     if "grad" in name or "loss" in name:
@@ -319,10 +323,17 @@ def run_glrm(args, world, rank, local):
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_s * 1e6,
-                "peak_source": peak_src, "share_of_step": tms / ms,
-                "alu": {"achieved_tflops": aflops / avg_s / 1e12, "peak_tflops": fp32_peak,
-                        "frac": aflops / avg_s / 1e12 / fp32_peak,
-                        "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled SM clock"}}
+                "peak_source": peak_src, "share_of_step": tms / ms}
+    if tname.startswith("dense_"):
+        # tensor cores: 2 m n k flop for U (+ 2 m n k for R W in a gradient pass),
+        # against the measured BF16 peak (the six split products are not counted)
+        tflops = (4.0 if "grad" in tname else 2.0) * t.m * t.n * t.k / avg_s / 1e12
+        roofline["tensor"] = {"achieved_tflops": tflops, "peak_tflops": peaks["bf16_tflops"],
+                              "frac": tflops / peaks["bf16_tflops"], "peak_source": peak_src}
+    else:
+        roofline["alu"] = {"achieved_tflops": aflops / avg_s / 1e12, "peak_tflops": fp32_peak,
+                           "frac": aflops / avg_s / 1e12 / fp32_peak,
+                           "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled SM clock"}
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / ms}
                for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
 
@@ -355,8 +366,8 @@ def run_glrm(args, world, rank, local):
         e2e = {"value": world * t.nnz * args.e2e_steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
                "steps": args.e2e_steps,
-               "includes": "set_observed_host (H2D copy + device validation + chunk tables), "
-                           "set_factors_host, one sweep, objective D2H"}
+               "includes": "set_observed_host (H2D copy + device validation + chunk tables + the "
+                           "chosen path's layout), set_factors_host, one sweep, objective D2H"}
         ge.close()
 
     cpu = None
@@ -378,7 +389,8 @@ def run_glrm(args, world, rank, local):
             "config": {"workload": WORKLOAD.format(m=t.m), "nnz": t.nnz, "m": t.m, "n": t.n, "k": t.k,
                        "paths": {"x": paths[0], "y": paths[1]},
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (CSR+CSC 0.96 GB); no flush"},
+                       "l2": "inputs larger than L2 (CSR+CSC 0.96 GB; stored densely for the dense "
+                             "path, 0.40 GB); no flush"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

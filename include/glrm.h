@@ -261,8 +261,13 @@ int glrm_set_state(glrm_t h, const void *buf_host, size_t len);
  *   GLRM_PATH_MASKED_SPLIT  the masked path with every tile split in two or
  *                      more units (glrm_get_path reports it whenever a masked
  *                      half-step runs split)
- * GLRM_PATH_AUTO picks masked when a tile's pairs average >= 8 observed lanes
- * (dense tables), else fused when the other factor fits, else blocked when a
+ *   GLRM_PATH_DENSE    (both half-steps) the table stored densely with NaN at
+ *                      the missing cells and swept by the tensor-core form of
+ *                      glrm_set_dense; FP32 models with k <= 64
+ * GLRM_PATH_AUTO picks dense for FP32 models with k <= 64 when at least 40% of
+ * the cells are observed (and the dense copy takes at most half the free
+ * device memory); otherwise masked when a tile's pairs average >= 8 observed
+ * lanes, else fused when the other factor fits, else blocked when a
  * (panel, segment) run holds >= 64 entries on average, else chunked.  The
  * staged paths need k <= 32.  glrm_set_path(h, xstep_path, ystep_path) may be
  * called before or after glrm_set_observed; an infeasible request returns

@@ -88,8 +88,8 @@ def test_auto_path_choice(G):
     t2 = W.small_mixed(m=60000, n=3000, k=8, p_obs=0.002, seed=4)
     g2 = G.GLRM.from_table(t2)
     assert G.glrm_get_path(g2.h) == (G.GLRM_PATH_FUSED, G.GLRM_PATH_CHUNKED)
-    # k > 32: chunked only
-    t3 = W.small_mixed(m=300, n=40, k=40, seed=5)
+    # k > 32 below the dense threshold: chunked only
+    t3 = W.small_mixed(m=300, n=40, k=40, p_obs=0.3, seed=5)
     g3 = G.GLRM.from_table(t3)
     assert G.glrm_get_path(g3.h) == (G.GLRM_PATH_CHUNKED, G.GLRM_PATH_CHUNKED)
     with pytest.raises(G.GLRMError):
