@@ -613,29 +613,57 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 // kDnNT rows, over the chunk rows (chunk q, element (c, t) of part w at byte
 // w part 2 + q KP kDnNT 2 + sw_off(c, t, 2 kDnNT)), all three parts.  Rows
 // from `rows` to rows_pad and coordinates from k to KP are zero.
-static __global__ void dense_pack_kernel(const float *__restrict__ W, int64_t rows, int k, int KP,
-                                         int64_t rows_pad, int64_t part, __nv_bfloat16 *__restrict__ pk,
-                                         __nv_bfloat16 *__restrict__ pt)
+template <int KP>
+__global__ void __launch_bounds__(256) dense_pack_kernel(const float *__restrict__ W, int64_t rows, int k,
+                                                         int64_t part, __nv_bfloat16 *__restrict__ pk,
+                                                         __nv_bfloat16 *__restrict__ pt)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows_pad * KP) return;
-    const int64_t r = i / KP;
-    const int c = (int)(i - r * KP);
-    const float v = (r < rows && c < k) ? W[r * k + c] : 0.f;
-    __nv_bfloat16 hi, mid, lo;
-    split3(v, hi, mid, lo);
-    // 8-row groups are contiguous, so the swizzle of a global row is that of
-    // its row within any 64-row chunk
-    const int64_t ik = (r >> 3) * 8 * KP + sw_off((uint32_t)(r & 7), (uint32_t)c, 2 * KP) / 2;
-    pk[ik] = hi;
-    pk[part + ik] = mid;
-    pk[2 * part + ik] = lo;
-    const int64_t q = r / kDnNT;
-    const int t = (int)(r - q * kDnNT);
-    const int64_t it = q * KP * kDnNT + sw_off((uint32_t)c, (uint32_t)t, 2 * kDnNT) / 2;
-    pt[it] = hi;
-    pt[part + it] = mid;
-    pt[2 * part + it] = lo;
+    // one CTA per chunk of kDnNT rows, staged in shared memory; every store
+    // is a 16-byte unit of eight BF16 values
+    __shared__ float tile[kDnNT][KP + 1];
+    const int64_t q = blockIdx.x, r0 = q * kDnNT;
+    for (int i = threadIdx.x; i < kDnNT * KP; i += blockDim.x) {
+        const int r = i / KP, c = i - r * KP;
+        tile[r][c] = (r0 + r < rows && c < k) ? W[(r0 + r) * k + c] : 0.f;
+    }
+    __syncthreads();
+    auto pack8 = [](const float (&v)[8], uint4 &h, uint4 &m, uint4 &l) {
+        uint32_t hv[4], mv[4], lv[4];
+#pragma unroll
+        for (int w = 0; w < 8; w += 2) {
+            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+            split3(v[w], h0, m0, l0);
+            split3(v[w + 1], h1, m1, l1);
+            hv[w / 2] = bf2_bits(__halves2bfloat162(h0, h1));
+            mv[w / 2] = bf2_bits(__halves2bfloat162(m0, m1));
+            lv[w / 2] = bf2_bits(__halves2bfloat162(l0, l1));
+        }
+        h = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        m = make_uint4(mv[0], mv[1], mv[2], mv[3]);
+        l = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    };
+    for (int i = threadIdx.x; i < kDnNT * (KP / 8); i += blockDim.x) {
+        // K-major over k: row r, coordinates 8 g .. 8 g + 7
+        const int r = i / (KP / 8), g = i - r * (KP / 8);
+        float v[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v[w] = tile[r][8 * g + w];
+        uint4 h, m, l;
+        pack8(v, h, m, l);
+        const int64_t o = r0 * KP + sw_off((uint32_t)r, (uint32_t)(8 * g), 2 * KP) / 2;
+        *reinterpret_cast<uint4 *>(pk + o) = h;
+        *reinterpret_cast<uint4 *>(pk + part + o) = m;
+        *reinterpret_cast<uint4 *>(pk + 2 * part + o) = l;
+        // K-major over the chunk rows: coordinate c (= i / 8 here), rows 8 t .. 8 t + 7
+        const int c = i / (kDnNT / 8), tg = i - c * (kDnNT / 8);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v[w] = tile[8 * tg + w][c];
+        pack8(v, h, m, l);
+        const int64_t ot = q * KP * kDnNT + sw_off((uint32_t)c, (uint32_t)(8 * tg), 2 * kDnNT) / 2;
+        *reinterpret_cast<uint4 *>(pt + ot) = h;
+        *reinterpret_cast<uint4 *>(pt + part + ot) = m;
+        *reinterpret_cast<uint4 *>(pt + 2 * part + ot) = l;
+    }
 }
 
 // Values outside a column loss's domain (flag 64) or not finite (flag 8).
@@ -763,10 +791,14 @@ cudaError_t dense_pack(glrm_s *h, const float *W, int64_t rows)
 {
     const Dense &d = h->dn;
     const int64_t rows_pad = (rows + kDnRows - 1) / kDnRows * kDnRows;
-    const int64_t total = rows_pad * d.KP;
     tmark(h, "dense_pack");
-    dense_pack_kernel<<<(unsigned)((total + 255) / 256), 256, 0, h->stream>>>(W, rows, h->k, d.KP, rows_pad,
-                                                                              d.pack_part, d.pk, d.pt);
+    const unsigned nchunks = (unsigned)(rows_pad / kDnNT);
+    if (d.KP == 16)
+        dense_pack_kernel<16><<<nchunks, 256, 0, h->stream>>>(W, rows, h->k, d.pack_part, d.pk, d.pt);
+    else if (d.KP == 32)
+        dense_pack_kernel<32><<<nchunks, 256, 0, h->stream>>>(W, rows, h->k, d.pack_part, d.pk, d.pt);
+    else
+        dense_pack_kernel<64><<<nchunks, 256, 0, h->stream>>>(W, rows, h->k, d.pack_part, d.pk, d.pt);
     h->launches += 1;
     return cudaGetLastError();
 }

@@ -160,6 +160,23 @@ __device__ __forceinline__ double reg1(int kind, T w, T x)
     }
 }
 
+// The same in the model's precision (a segment's regulariser for the accept /
+// reject test; FP64 only where the segment terms are combined).
+template <class T>
+__device__ __forceinline__ T reg1t(int kind, T w, T x)
+{
+    switch (kind) {
+    case kRegQuad:
+        return w * x * x;
+    case kRegL1:
+        return w * fabs(x);
+    case kRegNonneg:
+        return x < T(0) ? xinf<T>() : T(0);
+    default:
+        return T(0);
+    }
+}
+
 // One coordinate of the regulariser's gradient: 2 w x, w sign(x), 0.
 template <class T>
 __device__ __forceinline__ T reg_grad1(int kind, T w, T x)

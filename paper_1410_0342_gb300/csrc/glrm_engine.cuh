@@ -143,6 +143,7 @@ static __global__ void to_bf16_kernel(const float *__restrict__ src, int64_t n, 
 __device__ __forceinline__ double seg_loss_sum(const double *__restrict__ part, int c_beg, int c_end,
                                                int lane)
 {
+    if (c_end - c_beg == 1) return part[c_beg];  // one partial: no FP64 reduction (slow on GB300)
     double v = 0.0;
     for (int c = c_beg + lane; c < c_end; c += 32) v += part[c];
     return warp_sum(v);
@@ -160,15 +161,15 @@ prox_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restr
     if (s >= nseg) return;
     const int cb = segchunk[s], ce = segchunk[s + 1];
     const T al = alpha[s];
-    double ro = 0.0, rn = 0.0;
+    T ro = T(0), rn = T(0);
     for (int c = lane; c < k; c += 32) {
         T g = T(0);
         for (int q = cb; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
         const T x = F[s * k + c];
         const T xp = prox1<T>(rkind, rw, al, x - al * g);
         cand[s * k + c] = xp;
-        ro += reg1<T>(rkind, rw, x);
-        rn += reg1<T>(rkind, rw, xp);
+        ro += reg1t<T>(rkind, rw, x);
+        rn += reg1t<T>(rkind, rw, xp);
     }
     ro = warp_sum(ro);
     rn = warp_sum(rn);

@@ -421,7 +421,7 @@ mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile
                                                           Ws, W, gbuf, Lsrc, sp);
             const T al = live ? alpha[s] : T(0);
             Vec<T, K> fp;
-            double rold = 0.0, rnew = 0.0;
+            T rold = T(0), rnew = T(0);
             {
                 T tmp[K];
 #pragma unroll
@@ -430,8 +430,8 @@ mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile
                     const T xp = c < k ? prox1<T>(rk, rw, al, x - al * g.get(c)) : T(0);
                     tmp[c] = xp;
                     if (c < k) {
-                        rold += reg1<T>(rk, rw, x);
-                        rnew += reg1<T>(rk, rw, xp);
+                        rold += reg1t<T>(rk, rw, x);
+                        rnew += reg1t<T>(rk, rw, xp);
                     }
                 }
                 fp.load_masked(tmp, K);
@@ -489,21 +489,26 @@ unit_prox_kernel(int64_t nseg, const int32_t *__restrict__ ubeg, const T *__rest
     const int64_t t = s / 32, l = s % 32;
     const int u0 = ubeg[t], u1 = ubeg[t + 1];
     const T al = alpha[s];
-    double ro = 0.0, rn = 0.0;
+    T ro = T(0), rn = T(0);
     for (int c = lane; c < k; c += 32) {
         T g = T(0);
         for (int u = u0; u < u1; ++u) g += part_grad[((int64_t)u * 32 + l) * K + c];
         const T x = F[s * k + c];
         const T xp = prox1<T>(rkind, rw, al, x - al * g);
         cand[s * k + c] = xp;
-        ro += reg1<T>(rkind, rw, x);
-        rn += reg1<T>(rkind, rw, xp);
+        ro += reg1t<T>(rkind, rw, x);
+        rn += reg1t<T>(rkind, rw, xp);
     }
     ro = warp_sum(ro);
     rn = warp_sum(rn);
-    double ls = 0.0;
-    for (int u = u0 + lane; u < u1; u += 32) ls += part_loss[(int64_t)u * 32 + l];
-    ls = warp_sum(ls);
+    double ls;
+    if (u1 - u0 == 1) {
+        ls = part_loss[(int64_t)u0 * 32 + l];
+    } else {
+        ls = 0.0;
+        for (int u = u0 + lane; u < u1; u += 32) ls += part_loss[(int64_t)u * 32 + l];
+        ls = warp_sum(ls);
+    }
     if (lane == 0) {
         f_old[s] = ls + ro;
         r_old[s] = ro;
@@ -524,9 +529,15 @@ unit_decide_kernel(int64_t nseg, const int32_t *__restrict__ ubeg,
     const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (s >= nseg) return;
     const int64_t t = s / 32, l = s % 32;
-    double ls = 0.0;
-    for (int u = ubeg[t] + lane; u < ubeg[t + 1]; u += 32) ls += part_loss_new[(int64_t)u * 32 + l];
-    const double fn = warp_sum(ls) + r_new[s];
+    double ls;
+    if (ubeg[t + 1] - ubeg[t] == 1) {
+        ls = part_loss_new[(int64_t)ubeg[t] * 32 + l];
+    } else {
+        ls = 0.0;
+        for (int u = ubeg[t] + lane; u < ubeg[t + 1]; u += 32) ls += part_loss_new[(int64_t)u * 32 + l];
+        ls = warp_sum(ls);
+    }
+    const double fn = ls + r_new[s];
     const double fo = f_old[s];
     const bool acc = fn <= fo;
     if (acc)

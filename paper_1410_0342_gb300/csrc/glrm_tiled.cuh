@@ -255,11 +255,11 @@ struct Vec<double, K> {
 template <class T, int K>
 __device__ __forceinline__ double reg_of(const Vec<T, K> &v, int k, int rk, T rw)
 {
-    double r = 0.0;
+    T r = T(0);
 #pragma unroll
     for (int c = 0; c < K; ++c)
-        if (c < k) r += reg1<T>(rk, rw, v.get(c));
-    return r;
+        if (c < k) r += reg1t<T>(rk, rw, v.get(c));
+    return (double)r;
 }
 
 // ------------------------------------------------- per-warp entry streams
@@ -455,7 +455,7 @@ fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *
         const double lold = warp_sum((double)lsum);
         const T al = alpha[s];
         Vec<T, K> fp;
-        double rold = 0.0, rnew = 0.0;
+        T rold = T(0), rnew = T(0);
         {
             T tmp[K];
 #pragma unroll
@@ -464,8 +464,8 @@ fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *
                 const T xp = c < k ? prox1<T>(rk, rw, al, x - al * g.get(c)) : T(0);
                 tmp[c] = xp;
                 if (c < k) {
-                    rold += reg1<T>(rk, rw, x);
-                    rnew += reg1<T>(rk, rw, xp);
+                    rold += reg1t<T>(rk, rw, x);
+                    rnew += reg1t<T>(rk, rw, xp);
                 }
             }
             fp.load_masked(tmp, K);
@@ -619,15 +619,15 @@ blocked_prox_kernel(int64_t nseg, int nb, const T *__restrict__ part_grad,
     const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (s >= nseg) return;
     const T al = alpha[s];
-    double ro = 0.0, rn = 0.0;
+    T ro = T(0), rn = T(0);
     for (int c = lane; c < k; c += 32) {
         T g = T(0);
         for (int b = 0; b < nb; ++b) g += part_grad[((int64_t)b * nseg + s) * K + c];
         const T x = F[s * k + c];
         const T xp = prox1<T>(rkind, rw, al, x - al * g);
         cand[s * k + c] = xp;
-        ro += reg1<T>(rkind, rw, x);
-        rn += reg1<T>(rkind, rw, xp);
+        ro += reg1t<T>(rkind, rw, x);
+        rn += reg1t<T>(rkind, rw, xp);
     }
     ro = warp_sum(ro);
     rn = warp_sum(rn);
