@@ -138,10 +138,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def source_digest() -> str:
+def source_digest(files=None) -> str:
+    """Digest of the kernel sources (all of csrc/, or the named files)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1410_0342_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in sorted(files if files is not None else os.listdir(csrc)):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -150,13 +151,16 @@ def source_digest() -> str:
 
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if it
-    was taken from the current kernel sources (else None)."""
+    was taken from the current sources of that kernel (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("source_digest") != source_digest():
+    try:
+        if d.get("source_digest") != source_digest(d.get("source_files")):
+            return None
+    except OSError:
         return None
     v = d.get("bytes_per_launch", {}).get(kernel)
     return float(v) if v is not None else None

@@ -121,8 +121,10 @@ int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss_host,
  * the model's element type.  The library copies and re-tiles everything into
  * buffers it owns (the caller may free its copies afterwards), validates it
  * on the device -- pointer monotonicity, index range, no duplicate (i,j),
- * CSR/CSC describing the same entries with bit-identical values, finite
- * values -- and resets every step size to 1/max(count, 1) (Section 7.2,
+ * CSR/CSC describing the same entries with bit-identical values (compared
+ * through 64-bit digests of the entries and of their values: a mismatch goes
+ * unnoticed with probability about 2^-64), finite values, values inside each
+ * column loss's domain -- and resets every step size to 1/max(count, 1) (Section 7.2,
  * "Choosing a step size").  Synchronises (it reads back the validation
  * result).  Returns GLRM_ERR_OMEGA or GLRM_ERR_NONFINITE when validation
  * fails; the previous Omega is then gone and sweeps return GLRM_ERR_STATE. */

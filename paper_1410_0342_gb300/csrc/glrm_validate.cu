@@ -1,7 +1,7 @@
 // Device-side validation of an observed set handed to glrm_set_observed:
 // pointer arrays, index ranges and ordering, finite values, and that CSR and
-// CSC list the same entries with bit-identical values.  Each check ORs a bit
-// into a device flag word; nothing traps.
+// CSC list the same entries with bit-identical values (64-bit digests).  Each
+// check ORs a bit into a device flag word; nothing traps.
 #include "glrm_handle.h"
 
 namespace glrm {
@@ -45,33 +45,53 @@ __global__ void validate_idx_kernel(const int32_t *__restrict__ ptr, const int32
     if (lane == 0 && f) atomicOr(flag, f);
 }
 
-// One warp per column: every CSC entry (i, j) found in CSR row i by binary
-// search with the same value bits.  With equal counts and no duplicates on
-// either side this makes the two a bijection.
+// The CSR / CSC agreement check compares two order-free digests of each
+// orientation's entries: the sum (mod 2^64) of H(i n + j) over its entries,
+// and the sum of H(H(i n + j) ^ value bits), H being the splitmix64 finaliser
+// (Steele, Lea and Flood, "Fast splittable pseudorandom number generators").
+// Both orientations already passed the per-segment checks (counts, ranges,
+// strict order, so no duplicates); equal index digests then mean the same
+// entries and equal value digests the same values, except with probability
+// about 2^-64 for a given mismatch.  One warp per segment, a grid-wide sum.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// digest[0], digest[1]: index and value sums of this orientation (CSR: seg is
+// the row; CSC: seg is the column).
 template <class T>
-__global__ void validate_cross_kernel(const int32_t *__restrict__ colptr,
-                                      const int32_t *__restrict__ rowidx, const T *__restrict__ cval,
-                                      int64_t n, const int32_t *__restrict__ rowptr,
-                                      const int32_t *__restrict__ colidx, const T *__restrict__ rval,
-                                      int *flag)
+__global__ void digest_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                              const T *__restrict__ val, int64_t nseg, int64_t n, bool rows,
+                              unsigned long long *__restrict__ digest)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= n) return;
-    int f = 0;
-    for (int q = colptr[j] + lane; q < colptr[j + 1]; q += 32) {
-        const int i = rowidx[q];
-        int lo = rowptr[i], hi = rowptr[i + 1];
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (colidx[mid] < j) lo = mid + 1;
-            else hi = mid;
-        }
-        if (lo >= rowptr[i + 1] || colidx[lo] != j) f |= 16;
-        else if (bits(rval[lo]) != bits(cval[q])) f |= 32;
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= nseg) return;
+    unsigned long long a = 0, b = 0;
+    for (int q = ptr[s] + lane; q < ptr[s + 1]; q += 32) {
+        const int64_t i = rows ? s : idx[q], j = rows ? idx[q] : s;
+        const unsigned long long h = mix64((unsigned long long)(i * n + j));
+        a += h;
+        b += mix64(h ^ (unsigned long long)bits(val[q]));
     }
-    for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0 && f) atomicOr(flag, f);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&digest[0], a);
+        atomicAdd(&digest[1], b);
+    }
+}
+
+__global__ void digest_compare_kernel(const unsigned long long *__restrict__ d, int *flag)
+{
+    if (d[0] != d[2]) atomicOr(flag, 16);
+    else if (d[1] != d[3]) atomicOr(flag, 32);
 }
 
 // One warp per column: values inside the column loss's domain (Boolean
@@ -130,16 +150,34 @@ cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const vo
 cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
                                   cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((csc.nseg + 7) / 8);
-    if (prec == GLRM_FP64)
-        validate_cross_kernel<double><<<nb, 256, 0, st>>>(csc.ptr, csc.idx, (const double *)csc.val,
-                                                          csc.nseg, csr.ptr, csr.idx,
-                                                          (const double *)csr.val, flag);
-    else
-        validate_cross_kernel<float><<<nb, 256, 0, st>>>(csc.ptr, csc.idx, (const float *)csc.val,
-                                                         csc.nseg, csr.ptr, csr.idx,
-                                                         (const float *)csr.val, flag);
-    return cudaGetLastError();
+    unsigned long long *d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, 4 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), st);
+    const int64_t n = csc.nseg;
+    const unsigned nbr = (unsigned)((csr.nseg + 7) / 8), nbc = (unsigned)((csc.nseg + 7) / 8);
+    if (e == cudaSuccess && csr.nseg > 0) {
+        if (prec == GLRM_FP64)
+            digest_kernel<double><<<nbr, 256, 0, st>>>(csr.ptr, csr.idx, (const double *)csr.val, csr.nseg, n, true, d);
+        else
+            digest_kernel<float><<<nbr, 256, 0, st>>>(csr.ptr, csr.idx, (const float *)csr.val, csr.nseg, n, true, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && csc.nseg > 0) {
+        if (prec == GLRM_FP64)
+            digest_kernel<double><<<nbc, 256, 0, st>>>(csc.ptr, csc.idx, (const double *)csc.val, csc.nseg, n, false,
+                                                       d + 2);
+        else
+            digest_kernel<float><<<nbc, 256, 0, st>>>(csc.ptr, csc.idx, (const float *)csc.val, csc.nseg, n, false,
+                                                      d + 2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        digest_compare_kernel<<<1, 1, 0, st>>>(d, flag);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(d, st);
+    return e != cudaSuccess ? e : e2;
 }
 
 }  // namespace glrm
