@@ -76,6 +76,12 @@ def dist_env():
     return world, rank, local
 
 
+def job_throughput(world: int, units_per_rank: float, steps: int, ms_max: float) -> float:
+    """Whole-job units per second: every rank processes units_per_rank per step
+    (replicas, weak scaling), timed by the slowest rank."""
+    return world * units_per_rank * steps / (ms_max / 1000.0)
+
+
 def max_over_ranks(value: float, world: int, device=None) -> float:
     """Max of a per-rank float over all ranks (identity when world == 1)."""
     if world == 1:
@@ -309,7 +315,7 @@ def run_glrm(args, world, rank, local):
     G.glrm_timing_enable(g.h, False)
     hist = g.sweep(1, history=True)
     ms_max = max_over_ranks(ms, world, dev)
-    value = world * t.nnz * args.steps / (ms_max / 1000.0)
+    value = job_throughput(world, t.nnz, args.steps, ms_max)
 
     # dominant kernel and its roofline
     peaks, peak_src = measured_peaks()
