@@ -151,12 +151,30 @@ template <int KIND, bool MISS>
 __device__ __forceinline__ void dn_block(const float (&u)[16], const float (&a)[16], float prm, float lev,
                                          float (&rr)[16], float &lsum)
 {
-    if constexpr (MISS) {
+    if constexpr (MISS && KIND == kLossQuad) {
+        // a missing cell's NaN propagates into r and is replaced by 0
+        const unsigned long long m1 = pk2(-1.f, -1.f);
+        unsigned long long acc = pk2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < 16; w += 2) {
+            float r0, r1;
+            upk2(ffma2(pk2(a[w], a[w + 1]), m1, pk2(u[w], u[w + 1])), r0, r1);  // u - a
+            r0 = a[w] == a[w] ? r0 : 0.f;
+            r1 = a[w + 1] == a[w + 1] ? r1 : 0.f;
+            const unsigned long long r = pk2(r0, r1);
+            acc = ffma2(r, r, acc);
+            upk2(fadd2(r, r), rr[w], rr[w + 1]);
+        }
+        float l0, l1;
+        upk2(acc, l0, l1);
+        lsum += l0 + l1;
+    } else if constexpr (MISS) {
+        // the losses tolerate a NaN value (no traps, no loops); its results are replaced by 0
 #pragma unroll
         for (int w = 0; w < 16; ++w) {
             const bool v = a[w] == a[w];
             float L;
-            const float d = loss_deriv_k<KIND, float>(u[w], v ? a[w] : 0.f, prm, lev, L);
+            const float d = loss_deriv_k<KIND, float>(u[w], a[w], prm, lev, L);
             lsum += v ? L : 0.f;
             rr[w] = v ? d : 0.f;
         }
