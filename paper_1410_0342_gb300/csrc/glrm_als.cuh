@@ -124,10 +124,10 @@ cudaError_t launch_als_half(glrm_s *h, bool xstep, double gamma)
     const size_t need = (size_t)std::max<int64_t>(1, std::max(h->csr.nchunks, h->csc.nchunks)) *
                         Tri<K>::P * sizeof(T);
     if (h->s.als_bytes < need) {
-        if (h->s.als_part) cudaFree(h->s.als_part);
+        dfree(h->s.als_part, h->stream);
         h->s.als_part = nullptr;
         h->s.als_bytes = 0;
-        cudaError_t e = cudaMalloc(&h->s.als_part, need);
+        cudaError_t e = dalloc(h, &h->s.als_part, need);
         if (e != cudaSuccess) return e;
         h->s.als_bytes = need;
     }

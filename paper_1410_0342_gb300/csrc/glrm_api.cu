@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -37,29 +39,22 @@ int cuda_fail(glrm_s *h, cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
     } while (0)
 
-template <class P>
-void dfree(P *&p)
+void free_orient(Orient &o, cudaStream_t st)
 {
-    if (p) cudaFree((void *)p);
-    p = nullptr;
-}
-
-void free_orient(Orient &o)
-{
-    dfree(o.ptr);
-    dfree(o.idx);
-    dfree(o.val);
-    dfree(o.chunks);
-    dfree(o.segchunk);
-    dfree(o.runptr);
-    dfree(o.perm);
-    dfree(o.tptr);
-    dfree(o.tidx);
-    dfree(o.tmask);
-    dfree(o.tval);
-    dfree(o.ubeg);
-    dfree(o.utile);
-    dfree(o.uvoff);
+    dfree(o.ptr, st);
+    dfree(o.idx, st);
+    dfree(o.val, st);
+    dfree(o.chunks, st);
+    dfree(o.segchunk, st);
+    dfree(o.runptr, st);
+    dfree(o.perm, st);
+    dfree(o.tptr, st);
+    dfree(o.tidx, st);
+    dfree(o.tmask, st);
+    dfree(o.tval, st);
+    dfree(o.ubeg, st);
+    dfree(o.utile, st);
+    dfree(o.uvoff, st);
     o.npairs = 0;
     o.nunits = 0;
     o.nchunks = 0;
@@ -69,14 +64,14 @@ void free_orient(Orient &o)
     o.smem_bytes = 0;
 }
 
-void free_scratch(Scratch &s)
+void free_scratch(Scratch &s, cudaStream_t st)
 {
-    dfree(s.part_grad); dfree(s.part_loss); dfree(s.part_loss2); dfree(s.cand);
-    dfree(s.f_old); dfree(s.r_old); dfree(s.r_new);
-    dfree(s.kept_obj_x); dfree(s.kept_reg_x); dfree(s.kept_obj_y); dfree(s.kept_reg_y);
-    dfree(s.acc_x); dfree(s.acc_y); dfree(s.red_part); dfree(s.red_cnt);
-    dfree(s.hist); dfree(s.accepts); dfree(s.scalar); dfree(s.als_part); dfree(s.err);
-    dfree(s.x_bf16); dfree(s.yt_bf16); dfree(s.u_csr); dfree(s.u_csc); dfree(s.u_new);
+    dfree(s.part_grad, st); dfree(s.part_loss, st); dfree(s.part_loss2, st); dfree(s.cand, st);
+    dfree(s.f_old, st); dfree(s.r_old, st); dfree(s.r_new, st);
+    dfree(s.kept_obj_x, st); dfree(s.kept_reg_x, st); dfree(s.kept_obj_y, st); dfree(s.kept_reg_y, st);
+    dfree(s.acc_x, st); dfree(s.acc_y, st); dfree(s.red_part, st); dfree(s.red_cnt, st);
+    dfree(s.hist, st); dfree(s.accepts, st); dfree(s.scalar, st); dfree(s.als_part, st); dfree(s.err, st);
+    dfree(s.x_bf16, st); dfree(s.yt_bf16, st); dfree(s.u_csr, st); dfree(s.u_csc, st); dfree(s.u_new, st);
     s.u_sweeps = -1;
     s.hist_cap = 0;
     s.als_bytes = 0;
@@ -137,7 +132,7 @@ int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, siz
     const int64_t nother = xstep ? h->n : h->m;
     const int64_t ntiles = (o.nseg + 31) / 32;
     const bool forced = force != GLRM_PATH_AUTO;
-    CK(cudaMalloc(&o.tptr, (size_t)(ntiles + 1) * sizeof(int32_t)));
+    CK(dalloc(h, &o.tptr, (size_t)(ntiles + 1) * sizeof(int32_t)));
     CK(launch_mt_count(o, o.tptr, h->stream));
     std::vector<int32_t> cnt((size_t)ntiles);
     CK(cudaMemcpyAsync(cnt.data(), o.tptr, (size_t)ntiles * sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -154,7 +149,7 @@ int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, siz
     off[ntiles] = (int32_t)tot;
     const double lanes = tot ? (double)h->nnz / (double)tot : 0.0;
     auto give_up = [&](const char *why) {
-        dfree(o.tptr);
+        dfree(o.tptr, h->stream);
         return forced ? fail(h, GLRM_ERR_ARG, why) : GLRM_OK;
     };
     if (!forced && lanes < 8.0) return give_up("");
@@ -198,13 +193,13 @@ int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, siz
     o.npairs = tot;
     CK(cudaMemcpyAsync(o.tptr, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                        h->stream));
-    CK(cudaMalloc(&o.tidx, (size_t)std::max<int64_t>(tot, 1) * sizeof(int32_t)));
-    CK(cudaMalloc(&o.tmask, (size_t)std::max<int64_t>(tot, 1) * sizeof(uint32_t)));
-    CK(cudaMalloc(&o.tval, ((size_t)h->nnz + kPad) * es));
+    CK(dalloc(h, &o.tidx, (size_t)std::max<int64_t>(tot, 1) * sizeof(int32_t)));
+    CK(dalloc(h, &o.tmask, (size_t)std::max<int64_t>(tot, 1) * sizeof(uint32_t)));
+    CK(dalloc(h, &o.tval, ((size_t)h->nnz + kPad) * es));
     CK(cudaMemsetAsync(o.tval, 0, ((size_t)h->nnz + kPad) * es, h->stream));
-    CK(cudaMalloc(&o.ubeg, ubeg.size() * sizeof(int32_t)));
-    CK(cudaMalloc(&o.utile, (size_t)nunits * sizeof(int32_t)));
-    CK(cudaMalloc(&o.uvoff, (size_t)nunits * sizeof(int32_t)));
+    CK(dalloc(h, &o.ubeg, ubeg.size() * sizeof(int32_t)));
+    CK(dalloc(h, &o.utile, (size_t)nunits * sizeof(int32_t)));
+    CK(dalloc(h, &o.uvoff, (size_t)nunits * sizeof(int32_t)));
     CK(cudaMemcpyAsync(o.ubeg, ubeg.data(), ubeg.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaMemcpyAsync(o.utile, utile.data(), utile.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
@@ -234,14 +229,14 @@ int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
     int dev = h->device, optin = 0, sms = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    dfree(o.runptr);
-    dfree(o.tptr);
-    dfree(o.tidx);
-    dfree(o.tmask);
-    dfree(o.tval);
-    dfree(o.ubeg);
-    dfree(o.utile);
-    dfree(o.uvoff);
+    dfree(o.runptr, h->stream);
+    dfree(o.tptr, h->stream);
+    dfree(o.tidx, h->stream);
+    dfree(o.tmask, h->stream);
+    dfree(o.tval, h->stream);
+    dfree(o.ubeg, h->stream);
+    dfree(o.utile, h->stream);
+    dfree(o.uvoff, h->stream);
     const int K = tiled_width(h->k);
     o.mode = kModeChunked;
     if (force == GLRM_PATH_CHUNKED) return GLRM_OK;
@@ -306,7 +301,7 @@ int choose_mode(glrm_s *h, Orient &o, bool xstep, int force)
     o.ngroups = (int)std::max<int64_t>(1, std::min<int64_t>(o.nseg, (4LL * sms + nb - 1) / nb));
     o.smem_bytes = (((size_t)R * K * es + 15) & ~(size_t)15) + (xstep ? (size_t)R * sizeof(LossSpec) : 0) +
                    per_cap * cap;
-    CK(cudaMalloc(&o.runptr, (size_t)(nb + 1) * o.nseg * sizeof(int32_t)));
+    CK(dalloc(h, &o.runptr, (size_t)(nb + 1) * o.nseg * sizeof(int32_t)));
     CK(launch_build_runptr(o, h->stream));
     return GLRM_OK;
 }
@@ -346,41 +341,41 @@ int64_t partial_slots(const Orient &o)
 int alloc_scratch(glrm_s *h)
 {
     Scratch &s = h->s;
-    free_scratch(s);
+    free_scratch(s, h->stream);
     const size_t es = elem_size(h->prec);
     int64_t nch = std::max<int64_t>(1, std::max(partial_slots(h->csr), partial_slots(h->csc)));
     if (h->dn.on) nch = std::max<int64_t>(nch, h->dn.slots);
     const int Kt = std::max(h->k, tiled_width(h->k));
     const int64_t mx = std::max(h->m, h->n);
-    CK(cudaMalloc(&s.part_grad, (size_t)nch * Kt * es));
-    CK(cudaMalloc(&s.part_loss, (size_t)nch * sizeof(double)));
-    CK(cudaMalloc(&s.part_loss2, (size_t)nch * sizeof(double)));
-    CK(cudaMalloc(&s.cand, (size_t)mx * h->k * es));
-    CK(cudaMalloc(&s.f_old, (size_t)mx * sizeof(double)));
-    CK(cudaMalloc(&s.r_old, (size_t)mx * sizeof(double)));
-    CK(cudaMalloc(&s.r_new, (size_t)mx * sizeof(double)));
-    CK(cudaMalloc(&s.kept_obj_x, (size_t)h->m * sizeof(double)));
-    CK(cudaMalloc(&s.kept_reg_x, (size_t)h->m * sizeof(double)));
-    CK(cudaMalloc(&s.kept_obj_y, (size_t)h->n * sizeof(double)));
-    CK(cudaMalloc(&s.kept_reg_y, (size_t)h->n * sizeof(double)));
-    CK(cudaMalloc(&s.acc_x, (size_t)h->m * sizeof(int32_t)));
-    CK(cudaMalloc(&s.acc_y, (size_t)h->n * sizeof(int32_t)));
-    CK(cudaMalloc(&s.red_part, kRedBlocks * sizeof(double)));
-    CK(cudaMalloc(&s.red_cnt, 2 * kRedBlocks * sizeof(long long)));
-    CK(cudaMalloc(&s.accepts, 2 * sizeof(long long)));
-    CK(cudaMalloc(&s.scalar, sizeof(double)));
-    CK(cudaMalloc(&s.err, sizeof(int)));
+    CK(dalloc(h, &s.part_grad, (size_t)nch * Kt * es));
+    CK(dalloc(h, &s.part_loss, (size_t)nch * sizeof(double)));
+    CK(dalloc(h, &s.part_loss2, (size_t)nch * sizeof(double)));
+    CK(dalloc(h, &s.cand, (size_t)mx * h->k * es));
+    CK(dalloc(h, &s.f_old, (size_t)mx * sizeof(double)));
+    CK(dalloc(h, &s.r_old, (size_t)mx * sizeof(double)));
+    CK(dalloc(h, &s.r_new, (size_t)mx * sizeof(double)));
+    CK(dalloc(h, &s.kept_obj_x, (size_t)h->m * sizeof(double)));
+    CK(dalloc(h, &s.kept_reg_x, (size_t)h->m * sizeof(double)));
+    CK(dalloc(h, &s.kept_obj_y, (size_t)h->n * sizeof(double)));
+    CK(dalloc(h, &s.kept_reg_y, (size_t)h->n * sizeof(double)));
+    CK(dalloc(h, &s.acc_x, (size_t)h->m * sizeof(int32_t)));
+    CK(dalloc(h, &s.acc_y, (size_t)h->n * sizeof(int32_t)));
+    CK(dalloc(h, &s.red_part, kRedBlocks * sizeof(double)));
+    CK(dalloc(h, &s.red_cnt, 2 * kRedBlocks * sizeof(long long)));
+    CK(dalloc(h, &s.accepts, 2 * sizeof(long long)));
+    CK(dalloc(h, &s.scalar, sizeof(double)));
+    CK(dalloc(h, &s.err, sizeof(int)));
     if (h->prec == GLRM_BF16) {
-        CK(cudaMalloc(&s.x_bf16, (size_t)h->m * h->k * sizeof(__nv_bfloat16)));
-        CK(cudaMalloc(&s.yt_bf16, (size_t)h->n * h->k * sizeof(__nv_bfloat16)));
+        CK(dalloc(h, &s.x_bf16, (size_t)h->m * h->k * sizeof(__nv_bfloat16)));
+        CK(dalloc(h, &s.yt_bf16, (size_t)h->n * h->k * sizeof(__nv_bfloat16)));
         const size_t nz = (size_t)std::max<int64_t>(h->nnz, 1);
-        CK(cudaMalloc(&s.u_csr, nz * sizeof(float)));
-        CK(cudaMalloc(&s.u_csc, nz * sizeof(float)));
-        CK(cudaMalloc(&s.u_new, nz * sizeof(float)));
+        CK(dalloc(h, &s.u_csr, nz * sizeof(float)));
+        CK(dalloc(h, &s.u_csc, nz * sizeof(float)));
+        CK(dalloc(h, &s.u_new, nz * sizeof(float)));
         s.u_sweeps = -1;
         if (h->csr.perm == nullptr && h->nnz > 0) {
-            CK(cudaMalloc(&h->csr.perm, nz * sizeof(int32_t)));
-            CK(cudaMalloc(&h->csc.perm, nz * sizeof(int32_t)));
+            CK(dalloc(h, &h->csr.perm, nz * sizeof(int32_t)));
+            CK(dalloc(h, &h->csc.perm, nz * sizeof(int32_t)));
             CK(launch_perm(h->csr, h->csc, h->stream));
             CK(launch_perm(h->csc, h->csr, h->stream));
         }
@@ -393,8 +388,8 @@ int alloc_scratch(glrm_s *h)
 int ensure_hist(glrm_s *h, int n)
 {
     if (h->s.hist_cap >= n) return GLRM_OK;
-    dfree(h->s.hist);
-    CK(cudaMalloc(&h->s.hist, (size_t)n * sizeof(double)));
+    dfree(h->s.hist, h->stream);
+    CK(dalloc(h, &h->s.hist, (size_t)n * sizeof(double)));
     h->s.hist_cap = n;
     return GLRM_OK;
 }
@@ -449,7 +444,7 @@ int configure_paths(glrm_s *h)
     if (rc != GLRM_OK) return rc;
     Dense &d = h->dn;
     d.lda = (h->n + 3) / 4 * 4;
-    CK(cudaMalloc(&d.A, std::max<size_t>((size_t)h->m * d.lda * sizeof(float), 16)));
+    CK(dalloc(h, &d.A, std::max<size_t>((size_t)h->m * d.lda * sizeof(float), 16)));
     cudaError_t e = launch_dense_scatter(h);
     if (e == cudaSuccess) e = dense_prepare(h);
     if (e != cudaSuccess) {
@@ -470,8 +465,8 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     if (!rp || !cp || (nnz > 0 && (!ci || !rv || !ri || !cv)))
         return fail(h, GLRM_ERR_ARG, "null observed-set pointer");
     h->have_omega = false;
-    free_orient(h->csr);
-    free_orient(h->csc);
+    free_orient(h->csr, h->stream);
+    free_orient(h->csc, h->stream);
     dense_free(h);
     const size_t es = elem_size(h->prec);
     cudaStream_t st = h->stream;
@@ -482,12 +477,12 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     // kPad extra zeroed entries let the staged kernels copy 16-byte aligned
     // supersets of any entry range.
     const size_t nz = (size_t)nnz + kPad;
-    CK(cudaMalloc(&R.ptr, (size_t)(h->m + 1) * sizeof(int32_t)));
-    CK(cudaMalloc(&C.ptr, (size_t)(h->n + 1) * sizeof(int32_t)));
-    CK(cudaMalloc(&R.idx, nz * sizeof(int32_t)));
-    CK(cudaMalloc(&C.idx, nz * sizeof(int32_t)));
-    CK(cudaMalloc(&R.val, nz * es));
-    CK(cudaMalloc(&C.val, nz * es));
+    CK(dalloc(h, &R.ptr, (size_t)(h->m + 1) * sizeof(int32_t)));
+    CK(dalloc(h, &C.ptr, (size_t)(h->n + 1) * sizeof(int32_t)));
+    CK(dalloc(h, &R.idx, nz * sizeof(int32_t)));
+    CK(dalloc(h, &C.idx, nz * sizeof(int32_t)));
+    CK(dalloc(h, &R.val, nz * es));
+    CK(dalloc(h, &C.val, nz * es));
     CK(cudaMemsetAsync(R.idx, 0, nz * sizeof(int32_t), st));
     CK(cudaMemsetAsync(C.idx, 0, nz * sizeof(int32_t), st));
     CK(cudaMemsetAsync(R.val, 0, nz * es, st));
@@ -502,7 +497,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     }
     // validation: pointers first (the index checks rely on them)
     int *flag = nullptr;
-    CK(cudaMalloc(&flag, sizeof(int)));
+    CK(dalloc(h, &flag, sizeof(int)));
     int hflag = 0;
     auto check = [&](void) -> int {
         cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -528,12 +523,12 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_cross");
         if (rc == GLRM_OK) rc = check();
     }
-    cudaFree(flag);
+    dfree(flag, h->stream);
     if (rc != GLRM_OK) return rc;
     if (hflag) {
         const int code = (hflag & 8) && !(hflag & ~8) ? GLRM_ERR_NONFINITE : GLRM_ERR_OMEGA;
-        free_orient(R);
-        free_orient(C);
+        free_orient(R, h->stream);
+        free_orient(C, h->stream);
         return fail(h, code, (hflag & 8) && !(hflag & ~8) ? "non-finite value in the observed set"
                                                         : flag_message(hflag));
     }
@@ -545,8 +540,8 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         std::vector<int32_t> segchunk;
         build_chunks(ptr, chunks, segchunk, o->maxlen);
         o->nchunks = (int64_t)chunks.size();
-        CK(cudaMalloc(&o->chunks, std::max<size_t>(1, chunks.size()) * sizeof(int4)));
-        CK(cudaMalloc(&o->segchunk, segchunk.size() * sizeof(int32_t)));
+        CK(dalloc(h, &o->chunks, std::max<size_t>(1, chunks.size()) * sizeof(int4)));
+        CK(dalloc(h, &o->segchunk, segchunk.size() * sizeof(int32_t)));
         if (!chunks.empty())
             CK(cudaMemcpy(o->chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(o->segchunk, segchunk.data(), segchunk.size() * sizeof(int32_t),
@@ -575,25 +570,25 @@ int set_dense_impl(glrm_s *h, const void *A, int64_t lda, cudaMemcpyKind kind)
     if (!dense_supported(h->k)) return fail(h, GLRM_ERR_RANGE, "the dense form supports k <= 64");
     DeviceGuard dg(h->device);
     h->have_omega = false;
-    free_orient(h->csr);
-    free_orient(h->csc);
+    free_orient(h->csr, h->stream);
+    free_orient(h->csc, h->stream);
     dense_free(h);
     cudaStream_t st = h->stream;
     Dense &d = h->dn;
     d.lda = (h->n + 3) / 4 * 4;
     const size_t bytes = (size_t)h->m * d.lda * sizeof(float);
-    CK(cudaMalloc(&d.A, std::max<size_t>(bytes, 16)));
+    CK(dalloc(h, &d.A, std::max<size_t>(bytes, 16)));
     if (d.lda != h->n) CK(cudaMemsetAsync(d.A, 0, bytes, st));
     CK(cudaMemcpy2DAsync(d.A, (size_t)d.lda * sizeof(float), A, (size_t)lda * sizeof(float),
                          (size_t)h->n * sizeof(float), (size_t)h->m, kind, st));
     int *flag = nullptr;
-    CK(cudaMalloc(&flag, sizeof(int)));
+    CK(dalloc(h, &flag, sizeof(int)));
     int hflag = 0;
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
     if (e == cudaSuccess) e = launch_dense_validate(d.A, d.lda, h->m, h->n, h->loss_dev, flag, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(flag);
+    dfree(flag, h->stream);
     if (e != cudaSuccess) {
         dense_free(h);
         return cuda_fail(h, e, "dense validation");
@@ -632,6 +627,56 @@ cudaError_t reset_steps_any(glrm_s *h)
 
 namespace glrm {
 size_t elem_size(int prec) { return prec == GLRM_FP64 ? sizeof(double) : sizeof(float); }
+
+// Device memory of the handles: one stream-ordered pool per device that
+// keeps freed blocks (a new observed set of the same sizes reuses them
+// instead of paying cudaMalloc / cudaFree again); trimmed when the device's
+// last handle goes.
+namespace {
+std::mutex g_pool_mu;
+std::map<int, std::pair<cudaMemPool_t, int>> g_pools;  // device -> (pool, live handles)
+}  // namespace
+
+cudaError_t pool_acquire(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it == g_pools.end()) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+        it = g_pools.emplace(dev, std::make_pair(pool, 0)).first;
+    }
+    it->second.second += 1;
+    return cudaSuccess;
+}
+
+void pool_release(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it == g_pools.end()) return;
+    if (--it->second.second == 0) cudaMemPoolTrimTo(it->second.first, 0);
+}
+
+cudaError_t dalloc_bytes(glrm_s *h, void **p, size_t bytes)
+{
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        auto it = g_pools.find(h->device);
+        if (it == g_pools.end()) return cudaErrorInitializationError;
+        pool = it->second.first;
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, h->stream);
+}
 
 void tmark(glrm_s *h, const char *name)
 {
@@ -717,12 +762,14 @@ int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss, int3
     h->rx_w = rx_weight;
     h->ry_w = ry_weight;
     cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = pool_acquire(h->device);
+    if (e == cudaSuccess) h->pooled = true;
     const size_t es = elem_size(precision);
-    if (e == cudaSuccess) e = cudaMalloc(&h->loss_dev, (size_t)n * sizeof(LossSpec));
-    if (e == cudaSuccess) e = cudaMalloc(&h->X, (size_t)m * k * es);
-    if (e == cudaSuccess) e = cudaMalloc(&h->Yt, (size_t)n * k * es);
-    if (e == cudaSuccess) e = cudaMalloc(&h->alpha_x, (size_t)m * es);
-    if (e == cudaSuccess) e = cudaMalloc(&h->alpha_y, (size_t)n * es);
+    if (e == cudaSuccess) e = dalloc(h, &h->loss_dev, (size_t)n * sizeof(LossSpec));
+    if (e == cudaSuccess) e = dalloc(h, &h->X, (size_t)m * k * es);
+    if (e == cudaSuccess) e = dalloc(h, &h->Yt, (size_t)n * k * es);
+    if (e == cudaSuccess) e = dalloc(h, &h->alpha_x, (size_t)m * es);
+    if (e == cudaSuccess) e = dalloc(h, &h->alpha_y, (size_t)n * es);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->loss_dev, spec.data(), (size_t)n * sizeof(LossSpec),
                             cudaMemcpyHostToDevice, h->stream);
@@ -1104,15 +1151,17 @@ void glrm_destroy(glrm_t h)
         DeviceGuard dg(h->device);
         cudaStreamSynchronize(h->stream);
         for (cudaEvent_t ev : h->timer.pool) cudaEventDestroy(ev);
-        free_orient(h->csr);
-        free_orient(h->csc);
+        free_orient(h->csr, h->stream);
+        free_orient(h->csc, h->stream);
         dense_free(h);
-        free_scratch(h->s);
-        dfree(h->loss_dev);
-        dfree(h->X);
-        dfree(h->Yt);
-        dfree(h->alpha_x);
-        dfree(h->alpha_y);
+        free_scratch(h->s, h->stream);
+        dfree(h->loss_dev, h->stream);
+        dfree(h->X, h->stream);
+        dfree(h->Yt, h->stream);
+        dfree(h->alpha_x, h->stream);
+        dfree(h->alpha_y, h->stream);
+        cudaStreamSynchronize(h->stream);
+        if (h->pooled) pool_release(h->device);
     }
     delete h;
 }

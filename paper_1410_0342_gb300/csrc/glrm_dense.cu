@@ -842,7 +842,7 @@ void dense_free(glrm_s *h)
     Dense &d = h->dn;
     for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf, (void *)d.segchunk_x,
                     (void *)d.segchunk_y})
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, h->stream);
     d = Dense();
 }
 
@@ -897,8 +897,8 @@ cudaError_t dense_prepare(glrm_s *h)
     choose_parts(h->n, h->m, sms, d.parts_y, d.per_part_y);
     const int64_t rows_pad = (std::max(h->m, h->n) + kDnRows - 1) / kDnRows * kDnRows;
     d.pack_part = rows_pad * d.KP;
-    if ((e = cudaMalloc(&d.pk, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&d.pt, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &d.pk, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &d.pt, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
     if ((e = encode_maps(h)) != cudaSuccess) return e;
     // column losses in FP32, each with the kind its 16-column group shares
     // (-1: mixed)
@@ -925,13 +925,13 @@ cudaError_t dense_prepare(glrm_s *h)
         const int32_t kd = gk[j / 16];
         memcpy(&lf[j].w, &kd, sizeof kd);
     }
-    if ((e = cudaMalloc(&d.lossf, (size_t)h->n * sizeof(float4))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &d.lossf, (size_t)h->n * sizeof(float4))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(d.lossf, lf.data(), lf.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
 
     d.slots = std::max(h->m * d.parts_x, h->n * d.parts_y);
-    if ((e = cudaMalloc(&d.segchunk_x, (size_t)(h->m + 1) * sizeof(int32_t))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&d.segchunk_y, (size_t)(h->n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &d.segchunk_x, (size_t)(h->m + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &d.segchunk_y, (size_t)(h->n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
     dense_segchunk_kernel<<<(unsigned)((h->m + 256) / 256), 256, 0, h->stream>>>(d.segchunk_x, h->m, d.parts_x);
     dense_segchunk_kernel<<<(unsigned)((h->n + 256) / 256), 256, 0, h->stream>>>(d.segchunk_y, h->n, d.parts_y);
     return cudaGetLastError();

@@ -147,11 +147,29 @@ struct glrm_s {
     int64_t sweeps_done = 0;
     int path_x = GLRM_PATH_AUTO, path_y = GLRM_PATH_AUTO;
     std::string err;
+    bool pooled = false;  // holds a reference on the device's memory pool
 };
 
 namespace glrm {
 
 size_t elem_size(int prec);
+
+// Handle memory: stream-ordered allocations from a per-device pool (on the
+// handle's stream; freeing is ordered after the work queued before it).
+cudaError_t pool_acquire(int dev);
+void pool_release(int dev);
+cudaError_t dalloc_bytes(glrm_s *h, void **p, size_t bytes);
+template <class P>
+cudaError_t dalloc(glrm_s *h, P **p, size_t bytes)
+{
+    return dalloc_bytes(h, reinterpret_cast<void **>(p), bytes);
+}
+template <class P>
+void dfree(P *&p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync((void *)p, st);
+    p = nullptr;
+}
 
 // Record a timing mark before the launch of kernel `name` (null closes the
 // last interval).  No-op unless timing is enabled.
