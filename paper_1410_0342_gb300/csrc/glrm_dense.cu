@@ -29,8 +29,10 @@
 // GEMM1 MMAs, the copies and the GEMM2 MMAs; 16 warps run the per-entry
 // work): GEMM1 runs two chunks ahead into a double-buffered accumulator, so
 // the tensor core computes U of chunk q + 1 while the warps evaluate the
-// losses of chunk q; W's GEMM1 parts are triple-buffered, its GEMM2 parts and
-// the A tiles double- (or more) buffered.
+// losses of chunk q; R is double-buffered in tensor memory, so the warps
+// write R of chunk q while GEMM2 of chunk q - 1 still reads the other buffer;
+// W's GEMM1 and GEMM2 parts are triple-buffered, the A tiles two to four
+// times.
 #include <cuda.h>
 
 #include <string.h>
@@ -46,11 +48,11 @@ constexpr int kDnNT = 64;        // chunk of the other dimension (UMMA N of GEMM
 constexpr int kDnRows = 128;     // own rows per CTA (UMMA M)
 constexpr int kDnWarps = 16;     // evaluating warp w: TMEM lanes 32 (w % 4) .. + 31, chunk columns 16 (w / 4) .. + 15
 constexpr int kDnThreads = (kDnWarps + 3) * 32;  // + the GEMM1 warp, the copy warp, the GEMM2 warp
-// TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), R (hi, mid,
-// lo; 32 columns each) at [192, 288), the own rows (hi, mid, lo; KP / 2
-// columns each) from 288
+// TMEM columns: U at [0, 64) and [64, 128), G at [128, 128 + KP), two buffers
+// of R (hi, mid, lo; 32 columns each) at [192, 288) and [288, 384), the own
+// rows (hi, mid, lo; KP / 2 columns each) from 384
 constexpr int kDnTmem = 512;
-constexpr int kDnColG = 128, kDnColR = 192, kDnColOwn = 288;
+constexpr int kDnColG = 128, kDnColR = 192, kDnColOwn = 384;
 constexpr int kDnMaxStages = 4;
 
 // Column loss with its parameters in FP32 (kind as int bits, Huber
@@ -74,7 +76,7 @@ struct DenseArgs {
 
 // Dynamic shared memory of one CTA: the A stages first (1024-byte aligned for
 // the swizzled boxes; 1024 bytes of slack align the base), then three stages
-// of W's three GEMM1 parts, two stages of W's two GEMM2 parts and three
+// of W's three GEMM1 parts, three stages of W's three GEMM2 parts and three
 // stages of the loss table (every operand buffer on a 1024-byte boundary).
 template <bool XSTEP, bool GRAD, int KP>
 struct DnSmem {
@@ -82,7 +84,7 @@ struct DnSmem {
     static constexpr size_t pt = GRAD ? (size_t)KP * kDnNT * 2 : 0;
     static constexpr size_t ls = XSTEP ? (size_t)kDnNT * sizeof(LossF) : 0;
     static constexpr size_t a = (size_t)kDnNT * kDnRows * 4;  // 32 KB A tile
-    static constexpr size_t fixed = 9 * pk + 6 * pt + 3 * ls;
+    static constexpr size_t fixed = 9 * pk + 9 * pt + 3 * ls;
     static size_t bytes(int nA) { return 1024 + fixed + (size_t)nA * a; }
 };
 
@@ -242,7 +244,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 {
     using SM = DnSmem<XSTEP, GRAD, KP>;
     extern __shared__ __align__(1024) unsigned char dsm_dense[];
-    __shared__ uint64_t barA[kDnMaxStages], barP[3], barL[3], barT[2], barG1[2], barG2, barU[2], barE[4];
+    __shared__ uint64_t barA[kDnMaxStages], barP[3], barL[3], barT[3], barG1[2], barG2[2], barU[2], barE[4];
     __shared__ uint32_t tslot;
     __shared__ double red[4][kDnRows];
     unsigned char *base = dsm_dense + ((1024 - (smem_u32(dsm_dense) & 1023)) & 1023);
@@ -250,7 +252,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     unsigned char *fx = base + (size_t)p.nA * SM::a;             // fixed buffers
     unsigned char *pkst = fx;                                    // pk stage s at pkst + s * 3 pk
     unsigned char *ptst = pkst + 9 * SM::pk;                     // pt stage s at ptst + s * 3 pt
-    unsigned char *lsst = ptst + 6 * SM::pt;                     // loss table stage s at lsst + s * ls
+    unsigned char *lsst = ptst + 9 * SM::pt;                     // loss table stage s at lsst + s * ls
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, grp = (warp >> 2) & 3;
@@ -273,11 +275,11 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
         for (int s = 0; s < kDnMaxStages; ++s) mbar_init(&barA[s], 1);
         for (int s = 0; s < 3; ++s) mbar_init(&barP[s], 1);
         for (int s = 0; s < 3; ++s) mbar_init(&barL[s], 1);
-        mbar_init(&barT[0], 1);
-        mbar_init(&barT[1], 1);
+        for (int s = 0; s < 3; ++s) mbar_init(&barT[s], 1);
         mbar_init(&barG1[0], 1);
         mbar_init(&barG1[1], 1);
-        mbar_init(&barG2, 1);
+        mbar_init(&barG2[0], 1);
+        mbar_init(&barG2[1], 1);
         mbar_init(&barU[0], kDnWarps);
         mbar_init(&barU[1], kDnWarps);
         for (int s = 0; s < 4; ++s) mbar_init(&barE[s], kDnWarps);
@@ -346,8 +348,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 bulk_g2s(lsst + s * SM::ls, p.lossf + t0, (unsigned)(nv * sizeof(LossF)), &barL[s]);
                 ++l_issued;
             };
-            auto issue_pt = [&](int64_t q) {  // GEMM2's W parts, stage q % 2
-                const int s = (int)((q - qb) & 1);
+            auto issue_pt = [&](int64_t q) {  // GEMM2's W parts, stage q % 3
+                const int s = (int)((q - qb) % 3);
                 unsigned char *st = ptst + s * 3 * SM::pt;
                 mbar_expect_tx(&barT[s], (unsigned)(3 * SM::pt));
 #pragma unroll
@@ -394,8 +396,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
             // GEMM2 of chunk q: G += R W, R from tensor memory
             auto issue_gemm2 = [&](int64_t q) -> bool {
                 const int c = (int)(q - qb);
-                const int s = c & 1;
-                if (!mbar_wait_bounded(&barT[s], (unsigned)(c >> 1) & 1u)) return false;
+                const int s = c % 3, rb = c & 1;
+                if (!mbar_wait_bounded(&barT[s], (unsigned)(c / 3) & 1u)) return false;
                 tc_fence_after();
                 const uint32_t idesc = umma_idesc_bf16(kDnRows, KP);
                 const unsigned char *wt = ptst + s * 3 * SM::pt;
@@ -406,10 +408,10 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
                     for (int ks = 0; ks < kDnNT / 16; ++ks)
-                        umma_bf16_ta(taddr + kDnColG, taddr + (uint32_t)(kDnColR + pa[pr] * 32 + ks * 8),
+                        umma_bf16_ta(taddr + kDnColG, taddr + (uint32_t)(kDnColR + rb * 96 + pa[pr] * 32 + ks * 8),
                                      umma_desc_sw(wt + pb[pr] * SM::pt + ks * 32, 2 * kDnNT), idesc,
                                      c > 0 || pr > 0 || ks > 0);
-                umma_commit(&barG2);
+                umma_commit(&barG2[rb]);
                 ++g2_issued;
                 return true;
             };
@@ -457,9 +459,9 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 }
                 for (int it = 0; it < nq; ++it) {
                     const int64_t q = qb + it;
-                    // the entries of chunk q are done: its A stage, loss-table stage
-                    // and (GEMM2 of q - 1 having completed before) the GEMM2 stage of
-                    // q - 1 are free
+                    // the entries of chunk q are done: its A stage and loss-table
+                    // stage are free, and (the warps having waited for GEMM2 of
+                    // q - 2 before writing R of q) so is the GEMM2 stage of q - 2
                     if (!mbar_wait_bounded(&barE[it & 3], (unsigned)(it >> 2) & 1u)) {
                         ok = false;
                         break;
@@ -544,7 +546,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
             }
             if constexpr (GRAD) {
                 // R of the previous chunk is no longer read once its GEMM2 is done
-                if (it > 0) ok = mbar_wait_bounded(&barG2, (unsigned)(it - 1) & 1u);
+                // R buffer it % 2 is free once GEMM2 of it - 2 is done
+                if (it > 1) ok = mbar_wait_bounded(&barG2[b], (unsigned)((it - 2) >> 1) & 1u);
                 tc_fence_after();
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
@@ -566,9 +569,10 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                     mi[w / 2] = bf2_bits(m2);
                     lo[w / 2] = bf2_bits(__floats2bfloat162_rn(b0, b1));
                 }
-                tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + tb / 2), hi);
-                tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + 32 + tb / 2), mi);
-                tmem_st8(taddr + lane_base + (uint32_t)(kDnColR + 64 + tb / 2), lo);
+                const uint32_t rcol = kDnColR + (uint32_t)(b * 96 + tb / 2);
+                tmem_st8(taddr + lane_base + rcol, hi);
+                tmem_st8(taddr + lane_base + rcol + 32, mi);
+                tmem_st8(taddr + lane_base + rcol + 64, lo);
                 tmem_wait_st();
             }
             tc_fence_before();
@@ -576,7 +580,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
             if (lane == 0) mbar_arrive(&barE[it & 3]);
         }
         if (GRAD && ok) {
-            ok = mbar_wait_bounded(&barG2, (unsigned)(nq - 1) & 1u);
+            ok = mbar_wait_bounded(&barG2[(nq - 1) & 1], (unsigned)((nq - 1) >> 1) & 1u);
+            if (ok && nq > 1) ok = mbar_wait_bounded(&barG2[nq & 1], (unsigned)((nq - 2) >> 1) & 1u);
             tc_fence_after();
             ok = __all_sync(0xffffffffu, ok);
         }
@@ -611,11 +616,12 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
             mbar_wait_bounded(&barL[c % 3], (unsigned)(c / 3) & 1u);
         for (int c = a_issued - nA > 0 ? a_issued - nA : 0; c < a_issued; ++c)
             mbar_wait_bounded(&barA[c % nA], (unsigned)(c / nA) & 1u);
-        for (int c = t_issued - 2 > 0 ? t_issued - 2 : 0; c < t_issued; ++c)
-            mbar_wait_bounded(&barT[c & 1], (unsigned)(c >> 1) & 1u);
+        for (int c = t_issued - 3 > 0 ? t_issued - 3 : 0; c < t_issued; ++c)
+            mbar_wait_bounded(&barT[c % 3], (unsigned)(c / 3) & 1u);
         for (int c = g1_issued - 2 > 0 ? g1_issued - 2 : 0; c < g1_issued; ++c)
             mbar_wait_bounded(&barG1[c & 1], (unsigned)(c >> 1) & 1u);
-        if (g2_issued > 0) mbar_wait_bounded(&barG2, (unsigned)(g2_issued - 1) & 1u);
+        for (int c = g2_issued - 2 > 0 ? g2_issued - 2 : 0; c < g2_issued; ++c)
+            mbar_wait_bounded(&barG2[c & 1], (unsigned)(c >> 1) & 1u);
     }
     tc_fence_before();
     __syncthreads();
