@@ -38,6 +38,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "glrm_tc.cuh"
@@ -59,6 +61,14 @@ constexpr int kDnMaxStages = 4;
 // threshold, ordinal level count, unused).
 using LossF = float4;
 
+// One CTA's work: chunks q0 .. q0 + nq - 1 of the other dimension against own
+// tile `tile`, the tile's part `part` of `parts`.  Row r of the tile keeps its
+// partial results in slot base + r * parts + part.
+struct DnItem {
+    int32_t tile, part, parts, q0, nq, pad;
+    int64_t base;
+};
+
 struct DenseArgs {
     int64_t nown, nother;
     int k;
@@ -67,10 +77,10 @@ struct DenseArgs {
     const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid
     int64_t pack_part;        // elements per part
     const LossF *lossf;       // n column losses; w: the kind of the column's 16-column group, else -1
-    int parts, nA;
-    int64_t nchunks, per_part;  // chunks of the other dimension, chunks per part
-    float *part_grad;           // (nown * parts) x k
-    double *part_loss;          // nown * parts
+    const DnItem *items;  // one per CTA
+    int nA;
+    float *part_grad;     // slots x k
+    double *part_loss;    // slots
     int *err;
 };
 
@@ -257,11 +267,11 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, grp = (warp >> 2) & 3;
     const int orow = quarter * 32 + lane;
-    const int64_t o0 = (int64_t)blockIdx.x * kDnRows;
-    const int part = blockIdx.y;
-    const int64_t qb = (int64_t)part * p.per_part;
-    const int64_t qe = qb + p.per_part < p.nchunks ? qb + p.per_part : p.nchunks;
-    const int nq = (int)(qe - qb);
+    const DnItem item = p.items[blockIdx.x];
+    const int64_t o0 = (int64_t)item.tile * kDnRows;
+    const int64_t qb = item.q0;
+    const int nq = item.nq;
+    const int64_t slot = item.base + (int64_t)orow * item.parts + item.part;
     const int nA = p.nA;
     // kDnWarps: GEMM1 warp, kDnWarps + 1: copy warp, kDnWarps + 2: GEMM2 warp
     const bool producer = warp >= kDnWarps;
@@ -590,7 +600,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     if (!fail && !producer) {
         red[grp][orow] = (double)lacc - (double)lcomp;
         if (GRAD && grp == 0) {
-            float *g = p.part_grad + ((o0 + orow) * p.parts + part) * p.k;
+            float *g = p.part_grad + slot * p.k;
 #pragma unroll
             for (int bb = 0; bb < KP / 16; ++bb) {
                 float v[16];
@@ -605,7 +615,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     }
     __syncthreads();
     if (!fail && !producer && grp == 0 && own_ok)
-        p.part_loss[(o0 + orow) * p.parts + part] = red[0][orow] + red[1][orow] + red[2][orow] + red[3][orow];
+        p.part_loss[slot] = red[0][orow] + red[1][orow] + red[2][orow] + red[3][orow];
     if (fail && producer && lane == 0) {  // each producer warp drains what it issued
         atomicOr(p.err, 1);
         // wait (bounded) for the last copy into each stage and the last MMA
@@ -726,10 +736,18 @@ static __global__ void dense_alpha_kernel(float *__restrict__ alpha, int64_t nse
     if (s < nseg) alpha[s] = value;
 }
 
-static __global__ void dense_segchunk_kernel(int32_t *__restrict__ sc, int64_t nseg, int parts)
+// Segment s (row s % 128 of own tile s / 128) -> its first partial slot;
+// tb holds per tile {first slot, parts}; sc[nseg] = total slots.
+static __global__ void dense_segchunk_kernel(int32_t *__restrict__ sc, int64_t nseg, const int64_t *__restrict__ tb,
+                                             int64_t total)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s <= nseg) sc[s] = (int32_t)(s * parts);
+    if (s < nseg) {
+        const int64_t t = s / kDnRows;
+        sc[s] = (int32_t)(tb[2 * t] + (s - t * kDnRows) * tb[2 * t + 1]);
+    } else if (s == nseg) {
+        sc[s] = (int32_t)total;
+    }
 }
 
 namespace {
@@ -742,15 +760,14 @@ int dense_width(int k)
 }
 
 template <bool XSTEP, bool GRAD, int KP, bool MISS>
-cudaError_t launch_dense_kp(glrm_s *h, const DenseArgs &a, int nA, unsigned tiles)
+cudaError_t launch_dense_kp(glrm_s *h, const DenseArgs &a, int nA, unsigned items)
 {
     const size_t smem = DnSmem<XSTEP, GRAD, KP>::bytes(nA);
     cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP, MISS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(XSTEP ? h->dn.tmap_x : h->dn.tmap_y);
-    dense_pass_kernel<XSTEP, GRAD, KP, MISS>
-        <<<dim3(tiles, (unsigned)a.parts), kDnThreads, smem, h->stream>>>(a, *map);
+    dense_pass_kernel<XSTEP, GRAD, KP, MISS><<<items, kDnThreads, smem, h->stream>>>(a, *map);
     h->launches += 1;
     return cudaGetLastError();
 }
@@ -783,13 +800,11 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     a.pt = d.pt;
     a.pack_part = d.pack_part;
     a.lossf = d.lossf;
-    a.parts = XSTEP ? d.parts_x : d.parts_y;
-    a.nchunks = (a.nother + kDnNT - 1) / kDnNT;
-    a.per_part = XSTEP ? d.per_part_x : d.per_part_y;
+    a.items = XSTEP ? d.items_x : d.items_y;
     a.part_grad = part_grad;
     a.part_loss = part_loss;
     a.err = h->s.err;
-    const unsigned tiles = (unsigned)((a.nown + kDnRows - 1) / kDnRows);
+    const unsigned tiles = (unsigned)(XSTEP ? d.nitems_x : d.nitems_y);
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     if (e != cudaSuccess) return e;
@@ -827,16 +842,96 @@ cudaError_t dense_pack(glrm_s *h, const float *W, int64_t rows)
     return cudaGetLastError();
 }
 
-// Parts of the other dimension per own tile: about four CTAs per SM in all,
-// no part empty.
-void choose_parts(int64_t nown, int64_t nother, int sms, int &parts, int64_t &per_part)
+// Relative cost of evaluating one entry of a 16- or 32-wide group of columns
+// (counted instructions of the loss blocks plus the per-entry load and sum
+// work): a group whose columns share one kind takes that kind's block; a
+// group that mixes kinds, or runs past the table, takes the per-entry switch
+// and pays for every kind present (its lanes diverge).
+double group_cost(const std::vector<LossSpec> &loss, int64_t j0, int width)
 {
+    auto extra = [](int kind) -> double {
+        switch (kind) {
+        case kLossQuad: return 2;
+        case kLossHuber: return 8;
+        case kLossHinge: return 4;
+        case kLossLogistic: return 22;
+        default: return 16;
+        }
+    };
+    const int64_t n = (int64_t)loss.size();
+    bool uniform = j0 + width <= n;
+    unsigned seen = 0;
+    for (int64_t j = j0; j < j0 + width; ++j) {
+        const int kd = j < n ? loss[j].kind : kLossQuad;  // lanes past the table run the quadratic block
+        if (j < n && kd != loss[j0].kind) uniform = false;
+        seen |= 1u << kd;
+    }
+    if (uniform) return 6 + extra(loss[j0].kind);
+    double c = 10;
+    for (int kd = 0; kd <= kLossOrdinal; ++kd)
+        if (seen >> kd & 1u) c += extra(kd);
+    return c;
+}
+
+// Work items of one pass: own tile t (rows t * 128 ..) takes parts_t items,
+// each a contiguous range of the other dimension's 64-wide chunks.  Entry
+// costs vary with the column losses: along the chunks in the X-step (the
+// columns are the other dimension), between the tiles in the Y-step.  The
+// parts are sized so every item carries about the same cost, about four
+// items per SM in all (no fewer items than tiles, no item empty), and the
+// items are ordered by the middle of their chunk range, so items reading the
+// same chunks of the other factor run close together.
+struct ItemPlan {
+    std::vector<DnItem> items;
+    std::vector<int64_t> tiles;  // per tile {first slot, parts}
+    int64_t slots = 0;
+};
+
+ItemPlan plan_items(int64_t nown, int64_t nother, int sms, const std::vector<double> &tile_cost,
+                    const std::vector<double> &chunk_cost)
+{
+    ItemPlan pl;
     const int64_t tiles = (nown + kDnRows - 1) / kDnRows;
     const int64_t nch = std::max<int64_t>(1, (nother + kDnNT - 1) / kDnNT);
-    int64_t want = (4LL * sms + tiles - 1) / tiles;
-    want = std::max<int64_t>(1, std::min<int64_t>(want, nch));
-    per_part = (nch + want - 1) / want;
-    parts = (int)((nch + per_part - 1) / per_part);
+    std::vector<double> pre(nch + 1, 0.0);
+    for (int64_t q = 0; q < nch; ++q) pre[q + 1] = pre[q] + chunk_cost[q];
+    double total = 0;
+    for (int64_t t = 0; t < tiles; ++t) total += tile_cost[t] * pre[nch];
+    const double per_item = total / (double)std::max<int64_t>(tiles, 4LL * sms);
+    pl.tiles.resize(2 * tiles);
+    for (int64_t t = 0; t < tiles; ++t) {
+        int64_t np = (int64_t)std::llround(tile_cost[t] * pre[nch] / per_item);
+        np = std::max<int64_t>(1, std::min<int64_t>(np, nch));
+        const int64_t rows = std::min<int64_t>(kDnRows, nown - t * kDnRows);
+        pl.tiles[2 * t] = pl.slots;
+        pl.tiles[2 * t + 1] = np;
+        int64_t q = 0;
+        for (int64_t i = 0; i < np; ++i) {
+            // end of range i: the first chunk boundary at or past (i + 1) / np
+            // of the tile's cost, leaving at least one chunk for each later range
+            int64_t e = nch;
+            if (i + 1 < np) {
+                const double goal = pre[nch] * (double)(i + 1) / (double)np;
+                e = std::lower_bound(pre.begin(), pre.end(), goal) - pre.begin();
+                e = std::max<int64_t>(e, q + 1);
+                e = std::min<int64_t>(e, nch - (np - 1 - i));
+            }
+            DnItem it{};
+            it.tile = (int32_t)t;
+            it.part = (int32_t)i;
+            it.parts = (int32_t)np;
+            it.q0 = (int32_t)q;
+            it.nq = (int32_t)(e - q);
+            it.base = pl.slots;
+            pl.items.push_back(it);
+            q = e;
+        }
+        pl.slots += rows * np;
+    }
+    std::stable_sort(pl.items.begin(), pl.items.end(), [](const DnItem &a, const DnItem &b) {
+        return 2LL * a.q0 + a.nq < 2LL * b.q0 + b.nq;
+    });
+    return pl;
 }
 
 }  // namespace
@@ -847,7 +942,7 @@ void dense_free(glrm_s *h)
 {
     Dense &d = h->dn;
     for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf, (void *)d.segchunk_x,
-                    (void *)d.segchunk_y})
+                    (void *)d.segchunk_y, (void *)d.items_x, (void *)d.items_y})
         if (p) cudaFreeAsync(p, h->stream);
     d = Dense();
 }
@@ -890,8 +985,8 @@ cudaError_t encode_maps(glrm_s *h)
 
 }  // namespace
 
-// Packs, part split and the segment -> partial-slot tables the shared prox
-// and decide kernels read (segment s owns slots s * parts .. s * parts + parts).
+// Packs, work items and the segment -> partial-slot tables the shared prox
+// and decide kernels read (segment s owns slots segchunk[s] .. segchunk[s + 1]).
 cudaError_t dense_prepare(glrm_s *h)
 {
     Dense &d = h->dn;
@@ -899,8 +994,6 @@ cudaError_t dense_prepare(glrm_s *h)
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
-    choose_parts(h->m, h->n, sms, d.parts_x, d.per_part_x);
-    choose_parts(h->n, h->m, sms, d.parts_y, d.per_part_y);
     const int64_t rows_pad = (std::max(h->m, h->n) + kDnRows - 1) / kDnRows * kDnRows;
     d.pack_part = rows_pad * d.KP;
     if ((e = dalloc(h, &d.pk, 3 * (size_t)d.pack_part * sizeof(__nv_bfloat16))) != cudaSuccess) return e;
@@ -932,15 +1025,50 @@ cudaError_t dense_prepare(glrm_s *h)
         memcpy(&lf[j].w, &kd, sizeof kd);
     }
     if ((e = dalloc(h, &d.lossf, (size_t)h->n * sizeof(float4))) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(d.lossf, lf.data(), lf.size() * sizeof(float4), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(d.lossf, lf.data(), lf.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                             h->stream)) != cudaSuccess)
         return e;
 
-    d.slots = std::max(h->m * d.parts_x, h->n * d.parts_y);
+    // X-step: chunks are 64 columns (four 16-column groups), tiles alike;
+    // Y-step: tiles are 128 columns (four 32-column warps), chunks alike
+    const int64_t tiles_x = (h->m + kDnRows - 1) / kDnRows, tiles_y = (h->n + kDnRows - 1) / kDnRows;
+    const int64_t nch_x = std::max<int64_t>(1, (h->n + kDnNT - 1) / kDnNT);
+    const int64_t nch_y = std::max<int64_t>(1, (h->m + kDnNT - 1) / kDnNT);
+    std::vector<double> cx(nch_x, 0.0), cy(tiles_y, 0.0);
+    for (int64_t q = 0; q < nch_x; ++q)
+        for (int g = 0; g < kDnNT / 16; ++g) cx[q] += 16 * group_cost(h->loss_host, q * kDnNT + 16 * g, 16);
+    for (int64_t t = 0; t < tiles_y; ++t)
+        for (int g = 0; g < kDnRows / 32; ++g) cy[t] += 32 * group_cost(h->loss_host, t * kDnRows + 32 * g, 32);
+    const ItemPlan px = plan_items(h->m, h->n, sms, std::vector<double>(tiles_x, 1.0), cx);
+    const ItemPlan py = plan_items(h->n, h->m, sms, cy, std::vector<double>(nch_y, 1.0));
+    if (px.slots > INT32_MAX || py.slots > INT32_MAX) return cudaErrorInvalidValue;
+    d.nitems_x = (int64_t)px.items.size();
+    d.nitems_y = (int64_t)py.items.size();
+    d.slots_x = px.slots;
+    d.slots_y = py.slots;
+    d.slots = std::max(px.slots, py.slots);
+    int64_t *tb = nullptr;
+    if ((e = dalloc(h, &d.items_x, px.items.size() * sizeof(DnItem))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &d.items_y, py.items.size() * sizeof(DnItem))) != cudaSuccess) return e;
     if ((e = dalloc(h, &d.segchunk_x, (size_t)(h->m + 1) * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = dalloc(h, &d.segchunk_y, (size_t)(h->n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
-    dense_segchunk_kernel<<<(unsigned)((h->m + 256) / 256), 256, 0, h->stream>>>(d.segchunk_x, h->m, d.parts_x);
-    dense_segchunk_kernel<<<(unsigned)((h->n + 256) / 256), 256, 0, h->stream>>>(d.segchunk_y, h->n, d.parts_y);
-    return cudaGetLastError();
+    if ((e = dalloc(h, &tb, (px.tiles.size() + py.tiles.size()) * sizeof(int64_t))) != cudaSuccess) return e;
+    const std::pair<const void *, void *> copies[4] = {{px.items.data(), d.items_x},
+                                                       {py.items.data(), d.items_y},
+                                                       {px.tiles.data(), tb},
+                                                       {py.tiles.data(), tb + px.tiles.size()}};
+    const size_t sizes[4] = {px.items.size() * sizeof(DnItem), py.items.size() * sizeof(DnItem),
+                             px.tiles.size() * sizeof(int64_t), py.tiles.size() * sizeof(int64_t)};
+    for (int c = 0; c < 4; ++c)
+        if ((e = cudaMemcpyAsync(copies[c].second, copies[c].first, sizes[c], cudaMemcpyHostToDevice, h->stream)) !=
+            cudaSuccess)
+            return e;
+    dense_segchunk_kernel<<<(unsigned)((h->m + 256) / 256), 256, 0, h->stream>>>(d.segchunk_x, h->m, tb, px.slots);
+    dense_segchunk_kernel<<<(unsigned)((h->n + 256) / 256), 256, 0, h->stream>>>(d.segchunk_y, h->n,
+                                                                                tb + px.tiles.size(), py.slots);
+    e = cudaGetLastError();
+    dfree(tb, h->stream);
+    return e;
 }
 
 cudaError_t launch_dense_scatter(glrm_s *h)
@@ -1020,7 +1148,7 @@ cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, doubl
     if ((e = launch_dense<true, false>(h, X, nullptr, s.part_loss)) != cudaSuccess) return e;
     tmark(h, "reduce_stage1");
     reduce_stage1<float><<<kRedBlocks, 256, 0, h->stream>>>(
-        s.part_loss, h->m * h->dn.parts_x, nullptr, 0, X, h->m, h->rx_kind, (float)h->rx_w, Yt, h->n,
+        s.part_loss, h->dn.slots_x, nullptr, 0, X, h->m, h->rx_kind, (float)h->rx_w, Yt, h->n,
         h->ry_kind, (float)h->ry_w, h->k, nullptr, 0, nullptr, 0, s.red_part, s.red_cnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, "reduce_stage2");

@@ -95,19 +95,21 @@ struct Scratch {
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 
 // Dense (fully observed) table and the tensor-core form's buffers.
+struct DnItem;
+
 struct Dense {
     bool on = false;
     bool missing = false;  // A holds NaN at cells outside Omega (a sparse table stored densely)
     float *A = nullptr;    // m x lda, lda = n rounded up to 4, padding zero
     int64_t lda = 0;
     int KP = 0;  // k padded to a multiple of 16
-    int parts_x = 1, parts_y = 1;         // partial slots per row / column
-    int64_t per_part_x = 0, per_part_y = 0;  // 64-wide chunks per part
+    DnItem *items_x = nullptr, *items_y = nullptr;  // per-CTA work items of the X- and Y-step passes
+    int64_t nitems_x = 0, nitems_y = 0;
     __nv_bfloat16 *pk = nullptr;  // packed other factor, K-major over k (parts hi, mid, lo)
     __nv_bfloat16 *pt = nullptr;  // packed other factor, K-major over chunk rows (parts hi, mid)
     int64_t pack_part = 0;        // elements per part
-    int32_t *segchunk_x = nullptr, *segchunk_y = nullptr;  // segment -> first partial slot (s * parts)
-    int64_t slots = 0;                                     // partial slots of the larger half-step
+    int32_t *segchunk_x = nullptr, *segchunk_y = nullptr;  // segment -> first partial slot
+    int64_t slots_x = 0, slots_y = 0, slots = 0;           // partial slots per half-step, the larger
     float4 *lossf = nullptr;      // n column losses in FP32 {kind bits, param, levels, group kind bits}
     alignas(64) unsigned char tmap_x[128] = {};  // CUtensorMap of A, X-step boxes
     alignas(64) unsigned char tmap_y[128] = {};  // CUtensorMap of A, Y-step boxes
