@@ -40,6 +40,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <functional>
+#include <queue>
 #include <vector>
 
 #include "glrm_tc.cuh"
@@ -60,14 +62,6 @@ constexpr int kDnMaxStages = 4;
 // Column loss with its parameters in FP32 (kind as int bits, Huber
 // threshold, ordinal level count, unused).
 using LossF = float4;
-
-// One CTA's work: chunks q0 .. q0 + nq - 1 of the other dimension against own
-// tile `tile`, the tile's part `part` of `parts`.  Row r of the tile keeps its
-// partial results in slot base + r * parts + part.
-struct DnItem {
-    int32_t tile, part, parts, q0, nq, pad;
-    int64_t base;
-};
 
 struct DenseArgs {
     int64_t nown, nother;
@@ -876,61 +870,138 @@ double group_cost(const std::vector<LossSpec> &loss, int64_t j0, int width)
 // Work items of one pass: own tile t (rows t * 128 ..) takes parts_t items,
 // each a contiguous range of the other dimension's 64-wide chunks.  Entry
 // costs vary with the column losses: along the chunks in the X-step (the
-// columns are the other dimension), between the tiles in the Y-step.  The
-// parts are sized so every item carries about the same cost, about four
-// items per SM in all (no fewer items than tiles, no item empty), and the
-// items are ordered by the middle of their chunk range, so items reading the
-// same chunks of the other factor run close together.
-struct ItemPlan {
-    std::vector<DnItem> items;
-    std::vector<int64_t> tiles;  // per tile {first slot, parts}
-    int64_t slots = 0;
+// columns are the other dimension), between the tiles in the Y-step.
+//
+// Plan: parts sized so items carry about equal cost, about four items per SM
+// (no fewer than tiles, none empty), launched in the order of the middle of
+// their chunk range (items reading the same chunks of the other factor run
+// close together).  One CTA is resident per SM, and a finished CTA's SM takes
+// the next item in launch order, so the pass ends when the last SM does:
+// the per-item cost target and the number of items split in two (halves
+// launched after the rest, to fill the last wave) are chosen by simulating
+// that schedule, with each item paying a fixed pipeline fill and drain of
+// about 1.3 average chunks on top of its entries.
+struct PlanRange {
+    int64_t tile, q0, q1;
+    bool tail;  // a half of a split item: launched after the others
 };
+
+double list_schedule_end(const std::vector<double> &t, int slots)
+{
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int i = 0; i < slots; ++i) free_at.push(0.0);
+    double end = 0;
+    for (double c : t) {
+        const double f = free_at.top() + c;
+        free_at.pop();
+        free_at.push(f);
+        end = std::max(end, f);
+    }
+    return end;
+}
 
 ItemPlan plan_items(int64_t nown, int64_t nother, int sms, const std::vector<double> &tile_cost,
                     const std::vector<double> &chunk_cost)
 {
-    ItemPlan pl;
     const int64_t tiles = (nown + kDnRows - 1) / kDnRows;
     const int64_t nch = std::max<int64_t>(1, (nother + kDnNT - 1) / kDnNT);
     std::vector<double> pre(nch + 1, 0.0);
     for (int64_t q = 0; q < nch; ++q) pre[q + 1] = pre[q] + chunk_cost[q];
     double total = 0;
     for (int64_t t = 0; t < tiles; ++t) total += tile_cost[t] * pre[nch];
-    const double per_item = total / (double)std::max<int64_t>(tiles, 4LL * sms);
-    pl.tiles.resize(2 * tiles);
+    const double fill = 1.3 * total / (double)(tiles * nch);
+    auto mid = [](const PlanRange &r) { return r.q0 + r.q1; };
+    auto order = [&](std::vector<PlanRange> &v) {
+        std::stable_sort(v.begin(), v.end(), [&](const PlanRange &a, const PlanRange &b) {
+            return a.tail != b.tail ? !a.tail : mid(a) < mid(b);
+        });
+    };
+    // the tile's chunks in np ranges of about equal cost, at least one chunk each
+    auto build = [&](double per_item) {
+        std::vector<PlanRange> v;
+        for (int64_t t = 0; t < tiles; ++t) {
+            int64_t np = (int64_t)std::llround(tile_cost[t] * pre[nch] / per_item);
+            np = std::max<int64_t>(1, std::min<int64_t>(np, nch));
+            int64_t q = 0;
+            for (int64_t i = 0; i < np; ++i) {
+                int64_t e = nch;
+                if (i + 1 < np) {
+                    const double goal = pre[nch] * (double)(i + 1) / (double)np;
+                    e = std::lower_bound(pre.begin(), pre.end(), goal) - pre.begin();
+                    e = std::max<int64_t>(e, q + 1);
+                    e = std::min<int64_t>(e, nch - (np - 1 - i));
+                }
+                v.push_back({t, q, e, false});
+                q = e;
+            }
+        }
+        order(v);
+        return v;
+    };
+    // the last `s` items of the launch order split in two at the middle of their cost
+    auto split = [&](const std::vector<PlanRange> &v, int64_t s) {
+        std::vector<PlanRange> w(v.begin(), v.end() - s);
+        for (auto r = v.end() - s; r != v.end(); ++r) {
+            if (r->q1 - r->q0 < 2) {
+                w.push_back(*r);
+                continue;
+            }
+            const double goal = 0.5 * (pre[r->q0] + pre[r->q1]);
+            int64_t e = std::lower_bound(pre.begin() + r->q0, pre.begin() + r->q1, goal) - pre.begin();
+            e = std::max<int64_t>(r->q0 + 1, std::min<int64_t>(e, r->q1 - 1));
+            w.push_back({r->tile, r->q0, e, true});
+            w.push_back({r->tile, e, r->q1, true});
+        }
+        order(w);
+        return w;
+    };
+    auto finish_time = [&](const std::vector<PlanRange> &v) {
+        std::vector<double> t(v.size());
+        for (size_t i = 0; i < v.size(); ++i) t[i] = tile_cost[v[i].tile] * (pre[v[i].q1] - pre[v[i].q0]) + fill;
+        return list_schedule_end(t, sms);
+    };
+    const double per0 = total / (double)std::max<int64_t>(tiles, 4LL * sms);
+    std::vector<PlanRange> best = build(per0);
+    if ((int64_t)best.size() <= 64LL * sms) {  // beyond that the last wave is a small share
+        double best_end = finish_time(best);
+        for (int f = 0; f <= 10; ++f) {
+            const std::vector<PlanRange> v = build(per0 * (1.0 + 0.03 * f));
+            const int64_t n = (int64_t)v.size();
+            for (int g = 0; g <= 24; ++g) {
+                const std::vector<PlanRange> w = g ? split(v, n * g / 24) : v;
+                const double end = finish_time(w);
+                if (end < best_end * (1.0 - 1e-9)) {
+                    best_end = end;
+                    best = w;
+                }
+            }
+        }
+    }
+    // parts per tile in chunk order, slots, items in launch order
+    ItemPlan pl;
+    pl.tiles.assign(2 * tiles, 0);
+    std::vector<std::vector<size_t>> by_tile(tiles);
+    for (size_t i = 0; i < best.size(); ++i) by_tile[best[i].tile].push_back(i);
+    pl.items.resize(best.size());
     for (int64_t t = 0; t < tiles; ++t) {
-        int64_t np = (int64_t)std::llround(tile_cost[t] * pre[nch] / per_item);
-        np = std::max<int64_t>(1, std::min<int64_t>(np, nch));
+        std::vector<size_t> &ix = by_tile[t];
+        std::sort(ix.begin(), ix.end(), [&](size_t a, size_t b) { return best[a].q0 < best[b].q0; });
         const int64_t rows = std::min<int64_t>(kDnRows, nown - t * kDnRows);
         pl.tiles[2 * t] = pl.slots;
-        pl.tiles[2 * t + 1] = np;
-        int64_t q = 0;
-        for (int64_t i = 0; i < np; ++i) {
-            // end of range i: the first chunk boundary at or past (i + 1) / np
-            // of the tile's cost, leaving at least one chunk for each later range
-            int64_t e = nch;
-            if (i + 1 < np) {
-                const double goal = pre[nch] * (double)(i + 1) / (double)np;
-                e = std::lower_bound(pre.begin(), pre.end(), goal) - pre.begin();
-                e = std::max<int64_t>(e, q + 1);
-                e = std::min<int64_t>(e, nch - (np - 1 - i));
-            }
+        pl.tiles[2 * t + 1] = (int64_t)ix.size();
+        for (size_t p = 0; p < ix.size(); ++p) {
+            const PlanRange &r = best[ix[p]];
             DnItem it{};
             it.tile = (int32_t)t;
-            it.part = (int32_t)i;
-            it.parts = (int32_t)np;
-            it.q0 = (int32_t)q;
-            it.nq = (int32_t)(e - q);
+            it.part = (int32_t)p;
+            it.parts = (int32_t)ix.size();
+            it.q0 = (int32_t)r.q0;
+            it.nq = (int32_t)(r.q1 - r.q0);
             it.base = pl.slots;
-            pl.items.push_back(it);
-            q = e;
+            pl.items[ix[p]] = it;
         }
-        pl.slots += rows * np;
+        pl.slots += rows * (int64_t)ix.size();
     }
-    std::stable_sort(pl.items.begin(), pl.items.end(), [](const DnItem &a, const DnItem &b) {
-        return 2LL * a.q0 + a.nq < 2LL * b.q0 + b.nq;
-    });
     return pl;
 }
 
@@ -1034,13 +1105,22 @@ cudaError_t dense_prepare(glrm_s *h)
     const int64_t tiles_x = (h->m + kDnRows - 1) / kDnRows, tiles_y = (h->n + kDnRows - 1) / kDnRows;
     const int64_t nch_x = std::max<int64_t>(1, (h->n + kDnNT - 1) / kDnNT);
     const int64_t nch_y = std::max<int64_t>(1, (h->m + kDnNT - 1) / kDnNT);
-    std::vector<double> cx(nch_x, 0.0), cy(tiles_y, 0.0);
-    for (int64_t q = 0; q < nch_x; ++q)
-        for (int g = 0; g < kDnNT / 16; ++g) cx[q] += 16 * group_cost(h->loss_host, q * kDnNT + 16 * g, 16);
-    for (int64_t t = 0; t < tiles_y; ++t)
-        for (int g = 0; g < kDnRows / 32; ++g) cy[t] += 32 * group_cost(h->loss_host, t * kDnRows + 32 * g, 32);
-    const ItemPlan px = plan_items(h->m, h->n, sms, std::vector<double>(tiles_x, 1.0), cx);
-    const ItemPlan py = plan_items(h->n, h->m, sms, cy, std::vector<double>(nch_y, 1.0));
+    DensePlan &pl = h->dnplan;  // depends only on m, n, the losses and the device: made once per handle
+    if (!pl.ready) {
+        std::vector<double> cx(nch_x, 0.0), cy(tiles_y, 0.0);
+        for (int64_t q = 0; q < nch_x; ++q)
+            for (int g = 0; g < kDnNT / 16; ++g) cx[q] += 16 * group_cost(h->loss_host, q * kDnNT + 16 * g, 16);
+        // a Y-step tile advances at the pace of its slowest 32-column quarter: a
+        // quarter's four warps (warp indices equal mod 4) share one SM
+        // sub-partition, and the quarters move through the chunks in step
+        for (int64_t t = 0; t < tiles_y; ++t)
+            for (int g = 0; g < kDnRows / 32; ++g)
+                cy[t] = std::max(cy[t], kDnRows * group_cost(h->loss_host, t * kDnRows + 32 * g, 32));
+        pl.x = plan_items(h->m, h->n, sms, std::vector<double>(tiles_x, 1.0), cx);
+        pl.y = plan_items(h->n, h->m, sms, cy, std::vector<double>(nch_y, 1.0));
+        pl.ready = true;
+    }
+    const ItemPlan &px = pl.x, &py = pl.y;
     if (px.slots > INT32_MAX || py.slots > INT32_MAX) return cudaErrorInvalidValue;
     d.nitems_x = (int64_t)px.items.size();
     d.nitems_y = (int64_t)py.items.size();

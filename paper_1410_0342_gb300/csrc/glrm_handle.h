@@ -95,7 +95,27 @@ struct Scratch {
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 
 // Dense (fully observed) table and the tensor-core form's buffers.
-struct DnItem;
+// One CTA's work in a dense pass: chunks q0 .. q0 + nq - 1 of the other
+// dimension against own tile `tile` (own rows tile * 128 ..), the tile's
+// part `part` of `parts`.  Row r of the tile keeps its partial results in
+// slot base + r * parts + part.
+struct DnItem {
+    int32_t tile, part, parts, q0, nq, pad;
+    int64_t base;
+};
+
+// The work items of one pass in launch order, per tile {first slot, parts},
+// and the number of partial slots.
+struct ItemPlan {
+    std::vector<DnItem> items;
+    std::vector<int64_t> tiles;
+    int64_t slots = 0;
+};
+
+struct DensePlan {
+    bool ready = false;
+    ItemPlan x, y;
+};
 
 struct Dense {
     bool on = false;
@@ -144,6 +164,7 @@ struct glrm_s {
     glrm::Orient csr, csc;
     glrm::Scratch s;
     glrm::Dense dn;
+    glrm::DensePlan dnplan;  // dense-pass work items (fixed by m, n and the losses)
     glrm::Timer timer;
     long long launches = 0;  // kernels enqueued since creation
     int64_t sweeps_done = 0;
