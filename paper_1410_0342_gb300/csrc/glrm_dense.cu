@@ -71,7 +71,9 @@ struct DenseArgs {
     const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid
     int64_t pack_part;        // elements per part
     const LossF *lossf;       // n column losses; w: the kind of the column's 16-column group, else -1
-    const DnItem *items;  // one per CTA
+    const DnItem *items;      // one per CTA
+    const int32_t *blocks;    // Y-step: per tile its four 32-column blocks (-1: none)
+    const int32_t *segchunk;  // own index -> first partial slot
     int nA;
     float *part_grad;     // slots x k
     double *part_loss;    // slots
@@ -265,12 +267,18 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     const int64_t o0 = (int64_t)item.tile * kDnRows;
     const int64_t qb = item.q0;
     const int nq = item.nq;
-    const int64_t slot = item.base + (int64_t)orow * item.parts + item.part;
     const int nA = p.nA;
     // kDnWarps: GEMM1 warp, kDnWarps + 1: copy warp, kDnWarps + 2: GEMM2 warp
     const bool producer = warp >= kDnWarps;
-    const bool own_ok = !producer && o0 + orow < p.nown;
-    const int nown_t = (int)(p.nown - o0 < kDnRows ? p.nown - o0 : kDnRows);
+    // this thread's own row (X-step) or column (Y-step: quarter q of the tile
+    // is the 32-column block blocks[4 tile + q]), and its partial slot
+    int64_t own = o0 + orow;
+    if (!XSTEP) {
+        const int32_t b = producer ? -1 : p.blocks[4 * (int64_t)item.tile + quarter];
+        own = b < 0 ? p.nown : 32 * (int64_t)b + lane;
+    }
+    const bool own_ok = !producer && own < p.nown;
+    const int64_t slot = own_ok ? (int64_t)p.segchunk[own] + item.part : 0;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const int tb = grp * 16;  // this warp's columns of a chunk
 
@@ -290,7 +298,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     }
     // Y-step: this thread's column loss, and whether the warp shares one kind
     LossF myspec = make_float4(__int_as_float(kLossQuad), 0.f, 0.f, 0.f);
-    if (!XSTEP && own_ok) myspec = p.lossf[o0 + orow];
+    if (!XSTEP && own_ok) myspec = p.lossf[own];
     int wkind = -1;
     if constexpr (!XSTEP) {
         const int kd = __float_as_int(myspec.x);
@@ -309,8 +317,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
             uint32_t hv[8], mv[8], lv[8];
 #pragma unroll
             for (int w = 0; w < 16; w += 2) {
-                const float v0 = (orow < nown_t && c0 + w < p.k) ? p.F[(o0 + orow) * p.k + c0 + w] : 0.f;
-                const float v1 = (orow < nown_t && c0 + w + 1 < p.k) ? p.F[(o0 + orow) * p.k + c0 + w + 1] : 0.f;
+                const float v0 = (own_ok && c0 + w < p.k) ? p.F[own * p.k + c0 + w] : 0.f;
+                const float v1 = (own_ok && c0 + w + 1 < p.k) ? p.F[own * p.k + c0 + w + 1] : 0.f;
                 __nv_bfloat16 h0, m0, l0, h1, m1, l1;
                 split3(v0, h0, m0, l0);
                 split3(v1, h1, m1, l1);
@@ -361,16 +369,27 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                     bulk_g2s(st + w * SM::pt, p.pt + w * p.pack_part + q * KP * kDnNT, (unsigned)SM::pt, &barT[s]);
                 ++t_issued;
             };
+            // Y-step: the tile's 32-column blocks (box q of a stage holds block q)
+            int32_t blk[4] = {-1, -1, -1, -1};
+            unsigned nblk = 0;
+            if constexpr (!XSTEP) {
+                for (int qd = 0; qd < 4; ++qd) {
+                    blk[qd] = p.blocks[4 * (int64_t)item.tile + qd];
+                    nblk += blk[qd] >= 0 ? 1u : 0u;
+                }
+            }
             auto issue_a = [&](int64_t q) {  // the A tile, stage q % nA (out-of-range elements read as 0)
                 const int s = (int)((q - qb) % nA);
                 unsigned char *dst = ast + s * SM::a;
                 const int t0 = (int)(q * kDnNT);
-                mbar_expect_tx(&barA[s], (unsigned)SM::a);
                 if constexpr (XSTEP) {
+                    mbar_expect_tx(&barA[s], (unsigned)SM::a);
                     tma_load_2d(dst, &amap, t0, (int)o0, &barA[s]);
                     tma_load_2d(dst + SM::a / 2, &amap, t0 + 32, (int)o0, &barA[s]);
                 } else {
-                    tma_load_2d(dst, &amap, (int)o0, t0, &barA[s]);
+                    mbar_expect_tx(&barA[s], nblk * (unsigned)(SM::a / 4));
+                    for (int qd = 0; qd < 4; ++qd)
+                        if (blk[qd] >= 0) tma_load_2d(dst + qd * (SM::a / 4), &amap, 32 * blk[qd], t0, &barA[s]);
                 }
                 ++a_issued;
             };
@@ -511,9 +530,10 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                         a[4 * w + 3] = v.w;
                     }
                 } else {
-                    const float *af = reinterpret_cast<const float *>(as);
+                    // box `quarter`: 64 chunk rows x 32 columns
+                    const float *af = reinterpret_cast<const float *>(as) + quarter * (kDnNT * 32);
 #pragma unroll
-                    for (int w = 0; w < 16; ++w) a[w] = af[(tb + w) * kDnRows + orow];
+                    for (int w = 0; w < 16; ++w) a[w] = af[(tb + w) * 32 + lane];
                 }
                 const int64_t nv = p.nother - t0 - tb;  // valid columns from tb on
                 const uint32_t valid = !own_ok ? 0u : (nv >= 16 ? 0xffffu : (nv <= 0 ? 0u : (1u << nv) - 1u));
@@ -795,6 +815,8 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     a.pack_part = d.pack_part;
     a.lossf = d.lossf;
     a.items = XSTEP ? d.items_x : d.items_y;
+    a.blocks = XSTEP ? nullptr : d.blocks_y;
+    a.segchunk = XSTEP ? d.segchunk_x : d.segchunk_y;
     a.part_grad = part_grad;
     a.part_loss = part_loss;
     a.err = h->s.err;
@@ -1013,7 +1035,7 @@ void dense_free(glrm_s *h)
 {
     Dense &d = h->dn;
     for (void *p : {(void *)d.A, (void *)d.pk, (void *)d.pt, (void *)d.lossf, (void *)d.segchunk_x,
-                    (void *)d.segchunk_y, (void *)d.items_x, (void *)d.items_y})
+                    (void *)d.segchunk_y, (void *)d.items_x, (void *)d.items_y, (void *)d.blocks_y})
         if (p) cudaFreeAsync(p, h->stream);
     d = Dense();
 }
@@ -1025,7 +1047,7 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // Tensor maps of A (FP32, dims n x m, row pitch lda): X-step boxes of 32
-// columns x 128 rows with the 128-byte swizzle, Y-step boxes of 128 columns x
+// columns x 128 rows with the 128-byte swizzle, Y-step boxes of 32 columns x
 // 64 rows.  Out-of-range elements load as zero.
 cudaError_t encode_maps(glrm_s *h)
 {
@@ -1043,7 +1065,7 @@ cudaError_t encode_maps(glrm_s *h)
     const cuuint64_t strides[1] = {(cuuint64_t)d.lda * sizeof(float)};
     const cuuint32_t estr[2] = {1, 1};
     const cuuint32_t box_x[2] = {32, (cuuint32_t)kDnRows};
-    const cuuint32_t box_y[2] = {(cuuint32_t)kDnRows, (cuuint32_t)kDnNT};
+    const cuuint32_t box_y[2] = {32, (cuuint32_t)kDnNT};
     CUresult r = encode(reinterpret_cast<CUtensorMap *>(d.tmap_x), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, d.A, dims,
                         strides, box_x, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1110,14 +1132,39 @@ cudaError_t dense_prepare(glrm_s *h)
         std::vector<double> cx(nch_x, 0.0), cy(tiles_y, 0.0);
         for (int64_t q = 0; q < nch_x; ++q)
             for (int g = 0; g < kDnNT / 16; ++g) cx[q] += 16 * group_cost(h->loss_host, q * kDnNT + 16 * g, 16);
-        // a Y-step tile advances at the pace of its slowest 32-column quarter: a
-        // quarter's four warps (warp indices equal mod 4) share one SM
-        // sub-partition, and the quarters move through the chunks in step
-        for (int64_t t = 0; t < tiles_y; ++t)
-            for (int g = 0; g < kDnRows / 32; ++g)
-                cy[t] = std::max(cy[t], kDnRows * group_cost(h->loss_host, t * kDnRows + 32 * g, 32));
+        // Y-step tiles: the 32-column blocks in order of cost (then loss kind),
+        // four to a tile.  A tile advances at the pace of its slowest block: a
+        // block's four warps (warp indices equal mod 4) share one SM
+        // sub-partition, and the four blocks move through the chunks in step;
+        // tiles of like blocks leave no sub-partition waiting on another.
+        const int64_t nb = (h->n + 31) / 32;
+        std::vector<double> bc(nb);
+        std::vector<int64_t> order(nb);
+        for (int64_t b = 0; b < nb; ++b) {
+            bc[b] = group_cost(h->loss_host, 32 * b, 32);
+            order[b] = b;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int64_t u, int64_t v) {
+            return bc[u] != bc[v] ? bc[u] < bc[v] : h->loss_host[32 * u].kind < h->loss_host[32 * v].kind;
+        });
+        pl.blocks_y.assign(4 * tiles_y, -1);
+        std::vector<int64_t> tile_of(nb);
+        for (int64_t i = 0; i < nb; ++i) {
+            pl.blocks_y[i] = (int32_t)order[i];
+            tile_of[order[i]] = i / 4;
+            cy[i / 4] = std::max(cy[i / 4], kDnRows * bc[order[i]]);
+        }
         pl.x = plan_items(h->m, h->n, sms, std::vector<double>(tiles_x, 1.0), cx);
         pl.y = plan_items(h->n, h->m, sms, cy, std::vector<double>(nch_y, 1.0));
+        // Y slots in column order: column j owns parts-of-its-tile slots
+        pl.seg_y.resize(h->n + 1);
+        int64_t run = 0;
+        for (int64_t j = 0; j < h->n; ++j) {
+            pl.seg_y[j] = (int32_t)std::min<int64_t>(run, INT32_MAX);
+            run += pl.y.tiles[2 * tile_of[j / 32] + 1];
+        }
+        pl.seg_y[h->n] = (int32_t)std::min<int64_t>(run, INT32_MAX);
+        pl.y.slots = run;
         pl.ready = true;
     }
     const ItemPlan &px = pl.x, &py = pl.y;
@@ -1130,22 +1177,23 @@ cudaError_t dense_prepare(glrm_s *h)
     int64_t *tb = nullptr;
     if ((e = dalloc(h, &d.items_x, px.items.size() * sizeof(DnItem))) != cudaSuccess) return e;
     if ((e = dalloc(h, &d.items_y, py.items.size() * sizeof(DnItem))) != cudaSuccess) return e;
+    if ((e = dalloc(h, &d.blocks_y, pl.blocks_y.size() * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = dalloc(h, &d.segchunk_x, (size_t)(h->m + 1) * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = dalloc(h, &d.segchunk_y, (size_t)(h->n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
-    if ((e = dalloc(h, &tb, (px.tiles.size() + py.tiles.size()) * sizeof(int64_t))) != cudaSuccess) return e;
-    const std::pair<const void *, void *> copies[4] = {{px.items.data(), d.items_x},
+    if ((e = dalloc(h, &tb, px.tiles.size() * sizeof(int64_t))) != cudaSuccess) return e;
+    const std::pair<const void *, void *> copies[5] = {{px.items.data(), d.items_x},
                                                        {py.items.data(), d.items_y},
-                                                       {px.tiles.data(), tb},
-                                                       {py.tiles.data(), tb + px.tiles.size()}};
-    const size_t sizes[4] = {px.items.size() * sizeof(DnItem), py.items.size() * sizeof(DnItem),
-                             px.tiles.size() * sizeof(int64_t), py.tiles.size() * sizeof(int64_t)};
-    for (int c = 0; c < 4; ++c)
+                                                       {pl.blocks_y.data(), d.blocks_y},
+                                                       {pl.seg_y.data(), d.segchunk_y},
+                                                       {px.tiles.data(), tb}};
+    const size_t sizes[5] = {px.items.size() * sizeof(DnItem), py.items.size() * sizeof(DnItem),
+                             pl.blocks_y.size() * sizeof(int32_t), pl.seg_y.size() * sizeof(int32_t),
+                             px.tiles.size() * sizeof(int64_t)};
+    for (int c = 0; c < 5; ++c)
         if ((e = cudaMemcpyAsync(copies[c].second, copies[c].first, sizes[c], cudaMemcpyHostToDevice, h->stream)) !=
             cudaSuccess)
             return e;
     dense_segchunk_kernel<<<(unsigned)((h->m + 256) / 256), 256, 0, h->stream>>>(d.segchunk_x, h->m, tb, px.slots);
-    dense_segchunk_kernel<<<(unsigned)((h->n + 256) / 256), 256, 0, h->stream>>>(d.segchunk_y, h->n,
-                                                                                tb + px.tiles.size(), py.slots);
     e = cudaGetLastError();
     dfree(tb, h->stream);
     return e;

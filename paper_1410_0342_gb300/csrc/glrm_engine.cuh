@@ -163,8 +163,12 @@ prox_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restr
     const T al = alpha[s];
     T ro = T(0), rn = T(0);
     for (int c = lane; c < k; c += 32) {
-        T g = T(0);
-        for (int q = cb; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
+        // in slot order; unrolled so the loads of a segment with many slots overlap
+        T g = ce > cb ? part_grad[(int64_t)cb * k + c] : T(0);
+        if (ce - cb > 1) {
+#pragma unroll 8
+            for (int q = cb + 1; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
+        }
         const T x = F[s * k + c];
         const T xp = prox1<T>(rkind, rw, al, x - al * g);
         cand[s * k + c] = xp;
@@ -305,8 +309,12 @@ seg_grad_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__r
     const int cb = segchunk[s], ce = segchunk[s + 1];
     const T sc = scale ? (T)*scale : T(1);
     for (int c = lane; c < k; c += 32) {
-        T g = T(0);
-        for (int q = cb; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
+        // in slot order; unrolled so the loads of a segment with many slots overlap
+        T g = ce > cb ? part_grad[(int64_t)cb * k + c] : T(0);
+        if (ce - cb > 1) {
+#pragma unroll 8
+            for (int q = cb + 1; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
+        }
         if (reg) g += reg_grad1<T>(rkind, rw, F[s * k + c]);
         G[s * k + c] = sc * g;
     }

@@ -114,7 +114,9 @@ struct ItemPlan {
 
 struct DensePlan {
     bool ready = false;
-    ItemPlan x, y;
+    ItemPlan x, y;  // y.items index Y-step tiles of blocks_y; y.slots from seg_y
+    std::vector<int32_t> blocks_y;  // per Y-step tile its four 32-column blocks (-1: none)
+    std::vector<int32_t> seg_y;     // column -> first partial slot (n + 1 entries)
 };
 
 struct Dense {
@@ -124,6 +126,7 @@ struct Dense {
     int64_t lda = 0;
     int KP = 0;  // k padded to a multiple of 16
     DnItem *items_x = nullptr, *items_y = nullptr;  // per-CTA work items of the X- and Y-step passes
+    int32_t *blocks_y = nullptr;                    // per Y-step tile its four 32-column blocks
     int64_t nitems_x = 0, nitems_y = 0;
     __nv_bfloat16 *pk = nullptr;  // packed other factor, K-major over k (parts hi, mid, lo)
     __nv_bfloat16 *pt = nullptr;  // packed other factor, K-major over chunk rows (parts hi, mid)
