@@ -477,53 +477,110 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     // kPad extra zeroed entries let the staged kernels copy 16-byte aligned
     // supersets of any entry range.
     const size_t nz = (size_t)nnz + kPad;
+    if (!h->aux) {
+        CK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_csr, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming));
+    }
+    cudaStream_t au = h->aux;
+    // every return below waits for the work queued on the auxiliary stream
+    struct AuxDrain {
+        cudaStream_t s;
+        ~AuxDrain() { cudaStreamSynchronize(s); }
+    } drain{au};
     CK(dalloc(h, &R.ptr, (size_t)(h->m + 1) * sizeof(int32_t)));
     CK(dalloc(h, &C.ptr, (size_t)(h->n + 1) * sizeof(int32_t)));
     CK(dalloc(h, &R.idx, nz * sizeof(int32_t)));
     CK(dalloc(h, &C.idx, nz * sizeof(int32_t)));
     CK(dalloc(h, &R.val, nz * es));
     CK(dalloc(h, &C.val, nz * es));
-    CK(cudaMemsetAsync(R.idx, 0, nz * sizeof(int32_t), st));
-    CK(cudaMemsetAsync(C.idx, 0, nz * sizeof(int32_t), st));
-    CK(cudaMemsetAsync(R.val, 0, nz * es, st));
-    CK(cudaMemsetAsync(C.val, 0, nz * es, st));
+    int *flag = nullptr;                // [0]: CSR checks, [1]: CSC checks
+    unsigned long long *dig = nullptr;  // index and value digests: CSR, then CSC
+    CK(dalloc(h, &flag, 2 * sizeof(int)));
+    CK(dalloc(h, &dig, 4 * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+    CK(cudaMemsetAsync(dig, 0, 4 * sizeof(unsigned long long), st));
+    // the copies fill entries 0 .. nnz - 1; only the padding is zeroed
+    CK(cudaMemsetAsync(R.idx + nnz, 0, kPad * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(C.idx + nnz, 0, kPad * sizeof(int32_t), st));
+    CK(cudaMemsetAsync((char *)R.val + (size_t)nnz * es, 0, kPad * es, st));
+    CK(cudaMemsetAsync((char *)C.val + (size_t)nnz * es, 0, kPad * es, st));
+    // CSR first: its checks and chunk table run on the auxiliary stream while
+    // the CSC arrays are still being copied
     CK(cudaMemcpyAsync(R.ptr, rp, (size_t)(h->m + 1) * sizeof(int32_t), kind, st));
-    CK(cudaMemcpyAsync(C.ptr, cp, (size_t)(h->n + 1) * sizeof(int32_t), kind, st));
     if (nnz > 0) {
         CK(cudaMemcpyAsync(R.idx, ci, (size_t)nnz * sizeof(int32_t), kind, st));
-        CK(cudaMemcpyAsync(C.idx, ri, (size_t)nnz * sizeof(int32_t), kind, st));
         CK(cudaMemcpyAsync(R.val, rv, (size_t)nnz * es, kind, st));
+    }
+    CK(cudaEventRecord(h->ev_csr, st));
+    CK(cudaMemcpyAsync(C.ptr, cp, (size_t)(h->n + 1) * sizeof(int32_t), kind, st));
+    if (nnz > 0) {
+        CK(cudaMemcpyAsync(C.idx, ri, (size_t)nnz * sizeof(int32_t), kind, st));
         CK(cudaMemcpyAsync(C.val, cv, (size_t)nnz * es, kind, st));
     }
-    // validation: pointers first (the index checks rely on them)
-    int *flag = nullptr;
-    CK(dalloc(h, &flag, sizeof(int)));
-    int hflag = 0;
-    auto check = [&](void) -> int {
-        cudaError_t e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    CK(cudaStreamWaitEvent(au, h->ev_csr, 0));
+    // validation, per orientation: pointers first (the index checks rely on
+    // them), then indices, values, the loss domains and the digests; the two
+    // orientations' digests are compared last
+    int hf[2] = {0, 0};
+    auto check = [&](int which, cudaStream_t s) -> int {
+        cudaError_t e = cudaMemcpyAsync(&hf[which], flag + which, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(h, e, "validation");
         return GLRM_OK;
     };
+    // chunk table of one orientation, host-built from its validated pointer array
+    auto chunk_table = [&](Orient &o, cudaStream_t s) -> int {
+        std::vector<int32_t> ptr(o.nseg + 1);
+        CK(cudaMemcpyAsync(ptr.data(), o.ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::vector<int4> chunks;
+        std::vector<int32_t> segchunk;
+        build_chunks(ptr, chunks, segchunk, o.maxlen);
+        o.nchunks = (int64_t)chunks.size();
+        CK(dalloc_on(h, &o.chunks, std::max<size_t>(1, chunks.size()) * sizeof(int4), s));
+        CK(dalloc_on(h, &o.segchunk, segchunk.size() * sizeof(int32_t), s));
+        if (!chunks.empty())
+            CK(cudaMemcpyAsync(o.chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(o.segchunk, segchunk.data(), segchunk.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           s));
+        CK(cudaStreamSynchronize(s));  // the host tables go out of scope
+        return GLRM_OK;
+    };
     int rc = GLRM_OK;
-    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = launch_validate_ptr(R.ptr, h->m, nnz, flag, st);
-    if (e == cudaSuccess) e = launch_validate_ptr(C.ptr, h->n, nnz, flag, st);
+    cudaError_t e = launch_validate_ptr(R.ptr, h->m, nnz, flag, au);
     if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_ptr");
-    if (rc == GLRM_OK) rc = check();
-    if (rc == GLRM_OK && hflag == 0) {
-        e = launch_validate_idx(R.ptr, R.idx, R.val, h->prec, h->m, h->n, flag, st);
-        if (e == cudaSuccess) e = launch_validate_idx(C.ptr, C.idx, C.val, h->prec, h->n, h->m, flag, st);
+    if (rc == GLRM_OK) rc = check(0, au);
+    if (rc == GLRM_OK && hf[0] == 0) {
+        e = launch_validate_idx(R.ptr, R.idx, R.val, h->prec, h->m, h->n, flag, au);
+        if (e == cudaSuccess) e = launch_validate_domain(R, true, h->n, h->prec, h->loss_dev, flag, au);
+        if (e == cudaSuccess) e = launch_digest(R, true, h->n, h->prec, dig, au);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
-        if (rc == GLRM_OK) rc = check();
+        if (rc == GLRM_OK) rc = check(0, au);
     }
-    if (rc == GLRM_OK && hflag == 0) {
-        e = launch_validate_cross(R, C, h->prec, flag, st);
-        if (e == cudaSuccess) e = launch_validate_domain(C, h->prec, h->loss_dev, flag, st);
-        if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_cross");
-        if (rc == GLRM_OK) rc = check();
+    if (rc == GLRM_OK && hf[0] == 0) rc = chunk_table(R, au);
+    if (rc == GLRM_OK && hf[0] == 0) {
+        // the CSC side: on the main stream, after its copies
+        e = cudaEventRecord(h->ev_aux, au);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_aux, 0);
+        if (e == cudaSuccess) e = launch_validate_ptr(C.ptr, h->n, nnz, flag + 1, st);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_ptr");
+        if (rc == GLRM_OK) rc = check(1, st);
+        if (rc == GLRM_OK && hf[1] == 0) {
+            e = launch_validate_idx(C.ptr, C.idx, C.val, h->prec, h->n, h->m, flag + 1, st);
+            if (e == cudaSuccess) e = launch_digest(C, false, h->n, h->prec, dig + 2, st);
+            if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
+            if (rc == GLRM_OK) rc = check(1, st);
+        }
+        if (rc == GLRM_OK && hf[1] == 0) {
+            e = launch_digest_compare(dig, flag + 1, st);
+            if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_cross");
+            if (rc == GLRM_OK) rc = check(1, st);
+        }
     }
-    dfree(flag, h->stream);
+    dfree(flag, st);
+    dfree(dig, st);
+    const int hflag = hf[0] | hf[1];
     if (rc != GLRM_OK) return rc;
     if (hflag) {
         const int code = (hflag & 8) && !(hflag & ~8) ? GLRM_ERR_NONFINITE : GLRM_ERR_OMEGA;
@@ -532,21 +589,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         return fail(h, code, (hflag & 8) && !(hflag & ~8) ? "non-finite value in the observed set"
                                                         : flag_message(hflag));
     }
-    // chunk tables (host-built from the validated pointer arrays)
-    for (Orient *o : {&R, &C}) {
-        std::vector<int32_t> ptr(o->nseg + 1);
-        CK(cudaMemcpy(ptr.data(), o->ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        std::vector<int4> chunks;
-        std::vector<int32_t> segchunk;
-        build_chunks(ptr, chunks, segchunk, o->maxlen);
-        o->nchunks = (int64_t)chunks.size();
-        CK(dalloc(h, &o->chunks, std::max<size_t>(1, chunks.size()) * sizeof(int4)));
-        CK(dalloc(h, &o->segchunk, segchunk.size() * sizeof(int32_t)));
-        if (!chunks.empty())
-            CK(cudaMemcpy(o->chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(o->segchunk, segchunk.data(), segchunk.size() * sizeof(int32_t),
-                      cudaMemcpyHostToDevice));
-    }
+    if ((rc = chunk_table(C, st)) != GLRM_OK) return rc;
     rc = configure_paths(h);
     if (rc == GLRM_OK) rc = alloc_scratch(h);
     if (rc != GLRM_OK) return rc;
@@ -666,7 +709,7 @@ void pool_release(int dev)
     if (--it->second.second == 0) cudaMemPoolTrimTo(it->second.first, 0);
 }
 
-cudaError_t dalloc_bytes(glrm_s *h, void **p, size_t bytes)
+cudaError_t dalloc_bytes(glrm_s *h, void **p, size_t bytes, cudaStream_t st)
 {
     cudaMemPool_t pool;
     {
@@ -675,7 +718,7 @@ cudaError_t dalloc_bytes(glrm_s *h, void **p, size_t bytes)
         if (it == g_pools.end()) return cudaErrorInitializationError;
         pool = it->second.first;
     }
-    return cudaMallocFromPoolAsync(p, bytes, pool, h->stream);
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
 void tmark(glrm_s *h, const char *name)
@@ -1161,6 +1204,9 @@ void glrm_destroy(glrm_t h)
         dfree(h->alpha_x, h->stream);
         dfree(h->alpha_y, h->stream);
         cudaStreamSynchronize(h->stream);
+        if (h->aux) cudaStreamDestroy(h->aux);
+        if (h->ev_csr) cudaEventDestroy(h->ev_csr);
+        if (h->ev_aux) cudaEventDestroy(h->ev_aux);
         if (h->pooled) pool_release(h->device);
     }
     delete h;

@@ -174,6 +174,10 @@ struct glrm_s {
     int path_x = GLRM_PATH_AUTO, path_y = GLRM_PATH_AUTO;
     std::string err;
     bool pooled = false;  // holds a reference on the device's memory pool
+    // set-up helpers: a non-blocking stream for the CSR checks that overlap the
+    // CSC copies, and an event to hand work between it and `stream`
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_csr = nullptr, ev_aux = nullptr;
 };
 
 namespace glrm {
@@ -184,11 +188,17 @@ size_t elem_size(int prec);
 // handle's stream; freeing is ordered after the work queued before it).
 cudaError_t pool_acquire(int dev);
 void pool_release(int dev);
-cudaError_t dalloc_bytes(glrm_s *h, void **p, size_t bytes);
+cudaError_t dalloc_bytes(glrm_s *h, void **p, size_t bytes, cudaStream_t st);
 template <class P>
 cudaError_t dalloc(glrm_s *h, P **p, size_t bytes)
 {
-    return dalloc_bytes(h, reinterpret_cast<void **>(p), bytes);
+    return dalloc_bytes(h, reinterpret_cast<void **>(p), bytes, h->stream);
+}
+// The same, ordered on another of the handle's streams.
+template <class P>
+cudaError_t dalloc_on(glrm_s *h, P **p, size_t bytes, cudaStream_t st)
+{
+    return dalloc_bytes(h, reinterpret_cast<void **>(p), bytes, st);
 }
 template <class P>
 void dfree(P *&p, cudaStream_t st)
@@ -224,12 +234,13 @@ cudaError_t launch_validate_ptr(const int32_t *ptr, int64_t nseg, int64_t nnz, i
 cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const void *val,
                                 int prec, int64_t nseg, int64_t other, int *flag,
                                 cudaStream_t st);
-cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
-                                  cudaStream_t st);
+cudaError_t launch_digest(const Orient &o, bool rows, int64_t n, int prec, unsigned long long *d,
+                          cudaStream_t st);
+cudaError_t launch_digest_compare(const unsigned long long *d, int *flag, cudaStream_t st);
 cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep);
 cudaError_t launch_perm(const Orient &o, const Orient &other, cudaStream_t st);
-cudaError_t launch_validate_domain(const Orient &csc, int prec, const LossSpec *loss, int *flag,
-                                   cudaStream_t st);
+cudaError_t launch_validate_domain(const Orient &o, bool rows, int64_t n, int prec, const LossSpec *loss,
+                                   int *flag, cudaStream_t st);
 // Dense, fully observed form (tensor cores, FP32 models).
 bool dense_supported(int k);
 void dense_free(glrm_s *h);

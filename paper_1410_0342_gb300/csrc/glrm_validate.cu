@@ -94,19 +94,25 @@ __global__ void digest_compare_kernel(const unsigned long long *__restrict__ d, 
     else if (d[1] != d[3]) atomicOr(flag, 32);
 }
 
-// One warp per column: values inside the column loss's domain (Boolean
-// losses: -1 or +1; ordinal hinge: an integer in 1..d).
+// One warp per segment: values inside their column loss's domain (Boolean
+// losses: -1 or +1; ordinal hinge: an integer in 1..d).  rows: the segments
+// are rows and an entry's column is its index (entries with an index outside
+// 0 .. n - 1 are skipped); else the segments are the n columns.  Non-finite
+// values are skipped too: the index check reports them.
 template <class T>
-__global__ void validate_domain_kernel(const int32_t *__restrict__ colptr, const T *__restrict__ cval,
-                                       int64_t n, const LossSpec *__restrict__ loss, int *flag)
+__global__ void validate_domain_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                       const T *__restrict__ val, int64_t nseg, bool rows, int64_t n,
+                                       const LossSpec *__restrict__ loss, int *flag)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= n) return;
-    const LossSpec sp = loss[j];
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= nseg) return;
     int f = 0;
-    for (int q = colptr[j] + lane; q < colptr[j + 1]; q += 32) {
-        const T a = cval[q];
+    for (int q = ptr[s] + lane; q < ptr[s + 1]; q += 32) {
+        const int64_t j = rows ? (int64_t)idx[q] : s;
+        const T a = val[q];
+        if (j < 0 || j >= n || !finite_val(a)) continue;
+        const LossSpec sp = loss[j];
         if ((sp.kind == kLossHinge || sp.kind == kLossLogistic) && !(a == T(1) || a == T(-1))) f |= 64;
         if (sp.kind == kLossOrdinal && !(a >= T(1) && a <= T(sp.levels) && a == (T)(int)a)) f |= 64;
     }
@@ -116,15 +122,16 @@ __global__ void validate_domain_kernel(const int32_t *__restrict__ colptr, const
 
 }  // namespace
 
-cudaError_t launch_validate_domain(const Orient &csc, int prec, const LossSpec *loss, int *flag,
-                                   cudaStream_t st)
+cudaError_t launch_validate_domain(const Orient &o, bool rows, int64_t n, int prec, const LossSpec *loss,
+                                   int *flag, cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((csc.nseg + 7) / 8);
+    if (o.nseg == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((o.nseg + 7) / 8);
     if (prec == GLRM_FP64)
-        validate_domain_kernel<double><<<nb, 256, 0, st>>>(csc.ptr, (const double *)csc.val, csc.nseg,
+        validate_domain_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, rows, n,
                                                            loss, flag);
     else
-        validate_domain_kernel<float><<<nb, 256, 0, st>>>(csc.ptr, (const float *)csc.val, csc.nseg,
+        validate_domain_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, rows, n,
                                                           loss, flag);
     return cudaGetLastError();
 }
@@ -147,37 +154,25 @@ cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const vo
     return cudaGetLastError();
 }
 
-cudaError_t launch_validate_cross(const Orient &csr, const Orient &csc, int prec, int *flag,
-                                  cudaStream_t st)
+// Digest of one orientation into d[0] (index sum) and d[1] (value sum); d
+// zeroed by the caller.  n: the table's column count.
+cudaError_t launch_digest(const Orient &o, bool rows, int64_t n, int prec, unsigned long long *d, cudaStream_t st)
 {
-    unsigned long long *d = nullptr;
-    cudaError_t e = cudaMallocAsync(&d, 4 * sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), st);
-    const int64_t n = csc.nseg;
-    const unsigned nbr = (unsigned)((csr.nseg + 7) / 8), nbc = (unsigned)((csc.nseg + 7) / 8);
-    if (e == cudaSuccess && csr.nseg > 0) {
-        if (prec == GLRM_FP64)
-            digest_kernel<double><<<nbr, 256, 0, st>>>(csr.ptr, csr.idx, (const double *)csr.val, csr.nseg, n, true, d);
-        else
-            digest_kernel<float><<<nbr, 256, 0, st>>>(csr.ptr, csr.idx, (const float *)csr.val, csr.nseg, n, true, d);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess && csc.nseg > 0) {
-        if (prec == GLRM_FP64)
-            digest_kernel<double><<<nbc, 256, 0, st>>>(csc.ptr, csc.idx, (const double *)csc.val, csc.nseg, n, false,
-                                                       d + 2);
-        else
-            digest_kernel<float><<<nbc, 256, 0, st>>>(csc.ptr, csc.idx, (const float *)csc.val, csc.nseg, n, false,
-                                                      d + 2);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        digest_compare_kernel<<<1, 1, 0, st>>>(d, flag);
-        e = cudaGetLastError();
-    }
-    cudaError_t e2 = cudaFreeAsync(d, st);
-    return e != cudaSuccess ? e : e2;
+    if (o.nseg == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((o.nseg + 7) / 8);
+    if (prec == GLRM_FP64)
+        digest_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, n, rows, d);
+    else
+        digest_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, n, rows, d);
+    return cudaGetLastError();
+}
+
+// Flag 16 when the CSR and CSC index digests (d[0], d[2]) differ, else 32
+// when the value digests (d[1], d[3]) do.
+cudaError_t launch_digest_compare(const unsigned long long *d, int *flag, cudaStream_t st)
+{
+    digest_compare_kernel<<<1, 1, 0, st>>>(d, flag);
+    return cudaGetLastError();
 }
 
 }  // namespace glrm
