@@ -2,6 +2,8 @@
 // pointer arrays, index ranges and ordering, finite values, and that CSR and
 // CSC list the same entries with bit-identical values (64-bit digests).  Each
 // check ORs a bit into a device flag word; nothing traps.
+#include <algorithm>
+
 #include "glrm_handle.h"
 
 namespace glrm {
@@ -25,20 +27,40 @@ __device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
 __device__ __forceinline__ long long bits(float v) { return __float_as_int(v); }
 __device__ __forceinline__ long long bits(double v) { return __double_as_longlong(v); }
 
-// One warp per segment: indices in range, strictly ascending, values finite.
+// The entry checks below run one warp per piece of a segment: segment s is
+// cut into `pieces` equal ranges of its entries (pieces is about the mean
+// segment length / 1024, so a table with few long segments, such as the CSC
+// of a tall table, still spreads over the whole GPU).  Returns false for a
+// warp past the last piece; [b, e) is the warp's range, sb the segment start.
+__device__ __forceinline__ bool piece_range(const int32_t *__restrict__ ptr, int64_t nseg, int pieces, int64_t &s,
+                                            int &sb, int &b, int &e)
+{
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    s = w / pieces;
+    if (s >= nseg) return false;
+    const int64_t pc = w - s * pieces;
+    sb = ptr[s];
+    const int se = ptr[s + 1];
+    const int64_t len = se > sb ? se - sb : 0, per = (len + pieces - 1) / pieces;
+    b = (int)(sb + std::min(len, pc * per));
+    e = (int)(sb + std::min(len, (pc + 1) * per));
+    return true;
+}
+
+// Indices in range, strictly ascending within the segment, values finite.
 template <class T>
 __global__ void validate_idx_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                    const T *__restrict__ val, int64_t nseg, int64_t other, int *flag)
+                                    const T *__restrict__ val, int64_t nseg, int pieces, int64_t other, int *flag)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (s >= nseg) return;
-    const int b = ptr[s], e = ptr[s + 1];
+    int64_t s;
+    int sb, b, e;
+    if (!piece_range(ptr, nseg, pieces, s, sb, b, e)) return;
     int f = 0;
     for (int q = b + lane; q < e; q += 32) {
         const int v = idx[q];
         if (v < 0 || v >= other) f |= 2;
-        if (q > b && idx[q - 1] >= v) f |= 4;
+        if (q > sb && idx[q - 1] >= v) f |= 4;
         if (!finite_val(val[q])) f |= 8;
     }
     for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
@@ -65,14 +87,15 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 // the row; CSC: seg is the column).
 template <class T>
 __global__ void digest_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                              const T *__restrict__ val, int64_t nseg, int64_t n, bool rows,
+                              const T *__restrict__ val, int64_t nseg, int pieces, int64_t n, bool rows,
                               unsigned long long *__restrict__ digest)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (s >= nseg) return;
+    int64_t s;
+    int sb, qb, qe;
+    if (!piece_range(ptr, nseg, pieces, s, sb, qb, qe)) return;
     unsigned long long a = 0, b = 0;
-    for (int q = ptr[s] + lane; q < ptr[s + 1]; q += 32) {
+    for (int q = qb + lane; q < qe; q += 32) {
         const int64_t i = rows ? s : idx[q], j = rows ? idx[q] : s;
         const unsigned long long h = mix64((unsigned long long)(i * n + j));
         a += h;
@@ -101,14 +124,15 @@ __global__ void digest_compare_kernel(const unsigned long long *__restrict__ d, 
 // values are skipped too: the index check reports them.
 template <class T>
 __global__ void validate_domain_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                       const T *__restrict__ val, int64_t nseg, bool rows, int64_t n,
+                                       const T *__restrict__ val, int64_t nseg, int pieces, bool rows, int64_t n,
                                        const LossSpec *__restrict__ loss, int *flag)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (s >= nseg) return;
+    int64_t s;
+    int sb, b, e;
+    if (!piece_range(ptr, nseg, pieces, s, sb, b, e)) return;
     int f = 0;
-    for (int q = ptr[s] + lane; q < ptr[s + 1]; q += 32) {
+    for (int q = b + lane; q < e; q += 32) {
         const int64_t j = rows ? (int64_t)idx[q] : s;
         const T a = val[q];
         if (j < 0 || j >= n || !finite_val(a)) continue;
@@ -120,19 +144,28 @@ __global__ void validate_domain_kernel(const int32_t *__restrict__ ptr, const in
     if (lane == 0 && f) atomicOr(flag, f);
 }
 
+// Pieces per segment and blocks (eight warps each) for nnz entries over nseg segments.
+int seg_pieces(int64_t nnz, int64_t nseg)
+{
+    const int64_t mean = nseg > 0 ? nnz / nseg : 0;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(1024, (mean + 1023) / 1024));
+}
+unsigned piece_blocks(int64_t nseg, int pieces) { return (unsigned)((nseg * pieces + 7) / 8); }
+
 }  // namespace
 
-cudaError_t launch_validate_domain(const Orient &o, bool rows, int64_t n, int prec, const LossSpec *loss,
-                                   int *flag, cudaStream_t st)
+cudaError_t launch_validate_domain(const Orient &o, bool rows, int64_t n, int64_t nnz, int prec,
+                                   const LossSpec *loss, int *flag, cudaStream_t st)
 {
     if (o.nseg == 0) return cudaSuccess;
-    const unsigned nb = (unsigned)((o.nseg + 7) / 8);
+    const int pc = seg_pieces(nnz, o.nseg);
+    const unsigned nb = piece_blocks(o.nseg, pc);
     if (prec == GLRM_FP64)
-        validate_domain_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, rows, n,
-                                                           loss, flag);
+        validate_domain_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, pc, rows,
+                                                           n, loss, flag);
     else
-        validate_domain_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, rows, n,
-                                                          loss, flag);
+        validate_domain_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, pc, rows,
+                                                          n, loss, flag);
     return cudaGetLastError();
 }
 
@@ -144,26 +177,30 @@ cudaError_t launch_validate_ptr(const int32_t *ptr, int64_t nseg, int64_t nnz, i
 }
 
 cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const void *val, int prec,
-                                int64_t nseg, int64_t other, int *flag, cudaStream_t st)
+                                int64_t nseg, int64_t other, int64_t nnz, int *flag, cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((nseg + 7) / 8);
+    if (nseg == 0) return cudaSuccess;
+    const int pc = seg_pieces(nnz, nseg);
+    const unsigned nb = piece_blocks(nseg, pc);
     if (prec == GLRM_FP64)
-        validate_idx_kernel<double><<<nb, 256, 0, st>>>(ptr, idx, (const double *)val, nseg, other, flag);
+        validate_idx_kernel<double><<<nb, 256, 0, st>>>(ptr, idx, (const double *)val, nseg, pc, other, flag);
     else
-        validate_idx_kernel<float><<<nb, 256, 0, st>>>(ptr, idx, (const float *)val, nseg, other, flag);
+        validate_idx_kernel<float><<<nb, 256, 0, st>>>(ptr, idx, (const float *)val, nseg, pc, other, flag);
     return cudaGetLastError();
 }
 
 // Digest of one orientation into d[0] (index sum) and d[1] (value sum); d
 // zeroed by the caller.  n: the table's column count.
-cudaError_t launch_digest(const Orient &o, bool rows, int64_t n, int prec, unsigned long long *d, cudaStream_t st)
+cudaError_t launch_digest(const Orient &o, bool rows, int64_t n, int64_t nnz, int prec, unsigned long long *d,
+                          cudaStream_t st)
 {
     if (o.nseg == 0) return cudaSuccess;
-    const unsigned nb = (unsigned)((o.nseg + 7) / 8);
+    const int pc = seg_pieces(nnz, o.nseg);
+    const unsigned nb = piece_blocks(o.nseg, pc);
     if (prec == GLRM_FP64)
-        digest_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, n, rows, d);
+        digest_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, pc, n, rows, d);
     else
-        digest_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, n, rows, d);
+        digest_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, pc, n, rows, d);
     return cudaGetLastError();
 }
 
