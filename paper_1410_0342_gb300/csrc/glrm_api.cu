@@ -411,28 +411,45 @@ const char *flag_message(int f)
 // sparse path (mixed table, k = 20, measured on GB300).
 constexpr double kDenseAutoDensity = 0.4;
 
-// Set up the kernel paths of an observed set (CSR / CSC and their chunk tables
-// already built): the dense form, or a sparse path per half-step.
-int configure_paths(glrm_s *h)
+// Whether the observed set goes to the dense form: 1 yes, 0 no, else a
+// GLRM error code (a dense request the model cannot take).
+int dense_choice(glrm_s *h)
 {
     const bool force_dense = h->path_x == GLRM_PATH_DENSE || h->path_y == GLRM_PATH_DENSE;
-    bool dense = false;
     if (force_dense) {
-        if (h->path_x != GLRM_PATH_DENSE && h->path_y != GLRM_PATH_DENSE)
-            return fail(h, GLRM_ERR_ARG, "bad path");
         if ((h->path_x != GLRM_PATH_DENSE && h->path_x != GLRM_PATH_AUTO) ||
             (h->path_y != GLRM_PATH_DENSE && h->path_y != GLRM_PATH_AUTO))
             return fail(h, GLRM_ERR_ARG, "the dense path runs both half-steps");
         if (h->prec != GLRM_FP32 || !dense_supported(h->k))
             return fail(h, GLRM_ERR_ARG, "the dense path needs an FP32 model with k <= 64");
-        dense = true;
-    } else if (h->path_x == GLRM_PATH_AUTO && h->path_y == GLRM_PATH_AUTO && h->prec == GLRM_FP32 &&
-               dense_supported(h->k) && (double)h->nnz >= kDenseAutoDensity * (double)h->m * (double)h->n) {
+        return 1;
+    }
+    if (h->path_x == GLRM_PATH_AUTO && h->path_y == GLRM_PATH_AUTO && h->prec == GLRM_FP32 &&
+        dense_supported(h->k) && (double)h->nnz >= kDenseAutoDensity * (double)h->m * (double)h->n) {
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
-        dense = (double)h->m * (double)((h->n + 3) / 4 * 4) * 4.0 <= 0.5 * (double)free_b;
+        return (double)h->m * (double)((h->n + 3) / 4 * 4) * 4.0 <= 0.5 * (double)free_b ? 1 : 0;
     }
+    return 0;
+}
+
+// Set up the kernel paths of an observed set (CSR / CSC and their chunk tables
+// already built): the dense form, or a sparse path per half-step.  preA: the
+// dense table already built from the CSR arrays (pitch (n + 3) / 4 * 4), taken
+// over by the dense form (or freed if the sparse paths are chosen).
+int configure_paths(glrm_s *h, float *preA = nullptr)
+{
+    const int choice = dense_choice(h);
+    if (choice < 0) {
+        if (preA) cudaFreeAsync(preA, h->stream);
+        return choice;
+    }
+    const bool dense = choice == 1;
     dense_free(h);
+    if (preA && !dense) {
+        cudaFreeAsync(preA, h->stream);
+        preA = nullptr;
+    }
     if (!dense) {
         int rc = choose_mode(h, h->csr, true, h->path_x);
         if (rc == GLRM_OK) rc = choose_mode(h, h->csc, false, h->path_y);
@@ -444,8 +461,13 @@ int configure_paths(glrm_s *h)
     if (rc != GLRM_OK) return rc;
     Dense &d = h->dn;
     d.lda = (h->n + 3) / 4 * 4;
-    CK(dalloc(h, &d.A, std::max<size_t>((size_t)h->m * d.lda * sizeof(float), 16)));
-    cudaError_t e = launch_dense_scatter(h);
+    cudaError_t e = cudaSuccess;
+    if (preA) {
+        d.A = preA;
+    } else {
+        CK(dalloc(h, &d.A, std::max<size_t>((size_t)h->m * d.lda * sizeof(float), 16)));
+        e = launch_dense_scatter(h, d.A, d.lda, h->stream);
+    }
     if (e == cudaSuccess) e = dense_prepare(h);
     if (e != cudaSuccess) {
         dense_free(h);
@@ -559,6 +581,18 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (rc == GLRM_OK) rc = check(0, au);
     }
     if (rc == GLRM_OK && hf[0] == 0) rc = chunk_table(R, au);
+    // the dense table needs the CSR arrays only: built here too when it will be chosen
+    float *preA = nullptr;
+    if (rc == GLRM_OK && hf[0] == 0 && dense_choice(h) == 1) {
+        const int64_t lda = (h->n + 3) / 4 * 4;
+        e = dalloc_on(h, &preA, std::max<size_t>((size_t)h->m * lda * sizeof(float), 16), au);
+        if (e == cudaSuccess) e = launch_dense_scatter(h, preA, lda, au);
+        if (e != cudaSuccess) {
+            if (preA) cudaFreeAsync(preA, au);
+            preA = nullptr;
+            rc = cuda_fail(h, e, "dense set-up");
+        }
+    }
     if (rc == GLRM_OK && hf[0] == 0) {
         // the CSC side: on the main stream, after its copies
         e = cudaEventRecord(h->ev_aux, au);
@@ -581,6 +615,11 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     dfree(flag, st);
     dfree(dig, st);
     const int hflag = hf[0] | hf[1];
+    if (preA && (rc != GLRM_OK || hflag)) {
+        cudaStreamSynchronize(au);
+        cudaFreeAsync(preA, st);
+        preA = nullptr;
+    }
     if (rc != GLRM_OK) return rc;
     if (hflag) {
         const int code = (hflag & 8) && !(hflag & ~8) ? GLRM_ERR_NONFINITE : GLRM_ERR_OMEGA;
@@ -589,8 +628,11 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         return fail(h, code, (hflag & 8) && !(hflag & ~8) ? "non-finite value in the observed set"
                                                         : flag_message(hflag));
     }
-    if ((rc = chunk_table(C, st)) != GLRM_OK) return rc;
-    rc = configure_paths(h);
+    if ((rc = chunk_table(C, st)) != GLRM_OK) {
+        if (preA) cudaFreeAsync(preA, st);
+        return rc;
+    }
+    rc = configure_paths(h, preA);
     if (rc == GLRM_OK) rc = alloc_scratch(h);
     if (rc != GLRM_OK) return rc;
     h->have_omega = true;

@@ -734,14 +734,18 @@ static __global__ void dense_validate_kernel(const float *__restrict__ A, int64_
     if (f) atomicOr(flag, f);
 }
 
-// Omega's values (CSR) into a dense table that holds NaN everywhere else.
+// Omega's values (CSR) into a dense table that holds NaN everywhere else:
+// one warp per row writes the row's NaN fill, then its entries.
 static __global__ void dense_scatter_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                                             const float *__restrict__ val, int64_t m, int64_t lda,
                                             float *__restrict__ A)
 {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= m) return;
-    for (int e = rowptr[i] + (threadIdx.x & 31); e < rowptr[i + 1]; e += 32) A[i * lda + colidx[e]] = val[e];
+    float *row = A + i * lda;
+    for (int64_t c = threadIdx.x & 31; c < lda; c += 32) row[c] = __int_as_float(0x7fffffff);
+    __syncwarp();
+    for (int e = rowptr[i] + (threadIdx.x & 31); e < rowptr[i + 1]; e += 32) row[colidx[e]] = val[e];
 }
 
 static __global__ void dense_alpha_kernel(float *__restrict__ alpha, int64_t nseg, float value)
@@ -1199,14 +1203,10 @@ cudaError_t dense_prepare(glrm_s *h)
     return e;
 }
 
-cudaError_t launch_dense_scatter(glrm_s *h)
+cudaError_t launch_dense_scatter(glrm_s *h, float *A, int64_t lda, cudaStream_t st)
 {
-    const Dense &d = h->dn;
-    cudaError_t e = cudaMemsetAsync(d.A, 0xFF, (size_t)h->m * d.lda * sizeof(float), h->stream);  // NaN
-    if (e != cudaSuccess) return e;
-    if (h->nnz == 0) return cudaSuccess;
-    dense_scatter_kernel<<<(unsigned)((h->m + 7) / 8), 256, 0, h->stream>>>(h->csr.ptr, h->csr.idx,
-                                                                          (const float *)h->csr.val, h->m, d.lda, d.A);
+    dense_scatter_kernel<<<(unsigned)((h->m + 7) / 8), 256, 0, st>>>(h->csr.ptr, h->csr.idx,
+                                                                   (const float *)h->csr.val, h->m, lda, A);
     h->launches += 1;
     return cudaGetLastError();
 }

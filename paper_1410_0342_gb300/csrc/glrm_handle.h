@@ -247,7 +247,8 @@ void dense_free(glrm_s *h);
 cudaError_t dense_prepare(glrm_s *h);
 cudaError_t launch_dense_validate(const float *A, int64_t lda, int64_t m, int64_t n, const LossSpec *loss,
                                   int *flag, cudaStream_t st);
-cudaError_t launch_dense_scatter(glrm_s *h);
+// The CSR entries into a dense m x lda table A, NaN at every other cell (on st).
+cudaError_t launch_dense_scatter(glrm_s *h, float *A, int64_t lda, cudaStream_t st);
 cudaError_t dense_reset_steps(glrm_s *h);
 cudaError_t dense_half_step(glrm_s *h, bool xstep);
 cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, double *out);
