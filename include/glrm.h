@@ -134,7 +134,11 @@ int glrm_set_observed(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_dev,
                       const void *csc_val_dev);
 
 /* Same as glrm_set_observed with host pointers: the library copies them to
- * the device on its stream first (pinned host memory makes that faster). */
+ * the device on its stream first (pinned host memory makes that faster).
+ * Both calls copy the CSR arrays first and check them (and build what the
+ * chosen path needs from them) on a second, non-blocking stream the handle
+ * owns while the CSC arrays are still being copied; they return after both
+ * streams are done. */
 int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host,
                            const int32_t *csr_colidx_host, const void *csr_val_host,
                            const int32_t *csc_colptr_host, const int32_t *csc_rowidx_host,
