@@ -264,6 +264,46 @@ def test_observed_set_validation(G, fault):
     assert np.isfinite(g.sweep(1)).all()
 
 
+@pytest.mark.parametrize("fault", [None, "unsorted", "dup", "range", "value", "cross"])
+def test_observed_set_validation_long_columns(G, oracle_mod, fault):
+    """A tall table (20,000 x 6, 90% observed): the CSC's columns hold about
+    18,000 entries each, so its checks and digest split every column into
+    pieces of about 1,024 entries; faults sit on a piece boundary or deep in a
+    column.  The valid table sweeps in step with the oracle."""
+    t = W.small_mixed(m=20000, n=6, k=4, p_obs=0.9, seed=73)
+    g = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry)
+    if fault is None:
+        G.glrm_set_observed(g.h, t.nnz, *_omega_tensors(t))
+        g.set_factors(torch.as_tensor(t.X0, dtype=torch.float32, device="cuda"),
+                      torch.as_tensor(t.Yt0, dtype=torch.float32, device="cuda"))
+        synced_sweeps(g, oracle_mod, t, 2, rtol=1e-5)
+        return
+    a = _omega_tensors(t)
+    j = 2
+    sb, se = int(t.colptr[j]), int(t.colptr[j + 1])
+    pieces = max(1, min(1024, (t.nnz // t.n + 1023) // 1024))
+    per = -(-(se - sb) // pieces)
+    q = sb + per  # first entry of the column's second piece
+    assert pieces > 1 and sb < q - 1 and q + 3 * per < se
+    if fault == "unsorted":
+        a[4][q - 1], a[4][q] = a[4][q].clone(), a[4][q - 1].clone()
+    elif fault == "dup":
+        a[4][q] = a[4][q - 1]
+    elif fault == "range":
+        a[4][q + 3 * per] = t.m
+    elif fault == "value":
+        a[5][q + 2 * per + 5] += 1.0
+    elif fault == "cross":
+        # a row index moved to an unobserved row, order kept: only the digests see it
+        gaps = np.nonzero(np.diff(t.rowidx[sb:se]) >= 2)[0]
+        a[4][sb + int(gaps[len(gaps) // 2])] += 1
+    with pytest.raises(G.GLRMError) as e:
+        G.glrm_set_observed(g.h, t.nnz, *a)
+    assert e.value.code == G.GLRM_ERR_OMEGA
+    G.glrm_set_observed(g.h, t.nnz, *_omega_tensors(t))
+    assert np.isfinite(g.sweep(1)).all()
+
+
 def test_host_entry_points(G, oracle_mod):
     t = W.small_mixed(m=120, n=40, k=5, seed=81)
     g = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry)
