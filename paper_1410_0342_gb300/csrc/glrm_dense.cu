@@ -68,7 +68,7 @@ struct DenseArgs {
     int k;
     const float *F;           // own factor, nown x k
     const __nv_bfloat16 *pk;  // other factor, K-major over k: parts hi, mid, lo (each pack_part)
-    const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid
+    const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid, lo
     int64_t pack_part;        // elements per part
     const LossF *lossf;       // n column losses; w: the kind of the column's 16-column group, else -1
     const DnItem *items;      // one per CTA

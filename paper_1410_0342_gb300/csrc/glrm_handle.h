@@ -94,18 +94,18 @@ struct Scratch {
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
 
-// Dense (fully observed) table and the tensor-core form's buffers.
 // One CTA's work in a dense pass: chunks q0 .. q0 + nq - 1 of the other
-// dimension against own tile `tile` (own rows tile * 128 ..), the tile's
-// part `part` of `parts`.  Row r of the tile keeps its partial results in
-// slot base + r * parts + part.
+// dimension against own tile `tile`, the tile's part `part` of `parts`.  An
+// own row / column s of the tile keeps its partial results in slot
+// segchunk[s] + part; for the X-step's tiles of 128 consecutive rows that is
+// base + (s - 128 tile) * parts + part (base: the tile's first slot).
 struct DnItem {
     int32_t tile, part, parts, q0, nq, pad;
     int64_t base;
 };
 
-// The work items of one pass in launch order, per tile {first slot, parts},
-// and the number of partial slots.
+// The work items of one pass in launch order, per tile {first slot, parts}
+// (first slot: X-step tiles only), and the number of partial slots.
 struct ItemPlan {
     std::vector<DnItem> items;
     std::vector<int64_t> tiles;
@@ -119,17 +119,18 @@ struct DensePlan {
     std::vector<int32_t> seg_y;     // column -> first partial slot (n + 1 entries)
 };
 
+// Dense (fully observed) table and the tensor-core form's buffers.
 struct Dense {
     bool on = false;
     bool missing = false;  // A holds NaN at cells outside Omega (a sparse table stored densely)
-    float *A = nullptr;    // m x lda, lda = n rounded up to 4, padding zero
+    float *A = nullptr;    // m x lda, lda = n rounded up to 4 (padding columns are never read)
     int64_t lda = 0;
     int KP = 0;  // k padded to a multiple of 16
     DnItem *items_x = nullptr, *items_y = nullptr;  // per-CTA work items of the X- and Y-step passes
     int32_t *blocks_y = nullptr;                    // per Y-step tile its four 32-column blocks
     int64_t nitems_x = 0, nitems_y = 0;
     __nv_bfloat16 *pk = nullptr;  // packed other factor, K-major over k (parts hi, mid, lo)
-    __nv_bfloat16 *pt = nullptr;  // packed other factor, K-major over chunk rows (parts hi, mid)
+    __nv_bfloat16 *pt = nullptr;  // packed other factor, K-major over chunk rows (parts hi, mid, lo)
     int64_t pack_part = 0;        // elements per part
     int32_t *segchunk_x = nullptr, *segchunk_y = nullptr;  // segment -> first partial slot
     int64_t slots_x = 0, slots_y = 0, slots = 0;           // partial slots per half-step, the larger
