@@ -574,9 +574,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_ptr");
     if (rc == GLRM_OK) rc = check(0, au);
     if (rc == GLRM_OK && hf[0] == 0) {
-        e = launch_validate_idx(R.ptr, R.idx, R.val, h->prec, h->m, h->n, nnz, flag, au);
-        if (e == cudaSuccess) e = launch_validate_domain(R, true, h->n, nnz, h->prec, h->loss_dev, flag, au);
-        if (e == cudaSuccess) e = launch_digest(R, true, h->n, nnz, h->prec, dig, au);
+        e = launch_check_entries(R, true, h->n, h->n, nnz, h->prec, h->loss_dev, flag, dig, au);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
         if (rc == GLRM_OK) rc = check(0, au);
     }
@@ -601,8 +599,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_ptr");
         if (rc == GLRM_OK) rc = check(1, st);
         if (rc == GLRM_OK && hf[1] == 0) {
-            e = launch_validate_idx(C.ptr, C.idx, C.val, h->prec, h->n, h->m, nnz, flag + 1, st);
-            if (e == cudaSuccess) e = launch_digest(C, false, h->n, nnz, h->prec, dig + 2, st);
+            e = launch_check_entries(C, false, h->m, h->n, nnz, h->prec, nullptr, flag + 1, dig + 2, st);
             if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
             if (rc == GLRM_OK) rc = check(1, st);
         }

@@ -232,16 +232,14 @@ struct Engine {
 // Validation of one orientation, writes bit flags into *flag (device int).
 cudaError_t launch_validate_ptr(const int32_t *ptr, int64_t nseg, int64_t nnz, int *flag,
                                 cudaStream_t st);
-cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const void *val,
-                                int prec, int64_t nseg, int64_t other, int64_t nnz, int *flag,
-                                cudaStream_t st);
-cudaError_t launch_digest(const Orient &o, bool rows, int64_t n, int64_t nnz, int prec, unsigned long long *d,
-                          cudaStream_t st);
+// Entry checks of one orientation in one pass (index range and order, finite
+// values; loss domains when `loss` is given; the digests into digest[0..1]
+// when `digest` is given).  rows: CSR; other: the index bound; n: columns.
+cudaError_t launch_check_entries(const Orient &o, bool rows, int64_t other, int64_t n, int64_t nnz, int prec,
+                                 const LossSpec *loss, int *flag, unsigned long long *digest, cudaStream_t st);
 cudaError_t launch_digest_compare(const unsigned long long *d, int *flag, cudaStream_t st);
 cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep);
 cudaError_t launch_perm(const Orient &o, const Orient &other, cudaStream_t st);
-cudaError_t launch_validate_domain(const Orient &o, bool rows, int64_t n, int64_t nnz, int prec,
-                                   const LossSpec *loss, int *flag, cudaStream_t st);
 // Dense, fully observed form (tensor cores, FP32 models).
 bool dense_supported(int k);
 void dense_free(glrm_s *h);

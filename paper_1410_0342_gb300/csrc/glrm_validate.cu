@@ -47,26 +47,6 @@ __device__ __forceinline__ bool piece_range(const int32_t *__restrict__ ptr, int
     return true;
 }
 
-// Indices in range, strictly ascending within the segment, values finite.
-template <class T>
-__global__ void validate_idx_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                    const T *__restrict__ val, int64_t nseg, int pieces, int64_t other, int *flag)
-{
-    const int lane = threadIdx.x & 31;
-    int64_t s;
-    int sb, b, e;
-    if (!piece_range(ptr, nseg, pieces, s, sb, b, e)) return;
-    int f = 0;
-    for (int q = b + lane; q < e; q += 32) {
-        const int v = idx[q];
-        if (v < 0 || v >= other) f |= 2;
-        if (q > sb && idx[q - 1] >= v) f |= 4;
-        if (!finite_val(val[q])) f |= 8;
-    }
-    for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0 && f) atomicOr(flag, f);
-}
-
 // The CSR / CSC agreement check compares two order-free digests of each
 // orientation's entries: the sum (mod 2^64) of H(i n + j) over its entries,
 // and the sum of H(H(i n + j) ^ value bits), H being the splitmix64 finaliser
@@ -74,7 +54,7 @@ __global__ void validate_idx_kernel(const int32_t *__restrict__ ptr, const int32
 // Both orientations already passed the per-segment checks (counts, ranges,
 // strict order, so no duplicates); equal index digests then mean the same
 // entries and equal value digests the same values, except with probability
-// about 2^-64 for a given mismatch.  One warp per segment, a grid-wide sum.
+// about 2^-64 for a given mismatch.  One warp per segment piece, a grid-wide sum.
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
     z += 0x9E3779B97F4A7C15ull;
@@ -83,65 +63,63 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
     return z ^ (z >> 31);
 }
 
-// digest[0], digest[1]: index and value sums of this orientation (CSR: seg is
-// the row; CSC: seg is the column).
-template <class T>
-__global__ void digest_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                              const T *__restrict__ val, int64_t nseg, int pieces, int64_t n, bool rows,
-                              unsigned long long *__restrict__ digest)
-{
-    const int lane = threadIdx.x & 31;
-    int64_t s;
-    int sb, qb, qe;
-    if (!piece_range(ptr, nseg, pieces, s, sb, qb, qe)) return;
-    unsigned long long a = 0, b = 0;
-    for (int q = qb + lane; q < qe; q += 32) {
-        const int64_t i = rows ? s : idx[q], j = rows ? idx[q] : s;
-        const unsigned long long h = mix64((unsigned long long)(i * n + j));
-        a += h;
-        b += mix64(h ^ (unsigned long long)bits(val[q]));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&digest[0], a);
-        atomicAdd(&digest[1], b);
-    }
-}
-
 __global__ void digest_compare_kernel(const unsigned long long *__restrict__ d, int *flag)
 {
     if (d[0] != d[2]) atomicOr(flag, 16);
     else if (d[1] != d[3]) atomicOr(flag, 32);
 }
 
-// One warp per segment: values inside their column loss's domain (Boolean
-// losses: -1 or +1; ordinal hinge: an integer in 1..d).  rows: the segments
-// are rows and an entry's column is its index (entries with an index outside
-// 0 .. n - 1 are skipped); else the segments are the n columns.  Non-finite
-// values are skipped too: the index check reports them.
+// One pass over the entries of a segment piece: indices in range and
+// strictly ascending within the segment, values finite (flags 2, 4, 8); with
+// `loss`, each value inside its column loss's domain (Boolean losses: -1 or
+// +1; ordinal hinge: an integer in 1..d; flag 64; entries whose index or
+// value already failed are skipped); with `digest`, the orientation's two
+// digests added into digest[0], digest[1].  rows: the segments are rows and
+// an entry's index its column; else the segments are columns.  n: the
+// table's column count; other: the index bound.
 template <class T>
-__global__ void validate_domain_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                       const T *__restrict__ val, int64_t nseg, int pieces, bool rows, int64_t n,
-                                       const LossSpec *__restrict__ loss, int *flag)
+__global__ void check_entries_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                     const T *__restrict__ val, int64_t nseg, int pieces, int64_t other, bool rows,
+                                     int64_t n, const LossSpec *__restrict__ loss, int *flag,
+                                     unsigned long long *__restrict__ digest)
 {
     const int lane = threadIdx.x & 31;
     int64_t s;
-    int sb, b, e;
-    if (!piece_range(ptr, nseg, pieces, s, sb, b, e)) return;
+    int sb, qb, qe;
+    if (!piece_range(ptr, nseg, pieces, s, sb, qb, qe)) return;
     int f = 0;
-    for (int q = b + lane; q < e; q += 32) {
-        const int64_t j = rows ? (int64_t)idx[q] : s;
+    unsigned long long da = 0, dv = 0;
+    for (int q = qb + lane; q < qe; q += 32) {
+        const int v = idx[q];
         const T a = val[q];
-        if (j < 0 || j >= n || !finite_val(a)) continue;
-        const LossSpec sp = loss[j];
-        if ((sp.kind == kLossHinge || sp.kind == kLossLogistic) && !(a == T(1) || a == T(-1))) f |= 64;
-        if (sp.kind == kLossOrdinal && !(a >= T(1) && a <= T(sp.levels) && a == (T)(int)a)) f |= 64;
+        const bool in_range = v >= 0 && v < other, fin = finite_val(a);
+        if (!in_range) f |= 2;
+        if (q > sb && idx[q - 1] >= v) f |= 4;
+        if (!fin) f |= 8;
+        if (loss && in_range && fin) {
+            const LossSpec sp = loss[rows ? (int64_t)v : s];
+            if ((sp.kind == kLossHinge || sp.kind == kLossLogistic) && !(a == T(1) || a == T(-1))) f |= 64;
+            if (sp.kind == kLossOrdinal && !(a >= T(1) && a <= T(sp.levels) && a == (T)(int)a)) f |= 64;
+        }
+        if (digest) {
+            const int64_t i = rows ? s : (int64_t)v, j = rows ? (int64_t)v : s;
+            const unsigned long long h = mix64((unsigned long long)(i * n + j));
+            da += h;
+            dv += mix64(h ^ (unsigned long long)bits(a));
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
-    if (lane == 0 && f) atomicOr(flag, f);
+    for (int o = 16; o > 0; o >>= 1) {
+        f |= __shfl_xor_sync(0xffffffffu, f, o);
+        da += __shfl_xor_sync(0xffffffffu, da, o);
+        dv += __shfl_xor_sync(0xffffffffu, dv, o);
+    }
+    if (lane == 0) {
+        if (f) atomicOr(flag, f);
+        if (digest) {
+            atomicAdd(&digest[0], da);
+            atomicAdd(&digest[1], dv);
+        }
+    }
 }
 
 // Pieces per segment and blocks (eight warps each) for nnz entries over nseg segments.
@@ -154,21 +132,6 @@ unsigned piece_blocks(int64_t nseg, int pieces) { return (unsigned)((nseg * piec
 
 }  // namespace
 
-cudaError_t launch_validate_domain(const Orient &o, bool rows, int64_t n, int64_t nnz, int prec,
-                                   const LossSpec *loss, int *flag, cudaStream_t st)
-{
-    if (o.nseg == 0) return cudaSuccess;
-    const int pc = seg_pieces(nnz, o.nseg);
-    const unsigned nb = piece_blocks(o.nseg, pc);
-    if (prec == GLRM_FP64)
-        validate_domain_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, pc, rows,
-                                                           n, loss, flag);
-    else
-        validate_domain_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, pc, rows,
-                                                          n, loss, flag);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_validate_ptr(const int32_t *ptr, int64_t nseg, int64_t nnz, int *flag,
                                 cudaStream_t st)
 {
@@ -176,31 +139,18 @@ cudaError_t launch_validate_ptr(const int32_t *ptr, int64_t nseg, int64_t nnz, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_validate_idx(const int32_t *ptr, const int32_t *idx, const void *val, int prec,
-                                int64_t nseg, int64_t other, int64_t nnz, int *flag, cudaStream_t st)
-{
-    if (nseg == 0) return cudaSuccess;
-    const int pc = seg_pieces(nnz, nseg);
-    const unsigned nb = piece_blocks(nseg, pc);
-    if (prec == GLRM_FP64)
-        validate_idx_kernel<double><<<nb, 256, 0, st>>>(ptr, idx, (const double *)val, nseg, pc, other, flag);
-    else
-        validate_idx_kernel<float><<<nb, 256, 0, st>>>(ptr, idx, (const float *)val, nseg, pc, other, flag);
-    return cudaGetLastError();
-}
-
-// Digest of one orientation into d[0] (index sum) and d[1] (value sum); d
-// zeroed by the caller.  n: the table's column count.
-cudaError_t launch_digest(const Orient &o, bool rows, int64_t n, int64_t nnz, int prec, unsigned long long *d,
-                          cudaStream_t st)
+cudaError_t launch_check_entries(const Orient &o, bool rows, int64_t other, int64_t n, int64_t nnz, int prec,
+                                 const LossSpec *loss, int *flag, unsigned long long *digest, cudaStream_t st)
 {
     if (o.nseg == 0) return cudaSuccess;
     const int pc = seg_pieces(nnz, o.nseg);
     const unsigned nb = piece_blocks(o.nseg, pc);
     if (prec == GLRM_FP64)
-        digest_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, pc, n, rows, d);
+        check_entries_kernel<double><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const double *)o.val, o.nseg, pc, other,
+                                                         rows, n, loss, flag, digest);
     else
-        digest_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, pc, n, rows, d);
+        check_entries_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, pc, other,
+                                                        rows, n, loss, flag, digest);
     return cudaGetLastError();
 }
 
