@@ -19,7 +19,10 @@ Parity status of each function (the pins live in tests/test_oracle_*.py):
   objective / gradient                 pinned (brute-force loops, finite
                                        differences)
   proxgrad                             pinned (qPCA closed form, Eckart-Young,
-                                       monotone objective, single-row brute force)
+                                       monotone objective, single-row brute force,
+                                       one 2 x 2 sweep followed by hand: Gauss-Seidel
+                                       order and both step-rule branches; empty
+                                       row / column: alpha = 1, x <- prox(x))
   als                                  pinned (normal equations vs numpy.linalg,
                                        qPCA closed form)
 """

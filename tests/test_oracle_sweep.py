@@ -211,3 +211,66 @@ def test_als_reaches_qpca_closed_form(oracle_mod):
     X, Yt, hist = p.als(t.X0, t.Yt0, 0.1, 5000)
     assert np.all(np.diff(hist) <= 1e-10 * np.abs(hist[1:]))
     assert (hist[-1] - fstar) / fstar < 1e-9
+
+
+def test_proxgrad_one_sweep_by_hand(oracle_mod):
+    """One full sweep (Algorithm 2, Sec. 7.2) of a 2 x 2 table with cell (1, 1)
+    missing, k = 1, quadratic loss (u - a)^2, no regularisers, followed by hand
+    in exact dyadic arithmetic.  Steps start at alpha = 1/n_i: 1/2 and 1 for
+    the rows, 1/2 and 1 for the columns.
+
+    X-step against y = (-1/2, 3/2):
+      row 0 (a = 1/2, 1/4): u = (5/8, -15/8), g = 2 (1/8 (-1/2) - 17/8 (3/2))
+        = -13/2, x+ = -5/4 + 13/4 = 2; f_old = 290/64 < f_new = 628/64:
+        rejected, x stays -5/4, alpha = 1/2 * 0.7.
+      row 1 (a = -1): u = 7/8, g = 2 (15/8)(-1/2) = -15/8, x+ = 1/8;
+        f_new = 225/256 <= f_old = 225/64: accepted, alpha = 1.05.
+    Y-step against the NEW x = (-5/4, 1/8) (Gauss-Seidel):
+      column 0 (a = 1/2, -1): u = (5/8, -1/16), g = 2 (1/8 (-5/4) + 15/16 (1/8))
+        = -5/64, y+ = -1/2 + 5/128 = -59/128; f_new = 937309/2^20 <=
+        f_old = 937984/2^20: accepted, alpha = 1/2 * 1.05.
+      column 1 (a = 1/4): u = -15/8, g = 85/16, y+ = -61/16; f_new =
+        83521/4096 > f_old = 289/64: rejected, alpha = 0.7.
+    A Jacobi sweep (Y-step against the old x = (-5/4, -7/4)) would reject
+    column 0 and keep y_0 = -1/2, so this pins the order of the half-steps
+    as well as both branches of the step-size rule."""
+    o = oracle_mod
+    rows = np.array([0, 0, 1], np.int32)
+    cols = np.array([0, 1, 0], np.int32)
+    vals = np.array([0.5, 0.25, -1.0])
+    p = o.Problem(2, 2, 1, rows, cols, vals, Q, 0.0, 0, rx=(RZ, 0.0), ry=(RZ, 0.0))
+    X0 = np.array([[-1.25], [-1.75]])
+    Yt0 = np.array([[-0.5], [1.5]])
+    ax0, ay0 = p.initial_alphas()
+    np.testing.assert_array_equal(ax0, [0.5, 1.0])
+    np.testing.assert_array_equal(ay0, [0.5, 1.0])
+    X1, Yt1, ax, ay, hist, acc = p.proxgrad(X0, Yt0, 1)
+    np.testing.assert_array_equal(X1[:, 0], [-1.25, 0.125])
+    np.testing.assert_array_equal(Yt1[:, 0], [-59.0 / 128.0, 1.5])
+    np.testing.assert_allclose(ax, [0.5 * 0.7, 1.05], rtol=1e-15)
+    np.testing.assert_allclose(ay, [0.5 * 1.05, 0.7], rtol=1e-15)
+    assert tuple(acc[0]) == (1, 1)
+    # objective of eq. gpca at the new factors: column 0's two terms + column 1's
+    assert hist[0] == 937309.0 / 2**20 + (-1.25 * 1.5 - 0.25) ** 2
+
+
+def test_proxgrad_empty_row_and_column(oracle_mod):
+    """A row and a column with no observed entries (Sec. 7.2 with n_i = 0):
+    their step starts at alpha = 1 / max(0, 1) = 1, the gradient is zero, so
+    the update is x <- prox_{alpha r}(x): soft thresholding at alpha lambda for
+    l1 on X, shrinkage by 1 / (1 + 2 alpha gamma) for gamma ||y||^2 on Y.  Both
+    lower r, so both are accepted and alpha becomes 1.05."""
+    o = oracle_mod
+    lam, gam = 0.5, 0.25
+    # 2 x 2 with row 1 and column 1 empty: the only entry is (0, 0)
+    p = o.Problem(2, 2, 3, np.array([0], np.int32), np.array([0], np.int32), np.array([0.3]),
+                  Q, 0.0, 0, rx=(RL1, lam), ry=(RQ, gam))
+    ax0, ay0 = p.initial_alphas()
+    np.testing.assert_array_equal(ax0, [1.0, 1.0])
+    np.testing.assert_array_equal(ay0, [1.0, 1.0])
+    X0 = np.array([[0.2, -0.1, 0.4], [0.75, -0.25, 0.1]])
+    Yt0 = np.array([[0.3, 0.6, -0.2], [1.0, -2.0, 0.5]])
+    X1, Yt1, ax, ay, hist, acc = p.proxgrad(X0, Yt0, 1)
+    np.testing.assert_array_equal(X1[1], [0.25, 0.0, 0.0])  # soft threshold at 1 * 0.5
+    np.testing.assert_array_equal(Yt1[1], Yt0[1] / (1.0 + 2.0 * gam))
+    assert ax[1] == 1.05 and ay[1] == 1.05
