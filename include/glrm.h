@@ -191,6 +191,26 @@ int glrm_reset_steps(glrm_t h);
  * synchronises.  With history_host NULL the call returns once enqueued. */
 int glrm_sweep(glrm_t h, int32_t nsweeps, double *history_host);
 
+/* Sweeps until a convergence test on the device passes (Section 7.2; the
+ * objective of eq. gpca never increases under the step-size rule, so its
+ * decrease is the natural stopping signal).  After every sweep the FP64
+ * objective F_t is compared on the GPU:
+ *   f_ref is NaN:  stop when F_{t-1} - F_t <= rtol |F_t|  (relative decrease;
+ *                  F_0 is the objective before the first sweep)
+ *   otherwise:     stop when F_t - f_ref <= rtol |f_ref|   (within rtol of a
+ *                  reference objective, e.g. a known optimum)
+ * or after max_sweeps sweeps (>= 1).  rtol >= 0.  FP32 and FP64 models run
+ * the whole loop as one launch of a CUDA graph whose conditional WHILE node
+ * repeats a captured sweep and its check (captured on the first call and
+ * kept until the buffers or kernel paths change); the BF16 form, which keeps
+ * host-side state between sweeps, reads the device's decision back after
+ * each sweep.  *sweeps_host receives the number of sweeps run; history_host,
+ * if not NULL, receives their objectives (max_sweeps doubles of room).  Each
+ * sweep is exactly the sweep of glrm_sweep, so the results equal those of
+ * glrm_sweep(h, *sweeps_host, ...).  Synchronises. */
+int glrm_sweep_until(glrm_t h, int32_t max_sweeps, double rtol, double f_ref,
+                     int32_t *sweeps_host, double *history_host);
+
 /* Accepted row and column steps of the last sweep run (host, 2 values);
  * synchronises. */
 int glrm_last_accepts(glrm_t h, int64_t *accepts_host);
@@ -217,6 +237,15 @@ int glrm_objective_at(glrm_t h, const void *X_dev, const void *Yt_dev, double *o
  * synchronise.  This is the backward of the differentiable form. */
 int glrm_grad_at(glrm_t h, const void *X_dev, const void *Yt_dev, void *GX_dev,
                  void *GYt_dev, int32_t include_reg, const double *scale_dev);
+
+/* Loss part of the gradient at the model's own factors (Section 7.2,
+ * "Gradient method"): GX_dev[i] = sum_{j in Omega_i} L_j'(x_i . y_j, A_ij) y_j
+ * (m x k) and GYt_dev[j] = sum_{i in Omega_j} L_j'(x_i . y_j, A_ij) x_i
+ * (n x k), element type of the model, caller-owned device buffers.  The
+ * regulariser's gradient is not added (the caller adds it where it exists).
+ * Equivalent to glrm_grad_at(h, X, Yt, GX_dev, GYt_dev, 0, NULL) with the
+ * handle's factors; does not synchronise. */
+int glrm_grad(glrm_t h, void *GX_dev, void *GYt_dev);
 
 /* Imputation (Section 5.3): for the cnt pairs (rows_dev[e], cols_dev[e])
  * write u = x_i . y_j (decode == 0) or the decoded value argmin_a L_j(u, a)
@@ -361,6 +390,17 @@ void glrm_batch_destroy(glrm_batch_t b);
 int glrm_tc_gemm_bf16(const void *A_dev, const void *B_dev, float *D_dev, int32_t M, int32_t N,
                       int32_t K, void *stream);
 
+/* Self-test of the device-side wait limit (not part of the method): one
+ * thread waits, with the library's bounded mbarrier wait and a limit of
+ * `attempts` try_wait attempts, on a barrier phase that completes only when
+ * arm != 0 (the thread arrives on it first).  Returns GLRM_OK when the wait
+ * completed and GLRM_ERR_TIMEOUT when it ran out (arm == 0): the same path a
+ * staged copy or a tensor-core completion that never lands takes in the
+ * sweep kernels, exercised without any copy or MMA in flight.  The GPU and the
+ * CUDA context stay usable either way.  Synchronises.  GLRM_ERR_ARG if
+ * attempts < 1. */
+int glrm_wait_selftest(int64_t attempts, int32_t arm, void *stream);
+
 /* Instrumentation (not part of the method).  glrm_timing_enable(h, 1)
  * records a CUDA event on the handle's stream before every kernel the handle
  * launches and after the last one, so each kernel's device time is measured
@@ -383,26 +423,33 @@ int glrm_launch_count(glrm_t h, int64_t *count_host);
  * (FP32 model, per-row loss sums plus regularisers, reduced in FP64), for
  * caller-owned data and without a handle.
  *
- * Inputs (device pointers, caller-owned): CSR rowptr (m+1), colidx, val (FP32)
- * of Omega; col_loss_dev: n glrm_loss descriptors in device memory, 16-byte
- * aligned; factors X_dev (m x k) and Yt_dev (n x k), FP32 row-major.  Output:
- * the objective in the device double out_dev.  Work is enqueued on `stream`
- * (a cudaStream_t, NULL = legacy default stream); the call does not
- * synchronise.  A column index outside [0, n) turns the result into NaN.
+ * Inputs (device pointers, caller-owned): CSR rowptr (m+1), colidx and val
+ * (nnz each, FP32) of Omega; col_loss_dev: n glrm_loss descriptors in device
+ * memory, 16-byte aligned; factors X_dev (m x k) and Yt_dev (n x k), FP32
+ * row-major.  Output: the objective in the device double out_dev.  Work is
+ * enqueued on `stream` (a cudaStream_t, NULL = legacy default stream); the
+ * call does not synchronise.  The device data is not validated the way
+ * glrm_set_observed validates it (no order or duplicate checks, no value
+ * domains); what would make a read go out of range or a loss undefined turns
+ * the result into NaN instead: a row range outside [0, nnz] or running
+ * backwards, a column index outside [0, n), a loss descriptor with an
+ * unknown kind, a Huber threshold that is not positive and finite, or fewer
+ * than two ordinal levels.  Regulariser kinds and weights (finite, >= 0) are
+ * checked on the host (GLRM_ERR_ARG).
  *
  * Scratch: a file-scope device array of GLRM_NOALLOC_MAX_TERMS doubles
  * (8 MiB) inside the library, held by every GPU that loads the library until
- * the process exits; m + n must not exceed GLRM_NOALLOC_MAX_TERMS
- * (GLRM_ERR_RANGE otherwise, nothing launched).  The first call on a device
+ * the process exits; m + n must not exceed GLRM_NOALLOC_MAX_TERMS and nnz
+ * must be below 2^31 (GLRM_ERR_RANGE otherwise, nothing launched).  The first call on a device
  * looks up the array's device address on that device, so make that first call
  * outside any stream capture.  Every call overwrites the slots it uses; calls
  * that overlap on the GPU share the array and race.  Limits: 1 <= k <= 64. */
 #define GLRM_NOALLOC_MAX_TERMS (1 << 20)
-int glrm_objective_noalloc(int64_t m, int64_t n, int32_t k, const int32_t *csr_rowptr_dev,
-                           const int32_t *csr_colidx_dev, const float *csr_val_dev,
-                           const glrm_loss *col_loss_dev, int32_t rx_kind, double rx_weight,
-                           int32_t ry_kind, double ry_weight, const float *X_dev,
-                           const float *Yt_dev, double *out_dev, void *stream);
+int glrm_objective_noalloc(int64_t m, int64_t n, int32_t k, int64_t nnz,
+                           const int32_t *csr_rowptr_dev, const int32_t *csr_colidx_dev,
+                           const float *csr_val_dev, const glrm_loss *col_loss_dev,
+                           int32_t rx_kind, double rx_weight, int32_t ry_kind, double ry_weight,
+                           const float *X_dev, const float *Yt_dev, double *out_dev, void *stream);
 
 /* Per-handle message for the last error (empty string when none). */
 const char *glrm_last_error(glrm_t h);

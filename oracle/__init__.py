@@ -18,6 +18,10 @@ Parity status of each function (the pins live in tests/test_oracle_*.py):
                                        finite differences, Huber identity)
   objective / gradient                 pinned (brute-force loops, finite
                                        differences)
+  gradient_abs                         pinned (brute-force loops; equals the
+                                       gradient where every term is >= 0)
+  gradient_variation                   pinned (closed form for quadratic loss,
+                                       the hinge's unit jump at its kink)
   proxgrad                             pinned (qPCA closed form, Eckart-Young,
                                        monotone objective, single-row brute force,
                                        one 2 x 2 sweep followed by hand: Gauss-Seidel
@@ -80,6 +84,11 @@ def _load():
                                          i32, d, i32, d, p, p, i32]
         lib.oracle_gradient.restype = i32
         lib.oracle_gradient.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, p, p, i32]
+        lib.oracle_gradient_abs.restype = i32
+        lib.oracle_gradient_abs.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, p, p, i32]
+        lib.oracle_gradient_variation.restype = i32
+        lib.oracle_gradient_variation.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, d, p,
+                                                  p, i32]
         lib.oracle_proxgrad.restype = i32
         lib.oracle_proxgrad.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, i32, d, i32, d,
                                         p, p, p, p, i32, p, p, i32]
@@ -192,6 +201,36 @@ class Problem:
         if rc:
             raise ValueError(f"oracle_gradient failed ({rc})")
         return GX, GYt
+
+    def gradient_abs(self, X, Yt, nthreads: int = 0):
+        """Per gradient coordinate, the sum of the magnitudes of its terms:
+        sum_{j in Omega_i} |L'| |y_j| and sum_{i in Omega_j} |L'| |x_i| (the
+        scale of the rounding error of any summation of the gradient)."""
+        X = _c(X, np.float64)
+        Yt = _c(Yt, np.float64)
+        SX = np.empty_like(X)
+        SYt = np.empty_like(Yt)
+        rc = _load().oracle_gradient_abs(*self._common(), *self._losses(), _ptr(X), _ptr(Yt),
+                                         _ptr(SX), _ptr(SYt), nthreads)
+        if rc:
+            raise ValueError(f"oracle_gradient_abs failed ({rc})")
+        return SX, SYt
+
+    def gradient_variation(self, X, Yt, u_rel: float, nthreads: int = 0):
+        """Per gradient coordinate, how far it can move when every product
+        x_i . y_j is off by at most u_rel * sum_c |x_ic y_jc|: sum over the
+        coordinate's entries of (L'(u + delta) - L'(u - delta)) |w| (L' is
+        nondecreasing for the convex losses here)."""
+        X = _c(X, np.float64)
+        Yt = _c(Yt, np.float64)
+        VX = np.empty_like(X)
+        VYt = np.empty_like(Yt)
+        rc = _load().oracle_gradient_variation(*self._common(), *self._losses(), _ptr(X),
+                                               _ptr(Yt), float(u_rel), _ptr(VX), _ptr(VYt),
+                                               nthreads)
+        if rc:
+            raise ValueError(f"oracle_gradient_variation failed ({rc})")
+        return VX, VYt
 
     def proxgrad(self, X, Yt, nsweeps: int, alpha_x=None, alpha_y=None, nthreads: int = 0):
         """Alternating proximal-gradient sweeps with the step-size safeguard

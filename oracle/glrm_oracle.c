@@ -404,6 +404,103 @@ int oracle_gradient(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row
     return 0;
 }
 
+/* Magnitude of the terms of each gradient coordinate (the scale of the
+ * rounding error of any summation of them):
+ *   SX[i] = sum_{j in Omega_i} |L'_j(x_i . y_j, A_ij)| |y_j|   (elementwise)
+ *   SYt[j] = sum_{i in Omega_j} |L'_j(x_i . y_j, A_ij)| |x_i|
+ * Same loops as oracle_gradient with absolute values. */
+int oracle_gradient_abs(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
+                        const int32_t *col, const double *val, const int32_t *lkind,
+                        const double *lparam, const int32_t *llevels, const double *X,
+                        const double *Yt, double *SX, double *SYt, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    int rc = lists_build(&L, m, n, nnz, row, col, val);
+    if (rc) { lists_free(&L); return rc; }
+    set_threads(nthreads);
+    int64_t i, j;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (i = 0; i < m; ++i) {
+        double *g = SX + i * k;
+        for (int c = 0; c < k; ++c) g[c] = 0.0;
+        for (int64_t e = L.rstart[i]; e < L.rstart[i + 1]; ++e) {
+            int32_t jj = L.rcol[e];
+            double u = dot(k, X + i * k, Yt + (int64_t)jj * k);
+            double r = fabs(oracle_dloss(lkind[jj], lparam[jj], llevels[jj], u, L.rval[e]));
+            for (int c = 0; c < k; ++c) g[c] += r * fabs(Yt[(int64_t)jj * k + c]);
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (j = 0; j < n; ++j) {
+        double *h = SYt + j * k;
+        for (int c = 0; c < k; ++c) h[c] = 0.0;
+        for (int64_t e = L.cstart[j]; e < L.cstart[j + 1]; ++e) {
+            int32_t ii = L.crow[e];
+            double u = dot(k, X + (int64_t)ii * k, Yt + j * k);
+            double r = fabs(oracle_dloss(lkind[j], lparam[j], llevels[j], u, L.cval[e]));
+            for (int c = 0; c < k; ++c) h[c] += r * fabs(X[(int64_t)ii * k + c]);
+        }
+    }
+    lists_free(&L);
+    return 0;
+}
+
+/* How far each gradient coordinate can move when every product u = x_i . y_j
+ * is perturbed by at most delta = u_rel * sum_c |x_ic y_jc| (the rounding
+ * bound of a low-precision dot product):
+ *   VX[i] = sum_{j in Omega_i} (L'_j(u + delta) - L'_j(u - delta)) |y_j|
+ *   VYt[j] = sum_{i in Omega_j} (L'_j(u + delta) - L'_j(u - delta)) |x_i|
+ * Every loss here is convex, so L' is nondecreasing and the difference is
+ * the variation of L' over [u - delta, u + delta]: the jump of the
+ * subgradient when a kink lies in that interval (hinge, ordinal hinge), about
+ * 2 delta L'' for smooth losses. */
+int oracle_gradient_variation(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
+                              const int32_t *col, const double *val, const int32_t *lkind,
+                              const double *lparam, const int32_t *llevels, const double *X,
+                              const double *Yt, double u_rel, double *VX, double *VYt,
+                              int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    int rc = lists_build(&L, m, n, nnz, row, col, val);
+    if (rc) { lists_free(&L); return rc; }
+    set_threads(nthreads);
+    int64_t i, j;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (i = 0; i < m; ++i) {
+        double *g = VX + i * k;
+        for (int c = 0; c < k; ++c) g[c] = 0.0;
+        for (int64_t e = L.rstart[i]; e < L.rstart[i + 1]; ++e) {
+            int32_t jj = L.rcol[e];
+            const double *x = X + i * k, *y = Yt + (int64_t)jj * k;
+            double u = dot(k, x, y), a = 0.0;
+            for (int c = 0; c < k; ++c) a += fabs(x[c] * y[c]);
+            double d = u_rel * a;
+            double v = oracle_dloss(lkind[jj], lparam[jj], llevels[jj], u + d, L.rval[e]) -
+                       oracle_dloss(lkind[jj], lparam[jj], llevels[jj], u - d, L.rval[e]);
+            for (int c = 0; c < k; ++c) g[c] += v * fabs(y[c]);
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (j = 0; j < n; ++j) {
+        double *h = VYt + j * k;
+        for (int c = 0; c < k; ++c) h[c] = 0.0;
+        for (int64_t e = L.cstart[j]; e < L.cstart[j + 1]; ++e) {
+            int32_t ii = L.crow[e];
+            const double *x = X + (int64_t)ii * k, *y = Yt + j * k;
+            double u = dot(k, x, y), a = 0.0;
+            for (int c = 0; c < k; ++c) a += fabs(x[c] * y[c]);
+            double d = u_rel * a;
+            double v = oracle_dloss(lkind[j], lparam[j], llevels[j], u + d, L.cval[e]) -
+                       oracle_dloss(lkind[j], lparam[j], llevels[j], u - d, L.cval[e]);
+            for (int c = 0; c < k; ++c) h[c] += v * fabs(x[c]);
+        }
+    }
+    lists_free(&L);
+    return 0;
+}
+
 /* Alternating proximal-gradient sweeps (Algorithm 2 with the proximal
  * gradient update and the per-row/per-column step-size rule of Section 7.2).
  * Sweep t updates every row x_i against Y^{t-1}, then every column y_j against

@@ -81,7 +81,7 @@ als_gram_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t 
 template <class T, int K>
 __global__ void __launch_bounds__(kAlsWarps * 32)
 als_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restrict__ part,
-                 int k, double gamma, T *__restrict__ F)
+                 int k, double gamma, T *__restrict__ F, int *__restrict__ err)
 {
     using TR = Tri<K>;
     __shared__ double G[kAlsWarps][K][K + 1];
@@ -111,7 +111,11 @@ als_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__
         b[wid][c] = 0.0;
     }
     __syncwarp();
-    warp_cholesky_solve<K, K + 1>(G[wid], b[wid]);
+    // a failed factorisation keeps the segment's factor and raises the flag
+    if (!warp_cholesky_solve<K, K + 1>(G[wid], b[wid])) {
+        if (lane == 0) atomicOr(err, kErrPivot);
+        return;
+    }
     if (lane < k) F[s * k + lane] = (T)b[wid][lane];
 }
 
@@ -141,7 +145,7 @@ cudaError_t launch_als_half(glrm_s *h, bool xstep, double gamma)
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "als_solve_x" : "als_solve_y");
     als_solve_kernel<T, K><<<blocks_for(o.nseg, kAlsWarps), kAlsWarps * 32, 0, h->stream>>>(
-        o.nseg, o.segchunk, part, h->k, gamma, F);
+        o.nseg, o.segchunk, part, h->k, gamma, F, h->s.err);
     tmark(h, nullptr);
     return cudaGetLastError();
 }

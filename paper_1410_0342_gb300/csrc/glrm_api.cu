@@ -3,6 +3,8 @@
 // that enqueue the per-precision engines.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -72,6 +74,7 @@ void free_scratch(Scratch &s, cudaStream_t st)
     dfree(s.acc_x, st); dfree(s.acc_y, st); dfree(s.red_part, st); dfree(s.red_cnt, st);
     dfree(s.hist, st); dfree(s.accepts, st); dfree(s.scalar, st); dfree(s.als_part, st); dfree(s.err, st);
     dfree(s.x_bf16, st); dfree(s.yt_bf16, st); dfree(s.u_csr, st); dfree(s.u_csc, st); dfree(s.u_new, st);
+    dfree(s.conv, st); dfree(s.conv_par, st); dfree(s.conv_cnt, st);
     s.u_sweeps = -1;
     s.hist_cap = 0;
     s.als_bytes = 0;
@@ -338,9 +341,18 @@ int64_t partial_slots(const Orient &o)
     return o.mode == kModeBlocked ? (int64_t)o.nb * o.nseg : o.nchunks;
 }
 
+// The captured sweep graph holds the buffer pointers and kernel paths of the
+// moment it was captured: drop it whenever either changes.
+void drop_conv_graph(glrm_s *h)
+{
+    if (h->conv_exec) cudaGraphExecDestroy(h->conv_exec);
+    h->conv_exec = nullptr;
+}
+
 int alloc_scratch(glrm_s *h)
 {
     Scratch &s = h->s;
+    drop_conv_graph(h);
     free_scratch(s, h->stream);
     const size_t es = elem_size(h->prec);
     int64_t nch = std::max<int64_t>(1, std::max(partial_slots(h->csr), partial_slots(h->csc)));
@@ -365,6 +377,9 @@ int alloc_scratch(glrm_s *h)
     CK(dalloc(h, &s.accepts, 2 * sizeof(long long)));
     CK(dalloc(h, &s.scalar, sizeof(double)));
     CK(dalloc(h, &s.err, sizeof(int)));
+    CK(dalloc(h, &s.conv, 2 * sizeof(double)));
+    CK(dalloc(h, &s.conv_par, 3 * sizeof(double)));
+    CK(dalloc(h, &s.conv_cnt, 3 * sizeof(int)));
     if (h->prec == GLRM_BF16) {
         CK(dalloc(h, &s.x_bf16, (size_t)h->m * h->k * sizeof(__nv_bfloat16)));
         CK(dalloc(h, &s.yt_bf16, (size_t)h->n * h->k * sizeof(__nv_bfloat16)));
@@ -388,6 +403,7 @@ int alloc_scratch(glrm_s *h)
 int ensure_hist(glrm_s *h, int n)
 {
     if (h->s.hist_cap >= n) return GLRM_OK;
+    drop_conv_graph(h);
     dfree(h->s.hist, h->stream);
     CK(dalloc(h, &h->s.hist, (size_t)n * sizeof(double)));
     h->s.hist_cap = n;
@@ -775,6 +791,32 @@ void tmark(glrm_s *h, const char *name)
 }
 }  // namespace glrm
 
+namespace glrm {
+
+// Convergence check after a sweep of glrm_sweep_until, one thread, FP64:
+// append the sweep's objective F (conv[1]) to the history and stop when
+//   use_ref:  F - F_ref <= rtol |F_ref|       (within rtol of a reference)
+//   else:     F_prev - F <= rtol |F|          (relative decrease of the sweep)
+// or when the sweep limit is reached.  Stopping clears the condition of the
+// enclosing WHILE graph node (graph mode) and sets the stop flag cnt[2].
+__global__ void converge_check_kernel(cudaGraphConditionalHandle cond, int graph, const double *__restrict__ par,
+                                      double *__restrict__ conv, int *__restrict__ cnt, double *__restrict__ hist)
+{
+    const double F = conv[1];
+    const int t = cnt[0];
+    hist[t] = F;
+    cnt[0] = t + 1;
+    const double rtol = par[0], fref = par[1];
+    const bool done = par[2] != 0.0 ? (F - fref <= rtol * fabs(fref)) : (conv[0] - F <= rtol * fabs(F));
+    conv[0] = F;
+    if (done || t + 1 >= cnt[1]) {
+        cnt[2] = 1;
+        if (graph) cudaGraphSetConditional(cond, 0);
+    }
+}
+
+}  // namespace glrm
+
 namespace {
 
 // Fold the recorded marks into per-kernel totals (synchronises).
@@ -793,6 +835,59 @@ int timer_collect(glrm_s *h)
     }
     t.marks.clear();
     return GLRM_OK;
+}
+
+
+// One sweep and its convergence check, enqueued on the handle's stream.
+cudaError_t sweep_and_check(glrm_s *h, cudaGraphConditionalHandle cond, int graph)
+{
+    cudaError_t e = half_step(h, true);
+    if (e == cudaSuccess) e = half_step(h, false);
+    if (e == cudaSuccess) e = reduce_sweep(h, h->s.conv + 1);
+    if (e != cudaSuccess) return e;
+    converge_check_kernel<<<1, 1, 0, h->stream>>>(cond, graph, h->s.conv_par, h->s.conv, h->s.conv_cnt, h->s.hist);
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+// Capture one sweep and its check as the body of a conditional WHILE node:
+// the body runs again while the check leaves the condition at 1.
+cudaError_t build_conv_graph(glrm_s *h)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const bool timing = h->timer.on;
+        h->timer.on = false;  // no per-kernel events inside the graph
+        const long long l0 = h->launches;
+        e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            const cudaError_t e2 = sweep_and_check(h, cond, 1);
+            e = cudaStreamEndCapture(h->stream, &body);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        h->conv_launches = h->launches - l0;
+        h->launches = l0;
+        h->timer.on = timing;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->conv_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->conv_exec = nullptr;
+        cudaGetLastError();  // a failed capture leaves no sticky error behind
+    }
+    return e;
 }
 
 }  // namespace
@@ -938,6 +1033,26 @@ int glrm_reset_steps(glrm_t h)
     return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "reset_steps");
 }
 
+// Read (synchronising) and clear the handle's device status word: a bounded
+// wait that expired, or an ALS factorisation that met a pivot that was not
+// positive and finite, since the status was last read.
+static int read_status(glrm_t h)
+{
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->s.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (!flag) return GLRM_OK;
+    CK(cudaMemsetAsync(h->s.err, 0, sizeof(int), h->stream));
+    if (flag & kErrWait)
+        return fail(h, GLRM_ERR_TIMEOUT, "a device-side wait (a staged copy or a tensor-core "
+                                         "operation) did not complete within its limit; results of "
+                                         "this call are invalid");
+    return fail(h, GLRM_ERR_NONFINITE, "an ALS row or column system was not numerically positive "
+                                       "definite (a Cholesky pivot was not positive and finite: "
+                                       "Inf or huge values in the data or factors); those rows or "
+                                       "columns kept their previous factor");
+}
+
 int glrm_sweep(glrm_t h, int32_t nsweeps, double *history)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
@@ -957,16 +1072,57 @@ int glrm_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (history) {
         CK(cudaMemcpyAsync(history, h->s.hist, (size_t)nsweeps * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
-        int flag = 0;
-        CK(cudaMemcpyAsync(&flag, h->s.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        if (flag) {
-            cudaMemsetAsync(h->s.err, 0, sizeof(int), h->stream);
-            return fail(h, GLRM_ERR_TIMEOUT, "a staged copy into shared memory did not complete "
-                                             "within its wait limit; results of this call are invalid");
-        }
+        return read_status(h);
     }
     return GLRM_OK;
+}
+
+int glrm_sweep_until(glrm_t h, int32_t max_sweeps, double rtol, double f_ref, int32_t *sweeps_host,
+                     double *history_host)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_sweep_until before glrm_set_observed");
+    if (max_sweeps < 1 || !(rtol >= 0.0) || !sweeps_host) return fail(h, GLRM_ERR_ARG, "bad arguments");
+    DeviceGuard dg(h->device);
+    int rc = ensure_hist(h, max_sweeps);
+    if (rc != GLRM_OK) return rc;
+    const bool use_ref = !std::isnan(f_ref);
+    const double par[3] = {rtol, use_ref ? f_ref : 0.0, use_ref ? 1.0 : 0.0};
+    const int cnt[3] = {0, max_sweeps, 0};
+    CK(cudaMemcpyAsync(h->s.conv_par, par, sizeof par, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->s.conv_cnt, cnt, sizeof cnt, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // the two small copies come from pageable memory
+    if (!use_ref) {
+        // F_0: the objective before the first sweep
+        rc = glrm_objective_at(h, h->X, h->Yt, h->s.conv);
+        if (rc != GLRM_OK) return rc;
+    }
+    int ran = 0;
+    if (h->prec != GLRM_BF16 && (h->conv_exec || build_conv_graph(h) == cudaSuccess)) {
+        // the whole loop on the device: one graph launch
+        CK(cudaGraphLaunch(h->conv_exec, h->stream));
+        CK(cudaMemcpyAsync(&ran, h->s.conv_cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->launches += (long long)ran * h->conv_launches;
+    } else {
+        // the BF16 form keeps host-side state between sweeps (refresh
+        // schedule): the device's decision is read back after every sweep
+        int host_cnt[3] = {0, 0, 0};
+        for (int t = 0; t < max_sweeps; ++t) {
+            const cudaError_t e = sweep_and_check(h, cudaGraphConditionalHandle(), 0);
+            if (e != cudaSuccess) return cuda_fail(h, e, "glrm_sweep_until");
+            CK(cudaMemcpyAsync(host_cnt, h->s.conv_cnt, sizeof host_cnt, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            if (host_cnt[2]) break;
+        }
+        ran = host_cnt[0];
+    }
+    h->sweeps_done += ran;
+    *sweeps_host = ran;
+    if (history_host && ran > 0)
+        CK(cudaMemcpyAsync(history_host, h->s.hist, (size_t)ran * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+    return read_status(h);
 }
 
 int glrm_last_accepts(glrm_t h, int64_t *acc)
@@ -1026,6 +1182,12 @@ int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, i
     return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_grad_at");
 }
 
+int glrm_grad(glrm_t h, void *GX, void *GYt)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    return glrm_grad_at(h, h->X, h->Yt, GX, GYt, 0, nullptr);
+}
+
 int glrm_predict(glrm_t h, int64_t cnt, const int32_t *rows, const int32_t *cols, void *out,
                  int32_t decode)
 {
@@ -1072,7 +1234,7 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (history) {
         CK(cudaMemcpyAsync(history, h->s.hist, (size_t)nsweeps * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
+        return read_status(h);
     }
     return GLRM_OK;
 }

@@ -191,17 +191,28 @@ __device__ __forceinline__ T reg_grad1(int kind, T w, T x)
     }
 }
 
-// 1/sqrt(d) in FP64 for d > 0 (and within float range): a float estimate
-// from rsqrtf refined by two Newton-Raphson steps y <- y (3 - d y^2) / 2 for
-// the root of 1/y^2 - d (each step squares the relative error: ~1e-7 ->
-// ~1e-14 -> below FP64 rounding).  Saves the FP64 division and square root,
-// which are slow on this GPU.
-__device__ __forceinline__ double rsqrt_fp64(double d)
+// 1/sqrt(d) in FP64 for a positive, finite, normal d; false (and y = 0)
+// otherwise: d <= 0, NaN, infinite or subnormal.  d = mant 2^e2 with e2 even
+// and mant in [1, 4) (exponent bits), so 1/sqrt(d) = 1/sqrt(mant) 2^(-e2/2):
+// a float estimate of 1/sqrt(mant) from rsqrtf refined by two Newton-Raphson
+// steps y <- y (3 - mant y^2) / 2 (each squares the relative error: ~1e-7 ->
+// ~1e-14 -> below FP64 rounding), then scaled exactly by a power of two.
+// Saves the FP64 division and square root, which are slow on this GPU, and
+// works for every double exponent, not only float-range ones.
+__device__ __forceinline__ bool rsqrt_fp64(double d, double &y)
 {
-    double y = (double)rsqrtf((float)d);
-    y = y * (1.5 - 0.5 * d * y * y);
-    y = y * (1.5 - 0.5 * d * y * y);
-    return y;
+    if (!(d >= 2.2250738585072014e-308 && d <= 1.7976931348623157e308)) {
+        y = 0.0;
+        return false;
+    }
+    const long long bits = __double_as_longlong(d);
+    const int e2 = ((int)((bits >> 52) & 0x7ff) - 1023) & ~1;
+    const double mant = d * __longlong_as_double((long long)(1023 - e2) << 52);
+    double r = (double)rsqrtf((float)mant);
+    r = r * (1.5 - 0.5 * mant * r * r);
+    r = r * (1.5 - 0.5 * mant * r * r);
+    y = r * __longlong_as_double((long long)(1023 - e2 / 2) << 52);
+    return true;
 }
 
 // Solve (C C^T) x = b in place for an SPD matrix G (row-major, leading
@@ -209,14 +220,18 @@ __device__ __forceinline__ double rsqrt_fp64(double d)
 // (overwritten by x), one warp, K <= 32.  Column by column: lane 0 takes the
 // pivot's reciprocal square root, lanes below it scale and update; the two
 // triangular solves are column-oriented too, so every step is one pass of the
-// warp.  FP64 throughout.
+// warp.  FP64 throughout.  Returns (to every lane) false when a pivot was not
+// positive, finite and normal: G was not numerically positive definite (or
+// held Inf / NaN); b then holds no solution and must not be used.
 template <int K, int LD>
-__device__ __forceinline__ void warp_cholesky_solve(double (*G)[LD], double *b)
+__device__ __forceinline__ bool warp_cholesky_solve(double (*G)[LD], double *b)
 {
     const int lane = threadIdx.x & 31;
+    bool ok = true;
     for (int c = 0; c < K; ++c) {
         if (lane == 0) {
-            const double r = rsqrt_fp64(G[c][c]);
+            double r;
+            ok = rsqrt_fp64(G[c][c], r) && ok;
             G[c][c] = r;  // the pivot slot keeps 1/C[c][c] from here on
         }
         __syncwarp();
@@ -241,7 +256,12 @@ __device__ __forceinline__ void warp_cholesky_solve(double (*G)[LD], double *b)
         if (lane < c) b[lane] -= G[c][lane] * b[c];
         __syncwarp();
     }
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
+
+// Bits of the handle's device status word (Scratch::err).
+constexpr int kErrWait = 1;   // a bounded wait hit its iteration limit
+constexpr int kErrPivot = 2;  // an ALS Cholesky pivot was not positive and finite
 
 __device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }

@@ -84,7 +84,10 @@ struct Scratch {
     int hist_cap = 0;
     void *als_part = nullptr;       // ALS per-chunk Gram partials
     size_t als_bytes = 0;
-    int *err = nullptr;             // device flag: a bounded wait expired
+    int *err = nullptr;             // device status word (kErrWait, kErrPivot bits)
+    double *conv = nullptr;         // sweep_until: [0] previous objective, [1] current one
+    double *conv_par = nullptr;     // sweep_until: rtol, reference objective, use-reference flag
+    int *conv_cnt = nullptr;        // sweep_until: [0] sweeps run, [1] sweep limit, [2] stop flag
     __nv_bfloat16 *x_bf16 = nullptr;   // BF16 form: BF16 copies of the factors
     __nv_bfloat16 *yt_bf16 = nullptr;
     float *u_csr = nullptr, *u_csc = nullptr;  // BF16 form: exact products per entry, both orders
@@ -179,6 +182,11 @@ struct glrm_s {
     // CSC copies, and an event to hand work between it and `stream`
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_csr = nullptr, ev_aux = nullptr;
+    // glrm_sweep_until: one sweep and the convergence check captured as the
+    // body of a conditional WHILE graph node (rebuilt after any change of the
+    // buffers or kernel paths it was captured with)
+    cudaGraphExec_t conv_exec = nullptr;
+    long long conv_launches = 0;  // kernels in one captured sweep
 };
 
 namespace glrm {

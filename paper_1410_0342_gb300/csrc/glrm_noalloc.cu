@@ -18,6 +18,8 @@
 // no ordering between them) share the array and race.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstddef>
 #include <mutex>
 
 #include "glrm.h"
@@ -26,6 +28,12 @@
 namespace {
 
 using glrm::LossSpec;
+
+// The caller's glrm_loss array is read in place as the kernels' LossSpec.
+static_assert(sizeof(glrm_loss) == sizeof(LossSpec), "glrm_loss and LossSpec differ in size");
+static_assert(offsetof(glrm_loss, kind) == offsetof(LossSpec, kind), "kind offset differs");
+static_assert(offsetof(glrm_loss, levels) == offsetof(LossSpec, levels), "levels offset differs");
+static_assert(offsetof(glrm_loss, param) == offsetof(LossSpec, param), "param offset differs");
 
 // Rows plus columns the scratch array can hold (8 MiB of doubles).
 constexpr int64_t kNoAllocMaxTerms = GLRM_NOALLOC_MAX_TERMS;
@@ -36,9 +44,31 @@ static __device__ __align__(256) double g_noalloc_terms[kNoAllocMaxTerms];
 std::mutex g_setup_mutex;
 double *g_terms_ptr[kMaxDevices] = {};
 
+// A loss descriptor the sweep accepts: a known kind, a positive finite Huber
+// threshold, at least two ordinal levels.
+__device__ __forceinline__ bool loss_ok(const LossSpec &L)
+{
+    switch (L.kind) {
+    case glrm::kLossQuad:
+    case glrm::kLossHinge:
+    case glrm::kLossLogistic:
+        return true;
+    case glrm::kLossHuber:
+        return L.param > 0.0 && L.param <= 1e300;
+    case glrm::kLossOrdinal:
+        return L.levels >= 2;
+    default:
+        return false;
+    }
+}
+
 // Warp per row: sum of the row's losses plus r(x_i); then one thread per
-// column: rt(y_j).  Indices outside [0, n) make the row's term NaN.
-__global__ void noalloc_terms_kernel(int64_t m, int64_t n, int k, const int32_t *__restrict__ rowptr,
+// column: rt(y_j).  A row whose entry range leaves [0, nnz] or runs
+// backwards, a column index outside [0, n), or a malformed loss descriptor
+// makes the row's term NaN (so the result is NaN); nothing is read out of
+// range.
+__global__ void noalloc_terms_kernel(int64_t m, int64_t n, int k, int64_t nnz,
+                                     const int32_t *__restrict__ rowptr,
                                      const int32_t *__restrict__ colidx, const float *__restrict__ val,
                                      const LossSpec *__restrict__ loss, int rxk, float rxw, int ryk,
                                      float ryw, const float *__restrict__ X,
@@ -50,10 +80,12 @@ __global__ void noalloc_terms_kernel(int64_t m, int64_t n, int k, const int32_t 
     for (int64_t i = warp; i < m; i += nwarps) {
         const float *x = X + i * k;
         double s = 0.0;
-        bool bad = false;
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+        const int64_t eb = rowptr[i], ee = rowptr[i + 1];
+        bool bad = eb < 0 || ee < eb || ee > nnz;
+        const int64_t lo = bad ? 0 : eb, hi = bad ? 0 : ee;
+        for (int64_t e = lo + lane; e < hi; e += 32) {
             const int j = colidx[e];
-            if (j < 0 || j >= n) {
+            if (j < 0 || j >= n || !loss_ok(loss[j])) {
                 bad = true;
                 continue;
             }
@@ -116,18 +148,23 @@ cudaError_t terms_ptr(double **out)
 
 }  // namespace
 
-extern "C" int glrm_objective_noalloc(int64_t m, int64_t n, int32_t k, const int32_t *csr_rowptr_dev,
-                                      const int32_t *csr_colidx_dev, const float *csr_val_dev,
-                                      const glrm_loss *col_loss_dev, int32_t rx_kind, double rx_weight,
-                                      int32_t ry_kind, double ry_weight, const float *X_dev,
-                                      const float *Yt_dev, double *out_dev, void *stream)
+extern "C" int glrm_objective_noalloc(int64_t m, int64_t n, int32_t k, int64_t nnz,
+                                      const int32_t *csr_rowptr_dev, const int32_t *csr_colidx_dev,
+                                      const float *csr_val_dev, const glrm_loss *col_loss_dev,
+                                      int32_t rx_kind, double rx_weight, int32_t ry_kind,
+                                      double ry_weight, const float *X_dev, const float *Yt_dev,
+                                      double *out_dev, void *stream)
 {
     if (m < 1 || n < 1 || k < 1 || k > 64) return GLRM_ERR_RANGE;
     if (m + n > kNoAllocMaxTerms) return GLRM_ERR_RANGE;
+    if (nnz < 0 || nnz >= (int64_t(1) << 31)) return GLRM_ERR_RANGE;
     if (!csr_rowptr_dev || !col_loss_dev || !X_dev || !Yt_dev || !out_dev) return GLRM_ERR_ARG;
+    if (nnz > 0 && (!csr_colidx_dev || !csr_val_dev)) return GLRM_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(col_loss_dev) % 16 != 0) return GLRM_ERR_ARG;
     for (int r : {rx_kind, ry_kind})
         if (r < GLRM_REG_ZERO || r > GLRM_REG_NONNEG) return GLRM_ERR_ARG;
+    for (double w : {rx_weight, ry_weight})
+        if (!std::isfinite(w) || w < 0.0) return GLRM_ERR_ARG;
     double *terms = nullptr;
     if (terms_ptr(&terms) != cudaSuccess) return GLRM_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -137,7 +174,7 @@ extern "C" int glrm_objective_noalloc(int64_t m, int64_t n, int32_t k, const int
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GLRM_ERR_CUDA;
     noalloc_terms_kernel<<<sms * 4, 256, 0, st>>>(
-        m, n, k, csr_rowptr_dev, csr_colidx_dev, csr_val_dev,
+        m, n, k, nnz, csr_rowptr_dev, csr_colidx_dev, csr_val_dev,
         reinterpret_cast<const LossSpec *>(col_loss_dev), rx_kind, (float)rx_weight, ry_kind,
         (float)ry_weight, X_dev, Yt_dev, terms);
     if (cudaGetLastError() != cudaSuccess) return GLRM_ERR_CUDA;

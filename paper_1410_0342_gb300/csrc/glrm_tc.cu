@@ -3,6 +3,23 @@
 
 namespace {
 static __device__ int g_tc_err;
+static __device__ int g_wait_err;
+
+// Self-test of the bounded wait used by every staged copy and tensor-core
+// completion in the library: one thread waits, with the library's own
+// mbar_wait_bounded and a caller-given attempt count, on an mbarrier phase.
+// With `arm` the thread first arrives on the barrier itself, so the phase
+// completes and the wait succeeds; without it nothing ever arrives, the wait
+// runs out, and the kernel takes the library's expiry path: it raises the
+// status flag and returns.  No copy or tensor-core operation is issued, so
+// nothing is in flight when the wait gives up.
+__global__ void wait_selftest_kernel(long limit, int arm, int *err)
+{
+    __shared__ uint64_t bar;
+    glrm::mbar_init(&bar, 1);
+    if (arm) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(glrm::smem_u32(&bar)) : "memory");
+    if (!glrm::mbar_wait_bounded(&bar, 0, limit)) atomicOr(err, 1);
+}
 }
 
 extern "C" int glrm_tc_gemm_bf16(const void *A_dev, const void *B_dev, float *D_dev, int32_t M, int32_t N,
@@ -24,6 +41,22 @@ extern "C" int glrm_tc_gemm_bf16(const void *A_dev, const void *B_dev, float *D_
     dim3 grid((unsigned)(M / 128), (unsigned)(N / kTcNT));
     tc_gemm_bf16_kernel<<<grid, 128, smem, st>>>((const __nv_bfloat16 *)A_dev, (const __nv_bfloat16 *)B_dev,
                                                  D_dev, M, N, K, err);
+    if (cudaGetLastError() != cudaSuccess) return GLRM_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GLRM_ERR_CUDA;
+    return h ? GLRM_ERR_TIMEOUT : GLRM_OK;
+}
+
+extern "C" int glrm_wait_selftest(int64_t attempts, int32_t arm, void *stream)
+{
+    if (attempts < 1) return GLRM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *err = nullptr;
+    if (cudaGetSymbolAddress((void **)&err, g_wait_err) != cudaSuccess) return GLRM_ERR_CUDA;
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return GLRM_ERR_CUDA;
+    wait_selftest_kernel<<<1, 1, 0, st>>>((long)attempts, arm ? 1 : 0, err);
     if (cudaGetLastError() != cudaSuccess) return GLRM_ERR_CUDA;
     int h = 0;
     if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

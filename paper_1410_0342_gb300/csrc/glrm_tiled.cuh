@@ -66,9 +66,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase)
+// Wait for phase `phase` of the mbarrier to complete, giving up after `limit`
+// try_wait attempts (each may suspend the thread for a while).  Returns false
+// on expiry; the caller then raises the error flag and leaves.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, long limit = kWaitLimit)
 {
-    for (long it = 0; it < kWaitLimit; ++it)
+    for (long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
 }

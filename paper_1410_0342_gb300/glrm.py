@@ -53,10 +53,12 @@ def _load():
         "glrm_get_factors_host": [p, p, p],
         "glrm_reset_steps": [p],
         "glrm_sweep": [p, i32, p],
+        "glrm_sweep_until": [p, i32, f64, f64, p, p],
         "glrm_last_accepts": [p, p],
         "glrm_objective": [p, p],
         "glrm_objective_at": [p, p, p, p],
         "glrm_grad_at": [p, p, p, p, p, i32, p],
+        "glrm_grad": [p, p, p],
         "glrm_predict": [p, i64, p, p, p, i32],
         "glrm_als_sweep": [p, i32, p],
         "glrm_get_state": [p, p, p],
@@ -66,7 +68,7 @@ def _load():
         "glrm_launch_count": [p, p],
         "glrm_set_path": [p, i32, i32],
         "glrm_get_path": [p, p],
-        "glrm_objective_noalloc": [i64, i64, i32, p, p, p, p, i32, f64, i32, f64, p, p, p, p],
+        "glrm_objective_noalloc": [i64, i64, i32, i64, p, p, p, p, i32, f64, i32, f64, p, p, p, p],
         "glrm_batch_create": [i32, p, p, p, p, p, p, p, p, p],
         "glrm_batch_set_factors": [p, p, p],
         "glrm_batch_get_factors": [p, p, p],
@@ -75,6 +77,7 @@ def _load():
         "glrm_batch_sweep": [p, i32, p, i32],
         "glrm_batch_autotune": [p, i32, p, p],
         "glrm_tc_gemm_bf16": [p, p, p, i32, i32, i32, p],
+        "glrm_wait_selftest": [i64, i32, p],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +208,16 @@ def glrm_sweep(h, nsweeps, history=True):
     return None
 
 
+def glrm_sweep_until(h, max_sweeps, rtol, f_ref=float("nan")):
+    """Sweeps until the device-side convergence test passes; returns the
+    objectives of the sweeps run (numpy float64)."""
+    ran = ctypes.c_int32(0)
+    out = np.empty(max_sweeps, dtype=np.float64)
+    _check(_lib.glrm_sweep_until(h, int(max_sweeps), float(rtol), float(f_ref), ctypes.byref(ran),
+                                 _ptr(out)), h)
+    return out[:ran.value].copy()
+
+
 def glrm_last_accepts(h):
     out = np.zeros(2, dtype=np.int64)
     _check(_lib.glrm_last_accepts(h, _ptr(out)), h)
@@ -225,6 +238,11 @@ def glrm_grad_at(h, X, Yt, GX, GYt, include_reg=True, scale=None):
     """scale: optional CUDA float64 tensor (one element) multiplying both gradients."""
     _check(_lib.glrm_grad_at(h, _ptr(X), _ptr(Yt), _ptr(GX), _ptr(GYt), int(bool(include_reg)),
                              _ptr(scale)), h)
+
+
+def glrm_grad(h, GX, GYt):
+    """Loss part of the gradient at the handle's factors into GX (m x k), GYt (n x k)."""
+    _check(_lib.glrm_grad(h, _ptr(GX), _ptr(GYt)), h)
 
 
 def glrm_predict(h, rows, cols, out, decode=True):
@@ -288,13 +306,13 @@ def glrm_launch_count(h) -> int:
     return int(out.value)
 
 
-def glrm_objective_noalloc(m, n, k, csr_rowptr, csr_colidx, csr_val, col_loss_dev, rx, ry, X, Yt,
-                           out, stream=None):
+def glrm_objective_noalloc(m, n, k, nnz, csr_rowptr, csr_colidx, csr_val, col_loss_dev, rx, ry, X,
+                           Yt, out, stream=None):
     """Objective without device allocation (see include/glrm.h); every
     argument is a CUDA tensor, col_loss_dev the raw bytes of n glrm_loss."""
     if stream is None:
         stream = torch.cuda.current_stream()
-    _check(_lib.glrm_objective_noalloc(m, n, k, _ptr(csr_rowptr), _ptr(csr_colidx), _ptr(csr_val),
+    _check(_lib.glrm_objective_noalloc(m, n, k, nnz, _ptr(csr_rowptr), _ptr(csr_colidx), _ptr(csr_val),
                                        _ptr(col_loss_dev), int(rx[0]), float(rx[1]), int(ry[0]),
                                        float(ry[1]), _ptr(X), _ptr(Yt), _ptr(out),
                                        ctypes.c_void_p(stream.cuda_stream)))
@@ -309,6 +327,13 @@ def glrm_tc_gemm_bf16(A, B, D, stream=None):
     N = B.shape[0]
     _check(_lib.glrm_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(D), M, N, K,
                                   ctypes.c_void_p(stream.cuda_stream)))
+
+
+def glrm_wait_selftest(attempts, arm, stream=None):
+    """Bounded-wait self-test; raises GLRMError(GLRM_ERR_TIMEOUT) when the wait ran out."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib.glrm_wait_selftest(int(attempts), int(bool(arm)), ctypes.c_void_p(stream.cuda_stream)))
 
 
 def glrm_destroy(h):
@@ -480,6 +505,9 @@ class GLRM:
     def sweep(self, nsweeps, history=True):
         return glrm_sweep(self.h, nsweeps, history)
 
+    def sweep_until(self, max_sweeps, rtol, f_ref=float("nan")):
+        return glrm_sweep_until(self.h, max_sweeps, rtol, f_ref)
+
     def als_sweep(self, nsweeps, history=True):
         return glrm_als_sweep(self.h, nsweeps, history)
 
@@ -488,6 +516,13 @@ class GLRM:
 
     def accepts(self):
         return glrm_last_accepts(self.h)
+
+    def grad(self):
+        """Loss part of the gradient at the current factors: (GX, GYt)."""
+        GX = torch.empty(self.m, self.k, dtype=self.dtype, device=self.device)
+        GYt = torch.empty(self.n, self.k, dtype=self.dtype, device=self.device)
+        glrm_grad(self.h, GX, GYt)
+        return GX, GYt
 
     def predict(self, rows, cols, decode=True):
         out = torch.empty(rows.numel(), dtype=self.dtype, device=self.device)

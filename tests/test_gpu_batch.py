@@ -59,13 +59,15 @@ def split_factors(wb, s, X, Yt):
             Yt[y0:y0 + n * k].reshape(n, k).double().cpu().numpy())
 
 
-def test_batch_matches_oracle(G, oracle_mod):
-    wb = small_batch()
-    meth = methods_of(wb, G)
+def check_batch(G, o, wb, meth, T, autotune=False):
+    """Every instance against the oracle: ALS instances free-running for T
+    sweeps (no accept / reject branch, so the trajectories stay together)
+    within 1e-4; proximal-gradient instances one sweep at a time from the
+    batch's own state within 1e-5."""
     B = G.Batch(wb, meth)
-    T = 4
+    if autotune:
+        B.autotune(reps=2)
     X0, Y0 = B.factors()
-    ax0, ay0 = B.steps()
     hist = []
     states = []
     for _ in range(T):
@@ -75,7 +77,7 @@ def test_batch_matches_oracle(G, oracle_mod):
         hist.append(B.sweep(1)[0])
     hist = np.array(hist)
     for s in range(wb.count):
-        p = oracle_for(oracle_mod, wb, s)
+        p = oracle_for(o, wb, s)
         if meth[s] == G.GLRM_BATCH_ALS:
             Xs, Ys = split_factors(wb, s, X0, Y0)
             *_, oh = p.als(Xs, Ys, 0.1, T)
@@ -91,6 +93,21 @@ def test_batch_matches_oracle(G, oracle_mod):
                 ays = ay[c0:c0 + n].double().cpu().numpy()
                 *_, oh, _ = p.proxgrad(Xs, Ys, 1, axs, ays)
                 assert abs(hist[t, s] - oh[0]) / abs(oh[0]) < 1e-5, (s, t, hist[t, s], oh[0])
+    B.close()
+
+
+def test_batch_matches_oracle(G, oracle_mod):
+    wb = small_batch()
+    check_batch(G, oracle_mod, wb, methods_of(wb, G), 4)
+
+
+def test_batch_workload_sizes_match_oracle(G, oracle_mod):
+    """The first 128 instances of the 4,096-instance workload itself (m up to
+    5,000, n up to 500, k in {4, 8, 16}, every size class), with the work-item
+    table autotuned first as the benchmark does."""
+    wb = W.batch_torch(128, device="cuda")
+    assert int(wb.m.max()) > 4000 and int(wb.n.max()) > 400 and set(wb.k.tolist()) == {4, 8, 16}
+    check_batch(G, oracle_mod, wb, methods_of(wb, G), 3, autotune=True)
 
 
 def test_launch_modes_agree(G):

@@ -139,3 +139,19 @@ def test_dense_path_switch_and_als(G, oracle_mod):
     assert (np.abs(hist - ohist) / ohist).max() < 1e-4
     with pytest.raises(G.GLRMError):
         G.glrm_set_path(gq.h, G.GLRM_PATH_DENSE, G.GLRM_PATH_CHUNKED)
+
+
+@pytest.mark.parametrize("m,nsweeps", [(20000, 5), (100000, 2)])
+def test_benchmark_table_dense_path_matches_oracle(G, oracle_mod, m, nsweeps):
+    """The benchmark's own table recipe (W.mixed: 60% observed, contiguous
+    blocks of 500 Huber, 300 hinge and 200 ordinal columns, l1 on X,
+    nonnegativity on Y, k = 20) on the path the benchmark times: stored
+    densely with NaN at the missing cells, 16-column loss groups of one kind,
+    cost-planned work items split across the tile's chunks.  At m = 100,000
+    this is the exact launch configuration of the benchmark; synced sweeps
+    against the oracle, objectives within 1e-5, factors and steps compared."""
+    t = W.mixed(m=m)
+    g = G.GLRM.from_table(t)
+    assert G.glrm_get_path(g.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    rels = synced_sweeps(g, oracle_mod, t, nsweeps)
+    assert rels.max() < 1e-5

@@ -274,3 +274,65 @@ def test_proxgrad_empty_row_and_column(oracle_mod):
     np.testing.assert_array_equal(X1[1], [0.25, 0.0, 0.0])  # soft threshold at 1 * 0.5
     np.testing.assert_array_equal(Yt1[1], Yt0[1] / (1.0 + 2.0 * gam))
     assert ax[1] == 1.05 and ay[1] == 1.05
+
+
+def test_gradient_abs_brute_force(oracle_mod):
+    """sum |L'| |w| per gradient coordinate, cell by cell over the entries; and
+    where every term is nonnegative (hinge with a = -1 and u > -1, so L' = 1,
+    and nonnegative factors) it equals the gradient itself."""
+    o = oracle_mod
+    t = W.small_mixed(m=11, n=9, k=3, seed=8, rx=(RZ, 0.0), ry=(RZ, 0.0))
+    p = _problem(o, t)
+    rows = t.rows()
+    SX, SY = p.gradient_abs(t.X0, t.Yt0)
+    bx = np.zeros_like(SX)
+    by = np.zeros_like(SY)
+    for e in range(t.nnz):
+        i, j, a = rows[e], t.colidx[e], t.val[e]
+        d = abs(o.dloss(int(t.loss_kind[j]), float(t.X0[i] @ t.Yt0[j]), a, float(t.loss_param[j]),
+                        int(t.loss_levels[j])))
+        bx[i] += d * np.abs(t.Yt0[j])
+        by[j] += d * np.abs(t.X0[i])
+    np.testing.assert_allclose(SX, bx, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(SY, by, rtol=1e-13, atol=1e-15)
+    rng = np.random.default_rng(2)
+    X = rng.uniform(0.1, 1.0, size=(6, 2))
+    Yt = rng.uniform(0.1, 1.0, size=(5, 2))
+    r, c = np.nonzero(rng.random((6, 5)) < 0.7)
+    q = o.Problem(6, 5, 2, r.astype(np.int32), c.astype(np.int32), -np.ones(r.size), HI, 0.0, 0)
+    GX, GY = q.gradient(X, Yt)
+    SX, SY = q.gradient_abs(X, Yt)
+    np.testing.assert_allclose(SX, GX, rtol=1e-14)
+    np.testing.assert_allclose(SY, GY, rtol=1e-14)
+
+
+def test_gradient_variation_closed_forms(oracle_mod):
+    """Quadratic loss: L'(u + d) - L'(u - d) = 4 d, so the variation is
+    sum 4 u_rel (sum_c |x_c y_c|) |w|.  Hinge with a = 1: a product exactly at
+    the kink u = 1 gives the unit jump (0 - (-1)) times |w|; products more than
+    delta away from it give 0."""
+    o = oracle_mod
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(4, 3))
+    Yt = rng.normal(size=(5, 3))
+    r, c = np.nonzero(rng.random((4, 5)) < 0.8)
+    r, c = r.astype(np.int32), c.astype(np.int32)
+    q = o.Problem(4, 5, 3, r, c, rng.normal(size=r.size), Q, 0.0, 0)
+    VX, VY = q.gradient_variation(X, Yt, 1e-3)
+    ex = np.zeros_like(X)
+    ey = np.zeros_like(Yt)
+    for i, j in zip(r, c):
+        d = 1e-3 * np.sum(np.abs(X[i] * Yt[j]))
+        ex[i] += 4 * d * np.abs(Yt[j])
+        ey[j] += 4 * d * np.abs(X[i])
+    np.testing.assert_allclose(VX, ex, rtol=1e-9)
+    np.testing.assert_allclose(VY, ey, rtol=1e-9)
+    # hinge: row 0 sits on the kink (u = 1) for column 0, far from it for column 1
+    Xh = np.array([[1.0, 0.0]])
+    Yh = np.array([[1.0, 0.5], [3.0, 2.0]])
+    h = o.Problem(1, 2, 2, np.array([0, 0], np.int32), np.array([0, 1], np.int32),
+                  np.array([1.0, 1.0]), HI, 0.0, 0)
+    VX, VY = h.gradient_variation(Xh, Yh, 1e-6)
+    np.testing.assert_allclose(VX[0], np.abs(Yh[0]), rtol=1e-15)
+    np.testing.assert_allclose(VY[0], np.abs(Xh[0]), rtol=1e-15)
+    assert not VY[1].any()
