@@ -52,10 +52,18 @@ def parse():
     ap.add_argument("--impl", default="glrm", choices=["glrm", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true",
+                    help="skip the sparse (masked-tile) path measurement on the same table")
+    ap.add_argument("--time-to-tol", type=int, default=1,
+                    help="1: measure the time to a 1e-4 relative objective (GPU and oracle)")
     ap.add_argument("--rows", type=int, default=100_000,
                     help="rows of the mixed table (smaller for profiling runs)")
     ap.add_argument("--path", default="auto",
                     help="kernel paths 'X,Y' (auto, chunked, fused, blocked, masked, split)")
+    ap.add_argument("--form-rows", type=int, default=0,
+                    help="rows of the completion form's table (0: its full 1,000,000)")
+    ap.add_argument("--count", type=int, default=4096, help="instances of the batched form")
+    ap.add_argument("--no-autotune", action="store_true", help="batched form: default work items")
     ap.add_argument("--form", default="sweep",
                     choices=["sweep", "batched", "autograd", "completion", "dense"],
                     help="sweep: the benchmark line; the others measure the batched, differentiable, "
@@ -173,27 +181,48 @@ def ncu_traffic(kernel: str):
 
 
 def algorithmic_bytes(name: str, t: W.Table, k: int) -> float:
-    """Bytes a kernel must move at minimum per launch (FP32 values, int32
-    indices): every observed entry's index and value once, every factor row it
-    reads once and every row it writes once.  A fused half-step reads the
-    entries once and both factors, and writes the updated factor and step
-    sizes; a gradient or loss pass reads the entries and both factors; prox /
-    decide kernels touch per-segment state only."""
+    """Bytes a kernel must move at minimum per launch, counted as the method's
+    own work: every observed entry's index and value once (8 bytes, int32 and
+    FP32), every factor row it reads once and every row it writes once.  A
+    fused half-step reads the entries once and both factors, and writes the
+    updated factor and step sizes; a gradient or loss pass (sparse or dense)
+    reads the entries and both factors, and a gradient pass writes per-segment
+    partial gradients; prox / decide kernels touch per-segment state only.
+    The dense form reads every cell of its table instead of the observed
+    entries; that figure is dense_cell_bytes."""
     nnz, m, n = t.nnz, t.m, t.n
     fb = 4 * k
     x = name.endswith("_x")
     nseg, other = (m, n) if x else (n, m)
-    if name.startswith("dense_grad") or name.startswith("dense_loss"):
-        # the dense form reads every cell of the table once (4 m n bytes, a
-        # missing cell is a NaN), both factors, and writes per-row partials
-        return 4.0 * m * n + (nseg + other) * fb + (nseg * fb if "grad" in name else 0)
     if "fused" in name:
         return nnz * 8 + (nseg + other) * fb + nseg * (fb + 4)
     if "grad" in name or "loss" in name:
-        return nnz * 8 + (nseg + other) * fb
+        return nnz * 8 + (nseg + other) * fb + (nseg * fb if "grad" in name else 0)
     if "prox" in name or "decide" in name:
         return nseg * (2 * fb + 4)
     return 0.0
+
+
+def dense_cell_bytes(name: str, t: W.Table, k: int) -> float:
+    """What a dense pass actually has to read: every cell of the m x n table
+    (4 bytes; a missing cell is a NaN), both factors, and for a gradient pass
+    the per-row partial gradients it writes."""
+    m, n = t.m, t.n
+    nseg, other = (m, n) if name.endswith("_x") else (n, m)
+    return 4.0 * m * n + (nseg + other) * 4 * k + (nseg * 4 * k if "grad" in name else 0)
+
+
+def sweep_bytes(t: W.Table, k: int) -> float:
+    """Algorithmic bytes of one whole sweep: each observed entry's index and
+    value read once per half-step (16 bytes), every factor row read and
+    written once per half-step, row / column pointers, step sizes and counts."""
+    return 16.0 * t.nnz + 4 * 4 * (t.m + t.n) * k + 4 * (t.m + t.n) + 8 * (t.m + t.n)
+
+
+def sweep_flops(t: W.Table, k: int) -> float:
+    """FP32 flops of one sweep: per observed entry and half-step a dot product,
+    the gradient update and the re-evaluating dot product (2k each)."""
+    return 12.0 * k * t.nnz
 
 
 def algorithmic_flops(name: str, t: W.Table, k: int) -> float:
@@ -222,8 +251,9 @@ def table_rows(t: W.Table, rows: int) -> W.Table:
                    t.Yt0)
 
 
-def oracle_rate(t: W.Table, steps: int, warmup: int = 0):
-    """Entries/s of the oracle's sweep (with its objective) on table t."""
+def oracle_rate(t: W.Table, steps: int, warmup: int = 0, nthreads: int = 0):
+    """Entries/s of the oracle's sweep (with its objective) on table t, on
+    nthreads host threads (0: all)."""
     import oracle
     oracle.build()
     p = oracle.Problem.from_csr(t.m, t.n, t.k, t.rowptr, t.colidx, t.val,
@@ -232,11 +262,71 @@ def oracle_rate(t: W.Table, steps: int, warmup: int = 0):
     X, Yt = t.X0.copy(), t.Yt0.copy()
     ax, ay = p.initial_alphas()
     if warmup:
-        X, Yt, ax, ay, _, _ = p.proxgrad(X, Yt, warmup, ax, ay)
+        X, Yt, ax, ay, _, _ = p.proxgrad(X, Yt, warmup, ax, ay, nthreads=nthreads)
     t0 = time.perf_counter()
-    X, Yt, ax, ay, hist, _ = p.proxgrad(X, Yt, steps, ax, ay)
+    X, Yt, ax, ay, hist, _ = p.proxgrad(X, Yt, steps, ax, ay, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    return t.nnz * steps / dt, dt, oracle.num_threads()
+    return t.nnz * steps / dt, dt, oracle.num_threads(nthreads)
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu / /proc/cpuinfo), for the baselines."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_time_to_tol(t: W.Table, rtol: float, f_ref=None, max_sweeps=2000, chunk=10,
+                       nthreads=0):
+    """Wall time of the oracle's sweeps from the table's initial factors up to
+    the first sweep that meets the test glrm_sweep_until applies: relative
+    decrease F_{t-1} - F_t <= rtol |F_t| (f_ref None; F_0 the initial
+    objective) or F_t - f_ref <= rtol |f_ref|.  Sweeps run in chunks; the time
+    of a chunk's sweeps past the stopping sweep is not counted."""
+    import oracle
+    oracle.build()
+    p = oracle.Problem.from_csr(t.m, t.n, t.k, t.rowptr, t.colidx, t.val,
+                                loss_kind=t.loss_kind, loss_param=t.loss_param,
+                                loss_levels=t.loss_levels, rx=t.rx, ry=t.ry)
+    X, Yt = t.X0.copy(), t.Yt0.copy()
+    ax, ay = p.initial_alphas()
+    prev = p.objective(X, Yt, nthreads) if f_ref is None else None
+    done, total = 0, 0.0
+    while done < max_sweeps:
+        c = min(chunk, max_sweeps - done)
+        t0 = time.perf_counter()
+        X, Yt, ax, ay, hist, _ = p.proxgrad(X, Yt, c, ax, ay, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        for q, F in enumerate(hist):
+            ok = (prev - F <= rtol * abs(F)) if f_ref is None else (F - f_ref <= rtol * abs(f_ref))
+            prev = F
+            if ok:
+                return {"sweeps": done + q + 1, "seconds": total + dt * (q + 1) / c,
+                        "objective": float(F), "threads": oracle.num_threads(nthreads)}
+        done += c
+        total += dt
+    return {"sweeps": None, "seconds": total, "objective": float(prev) if prev is not None else None,
+            "threads": oracle.num_threads(nthreads), "note": f"not reached in {max_sweeps} sweeps"}
+
+
+def qpca_fstar(t: W.Table) -> float:
+    """Closed-form optimum of quadratically regularised PCA on a fully observed
+    table: ||A||^2 - sum_{i<=k} ((s_i - gamma)_+)^2 (Appendix A)."""
+    A = t.val.reshape(t.m, t.n)
+    s = np.linalg.svd(A, compute_uv=False)
+    return float(np.sum(A * A) - np.sum(np.maximum(s[:t.k] - t.rx[1], 0.0) ** 2))
 
 
 # ------------------------------------------------------------------- arms
@@ -256,10 +346,39 @@ def run_reference(args, world, rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD.format(m=t.m), "l2": "CPU run"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample_desc},
+                         "sample": sample_desc, "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count()},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def kernel_roofline(name, ms, count, t, fp32_tflops, peaks, peak_src):
+    """Roofline of one kernel from its per-launch CUDA-event time: HBM with the
+    method's algorithmic bytes, and the FP32 pipe (sparse passes) or the BF16
+    tensor pipe (dense passes) with the method's flops."""
+    avg_s = ms / count / 1000.0
+    abytes = algorithmic_bytes(name, t, t.k)
+    achieved = abytes / avg_s / 1e9
+    r = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+         "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(name),
+         "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_s * 1e6,
+         "peak_source": peak_src}
+    if name.startswith("dense_"):
+        cb = dense_cell_bytes(name, t, t.k)
+        r["dense_cell"] = {"bytes_per_launch": cb, "achieved_gbs": cb / avg_s / 1e9,
+                           "frac": cb / avg_s / 1e9 / peaks["hbm_gbs"]}
+        # 2 m n k flop for U (+ 2 m n k for R W in a gradient pass) against the
+        # measured BF16 peak (the six split products are not counted)
+        tflops = (4.0 if "grad" in name else 2.0) * t.m * t.n * t.k / avg_s / 1e12
+        r["tensor"] = {"achieved_tflops": tflops, "peak_tflops": peaks["bf16_tflops"],
+                       "frac": tflops / peaks["bf16_tflops"], "peak_source": peak_src}
+    else:
+        af = algorithmic_flops(name, t, t.k)
+        r["alu"] = {"achieved_tflops": af / avg_s / 1e12, "peak_tflops": fp32_tflops,
+                    "frac": af / avg_s / 1e12 / fp32_tflops,
+                    "peak_source": "measured FP32 FMA probe (glrm_fma_peak)"}
+    return r
 
 
 def run_glrm(args, world, rank, local):
@@ -282,6 +401,7 @@ def run_glrm(args, world, rank, local):
         G.glrm_set_path(g.h, px, py)
     paths = G.glrm_get_path(g.h)
     torch.cuda.synchronize(dev)
+    fp32_tflops, sms = G.glrm_fma_peak(stream=stream)
 
     def barrier():
         if world > 1:
@@ -317,35 +437,46 @@ def run_glrm(args, world, rank, local):
     ms_max = max_over_ranks(ms, world, dev)
     value = job_throughput(world, t.nnz, args.steps, ms_max)
 
-    # dominant kernel and its roofline
+    # dominant kernel and its roofline; the whole sweep against section 8(d)'s bytes and flops
     peaks, peak_src = measured_peaks()
-    top = max(kern.items(), key=lambda kv: kv[1][0])
-    tname, (tms, tcount) = top
-    avg_s = tms / tcount / 1000.0
-    abytes = algorithmic_bytes(tname, t, t.k)
-    achieved = abytes / avg_s / 1e9
-    traffic = ncu_traffic(tname)
-    # the FP32 pipe: 152 SMs x 128 lanes x 2 flop per FMA x the sampled SM clock
-    clk_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
-    aflops = algorithmic_flops(tname, t, t.k)
-    roofline = {"bound": "hbm", "kernel": tname, "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "algorithmic_bytes_per_launch": abytes, "avg_launch_us": avg_s * 1e6,
-                "peak_source": peak_src, "share_of_step": tms / ms}
-    if tname.startswith("dense_"):
-        # tensor cores: 2 m n k flop for U (+ 2 m n k for R W in a gradient pass),
-        # against the measured BF16 peak (the six split products are not counted)
-        tflops = (4.0 if "grad" in tname else 2.0) * t.m * t.n * t.k / avg_s / 1e12
-        roofline["tensor"] = {"achieved_tflops": tflops, "peak_tflops": peaks["bf16_tflops"],
-                              "frac": tflops / peaks["bf16_tflops"], "peak_source": peak_src}
-    else:
-        roofline["alu"] = {"achieved_tflops": aflops / avg_s / 1e12, "peak_tflops": fp32_peak,
-                           "frac": aflops / avg_s / 1e12 / fp32_peak,
-                           "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled SM clock"}
+    tname, (tms, tcount) = max(kern.items(), key=lambda kv: kv[1][0])
+    roofline = kernel_roofline(tname, tms, tcount, t, fp32_tflops, peaks, peak_src)
+    roofline["share_of_step"] = tms / ms
+    sw_s = ms / args.steps / 1000.0
+    sweep_rf = {"algorithmic_bytes": sweep_bytes(t, t.k), "algorithmic_flops": sweep_flops(t, t.k),
+                "hbm_frac": sweep_bytes(t, t.k) / sw_s / 1e9 / peaks["hbm_gbs"],
+                "fp32_frac": sweep_flops(t, t.k) / sw_s / 1e12 / fp32_tflops,
+                "fp32_peak_tflops": fp32_tflops, "sms": sms}
+    roofline["sweep"] = sweep_rf
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / ms}
                for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
+
+    # the sparse sampled-residual path (masked tiles) on the same table
+    sparse = None
+    if rank == 0 and args.path == "auto" and not args.no_sparse:
+        gs = G.GLRM.from_table(t, precision=G.GLRM_FP32, device=dev, stream=stream)
+        # masked tiles in both half-steps, split over the GPU's warps by the planner
+        G.glrm_set_path(gs.h, PATH_CODES["masked"], PATH_CODES["masked"])
+        spaths = G.glrm_get_path(gs.h)
+        gs.sweep(args.warmup, history=False)
+        G.glrm_timing_enable(gs.h, True)
+        torch.cuda.synchronize(dev)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        gs.sweep(args.steps, history=False)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        sms_ = s0.elapsed_time(s1)
+        sk = G.glrm_timing_read(gs.h)
+        G.glrm_timing_enable(gs.h, False)
+        sn, (sms_k, scnt) = max(sk.items(), key=lambda kv: kv[1][0])
+        srf = kernel_roofline(sn, sms_k, scnt, t, fp32_tflops, peaks, peak_src)
+        srf["share_of_step"] = sms_k / sms_
+        sparse = {"paths": {"x": spaths[0], "y": spaths[1]}, "value": t.nnz * args.steps / (sms_ / 1e3),
+                  "unit": UNIT, "ms_per_step": sms_ / args.steps, "roofline": srf,
+                  "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / sms_}
+                              for k, v in sorted(sk.items(), key=lambda kv: -kv[1][0])}}
+        gs.close()
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -381,15 +512,55 @@ def run_glrm(args, world, rank, local):
                            "chosen path's layout), set_factors_host, one sweep, objective D2H"}
         ge.close()
 
+    # time to a 1e-4 relative objective: the device-side convergence test
+    # (glrm_sweep_until) from the initial factors, beside the oracle's time to
+    # the same test on the same table (row sample) and on the qPCA table
+    ttt = None
+    if rank == 0 and world == 1 and args.time_to_tol and args.rows == 100_000:
+        ttt = {"rtol": 1e-4}
+
+        def gpu_ttt(table, rtol, f_ref=float("nan"), prec=G.GLRM_FP32, max_sweeps=3000):
+            gg = G.GLRM.from_table(table, precision=prec, device=dev, stream=stream)
+            # capture the graph with the same history size (one sweep: any objective is
+            # below the reference 1e300), then restart the fit from the initial factors
+            gg.sweep_until(max_sweeps, 0.0, 1e300)
+            gg.set_factors(torch.as_tensor(table.X0, dtype=gg.dtype, device=dev),
+                           torch.as_tensor(table.Yt0, dtype=gg.dtype, device=dev))
+            G.glrm_reset_steps(gg.h)
+            torch.cuda.synchronize(dev)
+            w0 = time.perf_counter()
+            h = gg.sweep_until(max_sweeps, rtol, f_ref)
+            wall = time.perf_counter() - w0
+            gg.close()
+            return {"sweeps": int(len(h)), "seconds": wall, "objective": float(h[-1]),
+                    "reached": bool(len(h) < max_sweeps)}
+
+        ttt["mixed_full"] = {"test": "relative decrease per sweep <= 1e-4",
+                             "gpu": gpu_ttt(t, 1e-4)}
+        sample = table_rows(t, ORACLE_SAMPLE_ROWS)
+        ttt["mixed_rows_10k"] = {"test": "relative decrease per sweep <= 1e-4",
+                                 "gpu": gpu_ttt(sample, 1e-4),
+                                 "oracle": oracle_time_to_tol(sample, 1e-4)}
+        q = W.qpca_dense()
+        fq = qpca_fstar(q)
+        ttt["qpca_200x100"] = {"test": "(F - f*) / f* <= 1e-4, f* the closed-form optimum", "f_star": fq,
+                               "gpu_fp64": gpu_ttt(q, 1e-4, fq, prec=G.GLRM_FP64),
+                               "oracle": oracle_time_to_tol(q, 1e-4, f_ref=fq, chunk=50)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the whole table, as many oracle sweeps as fit in about 15 s
+        # the whole table, as many oracle sweeps as fit in about 15 s, on all
+        # host cores; then one sweep on one core
         _, dt1, _ = oracle_rate(t, 1, 0)
         nsw = max(1, min(50, int(15.0 / max(dt1, 1e-3))))
         rate, dt, cores = oracle_rate(t, nsw, 0)
+        rate1, dt_1, _ = oracle_rate(t, 1, 0, nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"the full table ({t.nnz} entries) from the same initial factors, "
-                         f"{nsw} sweeps with the objective after each, {dt:.1f} s"}
+                         f"{nsw} sweeps with the objective after each, {dt:.1f} s",
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": f"one sweep of the full table, {dt_1:.1f} s"},
+               "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
     if rank == 0:
         line = {
@@ -408,6 +579,8 @@ def run_glrm(args, world, rank, local):
             "gpu_launches": launches,
             "clocks": clk,
             "kernels": kernels,
+            "sparse": sparse,
+            "time_to_tol": ttt,
             "objective_after": float(hist[-1]),
         }
         print(json.dumps(line), flush=True)
@@ -439,11 +612,11 @@ def run_form(args):
     line = {"form": args.form, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
     if args.form == "batched":
         t0 = time.time()
-        wb = W.batch_torch(4096, device=dev)
+        wb = W.batch_torch(args.count, device=dev)
         gen_s = time.time() - t0
         meth = [G.GLRM_BATCH_ALS if s % 2 == 0 else G.GLRM_BATCH_PROXGRAD for s in range(wb.count)]
         B = G.Batch(wb, meth, stream=st)
-        tx, ty = B.autotune(reps=2)
+        tx, ty = (np.zeros(32, np.int32), np.zeros(32, np.int32)) if args.no_autotune else B.autotune(reps=2)
         nnz = int(wb.nnz.sum())
         B.sweep(args.steps, G.GLRM_BATCH_GRAPH, history=False)  # capture + warm-up
         for _ in range(max(0, args.warmup - 1)):
@@ -453,7 +626,7 @@ def run_form(args):
         ms_inst = _events(torch, st, lambda: B.sweep(args.steps, G.GLRM_BATCH_PER_INSTANCE, history=False))
         line.update({
             "metric": METRIC, "unit": UNIT, "value": nnz * args.steps / (ms_graph / 1e3),
-            "config": {"workload": "4096 instances, m~U[50,5000], n~U[20,500], k in {4,8,16}, even "
+            "config": {"workload": f"{wb.count} instances, m~U[50,5000], n~U[20,500], k in {{4,8,16}}, even "
                                    "quadratic (ALS, FP64 Cholesky), odd Huber (prox-grad), 30% missing, "
                                    "gamma=0.1, FP32", "nnz": nnz, "generate_s": gen_s},
             "ms_per_sweep": {"graph": ms_graph / args.steps, "stream": ms_stream / args.steps,
@@ -511,7 +684,7 @@ def run_form(args):
                          "tensor_frac_of_bf16": (flops_pass / (per[top] / 1e3) / 1e12) / tc if tc else None}})
         g.close()
     else:
-        t = W.completion()
+        t = W.completion(m=args.form_rows) if args.form_rows else W.completion()
         res = {}
         for name, prec in (("fp32", G.GLRM_FP32), ("bf16", G.GLRM_BF16)):
             g = G.GLRM.from_table(t, precision=prec, stream=st)
@@ -528,7 +701,7 @@ def run_form(args):
             g.close()
         line.update({"metric": METRIC, "unit": UNIT, "value": res["bf16"]["value"],
                      "dtype": "bf16 gathers, fp32 accumulation and re-evaluation",
-                     "config": {"workload": "matrix completion m=1e6 n=20000 k=64, 200 entries "
+                     "config": {"workload": f"matrix completion m={t.m} n=20000 k=64, 200 entries "
                                             "per row, quadratic loss, gamma=0.05", "nnz": t.nnz},
                      "forms": res})
     print(json.dumps(line), flush=True)

@@ -401,6 +401,14 @@ int glrm_tc_gemm_bf16(const void *A_dev, const void *B_dev, float *D_dev, int32_
  * attempts < 1. */
 int glrm_wait_selftest(int64_t attempts, int32_t arm, void *stream);
 
+/* FP32 FMA throughput of the current device (not part of the method; the
+ * denominator of the CUDA-core roofline): a kernel whose threads each run 8
+ * independent chains of `iters` fmaf (iters a multiple of 16, >= 16), at full
+ * occupancy on every SM, timed with CUDA events over 5 launches after a
+ * warm-up.  *tflops_host receives 2 x FMAs / time in TFLOP/s, *sms_host
+ * (nullable) the SM count read from the device.  Synchronises. */
+int glrm_fma_peak(int32_t iters, double *tflops_host, int32_t *sms_host, void *stream);
+
 /* Instrumentation (not part of the method).  glrm_timing_enable(h, 1)
  * records a CUDA event on the handle's stream before every kernel the handle
  * launches and after the last one, so each kernel's device time is measured

@@ -48,6 +48,7 @@ void free_orient(Orient &o, cudaStream_t st)
     dfree(o.val, st);
     dfree(o.chunks, st);
     dfree(o.segchunk, st);
+    dfree(o.order, st);
     dfree(o.runptr, st);
     dfree(o.perm, st);
     dfree(o.tptr, st);
@@ -333,6 +334,24 @@ void build_chunks(const std::vector<int32_t> &ptr, std::vector<int4> &chunks,
     segchunk[nseg] = (int32_t)chunks.size();
 }
 
+// Launch order of the chunked passes when the other factor does not stay in
+// L2: chunk q of every segment before chunk q + 1 of any.  Within a segment
+// the entries are sorted by the other index, so on tables whose segments
+// spread alike over the other dimension (uniform sampling) the warps running
+// at one time gather rows from one band of the other factor, which then
+// stays in L2 instead of being read from HBM once per entry.
+std::vector<int32_t> chunk_order(const std::vector<int4> &chunks, const std::vector<int32_t> &segchunk)
+{
+    std::vector<int32_t> ord(chunks.size());
+    std::vector<int32_t> rank(chunks.size());
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        ord[c] = (int32_t)c;
+        rank[c] = (int32_t)c - segchunk[chunks[c].x];
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return rank[a] < rank[b]; });
+    return ord;
+}
+
 // Number of partial slots an orientation's passes write (chunks, or
 // panels x segments when blocked).
 int64_t partial_slots(const Orient &o)
@@ -568,7 +587,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         return GLRM_OK;
     };
     // chunk table of one orientation, host-built from its validated pointer array
-    auto chunk_table = [&](Orient &o, cudaStream_t s) -> int {
+    auto chunk_table = [&](Orient &o, int64_t nother, cudaStream_t s) -> int {
         std::vector<int32_t> ptr(o.nseg + 1);
         CK(cudaMemcpyAsync(ptr.data(), o.ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -582,6 +601,12 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
             CK(cudaMemcpyAsync(o.chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(o.segchunk, segchunk.data(), segchunk.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                            s));
+        std::vector<int32_t> ord;
+        if ((double)nother * h->k * (double)es > kBandBytes && !chunks.empty()) {
+            ord = chunk_order(chunks, segchunk);
+            CK(dalloc_on(h, &o.order, ord.size() * sizeof(int32_t), s));
+            CK(cudaMemcpyAsync(o.order, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        }
         CK(cudaStreamSynchronize(s));  // the host tables go out of scope
         return GLRM_OK;
     };
@@ -594,7 +619,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
         if (rc == GLRM_OK) rc = check(0, au);
     }
-    if (rc == GLRM_OK && hf[0] == 0) rc = chunk_table(R, au);
+    if (rc == GLRM_OK && hf[0] == 0) rc = chunk_table(R, h->n, au);
     // the dense table needs the CSR arrays only: built here too when it will be chosen
     float *preA = nullptr;
     if (rc == GLRM_OK && hf[0] == 0 && dense_choice(h) == 1) {
@@ -641,7 +666,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         return fail(h, code, (hflag & 8) && !(hflag & ~8) ? "non-finite value in the observed set"
                                                         : flag_message(hflag));
     }
-    if ((rc = chunk_table(C, st)) != GLRM_OK) {
+    if ((rc = chunk_table(C, h->m, st)) != GLRM_OK) {
         if (preA) cudaFreeAsync(preA, st);
         return rc;
     }

@@ -68,7 +68,10 @@ bf16_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
     const int lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (c >= nchunks) return;
-    const int gl = lane % G, grp = lane / G, c0 = gl * S;
+    // f and the gathered rows share one lane layout: FP32 units (4 values)
+    // for the exact refresh, BF16 units (8 values) otherwise
+    constexpr int VW = MODE == kBfExact ? 4 : 8;
+    const int gl = lane % G, grp = lane / G;
     const int4 ch = chunks[c];
     if constexpr (MODE == kBfUpdate) {
         if (!accepted[ch.x]) return;
@@ -82,12 +85,12 @@ bf16_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
     float f[S], g[S];
     if constexpr (MODE == kBfLoss) {
         float fp[S];
-        load_slice<float, S, VEC>(f, F + (int64_t)ch.x * k, c0, k);
-        load_slice<float, S, VEC>(fp, cand + (int64_t)ch.x * k, c0, k);
+        load_lane<float, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
+        load_lane<float, S, G, VW, VEC>(fp, cand + (int64_t)ch.x * k, gl, k);
 #pragma unroll
         for (int s = 0; s < S; ++s) f[s] = fp[s] - f[s];  // the step
     } else {
-        load_slice<float, S, VEC>(f, F + (int64_t)ch.x * k, c0, k);
+        load_lane<float, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) g[s] = 0.f;
@@ -103,8 +106,8 @@ bf16_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
         if (ok) {
             j = __ldg(idx + e);
             a = __ldg(val + e);
-            if constexpr (MODE == kBfExact) load_slice<float, S, VEC>(w, W + (int64_t)j * k, c0, k);
-            else load_slice_bf16<S, VEC>(w, Wb + (int64_t)j * k, c0, k);
+            if constexpr (MODE == kBfExact) load_lane<float, S, G, VW, VEC>(w, W + (int64_t)j * k, gl, k);
+            else load_lane_bf16<S, G, VEC>(w, Wb + (int64_t)j * k, gl, k);
         } else {
 #pragma unroll
             for (int s = 0; s < S; ++s) w[s] = 0.f;
@@ -148,7 +151,7 @@ bf16_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
         if (grp == 0) {
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                if (c0 + s < k) part_grad[c * k + c0 + s] = g[s];
+                if (slot_coord<S, G, VW, VEC>(s, gl) < k) part_grad[c * k + slot_coord<S, G, VW, VEC>(s, gl)] = g[s];
         }
     }
     const double ls = warp_sum((double)lsum);

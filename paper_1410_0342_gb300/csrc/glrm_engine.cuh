@@ -33,18 +33,60 @@ struct Lanes {
     static constexpr int PER = 32 / G;  // entries per warp iteration
 };
 
-// Coordinates c0 .. c0+S-1 of a BF16 row (the BF16 copy of the other factor
-// in the BF16 form), widened to FP32.
-template <int S, bool VEC>
-__device__ __forceinline__ void load_slice_bf16(float (&v)[S], const __nv_bfloat16 *__restrict__ row,
-                                                int c0, int k)
+// Lane layout of an entry's k coordinates over the G lanes that share it.
+// The vector form cuts a row into 16-byte units of VW coordinates (VW = 4
+// FP32, 2 FP64, 8 BF16 values) and gives lane gl units gl, G + gl, 2G + gl,
+// ...: at every load instruction the G lanes of an entry read G adjacent
+// units, whole 32-byte sectors of the row, so each sector is fetched once.
+// Slot s of lane gl holds coordinate VW ((s / VW) G + gl) + s % VW.  The
+// scalar form (any k) gives lane gl the contiguous coordinates gl S .. gl S + S - 1.
+template <int S, int G, int VW, bool VEC>
+__device__ __forceinline__ int slot_coord(int s, int gl)
+{
+    return VEC ? VW * ((s / VW) * G + gl) + s % VW : gl * S + s;
+}
+
+// A row's slots for lane gl in the layout above (T values, units of VW).
+template <class T, int S, int G, int VW, bool VEC>
+__device__ __forceinline__ void load_lane(T (&v)[S], const T *__restrict__ row, int gl, int k)
 {
     if constexpr (VEC) {
-        static_assert(S % 8 == 0, "bf16 slice must be a multiple of 8");
-        const uint4 *p = reinterpret_cast<const uint4 *>(row + c0);
+        constexpr int VT = 16 / (int)sizeof(T);  // values per 16-byte load
+        static_assert(S % VW == 0 && VW % VT == 0, "slots must be whole units");
+#pragma unroll
+        for (int q = 0; q < S / VW; ++q) {
+#pragma unroll
+            for (int h = 0; h < VW / VT; ++h) {
+                const T *src = row + VW * (q * G + gl) + VT * h;
+                if constexpr (sizeof(T) == 4) {
+                    const float4 t = __ldg(reinterpret_cast<const float4 *>(src));
+                    v[q * VW + VT * h + 0] = t.x;
+                    v[q * VW + VT * h + 1] = t.y;
+                    v[q * VW + VT * h + 2] = t.z;
+                    v[q * VW + VT * h + 3] = t.w;
+                } else {
+                    const double2 t = __ldg(reinterpret_cast<const double2 *>(src));
+                    v[q * VW + VT * h + 0] = t.x;
+                    v[q * VW + VT * h + 1] = t.y;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) v[s] = (gl * S + s < k) ? __ldg(row + gl * S + s) : T(0);
+    }
+}
+
+// The same for a BF16 row (units of 8 values), widened to FP32.
+template <int S, int G, bool VEC>
+__device__ __forceinline__ void load_lane_bf16(float (&v)[S], const __nv_bfloat16 *__restrict__ row, int gl,
+                                               int k)
+{
+    if constexpr (VEC) {
+        static_assert(S % 8 == 0, "bf16 slots must be whole units");
 #pragma unroll
         for (int q = 0; q < S / 8; ++q) {
-            const uint4 t = __ldg(p + q);
+            const uint4 t = __ldg(reinterpret_cast<const uint4 *>(row + 8 * (q * G + gl)));
             const uint32_t w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -54,33 +96,43 @@ __device__ __forceinline__ void load_slice_bf16(float (&v)[S], const __nv_bfloat
         }
     } else {
 #pragma unroll
-        for (int s = 0; s < S; ++s) v[s] = (c0 + s < k) ? __bfloat162float(row[c0 + s]) : 0.f;
+        for (int s = 0; s < S; ++s) v[s] = (gl * S + s < k) ? __bfloat162float(row[gl * S + s]) : 0.f;
     }
 }
 
-template <class T, int S, bool VEC, class WT>
-__device__ __forceinline__ void load_w(T (&v)[S], const WT *__restrict__ row, int c0, int k)
+// Coordinates per 16-byte unit of a row of type WT.
+template <class WT>
+constexpr int unit_of() { return 16 / (int)sizeof(WT); }
+
+template <class T, int S, int G, bool VEC, class WT>
+__device__ __forceinline__ void load_lane_w(T (&v)[S], const WT *__restrict__ row, int gl, int k)
 {
-    if constexpr (std::is_same<WT, __nv_bfloat16>::value) load_slice_bf16<S, VEC>(v, row, c0, k);
-    else load_slice<T, S, VEC>(v, row, c0, k);
+    if constexpr (std::is_same<WT, __nv_bfloat16>::value) load_lane_bf16<S, G, VEC>(v, row, gl, k);
+    else load_lane<T, S, G, unit_of<WT>(), VEC>(v, row, gl, k);
 }
 
+// One warp per chunk: entries base + grp for base = begin, begin + PER, ...
+// (G lanes per entry, PER = 32 / G entries per iteration), the rows of the
+// other factor gathered in the lane layout above.  `order` (nullable) is the
+// chunk launch order.
 template <class T, int K, bool XSTEP, bool VEC, bool GRAD, class WT = T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ idx,
-            const T *__restrict__ val, const T *__restrict__ F, const WT *__restrict__ W, int k,
-            const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
+pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ order,
+            const int32_t *__restrict__ idx, const T *__restrict__ val, const T *__restrict__ F,
+            const WT *__restrict__ W, int k, const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
             double *__restrict__ part_loss)
 {
     using LN = Lanes<K>;
     constexpr int G = LN::G, S = LN::S, PER = LN::PER;
+    constexpr int VW = unit_of<WT>();  // f and the gathered rows share the layout of WT's units
     const int lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (c >= nchunks) return;  // the whole warp leaves together
-    const int gl = lane % G, grp = lane / G, c0 = gl * S;
+    const int64_t lin = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (lin >= nchunks) return;  // the whole warp leaves together
+    const int64_t c = order ? (int64_t)__ldg(order + lin) : lin;
+    const int gl = lane % G, grp = lane / G;
     const int4 ch = chunks[c];
     T f[S], g[S];
-    load_slice<T, S, VEC>(f, F + (int64_t)ch.x * k, c0, k);
+    load_lane<T, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
 #pragma unroll
     for (int s = 0; s < S; ++s) g[s] = T(0);
     T lsum = T(0);
@@ -95,7 +147,7 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
         if (ok) {
             j = __ldg(idx + e);
             a = __ldg(val + e);
-            load_w<T, S, VEC, WT>(w, W + (int64_t)j * k, c0, k);
+            load_lane_w<T, S, G, VEC, WT>(w, W + (int64_t)j * k, gl, k);
         } else {
 #pragma unroll
             for (int s = 0; s < S; ++s) w[s] = T(0);
@@ -124,8 +176,10 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
         }
         if (grp == 0) {
 #pragma unroll
-            for (int s = 0; s < S; ++s)
-                if (c0 + s < k) part_grad[c * k + c0 + s] = g[s];
+            for (int s = 0; s < S; ++s) {
+                const int cc = slot_coord<S, G, VW, VEC>(s, gl);
+                if (cc < k) part_grad[c * k + cc] = g[s];
+            }
         }
     }
     const double ls = warp_sum((double)lsum);
@@ -366,14 +420,14 @@ cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const L
     const unsigned nb = blocks_for(o.nchunks, kWarpsPerBlock);
     if constexpr (std::is_same<WT, __nv_bfloat16>::value && Lanes<K>::S % 8 != 0) {
         pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-            o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+            o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
     } else {
         if (vec)
             pass_kernel<T, K, XSTEP, true, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-                o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
         else
             pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-                o.nchunks, o.chunks, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
     }
     return cudaGetLastError();
 }

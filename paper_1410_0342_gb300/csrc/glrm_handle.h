@@ -23,6 +23,9 @@ constexpr int kStreamWarps = 8;  // warps per CTA of the staged (fused / blocked
 constexpr int kMaskedWarps = 16;   // warps per CTA of the masked-tile kernels
 constexpr int kRingSlotsHost = 8;  // value-stream ring slots per warp (masked kernels)
 constexpr int kRingBytes = 1024;   // bytes per ring slot
+// Other factors larger than this are walked band by band by the chunked
+// passes (chunk launch order, see chunk_order) so that they stay in L2.
+constexpr double kBandBytes = 32.0 * 1024 * 1024;
 
 // How a half-step runs over one orientation (chosen at set-up):
 // chunked: entries cut into chunks, the other factor gathered from global
@@ -42,6 +45,7 @@ struct Orient {
     void *val = nullptr;          // nnz values, element type of the model
     int4 *chunks = nullptr;       // {segment, begin, end, 0}
     int32_t *segchunk = nullptr;  // nseg + 1: first chunk of each segment
+    int32_t *order = nullptr;     // nchunks: launch order of the chunks (null: chunk order)
     int64_t nchunks = 0;
     int32_t maxlen = 0;
     int mode = kModeChunked;

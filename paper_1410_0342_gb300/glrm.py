@@ -78,6 +78,7 @@ def _load():
         "glrm_batch_autotune": [p, i32, p, p],
         "glrm_tc_gemm_bf16": [p, p, p, i32, i32, i32, p],
         "glrm_wait_selftest": [i64, i32, p],
+        "glrm_fma_peak": [i32, p, p, p],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -334,6 +335,17 @@ def glrm_wait_selftest(attempts, arm, stream=None):
     if stream is None:
         stream = torch.cuda.current_stream()
     _check(_lib.glrm_wait_selftest(int(attempts), int(bool(arm)), ctypes.c_void_p(stream.cuda_stream)))
+
+
+def glrm_fma_peak(iters=8192, stream=None):
+    """(FP32 FMA TFLOP/s measured on the current device, SM count)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    tf = ctypes.c_double(0.0)
+    sms = ctypes.c_int32(0)
+    _check(_lib.glrm_fma_peak(int(iters), ctypes.byref(tf), ctypes.byref(sms),
+                              ctypes.c_void_p(stream.cuda_stream)))
+    return tf.value, sms.value
 
 
 def glrm_destroy(h):
