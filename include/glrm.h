@@ -193,22 +193,25 @@ int glrm_sweep(glrm_t h, int32_t nsweeps, double *history_host);
 
 /* Sweeps until a convergence test on the device passes (Section 7.2; the
  * objective of eq. gpca never increases under the step-size rule, so its
- * decrease is the natural stopping signal).  After every sweep the FP64
- * objective F_t is compared on the GPU:
- *   f_ref is NaN:  stop when F_{t-1} - F_t <= rtol |F_t|  (relative decrease;
+ * decrease is the natural stopping signal; the paper leaves the stopping
+ * condition open).  After every sweep t the FP64 objective F_t is compared on
+ * the GPU:
+ *   f_ref is NaN:  stop when t >= window and
+ *                  F_{t-window} - F_t <= window * rtol * |F_t|
+ *                  (average relative decrease over the last `window` sweeps;
  *                  F_0 is the objective before the first sweep)
  *   otherwise:     stop when F_t - f_ref <= rtol |f_ref|   (within rtol of a
  *                  reference objective, e.g. a known optimum)
- * or after max_sweeps sweeps (>= 1).  rtol >= 0.  FP32 and FP64 models run
- * the whole loop as one launch of a CUDA graph whose conditional WHILE node
- * repeats a captured sweep and its check (captured on the first call and
- * kept until the buffers or kernel paths change); the BF16 form, which keeps
- * host-side state between sweeps, reads the device's decision back after
- * each sweep.  *sweeps_host receives the number of sweeps run; history_host,
- * if not NULL, receives their objectives (max_sweeps doubles of room).  Each
- * sweep is exactly the sweep of glrm_sweep, so the results equal those of
- * glrm_sweep(h, *sweeps_host, ...).  Synchronises. */
-int glrm_sweep_until(glrm_t h, int32_t max_sweeps, double rtol, double f_ref,
+ * or after max_sweeps sweeps (>= 1).  rtol >= 0, window >= 1.  FP32 and FP64
+ * models run the whole loop as one launch of a CUDA graph whose conditional
+ * WHILE node repeats a captured sweep and its check (captured on the first
+ * call and kept until the buffers or kernel paths change); the BF16 form,
+ * which keeps host-side state between sweeps, reads the device's decision back
+ * after each sweep.  *sweeps_host receives the number of sweeps run;
+ * history_host, if not NULL, receives their objectives (max_sweeps doubles of
+ * room).  Each sweep is exactly the sweep of glrm_sweep, so the results equal
+ * those of glrm_sweep(h, *sweeps_host, ...).  Synchronises. */
+int glrm_sweep_until(glrm_t h, int32_t max_sweeps, double rtol, double f_ref, int32_t window,
                      int32_t *sweeps_host, double *history_host);
 
 /* Accepted row and column steps of the last sweep run (host, 2 values);
@@ -328,10 +331,16 @@ int glrm_get_path(glrm_t h, int32_t *paths_host);
  * gamma ||.||^2 on both factors, by alternating minimisation (Algorithm 1 with
  * the row / column problems of Section 2.4 solved exactly: Gram matrix of the
  * observed entries in FP32, k x k Cholesky factorisation and solves in FP64).
- * A sweep of the batch runs every instance's X-step in one launch, every
- * Y-step in a second and the per-instance objectives in a third; with
- * GLRM_BATCH_GRAPH the nsweeps sweeps are captured once into a CUDA graph and
- * replayed with one graph launch.  k must be 4, 8 or 16 (FP32). */
+ * All nsweeps sweeps of a call run in one persistent launch: its warps take
+ * work items from a device queue -- for each sweep every instance's X-step
+ * items (an instance and a range of its rows), then the Y-step items, then one
+ * objective item per instance -- and per-instance completion counters order
+ * them (an instance's Y-step after its X-step, its objective after its Y-step,
+ * its next X-step after its objective).  Each dependency wait is bounded
+ * (glrm_batch_set_wait_limit); a wait that runs out makes the call return
+ * GLRM_ERR_TIMEOUT.  With GLRM_BATCH_GRAPH the launch (and the counter reset
+ * before it) is captured once into a CUDA graph and replayed.  k must be 4, 8
+ * or 16 (FP32). */
 typedef struct glrm_batch_s *glrm_batch_t;
 enum { GLRM_BATCH_PROXGRAD = 0, GLRM_BATCH_ALS = 1 };
 /* sweep modes: graph replay, plain launches on the stream, and one launch per
@@ -366,8 +375,21 @@ int glrm_batch_set_steps(glrm_batch_t b, const float *ax_dev, const float *ay_de
 int glrm_batch_get_steps(glrm_batch_t b, float *ax_dev, float *ay_dev);
 /* nsweeps sweeps of every instance; objectives_host, if not NULL, receives
  * nsweeps x count doubles (sweep-major), the objective of each instance after
- * each sweep, and the call synchronises. */
+ * each sweep, and the call synchronises and reports the device status:
+ * GLRM_ERR_TIMEOUT when a dependency wait ran out (results invalid),
+ * GLRM_ERR_NONFINITE when an ALS system was not numerically positive definite
+ * (those rows / columns kept their factor).  Modes: GLRM_BATCH_GRAPH and
+ * GLRM_BATCH_STREAM make the one queue launch (replayed from a graph, or
+ * enqueued directly); GLRM_BATCH_PER_INSTANCE, for comparison, launches the
+ * same kernel once per instance and half-step, and once per sweep for the
+ * objectives. */
 int glrm_batch_sweep(glrm_batch_t b, int32_t nsweeps, double *objectives_host, int32_t mode);
+/* The number of polls (about 0.1 us each) a work item may spend waiting for
+ * the items it depends on before it gives up and raises GLRM_ERR_TIMEOUT
+ * (default 2^24).  Waits normally end within the run time of one item; a
+ * small limit makes them run out on purpose (a test of the expiry path), 0
+ * lets an item proceed only if its dependencies are already complete. */
+int glrm_batch_set_wait_limit(glrm_batch_t b, int64_t polls);
 /* Autotuner: for every bucket of instances (k, method, entries per row or
  * column class) and each half-step, times the half-step kernel on that
  * bucket's instances with 1, 2, 4 and 8 rows (columns) per work item and keeps

@@ -397,7 +397,7 @@ int alloc_scratch(glrm_s *h)
     CK(dalloc(h, &s.scalar, sizeof(double)));
     CK(dalloc(h, &s.err, sizeof(int)));
     CK(dalloc(h, &s.conv, 2 * sizeof(double)));
-    CK(dalloc(h, &s.conv_par, 3 * sizeof(double)));
+    CK(dalloc(h, &s.conv_par, 4 * sizeof(double)));
     CK(dalloc(h, &s.conv_cnt, 3 * sizeof(int)));
     if (h->prec == GLRM_BF16) {
         CK(dalloc(h, &s.x_bf16, (size_t)h->m * h->k * sizeof(__nv_bfloat16)));
@@ -819,27 +819,37 @@ void tmark(glrm_s *h, const char *name)
 namespace glrm {
 
 // Convergence check after a sweep of glrm_sweep_until, one thread, FP64:
-// append the sweep's objective F (conv[1]) to the history and stop when
-//   use_ref:  F - F_ref <= rtol |F_ref|       (within rtol of a reference)
-//   else:     F_prev - F <= rtol |F|          (relative decrease of the sweep)
+// append the sweep's objective F_t (conv[1]) to the history and stop when
+//   use_ref:  F_t - F_ref <= rtol |F_ref|            (within rtol of a reference)
+//   else:     F_{t-w} - F_t <= w rtol |F_t|, t >= w   (average relative decrease
+//             over the last w sweeps; F_0 = conv[0], the objective at the start)
 // or when the sweep limit is reached.  Stopping clears the condition of the
 // enclosing WHILE graph node (graph mode) and sets the stop flag cnt[2].
+// par = {rtol, F_ref, use_ref, w}; cnt = {sweeps run, sweep limit, stop flag}.
 __global__ void converge_check_kernel(cudaGraphConditionalHandle cond, int graph, const double *__restrict__ par,
-                                      double *__restrict__ conv, int *__restrict__ cnt, double *__restrict__ hist)
+                                      const double *__restrict__ conv, int *__restrict__ cnt,
+                                      double *__restrict__ hist)
 {
     const double F = conv[1];
-    const int t = cnt[0];
-    hist[t] = F;
-    cnt[0] = t + 1;
+    const int t = cnt[0] + 1;
+    hist[t - 1] = F;
+    cnt[0] = t;
     const double rtol = par[0], fref = par[1];
-    const bool done = par[2] != 0.0 ? (F - fref <= rtol * fabs(fref)) : (conv[0] - F <= rtol * fabs(F));
-    conv[0] = F;
-    if (done || t + 1 >= cnt[1]) {
+    const int w = (int)par[3];
+    bool done;
+    if (par[2] != 0.0) {
+        done = F - fref <= rtol * fabs(fref);
+    } else if (t >= w) {
+        const double Fw = t == w ? conv[0] : hist[t - w - 1];
+        done = Fw - F <= (double)w * rtol * fabs(F);
+    } else {
+        done = false;
+    }
+    if (done || t >= cnt[1]) {
         cnt[2] = 1;
         if (graph) cudaGraphSetConditional(cond, 0);
     }
 }
-
 }  // namespace glrm
 
 namespace {
@@ -1102,17 +1112,18 @@ int glrm_sweep(glrm_t h, int32_t nsweeps, double *history)
     return GLRM_OK;
 }
 
-int glrm_sweep_until(glrm_t h, int32_t max_sweeps, double rtol, double f_ref, int32_t *sweeps_host,
-                     double *history_host)
+int glrm_sweep_until(glrm_t h, int32_t max_sweeps, double rtol, double f_ref, int32_t window,
+                     int32_t *sweeps_host, double *history_host)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_sweep_until before glrm_set_observed");
-    if (max_sweeps < 1 || !(rtol >= 0.0) || !sweeps_host) return fail(h, GLRM_ERR_ARG, "bad arguments");
+    if (max_sweeps < 1 || !(rtol >= 0.0) || window < 1 || !sweeps_host)
+        return fail(h, GLRM_ERR_ARG, "bad arguments");
     DeviceGuard dg(h->device);
     int rc = ensure_hist(h, max_sweeps);
     if (rc != GLRM_OK) return rc;
     const bool use_ref = !std::isnan(f_ref);
-    const double par[3] = {rtol, use_ref ? f_ref : 0.0, use_ref ? 1.0 : 0.0};
+    const double par[4] = {rtol, use_ref ? f_ref : 0.0, use_ref ? 1.0 : 0.0, (double)window};
     const int cnt[3] = {0, max_sweeps, 0};
     CK(cudaMemcpyAsync(h->s.conv_par, par, sizeof par, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->s.conv_cnt, cnt, sizeof cnt, cudaMemcpyHostToDevice, h->stream));

@@ -1,4 +1,4 @@
-// Batched form: many independent GLRMs of uneven size in one set of launches.
+// Batched form: many independent GLRMs of uneven size fitted together.
 //
 // Every instance is a GLRM of its own (eq. gpca) with one loss for all its
 // columns and quadratic / l1 / nonnegativity / zero regularisers, fitted
@@ -8,14 +8,22 @@
 // minimisation (Algorithm 1, rows and columns solved exactly as in Section 2.4
 // with the Gram matrix of each row's / column's observed entries, Section 2.5).
 //
-// A sweep of the whole batch is three launches: every instance's X-step, every
-// instance's Y-step, the per-instance objectives.  The work of a half-step is a
-// list of items (instance, range of rows or columns) built at set-up; a warp
-// takes items in turn and runs each row (column) of its item to completion
-// (gradient, prox, re-evaluation, decision; or Gram, FP64 Cholesky, solve).
+// All the sweeps of a call run in ONE persistent launch.  Its warps take work
+// items from a device queue (an atomic counter): for every sweep t, the
+// X-step items (instance, range of rows), then the Y-step items (instance,
+// range of columns), then one objective item per instance.  A warp runs each
+// row (column) of its item to completion (gradient, prox, re-evaluation,
+// decision; or Gram, FP64 Cholesky, solve).  Per-instance completion counters
+// order the work: a Y-step item waits until every X-step item of its
+// instance in that sweep is done, an objective item until every Y-step item
+// is, and the next sweep's X-step items until the objective is.  An item is
+// only ever waiting for items handed out before it, which are held by warps
+// that are already running and never wait for a later item, so every wait
+// ends; each wait is bounded all the same (a host-set number of polls), and
+// on expiry the warp raises the error flag and carries on without the work.
 // Items are as many rows / columns as the autotuned table says for the
-// instance's (k, method, segment-length) bucket, and are ordered by decreasing
-// work.  T sweeps are captured once into a CUDA graph and replayed.
+// instance's (k, method, segment-length) bucket, ordered by decreasing work
+// or grouped by instance.  The launch is captured once into a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,6 +75,13 @@ struct glrm_batch_s {
     int hist_cap = 0;
     int4 *items_x = nullptr, *items_y = nullptr;
     int64_t nitems_x = 0, nitems_y = 0;
+    int32_t *need_x = nullptr, *need_y = nullptr;  // per instance: its items in items_x / items_y
+    int32_t *obj_inst = nullptr;                   // 0 .. count - 1
+    unsigned long long *qhead = nullptr;           // the queue's next item
+    int32_t *done = nullptr;                       // 3 x count completion counters (X, Y, objective)
+    int *status = nullptr;                         // device status word (kErrWait, kErrPivot bits)
+    long long wait_limit = 1LL << 24;              // polls a dependency wait may take
+    int qgrid = 0;                                 // CTAs of a full queue launch (all resident)
     std::vector<int64_t> inst_items_x, inst_items_y;  // first item of each instance (unbatched mode)
     int32_t tile_x[kBucketCount], tile_y[kBucketCount];
     int order_x = 0, order_y = 0;  // 0: items by decreasing work; 1: grouped by instance
@@ -171,13 +186,14 @@ __device__ void pg_segment(const Seg &g, const LossSpec &sp, int64_t s)
     const double lold = warp_sum((double)lsum);
     const float al = g.alpha[s];
     float fp[K];
-    double rold = 0.0, rnew = 0.0;
+    float rof = 0.f, rnf = 0.f;  // regulariser terms in FP32, combined with the losses in FP64
 #pragma unroll
     for (int c = 0; c < K; ++c) {
         fp[c] = prox1<float>(g.rk, g.rw, al, f[c] - al * gr[c]);
-        rold += reg1<float>(g.rk, g.rw, f[c]);
-        rnew += reg1<float>(g.rk, g.rw, fp[c]);
+        rof += reg1<float>(g.rk, g.rw, f[c]);
+        rnf += reg1<float>(g.rk, g.rw, fp[c]);
     }
+    const double rold = (double)rof, rnew = (double)rnf;
     float lsum2 = 0.f;
     for (int q = b + lane; q < e; q += 32) {
         float w[K];
@@ -203,28 +219,93 @@ __device__ void pg_segment(const Seg &g, const LossSpec &sp, int64_t s)
 }
 
 struct AlsSmem {
-    float w[32][kBK + 1];
-    float a[32];
-    double G[kBK][kBK + 1];
-    double rhs[kBK];
+    float w[32][kBK + 1];   // staged rows of the other factor, one per lane
+    float a[32];            // their values
+    double G[2 * kBK * (kBK + 1)];  // per lane group: its k x (k + 1) system (32 / k groups)
+    double rhs[32];                 // per lane group: its k right-hand side values
 };
 
-// One row (column) of an ALS instance, whole warp:
-// (sum_e w_e w_e^T + gamma I) f = sum_e a_e w_e, Gram in FP32, factor and
-// solves in FP64.  With `objective` the segment's loss sum at the solution is
-// computed (Y-step: the column's share of the objective).
+// Sum over the K lanes of a lane group (K a power of two, groups aligned).
+template <int K, class T>
+__device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int o = K / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (C C^T) x = b for the k x k system of every lane group at once: G (row
+// stride K + 1) and b in shared memory, lane lr of the group owns row lr.
+// The same column-by-column scheme as warp_cholesky_solve (FP64 throughout,
+// reciprocal square roots by rsqrt_fp64, the trailing update's pairs spread
+// over the group's lanes), but each FP64 instruction serves 32 / K systems.
+// Returns (to every lane of the group) false when a pivot was not positive,
+// finite and normal.
 template <int K>
-__device__ void als_segment(const Seg &g, double gamma, int64_t s, AlsSmem &sm, bool objective)
+__device__ bool group_cholesky_solve(double *G, double *b)
+{
+    constexpr int LD = K + 1;
+    const int lane = threadIdx.x & 31, lr = lane % K;
+    bool ok = true;
+    for (int c = 0; c < K; ++c) {
+        if (lr == 0) {
+            double r;
+            ok = rsqrt_fp64(G[c * LD + c], r) && ok;
+            G[c * LD + c] = r;  // the pivot slot keeps 1/C[c][c] from here on
+        }
+        __syncwarp();
+        const double r = G[c * LD + c];
+        if (lr > c) G[lr * LD + c] *= r;
+        __syncwarp();
+        const int n = K - 1 - c;
+        for (int p = lr; p < n * (n + 1) / 2; p += K) {
+            int i = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+            while ((i + 1) * (i + 2) / 2 <= p) ++i;
+            while (i * (i + 1) / 2 > p) --i;
+            const int row = c + 1 + i, col = c + 1 + p - i * (i + 1) / 2;
+            G[row * LD + col] -= G[row * LD + c] * G[col * LD + c];
+        }
+        __syncwarp();
+    }
+    for (int c = 0; c < K; ++c) {
+        if (lr == 0) b[c] *= G[c * LD + c];
+        __syncwarp();
+        if (lr > c) b[lr] -= G[lr * LD + c] * b[c];
+        __syncwarp();
+    }
+    for (int c = K - 1; c >= 0; --c) {
+        if (lr == 0) b[c] *= G[c * LD + c];
+        __syncwarp();
+        if (lr < c) b[lr] -= G[c * LD + lr] * b[c];
+        __syncwarp();
+    }
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, lane - lr) != 0;
+}
+
+// Up to 32 / K rows (columns) s_begin + grp of an ALS instance at once, one
+// lane group of K lanes each: (sum_e w_e w_e^T + gamma I) f = sum_e a_e w_e,
+// Gram in FP32 (lane lr accumulates entries lr, lr + K, ... of the lower
+// triangle), factor and solves in FP64.  With `objective` the segment's loss
+// sum at the solution is computed (Y-step: the column's share of the
+// objective).  A system whose factorisation fails keeps its old factor and
+// raises kErrPivot.
+template <int K>
+__device__ void als_group(const Seg &g, double gamma, int64_t s_begin, int64_t s_end, AlsSmem &sm,
+                          bool objective, int *err)
 {
     constexpr int N = K * (K + 1) / 2;
-    constexpr int NP = (N + 31) / 32;
-    const int lane = threadIdx.x & 31;
-    const int b = g.ptr[s], e = g.ptr[s + 1];
-    int rq[NP], cq[NP];
-    float acc[NP];
+    constexpr int NQ = (N + K - 1) / K;
+    constexpr int LD = K + 1;
+    const int lane = threadIdx.x & 31, grp = lane / K, lr = lane % K;
+    const int64_t s = s_begin + grp;
+    const bool active = s < s_end;
+    const int b = active ? g.ptr[s] : 0, e = active ? g.ptr[s + 1] : 0;
+    const int len = e - b;
+    int rq[NQ], cq[NQ];
+    float acc[NQ];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        int p = lane + 32 * q;
+    for (int q = 0; q < NQ; ++q) {
+        int p = lr + K * q;
         if (p >= N) p = 0;
         int r = 0;
         while ((r + 1) * (r + 2) / 2 <= p) ++r;
@@ -233,9 +314,12 @@ __device__ void als_segment(const Seg &g, double gamma, int64_t s, AlsSmem &sm, 
         acc[q] = 0.f;
     }
     float bacc = 0.f;
-    for (int base = b; base < e; base += 32) {
-        const int q0 = base + lane;
-        if (q0 < e) {
+    int maxlen = len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    for (int base = 0; base < maxlen; base += K) {
+        if (base + lr < len) {
+            const int q0 = b + base + lr;
             float w[K];
             bload<K>(w, g.W + (int64_t)__ldg(g.idx + q0) * K);
 #pragma unroll
@@ -243,112 +327,197 @@ __device__ void als_segment(const Seg &g, double gamma, int64_t s, AlsSmem &sm, 
             sm.a[lane] = __ldg(g.val + q0);
         }
         __syncwarp();
-        const int cnt = min(32, e - base);
+        const int cnt = min(K, len - base);
         for (int t = 0; t < cnt; ++t) {
+            const float *wr = sm.w[grp * K + t];
 #pragma unroll
-            for (int q = 0; q < NP; ++q) acc[q] = fmaf(sm.w[t][rq[q]], sm.w[t][cq[q]], acc[q]);
-            if (lane < K) bacc = fmaf(sm.a[t], sm.w[t][lane], bacc);
+            for (int q = 0; q < NQ; ++q) acc[q] = fmaf(wr[rq[q]], wr[cq[q]], acc[q]);
+            bacc = fmaf(sm.a[grp * K + t], wr[lr], bacc);
         }
         __syncwarp();
     }
+    double *G = sm.G + grp * K * LD;
+    double *rhs = sm.rhs + grp * K;
 #pragma unroll
-    for (int q = 0; q < NP; ++q)
-        if (lane + 32 * q < N) sm.G[rq[q]][cq[q]] = (double)acc[q] + (rq[q] == cq[q] ? gamma : 0.0);
-    if (lane < K) sm.rhs[lane] = (double)bacc;
+    for (int q = 0; q < NQ; ++q)
+        if (lr + K * q < N) G[rq[q] * LD + cq[q]] = (double)acc[q] + (rq[q] == cq[q] ? gamma : 0.0);
+    rhs[lr] = (double)bacc;
     __syncwarp();
-    warp_cholesky_solve<K, kBK + 1>(sm.G, sm.rhs);
+    const bool solved = group_cholesky_solve<K>(G, rhs);
+    // lane lr holds coordinate lr of the solution (of the old factor when the
+    // factorisation failed); the regulariser's terms once per coordinate
+    const float fl = active ? (solved ? (float)rhs[lr] : g.F[s * K + lr]) : 0.f;
+    const double reg = group_sum<K>(gamma * (double)fl * (double)fl);
+    if (active && !solved && lr == 0) atomicOr(err, kErrPivot);
     float f[K];
-    double reg = 0.0;
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-        f[c] = (float)sm.rhs[c];
-        reg += gamma * (double)f[c] * (double)f[c];
-    }
-    if (lane < K) g.F[s * K + lane] = f[lane];
+    for (int c = 0; c < K; ++c) f[c] = __shfl_sync(0xffffffffu, fl, grp * K + c);
+    if (active && solved) g.F[s * K + lr] = fl;
     double lsum = 0.0;
     if (objective) {
         float ls = 0.f;
-        for (int q = b + lane; q < e; q += 32) {
+        for (int q = b + lr; q < e; q += K) {
             float w[K];
             bload<K>(w, g.W + (int64_t)__ldg(g.idx + q) * K);
             const float r = bdot<K>(f, w) - __ldg(g.val + q);
             ls = fmaf(r, r, ls);
         }
-        lsum = warp_sum((double)ls);
+        lsum = group_sum<K>((double)ls);
     }
     __syncwarp();
-    if (lane == 0) {
+    if (active && lr == 0) {
         g.kobj[s] = lsum + reg;
         g.kreg[s] = reg;
         g.acc[s] = 1;
     }
 }
 
-template <bool XSTEP>
-__global__ void __launch_bounds__(kBWarps * 32)
-batch_half_kernel(const BInst *__restrict__ inst, const int4 *__restrict__ items, int64_t nitems,
-                  const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                  const float *__restrict__ val, const int32_t *__restrict__ colptr,
-                  const int32_t *__restrict__ rowidx, const float *__restrict__ cval, float *X, float *Yt,
-                  float *ax, float *ay, double *kobj_x, double *kreg_x, int32_t *acc_x, double *kobj_y,
-                  double *kreg_y, int32_t *acc_y)
+// Everything one launch of the queue kernel needs.  The queue holds, for
+// each sweep t = t0 .. t0 + sweeps - 1, nx X-step items, ny Y-step items and
+// no objective items (instance numbers); item q of the launch is sweep
+// t0 + q / (nx + ny + no), position q % (nx + ny + no).  With wait == 0 the
+// dependency waits are skipped (a launch that times one phase on its own).
+struct BQueue {
+    const BInst *inst;
+    const int4 *items_x, *items_y;
+    const int32_t *obj_inst;
+    int64_t nx, ny, no;
+    const int32_t *need_x, *need_y;  // per instance: its X- / Y-step items in a full sweep
+    int t0, sweeps, count, wait;
+    unsigned long long *head;        // the queue's next item
+    int32_t *done_x, *done_y, *done_o;  // per instance, counted over all sweeps of the call
+    int *err;
+    long long limit;                 // polls a wait may take
+    double *hist;                    // objectives, sweep-major (sweep t at t * count)
+    const int32_t *rowptr, *colidx, *colptr, *rowidx;
+    const float *val, *cval;
+    float *X, *Yt, *ax, *ay;
+    double *kobj_x, *kreg_x, *kobj_y, *kreg_y;
+    int32_t *acc_x, *acc_y;
+};
+
+__device__ __forceinline__ int load_acquire(const int32_t *p)
 {
-    __shared__ AlsSmem als[kBWarps];
-    const int wid = threadIdx.x >> 5;
-    const int64_t nw = (int64_t)gridDim.x * kBWarps;
-    for (int64_t q = (int64_t)blockIdx.x * kBWarps + wid; q < nitems; q += nw) {
-        const int4 it = items[q];
-        const BInst &I = inst[it.x];
-        Seg g;
-        if (XSTEP) {
-            g = Seg{rowptr + I.rp_off, colidx + I.e_off, val + I.e_off, X + I.x_off, Yt + I.y_off,
-                    ax + I.row_base, kobj_x + I.row_base, kreg_x + I.row_base, acc_x + I.row_base,
-                    I.rxk, (float)I.rxw};
-        } else {
-            g = Seg{colptr + I.cp_off, rowidx + I.e_off, cval + I.e_off, Yt + I.y_off, X + I.x_off,
-                    ay + I.col_base, kobj_y + I.col_base, kreg_y + I.col_base, acc_y + I.col_base,
-                    I.ryk, (float)I.ryw};
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Whole warp: wait until *ctr >= target (lane 0 polls, at most `limit`
+// times, and gives up at once when the error flag is up).  True when the
+// condition holds; the writes counted by *ctr are then visible to every lane.
+__device__ bool warp_wait_count(const int32_t *ctr, int target, long long limit, int *err)
+{
+    const int lane = threadIdx.x & 31;
+    int ok = 1;
+    if (lane == 0) {
+        long long it = 0;
+        while (load_acquire(ctr) < target) {
+            if (it++ >= limit || *(volatile int *)err) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
         }
-        const LossSpec sp{I.kind, I.levels, I.param};
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __threadfence();
+    __syncwarp();
+    return ok != 0;
+}
+
+// Whole warp: publish the warp's writes, then count one finished item.
+__device__ __forceinline__ void warp_done(int32_t *ctr)
+{
+    __threadfence();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) atomicAdd(ctr, 1);
+}
+
+template <bool XSTEP>
+__device__ void run_item(const BQueue &Q, const int4 &it, AlsSmem &als)
+{
+    const BInst &I = Q.inst[it.x];
+    Seg g;
+    if (XSTEP) {
+        g = Seg{Q.rowptr + I.rp_off, Q.colidx + I.e_off, Q.val + I.e_off, Q.X + I.x_off, Q.Yt + I.y_off,
+                Q.ax + I.row_base, Q.kobj_x + I.row_base, Q.kreg_x + I.row_base, Q.acc_x + I.row_base,
+                I.rxk, (float)I.rxw};
+    } else {
+        g = Seg{Q.colptr + I.cp_off, Q.rowidx + I.e_off, Q.cval + I.e_off, Q.Yt + I.y_off, Q.X + I.x_off,
+                Q.ay + I.col_base, Q.kobj_y + I.col_base, Q.kreg_y + I.col_base, Q.acc_y + I.col_base,
+                I.ryk, (float)I.ryw};
+    }
+    const LossSpec sp{I.kind, I.levels, I.param};
+    if (I.method == GLRM_BATCH_ALS) {
+        // 32 / k rows (columns) at a time, one lane group each
+        const int spw = 32 / I.k;
+        for (int64_t s = it.y; s < it.z; s += spw) {
+            switch (I.k) {
+            case 4: als_group<4>(g, I.rxw, s, it.z, als, !XSTEP, Q.err); break;
+            case 8: als_group<8>(g, I.rxw, s, it.z, als, !XSTEP, Q.err); break;
+            default: als_group<16>(g, I.rxw, s, it.z, als, !XSTEP, Q.err); break;
+            }
+        }
+    } else {
         for (int64_t s = it.y; s < it.z; ++s) {
-            if (I.method == GLRM_BATCH_ALS) {
-                switch (I.k) {
-                case 4: als_segment<4>(g, I.rxw, s, als[wid], !XSTEP); break;
-                case 8: als_segment<8>(g, I.rxw, s, als[wid], !XSTEP); break;
-                default: als_segment<16>(g, I.rxw, s, als[wid], !XSTEP); break;
-                }
-            } else {
-                switch (I.k) {
-                case 4: pg_segment<4>(g, sp, s); break;
-                case 8: pg_segment<8>(g, sp, s); break;
-                default: pg_segment<16>(g, sp, s); break;
-                }
+            switch (I.k) {
+            case 4: pg_segment<4>(g, sp, s); break;
+            case 8: pg_segment<8>(g, sp, s); break;
+            default: pg_segment<16>(g, sp, s); break;
             }
         }
     }
 }
 
-// Per-instance objective: the Y-step's kept column objectives (every loss
-// term plus rt(y_j)) plus the X-step's kept r(x_i); one block per instance,
-// fixed summation order.
-__global__ void __launch_bounds__(256)
-batch_objective_kernel(const BInst *__restrict__ inst, int count, const double *__restrict__ kobj_y,
-                       const double *__restrict__ kreg_x, double *__restrict__ out)
+// Objective of instance s after a sweep: the Y-step's kept column objectives
+// (every loss term plus rt(y_j)) plus the X-step's kept r(x_i), one warp,
+// lane-strided sums and a butterfly: a fixed order.
+__device__ double instance_objective(const BQueue &Q, int s)
 {
-    __shared__ double sh[256];
-    for (int s = blockIdx.x; s < count; s += gridDim.x) {
-        const BInst &I = inst[s];
-        double v = 0.0;
-        for (int64_t j = threadIdx.x; j < I.n; j += 256) v += kobj_y[I.col_base + j];
-        for (int64_t i = threadIdx.x; i < I.m; i += 256) v += kreg_x[I.row_base + i];
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-            __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const BInst &I = Q.inst[s];
+    double v = 0.0;
+    for (int64_t j = lane; j < I.n; j += 32) v += Q.kobj_y[I.col_base + j];
+    for (int64_t i = lane; i < I.m; i += 32) v += Q.kreg_x[I.row_base + i];
+    return warp_sum(v);
+}
+
+__global__ void __launch_bounds__(kBWarps * 32)
+batch_queue_kernel(const BQueue Q)
+{
+    __shared__ AlsSmem als[kBWarps];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t per = Q.nx + Q.ny + Q.no;
+    const unsigned long long total = (unsigned long long)per * (unsigned long long)Q.sweeps;
+    for (;;) {
+        unsigned long long q = 0;
+        if (lane == 0) q = atomicAdd(Q.head, 1ULL);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= total) break;  // warp-uniform
+        const int t = Q.t0 + (int)(q / (unsigned long long)per);
+        const int64_t r = (int64_t)(q % (unsigned long long)per);
+        if (r < Q.nx) {
+            const int4 it = Q.items_x[r];
+            // the previous sweep's objective of the instance (which follows its Y-step) is in
+            const bool ok = !Q.wait || warp_wait_count(Q.done_o + it.x, t, Q.limit, Q.err);
+            if (ok) run_item<true>(Q, it, als[wid]);
+            else if (lane == 0) atomicOr(Q.err, kErrWait);
+            warp_done(Q.done_x + it.x);
+        } else if (r < Q.nx + Q.ny) {
+            const int4 it = Q.items_y[r - Q.nx];
+            const bool ok = !Q.wait || warp_wait_count(Q.done_x + it.x, (t + 1) * Q.need_x[it.x], Q.limit, Q.err);
+            if (ok) run_item<false>(Q, it, als[wid]);
+            else if (lane == 0) atomicOr(Q.err, kErrWait);
+            warp_done(Q.done_y + it.x);
+        } else {
+            const int s = Q.obj_inst[r - Q.nx - Q.ny];
+            const bool ok = !Q.wait || warp_wait_count(Q.done_y + s, (t + 1) * Q.need_y[s], Q.limit, Q.err);
+            const double v = ok ? instance_objective(Q, s) : (double)NAN;
+            if (!ok && lane == 0) atomicOr(Q.err, kErrWait);
+            if (lane == 0) Q.hist[(int64_t)t * Q.count + s] = v;
+            warp_done(Q.done_o + s);
         }
-        if (threadIdx.x == 0) out[s] = sh[0];
-        __syncthreads();
     }
 }
 
@@ -502,6 +671,11 @@ int upload_items(glrm_batch_s *b)
     BCK(cudaMemcpy(b->items_y, iy.data(), iy.size() * sizeof(int4), cudaMemcpyHostToDevice));
     b->nitems_x = (int64_t)ix.size();
     b->nitems_y = (int64_t)iy.size();
+    std::vector<int32_t> nx((size_t)b->count, 0), ny((size_t)b->count, 0);
+    for (const int4 &it : ix) nx[it.x]++;
+    for (const int4 &it : iy) ny[it.x]++;
+    BCK(cudaMemcpy(b->need_x, nx.data(), nx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->need_y, ny.data(), ny.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -510,33 +684,71 @@ int upload_items(glrm_batch_s *b)
     return GLRM_OK;
 }
 
-cudaError_t launch_half(glrm_batch_s *b, bool xstep, const int4 *items, int64_t n, cudaStream_t st)
+// One launch of the queue kernel over the given lists (sweeps t0 ..
+// t0 + sweeps - 1); the queue head is reset first.  A full launch uses the
+// persistent grid, a small one no more CTAs than it has items for.
+cudaError_t launch_queue(glrm_batch_s *b, const int4 *ix, int64_t nx, const int4 *iy, int64_t ny, int64_t no,
+                         int t0, int sweeps, int wait, cudaStream_t st)
 {
-    if (n == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<int64_t>(b->grid, (n + kBWarps - 1) / kBWarps);
-    if (xstep)
-        batch_half_kernel<true><<<grid, kBWarps * 32, 0, st>>>(
-            b->inst, items, n, b->rowptr, b->colidx, b->val, b->colptr, b->rowidx, b->cval, b->X,
-            b->Yt, b->ax, b->ay, b->kept_obj_x, b->kept_reg_x, b->acc_x, b->kept_obj_y, b->kept_reg_y,
-            b->acc_y);
-    else
-        batch_half_kernel<false><<<grid, kBWarps * 32, 0, st>>>(
-            b->inst, items, n, b->rowptr, b->colidx, b->val, b->colptr, b->rowidx, b->cval, b->X,
-            b->Yt, b->ax, b->ay, b->kept_obj_x, b->kept_reg_x, b->acc_x, b->kept_obj_y, b->kept_reg_y,
-            b->acc_y);
+    const int64_t total = (nx + ny + no) * sweeps;
+    if (total == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(b->qhead, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    BQueue Q;
+    Q.inst = b->inst;
+    Q.items_x = ix;
+    Q.items_y = iy;
+    Q.obj_inst = b->obj_inst;
+    Q.nx = nx;
+    Q.ny = ny;
+    Q.no = no;
+    Q.need_x = b->need_x;
+    Q.need_y = b->need_y;
+    Q.t0 = t0;
+    Q.sweeps = sweeps;
+    Q.count = b->count;
+    Q.wait = wait;
+    Q.head = b->qhead;
+    Q.done_x = b->done;
+    Q.done_y = b->done + b->count;
+    Q.done_o = b->done + 2 * (size_t)b->count;
+    Q.err = b->status;
+    Q.limit = b->wait_limit;
+    Q.hist = b->hist;
+    Q.rowptr = b->rowptr;
+    Q.colidx = b->colidx;
+    Q.colptr = b->colptr;
+    Q.rowidx = b->rowidx;
+    Q.val = b->val;
+    Q.cval = b->cval;
+    Q.X = b->X;
+    Q.Yt = b->Yt;
+    Q.ax = b->ax;
+    Q.ay = b->ay;
+    Q.kobj_x = b->kept_obj_x;
+    Q.kreg_x = b->kept_reg_x;
+    Q.kobj_y = b->kept_obj_y;
+    Q.kreg_y = b->kept_reg_y;
+    Q.acc_x = b->acc_x;
+    Q.acc_y = b->acc_y;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(b->qgrid, (total + kBWarps - 1) / kBWarps));
+    batch_queue_kernel<<<grid, kBWarps * 32, 0, st>>>(Q);
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_sweep(glrm_batch_s *b, double *hist_slot, cudaStream_t st)
+// A half-step on its own (autotuning): no dependency waits.
+cudaError_t launch_half(glrm_batch_s *b, bool xstep, const int4 *items, int64_t n, cudaStream_t st)
 {
-    cudaError_t e = launch_half(b, true, b->items_x, b->nitems_x, st);
-    if (e == cudaSuccess) e = launch_half(b, false, b->items_y, b->nitems_y, st);
-    if (e == cudaSuccess) {
-        batch_objective_kernel<<<std::min(b->count, 4096), 256, 0, st>>>(b->inst, b->count, b->kept_obj_y,
-                                                                          b->kept_reg_x, hist_slot);
-        e = cudaGetLastError();
-    }
-    return e;
+    return xstep ? launch_queue(b, items, n, nullptr, 0, 0, 0, 1, 0, st)
+                 : launch_queue(b, nullptr, 0, items, n, 0, 0, 1, 0, st);
+}
+
+// Every sweep of a call in one launch, after the completion counters are reset.
+cudaError_t enqueue_sweeps(glrm_batch_s *b, int nsweeps, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(b->done, 0, 3 * sizeof(int32_t) * (size_t)b->count, st);
+    if (e != cudaSuccess) return e;
+    return launch_queue(b, b->items_x, b->nitems_x, b->items_y, b->nitems_y, b->count, 0, nsweeps, 1, st);
 }
 
 }  // namespace
@@ -618,7 +830,9 @@ int glrm_batch_create(int32_t count, const glrm_batch_instance *ih, const int32_
     BCK(cudaGetDevice(&b->device));
     int sms = 0;
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    b->grid = sms * 4;
+    int per_sm = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_queue_kernel, kBWarps * 32, 0));
+    b->qgrid = sms * std::max(per_sm, 1);
     BCK(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
     cudaStream_t st = b->stream;
     const size_t nz = (size_t)std::max<int64_t>(e, 1);
@@ -639,6 +853,19 @@ int glrm_batch_create(int32_t count, const glrm_batch_instance *ih, const int32_
     BCK(cudaMalloc(&b->kept_reg_y, sizeof(double) * cb));
     BCK(cudaMalloc(&b->acc_x, sizeof(int32_t) * rb));
     BCK(cudaMalloc(&b->acc_y, sizeof(int32_t) * cb));
+    BCK(cudaMalloc(&b->need_x, sizeof(int32_t) * count));
+    BCK(cudaMalloc(&b->need_y, sizeof(int32_t) * count));
+    BCK(cudaMalloc(&b->obj_inst, sizeof(int32_t) * count));
+    BCK(cudaMalloc(&b->qhead, sizeof(unsigned long long)));
+    BCK(cudaMalloc(&b->done, 3 * sizeof(int32_t) * count));
+    BCK(cudaMalloc(&b->status, sizeof(int)));
+    BCK(cudaMemsetAsync(b->status, 0, sizeof(int), st));
+    {
+        std::vector<int32_t> ids((size_t)count);
+        for (int q = 0; q < count; ++q) ids[q] = q;
+        BCK(cudaMemcpyAsync(b->obj_inst, ids.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+        BCK(cudaStreamSynchronize(st));
+    }
     BCK(cudaMemcpyAsync(b->inst, in.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, st));
     BCK(cudaMemcpyAsync(b->rowptr, rowptr, sizeof(int32_t) * rp, cudaMemcpyDeviceToDevice, st));
     BCK(cudaMemcpyAsync(b->colptr, colptr, sizeof(int32_t) * cp, cudaMemcpyDeviceToDevice, st));
@@ -738,34 +965,32 @@ int glrm_batch_sweep(glrm_batch_t b, int32_t nsweeps, double *objectives, int32_
     }
     cudaStream_t st = b->stream;
     if (mode == GLRM_BATCH_GRAPH) {
+        // the counter reset and the one queue launch, captured once per sweep count
         if (!b->graph || b->graph_sweeps != nsweeps) {
             if (b->graph) cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
             cudaGraph_t g = nullptr;
             BCK(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = cudaSuccess;
-            for (int t = 0; t < nsweeps && e == cudaSuccess; ++t)
-                e = enqueue_sweep(b, b->hist + (size_t)t * b->count, b->capture);
-            cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
+            const cudaError_t e = enqueue_sweeps(b, nsweeps, b->capture);
+            const cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
                 return bfail(b, GLRM_ERR_CUDA, std::string("graph capture: ") +
                                                    cudaGetErrorString(e != cudaSuccess ? e : e2));
             }
-            e = cudaGraphInstantiate(&b->graph, g, 0);
+            const cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
             cudaGraphDestroy(g);
-            if (e != cudaSuccess) return bfail(b, GLRM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            if (e3 != cudaSuccess)
+                return bfail(b, GLRM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
             b->graph_sweeps = nsweeps;
         }
         BCK(cudaGraphLaunch(b->graph, st));
     } else if (mode == GLRM_BATCH_STREAM) {
-        for (int t = 0; t < nsweeps; ++t) {
-            cudaError_t e = enqueue_sweep(b, b->hist + (size_t)t * b->count, st);
-            if (e != cudaSuccess) return bfail(b, GLRM_ERR_CUDA, cudaGetErrorString(e));
-        }
+        const cudaError_t e = enqueue_sweeps(b, nsweeps, st);
+        if (e != cudaSuccess) return bfail(b, GLRM_ERR_CUDA, cudaGetErrorString(e));
     } else {
-        // one launch per instance and half-step: the same kernels over each
-        // instance's items alone
+        // for comparison: one launch per instance and half-step (the same
+        // kernel over each instance's items alone) and one for the objectives
         std::vector<int4> ix, iy;
         std::vector<int64_t> fx, fy;
         build_items(b, true, b->tile_x, nullptr, ix, &fx);
@@ -775,17 +1000,13 @@ int glrm_batch_sweep(glrm_batch_t b, int32_t nsweeps, double *objectives, int32_
         BCK(cudaMalloc(&dy, std::max<size_t>(1, iy.size()) * sizeof(int4)));
         BCK(cudaMemcpy(dx, ix.data(), ix.size() * sizeof(int4), cudaMemcpyHostToDevice));
         BCK(cudaMemcpy(dy, iy.data(), iy.size() * sizeof(int4), cudaMemcpyHostToDevice));
-        cudaError_t e = cudaSuccess;
+        cudaError_t e = cudaMemsetAsync(b->done, 0, 3 * sizeof(int32_t) * (size_t)b->count, st);
         for (int t = 0; t < nsweeps && e == cudaSuccess; ++t) {
             for (int s = 0; s < b->count && e == cudaSuccess; ++s)
-                e = launch_half(b, true, dx + fx[s], fx[s + 1] - fx[s], st);
+                e = launch_queue(b, dx + fx[s], fx[s + 1] - fx[s], nullptr, 0, 0, t, 1, 1, st);
             for (int s = 0; s < b->count && e == cudaSuccess; ++s)
-                e = launch_half(b, false, dy + fy[s], fy[s + 1] - fy[s], st);
-            if (e == cudaSuccess) {
-                batch_objective_kernel<<<std::min(b->count, 4096), 256, 0, st>>>(
-                    b->inst, b->count, b->kept_obj_y, b->kept_reg_x, b->hist + (size_t)t * b->count);
-                e = cudaGetLastError();
-            }
+                e = launch_queue(b, nullptr, 0, dy + fy[s], fy[s + 1] - fy[s], 0, t, 1, 1, st);
+            if (e == cudaSuccess) e = launch_queue(b, nullptr, 0, nullptr, 0, b->count, t, 1, 1, st);
         }
         cudaStreamSynchronize(st);
         cudaFree(dx);
@@ -795,7 +1016,30 @@ int glrm_batch_sweep(glrm_batch_t b, int32_t nsweeps, double *objectives, int32_
     if (objectives) {
         BCK(cudaMemcpyAsync(objectives, b->hist, sizeof(double) * (size_t)nsweeps * b->count,
                             cudaMemcpyDeviceToHost, st));
+        int flag = 0;
+        BCK(cudaMemcpyAsync(&flag, b->status, sizeof(int), cudaMemcpyDeviceToHost, st));
         BCK(cudaStreamSynchronize(st));
+        if (flag) {
+            BCK(cudaMemsetAsync(b->status, 0, sizeof(int), st));
+            if (flag & kErrWait)
+                return bfail(b, GLRM_ERR_TIMEOUT, "a work item's wait for the items it depends on ran past "
+                                                  "its limit; results of this call are invalid");
+            return bfail(b, GLRM_ERR_NONFINITE, "an ALS row or column system was not numerically positive "
+                                                "definite; those rows or columns kept their previous factor");
+        }
+    }
+    return GLRM_OK;
+}
+
+int glrm_batch_set_wait_limit(glrm_batch_t b, int64_t polls)
+{
+    if (!b) return bfail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (polls < 0) return bfail(b, GLRM_ERR_ARG, "polls < 0");
+    b->wait_limit = polls;
+    if (b->graph) {  // the limit is a kernel argument: capture again
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_sweeps = 0;
     }
     return GLRM_OK;
 }
@@ -926,6 +1170,12 @@ void glrm_batch_destroy(glrm_batch_t b)
     bfree(b->hist);
     bfree(b->items_x);
     bfree(b->items_y);
+    bfree(b->need_x);
+    bfree(b->need_y);
+    bfree(b->obj_inst);
+    bfree(b->qhead);
+    bfree(b->done);
+    bfree(b->status);
     delete b;
 }
 

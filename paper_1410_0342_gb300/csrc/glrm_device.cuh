@@ -218,11 +218,14 @@ __device__ __forceinline__ bool rsqrt_fp64(double d, double &y)
 // Solve (C C^T) x = b in place for an SPD matrix G (row-major, leading
 // dimension LD, lower triangle used; overwritten by C) and right-hand side b
 // (overwritten by x), one warp, K <= 32.  Column by column: lane 0 takes the
-// pivot's reciprocal square root, lanes below it scale and update; the two
-// triangular solves are column-oriented too, so every step is one pass of the
-// warp.  FP64 throughout.  Returns (to every lane) false when a pivot was not
-// positive, finite and normal: G was not numerically positive definite (or
-// held Inf / NaN); b then holds no solution and must not be used.
+// pivot's reciprocal square root, lanes below it scale the column, and the
+// trailing update's (row, column) pairs are spread over all 32 lanes (an
+// FP64 instruction costs the same issue time however few lanes it has, and
+// FP64 runs at 1/64 of the FP32 rate here, so no lane should sit idle in
+// it); the two triangular solves are column-oriented.  FP64 throughout.
+// Returns (to every lane) false when a pivot was not positive, finite and
+// normal: G was not numerically positive definite (or held Inf / NaN); b
+// then holds no solution and must not be used.
 template <int K, int LD>
 __device__ __forceinline__ bool warp_cholesky_solve(double (*G)[LD], double *b)
 {
@@ -238,8 +241,15 @@ __device__ __forceinline__ bool warp_cholesky_solve(double (*G)[LD], double *b)
         const double r = G[c][c];
         if (lane > c && lane < K) G[lane][c] *= r;
         __syncwarp();
-        if (lane > c && lane < K)
-            for (int q = c + 1; q <= lane; ++q) G[lane][q] -= G[lane][c] * G[q][c];
+        // pairs (c + 1 + i, c + 1 + j), 0 <= j <= i < n, numbered p = i (i + 1) / 2 + j
+        const int n = K - 1 - c;
+        for (int p = lane; p < n * (n + 1) / 2; p += 32) {
+            int i = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+            while ((i + 1) * (i + 2) / 2 <= p) ++i;
+            while (i * (i + 1) / 2 > p) --i;
+            const int row = c + 1 + i, col = c + 1 + p - i * (i + 1) / 2;
+            G[row][col] -= G[row][c] * G[col][c];
+        }
         __syncwarp();
     }
     // C w = b: w[c] = b[c] / C[c][c], then b[r] -= C[r][c] w[c] for r > c

@@ -53,7 +53,7 @@ def _load():
         "glrm_get_factors_host": [p, p, p],
         "glrm_reset_steps": [p],
         "glrm_sweep": [p, i32, p],
-        "glrm_sweep_until": [p, i32, f64, f64, p, p],
+        "glrm_sweep_until": [p, i32, f64, f64, i32, p, p],
         "glrm_last_accepts": [p, p],
         "glrm_objective": [p, p],
         "glrm_objective_at": [p, p, p, p],
@@ -76,6 +76,7 @@ def _load():
         "glrm_batch_get_steps": [p, p, p],
         "glrm_batch_sweep": [p, i32, p, i32],
         "glrm_batch_autotune": [p, i32, p, p],
+        "glrm_batch_set_wait_limit": [p, i64],
         "glrm_tc_gemm_bf16": [p, p, p, i32, i32, i32, p],
         "glrm_wait_selftest": [i64, i32, p],
         "glrm_fma_peak": [i32, p, p, p],
@@ -209,13 +210,13 @@ def glrm_sweep(h, nsweeps, history=True):
     return None
 
 
-def glrm_sweep_until(h, max_sweeps, rtol, f_ref=float("nan")):
+def glrm_sweep_until(h, max_sweeps, rtol, f_ref=float("nan"), window=1):
     """Sweeps until the device-side convergence test passes; returns the
     objectives of the sweeps run (numpy float64)."""
     ran = ctypes.c_int32(0)
     out = np.empty(max_sweeps, dtype=np.float64)
-    _check(_lib.glrm_sweep_until(h, int(max_sweeps), float(rtol), float(f_ref), ctypes.byref(ran),
-                                 _ptr(out)), h)
+    _check(_lib.glrm_sweep_until(h, int(max_sweeps), float(rtol), float(f_ref), int(window),
+                                 ctypes.byref(ran), _ptr(out)), h)
     return out[:ran.value].copy()
 
 
@@ -427,6 +428,9 @@ class Batch:
     def set_steps(self, ax, ay):
         _bcheck(_lib.glrm_batch_set_steps(self.b, _ptr(ax), _ptr(ay)), self.b)
 
+    def set_wait_limit(self, polls):
+        _bcheck(_lib.glrm_batch_set_wait_limit(self.b, int(polls)), self.b)
+
     def autotune(self, reps=3):
         tx = np.zeros(32, np.int32)
         ty = np.zeros(32, np.int32)
@@ -517,8 +521,8 @@ class GLRM:
     def sweep(self, nsweeps, history=True):
         return glrm_sweep(self.h, nsweeps, history)
 
-    def sweep_until(self, max_sweeps, rtol, f_ref=float("nan")):
-        return glrm_sweep_until(self.h, max_sweeps, rtol, f_ref)
+    def sweep_until(self, max_sweeps, rtol, f_ref=float("nan"), window=1):
+        return glrm_sweep_until(self.h, max_sweeps, rtol, f_ref, window)
 
     def als_sweep(self, nsweeps, history=True):
         return glrm_als_sweep(self.h, nsweeps, history)

@@ -170,3 +170,35 @@ def test_batch_validation(G):
     with pytest.raises(G.GLRMError) as e:
         G.Batch(bad2, meth)
     assert e.value.code == G.GLRM_ERR_OMEGA
+
+
+def test_wait_limit_expiry_returns_timeout(G, oracle_mod):
+    """The one-launch queue: with a wait limit of 0 polls, an item whose
+    dependencies are not complete when it is taken gives up at once.  The
+    Y-step items are handed out while the X-step items of their instances
+    still run (the GPU holds thousands of warps and the batch a few hundred
+    items), so the call returns GLRM_ERR_TIMEOUT, and does not hang.  With the
+    default limit, batches fit normally and the graph and stream modes agree
+    bit for bit."""
+    wb = small_batch(count=64, m_range=(50, 400))
+    meth = methods_of(wb, G)
+    B = G.Batch(wb, meth)
+    B.set_wait_limit(0)
+    timed_out = False
+    for _ in range(5):
+        B.set_factors(wb.X0, wb.Yt0)
+        try:
+            B.sweep(3, mode=G.GLRM_BATCH_STREAM)
+        except G.GLRMError as e:
+            assert e.code == G.GLRM_ERR_TIMEOUT, e
+            timed_out = True
+            break
+    assert timed_out
+    B.close()
+    B1 = G.Batch(wb, meth)
+    B1.set_wait_limit(1 << 24)
+    h1 = B1.sweep(3, mode=G.GLRM_BATCH_GRAPH)
+    B2 = G.Batch(wb, meth)
+    h2 = B2.sweep(3, mode=G.GLRM_BATCH_STREAM)
+    np.testing.assert_array_equal(h1, h2)
+    assert np.isfinite(h1).all()

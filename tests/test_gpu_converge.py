@@ -21,27 +21,27 @@ def G():
     return glrm
 
 
-def first_rel_decrease(F0, hist, rtol):
-    prev = F0
-    for t, f in enumerate(hist):
-        if prev - f <= rtol * abs(f):
-            return t + 1
-        prev = f
+def first_rel_decrease(F0, hist, rtol, w):
+    """First sweep t >= w with F_{t-w} - F_t <= w rtol |F_t| (F_0 = F0)."""
+    F = np.concatenate([[F0], hist])
+    for t in range(w, len(F)):
+        if F[t - w] - F[t] <= w * rtol * abs(F[t]):
+            return t
     return None
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "bf16"])
-def test_relative_decrease_stop(G, prec):
+@pytest.mark.parametrize("prec,window", [("fp32", 1), ("fp64", 1), ("bf16", 1), ("fp32", 5)])
+def test_relative_decrease_stop(G, prec, window):
     t = W.small_mixed(m=3000, n=120, k=8, p_obs=0.5, seed=17, rx=(1, 0.1), ry=(2, 0.02))
     P = {"fp32": G.GLRM_FP32, "fp64": G.GLRM_FP64, "bf16": G.GLRM_BF16}[prec]
     ref = G.GLRM.from_table(t, precision=P)
     F0 = ref.objective()
     hist_ref = ref.sweep(400)
     rtol = 1e-4
-    want = first_rel_decrease(F0, hist_ref, rtol)
+    want = first_rel_decrease(F0, hist_ref, rtol, window)
     assert want is not None and want > 3
     g = G.GLRM.from_table(t, precision=P)
-    h = g.sweep_until(400, rtol)
+    h = g.sweep_until(400, rtol, window=window)
     assert len(h) == want
     np.testing.assert_array_equal(h, hist_ref[:want])
     # a second call continues the same fit (the captured graph is replayed);
@@ -69,6 +69,7 @@ def test_sweep_limit_and_arguments(G):
     t = W.small_mixed(m=500, n=60, k=6, seed=18, rx=(1, 0.1), ry=(1, 0.1))
     g = G.GLRM.from_table(t)
     assert len(g.sweep_until(7, 0.0, -1e300)) == 7   # an unreachable reference: the limit stops it
-    with pytest.raises(G.GLRMError) as e:
-        g.sweep_until(0, 1e-4)
-    assert e.value.code == G.GLRM_ERR_ARG
+    for bad in ((0, 1e-4, 1), (5, -1.0, 1), (5, 1e-4, 0)):
+        with pytest.raises(G.GLRMError) as e:
+            g.sweep_until(bad[0], bad[1], window=bad[2])
+        assert e.value.code == G.GLRM_ERR_ARG
