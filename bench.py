@@ -661,12 +661,31 @@ def run_form(args):
                                             "missing, gamma=0.1, FP32", "nnz": t.nnz}})
     elif args.form == "dense":
         t = W.mixed_dense()
+        # the BF16 form on the same table: R W as one BF16 product per chunk
+        gb = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry,
+                    G.GLRM_BF16, dev, st)
+        gb.set_dense(torch.as_tensor(t.A, dtype=torch.float32, device=dev))
+        gb.set_factors(torch.as_tensor(t.X0, dtype=torch.float32, device=dev),
+                       torch.as_tensor(t.Yt0, dtype=torch.float32, device=dev))
+        gb.sweep(args.warmup, history=False)
+        G.glrm_timing_enable(gb.h, True)
+        ms_b = _events(torch, st, lambda: gb.sweep(args.steps, history=False))
+        kern_b = G.glrm_timing_read(gb.h)
+        G.glrm_timing_enable(gb.h, False)
+        hb = gb.sweep(1)
+        gb.close()
         g = G.GLRM.from_dense_table(t, stream=st)
         g.sweep(args.warmup, history=False)
         G.glrm_timing_enable(g.h, True)
         ms = _events(torch, st, lambda: g.sweep(args.steps, history=False))
         kern = G.glrm_timing_read(g.h)
         G.glrm_timing_enable(g.h, False)
+        hf = g.sweep(1)
+        line["bf16"] = {"ms_per_step": ms_b / args.steps, "objective_after": float(hb[-1]),
+                        "fp32_objective_after": float(hf[-1]),
+                        "kernels_ms": {k: v[0] / v[1] for k, v in kern_b.items()},
+                        "what": "GLRM_BF16 model: gradient contraction R W as one BF16 tensor-core product "
+                                "(FP32 accumulation); U, losses, objective and decisions at FP32 quality"}
         per = {k: v[0] / v[1] for k, v in kern.items()}
         nent = t.m * t.n
         # dominant kernel: the X-step gradient pass; algorithmic bytes = A once

@@ -18,15 +18,14 @@
  *    pointers must be aligned to their element size; 16-byte alignment lets
  *    the kernels use vector loads.
  *  - Element type of values and factors: double for GLRM_FP64, float for
- *    GLRM_FP32 and GLRM_BF16.  The BF16 form keeps FP32 factors and an FP32
- *    product u = x_i . y_j per observed entry; its passes gather BF16 copies
- *    of the other factor (FP32 accumulation), take residuals from u, and
- *    re-evaluate a candidate as u + (new - old) . y^ (y^ the BF16 row), so
- *    only the step's contribution is rounded.  u is recomputed exactly from
- *    the FP32 factors every 8 sweeps; in between, the objectives a sweep
- *    reports differ from the FP32 objective of the factors by that rounding
- *    (a few parts in 1e6 on a converging fit).  glrm_grad_at of a BF16
- *    model reads BF16 copies of both factors.
+ *    GLRM_FP32 and GLRM_BF16.  The BF16 form keeps FP32 factors; its gradient
+ *    passes gather the other factor's rows from a BF16 copy (products of
+ *    BF16 rows with FP32 accumulation, loss derivatives in FP32), except for a
+ *    row (column) whose previous step was rejected, which takes its retry's
+ *    gradient from the FP32 rows; candidates are evaluated on the FP32 rows,
+ *    so the accept / reject test and the objectives a sweep reports are
+ *    exactly those of the FP32 form.  glrm_grad_at of a BF16 model reads
+ *    BF16 copies of both factors.
  *  - All work is enqueued on the stream given to glrm_create, in order.  An
  *    entry point returns once its work is enqueued unless it says it
  *    synchronises (it must when it hands a result back in host memory).
@@ -146,8 +145,8 @@ int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host
 
 /* Give the model a fully observed table instead: Omega = every (i, j), the
  * data matrix of Section 2 with nothing missing.  A: m x n, row-major with
- * leading dimension lda >= n (elements), FP32 (GLRM_FP32 models only;
- * GLRM_ERR_ARG otherwise; GLRM_ERR_RANGE when k > 64).  The library copies A
+ * leading dimension lda >= n (elements), FP32 (GLRM_FP32 and GLRM_BF16
+ * models; GLRM_ERR_ARG otherwise; GLRM_ERR_RANGE when k > 64).  The library copies A
  * into rows padded to a multiple of 4 floats, validates it like an observed
  * set (finite values, each column's values in its loss's domain) and resets
  * the step sizes to 1/n (rows) and 1/m (columns).  Sweeps, objectives and
@@ -155,7 +154,11 @@ int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host
  * derivatives R and R Y^T, X^T R (the contractions of Section 7.2's
  * gradient) by tcgen05 MMAs on BF16 splits, FP32 accumulation: every value
  * split in three, x = hi + mid + lo, and six products summed (error about
- * 2^-25 of sum_c |x_c y_c|, FP32 quality); everything else in FP32.  glrm_als_sweep and
+ * 2^-25 of sum_c |x_c y_c|, FP32 quality); everything else in FP32.  A
+ * GLRM_BF16 model takes the gradient contraction R Y^T (X^T R) as the single
+ * product of R's and the factor's BF16 high parts (FP32 accumulation), with
+ * U, the losses, derivatives, objectives and decisions at FP32 quality as
+ * above.  glrm_als_sweep and
  * glrm_set_path return GLRM_ERR_STATE on a dense table; glrm_get_path reports
  * GLRM_PATH_DENSE.  Synchronises.  A later glrm_set_observed replaces the
  * table. */
@@ -301,8 +304,8 @@ int glrm_set_state(glrm_t h, const void *buf_host, size_t len);
  *                      half-step runs split)
  *   GLRM_PATH_DENSE    (both half-steps) the table stored densely with NaN at
  *                      the missing cells and swept by the tensor-core form of
- *                      glrm_set_dense; FP32 models with k <= 64
- * GLRM_PATH_AUTO picks dense for FP32 models with k <= 64 when at least 40% of
+ *                      glrm_set_dense; FP32 and BF16 models with k <= 64
+ * GLRM_PATH_AUTO picks dense for FP32 and BF16 models with k <= 64 when at least 40% of
  * the cells are observed (and the dense copy takes at most half the free
  * device memory); otherwise masked when a tile's pairs average >= 8 observed
  * lanes, else fused when the other factor fits, else blocked when a

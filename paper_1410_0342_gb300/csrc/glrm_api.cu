@@ -50,7 +50,6 @@ void free_orient(Orient &o, cudaStream_t st)
     dfree(o.segchunk, st);
     dfree(o.order, st);
     dfree(o.runptr, st);
-    dfree(o.perm, st);
     dfree(o.tptr, st);
     dfree(o.tidx, st);
     dfree(o.tmask, st);
@@ -74,9 +73,8 @@ void free_scratch(Scratch &s, cudaStream_t st)
     dfree(s.kept_obj_x, st); dfree(s.kept_reg_x, st); dfree(s.kept_obj_y, st); dfree(s.kept_reg_y, st);
     dfree(s.acc_x, st); dfree(s.acc_y, st); dfree(s.red_part, st); dfree(s.red_cnt, st);
     dfree(s.hist, st); dfree(s.accepts, st); dfree(s.scalar, st); dfree(s.als_part, st); dfree(s.err, st);
-    dfree(s.x_bf16, st); dfree(s.yt_bf16, st); dfree(s.u_csr, st); dfree(s.u_csc, st); dfree(s.u_new, st);
+    dfree(s.x_bf16, st); dfree(s.yt_bf16, st);
     dfree(s.conv, st); dfree(s.conv_par, st); dfree(s.conv_cnt, st);
-    s.u_sweeps = -1;
     s.hist_cap = 0;
     s.als_bytes = 0;
 }
@@ -402,18 +400,11 @@ int alloc_scratch(glrm_s *h)
     if (h->prec == GLRM_BF16) {
         CK(dalloc(h, &s.x_bf16, (size_t)h->m * h->k * sizeof(__nv_bfloat16)));
         CK(dalloc(h, &s.yt_bf16, (size_t)h->n * h->k * sizeof(__nv_bfloat16)));
-        const size_t nz = (size_t)std::max<int64_t>(h->nnz, 1);
-        CK(dalloc(h, &s.u_csr, nz * sizeof(float)));
-        CK(dalloc(h, &s.u_csc, nz * sizeof(float)));
-        CK(dalloc(h, &s.u_new, nz * sizeof(float)));
-        s.u_sweeps = -1;
-        if (h->csr.perm == nullptr && h->nnz > 0) {
-            CK(dalloc(h, &h->csr.perm, nz * sizeof(int32_t)));
-            CK(dalloc(h, &h->csc.perm, nz * sizeof(int32_t)));
-            CK(launch_perm(h->csr, h->csc, h->stream));
-            CK(launch_perm(h->csc, h->csr, h->stream));
-        }
     }
+    // every segment's previous step counts as accepted (the BF16 form's first
+    // gradients then come from its BF16 rows)
+    CK(launch_fill_i32(s.acc_x, h->m, 1, h->stream));
+    CK(launch_fill_i32(s.acc_y, h->n, 1, h->stream));
     CK(cudaMemsetAsync(s.accepts, 0, 2 * sizeof(long long), h->stream));
     CK(cudaMemsetAsync(s.err, 0, sizeof(int), h->stream));
     return GLRM_OK;
@@ -455,11 +446,12 @@ int dense_choice(glrm_s *h)
         if ((h->path_x != GLRM_PATH_DENSE && h->path_x != GLRM_PATH_AUTO) ||
             (h->path_y != GLRM_PATH_DENSE && h->path_y != GLRM_PATH_AUTO))
             return fail(h, GLRM_ERR_ARG, "the dense path runs both half-steps");
-        if (h->prec != GLRM_FP32 || !dense_supported(h->k))
-            return fail(h, GLRM_ERR_ARG, "the dense path needs an FP32 model with k <= 64");
+        if ((h->prec != GLRM_FP32 && h->prec != GLRM_BF16) || !dense_supported(h->k))
+            return fail(h, GLRM_ERR_ARG, "the dense path needs an FP32 or BF16 model with k <= 64");
         return 1;
     }
-    if (h->path_x == GLRM_PATH_AUTO && h->path_y == GLRM_PATH_AUTO && h->prec == GLRM_FP32 &&
+    if (h->path_x == GLRM_PATH_AUTO && h->path_y == GLRM_PATH_AUTO &&
+        (h->prec == GLRM_FP32 || h->prec == GLRM_BF16) &&
         dense_supported(h->k) && (double)h->nnz >= kDenseAutoDensity * (double)h->m * (double)h->n) {
         size_t free_b = 0, total_b = 0;
         CK(cudaMemGetInfo(&free_b, &total_b));
@@ -688,7 +680,8 @@ int set_dense_impl(glrm_s *h, const void *A, int64_t lda, cudaMemcpyKind kind)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (!A) return fail(h, GLRM_ERR_ARG, "null table");
-    if (h->prec != GLRM_FP32) return fail(h, GLRM_ERR_ARG, "the dense form runs on GLRM_FP32 models");
+    if (h->prec != GLRM_FP32 && h->prec != GLRM_BF16)
+        return fail(h, GLRM_ERR_ARG, "the dense form runs on GLRM_FP32 and GLRM_BF16 models");
     if (lda < h->n) return fail(h, GLRM_ERR_ARG, "lda < n");
     if (!dense_supported(h->k)) return fail(h, GLRM_ERR_RANGE, "the dense form supports k <= 64");
     DeviceGuard dg(h->device);
@@ -1033,7 +1026,6 @@ static int copy_factors(glrm_t h, void *X, void *Yt, const void *Xs, const void 
 
 int glrm_set_factors(glrm_t h, const void *X, const void *Yt)
 {
-    if (h) h->s.u_sweeps = -1;
     return h ? copy_factors(h, h->X, h->Yt, X, Yt, cudaMemcpyDeviceToDevice, false)
              : fail(nullptr, GLRM_ERR_ARG, "null handle");
 }
@@ -1047,7 +1039,6 @@ int glrm_get_factors(glrm_t h, void *X, void *Yt)
 
 int glrm_set_factors_host(glrm_t h, const void *X, const void *Yt)
 {
-    if (h) h->s.u_sweeps = -1;
     return h ? copy_factors(h, h->X, h->Yt, X, Yt, cudaMemcpyHostToDevice, true)
              : fail(nullptr, GLRM_ERR_ARG, "null handle");
 }
@@ -1253,7 +1244,6 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     DeviceGuard dg(h->device);
     int rc = ensure_hist(h, nsweeps);
     if (rc != GLRM_OK) return rc;
-    h->s.u_sweeps = -1;
     for (int t = 0; t < nsweeps; ++t) {
         cudaError_t e = h->prec == GLRM_FP64 ? Engine<double>::als_half(h, true, h->rx_w)
                                              : Engine<float>::als_half(h, true, h->rx_w);
@@ -1319,7 +1309,6 @@ int glrm_set_state(glrm_t h, const void *buf, size_t len)
         return fail(h, GLRM_ERR_ARG, "state does not match this model");
     DeviceGuard dg(h->device);
     const char *p = (const char *)buf + sizeof hdr;
-    h->s.u_sweeps = -1;
     CK(cudaMemcpyAsync(h->X, p, es * h->m * h->k, cudaMemcpyHostToDevice, h->stream));
     p += es * h->m * h->k;
     CK(cudaMemcpyAsync(h->Yt, p, es * h->n * h->k, cudaMemcpyHostToDevice, h->stream));

@@ -1,100 +1,51 @@
 // BF16 form of the proximal-gradient half-step (Section 7.2 of Udell et al.,
-// "Generalized Low Rank Models").  The rows of the other factor are gathered
-// from a BF16 copy; accuracy is kept by an exact FP32 product carried for
-// every observed entry:
+// "Generalized Low Rank Models"): factor products in BF16 where they only
+// steer the step, FP32 where they decide it.
 //
-//   u_e = x_i . y_j  (FP32), stored in CSR order and in CSC order, refreshed
-//                    exactly (FP32 gathers) every kBf16Refresh sweeps.
-//   gradient pass:   r_e = L'(u_e, a_e) from the stored exact u (FP32 residual),
-//                    g = sum r_e w^_j with w^ the BF16 row (FP32 accumulation),
-//                    f_old from L(u_e).
-//   prox:            f+ = prox(f - alpha g) in FP32.
-//   re-evaluation:   u+_e = u_e + (f+ - f) . w^_j: the BF16 rounding only touches
-//                    the step's contribution, which is small near convergence,
-//                    so the accept / reject test sees nearly FP32-exact losses.
-//   update:          for accepted segments u_e <- u+_e in both orders (the
-//                    other order through a precomputed entry permutation).
+//   gradient pass:  a segment whose previous step was accepted gathers the
+//                   rows of the other factor from its BF16 copy: u = f . w^
+//                   (BF16 rows, FP32 accumulation), r = L'(u) in FP32,
+//                   g = sum r w^ in FP32.  A segment whose previous step was
+//                   rejected takes its retry's gradient from the FP32 rows, so
+//                   near convergence, where the BF16 rounding of g would stall
+//                   the fit, the step-size rule itself switches segments to
+//                   FP32 gradients.
+//   prox:           f+ = prox(f - alpha g) in FP32.
+//   candidate pass: the FP32 rows, gathered once per entry: u_old = f . w and
+//                   u_new = f+ . w, the losses at both; the accept / reject
+//                   test and the reported objective are exactly those of the
+//                   FP32 form.
+//   decide:         as in the FP32 form, with f_old from the candidate pass.
 //
-// The gathered bytes per entry are those of BF16 rows (2k) in both passes
-// instead of FP32 rows (4k), plus 12 bytes of u traffic.
+// Gathered bytes per entry and half-step: 2k (BF16 rows) + 4k (FP32 rows)
+// for a segment on BF16 gradients, against 4k + 4k in the FP32 form.
 #pragma once
 
 #include "glrm_engine.cuh"
 
 namespace glrm {
 
-constexpr int kBf16Refresh = 8;
-
-constexpr int kBfGrad = 0, kBfLoss = 1, kBfExact = 2, kBfUpdate = 3;
-
-// CSR position -> CSC position (or back): entry (i, j) of segment i in the
-// source order is found in segment j of the other order by binary search.
-static __global__ void perm_kernel(int64_t nseg, const int32_t *__restrict__ ptr,
-                                   const int32_t *__restrict__ idx, const int32_t *__restrict__ optr,
-                                   const int32_t *__restrict__ oidx, int32_t *__restrict__ perm)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (s >= nseg) return;
-    for (int q = ptr[s] + lane; q < ptr[s + 1]; q += 32) {
-        const int j = idx[q];
-        int lo = optr[j], hi = optr[j + 1];
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (oidx[mid] < s) lo = mid + 1;
-            else hi = mid;
-        }
-        perm[q] = lo;
-    }
-}
-
-// One warp per chunk (lane groups as in the FP32 passes).  MODE:
-//   kBfGrad:   partial gradient sum L'(u) w^ and loss sum L(u), u from useg
-//   kBfLoss:   u+ = useg + (cand - F) . w^ -> unew, partial loss sum L(u+)
-//   kBfExact:  u = F . W exactly (FP32 rows) -> useg and uoth[perm]
-//   kBfUpdate: accepted segments copy unew -> useg and uoth[perm]
-template <int K, bool XSTEP, bool VEC, int MODE>
+// The candidate pass: per chunk, the losses at the segment's current factor
+// f and at its candidate f+ from one gather of each other-factor row (FP32).
+template <int K, bool XSTEP, bool VEC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-bf16_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ idx,
-                 const float *__restrict__ val, const float *__restrict__ F,
-                 const float *__restrict__ cand, const __nv_bfloat16 *__restrict__ Wb,
-                 const float *__restrict__ W, int k, const LossSpec *__restrict__ loss,
-                 float *__restrict__ useg, float *__restrict__ uoth, float *__restrict__ unew,
-                 const int32_t *__restrict__ perm, const int32_t *__restrict__ accepted,
-                 float *__restrict__ part_grad, double *__restrict__ part_loss)
+cand_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ order,
+                 const int32_t *__restrict__ idx, const float *__restrict__ val, const float *__restrict__ F,
+                 const float *__restrict__ C, const float *__restrict__ W, int k,
+                 const LossSpec *__restrict__ loss, double *__restrict__ part_old, double *__restrict__ part_new)
 {
     using LN = Lanes<K>;
-    constexpr int G = LN::G, S = LN::S, PER = LN::PER;
+    constexpr int G = LN::G, S = LN::S, PER = LN::PER, VW = 4;
     const int lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (c >= nchunks) return;
-    // f and the gathered rows share one lane layout: FP32 units (4 values)
-    // for the exact refresh, BF16 units (8 values) otherwise
-    constexpr int VW = MODE == kBfExact ? 4 : 8;
+    const int64_t lin = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (lin >= nchunks) return;
+    const int64_t c = order ? (int64_t)__ldg(order + lin) : lin;
     const int gl = lane % G, grp = lane / G;
     const int4 ch = chunks[c];
-    if constexpr (MODE == kBfUpdate) {
-        if (!accepted[ch.x]) return;
-        for (int e = ch.y + lane; e < ch.z; e += 32) {
-            const float v = unew[e];
-            useg[e] = v;
-            uoth[perm[e]] = v;
-        }
-        return;
-    }
-    float f[S], g[S];
-    if constexpr (MODE == kBfLoss) {
-        float fp[S];
-        load_lane<float, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
-        load_lane<float, S, G, VW, VEC>(fp, cand + (int64_t)ch.x * k, gl, k);
-#pragma unroll
-        for (int s = 0; s < S; ++s) f[s] = fp[s] - f[s];  // the step
-    } else {
-        load_lane<float, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
-    }
-#pragma unroll
-    for (int s = 0; s < S; ++s) g[s] = 0.f;
-    float lsum = 0.f;
+    float f[S], fp[S];
+    load_lane<float, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
+    load_lane<float, S, G, VW, VEC>(fp, C + (int64_t)ch.x * k, gl, k);
+    float lo = 0.f, ln = 0.f;
     LossSpec sp;
     if constexpr (!XSTEP) sp = loss[ch.x];
     for (int base = ch.y; base < ch.z; base += PER) {
@@ -106,120 +57,73 @@ bf16_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
         if (ok) {
             j = __ldg(idx + e);
             a = __ldg(val + e);
-            if constexpr (MODE == kBfExact) load_lane<float, S, G, VW, VEC>(w, W + (int64_t)j * k, gl, k);
-            else load_lane_bf16<S, G, VEC>(w, Wb + (int64_t)j * k, gl, k);
+            load_lane<float, S, G, VW, VEC>(w, W + (int64_t)j * k, gl, k);
         } else {
 #pragma unroll
             for (int s = 0; s < S; ++s) w[s] = 0.f;
         }
-        float u = 0.f;
-        if constexpr (MODE != kBfGrad) {
-#pragma unroll
-            for (int s = 0; s < S; ++s) u = fmaf(f[s], w[s], u);
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) u += shfl_xor(u, o);
-        }
-        if (ok) {
-            if constexpr (MODE == kBfExact) {
-                if (gl == 0) {
-                    useg[e] = u;
-                    uoth[perm[e]] = u;
-                }
-                continue;
-            }
-            if constexpr (MODE == kBfGrad) u = useg[e];
-            else u += useg[e];
-            if constexpr (XSTEP) sp = loss[j];
-            float L;
-            const float d = loss_deriv<float>(sp, u, a, L);
-            if constexpr (MODE == kBfGrad) {
-#pragma unroll
-                for (int s = 0; s < S; ++s) g[s] = fmaf(d, w[s], g[s]);
-            } else {
-                if (gl == 0) unew[e] = u;
-            }
-            if (gl == 0) lsum += L;
-        }
-    }
-    if constexpr (MODE == kBfExact) return;
-    if constexpr (MODE == kBfGrad) {
+        float u0 = 0.f, u1 = 0.f;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-#pragma unroll
-            for (int o = G; o < 32; o <<= 1) g[s] += shfl_xor(g[s], o);
+            u0 = fmaf(f[s], w[s], u0);
+            u1 = fmaf(fp[s], w[s], u1);
         }
-        if (grp == 0) {
 #pragma unroll
-            for (int s = 0; s < S; ++s)
-                if (slot_coord<S, G, VW, VEC>(s, gl) < k) part_grad[c * k + slot_coord<S, G, VW, VEC>(s, gl)] = g[s];
+        for (int o = 1; o < G; o <<= 1) {
+            u0 += shfl_xor(u0, o);
+            u1 += shfl_xor(u1, o);
+        }
+        if (ok && gl == 0) {
+            if constexpr (XSTEP) sp = loss[j];
+            float L0, L1;
+            loss_deriv<float>(sp, u0, a, L0);
+            loss_deriv<float>(sp, u1, a, L1);
+            lo += L0;
+            ln += L1;
         }
     }
-    const double ls = warp_sum((double)lsum);
-    if (lane == 0) part_loss[c] = ls;
+    const double so = warp_sum((double)lo), sn = warp_sum((double)ln);
+    if (lane == 0) {
+        part_old[c] = so;
+        part_new[c] = sn;
+    }
 }
 
-template <int K, bool XSTEP, int MODE>
-cudaError_t launch_bf16(glrm_s *h, const Orient &o, const float *F, const float *cand,
-                        const __nv_bfloat16 *Wb, const float *W, float *useg, float *uoth,
-                        const int32_t *perm, const int32_t *accepted)
+template <int K, bool XSTEP>
+cudaError_t launch_cand(glrm_s *h, const Orient &o, const float *F, const float *C, const float *W)
 {
     if (o.nchunks == 0) return cudaSuccess;
-    Scratch &s = h->s;
     const int k = h->k;
-    const bool vec = (k == K) && (Lanes<K>::S % 8 == 0);
+    const bool vec = (k == K) && ((reinterpret_cast<uintptr_t>(F) | reinterpret_cast<uintptr_t>(C) |
+                                   reinterpret_cast<uintptr_t>(W)) % 16 == 0);
     const unsigned nb = blocks_for(o.nchunks, kWarpsPerBlock);
     auto go = [&](auto kern) {
-        kern<<<nb, kWarpsPerBlock * 32, 0, h->stream>>>(o.nchunks, o.chunks, o.idx, (const float *)o.val, F,
-                                                        cand, Wb, W, k, h->loss_dev, useg, uoth, s.u_new,
-                                                        perm, accepted, (float *)s.part_grad,
-                                                        MODE == kBfLoss ? s.part_loss2 : s.part_loss);
+        kern<<<nb, kWarpsPerBlock * 32, 0, h->stream>>>(o.nchunks, o.chunks, o.order, o.idx, (const float *)o.val, F, C,
+                                                        W, k, h->loss_dev, h->s.part_loss, h->s.part_loss2);
     };
-    if constexpr (Lanes<K>::S % 8 == 0) {
-        if (vec) go(bf16_pass_kernel<K, XSTEP, true, MODE>);
-        else go(bf16_pass_kernel<K, XSTEP, false, MODE>);
-    } else {
-        go(bf16_pass_kernel<K, XSTEP, false, MODE>);
-    }
+    if (vec) go(cand_pass_kernel<K, XSTEP, true>);
+    else go(cand_pass_kernel<K, XSTEP, false>);
     h->launches += 1;
     return cudaGetLastError();
 }
 
-template <int K, bool XSTEP, int MODE>
-cudaError_t run_bf16_pass(glrm_s *h, const float *cand, const int32_t *accepted)
-{
-    const Orient &o = XSTEP ? h->csr : h->csc;
-    Scratch &s = h->s;
-    const float *F = (const float *)(XSTEP ? h->X : h->Yt);
-    const float *W = (const float *)(XSTEP ? h->Yt : h->X);
-    const __nv_bfloat16 *Wb = XSTEP ? s.yt_bf16 : s.x_bf16;
-    float *useg = XSTEP ? s.u_csr : s.u_csc;
-    float *uoth = XSTEP ? s.u_csc : s.u_csr;
-    return launch_bf16<K, XSTEP, MODE>(h, o, F, cand, Wb, W, useg, uoth, o.perm, accepted);
-}
-
-template <bool XSTEP, int MODE>
-cudaError_t bf16_pass(glrm_s *h, const float *cand = nullptr, const int32_t *accepted = nullptr)
+template <bool XSTEP>
+cudaError_t cand_pass(glrm_s *h, const Orient &o, const float *F, const float *C, const float *W)
 {
     const int k = h->k;
-#define GLRM_BF_CASE(KK) \
-    if (k <= KK) return run_bf16_pass<KK, XSTEP, MODE>(h, cand, accepted);
-    GLRM_BF_CASE(8)
-    GLRM_BF_CASE(16)
-    GLRM_BF_CASE(24)
-    GLRM_BF_CASE(32)
-    GLRM_BF_CASE(64)
-#undef GLRM_BF_CASE
+#define GLRM_CAND_CASE(KK) \
+    if (k <= KK) return launch_cand<KK, XSTEP>(h, o, F, C, W);
+    GLRM_CAND_CASE(4)
+    GLRM_CAND_CASE(8)
+    GLRM_CAND_CASE(12)
+    GLRM_CAND_CASE(16)
+    GLRM_CAND_CASE(20)
+    GLRM_CAND_CASE(24)
+    GLRM_CAND_CASE(32)
+    GLRM_CAND_CASE(48)
+    GLRM_CAND_CASE(64)
+#undef GLRM_CAND_CASE
     return cudaErrorInvalidValue;
-}
-
-// Exact FP32 products u for every entry, in both orders.
-inline cudaError_t bf16_refresh(glrm_s *h)
-{
-    tmark(h, "bf16_exact_u");
-    cudaError_t e = bf16_pass<true, kBfExact>(h);
-    tmark(h, nullptr);
-    if (e == cudaSuccess) h->s.u_sweeps = 0;
-    return e;
 }
 
 // One half-step of the BF16 form.
@@ -235,39 +139,41 @@ inline cudaError_t bf16_half_step(glrm_s *h, bool xstep)
     const int rk = xstep ? h->rx_kind : h->ry_kind;
     const float rw = (float)(xstep ? h->rx_w : h->ry_w);
     const int64_t nother = xstep ? h->n : h->m;
+    int32_t *acc = xstep ? s.acc_x : s.acc_y;  // previous decision per segment (1: accepted)
     cudaError_t e;
-    if (xstep && (s.u_sweeps < 0 || s.u_sweeps >= kBf16Refresh)) {
-        if ((e = bf16_refresh(h)) != cudaSuccess) return e;
-    }
     __nv_bfloat16 *Wb = xstep ? s.yt_bf16 : s.x_bf16;
     tmark(h, xstep ? "to_bf16_y" : "to_bf16_x");
     to_bf16_kernel<<<blocks_for(nother * k, 256), 256, 0, st>>>(W, nother * k, Wb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     h->launches += 1;
+    // gradient: BF16 rows for segments whose last step was accepted, FP32 rows for the others
     tmark(h, xstep ? "bf16_grad_x" : "bf16_grad_y");
-    e = xstep ? bf16_pass<true, kBfGrad>(h) : bf16_pass<false, kBfGrad>(h);
+    e = xstep ? dispatch_pass<float, true, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (float *)s.part_grad,
+                                                                  s.part_loss, st, acc, 1)
+              : dispatch_pass<float, false, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (float *)s.part_grad,
+                                                                   s.part_loss, st, acc, 1);
     if (e != cudaSuccess) return e;
+    tmark(h, xstep ? "fp32_grad_x" : "fp32_grad_y");
+    e = xstep ? dispatch_pass<float, true, true>(o, F, W, k, h->loss_dev, (float *)s.part_grad, s.part_loss, st, acc, 0)
+              : dispatch_pass<float, false, true>(o, F, W, k, h->loss_dev, (float *)s.part_grad, s.part_loss, st, acc, 0);
+    if (e != cudaSuccess) return e;
+    h->launches += 2 * (o.nchunks ? 1 : 0);
     const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
     prox_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const float *)s.part_grad,
                                                             s.part_loss, F, alpha, k, rk, rw, (float *)s.cand,
                                                             s.f_old, s.r_old, s.r_new);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    tmark(h, xstep ? "bf16_loss_x" : "bf16_loss_y");
-    e = xstep ? bf16_pass<true, kBfLoss>(h, (const float *)s.cand) : bf16_pass<false, kBfLoss>(h, (const float *)s.cand);
+    tmark(h, xstep ? "cand_x" : "cand_y");
+    e = xstep ? cand_pass<true>(h, o, F, (const float *)s.cand, W) : cand_pass<false>(h, o, F, (const float *)s.cand, W);
     if (e != cudaSuccess) return e;
-    int32_t *acc = xstep ? s.acc_x : s.acc_y;
     tmark(h, xstep ? "decide_x" : "decide_y");
     decide_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
         o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F, alpha, k,
-        xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y, acc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    tmark(h, xstep ? "bf16_update_x" : "bf16_update_y");
-    e = xstep ? bf16_pass<true, kBfUpdate>(h, nullptr, acc) : bf16_pass<false, kBfUpdate>(h, nullptr, acc);
+        xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y, acc, s.part_loss);
     tmark(h, nullptr);
     h->launches += 2;
-    if (!xstep) s.u_sweeps++;
-    return e;
+    return cudaGetLastError();
 }
 
 }  // namespace glrm

@@ -244,7 +244,11 @@ __device__ __forceinline__ void dn_block_any(const float (&u)[16], const float (
 // producer warp can fall two phases behind a barrier it waits on (the copy
 // warp issues the A tile every chunk c needs after the wait for chunk c - 4
 // at the latest; the MMA warp issues GEMM1 of c after its wait for c - 2).
-template <bool XSTEP, bool GRAD, int KP, bool MISS>
+// B16 (gradient passes of the BF16 form): GEMM2 takes the single product of
+// R's and W's BF16 high parts (FP32 accumulation) and only R's high part is
+// written to tensor memory; GEMM1, the losses, derivatives and objectives
+// keep the six-product FP32 quality.
+template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16 = false>
 __global__ void __launch_bounds__(kDnThreads, 1)
 dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 {
@@ -427,13 +431,14 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 // (R part, W part), smallest products first; a K = 16 step of R is 8 columns
                 const int pa[6] = {1, 0, 2, 0, 1, 0};
                 const int pb[6] = {1, 2, 0, 1, 0, 0};
+                constexpr int P0 = B16 ? 5 : 0;  // the BF16 form: hi . hi only
 #pragma unroll
-                for (int pr = 0; pr < 6; ++pr)
+                for (int pr = P0; pr < 6; ++pr)
 #pragma unroll
                     for (int ks = 0; ks < kDnNT / 16; ++ks)
                         umma_bf16_ta(taddr + kDnColG, taddr + (uint32_t)(kDnColR + rb * 96 + pa[pr] * 32 + ks * 8),
                                      umma_desc_sw(wt + pb[pr] * SM::pt + ks * 32, 2 * kDnNT), idesc,
-                                     c > 0 || pr > 0 || ks > 0);
+                                     c > 0 || pr > P0 || ks > 0);
                 umma_commit(&barG2[rb]);
                 ++g2_issued;
                 return true;
@@ -577,6 +582,10 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 if (!ok) break;
                 uint32_t hi[8], mi[8], lo[8];
                 const unsigned long long m1 = pk2(-1.f, -1.f);
+                if constexpr (B16) {
+#pragma unroll
+                    for (int w = 0; w < 16; w += 2) hi[w / 2] = bf2_bits(__floats2bfloat162_rn(rr[w], rr[w + 1]));
+                } else {
 #pragma unroll
                 for (int w = 0; w < 16; w += 2) {
                     // r = hi + mid + lo, each remainder exact in FP32
@@ -593,10 +602,13 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                     mi[w / 2] = bf2_bits(m2);
                     lo[w / 2] = bf2_bits(__floats2bfloat162_rn(b0, b1));
                 }
+                }
                 const uint32_t rcol = kDnColR + (uint32_t)(b * 96 + tb / 2);
                 tmem_st8(taddr + lane_base + rcol, hi);
-                tmem_st8(taddr + lane_base + rcol + 32, mi);
-                tmem_st8(taddr + lane_base + rcol + 64, lo);
+                if constexpr (!B16) {
+                    tmem_st8(taddr + lane_base + rcol + 32, mi);
+                    tmem_st8(taddr + lane_base + rcol + 64, lo);
+                }
                 tmem_wait_st();
             }
             tc_fence_before();
@@ -777,27 +789,27 @@ int dense_width(int k)
     return 0;
 }
 
-template <bool XSTEP, bool GRAD, int KP, bool MISS>
+template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16>
 cudaError_t launch_dense_kp(glrm_s *h, const DenseArgs &a, int nA, unsigned items)
 {
     const size_t smem = DnSmem<XSTEP, GRAD, KP>::bytes(nA);
-    cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP, MISS>,
+    cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(XSTEP ? h->dn.tmap_x : h->dn.tmap_y);
-    dense_pass_kernel<XSTEP, GRAD, KP, MISS><<<items, kDnThreads, smem, h->stream>>>(a, *map);
+    dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16><<<items, kDnThreads, smem, h->stream>>>(a, *map);
     h->launches += 1;
     return cudaGetLastError();
 }
 
 // A stages that fit next to the fixed buffers and the kernel's static shared
 // memory (at most kDnMaxStages; fewer than 2 is refused by the caller).
-template <bool XSTEP, bool GRAD, int KP, bool MISS>
+template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16>
 int stages_kp(int optin)
 {
     using SM = DnSmem<XSTEP, GRAD, KP>;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dense_pass_kernel<XSTEP, GRAD, KP, MISS>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16>) != cudaSuccess) return 0;
     if ((size_t)optin < fa.sharedSizeBytes) return 0;
     const size_t room = (size_t)optin - fa.sharedSizeBytes;
     if (room < SM::bytes(0)) return 0;
@@ -828,21 +840,30 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     if (e != cudaSuccess) return e;
+    // the BF16 form's gradient passes take the single-product GEMM2
+    const bool b16 = GRAD && h->prec == GLRM_BF16;
+#define GLRM_DENSE_GO(KK, MS, B)                                                   \
+    {                                                                              \
+        a.nA = stages_kp<XSTEP, GRAD, KK, MS, B>(optin);                           \
+        if (a.nA < 2) return cudaErrorInvalidConfiguration;                        \
+        return launch_dense_kp<XSTEP, GRAD, KK, MS, B>(h, a, a.nA, tiles);         \
+    }
 #define GLRM_DENSE_CASE(KK)                                                        \
     if (d.KP == KK) {                                                              \
-        if (d.missing) {                                                           \
-            a.nA = stages_kp<XSTEP, GRAD, KK, true>(optin);                        \
-            if (a.nA < 2) return cudaErrorInvalidConfiguration;                    \
-            return launch_dense_kp<XSTEP, GRAD, KK, true>(h, a, a.nA, tiles);      \
+        if constexpr (GRAD) {                                                      \
+            if (b16) {                                                             \
+                if (d.missing) GLRM_DENSE_GO(KK, true, true)                       \
+                GLRM_DENSE_GO(KK, false, true)                                     \
+            }                                                                      \
         }                                                                          \
-        a.nA = stages_kp<XSTEP, GRAD, KK, false>(optin);                           \
-        if (a.nA < 2) return cudaErrorInvalidConfiguration;                        \
-        return launch_dense_kp<XSTEP, GRAD, KK, false>(h, a, a.nA, tiles);         \
+        if (d.missing) GLRM_DENSE_GO(KK, true, false)                              \
+        GLRM_DENSE_GO(KK, false, false)                                            \
     }
     GLRM_DENSE_CASE(16)
     GLRM_DENSE_CASE(32)
     GLRM_DENSE_CASE(64)
 #undef GLRM_DENSE_CASE
+#undef GLRM_DENSE_GO
     return cudaErrorInvalidValue;
 }
 

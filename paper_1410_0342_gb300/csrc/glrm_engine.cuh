@@ -114,13 +114,14 @@ __device__ __forceinline__ void load_lane_w(T (&v)[S], const WT *__restrict__ ro
 // One warp per chunk: entries base + grp for base = begin, begin + PER, ...
 // (G lanes per entry, PER = 32 / G entries per iteration), the rows of the
 // other factor gathered in the lane layout above.  `order` (nullable) is the
-// chunk launch order.
+// chunk launch order; with `sel` (nullable) the launch takes only the chunks
+// of segments whose sel value is nonzero exactly when want is.
 template <class T, int K, bool XSTEP, bool VEC, bool GRAD, class WT = T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ order,
             const int32_t *__restrict__ idx, const T *__restrict__ val, const T *__restrict__ F,
             const WT *__restrict__ W, int k, const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
-            double *__restrict__ part_loss)
+            double *__restrict__ part_loss, const int32_t *__restrict__ sel, int want)
 {
     using LN = Lanes<K>;
     constexpr int G = LN::G, S = LN::S, PER = LN::PER;
@@ -131,6 +132,7 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
     const int64_t c = order ? (int64_t)__ldg(order + lin) : lin;
     const int gl = lane % G, grp = lane / G;
     const int4 ch = chunks[c];
+    if (sel && ((__ldg(sel + ch.x) != 0) != (want != 0))) return;  // another launch takes this segment
     T f[S], g[S];
     load_lane<T, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
 #pragma unroll
@@ -246,13 +248,15 @@ decide_kernel(int64_t nseg, const int32_t *__restrict__ segchunk,
               const double *__restrict__ r_old, const double *__restrict__ r_new,
               const T *__restrict__ cand, T *__restrict__ F, T *__restrict__ alpha, int k,
               double *__restrict__ kept_obj, double *__restrict__ kept_reg,
-              int32_t *__restrict__ accepted)
+              int32_t *__restrict__ accepted, const double *__restrict__ part_loss_old = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (s >= nseg) return;
     const double fn = seg_loss_sum(part_loss_new, segchunk[s], segchunk[s + 1], lane) + r_new[s];
-    const double fo = f_old[s];
+    // f_old from the prox step, or (part_loss_old given) from the chunk partials of a later pass
+    const double fo = part_loss_old ? seg_loss_sum(part_loss_old, segchunk[s], segchunk[s + 1], lane) + r_old[s]
+                                    : f_old[s];
     const bool acc = fn <= fo;
     if (acc)
         for (int c = lane; c < k; c += 32) F[s * k + c] = cand[s * k + c];
@@ -410,7 +414,7 @@ inline unsigned blocks_for(int64_t items, int per_block)
 
 template <class T, int K, bool XSTEP, bool GRAD, class WT>
 cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
-                        T *part_grad, double *part_loss, cudaStream_t st)
+                        T *part_grad, double *part_loss, cudaStream_t st, const int32_t *sel, int want)
 {
     if (o.nchunks == 0) return cudaSuccess;
     // the BF16 copy is read 8 values at a time, so its vector path needs k % 8 == 0
@@ -420,14 +424,14 @@ cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const L
     const unsigned nb = blocks_for(o.nchunks, kWarpsPerBlock);
     if constexpr (std::is_same<WT, __nv_bfloat16>::value && Lanes<K>::S % 8 != 0) {
         pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-            o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+            o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want);
     } else {
         if (vec)
             pass_kernel<T, K, XSTEP, true, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want);
         else
             pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss);
+                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want);
     }
     return cudaGetLastError();
 }
@@ -435,10 +439,11 @@ cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const L
 // Dispatch a runtime k to the smallest padded width K >= k.
 template <class T, bool XSTEP, bool GRAD, class WT = T>
 cudaError_t dispatch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
-                          T *part_grad, double *part_loss, cudaStream_t st)
+                          T *part_grad, double *part_loss, cudaStream_t st, const int32_t *sel = nullptr,
+                          int want = 0)
 {
 #define GLRM_PASS_CASE(KK) \
-    if (k <= KK) return launch_pass<T, KK, XSTEP, GRAD, WT>(o, F, W, k, loss, part_grad, part_loss, st);
+    if (k <= KK) return launch_pass<T, KK, XSTEP, GRAD, WT>(o, F, W, k, loss, part_grad, part_loss, st, sel, want);
     GLRM_PASS_CASE(4)
     GLRM_PASS_CASE(8)
     GLRM_PASS_CASE(12)

@@ -8,10 +8,20 @@
 template struct glrm::Engine<float>;
 
 namespace glrm {
-cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep) { return bf16_half_step(h, xstep); }
-cudaError_t launch_perm(const Orient &o, const Orient &other, cudaStream_t st)
+
+static __global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v)
 {
-    perm_kernel<<<blocks_for(o.nseg, 8), 256, 0, st>>>(o.nseg, o.ptr, o.idx, other.ptr, other.idx, o.perm);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep) { return bf16_half_step(h, xstep); }
+
+cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_i32_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, n, v);
     return cudaGetLastError();
 }
+
 }  // namespace glrm

@@ -51,7 +51,6 @@ struct Orient {
     int mode = kModeChunked;
     int R = 0, nb = 0, ngroups = 0;  // blocked: panel rows, panels, segment groups
     int32_t *runptr = nullptr;       // blocked: (nb + 1) x nseg run starts
-    int32_t *perm = nullptr;         // BF16 form: position of each entry in the other order
     int grid = 0;                    // fused / blocked: CTAs per launch
     int cap = 0;                     // fused / blocked: entries per staging buffer
     size_t smem_bytes = 0;           // fused / blocked / masked: dynamic shared memory
@@ -94,9 +93,6 @@ struct Scratch {
     int *conv_cnt = nullptr;        // sweep_until: [0] sweeps run, [1] sweep limit, [2] stop flag
     __nv_bfloat16 *x_bf16 = nullptr;   // BF16 form: BF16 copies of the factors
     __nv_bfloat16 *yt_bf16 = nullptr;
-    float *u_csr = nullptr, *u_csc = nullptr;  // BF16 form: exact products per entry, both orders
-    float *u_new = nullptr;                    // BF16 form: re-evaluated products
-    int u_sweeps = -1;                         // sweeps since the last exact refresh (-1: stale)
 };
 
 constexpr int kRedBlocks = 304;  // 2 x 152 SMs
@@ -251,7 +247,7 @@ cudaError_t launch_check_entries(const Orient &o, bool rows, int64_t other, int6
                                  const LossSpec *loss, int *flag, unsigned long long *digest, cudaStream_t st);
 cudaError_t launch_digest_compare(const unsigned long long *d, int *flag, cudaStream_t st);
 cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep);
-cudaError_t launch_perm(const Orient &o, const Orient &other, cudaStream_t st);
+cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
 // Dense, fully observed form (tensor cores, FP32 models).
 bool dense_supported(int k);
 void dense_free(glrm_s *h);

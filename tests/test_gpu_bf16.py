@@ -1,6 +1,7 @@
-"""The BF16 form: gradient passes on BF16 copies of the factors with FP32
-accumulation and FP32 loss derivatives; candidates re-evaluated in FP32
-before the accept / reject test.  Checked against the FP64 oracle (gradient
+"""The BF16 form: gradient passes on BF16 copies of the other factor with
+FP32 accumulation and FP32 loss derivatives (FP32 rows for a segment retrying
+after a rejected step); candidates evaluated on FP32 rows, so the accept /
+reject test and the objective are those of the FP32 form.  Checked against the FP64 oracle (gradient
 element by element within 2e-2, objectives and sampled predictions of a
 row-reduced completion table) and against the plain FP32 sweep (objective
 accuracy)."""
@@ -52,27 +53,30 @@ def test_bf16_gradient_within_2e2(G, oracle_mod, k):
         assert rel > 1e-7  # it really ran on BF16 copies
 
 
-def test_bf16_sweep_small_table(G, oracle_mod):
-    """20,000 x 400, k = 64: the BF16 form never increases the objective, the
-    reported values track the FP32 objective of the accepted factors (exact
-    at every refresh of the carried products, off by the BF16 rounding of the
-    step contributions in between: measured 5e-6 four sweeps after one), and
-    after 20 sweeps it is within 1e-2 of the FP32 form and of the oracle (the
-    BF16 gradient slows convergence on a table this small; measured 0.8%)."""
+def test_bf16_reaches_fp32_objective_small_table(G, oracle_mod):
+    """20,000 x 400, k = 64, 40 entries per row, compared with the FP32 sweep
+    at the same objective accuracy: the BF16 form never increases the
+    objective, the objective it reports is the FP32 objective of the factors
+    it keeps (candidates and decisions are evaluated on FP32 rows), and it
+    reaches the FP32 form's 20-sweep objective to within 1e-4 (the FP32 form
+    itself is within 1e-4 of the FP64 oracle there).  On this small,
+    underdetermined table (40 entries per row, k = 64) its BF16 gradients take
+    more sweeps to get there; the count is printed."""
     t = W.completion(m=20000, n=400, k=64, per_row=40, seed=79)
     gb = G.GLRM.from_table(t, precision=G.GLRM_BF16)
     gf = G.GLRM.from_table(t, precision=G.GLRM_FP32)
-    hb = gb.sweep(20)
     hf = gf.sweep(20)
+    hb = gb.sweep(200)
     *_, oh, _ = oracle_problem(oracle_mod, t).proxgrad(t.X0, t.Yt0, 20)
+    assert abs(hf[-1] - oh[-1]) / oh[-1] < 1e-4, (hf[-1], oh[-1])
     assert np.all(np.diff(hb) <= 1e-7 * np.abs(hb[1:]))
-    assert abs(hb[-1] - hf[-1]) / hf[-1] < 1e-2, (hb[-1], hf[-1])
-    assert abs(hb[-1] - oh[-1]) / oh[-1] < 1e-2, (hb[-1], oh[-1])
-    # the reported objective against the FP32 objective of the factors kept
+    reach = np.nonzero(hb <= hf[-1] * (1 + 1e-4))[0]
+    print(f"BF16 form reaches the FP32 form's 20-sweep objective after {reach[0] + 1 if reach.size else None} sweeps")
+    assert reach.size, (hb[-1], hf[-1])
     X, Yt = gb.factors()
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     G.glrm_objective_at(gb.h, X, Yt, out)
-    assert abs(out.item() - hb[-1]) / hb[-1] < 1e-4
+    assert abs(out.item() - hb[-1]) / hb[-1] < 1e-5
 
 
 def test_bf16_matches_fp32_objective_midsize(G):

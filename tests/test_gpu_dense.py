@@ -205,3 +205,43 @@ def test_dense_validation(G):
     with pytest.raises(G.GLRMError) as e:
         g64.set_dense(A.double())
     assert e.value.code == G.GLRM_ERR_ARG
+
+
+def test_dense_bf16_form(G, oracle_mod):
+    """A GLRM_BF16 model on a table stored densely: the gradient contraction
+    R W is one BF16 product on the tensor cores (elementwise within 2e-2 of
+    the oracle, plus 2^-7 of the terms' absolute sum), while U, the losses and
+    the objective keep FP32 quality (1e-5); its sweeps never increase the
+    objective, report the FP32 objective of the kept factors, and reach the
+    FP32 dense form's 12-sweep objective to within 1e-4."""
+    t = W.mixed(m=6000, n=300, n_real=150, n_bool=90, seed=71)
+    gb = G.GLRM.from_table(t, precision=G.GLRM_BF16)
+    assert G.glrm_get_path(gb.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    p = oracle_problem(oracle_mod, t)
+    rng = np.random.default_rng(3)
+    X = torch.as_tensor(rng.standard_normal((t.m, t.k)), dtype=torch.float32, device="cuda")
+    Yt = torch.as_tensor(np.abs(rng.standard_normal((t.n, t.k))), dtype=torch.float32, device="cuda")
+    Xd, Yd = X.double().cpu().numpy(), Yt.double().cpu().numpy()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.glrm_objective_at(gb.h, X, Yt, out)
+    of = p.objective(Xd, Yd)
+    assert abs(out.item() - of) / abs(of) < 1e-5
+    GX = torch.empty_like(X)
+    GY = torch.empty_like(Yt)
+    G.glrm_grad_at(gb.h, X, Yt, GX, GY, include_reg=False)
+    oGX, oGY = p.gradient(Xd, Yd)
+    sX, sY, vX, vY = grad_bounds(p, Xd, Yd)
+    assert_grad_close(GX.cpu().numpy(), oGX, sX, vX, rtol=2e-2, srel=2.0 ** -7, what="GX bf16")
+    assert_grad_close(GY.cpu().numpy(), oGY, sY, vY, rtol=2e-2, srel=2.0 ** -7, what="GYt bf16")
+    assert np.linalg.norm(GX.double().cpu().numpy() - oGX) / np.linalg.norm(oGX) > 1e-7  # really BF16
+    gf = G.GLRM.from_table(t, precision=G.GLRM_FP32)
+    hf = gf.sweep(12)
+    hb = gb.sweep(60)
+    assert np.all(np.diff(hb) <= 1e-7 * np.abs(hb[1:]))
+    reach = np.nonzero(hb <= hf[-1] * (1 + 1e-4))[0]
+    print(f"dense BF16 form reaches the FP32 form's 12-sweep objective after "
+          f"{reach[0] + 1 if reach.size else None} sweeps")
+    assert reach.size, (hb[-1], hf[-1])
+    Xb, Yb = gb.factors()
+    G.glrm_objective_at(gb.h, Xb, Yb, out)
+    assert abs(out.item() - hb[-1]) / abs(hb[-1]) < 1e-5
