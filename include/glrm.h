@@ -69,13 +69,19 @@ typedef enum {
  *   GLRM_LOSS_ORDINAL_HINGE
  *                       sum_{a'<a} (1 - u + a')_+ + sum_{a'>a, a'<=d} (1 + u - a')_+
  *                       with a in {1..d}, d = levels                 eq. ord-pca
- * At a kink the derivative of the kinked term is taken as 0. */
+ *   GLRM_LOSS_L1        |a - u|                                      Sec. 4.2, robust PCA
+ *   GLRM_LOSS_QUANTILE  alpha (a - u)_+ + (1 - alpha) (u - a)_+, alpha = param
+ *                       in (0, 1)                                   Sec. 4.2, quantile PCA
+ * At a kink the derivative of the kinked term is taken as 0.  The batched
+ * form takes kinds 0 .. 4. */
 typedef enum {
     GLRM_LOSS_QUAD = 0,
     GLRM_LOSS_HUBER = 1,
     GLRM_LOSS_HINGE = 2,
     GLRM_LOSS_LOGISTIC = 3,
-    GLRM_LOSS_ORDINAL_HINGE = 4
+    GLRM_LOSS_ORDINAL_HINGE = 4,
+    GLRM_LOSS_L1 = 5,
+    GLRM_LOSS_QUANTILE = 6
 } glrm_loss_kind;
 
 /* Row / column regulariser r(x) with weight w.
@@ -97,7 +103,7 @@ typedef enum { GLRM_FP64 = 0, GLRM_FP32 = 1, GLRM_BF16 = 2 } glrm_precision;
 typedef struct {
     int32_t kind;   /* glrm_loss_kind */
     int32_t levels; /* ordinal level count d >= 2; ignored otherwise */
-    double param;   /* Huber delta; ignored otherwise */
+    double param;   /* Huber delta or quantile alpha; ignored otherwise */
 } glrm_loss;
 
 /* Limits: 1 <= k <= 64; m, n >= 1; m, n, nnz < 2^31. */
@@ -255,7 +261,7 @@ int glrm_grad(glrm_t h, void *GX_dev, void *GYt_dev);
 
 /* Imputation (Section 5.3): for the cnt pairs (rows_dev[e], cols_dev[e])
  * write u = x_i . y_j (decode == 0) or the decoded value argmin_a L_j(u, a)
- * (decode != 0): u for quadratic and Huber columns, +1 if u >= 0 else -1 for
+ * (decode != 0): u for quadratic, Huber, l1 and quantile columns, +1 if u >= 0 else -1 for
  * hinge and logistic columns, 1 + #{a in 1..d-1 : u > a + 1/2} for ordinal
  * columns (the minimiser of the ordinal hinge, ties to the lower level).
  * out_dev holds cnt values of the model's element type.  Indices out of range
@@ -274,6 +280,25 @@ int glrm_predict(glrm_t h, int64_t cnt, const int32_t *rows_dev, const int32_t *
  * GLRM_LOSS_QUAD and rx, ry both GLRM_REG_QUAD with the same weight gamma
  * (else GLRM_ERR_ARG).  history_host as in glrm_sweep. */
 int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history_host);
+
+/* Prox-prox sweeps for quadratic loss and any of the regularisers (Section
+ * 7.2, "Prox-prox method", with the cached factorisation of Section 7.3):
+ * every row x_i, then every column y_j (against the new X), takes `inner`
+ * updates
+ *     x <- prox_{alpha r}(prox_{alpha f}(x)),
+ *     prox_{alpha f}(x) = argmin_x' alpha f(x') + ||x' - x||^2 / 2
+ *                       = (2 alpha G + I)^{-1} (2 alpha b + x),
+ * f(x) = sum_{j in Omega_i} (x . y_j - A_ij)^2, G = sum y_j y_j^T,
+ * b = sum A_ij y_j, with one FP64 Cholesky factorisation of 2 alpha G + I
+ * per row reused by the `inner` updates (Gram matrices accumulated in the
+ * model's element type).  The update's fixed point minimises the Moreau
+ * envelope of f plus r; for r = 0 that is the least-squares row problem's
+ * solution.  alpha > 0 (a constant step), inner >= 1, k <= 32; every column
+ * loss must be GLRM_LOSS_QUAD (GLRM_ERR_ARG otherwise).  history_host as in
+ * glrm_sweep (the objective of eq. gpca after each sweep, FP64).  A row
+ * system whose factorisation fails keeps its factor; with history_host the
+ * call then returns GLRM_ERR_NONFINITE. */
+int glrm_proxprox_sweep(glrm_t h, int32_t nsweeps, double alpha, int32_t inner, double *history_host);
 
 /* Serialise the fit state (factors, step sizes, sweep counter) into buf_host.
  * With buf_host NULL, *len receives the size needed.  Synchronises.

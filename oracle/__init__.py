@@ -29,6 +29,11 @@ Parity status of each function (the pins live in tests/test_oracle_*.py):
                                        row / column: alpha = 1, x <- prox(x))
   als                                  pinned (normal equations vs numpy.linalg,
                                        qPCA closed form)
+  proxprox                             pinned (fixed points: the least-squares
+                                       solution for r = 0, the closed form
+                                       ((1 + 2 alpha gamma) G + gamma I) x = b
+                                       for gamma ||x||^2, the NNLS optimality
+                                       conditions of the envelope for x >= 0)
 """
 from __future__ import annotations
 
@@ -40,6 +45,7 @@ import threading
 import numpy as np
 
 LOSS_QUAD, LOSS_HUBER, LOSS_HINGE, LOSS_LOGISTIC, LOSS_ORDINAL = 0, 1, 2, 3, 4
+LOSS_L1, LOSS_QUANTILE = 5, 6
 REG_ZERO, REG_QUAD, REG_L1, REG_NONNEG = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -94,6 +100,9 @@ def _load():
                                         p, p, p, p, i32, p, p, i32]
         lib.oracle_als.restype = i32
         lib.oracle_als.argtypes = [i64, i64, i32, i64, p, p, p, d, p, p, i32, p, i32]
+        lib.oracle_proxprox.restype = i32
+        lib.oracle_proxprox.argtypes = [i64, i64, i32, i64, p, p, p, i32, d, i32, d, d, i32, p, p, i32,
+                                        p, i32]
         lib.oracle_num_threads.restype = i32
         lib.oracle_num_threads.argtypes = [i32]
         _lib = lib
@@ -111,7 +120,8 @@ def _c(a, dtype):
 # ----------------------------------------------------------------- entrywise
 
 def loss(kind: int, u: float, a: float, param: float = 1.0, levels: int = 0) -> float:
-    """L(u, a): eq. qpca, Huber (Sec. 4.3), hinge and logistic (Sec. 5.2), eq. ord-pca."""
+    """L(u, a): eq. qpca, Huber (Sec. 4.3), hinge and logistic (Sec. 5.2), eq. ord-pca,
+    l1 and quantile (Sec. 4.2, robust and quantile PCA; param = alpha)."""
     return _load().oracle_loss(kind, param, levels, float(u), float(a))
 
 
@@ -262,6 +272,21 @@ class Problem:
                                 nthreads)
         if rc:
             raise ValueError(f"oracle_als failed ({rc})")
+        return X, Yt, hist
+
+    def proxprox(self, X, Yt, alpha: float, inner: int, nsweeps: int, nthreads: int = 0):
+        """Alternating prox-prox sweeps for quadratic loss (Sec. 7.2 prox-prox
+        update, Sec. 7.3 cached factorisation) with the problem's regularisers:
+        each row, then each column, takes `inner` updates
+        v <- prox_{alpha r}((2 alpha G + I)^{-1} (2 alpha b + v)).  Returns
+        (X, Yt, history)."""
+        X = np.array(X, dtype=np.float64, order="C")
+        Yt = np.array(Yt, dtype=np.float64, order="C")
+        hist = np.empty(nsweeps, dtype=np.float64)
+        rc = _load().oracle_proxprox(*self._common(), *self.rx, *self.ry, float(alpha), int(inner),
+                                     _ptr(X), _ptr(Yt), nsweeps, _ptr(hist), nthreads)
+        if rc:
+            raise ValueError(f"oracle_proxprox failed ({rc})")
         return X, Yt, hist
 
 

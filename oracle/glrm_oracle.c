@@ -42,7 +42,8 @@
 #include <omp.h>
 #endif
 
-enum { LOSS_QUAD = 0, LOSS_HUBER = 1, LOSS_HINGE = 2, LOSS_LOGISTIC = 3, LOSS_ORDINAL = 4 };
+enum { LOSS_QUAD = 0, LOSS_HUBER = 1, LOSS_HINGE = 2, LOSS_LOGISTIC = 3, LOSS_ORDINAL = 4,
+       LOSS_L1 = 5, LOSS_QUANTILE = 6 };
 enum { REG_ZERO = 0, REG_QUAD = 1, REG_L1 = 2, REG_NONNEG = 3 };
 
 static double pos(double v) { return v > 0.0 ? v : 0.0; }
@@ -51,7 +52,9 @@ static double pos(double v) { return v > 0.0 ? v : 0.0; }
 
 /* L(u, a).  Quadratic (eq. qpca), Huber (Section 4.3, "Huber PCA"), hinge
  * (Section 5.2, "Boolean PCA"), logistic (Section 5.2, "Logistic PCA"),
- * ordinal hinge (eq. ord-pca). */
+ * ordinal hinge (eq. ord-pca), l1 |a - u| (Section 4.2, robust PCA) and the
+ * quantile loss alpha (a - u)_+ + (1 - alpha) (u - a)_+ with alpha = param
+ * (Section 4.2, "Quantile PCA"). */
 double oracle_loss(int kind, double param, int levels, double u, double a)
 {
     switch (kind) {
@@ -75,6 +78,10 @@ double oracle_loss(int kind, double param, int levels, double u, double a)
         for (int ap = lev + 1; ap <= levels; ++ap) s += pos(1.0 + u - ap);
         return s;
     }
+    case LOSS_L1:
+        return fabs(a - u);
+    case LOSS_QUANTILE:
+        return param * pos(a - u) + (1.0 - param) * pos(u - a);
     }
     return NAN;
 }
@@ -105,12 +112,16 @@ double oracle_dloss(int kind, double param, int levels, double u, double a)
             if (1.0 + u - ap > 0.0) s += 1.0;
         return s;
     }
+    case LOSS_L1:
+        return u > a ? 1.0 : (u < a ? -1.0 : 0.0);
+    case LOSS_QUANTILE:
+        return u > a ? 1.0 - param : (u < a ? -param : 0.0);
     }
     return NAN;
 }
 
 /* Imputation (Section 5.3): argmin over the loss's domain of L(u, a).
- * Real-valued losses return u; Boolean losses return sign(u) with sign(0)=+1;
+ * Real-valued losses (quadratic, Huber, l1, quantile) return u; Boolean losses return sign(u) with sign(0)=+1;
  * the ordinal hinge is minimised by trying every level 1..d (ties to the
  * smaller level). */
 double oracle_decode(int kind, int levels, double u)
@@ -118,6 +129,8 @@ double oracle_decode(int kind, int levels, double u)
     switch (kind) {
     case LOSS_QUAD:
     case LOSS_HUBER:
+    case LOSS_L1:
+    case LOSS_QUANTILE:
         return u;
     case LOSS_HINGE:
     case LOSS_LOGISTIC:
@@ -639,6 +652,78 @@ int oracle_als(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row, con
         }
         if (history)
             history[t] = objective_lists(&L, k, X, Yt, &lt, REG_QUAD, gamma, REG_QUAD, gamma);
+    }
+    free(kind); free(param); free(lev);
+    lists_free(&L);
+    return bad ? -3 : 0;
+}
+
+/* Prox-prox update of one factor vector for quadratic loss (Section 7.2,
+ * "Prox-prox method", with the cached factorisation of Section 7.3): with
+ * f(v) = sum_e (v . w_e - a_e)^2, G = sum_e w_e w_e^T and b = sum_e a_e w_e,
+ *   prox_{alpha f}(v) = argmin_v' alpha f(v') + 1/2 ||v' - v||^2
+ *                     = (2 alpha G + I)^{-1} (2 alpha b + v),
+ * then v <- prox_{alpha r}(prox_{alpha f}(v)), `inner` times with the same
+ * factorisation of 2 alpha G + I. */
+static int proxprox_vector(int k, double *v, const double *W, const int32_t *idx, const double *a,
+                           int64_t cnt, double alpha, int inner, int rkind, double rw)
+{
+    double G[k * k], Gc[k * k], b[k], rhs[k];
+    for (int p = 0; p < k * k; ++p) G[p] = 0.0;
+    for (int c = 0; c < k; ++c) b[c] = 0.0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        const double *w = W + (int64_t)idx[e] * k;
+        for (int r = 0; r < k; ++r) {
+            b[r] += a[e] * w[r];
+            for (int c = 0; c < k; ++c) G[r * k + c] += w[r] * w[c];
+        }
+    }
+    for (int t = 0; t < inner; ++t) {
+        /* the factorisation is recomputed here for plainness; it does not
+         * change between the inner iterations */
+        for (int p = 0; p < k * k; ++p) Gc[p] = 2.0 * alpha * G[p];
+        for (int c = 0; c < k; ++c) Gc[c * k + c] += 1.0;
+        for (int c = 0; c < k; ++c) rhs[c] = 2.0 * alpha * b[c] + v[c];
+        if (chol_solve(k, Gc, rhs)) return -1;
+        oracle_prox(rkind, rw, alpha, k, rhs, v);
+    }
+    return 0;
+}
+
+/* Alternating prox-prox sweeps for quadratic loss and any regulariser: every
+ * row x_i takes `inner` prox-prox updates against Y^{t-1}, then every column
+ * y_j against X^t.  history[t] receives the objective after sweep t. */
+int oracle_proxprox(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row, const int32_t *col,
+                    const double *val, int rxk, double rxw, int ryk, double ryw, double alpha, int inner,
+                    double *X, double *Yt, int nsweeps, double *history, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    int rc = lists_build(&L, m, n, nnz, row, col, val);
+    if (rc) { lists_free(&L); return rc; }
+    set_threads(nthreads);
+    int32_t *kind = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    double *param = malloc(sizeof(double) * (size_t)(n ? n : 1));
+    int32_t *lev = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    for (int64_t j = 0; j < n; ++j) { kind[j] = LOSS_QUAD; param[j] = 0.0; lev[j] = 0; }
+    loss_table lt = { kind, param, lev };
+    int bad = 0;
+    for (int t = 0; t < nsweeps && !bad; ++t) {
+        int64_t i, j;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+        for (i = 0; i < m; ++i) {
+            int64_t b = L.rstart[i];
+            bad |= proxprox_vector(k, X + i * k, Yt, L.rcol + b, L.rval + b, L.rstart[i + 1] - b, alpha,
+                                   inner, rxk, rxw) != 0;
+        }
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+        for (j = 0; j < n; ++j) {
+            int64_t b = L.cstart[j];
+            bad |= proxprox_vector(k, Yt + j * k, X, L.crow + b, L.cval + b, L.cstart[j + 1] - b, alpha,
+                                   inner, ryk, ryw) != 0;
+        }
+        if (history)
+            history[t] = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw);
     }
     free(kind); free(param); free(lev);
     lists_free(&L);

@@ -119,6 +119,63 @@ als_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__
     if (lane < k) F[s * k + lane] = (T)b[wid][lane];
 }
 
+// Prox-prox update for quadratic loss (Section 7.2, "Prox-prox method"; the
+// cached factorisation of Section 7.3), one warp per segment: with the
+// segment's Gram matrix G and right-hand side b (the ALS partials), factor
+// M = 2 alpha G + I once in FP64, then `inner` times
+//     f <- prox_{alpha r}(M^{-1} (2 alpha b + f)),
+// prox_{alpha f}(f) = argmin alpha sum_e (f . w_e - a_e)^2 + ||f' - f||^2 / 2
+// being M^{-1}(2 alpha b + f).  A failed factorisation keeps the factor and
+// raises the status flag.
+template <class T, int K>
+__global__ void __launch_bounds__(kAlsWarps * 32)
+proxprox_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restrict__ part,
+                      int k, double alpha, int inner, int rkind, double rw, T *__restrict__ F,
+                      int *__restrict__ err)
+{
+    using TR = Tri<K>;
+    __shared__ double G[kAlsWarps][K][K + 1];
+    __shared__ double b[kAlsWarps][K];
+    __shared__ double x[kAlsWarps][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t s = (int64_t)blockIdx.x * kAlsWarps + wid;
+    if (s >= nseg) return;
+    const int cb = segchunk[s], ce = segchunk[s + 1];
+    for (int p = lane; p < TR::N; p += 32) {
+        int r, c;
+        tri_rc(p, r, c);
+        double v = 0.0;
+        for (int q = cb; q < ce; ++q) v += (double)part[(int64_t)q * TR::P + p];
+        G[wid][r][c] = 2.0 * alpha * v + (r == c ? 1.0 : 0.0);
+    }
+    if (lane < K) {
+        double v = 0.0;
+        for (int q = cb; q < ce; ++q) v += (double)part[(int64_t)q * TR::P + TR::N + lane];
+        b[wid][lane] = 2.0 * alpha * v;
+    }
+    __syncwarp();
+    // unused rows / columns beyond k become identity rows of a K x K system
+    for (int c = k + lane; c < K; c += 32) {
+        for (int q = 0; q < c; ++q) G[wid][c][q] = 0.0;
+        G[wid][c][c] = 1.0;
+        b[wid][c] = 0.0;
+    }
+    __syncwarp();
+    if (!warp_cholesky_factor<K, K + 1>(G[wid])) {
+        if (lane == 0) atomicOr(err, kErrPivot);
+        return;
+    }
+    double f = lane < k ? (double)F[s * k + lane] : 0.0;
+    for (int it = 0; it < inner; ++it) {
+        if (lane < K) x[wid][lane] = b[wid][lane] + f;
+        __syncwarp();
+        warp_cholesky_subst<K, K + 1>(G[wid], x[wid]);
+        if (lane < K) f = lane < k ? prox1<double>(rkind, rw, alpha, x[wid][lane]) : 0.0;
+        __syncwarp();
+    }
+    if (lane < k) F[s * k + lane] = (T)f;
+}
+
 template <class T, int K>
 cudaError_t launch_als_half(glrm_s *h, bool xstep, double gamma)
 {
@@ -148,6 +205,50 @@ cudaError_t launch_als_half(glrm_s *h, bool xstep, double gamma)
         o.nseg, o.segchunk, part, h->k, gamma, F, h->s.err);
     tmark(h, nullptr);
     return cudaGetLastError();
+}
+
+template <class T, int K>
+cudaError_t launch_proxprox_half(glrm_s *h, bool xstep, double alpha, int inner)
+{
+    // the Gram partials of the ALS half-step (no solve), then the prox-prox solves
+    const Orient &o = xstep ? h->csr : h->csc;
+    T *F = (T *)(xstep ? h->X : h->Yt);
+    const T *W = (const T *)(xstep ? h->Yt : h->X);
+    const size_t need = (size_t)std::max<int64_t>(1, std::max(h->csr.nchunks, h->csc.nchunks)) *
+                        Tri<K>::P * sizeof(T);
+    if (h->s.als_bytes < need) {
+        dfree(h->s.als_part, h->stream);
+        h->s.als_part = nullptr;
+        h->s.als_bytes = 0;
+        cudaError_t e = dalloc(h, &h->s.als_part, need);
+        if (e != cudaSuccess) return e;
+        h->s.als_bytes = need;
+    }
+    T *part = (T *)h->s.als_part;
+    h->launches += 1 + (o.nchunks ? 1 : 0);
+    tmark(h, xstep ? "als_gram_x" : "als_gram_y");
+    if (o.nchunks)
+        als_gram_kernel<T, K><<<blocks_for(o.nchunks, kAlsWarps), kAlsWarps * 32, 0, h->stream>>>(
+            o.nchunks, o.chunks, o.idx, (const T *)o.val, W, h->k, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tmark(h, xstep ? "proxprox_x" : "proxprox_y");
+    proxprox_solve_kernel<T, K><<<blocks_for(o.nseg, kAlsWarps), kAlsWarps * 32, 0, h->stream>>>(
+        o.nseg, o.segchunk, part, h->k, alpha, inner, xstep ? h->rx_kind : h->ry_kind,
+        xstep ? h->rx_w : h->ry_w, F, h->s.err);
+    tmark(h, nullptr);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Engine<T>::proxprox_half(glrm_s *h, bool xstep, double alpha, int inner)
+{
+    const int k = h->k;
+    if (k <= 4) return launch_proxprox_half<T, 4>(h, xstep, alpha, inner);
+    if (k <= 8) return launch_proxprox_half<T, 8>(h, xstep, alpha, inner);
+    if (k <= 16) return launch_proxprox_half<T, 16>(h, xstep, alpha, inner);
+    if (k <= 32) return launch_proxprox_half<T, 32>(h, xstep, alpha, inner);
+    return cudaErrorInvalidValue;
 }
 
 template <class T>

@@ -945,14 +945,16 @@ int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss, int3
     std::vector<LossSpec> spec((size_t)n);
     for (int64_t j = 0; j < n; ++j) {
         const glrm_loss &L = col_loss[j];
-        if (L.kind < kLossQuad || L.kind > kLossOrdinal)
+        if (L.kind < kLossQuad || L.kind >= kLossKinds)
             return fail(nullptr, GLRM_ERR_ARG, "bad loss kind in column " + std::to_string(j));
         if (L.kind == kLossHuber && !(L.param > 0.0 && isfinite(L.param)))
             return fail(nullptr, GLRM_ERR_ARG, "Huber threshold must be > 0 (column " + std::to_string(j) + ")");
+        if (L.kind == kLossQuantile && !(L.param > 0.0 && L.param < 1.0))
+            return fail(nullptr, GLRM_ERR_ARG, "quantile alpha must be in (0, 1) (column " + std::to_string(j) + ")");
         if (L.kind == kLossOrdinal && (L.levels < 2 || L.levels > 1024))
             return fail(nullptr, GLRM_ERR_ARG, "ordinal levels must be in [2, 1024] (column " + std::to_string(j) + ")");
         spec[j] = LossSpec{L.kind, L.kind == kLossOrdinal ? L.levels : 0,
-                           L.kind == kLossHuber ? L.param : 0.0};
+                           (L.kind == kLossHuber || L.kind == kLossQuantile) ? L.param : 0.0};
     }
     glrm_s *h = new (std::nothrow) glrm_s;
     if (!h) return fail(nullptr, GLRM_ERR_NOMEM, "host allocation failed");
@@ -1260,6 +1262,42 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (history) {
         CK(cudaMemcpyAsync(history, h->s.hist, (size_t)nsweeps * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
+        return read_status(h);
+    }
+    return GLRM_OK;
+}
+
+int glrm_proxprox_sweep(glrm_t h, int32_t nsweeps, double alpha, int32_t inner, double *history)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "glrm_proxprox_sweep before glrm_set_observed");
+    if (nsweeps < 0 || inner < 1 || !(alpha > 0.0) || !std::isfinite(alpha))
+        return fail(h, GLRM_ERR_ARG, "nsweeps >= 0, inner >= 1 and a finite alpha > 0 are required");
+    if (h->dn.on && !h->dn.missing)
+        return fail(h, GLRM_ERR_STATE, "prox-prox runs on an observed set, not on a dense table");
+    if (h->k > 32) return fail(h, GLRM_ERR_RANGE, "prox-prox supports k <= 32");
+    for (const LossSpec &L : h->loss_host)
+        if (L.kind != kLossQuad) return fail(h, GLRM_ERR_ARG, "prox-prox needs quadratic loss in every column");
+    if (nsweeps == 0) return GLRM_OK;
+    DeviceGuard dg(h->device);
+    int rc = ensure_hist(h, nsweeps);
+    if (rc != GLRM_OK) return rc;
+    const bool f64 = h->prec == GLRM_FP64;
+    for (int t = 0; t < nsweeps; ++t) {
+        cudaError_t e = f64 ? Engine<double>::proxprox_half(h, true, alpha, inner)
+                            : Engine<float>::proxprox_half(h, true, alpha, inner);
+        if (e == cudaSuccess)
+            e = f64 ? Engine<double>::proxprox_half(h, false, alpha, inner)
+                    : Engine<float>::proxprox_half(h, false, alpha, inner);
+        if (e == cudaSuccess)
+            e = f64 ? Engine<double>::objective_at(h, (const double *)h->X, (const double *)h->Yt, h->s.hist + t)
+                    : Engine<float>::objective_at(h, (const float *)h->X, (const float *)h->Yt, h->s.hist + t);
+        if (e != cudaSuccess) return cuda_fail(h, e, "glrm_proxprox_sweep");
+        h->sweeps_done++;
+    }
+    if (history) {
+        CK(cudaMemcpyAsync(history, h->s.hist, (size_t)nsweeps * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
         return read_status(h);
     }
     return GLRM_OK;

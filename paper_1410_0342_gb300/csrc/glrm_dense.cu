@@ -896,6 +896,8 @@ double group_cost(const std::vector<LossSpec> &loss, int64_t j0, int width)
         case kLossHuber: return 8;
         case kLossHinge: return 4;
         case kLossLogistic: return 22;
+        case kLossL1: return 5;
+        case kLossQuantile: return 6;
         default: return 16;
         }
     };
@@ -909,7 +911,7 @@ double group_cost(const std::vector<LossSpec> &loss, int64_t j0, int width)
     }
     if (uniform) return 6 + extra(loss[j0].kind);
     double c = 10;
-    for (int kd = 0; kd <= kLossOrdinal; ++kd)
+    for (int kd = 0; kd < kLossKinds; ++kd)
         if (seen >> kd & 1u) c += extra(kd);
     return c;
 }

@@ -12,6 +12,7 @@
 namespace glrm {
 
 constexpr int kLossQuad = 0, kLossHuber = 1, kLossHinge = 2, kLossLogistic = 3, kLossOrdinal = 4;
+constexpr int kLossL1 = 5, kLossQuantile = 6, kLossKinds = 7;
 constexpr int kRegZero = 0, kRegQuad = 1, kRegL1 = 2, kRegNonneg = 3;
 
 // One column's loss, 16 bytes so that a lane loads it with one instruction.
@@ -36,8 +37,11 @@ template <> __device__ __forceinline__ double xinf<double>() { return __longlong
 //   hinge (1 - a u)_+                                      Sec. 5.2
 //   logistic log(1 + exp(-a u)), overflow-free form        Sec. 5.2
 //   ordinal hinge over levels 1..d                         eq. ord-pca
+//   l1 |a - u|                                             Sec. 4.2 (robust PCA)
+//   quantile alpha (a - u)_+ + (1 - alpha) (u - a)_+        Sec. 4.2 (quantile PCA)
 // loss_deriv_k: one kind, its parameters already in T (param: the Huber
-// threshold; levels: the ordinal level count; others ignore them).
+// threshold or the quantile alpha; levels: the ordinal level count; others
+// ignore them).
 template <int KIND, class T>
 __device__ __forceinline__ T loss_deriv_k(T u, T a, T param, T levels, T &L)
 {
@@ -68,6 +72,14 @@ __device__ __forceinline__ T loss_deriv_k(T u, T a, T param, T levels, T &L)
         L = fmax(z, T(0)) + xlog1p(e);
         T sg = z >= T(0) ? T(1) / (T(1) + e) : e / (T(1) + e);
         return -a * sg;
+    } else if constexpr (KIND == kLossL1) {
+        T x = u - a;
+        L = fabs(x);
+        return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0));
+    } else if constexpr (KIND == kLossQuantile) {
+        T x = u - a;
+        L = x > T(0) ? (T(1) - param) * x : -param * x;
+        return x > T(0) ? T(1) - param : (x < T(0) ? -param : T(0));
     } else {
         // Ordinal hinge in closed form.  A term (1 - u + a')_+ with a' < a is
         // active (> 0) exactly for a' >= floor(u); a term (1 + u - a')_+ with
@@ -93,6 +105,8 @@ __device__ __forceinline__ T loss_deriv_kind(int kind, T u, T a, T param, T leve
     case kLossHuber: return loss_deriv_k<kLossHuber, T>(u, a, param, levels, L);
     case kLossHinge: return loss_deriv_k<kLossHinge, T>(u, a, param, levels, L);
     case kLossLogistic: return loss_deriv_k<kLossLogistic, T>(u, a, param, levels, L);
+    case kLossL1: return loss_deriv_k<kLossL1, T>(u, a, param, levels, L);
+    case kLossQuantile: return loss_deriv_k<kLossQuantile, T>(u, a, param, levels, L);
     default: return loss_deriv_k<kLossOrdinal, T>(u, a, param, levels, L);
     }
 }
@@ -227,7 +241,7 @@ __device__ __forceinline__ bool rsqrt_fp64(double d, double &y)
 // normal: G was not numerically positive definite (or held Inf / NaN); b
 // then holds no solution and must not be used.
 template <int K, int LD>
-__device__ __forceinline__ bool warp_cholesky_solve(double (*G)[LD], double *b)
+__device__ __forceinline__ bool warp_cholesky_factor(double (*G)[LD])
 {
     const int lane = threadIdx.x & 31;
     bool ok = true;
@@ -252,21 +266,35 @@ __device__ __forceinline__ bool warp_cholesky_solve(double (*G)[LD], double *b)
         }
         __syncwarp();
     }
-    // C w = b: w[c] = b[c] / C[c][c], then b[r] -= C[r][c] w[c] for r > c
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+// b <- (C C^T)^{-1} b with the factor warp_cholesky_factor left in G: C w = b
+// (w[c] = b[c] / C[c][c], then b[r] -= C[r][c] w[c] for r > c), then C^T x = w.
+template <int K, int LD>
+__device__ __forceinline__ void warp_cholesky_subst(double (*G)[LD], double *b)
+{
+    const int lane = threadIdx.x & 31;
     for (int c = 0; c < K; ++c) {
         if (lane == 0) b[c] *= G[c][c];
         __syncwarp();
         if (lane > c && lane < K) b[lane] -= G[lane][c] * b[c];
         __syncwarp();
     }
-    // C^T x = w: x[c] = w[c] / C[c][c], then b[r] -= C[c][r] x[c] for r < c
     for (int c = K - 1; c >= 0; --c) {
         if (lane == 0) b[c] *= G[c][c];
         __syncwarp();
         if (lane < c) b[lane] -= G[c][lane] * b[c];
         __syncwarp();
     }
-    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+template <int K, int LD>
+__device__ __forceinline__ bool warp_cholesky_solve(double (*G)[LD], double *b)
+{
+    const bool ok = warp_cholesky_factor<K, LD>(G);
+    warp_cholesky_subst<K, LD>(G, b);
+    return ok;
 }
 
 // Bits of the handle's device status word (Scratch::err).

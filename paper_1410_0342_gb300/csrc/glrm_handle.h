@@ -233,6 +233,7 @@ struct Engine {
                                T *out, bool decode);
     static cudaError_t reset_steps(glrm_s *h);
     static cudaError_t als_half(glrm_s *h, bool xstep, double gamma);
+    static cudaError_t proxprox_half(glrm_s *h, bool xstep, double alpha, int inner);
     static cudaError_t tiled_half_step(glrm_s *h, bool xstep);
     static cudaError_t masked_half_step(glrm_s *h, bool xstep);
 };

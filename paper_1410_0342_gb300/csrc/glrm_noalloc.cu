@@ -45,7 +45,7 @@ std::mutex g_setup_mutex;
 double *g_terms_ptr[kMaxDevices] = {};
 
 // A loss descriptor the sweep accepts: a known kind, a positive finite Huber
-// threshold, at least two ordinal levels.
+// threshold, a quantile alpha in (0, 1), at least two ordinal levels.
 __device__ __forceinline__ bool loss_ok(const LossSpec &L)
 {
     switch (L.kind) {
@@ -53,8 +53,12 @@ __device__ __forceinline__ bool loss_ok(const LossSpec &L)
     case glrm::kLossHinge:
     case glrm::kLossLogistic:
         return true;
+    case glrm::kLossL1:
+        return true;
     case glrm::kLossHuber:
         return L.param > 0.0 && L.param <= 1e300;
+    case glrm::kLossQuantile:
+        return L.param > 0.0 && L.param < 1.0;
     case glrm::kLossOrdinal:
         return L.levels >= 2;
     default:

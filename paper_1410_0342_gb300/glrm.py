@@ -18,6 +18,7 @@ GLRM_OK = 0
 GLRM_ERR_ARG, GLRM_ERR_RANGE, GLRM_ERR_OMEGA, GLRM_ERR_NONFINITE = -1, -2, -3, -4
 GLRM_ERR_CUDA, GLRM_ERR_TIMEOUT, GLRM_ERR_STATE, GLRM_ERR_NOMEM = -5, -6, -7, -8
 GLRM_LOSS_QUAD, GLRM_LOSS_HUBER, GLRM_LOSS_HINGE, GLRM_LOSS_LOGISTIC, GLRM_LOSS_ORDINAL_HINGE = range(5)
+GLRM_LOSS_L1, GLRM_LOSS_QUANTILE = 5, 6
 GLRM_REG_ZERO, GLRM_REG_QUAD, GLRM_REG_L1, GLRM_REG_NONNEG = range(4)
 GLRM_FP64, GLRM_FP32, GLRM_BF16 = 0, 1, 2
 GLRM_PATH_AUTO, GLRM_PATH_CHUNKED, GLRM_PATH_FUSED, GLRM_PATH_BLOCKED = 0, 1, 2, 3
@@ -61,6 +62,7 @@ def _load():
         "glrm_grad": [p, p, p],
         "glrm_predict": [p, i64, p, p, p, i32],
         "glrm_als_sweep": [p, i32, p],
+        "glrm_proxprox_sweep": [p, i32, f64, i32, p],
         "glrm_get_state": [p, p, p],
         "glrm_set_state": [p, p, ctypes.c_size_t],
         "glrm_timing_enable": [p, i32],
@@ -258,6 +260,15 @@ def glrm_als_sweep(h, nsweeps, history=True):
         _check(_lib.glrm_als_sweep(h, nsweeps, _ptr(out)), h)
         return out
     _check(_lib.glrm_als_sweep(h, nsweeps, None), h)
+    return None
+
+
+def glrm_proxprox_sweep(h, nsweeps, alpha, inner, history=True):
+    if history:
+        out = np.empty(nsweeps, dtype=np.float64)
+        _check(_lib.glrm_proxprox_sweep(h, nsweeps, float(alpha), int(inner), _ptr(out)), h)
+        return out
+    _check(_lib.glrm_proxprox_sweep(h, nsweeps, float(alpha), int(inner), None), h)
     return None
 
 
@@ -526,6 +537,9 @@ class GLRM:
 
     def als_sweep(self, nsweeps, history=True):
         return glrm_als_sweep(self.h, nsweeps, history)
+
+    def proxprox_sweep(self, nsweeps, alpha, inner, history=True):
+        return glrm_proxprox_sweep(self.h, nsweeps, alpha, inner, history)
 
     def objective(self):
         return glrm_objective(self.h)

@@ -22,6 +22,7 @@ import dataclasses
 import numpy as np
 
 LOSS_QUAD, LOSS_HUBER, LOSS_HINGE, LOSS_LOGISTIC, LOSS_ORDINAL = 0, 1, 2, 3, 4
+LOSS_L1, LOSS_QUANTILE = 5, 6
 REG_ZERO, REG_QUAD, REG_L1, REG_NONNEG = 0, 1, 2, 3
 
 BASE_SEED = 1410034200
@@ -253,14 +254,16 @@ def batch_instance(s: int, seed=BASE_SEED + 5, m_range=(50, 5000), n_range=(20, 
 
 
 def small_mixed(m=97, n=41, k=6, p_obs=0.55, seed=BASE_SEED + 20, rx=(REG_L1, 0.05),
-                ry=(REG_NONNEG, 0.0), levels=5):
-    """A small mixed table with every loss kind, for parity on ragged shapes."""
+                ry=(REG_NONNEG, 0.0), levels=5, nkinds=5, alpha=0.3):
+    """A small mixed table for parity on ragged shapes: column j takes loss
+    kind j mod nkinds (5: quadratic, Huber, hinge, logistic, ordinal hinge;
+    7: also l1 and the quantile loss with the given alpha)."""
     rng = rng_for(seed)
     X0 = rng.standard_normal((m, k))
     Y0t = rng.standard_normal((n, k))
     rowptr, colidx = omega_bernoulli(m, n, p_obs, rng)
     u = sampled_products(X0, Y0t, rowptr, colidx)
-    kinds = np.arange(n) % 5
+    kinds = np.arange(n) % nkinds
     val = np.empty_like(u)
     ke = kinds[colidx]
     val[ke == LOSS_QUAD] = u[ke == LOSS_QUAD] + 0.1 * rng.standard_normal(int((ke == 0).sum()))
@@ -271,7 +274,10 @@ def small_mixed(m=97, n=41, k=6, p_obs=0.55, seed=BASE_SEED + 20, rx=(REG_L1, 0.
         val[sel] = np.where(u[sel] + 0.5 * rng.standard_normal(int(sel.sum())) >= 0, 1.0, -1.0)
     sel = ke == LOSS_ORDINAL
     val[sel] = np.clip(np.round(u[sel] / 2.0 + (levels + 1) / 2.0), 1, levels)
-    param = np.where(kinds == LOSS_HUBER, 1.0, 0.0)
+    for kk in (LOSS_L1, LOSS_QUANTILE):
+        sel = ke == kk
+        val[sel] = u[sel] + rng.laplace(0.0, 0.5, int(sel.sum()))
+    param = np.where(kinds == LOSS_HUBER, 1.0, np.where(kinds == LOSS_QUANTILE, alpha, 0.0))
     lv = np.where(kinds == LOSS_ORDINAL, levels, 0)
     return _finish("small_mixed", m, n, k, rowptr, colidx, val, kinds, param, lv, rx, ry, rng)
 

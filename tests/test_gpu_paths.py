@@ -155,3 +155,14 @@ def test_benchmark_table_dense_path_matches_oracle(G, oracle_mod, m, nsweeps):
     assert G.glrm_get_path(g.h) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
     rels = synced_sweeps(g, oracle_mod, t, nsweeps)
     assert rels.max() < 1e-5
+
+
+@pytest.mark.parametrize("paths", [(1, 1), (2, 2), (3, 3), (4, 4), (4, 5), (6, 6)])
+def test_l1_and_quantile_losses_on_every_path(G, oracle_mod, paths):
+    """Columns cycling through all seven loss kinds (quadratic, Huber, hinge,
+    logistic, ordinal hinge, l1, quantile with alpha = 0.3) on every kernel
+    path, the dense form included: synced sweeps against the oracle."""
+    t = W.small_mixed(m=1303, n=140, k=12, p_obs=0.5, seed=407, nkinds=7)
+    g = G.GLRM.from_table(t)
+    G.glrm_set_path(g.h, *paths)
+    synced_sweeps(g, oracle_mod, t, 6)

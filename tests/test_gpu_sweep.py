@@ -332,3 +332,33 @@ def test_host_entry_points(G, oracle_mod):
     Xd, Yd = g.factors()
     np.testing.assert_array_equal(X, Xd.cpu().numpy())
     np.testing.assert_array_equal(Y, Yd.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec,reg,tol", [(0, (RQ, 0.1), 1e-9), (0, (RL1, 0.05), 1e-9),
+                                          (0, (RNN, 0.0), 1e-9), (1, (RQ, 0.1), 1e-4),
+                                          (1, (RNN, 0.0), 1e-4)])
+def test_proxprox_matches_oracle(G, oracle_mod, prec, reg, tol):
+    """Prox-prox sweeps (Sec. 7.2 update, Sec. 7.3 cached factorisation) on a
+    30%-missing quadratic-loss table with the given regulariser on both
+    factors: objectives after each of 6 sweeps (3 updates per row / column,
+    alpha = 0.5) and the final factors against the oracle's (no accept /
+    reject branch, so FP32 trajectories stay with the FP64 ones)."""
+    import dataclasses
+    t = W.batch_instance(0, m_range=(400, 400), n_range=(120, 120), ks=(8,))
+    t = dataclasses.replace(t, rx=reg, ry=reg)
+    g = G.GLRM.from_table(t, precision=prec)
+    h = g.proxprox_sweep(6, 0.5, 3)
+    X, Yt, oh = oracle_problem(oracle_mod, t).proxprox(t.X0, t.Yt0, 0.5, 3, 6)
+    assert np.isfinite(h).all()
+    assert relerr(h, oh).max() < tol, relerr(h, oh)
+    Xg, Yg = g.factors()
+    np.testing.assert_allclose(Xg.double().cpu().numpy(), X, rtol=tol * 10, atol=tol * 10)
+    np.testing.assert_allclose(Yg.double().cpu().numpy(), Yt, rtol=tol * 10, atol=tol * 10)
+
+
+def test_proxprox_rejects_non_quadratic(G):
+    t = W.small_mixed(m=50, n=20, k=4)
+    g = G.GLRM.from_table(t)
+    with pytest.raises(G.GLRMError) as e:
+        g.proxprox_sweep(1, 0.5, 2)
+    assert e.value.code == G.GLRM_ERR_ARG

@@ -11,6 +11,7 @@ import pytest
 from scipy import optimize, special
 
 Q, HU, HI, LO, OR = 0, 1, 2, 3, 4
+L1, QT = 5, 6
 RZ, RQ, RL1, RNN = 0, 1, 2, 3
 
 
@@ -25,6 +26,9 @@ def _fd(o, kind, u, a, param, levels, h=1e-6):
     (HI, 0.0, 0, [-1.0, 1.0]),
     (LO, 0.0, 0, [-1.0, 1.0]),
     (OR, 0.0, 7, [1, 2, 4, 7]),
+    (L1, 0.0, 0, [-1.3, 0.0, 2.5]),
+    (QT, 0.2, 0, [-1.3, 0.0, 2.5]),
+    (QT, 0.85, 0, [-1.3, 0.0, 2.5]),
 ])
 def test_derivative_matches_finite_difference(oracle_mod, kind, param, levels, avals):
     o = oracle_mod
@@ -37,6 +41,8 @@ def test_derivative_matches_finite_difference(oracle_mod, kind, param, levels, a
             if kind == HI and abs(a * u - 1) < 1e-3:
                 continue
             if kind == OR and abs(u - round(u)) < 1e-3:
+                continue
+            if kind in (L1, QT) and abs(u - a) < 1e-3:
                 continue
             assert o.dloss(kind, u, a, param, levels) == pytest.approx(
                 _fd(o, kind, u, a, param, levels), abs=1e-6, rel=1e-6)
@@ -171,3 +177,38 @@ def test_reg_values(oracle_mod):
     assert o.reg(RL1, 0.1, x) == pytest.approx(0.1 * np.abs(x).sum())
     assert math.isinf(o.reg(RNN, 0.0, x))
     assert o.reg(RNN, 0.0, np.abs(x)) == 0.0
+
+
+def test_l1_and_quantile_closed_forms(oracle_mod):
+    """l1: |a - u| (Sec. 4.2, robust PCA); quantile: alpha (a - u)_+ +
+    (1 - alpha) (u - a)_+ (Sec. 4.2, quantile PCA), which at alpha = 1/2 is
+    half the l1 loss; at the kink u = a both take the zero subgradient; both
+    decode to u."""
+    o = oracle_mod
+    rng = np.random.default_rng(7)
+    for u, a in rng.normal(0, 2, size=(50, 2)):
+        assert o.loss(L1, u, a) == pytest.approx(abs(a - u), rel=1e-15)
+        assert o.loss(QT, u, a, 0.5) == pytest.approx(0.5 * abs(a - u), rel=1e-15)
+        al = 0.3
+        want = al * (a - u) if a > u else (1 - al) * (u - a)
+        assert o.loss(QT, u, a, al) == pytest.approx(want, rel=1e-15)
+    assert o.dloss(L1, 1.25, 1.25) == 0.0 and o.dloss(QT, -0.5, -0.5, 0.3) == 0.0
+    assert o.decode(L1, 3.7) == 3.7 and o.decode(QT, -2.25) == -2.25
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.5, 0.9])
+def test_quantile_loss_minimiser_is_the_quantile(oracle_mod, alpha):
+    """The scalene loss performs quantile regression (Sec. 4.2): over a
+    constant prediction mu, sum_i L(mu, a_i) is minimised at the alpha-quantile
+    of the a_i -- the order statistic a_(ceil(alpha n)) -- which brute force
+    over a fine grid confirms."""
+    o = oracle_mod
+    rng = np.random.default_rng(11)
+    a = rng.normal(0, 1, size=101)
+    total = lambda mu: sum(o.loss(QT, float(mu), float(ai), alpha) for ai in a)
+    q = np.sort(a)[int(np.ceil(alpha * a.size)) - 1]
+    grid = np.linspace(a.min() - 0.5, a.max() + 0.5, 4001)
+    best = min(total(g) for g in grid)
+    assert total(q) <= best + 1e-12
+    # and strictly better than moving off it in either direction
+    assert total(q - 0.05) > total(q) and total(q + 0.05) > total(q)

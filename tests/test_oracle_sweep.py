@@ -36,10 +36,11 @@ def test_objective_matches_matrix_form(oracle_mod):
     assert p.objective(X, Yt) == pytest.approx(ref, rel=1e-13)
 
 
-def test_objective_brute_force_mixed(oracle_mod):
+@pytest.mark.parametrize("nkinds", [5, 7])
+def test_objective_brute_force_mixed(oracle_mod, nkinds):
     """Every loss kind and regulariser, summed cell by cell over a dense mask."""
     o = oracle_mod
-    t = W.small_mixed(m=13, n=11, k=3, seed=3, rx=(RL1, 0.2), ry=(RQ, 0.3))
+    t = W.small_mixed(m=13, n=11, k=3, seed=3, rx=(RL1, 0.2), ry=(RQ, 0.3), nkinds=nkinds)
     p = _problem(o, t)
     rows = t.rows()
     X, Yt = t.X0, t.Yt0
@@ -336,3 +337,63 @@ def test_gradient_variation_closed_forms(oracle_mod):
     np.testing.assert_allclose(VX[0], np.abs(Yh[0]), rtol=1e-15)
     np.testing.assert_allclose(VY[0], np.abs(Xh[0]), rtol=1e-15)
     assert not VY[1].any()
+
+
+def _one_row(o, rng, n=9, k=3, reg=(RZ, 0.0)):
+    Yt = rng.normal(size=(n, k))
+    a = rng.normal(size=n)
+    p = o.Problem(1, n, k, np.zeros(n, np.int32), np.arange(n, dtype=np.int32), a, Q, 0.0, 0,
+                  rx=reg, ry=(RZ, 0.0))
+    return p, Yt, a, Yt.T @ Yt, Yt.T @ a
+
+
+def test_proxprox_fixed_point_least_squares(oracle_mod):
+    """r = 0: the prox-prox update's fixed point (Sec. 7.2) is the exact
+    least-squares solution G x = b of the row problem (the Y-step that
+    follows does not touch the returned row)."""
+    o = oracle_mod
+    rng = np.random.default_rng(21)
+    p, Yt, a, G, b = _one_row(o, rng)
+    X, *_ = p.proxprox(rng.normal(size=(1, 3)), Yt, alpha=0.5, inner=4000, nsweeps=1)
+    np.testing.assert_allclose(X[0], np.linalg.solve(G, b), rtol=1e-9)
+
+
+def test_proxprox_fixed_point_quadratic_regulariser(oracle_mod):
+    """r = gamma ||x||^2: x = prox_{alpha r}(prox_{alpha f}(x)) with
+    prox_{alpha f}(x) = (2 alpha G + I)^{-1}(2 alpha b + x) and prox_{alpha r}
+    = scaling by 1 / (1 + 2 alpha gamma) holds exactly when
+    ((1 + 2 alpha gamma) G + gamma I) x = b (derived by substituting one into
+    the other).  That is the minimiser of the Moreau envelope of f plus r,
+    which differs from the minimiser of f + r, (G + gamma I) x = b, unless
+    alpha -> 0."""
+    o = oracle_mod
+    rng = np.random.default_rng(22)
+    gam, al = 0.7, 0.4
+    p, Yt, a, G, b = _one_row(o, rng, reg=(RQ, gam))
+    X, *_ = p.proxprox(rng.normal(size=(1, 3)), Yt, alpha=al, inner=4000, nsweeps=1)
+    np.testing.assert_allclose(X[0], np.linalg.solve((1 + 2 * al * gam) * G + gam * np.eye(3), b),
+                               rtol=1e-9)
+    assert np.abs(X[0] - np.linalg.solve(G + gam * np.eye(3), b)).max() > 1e-3
+
+
+def test_proxprox_fixed_point_nonnegative(oracle_mod):
+    """r = indicator of x >= 0: the update is a projected gradient step on the
+    Moreau envelope M(x) = f(P x) + ||x - P x||^2 / (2 alpha), P x =
+    prox_{alpha f}(x), so its fixed point minimises M over x >= 0; an
+    independent bounded quasi-Newton solve of that problem agrees."""
+    from scipy import optimize
+    o = oracle_mod
+    rng = np.random.default_rng(23)
+    al = 0.3
+    p, Yt, a, G, b = _one_row(o, rng, n=12, k=4, reg=(RNN, 0.0))
+    X, *_ = p.proxprox(np.abs(rng.normal(size=(1, 4))), Yt, alpha=al, inner=20000, nsweeps=1)
+    Mi = np.linalg.inv(2 * al * G + np.eye(4))
+
+    def env(x):
+        px = Mi @ (2 * al * b + x)
+        return np.sum((Yt @ px - a) ** 2) + np.sum((x - px) ** 2) / (2 * al)
+
+    res = optimize.minimize(env, np.ones(4), method="L-BFGS-B", bounds=[(0, None)] * 4,
+                            options={"ftol": 1e-15, "gtol": 1e-12, "maxiter": 10000})
+    assert X[0].min() >= 0.0 and (X[0] == 0.0).any()
+    np.testing.assert_allclose(X[0], res.x, atol=2e-5)
