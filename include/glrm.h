@@ -183,6 +183,45 @@ int glrm_get_factors(glrm_t h, void *X_dev, void *Yt_dev);
 int glrm_set_factors_host(glrm_t h, const void *X_host, const void *Yt_host);
 int glrm_get_factors_host(glrm_t h, void *X_host, void *Yt_host);
 
+/* Offset (Section 3.4, "Offsets and scaling"; the k+1 construction): with
+ * on != 0 the last coordinate of every row of X is held at 1 (its
+ * regulariser is the indicator of x_ik = 1, whose prox returns 1) and the
+ * last coordinate of every column of Y is not regularised, so y_jk acts as a
+ * per-column offset mu_j of x_i . y_j.  The other k-1 coordinates keep the
+ * model's regulariser.  A row whose last coordinate is not 1 has objective
+ * +inf until its next X-step, which sets it to 1 (the step is accepted: its
+ * candidate's objective is finite).  Applies to glrm_sweep,
+ * glrm_sweep_until, glrm_objective* and glrm_grad* on every path (the
+ * regulariser gradient of the held coordinate is taken as 0);
+ * glrm_als_sweep and glrm_proxprox_sweep return GLRM_ERR_ARG while it is on.
+ * Takes effect for work enqueued afterwards; on = 0 turns it off. */
+int glrm_set_offset(glrm_t h, int32_t on);
+
+/* Column statistics of the automatic loss scaling (Section 4.3, "Offsets and
+ * scaling"): for each column j with c_j >= 1 observed entries a_e,
+ *   mu_dev[j]     = the smallest minimiser of S_j(mu) = sum_e L_j(mu, a_e)
+ *                   (the mean for quadratic loss, the lower median for l1,
+ *                   the alpha-quantile for quantile loss),
+ *   sigma2_dev[j] = S_j(mu_j) / (c_j - 1)   (the sample variance for
+ *                   quadratic loss; NaN when c_j < 2),
+ * both NaN for an empty column.  mu_j is found by bisection on the sign of
+ * the FP64 sum of L_j'(mu, a_e) in [min a - 32, max a + 32], to 2^-62 of that
+ * width; where S_j has no minimiser (a hinge or logistic column of one
+ * label) mu_j is the bracket end it decreases towards.  Device pointers, n
+ * doubles each, written on the handle's stream (returns once enqueued).
+ * Reads the observed set (or the dense table). */
+int glrm_column_stats(glrm_t h, double *mu_dev, double *sigma2_dev);
+
+/* Per-column loss weights (the scaled losses of Section 4.3): with
+ * w_host != NULL (n finite doubles > 0, copied) column j's loss becomes
+ * w_j L_j everywhere (sweeps, objective, gradients); w_j = 1 / sigma2_j
+ * gives the paper's standardised GLRM.  NULL removes them.  Weighted models
+ * run every half-step on the chunked path (glrm_get_path reports
+ * GLRM_PATH_CHUNKED); GLRM_BF16 models and fully observed dense tables
+ * (glrm_set_dense) return GLRM_ERR_ARG / GLRM_ERR_STATE, as do
+ * glrm_als_sweep and glrm_proxprox_sweep on a weighted model.  Synchronises. */
+int glrm_set_column_scale(glrm_t h, const double *w_host);
+
 /* Reset every row step size to 1/max(n_i, 1) and every column step size to
  * 1/max(m_j, 1) (Section 7.2, "Choosing a step size", scale 1). */
 int glrm_reset_steps(glrm_t h);

@@ -29,6 +29,11 @@ Parity status of each function (the pins live in tests/test_oracle_*.py):
                                        row / column: alpha = 1, x <- prox(x))
   als                                  pinned (normal equations vs numpy.linalg,
                                        qPCA closed form)
+  column_stats                         pinned (quadratic: mean and sample variance;
+                                       l1: median; quantile: the alpha-quantile,
+                                       brute force over a grid)
+  offset                               pinned (k = 1: the offset row converges
+                                       to the column statistic mu_j)
   proxprox                             pinned (fixed points: the least-squares
                                        solution for r = 0, the closed form
                                        ((1 + 2 alpha gamma) G + gamma I) x = b
@@ -87,22 +92,24 @@ def _load():
         lib.oracle_prox.argtypes = [i32, d, d, i32, p, p]
         lib.oracle_objective.restype = d
         lib.oracle_objective.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p,
-                                         i32, d, i32, d, p, p, i32]
+                                         i32, d, i32, d, i32, p, p, p, i32]
         lib.oracle_gradient.restype = i32
-        lib.oracle_gradient.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, p, p, i32]
+        lib.oracle_gradient.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, p, p, p, i32]
         lib.oracle_gradient_abs.restype = i32
         lib.oracle_gradient_abs.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, p, p, i32]
         lib.oracle_gradient_variation.restype = i32
         lib.oracle_gradient_variation.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, d, p,
                                                   p, i32]
         lib.oracle_proxgrad.restype = i32
-        lib.oracle_proxgrad.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, i32, d, i32, d,
-                                        p, p, p, p, i32, p, p, i32]
+        lib.oracle_proxgrad.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, i32, d, i32, d, i32,
+                                        p, p, p, p, p, i32, p, p, i32]
         lib.oracle_als.restype = i32
         lib.oracle_als.argtypes = [i64, i64, i32, i64, p, p, p, d, p, p, i32, p, i32]
         lib.oracle_proxprox.restype = i32
         lib.oracle_proxprox.argtypes = [i64, i64, i32, i64, p, p, p, i32, d, i32, d, d, i32, p, p, i32,
                                         p, i32]
+        lib.oracle_column_stats.restype = i32
+        lib.oracle_column_stats.argtypes = [i64, i64, i64, p, p, p, p, p, p, p, p, i32]
         lib.oracle_num_threads.restype = i32
         lib.oracle_num_threads.argtypes = [i32]
         _lib = lib
@@ -156,7 +163,7 @@ class Problem:
     per-column losses and the row / column regularisers."""
 
     def __init__(self, m, n, k, rows, cols, vals, loss_kind, loss_param, loss_levels,
-                 rx=(REG_ZERO, 0.0), ry=(REG_ZERO, 0.0)):
+                 rx=(REG_ZERO, 0.0), ry=(REG_ZERO, 0.0), offset=False, col_scale=None):
         self.m, self.n, self.k = int(m), int(n), int(k)
         self.rows = _c(rows, np.int32)
         self.cols = _c(cols, np.int32)
@@ -167,6 +174,11 @@ class Problem:
         self.loss_levels = _c(np.broadcast_to(loss_levels, (self.n,)), np.int32)
         self.rx = (int(rx[0]), float(rx[1]))
         self.ry = (int(ry[0]), float(ry[1]))
+        # offset (Sec. 3.4): the last coordinate of X is held at 1, that of Y
+        # is not penalised
+        self.offset = bool(offset)
+        # per-column loss weights w_j (the scaled losses w_j L_j of Sec. 4.3)
+        self.col_scale = None if col_scale is None else _c(np.broadcast_to(col_scale, (self.n,)), np.float64)
 
     @classmethod
     def from_csr(cls, m, n, k, rowptr, colidx, vals, **kw):
@@ -190,6 +202,9 @@ class Problem:
         return (self.m, self.n, self.k, self.nnz, _ptr(self.rows), _ptr(self.cols),
                 _ptr(self.vals))
 
+    def _scale(self):
+        return None if self.col_scale is None else _ptr(self.col_scale)
+
     def _losses(self):
         return (_ptr(self.loss_kind), _ptr(self.loss_param), _ptr(self.loss_levels))
 
@@ -198,7 +213,7 @@ class Problem:
         X = _c(X, np.float64)
         Yt = _c(Yt, np.float64)
         return _load().oracle_objective(*self._common(), *self._losses(), *self.rx, *self.ry,
-                                        _ptr(X), _ptr(Yt), nthreads)
+                                        int(self.offset), self._scale(), _ptr(X), _ptr(Yt), nthreads)
 
     def gradient(self, X, Yt, nthreads: int = 0):
         """Loss part of the gradient: G_X = R Y^T and G_Y^T = R^T X over Omega (Sec. 7.2)."""
@@ -206,7 +221,7 @@ class Problem:
         Yt = _c(Yt, np.float64)
         GX = np.empty_like(X)
         GYt = np.empty_like(Yt)
-        rc = _load().oracle_gradient(*self._common(), *self._losses(), _ptr(X), _ptr(Yt),
+        rc = _load().oracle_gradient(*self._common(), *self._losses(), self._scale(), _ptr(X), _ptr(Yt),
                                      _ptr(GX), _ptr(GYt), nthreads)
         if rc:
             raise ValueError(f"oracle_gradient failed ({rc})")
@@ -256,7 +271,9 @@ class Problem:
         hist = np.empty(nsweeps, dtype=np.float64)
         acc = np.empty(2 * nsweeps, dtype=np.int64)
         rc = _load().oracle_proxgrad(*self._common(), *self._losses(), *self.rx, *self.ry,
-                                     _ptr(X), _ptr(Yt), _ptr(alpha_x), _ptr(alpha_y), nsweeps,
+                                     int(self.offset), self._scale(), _ptr(X), _ptr(Yt), _ptr(alpha_x),
+                                     _ptr(alpha_y),
+                                     nsweeps,
                                      _ptr(hist), _ptr(acc), nthreads)
         if rc:
             raise ValueError(f"oracle_proxgrad failed ({rc})")
@@ -273,6 +290,18 @@ class Problem:
         if rc:
             raise ValueError(f"oracle_als failed ({rc})")
         return X, Yt, hist
+
+    def column_stats(self, nthreads: int = 0):
+        """(mu, sigma2) per column (Sec. 4.3, "Offsets and scaling"): mu_j
+        minimises sum_i L_j(mu, A_ij) over the column's observed entries and
+        sigma2_j = sum_i L_j(mu_j, A_ij) / (n_j - 1)."""
+        mu = np.empty(self.n)
+        s2 = np.empty(self.n)
+        rc = _load().oracle_column_stats(self.m, self.n, self.nnz, _ptr(self.rows), _ptr(self.cols),
+                                         _ptr(self.vals), *self._losses(), _ptr(mu), _ptr(s2), nthreads)
+        if rc:
+            raise ValueError(f"oracle_column_stats failed ({rc})")
+        return mu, s2
 
     def proxprox(self, X, Yt, alpha: float, inner: int, nsweeps: int, nthreads: int = 0):
         """Alternating prox-prox sweeps for quadratic loss (Sec. 7.2 prox-prox

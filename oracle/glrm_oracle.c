@@ -205,6 +205,32 @@ void oracle_prox(int kind, double w, double alpha, int k, const double *z, doubl
     }
 }
 
+/* Offsets (Section 3.4, "Offsets and scaling"): the model's factors carry one
+ * extra coordinate, here the last one (index k-1).  The regulariser of a row
+ * of X becomes r'(x) = r(x_1 .. x_{k-1}) if x_k = 1, +inf otherwise, and that
+ * of a column of Y becomes r~'(y) = r~(y_1 .. y_{k-1}): the offset column of X
+ * is the constant 1 and the offset row of Y (the column offsets mu_j) is not
+ * penalised.  role: 0 none, 1 a row of X, 2 a column of Y. */
+static double reg_vec(int kind, double w, int k, const double *x, int role)
+{
+    if (role == 0) return oracle_reg(kind, w, k, x);
+    double r = oracle_reg(kind, w, k - 1, x);
+    if (role == 1 && x[k - 1] != 1.0) return INFINITY;
+    return r;
+}
+
+/* prox of the regulariser above: r's prox on the first k-1 coordinates; the
+ * last one is projected onto {1} (a row of X) or left as it is (a column of Y). */
+static void prox_vec(int kind, double w, double alpha, int k, const double *z, double *out, int role)
+{
+    if (role == 0) {
+        oracle_prox(kind, w, alpha, k, z, out);
+        return;
+    }
+    oracle_prox(kind, w, alpha, k - 1, z, out);
+    out[k - 1] = role == 1 ? 1.0 : z[k - 1];
+}
+
 /* ------------------------------------------------------------- Omega lists */
 
 /* The observed set is given as coordinate triples (row, col, value) sorted by
@@ -279,7 +305,10 @@ typedef struct {
     const int32_t *kind;
     const double *param;
     const int32_t *levels;
+    const double *w; /* per-column loss weights (Section 4.3 scaling); NULL: all 1 */
 } loss_table;
+
+static double col_weight(const loss_table *lt, int64_t j) { return lt->w ? lt->w[j] : 1.0; }
 
 static double list_loss(int k, const double *v, const double *W, const int32_t *idx,
                         const double *a, int64_t cnt, const loss_table *lt, int64_t fixed_col)
@@ -288,7 +317,7 @@ static double list_loss(int k, const double *v, const double *W, const int32_t *
     for (int64_t e = 0; e < cnt; ++e) {
         int64_t j = fixed_col >= 0 ? fixed_col : idx[e];
         double u = dot(k, v, W + (int64_t)idx[e] * k);
-        s += oracle_loss(lt->kind[j], lt->param[j], lt->levels[j], u, a[e]);
+        s += col_weight(lt, j) * oracle_loss(lt->kind[j], lt->param[j], lt->levels[j], u, a[e]);
     }
     return s;
 }
@@ -302,7 +331,7 @@ static double list_loss(int k, const double *v, const double *W, const int32_t *
  * Returns 1 when the step was accepted.  *fkept receives f of the kept vector. */
 static int update_vector(int k, double *v, double *alpha, const double *W, const int32_t *idx,
                          const double *a, int64_t cnt, const loss_table *lt, int64_t fixed_col,
-                         int rkind, double rw, double *fkept, double *rkept)
+                         int rkind, double rw, int role, double *fkept, double *rkept)
 {
     double g[k], z[k], vp[k];
     for (int c = 0; c < k; ++c) g[c] = 0.0;
@@ -310,13 +339,13 @@ static int update_vector(int k, double *v, double *alpha, const double *W, const
         int64_t j = fixed_col >= 0 ? fixed_col : idx[e];
         const double *w = W + (int64_t)idx[e] * k;
         double u = dot(k, v, w);
-        double r = oracle_dloss(lt->kind[j], lt->param[j], lt->levels[j], u, a[e]);
+        double r = col_weight(lt, j) * oracle_dloss(lt->kind[j], lt->param[j], lt->levels[j], u, a[e]);
         for (int c = 0; c < k; ++c) g[c] += r * w[c];
     }
     for (int c = 0; c < k; ++c) z[c] = v[c] - (*alpha) * g[c];
-    oracle_prox(rkind, rw, *alpha, k, z, vp);
-    double r_old = oracle_reg(rkind, rw, k, v);
-    double r_new = oracle_reg(rkind, rw, k, vp);
+    prox_vec(rkind, rw, *alpha, k, z, vp, role);
+    double r_old = reg_vec(rkind, rw, k, v, role);
+    double r_new = reg_vec(rkind, rw, k, vp, role);
     double f_old = list_loss(k, v, W, idx, a, cnt, lt, fixed_col) + r_old;
     double f_new = list_loss(k, vp, W, idx, a, cnt, lt, fixed_col) + r_new;
     if (f_new <= f_old) {
@@ -346,7 +375,7 @@ static int set_threads(int nthreads)
 /* Full objective (eq. gpca):  sum over Omega of L (rows ascending, then each
  * row's columns ascending) + sum_i r(x_i) + sum_j rt(y_j). */
 static double objective_lists(const omega_lists *L, int k, const double *X, const double *Yt,
-                              const loss_table *lt, int rxk, double rxw, int ryk, double ryw)
+                              const loss_table *lt, int rxk, double rxw, int ryk, double ryw, int offset)
 {
     double *rowsum = malloc(sizeof(double) * (size_t)(L->m ? L->m : 1));
     int64_t i;
@@ -356,8 +385,8 @@ static double objective_lists(const omega_lists *L, int k, const double *X, cons
                               L->rstart[i + 1] - L->rstart[i], lt, -1);
     double F = 0.0;
     for (i = 0; i < L->m; ++i) F += rowsum[i];
-    for (i = 0; i < L->m; ++i) F += oracle_reg(rxk, rxw, k, X + i * k);
-    for (int64_t j = 0; j < L->n; ++j) F += oracle_reg(ryk, ryw, k, Yt + j * k);
+    for (i = 0; i < L->m; ++i) F += reg_vec(rxk, rxw, k, X + i * k, offset ? 1 : 0);
+    for (int64_t j = 0; j < L->n; ++j) F += reg_vec(ryk, ryw, k, Yt + j * k, offset ? 2 : 0);
     free(rowsum);
     return F;
 }
@@ -365,14 +394,15 @@ static double objective_lists(const omega_lists *L, int k, const double *X, cons
 double oracle_objective(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
                         const int32_t *col, const double *val, const int32_t *lkind,
                         const double *lparam, const int32_t *llevels, int rxk, double rxw,
-                        int ryk, double ryw, const double *X, const double *Yt, int nthreads)
+                        int ryk, double ryw, int offset, const double *wcol, const double *X,
+                        const double *Yt, int nthreads)
 {
     omega_lists L;
     memset(&L, 0, sizeof L);
     if (lists_build(&L, m, n, nnz, row, col, val)) { lists_free(&L); return NAN; }
     set_threads(nthreads);
-    loss_table lt = { lkind, lparam, llevels };
-    double F = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw);
+    loss_table lt = { lkind, lparam, llevels, wcol };
+    double F = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw, offset);
     lists_free(&L);
     return F;
 }
@@ -382,8 +412,8 @@ double oracle_objective(int64_t m, int64_t n, int k, int64_t nnz, const int32_t 
  *   GYt[j] = sum_{i in Omega_j} L'_j(x_i . y_j, A_ij) x_i               */
 int oracle_gradient(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
                     const int32_t *col, const double *val, const int32_t *lkind,
-                    const double *lparam, const int32_t *llevels, const double *X,
-                    const double *Yt, double *GX, double *GYt, int nthreads)
+                    const double *lparam, const int32_t *llevels, const double *wcol,
+                    const double *X, const double *Yt, double *GX, double *GYt, int nthreads)
 {
     omega_lists L;
     memset(&L, 0, sizeof L);
@@ -398,7 +428,7 @@ int oracle_gradient(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row
         for (int64_t e = L.rstart[i]; e < L.rstart[i + 1]; ++e) {
             int32_t jj = L.rcol[e];
             double u = dot(k, X + i * k, Yt + (int64_t)jj * k);
-            double r = oracle_dloss(lkind[jj], lparam[jj], llevels[jj], u, L.rval[e]);
+            double r = (wcol ? wcol[jj] : 1.0) * oracle_dloss(lkind[jj], lparam[jj], llevels[jj], u, L.rval[e]);
             for (int c = 0; c < k; ++c) g[c] += r * Yt[(int64_t)jj * k + c];
         }
     }
@@ -409,7 +439,7 @@ int oracle_gradient(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row
         for (int64_t e = L.cstart[j]; e < L.cstart[j + 1]; ++e) {
             int32_t ii = L.crow[e];
             double u = dot(k, X + (int64_t)ii * k, Yt + j * k);
-            double r = oracle_dloss(lkind[j], lparam[j], llevels[j], u, L.cval[e]);
+            double r = (wcol ? wcol[j] : 1.0) * oracle_dloss(lkind[j], lparam[j], llevels[j], u, L.cval[e]);
             for (int c = 0; c < k; ++c) h[c] += r * X[(int64_t)ii * k + c];
         }
     }
@@ -524,15 +554,15 @@ int oracle_gradient_variation(int64_t m, int64_t n, int k, int64_t nnz, const in
 int oracle_proxgrad(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row,
                     const int32_t *col, const double *val, const int32_t *lkind,
                     const double *lparam, const int32_t *llevels, int rxk, double rxw, int ryk,
-                    double ryw, double *X, double *Yt, double *alpha_x, double *alpha_y,
-                    int nsweeps, double *history, int64_t *accepts, int nthreads)
+                    double ryw, int offset, const double *wcol, double *X, double *Yt, double *alpha_x,
+                    double *alpha_y, int nsweeps, double *history, int64_t *accepts, int nthreads)
 {
     omega_lists L;
     memset(&L, 0, sizeof L);
     int rc = lists_build(&L, m, n, nnz, row, col, val);
     if (rc) { lists_free(&L); return rc; }
     set_threads(nthreads);
-    loss_table lt = { lkind, lparam, llevels };
+    loss_table lt = { lkind, lparam, llevels, wcol };
     double *fx = malloc(sizeof(double) * (size_t)(m ? m : 1));
     double *rx = malloc(sizeof(double) * (size_t)(m ? m : 1));
     double *fy = malloc(sizeof(double) * (size_t)(n ? n : 1));
@@ -545,20 +575,20 @@ int oracle_proxgrad(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row
         for (i = 0; i < m; ++i) {
             int64_t b = L.rstart[i];
             ax[i] = update_vector(k, X + i * k, alpha_x + i, Yt, L.rcol + b, L.rval + b,
-                                  L.rstart[i + 1] - b, &lt, -1, rxk, rxw, fx + i, rx + i);
+                                  L.rstart[i + 1] - b, &lt, -1, rxk, rxw, offset ? 1 : 0, fx + i, rx + i);
         }
 #pragma omp parallel for schedule(dynamic, 4)
         for (j = 0; j < n; ++j) {
             int64_t b = L.cstart[j];
             ay[j] = update_vector(k, Yt + j * k, alpha_y + j, X, L.crow + b, L.cval + b,
-                                  L.cstart[j + 1] - b, &lt, j, ryk, ryw, fy + j, ry + j);
+                                  L.cstart[j + 1] - b, &lt, j, ryk, ryw, offset ? 2 : 0, fy + j, ry + j);
         }
         int64_t na = 0, nb = 0;
         for (i = 0; i < m; ++i) na += ax[i];
         for (j = 0; j < n; ++j) nb += ay[j];
         if (accepts) { accepts[2 * t] = na; accepts[2 * t + 1] = nb; }
         if (history)
-            history[t] = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw);
+            history[t] = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw, offset);
     }
     free(fx); free(rx); free(fy); free(ry); free(ax); free(ay);
     lists_free(&L);
@@ -636,7 +666,7 @@ int oracle_als(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row, con
     double *param = malloc(sizeof(double) * (size_t)(n ? n : 1));
     int32_t *lev = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
     for (int64_t j = 0; j < n; ++j) { kind[j] = LOSS_QUAD; param[j] = 0.0; lev[j] = 0; }
-    loss_table lt = { kind, param, lev };
+    loss_table lt = { kind, param, lev, NULL };
     int bad = 0;
     for (int t = 0; t < nsweeps && !bad; ++t) {
         int64_t i, j;
@@ -651,7 +681,7 @@ int oracle_als(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row, con
             bad |= solve_vector(k, Yt + j * k, X, L.crow + b, L.cval + b, L.cstart[j + 1] - b, gamma) != 0;
         }
         if (history)
-            history[t] = objective_lists(&L, k, X, Yt, &lt, REG_QUAD, gamma, REG_QUAD, gamma);
+            history[t] = objective_lists(&L, k, X, Yt, &lt, REG_QUAD, gamma, REG_QUAD, gamma, 0);
     }
     free(kind); free(param); free(lev);
     lists_free(&L);
@@ -706,7 +736,7 @@ int oracle_proxprox(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row
     double *param = malloc(sizeof(double) * (size_t)(n ? n : 1));
     int32_t *lev = malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
     for (int64_t j = 0; j < n; ++j) { kind[j] = LOSS_QUAD; param[j] = 0.0; lev[j] = 0; }
-    loss_table lt = { kind, param, lev };
+    loss_table lt = { kind, param, lev, NULL };
     int bad = 0;
     for (int t = 0; t < nsweeps && !bad; ++t) {
         int64_t i, j;
@@ -723,11 +753,73 @@ int oracle_proxprox(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row
                                    inner, ryk, ryw) != 0;
         }
         if (history)
-            history[t] = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw);
+            history[t] = objective_lists(&L, k, X, Yt, &lt, rxk, rxw, ryk, ryw, 0);
     }
     free(kind); free(param); free(lev);
     lists_free(&L);
     return bad ? -3 : 0;
+}
+
+/* Column statistics for the automatic scaling of Section 4.3 ("Offsets and
+ * scaling"): for each column j with observed entries a_i,
+ *   mu_j      = argmin_mu sum_i L_j(mu, a_i),
+ *   sigma2_j  = sum_i L_j(mu_j, a_i) / (n_j - 1)     (NaN when n_j < 2).
+ * The sum is convex in mu; it is minimised directly by golden-section search
+ * on [min a - 32, max a + 32] down to an interval of 1e-13 of its width.
+ * The search compares sums, so their rounding error limits where it can place
+ * the minimiser: the sums are compensated (Neumaier), which keeps them
+ * accurate to a few units of rounding whatever the column's length. */
+static double col_sum(int kind, double param, int levels, const double *a, int64_t cnt, double mu)
+{
+    double s = 0.0, c = 0.0;
+    for (int64_t e = 0; e < cnt; ++e) {
+        double v = oracle_loss(kind, param, levels, mu, a[e]);
+        double t = s + v;
+        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    return s + c;
+}
+
+int oracle_column_stats(int64_t m, int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
+                        const double *val, const int32_t *lkind, const double *lparam,
+                        const int32_t *llevels, double *mu, double *sigma2, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    int rc = lists_build(&L, m, n, nnz, row, col, val);
+    if (rc) { lists_free(&L); return rc; }
+    set_threads(nthreads);
+    int64_t j;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (j = 0; j < n; ++j) {
+        const double *a = L.cval + L.cstart[j];
+        const int64_t cnt = L.cstart[j + 1] - L.cstart[j];
+        if (cnt == 0) { mu[j] = NAN; sigma2[j] = NAN; continue; }
+        double lo = a[0], hi = a[0];
+        for (int64_t e = 1; e < cnt; ++e) { lo = a[e] < lo ? a[e] : lo; hi = a[e] > hi ? a[e] : hi; }
+        lo -= 32.0;
+        hi += 32.0;
+        const double gr = 0.5 * (sqrt(5.0) - 1.0), width = hi - lo;
+        double x1 = hi - gr * (hi - lo), x2 = lo + gr * (hi - lo);
+        double f1 = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, x1);
+        double f2 = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, x2);
+        while (hi - lo > 1e-13 * width) {
+            if (f1 <= f2) {
+                hi = x2; x2 = x1; f2 = f1;
+                x1 = hi - gr * (hi - lo);
+                f1 = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, x1);
+            } else {
+                lo = x1; x1 = x2; f1 = f2;
+                x2 = lo + gr * (hi - lo);
+                f2 = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, x2);
+            }
+        }
+        mu[j] = 0.5 * (lo + hi);
+        sigma2[j] = cnt > 1 ? col_sum(lkind[j], lparam[j], llevels[j], a, cnt, mu[j]) / (double)(cnt - 1) : NAN;
+    }
+    lists_free(&L);
+    return 0;
 }
 
 int oracle_num_threads(int nthreads) { return set_threads(nthreads); }

@@ -170,7 +170,7 @@ proxprox_solve_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const 
         if (lane < K) x[wid][lane] = b[wid][lane] + f;
         __syncwarp();
         warp_cholesky_subst<K, K + 1>(G[wid], x[wid]);
-        if (lane < K) f = lane < k ? prox1<double>(rkind, rw, alpha, x[wid][lane]) : 0.0;
+        if (lane < K) f = lane < k ? prox1<double>(reg_kind_at(rkind, lane, k), rw, alpha, x[wid][lane]) : 0.0;
         __syncwarp();
     }
     if (lane < k) F[s * k + lane] = (T)f;
@@ -234,7 +234,7 @@ cudaError_t launch_proxprox_half(glrm_s *h, bool xstep, double alpha, int inner)
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "proxprox_x" : "proxprox_y");
     proxprox_solve_kernel<T, K><<<blocks_for(o.nseg, kAlsWarps), kAlsWarps * 32, 0, h->stream>>>(
-        o.nseg, o.segchunk, part, h->k, alpha, inner, xstep ? h->rx_kind : h->ry_kind,
+        o.nseg, o.segchunk, part, h->k, alpha, inner, reg_code(h, xstep),
         xstep ? h->rx_w : h->ry_w, F, h->s.err);
     tmark(h, nullptr);
     return cudaGetLastError();

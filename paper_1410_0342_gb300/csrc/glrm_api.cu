@@ -100,6 +100,8 @@ cudaError_t run_half(glrm_s *h, bool xstep) { return Engine<T>::half_step(h, xst
 
 cudaError_t half_step(glrm_s *h, bool xstep)
 {
+    // scaled losses (glrm_set_column_scale) run on the chunked path
+    if (h->lscale) return h->prec == GLRM_FP64 ? run_half<double>(h, xstep) : run_half<float>(h, xstep);
     if (h->dn.on) return dense_half_step(h, xstep);
     const Orient &o = xstep ? h->csr : h->csc;
     if (o.mode == kModeMasked)
@@ -373,6 +375,9 @@ int alloc_scratch(glrm_s *h)
     free_scratch(s, h->stream);
     const size_t es = elem_size(h->prec);
     int64_t nch = std::max<int64_t>(1, std::max(partial_slots(h->csr), partial_slots(h->csc)));
+    // the chunked passes (objective, gradient, weighted half-steps) write one
+    // slot per chunk whatever path the half-steps take
+    nch = std::max<int64_t>(nch, std::max(h->csr.nchunks, h->csc.nchunks));
     if (h->dn.on) nch = std::max<int64_t>(nch, h->dn.slots);
     const int Kt = std::max(h->k, tiled_width(h->k));
     const int64_t mx = std::max(h->m, h->n);
@@ -1052,6 +1057,51 @@ int glrm_get_factors_host(glrm_t h, void *X, void *Yt)
              : fail(nullptr, GLRM_ERR_ARG, "null handle");
 }
 
+int glrm_set_offset(glrm_t h, int32_t on)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (h->offset != (on != 0)) drop_conv_graph(h);  // captured sweeps carry the regulariser codes
+    h->offset = on != 0;
+    return GLRM_OK;
+}
+
+int glrm_set_column_scale(glrm_t h, const double *w_host)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (h->prec == GLRM_BF16) return fail(h, GLRM_ERR_ARG, "column loss weights need a GLRM_FP32 or GLRM_FP64 model");
+    if (w_host && h->dn.on && !h->dn.missing)
+        return fail(h, GLRM_ERR_STATE, "column loss weights run on an observed set, not on a dense table");
+    DeviceGuard dg(h->device);
+    drop_conv_graph(h);  // captured sweeps carry the weight pointer
+    if (!w_host) {
+        dfree(h->lscale, h->stream);
+        return GLRM_OK;
+    }
+    for (int64_t j = 0; j < h->n; ++j)
+        if (!(w_host[j] > 0.0) || !std::isfinite(w_host[j]))
+            return fail(h, GLRM_ERR_ARG, "column loss weights must be finite and > 0");
+    const size_t es = elem_size(h->prec);
+    std::vector<unsigned char> buf((size_t)h->n * es);
+    for (int64_t j = 0; j < h->n; ++j) {
+        if (h->prec == GLRM_FP64) reinterpret_cast<double *>(buf.data())[j] = w_host[j];
+        else reinterpret_cast<float *>(buf.data())[j] = (float)w_host[j];
+    }
+    if (!h->lscale) CK(dalloc_bytes(h, &h->lscale, buf.size(), h->stream));
+    CK(cudaMemcpyAsync(h->lscale, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GLRM_OK;
+}
+
+int glrm_column_stats(glrm_t h, double *mu_dev, double *sigma2_dev)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!mu_dev || !sigma2_dev) return fail(h, GLRM_ERR_ARG, "null pointer");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    DeviceGuard dg(h->device);
+    cudaError_t e = launch_column_stats(h, mu_dev, sigma2_dev);
+    return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_column_stats");
+}
+
 int glrm_reset_steps(glrm_t h)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
@@ -1173,7 +1223,7 @@ int glrm_objective_at(glrm_t h, const void *X, const void *Yt, double *out)
     if (!X || !Yt || !out) return fail(h, GLRM_ERR_ARG, "null pointer");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->dn.on ? dense_objective_at(h, (const float *)X, (const float *)Yt, out)
+    cudaError_t e = h->dn.on && !h->lscale ? dense_objective_at(h, (const float *)X, (const float *)Yt, out)
                     : h->prec == GLRM_FP64
                         ? Engine<double>::objective_at(h, (const double *)X, (const double *)Yt, out)
                         : Engine<float>::objective_at(h, (const float *)X, (const float *)Yt, out);
@@ -1201,7 +1251,7 @@ int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, i
     if (include_reg && (h->rx_kind == kRegNonneg || h->ry_kind == kRegNonneg))
         return fail(h, GLRM_ERR_ARG, "the nonnegativity indicator has no gradient");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->dn.on ? dense_grad_at(h, (const float *)X, (const float *)Yt, (float *)GX, (float *)GYt,
+    cudaError_t e = h->dn.on && !h->lscale ? dense_grad_at(h, (const float *)X, (const float *)Yt, (float *)GX, (float *)GYt,
                                              include_reg != 0, scale)
                     : h->prec == GLRM_FP64
                         ? Engine<double>::grad_at(h, (const double *)X, (const double *)Yt,
@@ -1236,6 +1286,8 @@ int glrm_als_sweep(glrm_t h, int32_t nsweeps, double *history)
     if (nsweeps < 0) return fail(h, GLRM_ERR_ARG, "nsweeps < 0");
     if (h->dn.on && !h->dn.missing)
         return fail(h, GLRM_ERR_STATE, "ALS runs on an observed set, not on a dense table");
+    if (h->offset) return fail(h, GLRM_ERR_ARG, "ALS does not take an offset (glrm_set_offset)");
+    if (h->lscale) return fail(h, GLRM_ERR_ARG, "ALS does not take column loss weights (glrm_set_column_scale)");
     if (h->rx_kind != kRegQuad || h->ry_kind != kRegQuad || h->rx_w != h->ry_w || !(h->rx_w > 0.0))
         return fail(h, GLRM_ERR_ARG,
                     "ALS needs quadratic regularisers of equal weight gamma > 0 on X and Y");
@@ -1276,6 +1328,8 @@ int glrm_proxprox_sweep(glrm_t h, int32_t nsweeps, double alpha, int32_t inner, 
     if (h->dn.on && !h->dn.missing)
         return fail(h, GLRM_ERR_STATE, "prox-prox runs on an observed set, not on a dense table");
     if (h->k > 32) return fail(h, GLRM_ERR_RANGE, "prox-prox supports k <= 32");
+    if (h->offset || h->lscale)
+        return fail(h, GLRM_ERR_ARG, "prox-prox takes neither an offset nor column loss weights");
     for (const LossSpec &L : h->loss_host)
         if (L.kind != kLossQuad) return fail(h, GLRM_ERR_ARG, "prox-prox needs quadratic loss in every column");
     if (nsweeps == 0) return GLRM_OK;
@@ -1396,6 +1450,10 @@ int glrm_get_path(glrm_t h, int32_t *paths_host)
 {
     if (!h || !paths_host) return fail(h, GLRM_ERR_ARG, "null argument");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    if (h->lscale) {
+        paths_host[0] = paths_host[1] = GLRM_PATH_CHUNKED;
+        return GLRM_OK;
+    }
     if (h->dn.on) {
         paths_host[0] = paths_host[1] = GLRM_PATH_DENSE;
         return GLRM_OK;
@@ -1463,6 +1521,7 @@ void glrm_destroy(glrm_t h)
         dense_free(h);
         free_scratch(h->s, h->stream);
         dfree(h->loss_dev, h->stream);
+        dfree(h->lscale, h->stream);
         dfree(h->X, h->stream);
         dfree(h->Yt, h->stream);
         dfree(h->alpha_x, h->stream);

@@ -136,7 +136,7 @@ inline cudaError_t bf16_half_step(glrm_s *h, bool xstep)
     float *F = (float *)(xstep ? h->X : h->Yt);
     const float *W = (const float *)(xstep ? h->Yt : h->X);
     float *alpha = (float *)(xstep ? h->alpha_x : h->alpha_y);
-    const int rk = xstep ? h->rx_kind : h->ry_kind;
+    const int rk = reg_code(h, xstep);
     const float rw = (float)(xstep ? h->rx_w : h->ry_w);
     const int64_t nother = xstep ? h->n : h->m;
     int32_t *acc = xstep ? s.acc_x : s.acc_y;  // previous decision per segment (1: accepted)

@@ -1261,7 +1261,7 @@ cudaError_t dense_half_step(glrm_s *h, bool xstep)
     float *F = (float *)(xstep ? h->X : h->Yt);
     const float *W = (const float *)(xstep ? h->Yt : h->X);
     float *alpha = (float *)(xstep ? h->alpha_x : h->alpha_y);
-    const int rk = xstep ? h->rx_kind : h->ry_kind;
+    const int rk = reg_code(h, xstep);
     const float rw = (float)(xstep ? h->rx_w : h->ry_w);
     Scratch &s = h->s;
     cudaStream_t st = h->stream;
@@ -1299,8 +1299,8 @@ cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, doubl
     if ((e = launch_dense<true, false>(h, X, nullptr, s.part_loss)) != cudaSuccess) return e;
     tmark(h, "reduce_stage1");
     reduce_stage1<float><<<kRedBlocks, 256, 0, h->stream>>>(
-        s.part_loss, h->dn.slots_x, nullptr, 0, X, h->m, h->rx_kind, (float)h->rx_w, Yt, h->n,
-        h->ry_kind, (float)h->ry_w, h->k, nullptr, 0, nullptr, 0, s.red_part, s.red_cnt);
+        s.part_loss, h->dn.slots_x, nullptr, 0, X, h->m, reg_code(h, true), (float)h->rx_w, Yt, h->n,
+        reg_code(h, false), (float)h->ry_w, h->k, nullptr, 0, nullptr, 0, s.red_part, s.red_cnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, "reduce_stage2");
     reduce_stage2<<<1, 256, 0, h->stream>>>(s.red_part, s.red_cnt, kRedBlocks, out, nullptr);
@@ -1319,14 +1319,14 @@ cudaError_t dense_grad_at(glrm_s *h, const float *X, const float *Yt, float *GX,
     if ((e = launch_dense<true, true>(h, X, (float *)s.part_grad, s.part_loss)) != cudaSuccess) return e;
     tmark(h, "grad_seg_x");
     seg_grad_kernel<float><<<blocks_for(h->m, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->m, h->dn.segchunk_x, (const float *)s.part_grad, X, h->k, h->rx_kind, (float)h->rx_w, reg, scale, GX);
+        h->m, h->dn.segchunk_x, (const float *)s.part_grad, X, h->k, reg_code(h, true), (float)h->rx_w, reg, scale, GX);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = dense_pack(h, X, h->m)) != cudaSuccess) return e;
     tmark(h, "dense_grad_y");
     if ((e = launch_dense<false, true>(h, Yt, (float *)s.part_grad, s.part_loss)) != cudaSuccess) return e;
     tmark(h, "grad_seg_y");
     seg_grad_kernel<float><<<blocks_for(h->n, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->n, h->dn.segchunk_y, (const float *)s.part_grad, Yt, h->k, h->ry_kind, (float)h->ry_w, reg, scale,
+        h->n, h->dn.segchunk_y, (const float *)s.part_grad, Yt, h->k, reg_code(h, false), (float)h->ry_w, reg, scale,
         GYt);
     tmark(h, nullptr);
     h->launches += 2;

@@ -14,6 +14,20 @@ namespace glrm {
 constexpr int kLossQuad = 0, kLossHuber = 1, kLossHinge = 2, kLossLogistic = 3, kLossOrdinal = 4;
 constexpr int kLossL1 = 5, kLossQuantile = 6, kLossKinds = 7;
 constexpr int kRegZero = 0, kRegQuad = 1, kRegL1 = 2, kRegNonneg = 3;
+// Internal: the indicator of x = 1 (an offset coordinate of X).
+constexpr int kRegFixOne = 4;
+// Offset roles carried above the regulariser kind passed to the kernels
+// (kind | role << 8): the last coordinate of X is held at 1 and the last
+// coordinate of Y is not penalised (Section 3.4, "Offsets and scaling").
+constexpr int kOffsetX = 1, kOffsetY = 2;
+
+// The regulariser kind of coordinate c of k under an encoded kind rk.
+__host__ __device__ __forceinline__ int reg_kind_at(int rk, int c, int k)
+{
+    const int role = rk >> 8;
+    if (role && c == k - 1) return role == kOffsetX ? kRegFixOne : kRegZero;
+    return rk & 0xff;
+}
 
 // One column's loss, 16 bytes so that a lane loads it with one instruction.
 struct __align__(16) LossSpec {
@@ -140,7 +154,8 @@ __device__ __forceinline__ T decode_value(const LossSpec &s, T u)
 }
 
 // prox_{alpha r} of one coordinate (every regulariser here is separable):
-// z/(1 + 2 alpha w), soft threshold at alpha w, max(z, 0), identity.
+// z/(1 + 2 alpha w), soft threshold at alpha w, max(z, 0), 1 (an offset
+// coordinate of X), identity.
 template <class T>
 __device__ __forceinline__ T prox1(int kind, T w, T alpha, T z)
 {
@@ -153,6 +168,8 @@ __device__ __forceinline__ T prox1(int kind, T w, T alpha, T z)
     }
     case kRegNonneg:
         return z > T(0) ? z : T(0);
+    case kRegFixOne:
+        return T(1);
     default:
         return z;
     }
@@ -169,6 +186,8 @@ __device__ __forceinline__ double reg1(int kind, T w, T x)
         return (double)w * fabs((double)x);
     case kRegNonneg:
         return x < T(0) ? xinf<double>() : 0.0;
+    case kRegFixOne:
+        return x == T(1) ? 0.0 : xinf<double>();
     default:
         return 0.0;
     }
@@ -186,6 +205,8 @@ __device__ __forceinline__ T reg1t(int kind, T w, T x)
         return w * fabs(x);
     case kRegNonneg:
         return x < T(0) ? xinf<T>() : T(0);
+    case kRegFixOne:
+        return x == T(1) ? T(0) : xinf<T>();
     default:
         return T(0);
     }

@@ -115,13 +115,16 @@ __device__ __forceinline__ void load_lane_w(T (&v)[S], const WT *__restrict__ ro
 // (G lanes per entry, PER = 32 / G entries per iteration), the rows of the
 // other factor gathered in the lane layout above.  `order` (nullable) is the
 // chunk launch order; with `sel` (nullable) the launch takes only the chunks
-// of segments whose sel value is nonzero exactly when want is.
+// of segments whose sel value is nonzero exactly when want is.  `lsc`
+// (nullable) holds per-column loss weights: entry (i, j) contributes
+// lsc[j] L_j and lsc[j] L_j' (the scaled losses of Section 4.3).
 template <class T, int K, bool XSTEP, bool VEC, bool GRAD, class WT = T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ order,
             const int32_t *__restrict__ idx, const T *__restrict__ val, const T *__restrict__ F,
             const WT *__restrict__ W, int k, const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
-            double *__restrict__ part_loss, const int32_t *__restrict__ sel, int want)
+            double *__restrict__ part_loss, const int32_t *__restrict__ sel, int want,
+            const T *__restrict__ lsc)
 {
     using LN = Lanes<K>;
     constexpr int G = LN::G, S = LN::S, PER = LN::PER;
@@ -139,7 +142,11 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
     for (int s = 0; s < S; ++s) g[s] = T(0);
     T lsum = T(0);
     LossSpec sp;
-    if constexpr (!XSTEP) sp = loss[ch.x];
+    T wsc = T(1);
+    if constexpr (!XSTEP) {
+        sp = loss[ch.x];
+        if (lsc) wsc = __ldg(lsc + ch.x);
+    }
     for (int base = ch.y; base < ch.z; base += PER) {
         const int e = base + grp;
         const bool ok = e < ch.z;
@@ -160,9 +167,16 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) u += shfl_xor(u, o);
         if (ok) {
-            if constexpr (XSTEP) sp = loss[j];
+            if constexpr (XSTEP) {
+                sp = loss[j];
+                if (lsc) wsc = __ldg(lsc + j);
+            }
             T L;
             T d = loss_deriv<T>(sp, u, a, L);
+            if (lsc) {
+                d *= wsc;
+                L *= wsc;
+            }
             if constexpr (GRAD) {
 #pragma unroll
                 for (int s = 0; s < S; ++s) g[s] = fma(d, w[s], g[s]);
@@ -226,10 +240,11 @@ prox_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restr
             for (int q = cb + 1; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
         }
         const T x = F[s * k + c];
-        const T xp = prox1<T>(rkind, rw, al, x - al * g);
+        const int rkc = reg_kind_at(rkind, c, k);
+        const T xp = prox1<T>(rkc, rw, al, x - al * g);
         cand[s * k + c] = xp;
-        ro += reg1t<T>(rkind, rw, x);
-        rn += reg1t<T>(rkind, rw, xp);
+        ro += reg1t<T>(rkc, rw, x);
+        rn += reg1t<T>(rkc, rw, xp);
     }
     ro = warp_sum(ro);
     rn = warp_sum(rn);
@@ -292,11 +307,13 @@ reduce_stage1(const double *__restrict__ a, int64_t na, const double *__restrict
     if (b) { range(nb, lo, hi); for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += b[i]; }
     if (X) {
         range(m * k, lo, hi);
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += reg1<T>(rxk, rxw, X[i]);
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+            v += reg1<T>(reg_kind_at(rxk, (int)(i % k), k), rxw, X[i]);
     }
     if (Yt) {
         range(n * k, lo, hi);
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += reg1<T>(ryk, ryw, Yt[i]);
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+            v += reg1<T>(reg_kind_at(ryk, (int)(i % k), k), ryw, Yt[i]);
     }
     if (ca) { range(nca, lo, hi); for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c1 += ca[i]; }
     if (cb) { range(ncb, lo, hi); for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c2 += cb[i]; }
@@ -373,7 +390,7 @@ seg_grad_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__r
 #pragma unroll 8
             for (int q = cb + 1; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
         }
-        if (reg) g += reg_grad1<T>(rkind, rw, F[s * k + c]);
+        if (reg) g += reg_grad1<T>(reg_kind_at(rkind, c, k), rw, F[s * k + c]);
         G[s * k + c] = sc * g;
     }
 }
@@ -414,7 +431,8 @@ inline unsigned blocks_for(int64_t items, int per_block)
 
 template <class T, int K, bool XSTEP, bool GRAD, class WT>
 cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
-                        T *part_grad, double *part_loss, cudaStream_t st, const int32_t *sel, int want)
+                        T *part_grad, double *part_loss, cudaStream_t st, const int32_t *sel, int want,
+                        const T *lsc)
 {
     if (o.nchunks == 0) return cudaSuccess;
     // the BF16 copy is read 8 values at a time, so its vector path needs k % 8 == 0
@@ -424,14 +442,14 @@ cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const L
     const unsigned nb = blocks_for(o.nchunks, kWarpsPerBlock);
     if constexpr (std::is_same<WT, __nv_bfloat16>::value && Lanes<K>::S % 8 != 0) {
         pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-            o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want);
+            o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want, lsc);
     } else {
         if (vec)
             pass_kernel<T, K, XSTEP, true, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want);
+                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want, lsc);
         else
             pass_kernel<T, K, XSTEP, false, GRAD, WT><<<nb, kWarpsPerBlock * 32, 0, st>>>(
-                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want);
+                o.nchunks, o.chunks, o.order, o.idx, (const T *)o.val, F, W, k, loss, part_grad, part_loss, sel, want, lsc);
     }
     return cudaGetLastError();
 }
@@ -440,10 +458,10 @@ cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const L
 template <class T, bool XSTEP, bool GRAD, class WT = T>
 cudaError_t dispatch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
                           T *part_grad, double *part_loss, cudaStream_t st, const int32_t *sel = nullptr,
-                          int want = 0)
+                          int want = 0, const T *lsc = nullptr)
 {
 #define GLRM_PASS_CASE(KK) \
-    if (k <= KK) return launch_pass<T, KK, XSTEP, GRAD, WT>(o, F, W, k, loss, part_grad, part_loss, st, sel, want);
+    if (k <= KK) return launch_pass<T, KK, XSTEP, GRAD, WT>(o, F, W, k, loss, part_grad, part_loss, st, sel, want, lsc);
     GLRM_PASS_CASE(4)
     GLRM_PASS_CASE(8)
     GLRM_PASS_CASE(12)
@@ -464,7 +482,7 @@ cudaError_t Engine<T>::half_step(glrm_s *h, bool xstep)
     T *F = (T *)(xstep ? h->X : h->Yt);
     const T *W = (const T *)(xstep ? h->Yt : h->X);
     T *alpha = (T *)(xstep ? h->alpha_x : h->alpha_y);
-    const int rk = xstep ? h->rx_kind : h->ry_kind;
+    const int rk = reg_code(h, xstep);
     const T rw = (T)(xstep ? h->rx_w : h->ry_w);
     Scratch &s = h->s;
     cudaStream_t st = h->stream;
@@ -475,8 +493,9 @@ cudaError_t Engine<T>::half_step(glrm_s *h, bool xstep)
         if (h->prec == GLRM_BF16) return bf16_half_step_entry(h, xstep);
     }
     tmark(h, xstep ? "pass_grad_x" : "pass_grad_y");
-    e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st)
-              : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st);
+    const T *lsc = (const T *)h->lscale;
+    e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st, nullptr, 0, lsc)
+              : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st, nullptr, 0, lsc);
     if (e != cudaSuccess) return e;
     const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
@@ -485,8 +504,10 @@ cudaError_t Engine<T>::half_step(glrm_s *h, bool xstep)
                                                        s.f_old, s.r_old, s.r_new);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, xstep ? "pass_loss_x" : "pass_loss_y");
-    e = xstep ? dispatch_pass<T, true, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st)
-              : dispatch_pass<T, false, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st);
+    e = xstep ? dispatch_pass<T, true, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st,
+                                              nullptr, 0, lsc)
+              : dispatch_pass<T, false, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st,
+                                               nullptr, 0, lsc);
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "decide_x" : "decide_y");
     decide_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
@@ -523,12 +544,12 @@ cudaError_t Engine<T>::objective_at(glrm_s *h, const T *X, const T *Yt, double *
     Scratch &s = h->s;
     tmark(h, "objective_pass");
     cudaError_t e = dispatch_pass<T, true, false>(h->csr, X, Yt, h->k, h->loss_dev, nullptr,
-                                                  s.part_loss, h->stream);
+                                                  s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     if (e != cudaSuccess) return e;
     tmark(h, "reduce_stage1");
     reduce_stage1<T><<<kRedBlocks, 256, 0, h->stream>>>(
-        s.part_loss, h->csr.nchunks, nullptr, 0, X, h->m, h->rx_kind, (T)h->rx_w, Yt, h->n,
-        h->ry_kind, (T)h->ry_w, h->k, nullptr, 0, nullptr, 0, s.red_part, s.red_cnt);
+        s.part_loss, h->csr.nchunks, nullptr, 0, X, h->m, reg_code(h, true), (T)h->rx_w, Yt, h->n,
+        reg_code(h, false), (T)h->ry_w, h->k, nullptr, 0, nullptr, 0, s.red_part, s.red_cnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, "reduce_stage2");
     reduce_stage2<<<1, 256, 0, h->stream>>>(s.red_part, s.red_cnt, kRedBlocks, out, nullptr);
@@ -561,15 +582,15 @@ cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt
                                                             (T *)s.part_grad, s.part_loss, h->stream);
         else
             e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev, (T *)s.part_grad,
-                                             s.part_loss, h->stream);
+                                             s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     } else {
         e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev, (T *)s.part_grad, s.part_loss,
-                                         h->stream);
+                                         h->stream, nullptr, 0, (const T *)h->lscale);
     }
     if (e != cudaSuccess) return e;
     tmark(h, "grad_seg_x");
     seg_grad_kernel<T><<<blocks_for(h->m, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->m, h->csr.segchunk, (const T *)s.part_grad, X, h->k, h->rx_kind, (T)h->rx_w, reg, scale, GX);
+        h->m, h->csr.segchunk, (const T *)s.part_grad, X, h->k, reg_code(h, true), (T)h->rx_w, reg, scale, GX);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tmark(h, "grad_pass_y");
     if constexpr (std::is_same<T, float>::value) {
@@ -578,15 +599,15 @@ cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt
                                                              (T *)s.part_grad, s.part_loss, h->stream);
         else
             e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
-                                              s.part_loss, h->stream);
+                                              s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     } else {
         e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
-                                          s.part_loss, h->stream);
+                                          s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     }
     if (e != cudaSuccess) return e;
     tmark(h, "grad_seg_y");
     seg_grad_kernel<T><<<blocks_for(h->n, kWarpsPerBlock), kWarpsPerBlock * 32, 0, h->stream>>>(
-        h->n, h->csc.segchunk, (const T *)s.part_grad, Yt, h->k, h->ry_kind, (T)h->ry_w, reg, scale, GYt);
+        h->n, h->csc.segchunk, (const T *)s.part_grad, Yt, h->k, reg_code(h, false), (T)h->ry_w, reg, scale, GYt);
     tmark(h, nullptr);
     h->launches += 2 + (h->csr.nchunks ? 1 : 0) + (h->csc.nchunks ? 1 : 0);
     return cudaGetLastError();

@@ -163,6 +163,8 @@ struct glrm_s {
     std::vector<glrm::LossSpec> loss_host;
     glrm::LossSpec *loss_dev = nullptr;
     int rx_kind = 0, ry_kind = 0;
+    bool offset = false;  // last coordinate of X held at 1, of Y unpenalised (glrm_set_offset)
+    void *lscale = nullptr;  // n per-column loss weights, element type (glrm_set_column_scale); null: all 1
     double rx_w = 0.0, ry_w = 0.0;
     void *X = nullptr, *Yt = nullptr;          // factors
     void *alpha_x = nullptr, *alpha_y = nullptr;  // step sizes, element type
@@ -192,6 +194,14 @@ struct glrm_s {
 namespace glrm {
 
 size_t elem_size(int prec);
+
+// The regulariser kind the kernels of one half-step take: the model's kind
+// with the offset role of that factor above it (see reg_kind_at).
+inline int reg_code(const glrm_s *h, bool xstep)
+{
+    const int rk = xstep ? h->rx_kind : h->ry_kind;
+    return h->offset ? rk | ((xstep ? kOffsetX : kOffsetY) << 8) : rk;
+}
 
 // Handle memory: stream-ordered allocations from a per-device pool (on the
 // handle's stream; freeing is ordered after the work queued before it).
@@ -249,6 +259,8 @@ cudaError_t launch_check_entries(const Orient &o, bool rows, int64_t other, int6
 cudaError_t launch_digest_compare(const unsigned long long *d, int *flag, cudaStream_t st);
 cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep);
 cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
+// Per-column statistics mu_j, sigma2_j of the loss scaling (glrm_stats.cu).
+cudaError_t launch_column_stats(glrm_s *h, double *mu, double *s2);
 // Dense, fully observed form (tensor cores, FP32 models).
 bool dense_supported(int k);
 void dense_free(glrm_s *h);

@@ -427,11 +427,11 @@ mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
                     const T x = f.get(c);
-                    const T xp = c < k ? prox1<T>(rk, rw, al, x - al * g.get(c)) : T(0);
+                    const T xp = c < k ? prox1<T>(reg_kind_at(rk, c, k), rw, al, x - al * g.get(c)) : T(0);
                     tmp[c] = xp;
                     if (c < k) {
-                        rold += reg1t<T>(rk, rw, x);
-                        rnew += reg1t<T>(rk, rw, xp);
+                        rold += reg1t<T>(reg_kind_at(rk, c, k), rw, x);
+                        rnew += reg1t<T>(reg_kind_at(rk, c, k), rw, xp);
                     }
                 }
                 fp.load_masked(tmp, K);
@@ -494,10 +494,11 @@ unit_prox_kernel(int64_t nseg, const int32_t *__restrict__ ubeg, const T *__rest
         T g = T(0);
         for (int u = u0; u < u1; ++u) g += part_grad[((int64_t)u * 32 + l) * K + c];
         const T x = F[s * k + c];
-        const T xp = prox1<T>(rkind, rw, al, x - al * g);
+        const int rkc = reg_kind_at(rkind, c, k);
+        const T xp = prox1<T>(rkc, rw, al, x - al * g);
         cand[s * k + c] = xp;
-        ro += reg1t<T>(rkind, rw, x);
-        rn += reg1t<T>(rkind, rw, xp);
+        ro += reg1t<T>(rkc, rw, x);
+        rn += reg1t<T>(rkc, rw, xp);
     }
     ro = warp_sum(ro);
     rn = warp_sum(rn);
@@ -575,7 +576,7 @@ cudaError_t mt_half_src(glrm_s *h)
     const T *W = (const T *)(XSTEP ? h->Yt : h->X);
     const int64_t nother = XSTEP ? h->n : h->m;
     T *alpha = (T *)(XSTEP ? h->alpha_x : h->alpha_y);
-    const int rk = XSTEP ? h->rx_kind : h->ry_kind;
+    const int rk = reg_code(h, XSTEP);
     const T rw = (T)(XSTEP ? h->rx_w : h->ry_w);
     Scratch &s = h->s;
     double *kobj = XSTEP ? s.kept_obj_x : s.kept_obj_y;

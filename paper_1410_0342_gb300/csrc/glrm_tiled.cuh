@@ -261,7 +261,7 @@ __device__ __forceinline__ double reg_of(const Vec<T, K> &v, int k, int rk, T rw
     T r = T(0);
 #pragma unroll
     for (int c = 0; c < K; ++c)
-        if (c < k) r += reg1t<T>(rk, rw, v.get(c));
+        if (c < k) r += reg1t<T>(reg_kind_at(rk, c, k), rw, v.get(c));
     return (double)r;
 }
 
@@ -464,11 +464,11 @@ fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *
 #pragma unroll
             for (int c = 0; c < K; ++c) {
                 const T x = f.get(c);
-                const T xp = c < k ? prox1<T>(rk, rw, al, x - al * g.get(c)) : T(0);
+                const T xp = c < k ? prox1<T>(reg_kind_at(rk, c, k), rw, al, x - al * g.get(c)) : T(0);
                 tmp[c] = xp;
                 if (c < k) {
-                    rold += reg1t<T>(rk, rw, x);
-                    rnew += reg1t<T>(rk, rw, xp);
+                    rold += reg1t<T>(reg_kind_at(rk, c, k), rw, x);
+                    rnew += reg1t<T>(reg_kind_at(rk, c, k), rw, xp);
                 }
             }
             fp.load_masked(tmp, K);
@@ -627,10 +627,11 @@ blocked_prox_kernel(int64_t nseg, int nb, const T *__restrict__ part_grad,
         T g = T(0);
         for (int b = 0; b < nb; ++b) g += part_grad[((int64_t)b * nseg + s) * K + c];
         const T x = F[s * k + c];
-        const T xp = prox1<T>(rkind, rw, al, x - al * g);
+        const int rkc = reg_kind_at(rkind, c, k);
+        const T xp = prox1<T>(rkc, rw, al, x - al * g);
         cand[s * k + c] = xp;
-        ro += reg1t<T>(rkind, rw, x);
-        rn += reg1t<T>(rkind, rw, xp);
+        ro += reg1t<T>(rkc, rw, x);
+        rn += reg1t<T>(rkc, rw, xp);
     }
     ro = warp_sum(ro);
     rn = warp_sum(rn);
@@ -710,7 +711,7 @@ cudaError_t tiled_half_K(glrm_s *h, bool xstep_unused)
     const T *W = (const T *)(XSTEP ? h->Yt : h->X);
     const int64_t nother = XSTEP ? h->n : h->m;
     T *alpha = (T *)(XSTEP ? h->alpha_x : h->alpha_y);
-    const int rk = XSTEP ? h->rx_kind : h->ry_kind;
+    const int rk = reg_code(h, XSTEP);
     const T rw = (T)(XSTEP ? h->rx_w : h->ry_w);
     Scratch &s = h->s;
     double *kobj = XSTEP ? s.kept_obj_x : s.kept_obj_y;

@@ -53,6 +53,9 @@ def _load():
         "glrm_set_factors_host": [p, p, p],
         "glrm_get_factors_host": [p, p, p],
         "glrm_reset_steps": [p],
+        "glrm_set_offset": [p, i32],
+        "glrm_column_stats": [p, p, p],
+        "glrm_set_column_scale": [p, p],
         "glrm_sweep": [p, i32, p],
         "glrm_sweep_until": [p, i32, f64, f64, i32, p, p],
         "glrm_last_accepts": [p, p],
@@ -196,6 +199,24 @@ def glrm_set_factors_host(h, X, Yt):
 
 def glrm_get_factors_host(h, X, Yt):
     _check(_lib.glrm_get_factors_host(h, _ptr(X), _ptr(Yt)), h)
+
+
+def glrm_set_offset(h, on=True):
+    _check(_lib.glrm_set_offset(h, 1 if on else 0), h)
+
+
+def glrm_column_stats(h, mu, sigma2):
+    """mu, sigma2: float64 device tensors of n values."""
+    _check(_lib.glrm_column_stats(h, _ptr(mu), _ptr(sigma2)), h)
+
+
+def glrm_set_column_scale(h, w=None):
+    """w: n positive finite weights (host), or None to remove them."""
+    if w is None:
+        _check(_lib.glrm_set_column_scale(h, None), h)
+        return
+    arr = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    _check(_lib.glrm_set_column_scale(h, _ptr(arr)), h)
 
 
 def glrm_reset_steps(h):
@@ -543,6 +564,20 @@ class GLRM:
 
     def objective(self):
         return glrm_objective(self.h)
+
+    def set_offset(self, on=True):
+        glrm_set_offset(self.h, on)
+
+    def column_stats(self):
+        """(mu, sigma2) per column, float64 on the device (Sec. 4.3)."""
+        mu = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        s2 = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        glrm_column_stats(self.h, mu, s2)
+        return mu, s2
+
+    def set_column_scale(self, w=None):
+        glrm_set_column_scale(self.h, None if w is None else
+                              (w.detach().cpu().numpy() if isinstance(w, torch.Tensor) else w))
 
     def accepts(self):
         return glrm_last_accepts(self.h)

@@ -29,10 +29,10 @@ def decode_state(buf: bytes, m: int, n: int, k: int, dtype=np.float32):
     return X, Yt, ax, ay, hdr[6]
 
 
-def oracle_problem(o, t, rx=None, ry=None):
+def oracle_problem(o, t, rx=None, ry=None, offset=False, col_scale=None):
     return o.Problem.from_csr(t.m, t.n, t.k, t.rowptr, t.colidx, t.val, loss_kind=t.loss_kind,
                               loss_param=t.loss_param, loss_levels=t.loss_levels,
-                              rx=rx or t.rx, ry=ry or t.ry)
+                              rx=rx or t.rx, ry=ry or t.ry, offset=offset, col_scale=col_scale)
 
 
 def _flipped(got, want, tol=1e-4):
@@ -42,15 +42,16 @@ def _flipped(got, want, tol=1e-4):
     return (np.abs(np.asarray(got, np.float64) - want).max(axis=1) / scale) > tol
 
 
-def synced_sweeps(g, o, t, nsweeps, rtol=1e-5, max_flip_frac=0.01):
+def synced_sweeps(g, o, t, nsweeps, rtol=1e-5, max_flip_frac=0.01, offset=False, col_scale=None):
     """Run nsweeps GPU sweeps; before each, hand the GPU state to the oracle
     and run the same sweep there.  Checks per sweep: objective within rtol,
     accepted row / column counts within max(2, max_flip_frac) of each other,
     X and Yt after the sweep equal (to 1e-4 of each row's scale) and both
     step-size arrays equal (to FP32 rounding, 1e-6) on all but the rows /
     columns whose decision flipped.  Returns the per-sweep relative objective
-    differences."""
-    p = oracle_problem(o, t)
+    differences.  offset / col_scale: the oracle's model of a handle with
+    glrm_set_offset / glrm_set_column_scale."""
+    p = oracle_problem(o, t, offset=offset, col_scale=col_scale)
     rels = []
     for _ in range(nsweeps):
         X, Yt, ax, ay, _ = decode_state(g.state(), t.m, t.n, t.k)
