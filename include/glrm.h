@@ -222,6 +222,74 @@ int glrm_column_stats(glrm_t h, double *mu_dev, double *sigma2_dev);
  * glrm_als_sweep and glrm_proxprox_sweep on a weighted model.  Synchronises. */
 int glrm_set_column_scale(glrm_t h, const double *w_host);
 
+/* ---- Tables of multi-dimensional features (Section 6, eq. mpca) ----------
+ * Feature j of such a table is represented by a block Y_j of d_j columns of
+ * Y and entry (i, j) costs L_j(x_i Y_j, A_ij):
+ *   GLRM_FEATURE_SCALAR       d_j = 1, any glrm_loss;
+ *   GLRM_FEATURE_CATEGORICAL  labels 1..levels, d_j = levels, the one-vs-all
+ *       loss (1 - u_a)_+ + sum_{a' != a} (1 + u_a')_+ ("Categorical PCA");
+ *   GLRM_FEATURE_ORDINAL      levels 1..levels, d_j = levels - 1, the loss
+ *       sum_{l < levels} (1 - s_l u_l)_+ with s_l = +1 if a > l, else -1
+ *       (eq. ord-mpca, its indicator read as this sign).
+ * Both block losses are sums of one hinge term (1 - b_l u_l)_+ per column of
+ * the block (b_l = +1 for the label's column and -1 elsewhere; b_l = s_l),
+ * so a feature table is fitted as the scalar table whose entry (i, j) becomes
+ * the d_j entries (i, first_j + l, b_l) with hinge loss (first_j = sum of
+ * the widths before j): glrm_embed_size / glrm_embed_features build that
+ * table, glrm_embed_losses its column losses, and a model of n = sum d_j
+ * columns created with them runs every sweep, path and form of the library
+ * unchanged (its Y-step updates the block's columns one by one, each with
+ * its own step size; the step sizes start at 1 / max(count, 1) over the
+ * embedded entries).  glrm_decode_features imputes labels. */
+typedef enum { GLRM_FEATURE_SCALAR = 0, GLRM_FEATURE_CATEGORICAL = 1, GLRM_FEATURE_ORDINAL = 2 } glrm_feature_kind;
+#define GLRM_FEATURE_MAX_LEVELS 65536
+
+typedef struct {
+    int32_t kind;   /* glrm_feature_kind */
+    int32_t levels; /* label / level count, 2..GLRM_FEATURE_MAX_LEVELS; ignored for scalar features */
+} glrm_feature;
+
+/* Column losses of the embedded table: out_host (sum d_j entries) receives
+ * scalar_loss_host[j] at a scalar feature's column and GLRM_LOSS_HINGE at
+ * every column of a block; *ncols_host (if not NULL) the width sum d_j.
+ * out_host may be NULL to ask for the width only.  Host only. */
+int glrm_embed_losses(int32_t nfeat, const glrm_feature *feat_host, const glrm_loss *scalar_loss_host,
+                      glrm_loss *out_host, int64_t *ncols_host);
+
+/* Width (sum d_j) and entry count of the embedded table, from the features'
+ * column pointers colptr_dev (nfeat + 1, device).  Synchronises. */
+int glrm_embed_size(int32_t nfeat, const glrm_feature *feat_host, const int32_t *colptr_dev, int64_t *ncols_host,
+                    int64_t *nnz_host, void *stream);
+
+/* Build the embedded table.  Input: the feature table in CSR (rowptr m+1,
+ * featidx nnz, val nnz) and CSC (colptr nfeat+1, rowidx nnz, cval nnz)
+ * forms, device pointers, values in the element type of `precision` (float
+ * for GLRM_FP32 / GLRM_BF16, double for GLRM_FP64): real values for scalar
+ * features, labels 1..levels (integral values) for block features.  Output,
+ * caller-allocated device arrays (sizes from glrm_embed_size): CSR e_rowptr
+ * (m+1), e_colidx, e_val and CSC e_colptr (sum d_j + 1), e_rowidx, e_cval,
+ * ready for glrm_set_observed (rows stay in order within a column, and the
+ * columns of a row ascend when its features do).  Temporary device memory is
+ * allocated on `stream` and freed.  GLRM_ERR_OMEGA for inconsistent pointer
+ * arrays, an index out of range or a label outside 1..levels.
+ * Synchronises. */
+int glrm_embed_features(int32_t nfeat, const glrm_feature *feat_host, int64_t m, int64_t nnz,
+                        const int32_t *rowptr_dev, const int32_t *featidx_dev, const void *val_dev,
+                        const int32_t *colptr_dev, const int32_t *rowidx_dev, const void *cval_dev,
+                        int32_t precision, int32_t *e_rowptr_dev, int32_t *e_colidx_dev, void *e_val_dev,
+                        int32_t *e_colptr_dev, int32_t *e_rowidx_dev, void *e_cval_dev, void *stream);
+
+/* Impute cnt (row, feature) pairs of a model fitted on the embedded table
+ * (h's n must equal sum d_j): u_l = x_i . y_{first_j + l} in the model's
+ * precision; a scalar feature decodes as glrm_predict with decode on, a
+ * categorical feature to argmax_l u_l (Section 6, "Categorical PCA"; the
+ * lowest of equal maxima), an ordinal feature to argmin_a L(u, a) (Section
+ * 5.3's rule; the lowest of equal minima, from the FP64 prefix sums of
+ * (1 - u_l)_+ - (1 + u_l)_+).  out_dev: cnt values in the model's element
+ * type; NaN for a pair out of range.  Synchronises. */
+int glrm_decode_features(glrm_t h, int32_t nfeat, const glrm_feature *feat_host, int64_t cnt,
+                         const int32_t *rows_dev, const int32_t *feats_dev, void *out_dev);
+
 /* Reset every row step size to 1/max(n_i, 1) and every column step size to
  * 1/max(m_j, 1) (Section 7.2, "Choosing a step size", scale 1). */
 int glrm_reset_steps(glrm_t h);

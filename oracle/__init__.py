@@ -52,6 +52,7 @@ import numpy as np
 LOSS_QUAD, LOSS_HUBER, LOSS_HINGE, LOSS_LOGISTIC, LOSS_ORDINAL = 0, 1, 2, 3, 4
 LOSS_L1, LOSS_QUANTILE = 5, 6
 REG_ZERO, REG_QUAD, REG_L1, REG_NONNEG = 0, 1, 2, 3
+FEAT_SCALAR, FEAT_CATEGORICAL, FEAT_ORDINAL_MD = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "glrm_oracle.c")
@@ -110,6 +111,19 @@ def _load():
                                         p, i32]
         lib.oracle_column_stats.restype = i32
         lib.oracle_column_stats.argtypes = [i64, i64, i64, p, p, p, p, p, p, p, p, i32]
+        lib.oracle_feature_dim.restype = i32
+        lib.oracle_feature_dim.argtypes = [i32, i32]
+        lib.oracle_mloss.restype = d
+        lib.oracle_mloss.argtypes = [i32, i32, p, d]
+        lib.oracle_mgrad.restype = None
+        lib.oracle_mgrad.argtypes = [i32, i32, p, d, p]
+        lib.oracle_mdecode.restype = d
+        lib.oracle_mdecode.argtypes = [i32, i32, p]
+        lib.oracle_mobjective.restype = d
+        lib.oracle_mobjective.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, i32, d, i32, d, p, p, i32]
+        lib.oracle_mproxgrad.restype = i32
+        lib.oracle_mproxgrad.argtypes = [i64, i64, i32, i64, p, p, p, p, p, p, p, p, i32, d, i32, d, p, p, p, p,
+                                         i32, p, p, i32]
         lib.oracle_num_threads.restype = i32
         lib.oracle_num_threads.argtypes = [i32]
         _lib = lib
@@ -154,6 +168,30 @@ def prox(kind: int, w: float, alpha: float, z) -> np.ndarray:
     out = np.empty_like(z)
     _load().oracle_prox(kind, w, alpha, z.size, _ptr(z), _ptr(out))
     return out
+
+
+def feature_dim(fkind: int, levels: int) -> int:
+    """Width d_j of a feature's block of Y (Sec. 6): 1 scalar, d categorical, d - 1 ordinal."""
+    return int(_load().oracle_feature_dim(fkind, levels))
+
+
+def mloss(fkind: int, levels: int, u, a: float) -> float:
+    """Multi-dimensional loss L(u, a), u in R^{d_j} (Sec. 6: one-vs-all categorical, eq. ord-mpca)."""
+    u = _c(u, np.float64)
+    return _load().oracle_mloss(fkind, levels, _ptr(u), float(a))
+
+
+def mgrad(fkind: int, levels: int, u, a: float) -> np.ndarray:
+    u = _c(u, np.float64)
+    g = np.empty_like(u)
+    _load().oracle_mgrad(fkind, levels, _ptr(u), float(a), _ptr(g))
+    return g
+
+
+def mdecode(fkind: int, levels: int, u) -> float:
+    """Categorical: argmax_l u_l; ordinal: argmin_a L(u, a) over every level (Sec. 6, Sec. 5.3)."""
+    u = _c(u, np.float64)
+    return _load().oracle_mdecode(fkind, levels, _ptr(u))
 
 
 # ------------------------------------------------------------------- problem
@@ -317,6 +355,68 @@ class Problem:
         if rc:
             raise ValueError(f"oracle_proxprox failed ({rc})")
         return X, Yt, hist
+
+
+class FeatureProblem:
+    """A table of features (eq. mpca, Sec. 6): Omega as sorted (row, feature,
+    value) triples, per feature its kind (FEAT_*), label / level count and,
+    for scalar features, its loss.  Y has d = sum_j d_j columns, feature j's
+    block first[j] .. first[j+1]-1; Yt is d x k."""
+
+    def __init__(self, m, nf, k, rows, feats, vals, fkind, flevels, loss_kind, loss_param, loss_levels,
+                 rx=(REG_ZERO, 0.0), ry=(REG_ZERO, 0.0)):
+        self.m, self.nf, self.k = int(m), int(nf), int(k)
+        self.rows = _c(rows, np.int32)
+        self.feats = _c(feats, np.int32)
+        self.vals = _c(vals, np.float64)
+        self.nnz = int(self.rows.size)
+        self.fkind = _c(np.broadcast_to(fkind, (self.nf,)), np.int32)
+        self.flevels = _c(np.broadcast_to(flevels, (self.nf,)), np.int32)
+        self.loss_kind = _c(np.broadcast_to(loss_kind, (self.nf,)), np.int32)
+        self.loss_param = _c(np.broadcast_to(loss_param, (self.nf,)), np.float64)
+        self.loss_levels = _c(np.broadcast_to(loss_levels, (self.nf,)), np.int32)
+        self.rx = (int(rx[0]), float(rx[1]))
+        self.ry = (int(ry[0]), float(ry[1]))
+        dims = np.array([feature_dim(int(a), int(b)) for a, b in zip(self.fkind, self.flevels)], np.int64)
+        self.first = np.concatenate([[0], np.cumsum(dims)]).astype(np.int64)
+        self.d = int(self.first[-1])
+
+    def _args(self):
+        return (self.m, self.nf, self.k, self.nnz, _ptr(self.rows), _ptr(self.feats), _ptr(self.vals),
+                _ptr(self.fkind), _ptr(self.flevels), _ptr(self.loss_kind), _ptr(self.loss_param),
+                _ptr(self.loss_levels), *self.rx, *self.ry)
+
+    def initial_alphas(self):
+        """1 / max(count, 1), count = scalar loss terms: sum of d_j over a row's
+        features; feature j's observation count for each column of its block."""
+        dims = np.diff(self.first)
+        rowterms = np.bincount(self.rows, weights=dims[self.feats], minlength=self.m)
+        fcount = np.bincount(self.feats, minlength=self.nf).astype(np.float64)
+        ax = 1.0 / np.maximum(rowterms, 1.0)
+        ay = 1.0 / np.maximum(np.repeat(fcount, dims), 1.0)
+        return ax, ay
+
+    def objective(self, X, Yt, nthreads: int = 0) -> float:
+        X = _c(X, np.float64)
+        Yt = _c(Yt, np.float64)
+        return _load().oracle_mobjective(*self._args(), _ptr(X), _ptr(Yt), nthreads)
+
+    def proxgrad(self, X, Yt, nsweeps: int, alpha_x=None, alpha_y=None, nthreads: int = 0):
+        """Sweeps of Algorithm 2 on eq. mpca; returns (X, Yt, alpha_x, alpha_y,
+        history, accepts) like Problem.proxgrad (accepts: rows, columns of Y)."""
+        X = np.array(X, dtype=np.float64, order="C")
+        Yt = np.array(Yt, dtype=np.float64, order="C")
+        if alpha_x is None or alpha_y is None:
+            alpha_x, alpha_y = self.initial_alphas()
+        alpha_x = np.array(alpha_x, dtype=np.float64)
+        alpha_y = np.array(alpha_y, dtype=np.float64)
+        hist = np.empty(nsweeps)
+        acc = np.empty(2 * nsweeps, dtype=np.int64)
+        rc = _load().oracle_mproxgrad(*self._args(), _ptr(X), _ptr(Yt), _ptr(alpha_x), _ptr(alpha_y),
+                                      nsweeps, _ptr(hist), _ptr(acc), nthreads)
+        if rc:
+            raise ValueError(f"oracle_mproxgrad failed ({rc})")
+        return X, Yt, alpha_x, alpha_y, hist, acc.reshape(nsweeps, 2)
 
 
 def num_threads(nthreads: int = 0) -> int:

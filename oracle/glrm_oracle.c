@@ -822,4 +822,319 @@ int oracle_column_stats(int64_t m, int64_t n, int64_t nnz, const int32_t *row, c
     return 0;
 }
 
+/* ------------------------------------------- multi-dimensional losses */
+
+/* Section 6 ("Multi-dimensional loss functions", eq. mpca): feature j of the
+ * table is represented by a block Y_j of d_j columns of Y, and entry (i, j)
+ * costs L_j(x_i Y_j, A_ij) with u = x_i Y_j in R^{d_j}.  Feature kinds:
+ *  - FEAT_SCALAR: d_j = 1 and one of the scalar losses above;
+ *  - FEAT_CATEGORICAL with d labels 1..d ("Categorical PCA", one-vs-all):
+ *        L(u, a) = (1 - u_a)_+ + sum_{a' != a} (1 + u_a')_+,   d_j = d;
+ *  - FEAT_ORDINAL_MD with d levels 1..d (eq. ord-mpca):
+ *        L(u, a) = sum_{a'=1}^{d-1} (1 - s(a, a') u_a')_+,       d_j = d - 1,
+ *    reading the printed indicator I_{a > a'} as the sign s = +1 if a > a'
+ *    and -1 otherwise (with a 0/1 indicator every term with a <= a' would be
+ *    the constant 1 and the loss could not prefer low levels).
+ * Kinks take derivative 0.  u is indexed from 0: u[l] is column l + 1. */
+enum { FEAT_SCALAR = 0, FEAT_CATEGORICAL = 1, FEAT_ORDINAL_MD = 2 };
+
+int oracle_feature_dim(int fkind, int levels)
+{
+    switch (fkind) {
+    case FEAT_SCALAR: return 1;
+    case FEAT_CATEGORICAL: return levels;
+    case FEAT_ORDINAL_MD: return levels - 1;
+    }
+    return -1;
+}
+
+double oracle_mloss(int fkind, int levels, const double *u, double a)
+{
+    const int lab = (int)a;
+    double s = 0.0;
+    if (fkind == FEAT_CATEGORICAL) {
+        for (int l = 1; l <= levels; ++l)
+            s += l == lab ? pos(1.0 - u[l - 1]) : pos(1.0 + u[l - 1]);
+        return s;
+    }
+    if (fkind == FEAT_ORDINAL_MD) {
+        for (int ap = 1; ap <= levels - 1; ++ap) {
+            const double sg = lab > ap ? 1.0 : -1.0;
+            s += pos(1.0 - sg * u[ap - 1]);
+        }
+        return s;
+    }
+    return NAN;
+}
+
+/* Gradient of oracle_mloss with respect to u (d_j entries into g). */
+void oracle_mgrad(int fkind, int levels, const double *u, double a, double *g)
+{
+    const int lab = (int)a;
+    if (fkind == FEAT_CATEGORICAL) {
+        for (int l = 1; l <= levels; ++l)
+            g[l - 1] = l == lab ? (1.0 - u[l - 1] > 0.0 ? -1.0 : 0.0) : (1.0 + u[l - 1] > 0.0 ? 1.0 : 0.0);
+        return;
+    }
+    if (fkind == FEAT_ORDINAL_MD) {
+        for (int ap = 1; ap <= levels - 1; ++ap) {
+            const double sg = lab > ap ? 1.0 : -1.0;
+            g[ap - 1] = 1.0 - sg * u[ap - 1] > 0.0 ? -sg : 0.0;
+        }
+    }
+}
+
+/* Imputation of a multi-dimensional feature: the categorical label is
+ * argmax_l u_l (Section 6, "Categorical PCA"; the first of equal maxima); the
+ * ordinal level is argmin_a L(u, a) over a = 1..d by trying every level (the
+ * general rule of Section 5.3; ties to the smaller level). */
+double oracle_mdecode(int fkind, int levels, const double *u)
+{
+    if (fkind == FEAT_CATEGORICAL) {
+        int best = 1;
+        for (int l = 2; l <= levels; ++l)
+            if (u[l - 1] > u[best - 1]) best = l;
+        return (double)best;
+    }
+    if (fkind == FEAT_ORDINAL_MD) {
+        int best = 1;
+        double bestv = oracle_mloss(fkind, levels, u, 1.0);
+        for (int a = 2; a <= levels; ++a) {
+            double v = oracle_mloss(fkind, levels, u, (double)a);
+            if (v < bestv) { bestv = v; best = a; }
+        }
+        return (double)best;
+    }
+    return NAN;
+}
+
+/* The feature model of one problem: per feature its kind, label / level
+ * count, scalar loss (FEAT_SCALAR), and first column of its block in Y
+ * (first[j] .. first[j] + d_j - 1; first[nf] = d, the embedded width). */
+typedef struct {
+    int64_t nf;
+    const int32_t *fkind, *flev, *lkind, *llev;
+    const double *lparam;
+    int64_t *first;
+} feat_model;
+
+/* u = x Y_j (d_j entries; Yt holds Y's columns as rows of k). */
+static void block_u(const feat_model *F, int k, int64_t j, const double *x, const double *Yt, double *u)
+{
+    const int64_t c0 = F->first[j], d = F->first[j + 1] - c0;
+    for (int64_t l = 0; l < d; ++l) u[l] = dot(k, x, Yt + (c0 + l) * k);
+}
+
+static double entry_loss(const feat_model *F, int64_t j, const double *u, double a)
+{
+    if (F->fkind[j] == FEAT_SCALAR) return oracle_loss(F->lkind[j], F->lparam[j], F->llev[j], u[0], a);
+    return oracle_mloss(F->fkind[j], F->flev[j], u, a);
+}
+
+static void entry_grad(const feat_model *F, int64_t j, const double *u, double a, double *g)
+{
+    if (F->fkind[j] == FEAT_SCALAR) g[0] = oracle_dloss(F->lkind[j], F->lparam[j], F->llev[j], u[0], a);
+    else oracle_mgrad(F->fkind[j], F->flev[j], u, a, g);
+}
+
+static int model_build(feat_model *F, int64_t nf, const int32_t *fkind, const int32_t *flev,
+                       const int32_t *lkind, const double *lparam, const int32_t *llev)
+{
+    F->nf = nf; F->fkind = fkind; F->flev = flev; F->lkind = lkind; F->lparam = lparam; F->llev = llev;
+    F->first = malloc(sizeof(int64_t) * (size_t)(nf + 1));
+    if (!F->first) return -1;
+    F->first[0] = 0;
+    for (int64_t j = 0; j < nf; ++j) {
+        int d = oracle_feature_dim(fkind[j], flev[j]);
+        if (d < 1) return -2;
+        F->first[j + 1] = F->first[j] + d;
+    }
+    return 0;
+}
+
+static int64_t model_dmax(const feat_model *F)
+{
+    int64_t dm = 1;
+    for (int64_t j = 0; j < F->nf; ++j) dm = F->first[j + 1] - F->first[j] > dm ? F->first[j + 1] - F->first[j] : dm;
+    return dm;
+}
+
+/* Loss of row i's entries at factor row x. */
+static double mrow_loss(const feat_model *F, int k, const double *x, const double *Yt, const omega_lists *L,
+                        int64_t i, double *u)
+{
+    double s = 0.0;
+    for (int64_t e = L->rstart[i]; e < L->rstart[i + 1]; ++e) {
+        const int64_t j = L->rcol[e];
+        block_u(F, k, j, x, Yt, u);
+        s += entry_loss(F, j, u, L->rval[e]);
+    }
+    return s;
+}
+
+static double mobjective_lists(const feat_model *F, const omega_lists *L, int k, const double *X, const double *Yt,
+                               int rxk, double rxw, int ryk, double ryw)
+{
+    const int64_t dmax = model_dmax(F);
+    double *rowsum = malloc(sizeof(double) * (size_t)(L->m ? L->m : 1));
+    int64_t i;
+#pragma omp parallel
+    {
+        double *u = malloc(sizeof(double) * (size_t)dmax);
+#pragma omp for schedule(dynamic, 64)
+        for (i = 0; i < L->m; ++i) rowsum[i] = mrow_loss(F, k, X + i * k, Yt, L, i, u);
+        free(u);
+    }
+    double tot = 0.0;
+    for (i = 0; i < L->m; ++i) tot += rowsum[i];
+    for (i = 0; i < L->m; ++i) tot += oracle_reg(rxk, rxw, k, X + i * k);
+    for (int64_t c = 0; c < F->first[F->nf]; ++c) tot += oracle_reg(ryk, ryw, k, Yt + c * k);
+    free(rowsum);
+    return tot;
+}
+
+/* Objective of eq. mpca: sum over Omega of L_j(x_i Y_j, A_ij) (rows
+ * ascending, then features ascending) + sum_i r(x_i) + sum over the d
+ * columns of Y of rt(y).  Omega: triples (row, feature, value) sorted by row
+ * then feature; Yt is d x k. */
+double oracle_mobjective(int64_t m, int64_t nf, int k, int64_t nnz, const int32_t *row, const int32_t *feat,
+                         const double *val, const int32_t *fkind, const int32_t *flev, const int32_t *lkind,
+                         const double *lparam, const int32_t *llev, int rxk, double rxw, int ryk, double ryw,
+                         const double *X, const double *Yt, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    feat_model F;
+    memset(&F, 0, sizeof F);
+    double out = NAN;
+    if (!lists_build(&L, m, nf, nnz, row, feat, val) && !model_build(&F, nf, fkind, flev, lkind, lparam, llev)) {
+        set_threads(nthreads);
+        out = mobjective_lists(&F, &L, k, X, Yt, rxk, rxw, ryk, ryw);
+    }
+    free(F.first);
+    lists_free(&L);
+    return out;
+}
+
+/* Alternating proximal-gradient sweeps on eq. mpca (Algorithm 2 with the
+ * update and step-size rule of Section 7.2).  X-step: row x_i against the
+ * blocks of its observed features, g = sum_j sum_l dL/du_l y_{j,l}, the rule
+ * on f(x) = sum_j L_j(x Y_j, A_ij) + r(x).  Y-step: the block Y_j is
+ * updated one column y_{j,l} at a time, each with its own step size and
+ * accept test on f(y) = sum_i L_j(x_i Y_j[l <- y], A_ij) + rt(y), the other
+ * columns held at their values from the start of the Y-step.  The losses of
+ * this section are sums of one term per column of the block and rt is a sum
+ * over columns, so minimising over Y_j separates exactly into these column
+ * problems (the paper notes the one-vs-all loss's separability); each column
+ * taking its own step size is the reading taken here.  Step sizes start at
+ * 1 / max(count, 1) with count the number of scalar loss terms: sum of d_j
+ * over a row's observed features, the observation count of feature j for each
+ * column of its block.  alpha_y has d entries; accepts[2t], accepts[2t+1]
+ * count accepted rows and columns of Y in sweep t. */
+int oracle_mproxgrad(int64_t m, int64_t nf, int k, int64_t nnz, const int32_t *row, const int32_t *feat,
+                     const double *val, const int32_t *fkind, const int32_t *flev, const int32_t *lkind,
+                     const double *lparam, const int32_t *llev, int rxk, double rxw, int ryk, double ryw,
+                     double *X, double *Yt, double *alpha_x, double *alpha_y, int nsweeps, double *history,
+                     int64_t *accepts, int nthreads)
+{
+    omega_lists L;
+    memset(&L, 0, sizeof L);
+    feat_model F;
+    memset(&F, 0, sizeof F);
+    int rc = lists_build(&L, m, nf, nnz, row, feat, val);
+    if (!rc) rc = model_build(&F, nf, fkind, flev, lkind, lparam, llev);
+    if (rc) { free(F.first); lists_free(&L); return rc; }
+    set_threads(nthreads);
+    const int64_t D = F.first[nf], dmax = model_dmax(&F);
+    int64_t *cfeat = malloc(sizeof(int64_t) * (size_t)(D ? D : 1));
+    double *Yold = malloc(sizeof(double) * (size_t)(D ? D : 1) * (size_t)k);
+    int *ax = malloc(sizeof(int) * (size_t)(m ? m : 1));
+    int *ay = malloc(sizeof(int) * (size_t)(D ? D : 1));
+    for (int64_t j = 0; j < nf; ++j)
+        for (int64_t c = F.first[j]; c < F.first[j + 1]; ++c) cfeat[c] = j;
+    for (int t = 0; t < nsweeps; ++t) {
+        int64_t i, c;
+#pragma omp parallel
+        {
+            double *u = malloc(sizeof(double) * (size_t)dmax);
+            double *gu = malloc(sizeof(double) * (size_t)dmax);
+            double g[k], z[k], xp[k];
+#pragma omp for schedule(dynamic, 64)
+            for (i = 0; i < m; ++i) {
+                double *x = X + i * k;
+                for (int q = 0; q < k; ++q) g[q] = 0.0;
+                for (int64_t e = L.rstart[i]; e < L.rstart[i + 1]; ++e) {
+                    const int64_t j = L.rcol[e];
+                    block_u(&F, k, j, x, Yt, u);
+                    entry_grad(&F, j, u, L.rval[e], gu);
+                    for (int64_t l = 0; l < F.first[j + 1] - F.first[j]; ++l)
+                        for (int q = 0; q < k; ++q) g[q] += gu[l] * Yt[(F.first[j] + l) * k + q];
+                }
+                for (int q = 0; q < k; ++q) z[q] = x[q] - alpha_x[i] * g[q];
+                oracle_prox(rxk, rxw, alpha_x[i], k, z, xp);
+                const double f_old = mrow_loss(&F, k, x, Yt, &L, i, u) + oracle_reg(rxk, rxw, k, x);
+                const double f_new = mrow_loss(&F, k, xp, Yt, &L, i, u) + oracle_reg(rxk, rxw, k, xp);
+                if (f_new <= f_old) {
+                    for (int q = 0; q < k; ++q) x[q] = xp[q];
+                    alpha_x[i] *= 1.05;
+                    ax[i] = 1;
+                } else {
+                    alpha_x[i] *= 0.7;
+                    ax[i] = 0;
+                }
+            }
+            free(u);
+            free(gu);
+        }
+        memcpy(Yold, Yt, sizeof(double) * (size_t)D * (size_t)k);
+#pragma omp parallel
+        {
+            double *u = malloc(sizeof(double) * (size_t)dmax);
+            double *gu = malloc(sizeof(double) * (size_t)dmax);
+            double g[k], z[k], yp[k];
+#pragma omp for schedule(dynamic, 4)
+            for (c = 0; c < D; ++c) {
+                const int64_t j = cfeat[c], l = c - F.first[j];
+                const double *y = Yold + c * k;
+                for (int q = 0; q < k; ++q) g[q] = 0.0;
+                for (int64_t e = L.cstart[j]; e < L.cstart[j + 1]; ++e) {
+                    const double *x = X + (int64_t)L.crow[e] * k;
+                    block_u(&F, k, j, x, Yold, u);
+                    entry_grad(&F, j, u, L.cval[e], gu);
+                    for (int q = 0; q < k; ++q) g[q] += gu[l] * x[q];
+                }
+                for (int q = 0; q < k; ++q) z[q] = y[q] - alpha_y[c] * g[q];
+                oracle_prox(ryk, ryw, alpha_y[c], k, z, yp);
+                double f_old = oracle_reg(ryk, ryw, k, y), f_new = oracle_reg(ryk, ryw, k, yp);
+                for (int64_t e = L.cstart[j]; e < L.cstart[j + 1]; ++e) {
+                    const double *x = X + (int64_t)L.crow[e] * k;
+                    block_u(&F, k, j, x, Yold, u);
+                    f_old += entry_loss(&F, j, u, L.cval[e]);
+                    u[l] = dot(k, x, yp);
+                    f_new += entry_loss(&F, j, u, L.cval[e]);
+                }
+                if (f_new <= f_old) {
+                    for (int q = 0; q < k; ++q) Yt[c * k + q] = yp[q];
+                    alpha_y[c] *= 1.05;
+                    ay[c] = 1;
+                } else {
+                    alpha_y[c] *= 0.7;
+                    ay[c] = 0;
+                }
+            }
+            free(u);
+            free(gu);
+        }
+        int64_t na = 0, nb = 0;
+        for (i = 0; i < m; ++i) na += ax[i];
+        for (c = 0; c < D; ++c) nb += ay[c];
+        if (accepts) { accepts[2 * t] = na; accepts[2 * t + 1] = nb; }
+        if (history) history[t] = mobjective_lists(&F, &L, k, X, Yt, rxk, rxw, ryk, ryw);
+    }
+    free(cfeat); free(Yold); free(ax); free(ay);
+    free(F.first);
+    lists_free(&L);
+    return 0;
+}
+
 int oracle_num_threads(int nthreads) { return set_threads(nthreads); }

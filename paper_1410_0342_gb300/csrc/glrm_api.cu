@@ -1102,6 +1102,205 @@ int glrm_column_stats(glrm_t h, double *mu_dev, double *sigma2_dev)
     return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_column_stats");
 }
 
+// ------------------------------------------------ multi-dimensional features
+
+namespace {
+
+// The features' device table (kind, levels, width, first column) and the
+// embedded width; GLRM_OK or an error for a bad kind or level count.
+int feature_table(int32_t nfeat, const glrm_feature *feat, std::vector<FeatDev> &F, int64_t &D, glrm_s *h)
+{
+    if (nfeat < 1 || !feat) return fail(h, GLRM_ERR_ARG, "need nfeat >= 1 feature descriptors");
+    F.resize((size_t)nfeat);
+    D = 0;
+    for (int32_t j = 0; j < nfeat; ++j) {
+        const glrm_feature &f = feat[j];
+        int w = 0;
+        if (f.kind == GLRM_FEATURE_SCALAR) w = 1;
+        else if (f.kind == GLRM_FEATURE_CATEGORICAL && f.levels >= 2 && f.levels <= GLRM_FEATURE_MAX_LEVELS) w = f.levels;
+        else if (f.kind == GLRM_FEATURE_ORDINAL && f.levels >= 2 && f.levels <= GLRM_FEATURE_MAX_LEVELS) w = f.levels - 1;
+        else return fail(h, GLRM_ERR_ARG, "bad feature kind or level count");
+        F[(size_t)j] = FeatDev{f.kind, f.levels, w, (int32_t)D};
+        D += w;
+        if (D >= (int64_t)INT32_MAX) return fail(h, GLRM_ERR_RANGE, "embedded width must be < 2^31");
+    }
+    return GLRM_OK;
+}
+
+// Embedded column pointers from the features' column pointers (host).
+int64_t embedded_colptr(const std::vector<FeatDev> &F, const std::vector<int32_t> &cp, std::vector<int64_t> &ecp)
+{
+    ecp.assign(1, 0);
+    for (size_t j = 0; j < F.size(); ++j) {
+        const int64_t c = cp[j + 1] - cp[j];
+        for (int l = 0; l < F[j].width; ++l) ecp.push_back(ecp.back() + c);
+    }
+    return ecp.back();
+}
+
+}  // namespace
+
+int glrm_embed_losses(int32_t nfeat, const glrm_feature *feat_host, const glrm_loss *scalar_loss_host,
+                      glrm_loss *out_host, int64_t *ncols_host)
+{
+    std::vector<FeatDev> F;
+    int64_t D = 0;
+    int rc = feature_table(nfeat, feat_host, F, D, nullptr);
+    if (rc != GLRM_OK) return rc;
+    if (ncols_host) *ncols_host = D;
+    if (!out_host) return GLRM_OK;
+    for (int32_t j = 0; j < nfeat; ++j) {
+        const FeatDev &f = F[(size_t)j];
+        if (f.kind == GLRM_FEATURE_SCALAR) {
+            if (!scalar_loss_host) return fail(nullptr, GLRM_ERR_ARG, "scalar features need their losses");
+            out_host[f.first] = scalar_loss_host[j];
+        } else {
+            for (int l = 0; l < f.width; ++l) out_host[f.first + l] = glrm_loss{GLRM_LOSS_HINGE, 0, 0.0};
+        }
+    }
+    return GLRM_OK;
+}
+
+int glrm_embed_size(int32_t nfeat, const glrm_feature *feat_host, const int32_t *colptr_dev, int64_t *ncols_host,
+                    int64_t *nnz_host, void *stream)
+{
+    std::vector<FeatDev> F;
+    int64_t D = 0;
+    int rc = feature_table(nfeat, feat_host, F, D, nullptr);
+    if (rc != GLRM_OK) return rc;
+    if (!colptr_dev || !ncols_host || !nnz_host) return fail(nullptr, GLRM_ERR_ARG, "null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> cp((size_t)nfeat + 1);
+    cudaError_t e = cudaMemcpyAsync(cp.data(), colptr_dev, cp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, GLRM_ERR_CUDA, std::string("glrm_embed_size: ") + cudaGetErrorString(e));
+    for (int32_t j = 0; j < nfeat; ++j)
+        if (cp[(size_t)j + 1] < cp[(size_t)j]) return fail(nullptr, GLRM_ERR_OMEGA, "column pointers decrease");
+    std::vector<int64_t> ecp;
+    *nnz_host = embedded_colptr(F, cp, ecp);
+    *ncols_host = D;
+    return GLRM_OK;
+}
+
+int glrm_embed_features(int32_t nfeat, const glrm_feature *feat_host, int64_t m, int64_t nnz,
+                        const int32_t *rowptr_dev, const int32_t *featidx_dev, const void *val_dev,
+                        const int32_t *colptr_dev, const int32_t *rowidx_dev, const void *cval_dev,
+                        int32_t precision, int32_t *e_rowptr_dev, int32_t *e_colidx_dev, void *e_val_dev,
+                        int32_t *e_colptr_dev, int32_t *e_rowidx_dev, void *e_cval_dev, void *stream)
+{
+    std::vector<FeatDev> F;
+    int64_t D = 0;
+    int rc = feature_table(nfeat, feat_host, F, D, nullptr);
+    if (rc != GLRM_OK) return rc;
+    if (!prec_ok(precision)) return fail(nullptr, GLRM_ERR_ARG, "bad precision");
+    if (m < 1 || nnz < 0 || nnz >= (int64_t)INT32_MAX) return fail(nullptr, GLRM_ERR_RANGE, "bad m or nnz");
+    if (!rowptr_dev || !colptr_dev || !e_rowptr_dev || !e_colptr_dev ||
+        (nnz > 0 && (!featidx_dev || !val_dev || !rowidx_dev || !cval_dev || !e_colidx_dev || !e_val_dev ||
+                     !e_rowidx_dev || !e_cval_dev)))
+        return fail(nullptr, GLRM_ERR_ARG, "null pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto cuda_err = [](cudaError_t e) {
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? GLRM_ERR_NOMEM : GLRM_ERR_CUDA,
+                    std::string("glrm_embed_features: ") + cudaGetErrorString(e));
+    };
+    // host copies of the two pointer arrays: the row / column structure is
+    // checked here, the embedded column pointers follow from them
+    std::vector<int32_t> rp((size_t)m + 1), cp((size_t)nfeat + 1);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), rowptr_dev, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cp.data(), colptr_dev, cp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (rp[0] != 0 || cp[0] != 0 || rp[(size_t)m] != nnz || cp[(size_t)nfeat] != nnz)
+        return fail(nullptr, GLRM_ERR_OMEGA, "pointer arrays do not span nnz entries");
+    int64_t maxcnt = 0;
+    for (int64_t i = 0; i < m; ++i)
+        if (rp[(size_t)i + 1] < rp[(size_t)i]) return fail(nullptr, GLRM_ERR_OMEGA, "row pointers decrease");
+    for (int32_t j = 0; j < nfeat; ++j) {
+        if (cp[(size_t)j + 1] < cp[(size_t)j]) return fail(nullptr, GLRM_ERR_OMEGA, "column pointers decrease");
+        maxcnt = std::max<int64_t>(maxcnt, cp[(size_t)j + 1] - cp[(size_t)j]);
+    }
+    std::vector<int64_t> ecp;
+    const int64_t ennz = embedded_colptr(F, cp, ecp);
+    if (ennz >= (int64_t)INT32_MAX) return fail(nullptr, GLRM_ERR_RANGE, "embedded nnz must be < 2^31");
+    // feature indices are checked on the device before the row counts use them
+    FeatDev *Fd = nullptr;
+    int64_t *cnt = nullptr;
+    int *flag = nullptr;
+    e = cudaMallocAsync((void **)&Fd, F.size() * sizeof(FeatDev), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&cnt, (size_t)m * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&flag, sizeof(int), st);
+    auto release = [&]() {
+        if (Fd) cudaFreeAsync(Fd, st);
+        if (cnt) cudaFreeAsync(cnt, st);
+        if (flag) cudaFreeAsync(flag, st);
+        cudaStreamSynchronize(st);
+    };
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Fd, F.data(), F.size() * sizeof(FeatDev), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    int hflag = 0;
+    if (e == cudaSuccess && nnz > 0) e = launch_check_index(featidx_dev, nnz, nfeat, flag, st);
+    if (e == cudaSuccess && nnz > 0) e = launch_check_index(rowidx_dev, nnz, m, flag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_err(e);
+    }
+    if (hflag) {
+        release();
+        return fail(nullptr, GLRM_ERR_OMEGA, "feature or row index out of range");
+    }
+    std::vector<int64_t> hc((size_t)m);
+    e = launch_embed_rowcount(m, rowptr_dev, featidx_dev, Fd, cnt, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, hc.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_err(e);
+    }
+    std::vector<int32_t> erp((size_t)m + 1), ecp32(ecp.size());
+    erp[0] = 0;
+    for (int64_t i = 0; i < m; ++i) erp[(size_t)i + 1] = erp[(size_t)i] + (int32_t)hc[(size_t)i];
+    for (size_t c = 0; c < ecp.size(); ++c) ecp32[c] = (int32_t)ecp[c];
+    e = cudaMemcpyAsync(e_rowptr_dev, erp.data(), erp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(e_colptr_dev, ecp32.data(), ecp32.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz > 0)
+        e = launch_embed(precision, m, nfeat, maxcnt, rowptr_dev, featidx_dev, val_dev, colptr_dev, rowidx_dev,
+                         cval_dev, Fd, e_rowptr_dev, e_colidx_dev, e_val_dev, e_colptr_dev, e_rowidx_dev, e_cval_dev,
+                         flag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_err(e);
+    if (hflag) return fail(nullptr, GLRM_ERR_OMEGA, "a categorical or ordinal value is not a label 1..levels");
+    return GLRM_OK;
+}
+
+int glrm_decode_features(glrm_t h, int32_t nfeat, const glrm_feature *feat_host, int64_t cnt,
+                         const int32_t *rows_dev, const int32_t *feats_dev, void *out_dev)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    std::vector<FeatDev> F;
+    int64_t D = 0;
+    int rc = feature_table(nfeat, feat_host, F, D, h);
+    if (rc != GLRM_OK) return rc;
+    if (D != h->n) return fail(h, GLRM_ERR_ARG, "the features' embedded width is not the model's n");
+    if (cnt < 0 || (cnt > 0 && (!rows_dev || !feats_dev || !out_dev))) return fail(h, GLRM_ERR_ARG, "bad request arrays");
+    if (cnt == 0) return GLRM_OK;
+    DeviceGuard dg(h->device);
+    FeatDev *Fd = nullptr;
+    CK(dalloc(h, &Fd, F.size() * sizeof(FeatDev)));
+    cudaError_t e = cudaMemcpyAsync(Fd, F.data(), F.size() * sizeof(FeatDev), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_decode_features(h, Fd, nfeat, cnt, rows_dev, feats_dev, out_dev);
+    // the host table must outlive the copy; the device one is freed in stream order
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    dfree(Fd, h->stream);
+    if (e == cudaSuccess) e = e2;
+    return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_decode_features");
+}
+
 int glrm_reset_steps(glrm_t h)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");

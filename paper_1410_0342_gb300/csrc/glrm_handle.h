@@ -261,6 +261,22 @@ cudaError_t bf16_half_step_entry(glrm_s *h, bool xstep);
 cudaError_t launch_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
 // Per-column statistics mu_j, sigma2_j of the loss scaling (glrm_stats.cu).
 cudaError_t launch_column_stats(glrm_s *h, double *mu, double *s2);
+// Tables of multi-dimensional features (glrm_features.cu): one feature's
+// kind, label / level count, width of its block of Y and first column.
+constexpr int kFeatScalar = 0, kFeatCategorical = 1, kFeatOrdinal = 2;
+struct FeatDev {
+    int32_t kind, levels, width, first;
+};
+// Raise *flag when an index lies outside [0, bound).
+cudaError_t launch_check_index(const int32_t *idx, int64_t n, int64_t bound, int *flag, cudaStream_t st);
+cudaError_t launch_embed_rowcount(int64_t m, const int32_t *rowptr, const int32_t *featidx, const FeatDev *F,
+                                  int64_t *cnt, cudaStream_t st);
+cudaError_t launch_embed(int prec, int64_t m, int64_t nf, int64_t maxcnt, const int32_t *rowptr,
+                         const int32_t *featidx, const void *val, const int32_t *colptr, const int32_t *rowidx,
+                         const void *cval, const FeatDev *F, const int32_t *e_rowptr, int32_t *e_colidx, void *e_val,
+                         const int32_t *e_colptr, int32_t *e_rowidx, void *e_cval, int *flag, cudaStream_t st);
+cudaError_t launch_decode_features(glrm_s *h, const FeatDev *F, int32_t nf, int64_t cnt, const int32_t *rows,
+                                   const int32_t *feats, void *out);
 // Dense, fully observed form (tensor cores, FP32 models).
 bool dense_supported(int k);
 void dense_free(glrm_s *h);

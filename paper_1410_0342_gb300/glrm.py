@@ -37,6 +37,13 @@ class glrm_loss(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32), ("param", ctypes.c_double)]
 
 
+class glrm_feature(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32)]
+
+
+GLRM_FEATURE_SCALAR, GLRM_FEATURE_CATEGORICAL, GLRM_FEATURE_ORDINAL = 0, 1, 2
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libglrm.so not built ({_LIB_PATH}); run __graft_entry__.build()")
@@ -53,6 +60,10 @@ def _load():
         "glrm_set_factors_host": [p, p, p],
         "glrm_get_factors_host": [p, p, p],
         "glrm_reset_steps": [p],
+        "glrm_embed_losses": [i32, p, p, p, p],
+        "glrm_embed_size": [i32, p, p, p, p, p],
+        "glrm_embed_features": [i32, p, i64, i64, p, p, p, p, p, p, i32, p, p, p, p, p, p, p],
+        "glrm_decode_features": [p, i32, p, i64, p, p, p],
         "glrm_set_offset": [p, i32],
         "glrm_column_stats": [p, p, p],
         "glrm_set_column_scale": [p, p],
@@ -217,6 +228,56 @@ def glrm_set_column_scale(h, w=None):
         return
     arr = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
     _check(_lib.glrm_set_column_scale(h, _ptr(arr)), h)
+
+
+def _features(fkind, flevels):
+    fkind = np.asarray(fkind)
+    flevels = np.asarray(flevels)
+    arr = (glrm_feature * len(fkind))()
+    for j in range(len(fkind)):
+        arr[j] = glrm_feature(int(fkind[j]), int(flevels[j]))
+    return arr
+
+
+def glrm_embed_losses(fkind, flevels, scalar_loss):
+    """scalar_loss: arrays (kind[nf], param[nf], levels[nf]) of the scalar
+    features.  Returns (kind, param, levels) of the embedded columns."""
+    nf = len(fkind)
+    feats = _features(fkind, flevels)
+    sl = (glrm_loss * nf)()
+    for j in range(nf):
+        sl[j] = glrm_loss(int(scalar_loss[0][j]), int(scalar_loss[2][j]), float(scalar_loss[1][j]))
+    D = ctypes.c_int64()
+    _check(_lib.glrm_embed_losses(nf, ctypes.cast(feats, ctypes.c_void_p), ctypes.cast(sl, ctypes.c_void_p),
+                                  None, ctypes.byref(D)))
+    out = (glrm_loss * D.value)()
+    _check(_lib.glrm_embed_losses(nf, ctypes.cast(feats, ctypes.c_void_p), ctypes.cast(sl, ctypes.c_void_p),
+                                  ctypes.cast(out, ctypes.c_void_p), None))
+    return (np.array([o.kind for o in out], np.int32), np.array([o.param for o in out]),
+            np.array([o.levels for o in out], np.int32))
+
+
+def glrm_embed_size(fkind, flevels, colptr, stream=None):
+    D = ctypes.c_int64()
+    nnz = ctypes.c_int64()
+    st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    _check(_lib.glrm_embed_size(len(fkind), ctypes.cast(_features(fkind, flevels), ctypes.c_void_p), _ptr(colptr),
+                                ctypes.byref(D), ctypes.byref(nnz), st))
+    return D.value, nnz.value
+
+
+def glrm_embed_features(fkind, flevels, m, nnz, rowptr, featidx, val, colptr, rowidx, cval, precision,
+                        e_rowptr, e_colidx, e_val, e_colptr, e_rowidx, e_cval, stream=None):
+    st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    _check(_lib.glrm_embed_features(len(fkind), ctypes.cast(_features(fkind, flevels), ctypes.c_void_p), m, nnz,
+                                    _ptr(rowptr), _ptr(featidx), _ptr(val), _ptr(colptr), _ptr(rowidx), _ptr(cval),
+                                    precision, _ptr(e_rowptr), _ptr(e_colidx), _ptr(e_val), _ptr(e_colptr),
+                                    _ptr(e_rowidx), _ptr(e_cval), st))
+
+
+def glrm_decode_features(h, fkind, flevels, rows, feats, out):
+    _check(_lib.glrm_decode_features(h, len(fkind), ctypes.cast(_features(fkind, flevels), ctypes.c_void_p),
+                                     rows.numel(), _ptr(rows), _ptr(feats), _ptr(out)), h)
 
 
 def glrm_reset_steps(h):
@@ -523,6 +584,36 @@ class GLRM:
             g.set_factors(torch.as_tensor(t.X0, dtype=g.dtype, device=g.device),
                           torch.as_tensor(t.Yt0, dtype=g.dtype, device=g.device))
         return g
+
+    @classmethod
+    def from_feature_table(cls, t, precision=GLRM_FP32, device=None, stream=None, factors=True):
+        """A workloads.FeatureTable: embedded on the device (glrm_embed_features)
+        into its Boolean block columns and given to a model of sum d_j columns."""
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        dt = dtype_of(precision)
+        i32 = torch.int32
+        src = [torch.as_tensor(np.asarray(a), dtype=ty, device=dev) for a, ty in
+               ((t.rowptr, i32), (t.featidx, i32), (t.val, dt), (t.colptr, i32), (t.rowidx, i32), (t.cval, dt))]
+        with torch.cuda.device(dev):
+            D, ennz = glrm_embed_size(t.fkind, t.flevels, src[3], stream)
+            out = [torch.empty(t.m + 1, dtype=i32, device=dev), torch.empty(max(ennz, 1), dtype=i32, device=dev),
+                   torch.empty(max(ennz, 1), dtype=dt, device=dev), torch.empty(D + 1, dtype=i32, device=dev),
+                   torch.empty(max(ennz, 1), dtype=i32, device=dev), torch.empty(max(ennz, 1), dtype=dt, device=dev)]
+            glrm_embed_features(t.fkind, t.flevels, t.m, t.nnz, *src, precision, *out, stream=stream)
+            losses = glrm_embed_losses(t.fkind, t.flevels, (t.loss_kind, t.loss_param, t.loss_levels))
+        g = cls(t.m, D, t.k, losses, t.rx, t.ry, precision, dev, stream)
+        g.fkind, g.flevels = np.asarray(t.fkind), np.asarray(t.flevels)
+        with torch.cuda.device(dev):
+            glrm_set_observed(g.h, ennz, *out)
+        if factors:
+            g.set_factors(torch.as_tensor(t.X0, dtype=dt, device=dev), torch.as_tensor(t.Yt0, dtype=dt, device=dev))
+        return g
+
+    def decode_features(self, rows, feats):
+        out = torch.empty(rows.numel(), dtype=self.dtype, device=self.device)
+        glrm_decode_features(self.h, self.fkind, self.flevels, rows.to(torch.int32).contiguous(),
+                             feats.to(torch.int32).contiguous(), out)
+        return out
 
     def set_dense(self, A):
         with torch.cuda.device(self.device):

@@ -428,3 +428,104 @@ def batch_torch(count=4096, device="cuda", **kw) -> Batch:
                  rowptr=cat("rowptr"), colidx=cat("colidx"), val=cat("val"),
                  colptr=cat("colptr"), rowidx=cat("rowidx"), cval=cat("cval"),
                  X0=cat("X0"), Yt0=cat("Yt0"))
+
+
+# ------------------------------------------------------ tables of features
+
+FEAT_SCALAR, FEAT_CATEGORICAL, FEAT_ORDINAL_MD = 0, 1, 2
+
+
+@dataclasses.dataclass
+class FeatureTable:
+    """A table of features (the multi-dimensional model of Sec. 6): Omega
+    over (row, feature) in CSR and CSC form, per feature its kind (FEAT_*),
+    its label / level count and, for scalar features, its loss.  Feature j
+    owns a block of Y of width 1 (scalar), d (categorical, d labels) or d - 1
+    (ordinal, d levels); Yt0 holds the initial blocks one after another
+    (sum of the widths rows of k)."""
+    name: str
+    m: int
+    nf: int
+    k: int
+    rowptr: np.ndarray      # int64 [m+1]
+    featidx: np.ndarray     # int32 [nnz]
+    val: np.ndarray         # float64 [nnz]: real values, +-1, or labels / levels 1..d
+    colptr: np.ndarray      # int64 [nf+1]
+    rowidx: np.ndarray      # int32 [nnz]
+    cval: np.ndarray        # float64 [nnz]
+    fkind: np.ndarray       # int32 [nf]
+    flevels: np.ndarray     # int32 [nf]
+    loss_kind: np.ndarray   # int32 [nf] (scalar features)
+    loss_param: np.ndarray  # float64 [nf]
+    loss_levels: np.ndarray  # int32 [nf]
+    rx: tuple
+    ry: tuple
+    X0: np.ndarray          # float64 [m, k]
+    Yt0: np.ndarray         # float64 [sum of block widths, k]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.featidx.size)
+
+    def rows(self) -> np.ndarray:
+        return np.repeat(np.arange(self.m, dtype=np.int32), np.diff(self.rowptr))
+
+    def widths(self) -> np.ndarray:
+        return np.where(self.fkind == FEAT_CATEGORICAL, self.flevels,
+                        np.where(self.fkind == FEAT_ORDINAL_MD, self.flevels - 1, 1)).astype(np.int64)
+
+
+def features_mixed(m=2000, n_real=6, n_bool=4, n_cat=5, n_ord=5, classes=4, levels=5, k=6, p_obs=0.6,
+                   seed=BASE_SEED + 30, rx=(REG_QUAD, 0.1), ry=(REG_QUAD, 0.1), cyclic=True,
+                   name="features_mixed"):
+    """A census-like table of mixed features (Sec. 6's categorical and
+    ordinal embeddings beside scalar columns): real features with Huber loss
+    (X0 y + Laplace(0, 0.5)), Boolean features with hinge loss (sign of
+    X0 y + N(0, 0.5^2)), categorical features with `classes` labels (argmax of
+    X0 W + Gumbel noise, W k x classes) and ordinal features with `levels`
+    levels (X0 w + N(0, 0.5^2) binned at its empirical quantiles).  Cells are
+    observed with probability p_obs.  cyclic: the kinds alternate feature by
+    feature, else they come in contiguous groups."""
+    rng = rng_for(seed)
+    kinds = [0] * n_real + [1] * n_bool + [2] * n_cat + [3] * n_ord
+    if cyclic:
+        # the i-th feature of every kind, then the (i+1)-th, ...
+        keys = [i * 4 + g for g, cnt in enumerate((n_real, n_bool, n_cat, n_ord)) for i in range(cnt)]
+        order = np.argsort(np.array(keys), kind="stable")
+        kinds = [kinds[o] for o in order]
+    nf = len(kinds)
+    X0 = rng.standard_normal((m, k))
+    rowptr, featidx = omega_bernoulli(m, nf, p_obs, rng)
+    rows = np.repeat(np.arange(m, dtype=np.int32), np.diff(rowptr))
+    val = np.empty(featidx.size)
+    fkind = np.zeros(nf, np.int32)
+    flev = np.zeros(nf, np.int32)
+    lkind = np.zeros(nf, np.int32)
+    lparam = np.zeros(nf)
+    llev = np.zeros(nf, np.int32)
+    for j, kd in enumerate(kinds):
+        sel = featidx == j
+        r = rows[sel]
+        if kd == 0:
+            u = X0[r] @ rng.standard_normal(k)
+            val[sel] = u + rng.laplace(0.0, 0.5, r.size)
+            lkind[j], lparam[j] = LOSS_HUBER, 1.0
+        elif kd == 1:
+            u = X0[r] @ rng.standard_normal(k)
+            val[sel] = np.where(u + 0.5 * rng.standard_normal(r.size) >= 0, 1.0, -1.0)
+            lkind[j] = LOSS_HINGE
+        elif kd == 2:
+            S = X0[r] @ rng.standard_normal((k, classes)) + rng.gumbel(size=(r.size, classes))
+            val[sel] = np.argmax(S, axis=1) + 1.0
+            fkind[j], flev[j] = FEAT_CATEGORICAL, classes
+        else:
+            s = X0 @ rng.standard_normal(k) + 0.5 * rng.standard_normal(m)
+            edges = np.quantile(s, np.linspace(0, 1, levels + 1)[1:-1])
+            val[sel] = np.searchsorted(edges, s[r]) + 1.0
+            fkind[j], flev[j] = FEAT_ORDINAL_MD, levels
+    widths = np.where(fkind == FEAT_CATEGORICAL, flev, np.where(fkind == FEAT_ORDINAL_MD, flev - 1, 1))
+    colptr, rowidx, cval = csc_from_csr(m, nf, rowptr, featidx, val)
+    Yt0 = rng.standard_normal((int(widths.sum()), k))
+    X0i = rng.standard_normal((m, k))
+    return FeatureTable(name, m, nf, k, rowptr, featidx.astype(np.int32), val.astype(np.float64), colptr,
+                        rowidx, cval.astype(np.float64), fkind, flev, lkind, lparam, llev, rx, ry, X0i, Yt0)

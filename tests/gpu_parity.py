@@ -42,7 +42,7 @@ def _flipped(got, want, tol=1e-4):
     return (np.abs(np.asarray(got, np.float64) - want).max(axis=1) / scale) > tol
 
 
-def synced_sweeps(g, o, t, nsweeps, rtol=1e-5, max_flip_frac=0.01, offset=False, col_scale=None):
+def synced_sweeps(g, o, t, nsweeps, rtol=1e-5, max_flip_frac=0.01, offset=False, col_scale=None, problem=None):
     """Run nsweeps GPU sweeps; before each, hand the GPU state to the oracle
     and run the same sweep there.  Checks per sweep: objective within rtol,
     accepted row / column counts within max(2, max_flip_frac) of each other,
@@ -50,11 +50,14 @@ def synced_sweeps(g, o, t, nsweeps, rtol=1e-5, max_flip_frac=0.01, offset=False,
     step-size arrays equal (to FP32 rounding, 1e-6) on all but the rows /
     columns whose decision flipped.  Returns the per-sweep relative objective
     differences.  offset / col_scale: the oracle's model of a handle with
-    glrm_set_offset / glrm_set_column_scale."""
-    p = oracle_problem(o, t, offset=offset, col_scale=col_scale)
+    glrm_set_offset / glrm_set_column_scale.  problem: an oracle problem to
+    use instead (a FeatureProblem for a model of an embedded feature table);
+    the sizes are the handle's."""
+    p = problem if problem is not None else oracle_problem(o, t, offset=offset, col_scale=col_scale)
+    m, n, k = g.m, g.n, g.k
     rels = []
     for _ in range(nsweeps):
-        X, Yt, ax, ay, _ = decode_state(g.state(), t.m, t.n, t.k)
+        X, Yt, ax, ay, _ = decode_state(g.state(), m, n, k)
         h = g.sweep(1)[0]
         acc = g.accepts()
         Xo, Yo, axo, ayo, oh, oacc = p.proxgrad(X.astype(np.float64), Yt.astype(np.float64), 1,
@@ -62,10 +65,10 @@ def synced_sweeps(g, o, t, nsweeps, rtol=1e-5, max_flip_frac=0.01, offset=False,
         rel = abs(h - oh[0]) / abs(oh[0])
         rels.append(rel)
         assert rel < rtol, (rel, h, oh[0])
-        for a, b, cnt in ((acc[0], oacc[0, 0], t.m), (acc[1], oacc[0, 1], t.n)):
+        for a, b, cnt in ((acc[0], oacc[0, 0], m), (acc[1], oacc[0, 1], n)):
             assert abs(int(a) - int(b)) <= max(2, int(max_flip_frac * cnt)), (acc, oacc)
-        Xg, Yg, axg, ayg, _ = decode_state(g.state(), t.m, t.n, t.k)
-        for F, Fo, a, ao, cnt, what in ((Xg, Xo, axg, axo, t.m, "X"), (Yg, Yo, ayg, ayo, t.n, "Yt")):
+        Xg, Yg, axg, ayg, _ = decode_state(g.state(), m, n, k)
+        for F, Fo, a, ao, cnt, what in ((Xg, Xo, axg, axo, m, "X"), (Yg, Yo, ayg, ayo, n, "Yt")):
             bad = _flipped(F, Fo)
             sbad = np.abs(np.asarray(a, np.float64) - ao) > 1e-6 * np.abs(ao)
             allowed = max(2, int(max_flip_frac * cnt))
