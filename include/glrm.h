@@ -222,6 +222,43 @@ int glrm_column_stats(glrm_t h, double *mu_dev, double *sigma2_dev);
  * glrm_als_sweep and glrm_proxprox_sweep on a weighted model.  Synchronises. */
 int glrm_set_column_scale(glrm_t h, const double *w_host);
 
+/* Change the regulariser weights (kinds stay).  Takes effect for work
+ * enqueued afterwards; step sizes are not touched. */
+int glrm_set_reg_weights(glrm_t h, double rx_weight, double ry_weight);
+
+/* Global optimality certificate (Section 7.6, eq. convex-certificate) of the
+ * current factors, for a model whose regulariser is w (||X||^2 + ||Y||^2)
+ * (both GLRM_REG_QUAD with one weight w > 0; no offset):
+ *     *norm_host = || (1/gamma) G + U V^T ||_2,   gamma = 2 w,
+ * G (m x n, zero off Omega) holding w_j L_j'(x_i . y_j, A_ij) (0 at a kink;
+ * column weights included) and U V^T the product of the singular vectors of
+ * Z = X Y with singular values above 1e-10 of the largest (singular values
+ * of X or Y below 1e-7 of their largest count as zero: they are found from
+ * the k x k Gram matrices).  gamma = 2 w because ||Z||_* is the infimum of
+ * (||X||^2 + ||Y||^2) / 2 over X Y = Z.  A value <= 1 certifies that
+ * (X, Y) solves the rank-constrained problem globally when the loss is
+ * convex and differentiable (for a nondifferentiable loss a value > 1 does
+ * not prove the opposite).  The 2-norm is estimated by power iteration on
+ * M^T M (FP64, a deterministic start vector) until the estimate changes by
+ * at most tol relative, or max_iters iterations (*iters_host, if not NULL,
+ * receives the count); the estimate approaches the norm from below.
+ * Sparse observed sets only (GLRM_ERR_STATE for glrm_set_dense tables).
+ * Allocates O(nnz + m + n) FP64 scratch.  Synchronises. */
+int glrm_certificate(glrm_t h, int32_t max_iters, double tol, double *norm_host, int32_t *iters_host);
+
+/* Regularisation path by homotopy (Section 8.1, "Regularization paths"):
+ * for t = 0 .. nvals-1 set both regulariser weights to gamma_host[t] (in the
+ * order given, normally decreasing), reset the step sizes
+ * (glrm_reset_steps), sweep from the current factors until
+ * glrm_sweep_until(max_sweeps, rtol, no reference, window) stops, and
+ * record the objective (objective_host[t]), the sweeps run (sweeps_host[t])
+ * and, with cert_host not NULL, glrm_certificate(cert_iters, 1e-10)
+ * (cert_host[t]).  The factors of the last weight remain in the handle.
+ * Synchronises. */
+int glrm_regularization_path(glrm_t h, int32_t nvals, const double *gamma_host, int32_t max_sweeps, double rtol,
+                             int32_t window, double *objective_host, int32_t *sweeps_host, double *cert_host,
+                             int32_t cert_iters);
+
 /* ---- Tables of multi-dimensional features (Section 6, eq. mpca) ----------
  * Feature j of such a table is represented by a block Y_j of d_j columns of
  * Y and entry (i, j) costs L_j(x_i Y_j, A_ij):

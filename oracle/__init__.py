@@ -111,6 +111,8 @@ def _load():
                                         p, i32]
         lib.oracle_column_stats.restype = i32
         lib.oracle_column_stats.argtypes = [i64, i64, i64, p, p, p, p, p, p, p, p, i32]
+        lib.oracle_entry_derivs.restype = i32
+        lib.oracle_entry_derivs.argtypes = [i64, i32, p, p, p, p, p, p, p, p, p, p]
         lib.oracle_feature_dim.restype = i32
         lib.oracle_feature_dim.argtypes = [i32, i32]
         lib.oracle_mloss.restype = d
@@ -340,6 +342,36 @@ class Problem:
         if rc:
             raise ValueError(f"oracle_column_stats failed ({rc})")
         return mu, s2
+
+    def entry_derivs(self, X, Yt):
+        """w_j L_j'(x_i . y_j, A_ij) per observed entry (rows, then columns)."""
+        X = _c(X, np.float64)
+        Yt = _c(Yt, np.float64)
+        out = np.empty(self.nnz)
+        _load().oracle_entry_derivs(self.nnz, self.k, _ptr(self.rows), _ptr(self.cols), _ptr(self.vals),
+                                    *self._losses(), self._scale(), _ptr(X), _ptr(Yt), _ptr(out))
+        return out
+
+    def certificate(self, X, Yt, rank_rtol: float = 1e-10):
+        """||(1/gamma) G + U V^T||_2 (Sec. 7.6, eq. convex-certificate) for the
+        quadratic regulariser w (||X||^2 + ||Y||^2) of this problem: with
+        ||Z||_* = inf 1/2 (||X||^2 + ||Y||^2) over X Y = Z (Sec. 7.6's lemma)
+        the convex problem is L(Z) + 2 w ||Z||_*, so gamma = 2 w.  G is the
+        m x n loss gradient (zero off Omega), U V^T the product of the
+        singular vectors of Z = X Y with singular values above rank_rtol
+        times the largest.  Dense numpy (library SVD and matrix 2-norm): for
+        small problems."""
+        if self.rx[0] != REG_QUAD or self.ry[0] != REG_QUAD or self.rx[1] != self.ry[1] or self.rx[1] <= 0:
+            raise ValueError("the certificate needs one quadratic regulariser weight on X and Y")
+        gamma = 2.0 * self.rx[1]
+        X = np.asarray(X, np.float64)
+        Yt = np.asarray(Yt, np.float64)
+        G = np.zeros((self.m, self.n))
+        G[self.rows, self.cols] = self.entry_derivs(X, Yt)
+        U, sv, Vt = np.linalg.svd(X @ Yt.T, full_matrices=False)
+        r = int(np.sum(sv > rank_rtol * sv[0])) if sv.size and sv[0] > 0 else 0
+        M = G / gamma + U[:, :r] @ Vt[:r]
+        return float(np.linalg.norm(M, 2))
 
     def proxprox(self, X, Yt, alpha: float, inner: int, nsweeps: int, nthreads: int = 0):
         """Alternating prox-prox sweeps for quadratic loss (Sec. 7.2 prox-prox

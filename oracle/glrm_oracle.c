@@ -822,6 +822,21 @@ int oracle_column_stats(int64_t m, int64_t n, int64_t nnz, const int32_t *row, c
     return 0;
 }
 
+/* Per observed entry, in the order given: w_j L_j'(x_i . y_j, A_ij) (w_j = 1
+ * when wcol is NULL) -- the entries of the loss gradient G in dL(Z) at
+ * Z = X Y (Section 7.6, eq. convex-certificate), 0 at a kink. */
+int oracle_entry_derivs(int64_t nnz, int k, const int32_t *row, const int32_t *col, const double *val,
+                        const int32_t *lkind, const double *lparam, const int32_t *llevels, const double *wcol,
+                        const double *X, const double *Yt, double *out)
+{
+    for (int64_t e = 0; e < nnz; ++e) {
+        const int32_t i = row[e], j = col[e];
+        const double u = dot(k, X + (int64_t)i * k, Yt + (int64_t)j * k);
+        out[e] = (wcol ? wcol[j] : 1.0) * oracle_dloss(lkind[j], lparam[j], llevels[j], u, val[e]);
+    }
+    return 0;
+}
+
 /* ------------------------------------------- multi-dimensional losses */
 
 /* Section 6 ("Multi-dimensional loss functions", eq. mpca): feature j of the

@@ -1102,6 +1102,65 @@ int glrm_column_stats(glrm_t h, double *mu_dev, double *sigma2_dev)
     return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_column_stats");
 }
 
+// ------------------------------------- certificate and regularisation path
+
+int glrm_set_reg_weights(glrm_t h, double rx_weight, double ry_weight)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!(rx_weight >= 0.0) || !(ry_weight >= 0.0) || !std::isfinite(rx_weight) || !std::isfinite(ry_weight))
+        return fail(h, GLRM_ERR_ARG, "regulariser weights must be finite and >= 0");
+    drop_conv_graph(h);  // captured sweeps carry the weights
+    h->rx_w = rx_weight;
+    h->ry_w = ry_weight;
+    return GLRM_OK;
+}
+
+int glrm_certificate(glrm_t h, int32_t max_iters, double tol, double *norm_host, int32_t *iters_host)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (!norm_host || max_iters < 1 || !(tol >= 0.0)) return fail(h, GLRM_ERR_ARG, "bad arguments");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    if (h->dn.on && !h->dn.missing)
+        return fail(h, GLRM_ERR_STATE, "the certificate runs on an observed set, not on a dense table");
+    if (h->rx_kind != kRegQuad || h->ry_kind != kRegQuad || h->rx_w != h->ry_w || !(h->rx_w > 0.0))
+        return fail(h, GLRM_ERR_ARG, "the certificate needs one quadratic regulariser weight > 0 on X and Y");
+    if (h->offset) return fail(h, GLRM_ERR_ARG, "the certificate does not take an offset");
+    DeviceGuard dg(h->device);
+    double nrm = 0.0;
+    int done = 0;
+    cudaError_t e = certificate_norm(h, max_iters, tol, &nrm, &done);
+    if (e != cudaSuccess) return cuda_fail(h, e, "glrm_certificate");
+    *norm_host = nrm;
+    if (iters_host) *iters_host = done;
+    return std::isfinite(nrm) ? GLRM_OK : fail(h, GLRM_ERR_NONFINITE, "non-finite certificate");
+}
+
+int glrm_regularization_path(glrm_t h, int32_t nvals, const double *gamma_host, int32_t max_sweeps, double rtol,
+                             int32_t window, double *objective_host, int32_t *sweeps_host, double *cert_host,
+                             int32_t cert_iters)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (nvals < 1 || !gamma_host || !objective_host || !sweeps_host || (cert_host && cert_iters < 1))
+        return fail(h, GLRM_ERR_ARG, "bad arguments");
+    for (int32_t t = 0; t < nvals; ++t)
+        if (!(gamma_host[t] >= 0.0) || !std::isfinite(gamma_host[t]))
+            return fail(h, GLRM_ERR_ARG, "regularisation weights must be finite and >= 0");
+    for (int32_t t = 0; t < nvals; ++t) {
+        int rc = glrm_set_reg_weights(h, gamma_host[t], gamma_host[t]);
+        if (rc == GLRM_OK) rc = glrm_reset_steps(h);
+        int32_t done = 0;
+        if (rc == GLRM_OK) rc = glrm_sweep_until(h, max_sweeps, rtol, NAN, window, &done, nullptr);
+        if (rc == GLRM_OK) rc = glrm_objective(h, objective_host + t);
+        if (rc != GLRM_OK) return rc;
+        sweeps_host[t] = done;
+        if (cert_host) {
+            rc = glrm_certificate(h, cert_iters, 1e-10, cert_host + t, nullptr);
+            if (rc != GLRM_OK) return rc;
+        }
+    }
+    return GLRM_OK;
+}
+
 // ------------------------------------------------ multi-dimensional features
 
 namespace {

@@ -267,6 +267,8 @@ constexpr int kFeatScalar = 0, kFeatCategorical = 1, kFeatOrdinal = 2;
 struct FeatDev {
     int32_t kind, levels, width, first;
 };
+// ||(1/gamma) G + U V^T||_2 by power iteration (glrm_cert.cu).
+cudaError_t certificate_norm(glrm_s *h, int iters, double tol, double *norm, int *done);
 // Raise *flag when an index lies outside [0, bound).
 cudaError_t launch_check_index(const int32_t *idx, int64_t n, int64_t bound, int *flag, cudaStream_t st);
 cudaError_t launch_embed_rowcount(int64_t m, const int32_t *rowptr, const int32_t *featidx, const FeatDev *F,

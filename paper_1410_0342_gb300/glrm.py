@@ -61,6 +61,9 @@ def _load():
         "glrm_get_factors_host": [p, p, p],
         "glrm_reset_steps": [p],
         "glrm_embed_losses": [i32, p, p, p, p],
+        "glrm_set_reg_weights": [p, f64, f64],
+        "glrm_certificate": [p, i32, f64, p, p],
+        "glrm_regularization_path": [p, i32, p, i32, f64, i32, p, p, p, i32],
         "glrm_embed_size": [i32, p, p, p, p, p],
         "glrm_embed_features": [i32, p, i64, i64, p, p, p, p, p, p, i32, p, p, p, p, p, p, p],
         "glrm_decode_features": [p, i32, p, i64, p, p, p],
@@ -228,6 +231,29 @@ def glrm_set_column_scale(h, w=None):
         return
     arr = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
     _check(_lib.glrm_set_column_scale(h, _ptr(arr)), h)
+
+
+def glrm_set_reg_weights(h, rx_weight, ry_weight):
+    _check(_lib.glrm_set_reg_weights(h, float(rx_weight), float(ry_weight)), h)
+
+
+def glrm_certificate(h, max_iters=1000, tol=1e-10):
+    """(norm, iterations) of the optimality certificate (Sec. 7.6)."""
+    nrm = ctypes.c_double()
+    it = ctypes.c_int32()
+    _check(_lib.glrm_certificate(h, int(max_iters), float(tol), ctypes.byref(nrm), ctypes.byref(it)), h)
+    return nrm.value, it.value
+
+
+def glrm_regularization_path(h, gammas, max_sweeps, rtol, window=1, cert_iters=0):
+    """(objectives, sweeps, certificates or None) per weight (Sec. 8.1)."""
+    g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64))
+    obj = np.empty(g.size)
+    sw = np.empty(g.size, dtype=np.int32)
+    cert = np.empty(g.size) if cert_iters > 0 else None
+    _check(_lib.glrm_regularization_path(h, g.size, _ptr(g), int(max_sweeps), float(rtol), int(window), _ptr(obj),
+                                         _ptr(sw), _ptr(cert) if cert is not None else None, int(cert_iters)), h)
+    return obj, sw, cert
 
 
 def _features(fkind, flevels):
@@ -655,6 +681,15 @@ class GLRM:
 
     def objective(self):
         return glrm_objective(self.h)
+
+    def certificate(self, max_iters=1000, tol=1e-10):
+        return glrm_certificate(self.h, max_iters, tol)
+
+    def set_reg_weights(self, rx_weight, ry_weight):
+        glrm_set_reg_weights(self.h, rx_weight, ry_weight)
+
+    def regularization_path(self, gammas, max_sweeps, rtol, window=1, cert_iters=0):
+        return glrm_regularization_path(self.h, gammas, max_sweeps, rtol, window, cert_iters)
 
     def set_offset(self, on=True):
         glrm_set_offset(self.h, on)
