@@ -259,6 +259,25 @@ int glrm_regularization_path(glrm_t h, int32_t nvals, const double *gamma_host, 
                              int32_t window, double *objective_host, int32_t *sweeps_host, double *cert_host,
                              int32_t cert_iters);
 
+/* SVD initialisation of the factors (Section 7.5).  With k' = k - 1 when
+ * the offset is on (glrm_set_offset), else k: the column statistics mu_j,
+ * sigma2_j of glrm_column_stats; the scaled table
+ *     A~_ij = m / (sigma_j m_j) (A_ij - mu_j) on Omega, 0 elsewhere
+ * (m_j = column j's observation count; a column without a finite
+ * sigma_j > 0 scales to 0 and takes sigma_j = 1 below); its top k' singular
+ * triples U S V^T by the randomized range finder (Section 7.5 names Halko et
+ * al.): a pseudo-random n x (k' + oversample) block from `seed` (at most 96
+ * columns), power_iters rounds of A~^T / A~ products each followed by an
+ * orthonormalisation (FP64 Gram eigendecomposition), then the eigenvectors
+ * of B B^T for B = Q^T A~; and
+ *     X = U S^1/2,   Y = S^1/2 V^T diag(sigma)
+ * written into the model's factors, with X's column k-1 set to 1 and Y's
+ * row k-1 to mu_j (0 for an empty column) when the offset is on.
+ * singular_values_host (k' doubles, may be NULL) receives S.  Step sizes are
+ * not touched.  Sparse observed sets only.  Allocates FP64 scratch of
+ * O(nnz + (m + n)(k' + oversample)).  Synchronises. */
+int glrm_svd_init(glrm_t h, int32_t oversample, int32_t power_iters, uint64_t seed, double *singular_values_host);
+
 /* ---- Tables of multi-dimensional features (Section 6, eq. mpca) ----------
  * Feature j of such a table is represented by a block Y_j of d_j columns of
  * Y and entry (i, j) costs L_j(x_i Y_j, A_ij):

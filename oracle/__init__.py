@@ -373,6 +373,33 @@ class Problem:
         M = G / gamma + U[:, :r] @ Vt[:r]
         return float(np.linalg.norm(M, 2))
 
+    def svd_init(self, offset: bool = False):
+        """SVD initialisation (Sec. 7.5): the scaled table
+        A~_ij = m / (sigma_j m_j) (A_ij - mu_j) on Omega (0 elsewhere; a column
+        without a finite sigma_j > 0 is 0 and takes sigma_j = 1), its top k'
+        singular triples (k' = k - 1 with the offset, else k; numpy's dense
+        SVD), X = U S^1/2, Y = S^1/2 V^T diag(sigma), and with the offset X's
+        last column 1 and Y's last row mu (0 where undefined).  Returns
+        (X, Yt, S[:k'])."""
+        kp = self.k - 1 if offset else self.k
+        mu, s2 = self.column_stats()
+        sg = np.sqrt(s2)
+        valid = np.isfinite(sg) & (sg > 0)
+        mj = self.col_counts().astype(np.float64)
+        fac = np.where(valid, self.m / (np.where(valid, sg, 1.0) * np.maximum(mj, 1.0)), 0.0)
+        At = np.zeros((self.m, self.n))
+        At[self.rows, self.cols] = fac[self.cols] * (self.vals - np.nan_to_num(mu)[self.cols])
+        U, S, Vt = np.linalg.svd(At, full_matrices=False)
+        X = np.zeros((self.m, self.k))
+        Yt = np.zeros((self.n, self.k))
+        r = np.sqrt(S[:kp])
+        X[:, :kp] = U[:, :kp] * r
+        Yt[:, :kp] = Vt[:kp].T * r * np.where(valid, sg, 1.0)[:, None]
+        if offset:
+            X[:, self.k - 1] = 1.0
+            Yt[:, self.k - 1] = np.nan_to_num(mu)
+        return X, Yt, S[:kp]
+
     def proxprox(self, X, Yt, alpha: float, inner: int, nsweeps: int, nthreads: int = 0):
         """Alternating prox-prox sweeps for quadratic loss (Sec. 7.2 prox-prox
         update, Sec. 7.3 cached factorisation) with the problem's regularisers:

@@ -768,7 +768,10 @@ int oracle_proxprox(int64_t m, int64_t n, int k, int64_t nnz, const int32_t *row
  * on [min a - 32, max a + 32] down to an interval of 1e-13 of its width.
  * The search compares sums, so their rounding error limits where it can place
  * the minimiser: the sums are compensated (Neumaier), which keeps them
- * accurate to a few units of rounding whatever the column's length. */
+ * accurate to a few units of rounding whatever the column's length.  Where
+ * the minimisers form an interval (a median of an even count, a quantile,
+ * the flat bottom of a hinge sum) mu_j is its smallest point: a bisection
+ * for the least x whose sum is within rounding of the minimum. */
 static double col_sum(int kind, double param, int levels, const double *a, int64_t cnt, double mu)
 {
     double s = 0.0, c = 0.0;
@@ -800,7 +803,7 @@ int oracle_column_stats(int64_t m, int64_t n, int64_t nnz, const int32_t *row, c
         for (int64_t e = 1; e < cnt; ++e) { lo = a[e] < lo ? a[e] : lo; hi = a[e] > hi ? a[e] : hi; }
         lo -= 32.0;
         hi += 32.0;
-        const double gr = 0.5 * (sqrt(5.0) - 1.0), width = hi - lo;
+        const double gr = 0.5 * (sqrt(5.0) - 1.0), width = hi - lo, lo0 = lo;
         double x1 = hi - gr * (hi - lo), x2 = lo + gr * (hi - lo);
         double f1 = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, x1);
         double f2 = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, x2);
@@ -815,7 +818,19 @@ int oracle_column_stats(int64_t m, int64_t n, int64_t nnz, const int32_t *row, c
                 f2 = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, x2);
             }
         }
-        mu[j] = 0.5 * (lo + hi);
+        /* the minimisers of S_j form an interval (a flat bottom for the
+         * piecewise-linear losses); take its smallest point: the least x in
+         * the bracket with S(x) within rounding of the minimum found */
+        double best = 0.5 * (lo + hi);
+        const double smin = col_sum(lkind[j], lparam[j], llevels[j], a, cnt, best);
+        const double slack = 4e-15 * (fabs(smin) > 1.0 ? fabs(smin) : 1.0);
+        double l0 = lo0, h0 = best;
+        for (int it = 0; it < 200 && h0 - l0 > 1e-15 * width; ++it) {
+            const double mid = 0.5 * (l0 + h0);
+            if (col_sum(lkind[j], lparam[j], llevels[j], a, cnt, mid) <= smin + slack) h0 = mid;
+            else l0 = mid;
+        }
+        mu[j] = h0;
         sigma2[j] = cnt > 1 ? col_sum(lkind[j], lparam[j], llevels[j], a, cnt, mu[j]) / (double)(cnt - 1) : NAN;
     }
     lists_free(&L);

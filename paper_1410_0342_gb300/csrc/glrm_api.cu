@@ -1161,6 +1161,19 @@ int glrm_regularization_path(glrm_t h, int32_t nvals, const double *gamma_host, 
     return GLRM_OK;
 }
 
+int glrm_svd_init(glrm_t h, int32_t oversample, int32_t power_iters, uint64_t seed, double *singular_values_host)
+{
+    if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
+    if (oversample < 0 || power_iters < 0 || power_iters > 100) return fail(h, GLRM_ERR_ARG, "bad arguments");
+    if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
+    if (h->dn.on && !h->dn.missing)
+        return fail(h, GLRM_ERR_STATE, "the SVD initialisation runs on an observed set, not on a dense table");
+    if (h->offset && h->k < 1) return fail(h, GLRM_ERR_ARG, "bad rank");
+    DeviceGuard dg(h->device);
+    cudaError_t e = svd_init(h, oversample, power_iters, (unsigned long long)seed, singular_values_host);
+    return e == cudaSuccess ? GLRM_OK : cuda_fail(h, e, "glrm_svd_init");
+}
+
 // ------------------------------------------------ multi-dimensional features
 
 namespace {

@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kCertBlocks = 304;  // partial sums of the reductions (2 x 152 SMs)
 constexpr int kJacobiSweeps = 60;
+constexpr int kSvdMaxL = 96;  // columns of the randomized range finder (k + oversampling)
 
 // g[e] = w_j L_j'(u, a) with u = x_i . y_j accumulated in FP64 in coordinate
 // order, one warp per segment; the same value in both orders.
@@ -425,7 +426,275 @@ cudaError_t certificate_impl(glrm_s *h, int iters, double tol, double *norm, int
     return e;
 }
 
+// ------------------------------------------------------- SVD initialisation
+// Section 7.5: the scaled table A~ (a_e -> (m / (sigma_j m_j)) (a_e - mu_j)
+// on Omega, 0 elsewhere), its top k' singular triples by the randomized range
+// finder with power iterations (Section 7.5 points to Halko et al.), and
+// X = U S^1/2, Y = S^1/2 V^T diag(sigma) (plus the offset column / row).
+
+// Scaled values in one orientation (FP64): column j's factor from its
+// statistics; a column without a finite sigma_j > 0 scales to 0.
+template <class T>
+__global__ void svd_scale_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                 const T *__restrict__ val, bool rows, int64_t m, const int32_t *__restrict__ colptr,
+                                 const double *__restrict__ mu, const double *__restrict__ s2,
+                                 double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nseg) return;
+    for (int e = ptr[s] + lane; e < ptr[s + 1]; e += 32) {
+        const int64_t j = rows ? idx[e] : s;
+        const double sg = sqrt(s2[j]);
+        const double mj = (double)(colptr[j + 1] - colptr[j]);
+        out[e] = (sg > 0.0 && sg < 1e300) ? (double)m / (sg * mj) * ((double)val[e] - mu[j]) : 0.0;
+    }
+}
+
+// out (nseg x l) = segment sums of a_e In[idx_e, :] (In: other x l, FP64),
+// one warp per segment, lanes over the l columns.
+__global__ void svd_spmm_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                const double *__restrict__ a, const double *__restrict__ In, int l,
+                                double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nseg) return;
+    double acc[kSvdMaxL / 32];
+#pragma unroll
+    for (int q = 0; q < kSvdMaxL / 32; ++q) acc[q] = 0.0;
+    for (int e = ptr[s]; e < ptr[s + 1]; ++e) {
+        const double av = a[e];
+        const double *row = In + (int64_t)idx[e] * l;
+#pragma unroll
+        for (int q = 0; q < kSvdMaxL / 32; ++q) {
+            const int c = q * 32 + lane;
+            if (c < l) acc[q] += av * row[c];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSvdMaxL / 32; ++q) {
+        const int c = q * 32 + lane;
+        if (c < l) out[s * l + c] = acc[q];
+    }
+}
+
+// Pseudo-random start block (splitmix64 of the seed and the index), in [-1/2, 1/2).
+__global__ void svd_random_kernel(int64_t cnt, unsigned long long seed, double *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    unsigned long long z = seed + (unsigned long long)i * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    out[i] = (double)(z >> 11) * 0x1p-53 - 0.5;
+}
+
+// Partial Gram matrices (all l x l entries) of a tall FP64 matrix.
+__global__ void svd_gram_kernel(int64_t rows, const double *__restrict__ F, int l, double *__restrict__ part)
+{
+    for (int t = threadIdx.x; t < l * l; t += blockDim.x) {
+        const int p = t / l, q = t % l;
+        double acc = 0.0;
+        if (q >= p)
+            for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) acc += F[r * l + p] * F[r * l + q];
+        part[(int64_t)blockIdx.x * l * l + t] = acc;
+    }
+}
+
+// Orthonormalising factor of a Gram matrix (upper triangle of G, l x l):
+// G = V D V^T (Jacobi); R = V D^-1/2 keeping eigenvalues above 1e-13 of the
+// largest (columns of the others zero), so F R has orthonormal (or zero)
+// columns.  One block.
+__global__ void svd_orth_kernel(const double *__restrict__ G, int l, double *__restrict__ scratch,
+                                double *__restrict__ R)
+{
+    double *A = scratch, *V = A + l * l;
+    const int r = threadIdx.x;
+    if (r < l)
+        for (int c = 0; c < l; ++c) A[r * l + c] = c >= r ? G[r * l + c] : G[c * l + r];
+    __syncthreads();
+    jacobi_eig(A, V, l);
+    double mx = 0.0;
+    for (int c = 0; c < l; ++c) mx = fmax(mx, A[c * l + c]);
+    if (r < l)
+        for (int c = 0; c < l; ++c) {
+            const double d = A[c * l + c];
+            R[r * l + c] = d > 1e-13 * mx && d > 0.0 ? V[r * l + c] / sqrt(d) : 0.0;
+        }
+}
+
+// The top kp eigenpairs of the Gram matrix of B^T (l x l, upper triangle):
+// eigenvalues s^2 descending; writes the right factors
+// PX = W_top diag(s^1/2) and PY = W_top diag(s^-1/2) (l x kp each; zero for
+// s below 1e-13 of the largest s^2).  One block.
+__global__ void svd_top_kernel(const double *__restrict__ G, int l, int kp, double *__restrict__ scratch,
+                               double *__restrict__ PX, double *__restrict__ PY, double *__restrict__ sv)
+{
+    double *A = scratch, *V = A + l * l;
+    int *order = (int *)(V + l * l);
+    const int r = threadIdx.x;
+    if (r < l)
+        for (int c = 0; c < l; ++c) A[r * l + c] = c >= r ? G[r * l + c] : G[c * l + r];
+    __syncthreads();
+    jacobi_eig(A, V, l);
+    if (r == 0) {
+        for (int c = 0; c < l; ++c) order[c] = c;
+        for (int a = 0; a < l; ++a)  // selection sort, descending, stable
+            for (int b = a + 1; b < l; ++b)
+                if (A[order[b] * l + order[b]] > A[order[a] * l + order[a]]) {
+                    const int t = order[a];
+                    order[a] = order[b];
+                    order[b] = t;
+                }
+    }
+    __syncthreads();
+    const double mx = A[order[0] * l + order[0]];
+    if (r < l)
+        for (int c = 0; c < kp; ++c) {
+            const double d = A[order[c] * l + order[c]];
+            const bool ok = d > 1e-13 * mx && d > 0.0;
+            const double s = ok ? sqrt(d) : 0.0;
+            PX[r * kp + c] = ok ? V[r * l + order[c]] * sqrt(s) : 0.0;
+            PY[r * kp + c] = ok ? V[r * l + order[c]] / sqrt(s) : 0.0;
+            if (r == 0) sv[c] = s;
+        }
+}
+
+// out = In R for row-major In (rows x l) and R (l x l): rows in place.
+__global__ void svd_right_kernel(int64_t rows, double *__restrict__ F, int l, const double *__restrict__ R)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= rows) return;
+    double in[kSvdMaxL / 32], out[kSvdMaxL / 32];
+#pragma unroll
+    for (int q = 0; q < kSvdMaxL / 32; ++q) {
+        const int c = q * 32 + lane;
+        in[q] = c < l ? F[s * l + c] : 0.0;
+        out[q] = 0.0;
+    }
+    for (int i = 0; i < l; ++i) {
+        const double fi = __shfl_sync(0xffffffffu, in[i / 32], i % 32);
+#pragma unroll
+        for (int q = 0; q < kSvdMaxL / 32; ++q) {
+            const int c = q * 32 + lane;
+            if (c < l) out[q] += fi * R[i * l + c];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSvdMaxL / 32; ++q) {
+        const int c = q * 32 + lane;
+        if (c < l) F[s * l + c] = out[q];
+    }
+}
+
+// Factor rows: dst[s, 0..kp) = scale_s * (In[s, :] P), scale_s = sigma_s (Y)
+// or 1 (X); with the offset, dst[s, k-1] = 1 (X) or mu_s (Y; 0 where NaN).
+template <class T>
+__global__ void svd_factor_kernel(int64_t rows, const double *__restrict__ In, int l, const double *__restrict__ P,
+                                  int kp, int k, const double *__restrict__ s2, const double *__restrict__ mu,
+                                  bool offset, T *__restrict__ dst)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= rows) return;
+    double sc = 1.0;
+    if (s2) {
+        const double sg = sqrt(s2[s]);
+        sc = (sg > 0.0 && sg < 1e300) ? sg : 1.0;
+    }
+    for (int c = 0; c < kp; ++c) {
+        double acc = 0.0;
+        for (int i = 0; i < l; ++i) acc += In[s * l + i] * P[i * kp + c];
+        dst[s * k + c] = (T)(sc * acc);
+    }
+    for (int c = kp; c < k; ++c) {
+        double v = 0.0;
+        if (offset && c == k - 1) v = mu ? (mu[s] == mu[s] ? mu[s] : 0.0) : 1.0;
+        dst[s * k + c] = (T)v;
+    }
+}
+
+template <class T>
+cudaError_t svd_init_impl(glrm_s *h, int oversample, int power_iters, unsigned long long seed, double *sv_host)
+{
+    cudaStream_t st = h->stream;
+    const int64_t m = h->m, n = h->n, nnz = h->nnz;
+    const int k = h->k, kp = h->offset ? k - 1 : k;
+    const int l = std::min(kSvdMaxL, kp + oversample);
+    double *mu = nullptr, *s2 = nullptr, *ar = nullptr, *ac = nullptr, *Qm = nullptr, *Qn = nullptr;
+    double *part = nullptr, *small = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](double **p, size_t cnt) {
+        if (e == cudaSuccess) e = dalloc_bytes(h, (void **)p, std::max<size_t>(cnt, 2) * sizeof(double), st);
+    };
+    A(&mu, n);
+    A(&s2, n);
+    A(&ar, nnz);
+    A(&ac, nnz);
+    A(&Qm, (size_t)m * l);
+    A(&Qn, (size_t)n * l);
+    A(&part, (size_t)kCertBlocks * l * l);
+    A(&small, (size_t)6 * l * l + 3 * (size_t)l + 64);
+    double *G = small, *R = G + l * l, *scratch = R + l * l, *PX = scratch + 2 * l * l + l, *PY = PX + l * kp;
+    double *sv = PY + l * kp;
+    const int bt = ((l + 31) / 32) * 32;
+    auto orth = [&](double *F, int64_t rows) {  // F <- F (V D^-1/2) of its Gram
+        svd_gram_kernel<<<kCertBlocks, 256, 0, st>>>(rows, F, l, part);
+        cert_sum_kernel<<<1, 256, 0, st>>>(part, kCertBlocks, l * l, G);
+        svd_orth_kernel<<<1, bt, 0, st>>>(G, l, scratch, R);
+        svd_right_kernel<<<nblk(rows, 8), 256, 0, st>>>(rows, F, l, R);
+        h->launches += 4;
+    };
+    if (e == cudaSuccess) {
+        e = launch_column_stats(h, mu, s2);
+        if (kp > 0) {
+            const T *rv = (const T *)h->csr.val, *cv = (const T *)h->csc.val;
+            svd_scale_kernel<T><<<nblk(m, 8), 256, 0, st>>>(m, h->csr.ptr, h->csr.idx, rv, true, m, h->csc.ptr, mu,
+                                                            s2, ar);
+            svd_scale_kernel<T><<<nblk(n, 8), 256, 0, st>>>(n, h->csc.ptr, h->csc.idx, cv, false, m, h->csc.ptr, mu,
+                                                            s2, ac);
+            svd_random_kernel<<<nblk(n * l, 256), 256, 0, st>>>(n * l, seed, Qn);
+            svd_spmm_kernel<<<nblk(m, 8), 256, 0, st>>>(m, h->csr.ptr, h->csr.idx, ar, Qn, l, Qm);  // A~ Omega
+            h->launches += 4;
+            orth(Qm, m);
+            for (int it = 0; it < power_iters; ++it) {
+                svd_spmm_kernel<<<nblk(n, 8), 256, 0, st>>>(n, h->csc.ptr, h->csc.idx, ac, Qm, l, Qn);  // A~^T Q
+                orth(Qn, n);
+                svd_spmm_kernel<<<nblk(m, 8), 256, 0, st>>>(m, h->csr.ptr, h->csr.idx, ar, Qn, l, Qm);  // A~ Q
+                orth(Qm, m);
+                h->launches += 2;
+            }
+            // B^T = A~^T Q (n x l); its Gram B B^T = W diag(s^2) W^T
+            svd_spmm_kernel<<<nblk(n, 8), 256, 0, st>>>(n, h->csc.ptr, h->csc.idx, ac, Qm, l, Qn);
+            svd_gram_kernel<<<kCertBlocks, 256, 0, st>>>(n, Qn, l, part);
+            cert_sum_kernel<<<1, 256, 0, st>>>(part, kCertBlocks, l * l, G);
+            svd_top_kernel<<<1, bt, 0, st>>>(G, l, kp, scratch, PX, PY, sv);
+            h->launches += 4;
+        }
+        // X = Q W S^1/2; Y^T = diag(sigma) B^T W S^-1/2 (A~ ~ (Q W) S (B^T W S^-1)^T)
+        svd_factor_kernel<T><<<nblk(m, 256), 256, 0, st>>>(m, Qm, l, PX, kp, k, nullptr, nullptr, h->offset,
+                                                           (T *)h->X);
+        svd_factor_kernel<T><<<nblk(n, 256), 256, 0, st>>>(n, Qn, l, PY, kp, k, s2, mu, h->offset, (T *)h->Yt);
+        h->launches += 2;
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess && sv_host && kp > 0)
+            e = cudaMemcpyAsync(sv_host, sv, kp * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    for (double *p : {mu, s2, ar, ac, Qm, Qn, part, small})
+        if (p) cudaFreeAsync(p, st);
+    return e;
+}
+
 }  // namespace
+
+cudaError_t svd_init(glrm_s *h, int oversample, int power_iters, unsigned long long seed, double *sv_host)
+{
+    return h->prec == GLRM_FP64 ? svd_init_impl<double>(h, oversample, power_iters, seed, sv_host)
+                                : svd_init_impl<float>(h, oversample, power_iters, seed, sv_host);
+}
 
 cudaError_t certificate_norm(glrm_s *h, int iters, double tol, double *norm, int *done)
 {

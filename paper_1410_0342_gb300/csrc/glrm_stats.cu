@@ -8,7 +8,9 @@
 // a point with g(u) < 0 lies at or below every minimiser and one with
 // g(u) >= 0 at or above the smallest one (the subgradient taken at a kink
 // lies between the one-sided derivatives), so the bracket keeps the smallest
-// minimiser.  It starts at [min a - 32, max a + 32]; where S_j has no
+// minimiser (a sum within 1e-12 of the sum of its terms' magnitudes counts
+// as zero, so that rounding does not decide the side on an interval of
+// minimisers).  It starts at [min a - 32, max a + 32]; where S_j has no
 // minimiser (a hinge or logistic column with one label) the result is the
 // bracket end the derivative pushes towards.
 #include "glrm_handle.h"
@@ -19,6 +21,11 @@ namespace {
 constexpr double kStatBracket = 32.0;
 constexpr int kStatMaxIters = 80;   // the bracket shrinks to 2^-62 of its width well before
 constexpr int kDenseStatWarps = 32;  // warps per CTA of the dense-table kernel (32 columns per CTA)
+// A derivative sum within this fraction of the sum of its terms' magnitudes
+// counts as zero: on an interval of minimisers (a flat bottom) the rounding
+// of the sum must not decide the side, so the bracket closes on its smallest
+// point.
+constexpr double kStatTieRel = 1e-12;
 
 __device__ __forceinline__ double warp_min(double v)
 {
@@ -65,13 +72,16 @@ colstats_csc_kernel(int64_t n, const int32_t *__restrict__ ptr, const T *__restr
         for (int it = 0; it < kStatMaxIters && hi - lo > tol; ++it) {
             const double mid = lo + 0.5 * (hi - lo);
             if (!(mid > lo && mid < hi)) break;
-            double g = 0.0;
+            double g = 0.0, ga = 0.0;
             for (int q = b + lane; q < e; q += 32) {
                 double L;
-                g += loss_deriv<double>(sp, mid, (double)val[q], L);
+                const double d = loss_deriv<double>(sp, mid, (double)val[q], L);
+                g += d;
+                ga += fabs(d);
             }
             g = warp_sum(g);
-            if (g < 0.0) lo = mid;
+            ga = warp_sum(ga);
+            if (g < -kStatTieRel * ga) lo = mid;
             else hi = mid;
         }
         double ls = 0.0;
@@ -96,7 +106,7 @@ __global__ void __launch_bounds__(kDenseStatWarps * 32)
 colstats_dense_kernel(int64_t m, int64_t n, const float *__restrict__ A, int64_t lda,
                       const LossSpec *__restrict__ loss, double *__restrict__ mu, double *__restrict__ s2)
 {
-    __shared__ double red[kDenseStatWarps][33];
+    __shared__ double red[kDenseStatWarps][33], red2[kDenseStatWarps][33];
     __shared__ double lo_s[32], hi_s[32], tol_s[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t j = (int64_t)blockIdx.x * 32 + lane;
@@ -131,20 +141,26 @@ colstats_dense_kernel(int64_t m, int64_t n, const float *__restrict__ A, int64_t
         const double l = lo_s[lane], hh = hi_s[lane];
         const double mid = l + 0.5 * (hh - l);
         const bool live = col && hh - l > tol_s[lane] && mid > l && mid < hh;
-        double g = 0.0;
+        double g = 0.0, ga = 0.0;
         if (live)
             for (int64_t r = w; r < m; r += kDenseStatWarps) {
                 double L;
-                g += loss_deriv<double>(sp, mid, (double)Aj[r * lda], L);
+                const double d = loss_deriv<double>(sp, mid, (double)Aj[r * lda], L);
+                g += d;
+                ga += fabs(d);
             }
         red[w][lane] = g;
+        red2[w][lane] = ga;
         // every thread reads its column's bracket above; the barrier orders
         // those reads before warp 0 moves it
         if (!__syncthreads_or(live)) break;
         if (w == 0 && live) {
-            double v = 0.0;
-            for (int q = 0; q < kDenseStatWarps; ++q) v += red[q][lane];
-            if (v < 0.0) lo_s[lane] = mid;
+            double v = 0.0, va = 0.0;
+            for (int q = 0; q < kDenseStatWarps; ++q) {
+                v += red[q][lane];
+                va += red2[q][lane];
+            }
+            if (v < -kStatTieRel * va) lo_s[lane] = mid;
             else hi_s[lane] = mid;
         }
         __syncthreads();

@@ -62,6 +62,7 @@ def _load():
         "glrm_reset_steps": [p],
         "glrm_embed_losses": [i32, p, p, p, p],
         "glrm_set_reg_weights": [p, f64, f64],
+        "glrm_svd_init": [p, i32, i32, ctypes.c_uint64, p],
         "glrm_certificate": [p, i32, f64, p, p],
         "glrm_regularization_path": [p, i32, p, i32, f64, i32, p, p, p, i32],
         "glrm_embed_size": [i32, p, p, p, p, p],
@@ -231,6 +232,13 @@ def glrm_set_column_scale(h, w=None):
         return
     arr = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
     _check(_lib.glrm_set_column_scale(h, _ptr(arr)), h)
+
+
+def glrm_svd_init(h, kp, oversample=8, power_iters=4, seed=1410034200):
+    """Sec. 7.5 initialisation; returns the kp singular values used."""
+    sv = np.empty(max(kp, 1))
+    _check(_lib.glrm_svd_init(h, int(oversample), int(power_iters), int(seed), _ptr(sv)), h)
+    return sv[:kp]
 
 
 def glrm_set_reg_weights(h, rx_weight, ry_weight):
@@ -682,6 +690,14 @@ class GLRM:
     def objective(self):
         return glrm_objective(self.h)
 
+    def svd_init(self, oversample=8, power_iters=4, seed=1410034200, offset=None):
+        """offset: None keeps the handle's setting."""
+        if offset is not None:
+            self.set_offset(offset)
+            self._offset = bool(offset)
+        kp = self.k - 1 if getattr(self, "_offset", False) else self.k
+        return glrm_svd_init(self.h, kp, oversample, power_iters, seed)
+
     def certificate(self, max_iters=1000, tol=1e-10):
         return glrm_certificate(self.h, max_iters, tol)
 
@@ -693,6 +709,7 @@ class GLRM:
 
     def set_offset(self, on=True):
         glrm_set_offset(self.h, on)
+        self._offset = bool(on)
 
     def column_stats(self):
         """(mu, sigma2) per column, float64 on the device (Sec. 4.3)."""

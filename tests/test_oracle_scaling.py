@@ -232,3 +232,20 @@ def test_weighted_sweep_invariance(oracle_mod):
     np.testing.assert_allclose(hc, c * h1, rtol=1e-12)
     np.testing.assert_array_equal(accc, acc1)
     np.testing.assert_allclose(axc * c, ax1, rtol=1e-14)
+
+
+def test_column_stats_smallest_minimiser(oracle_mod):
+    """Where the minimisers form an interval mu_j is its smallest point: the
+    lower median of an even count (l1), the lower alpha-quantile, -1 for a
+    hinge column with as many +1 as -1 labels (S flat on [-1, 1])."""
+    o = oracle_mod
+    rng = np.random.default_rng(21)
+    v = np.sort(rng.normal(size=10))
+    mu, _ = _columns(o, [v], L1).column_stats()
+    assert mu[0] == pytest.approx(v[4], abs=1e-12)
+    alpha = 0.3  # alpha c = 3 for c = 10: every x in [v_3, v_4] (1-based) minimises
+    mu, _ = _columns(o, [v], QT, param=alpha).column_stats()
+    assert mu[0] == pytest.approx(v[2], abs=1e-12)
+    mu, s2 = _columns(o, [[1.0] * 3 + [-1.0] * 3], HI).column_stats()
+    assert mu[0] == pytest.approx(-1.0, abs=1e-12)
+    assert s2[0] == pytest.approx(6.0 / 5.0)
