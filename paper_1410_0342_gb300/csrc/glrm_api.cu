@@ -978,13 +978,21 @@ int glrm_create(int64_t m, int64_t n, int32_t k, const glrm_loss *col_loss, int3
     if (e == cudaSuccess) h->pooled = true;
     const size_t es = elem_size(precision);
     if (e == cudaSuccess) e = dalloc(h, &h->loss_dev, (size_t)n * sizeof(LossSpec));
+    if (e == cudaSuccess) e = dalloc(h, &h->loss_f, (size_t)n * sizeof(LossSpecF));
     if (e == cudaSuccess) e = dalloc(h, &h->X, (size_t)m * k * es);
     if (e == cudaSuccess) e = dalloc(h, &h->Yt, (size_t)n * k * es);
     if (e == cudaSuccess) e = dalloc(h, &h->alpha_x, (size_t)m * es);
     if (e == cudaSuccess) e = dalloc(h, &h->alpha_y, (size_t)n * es);
+    std::vector<LossSpecF> specf((size_t)n);
+    for (int64_t j = 0; j < n; ++j)
+        specf[(size_t)j] = LossSpecF{spec[(size_t)j].kind, spec[(size_t)j].levels, (float)spec[(size_t)j].param,
+                                     (float)spec[(size_t)j].levels};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->loss_dev, spec.data(), (size_t)n * sizeof(LossSpec),
                             cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->loss_f, specf.data(), (size_t)n * sizeof(LossSpecF), cudaMemcpyHostToDevice,
+                            h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->X, 0, (size_t)m * k * es, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Yt, 0, (size_t)n * k * es, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1792,6 +1800,7 @@ void glrm_destroy(glrm_t h)
         dense_free(h);
         free_scratch(h->s, h->stream);
         dfree(h->loss_dev, h->stream);
+        dfree(h->loss_f, h->stream);
         dfree(h->lscale, h->stream);
         dfree(h->X, h->stream);
         dfree(h->Yt, h->stream);

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 cand_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ order,
                  const int32_t *__restrict__ idx, const float *__restrict__ val, const float *__restrict__ F,
                  const float *__restrict__ C, const float *__restrict__ W, int k,
-                 const LossSpec *__restrict__ loss, double *__restrict__ part_old, double *__restrict__ part_new)
+                 const LossSpecF *__restrict__ loss, double *__restrict__ part_old, double *__restrict__ part_new)
 {
     using LN = Lanes<K>;
     constexpr int G = LN::G, S = LN::S, PER = LN::PER, VW = 4;
@@ -46,7 +46,7 @@ cand_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
     load_lane<float, S, G, VW, VEC>(f, F + (int64_t)ch.x * k, gl, k);
     load_lane<float, S, G, VW, VEC>(fp, C + (int64_t)ch.x * k, gl, k);
     float lo = 0.f, ln = 0.f;
-    LossSpec sp;
+    LossSpecF sp;
     if constexpr (!XSTEP) sp = loss[ch.x];
     for (int base = ch.y; base < ch.z; base += PER) {
         const int e = base + grp;
@@ -99,7 +99,7 @@ cudaError_t launch_cand(glrm_s *h, const Orient &o, const float *F, const float 
     const unsigned nb = blocks_for(o.nchunks, kWarpsPerBlock);
     auto go = [&](auto kern) {
         kern<<<nb, kWarpsPerBlock * 32, 0, h->stream>>>(o.nchunks, o.chunks, o.order, o.idx, (const float *)o.val, F, C,
-                                                        W, k, h->loss_dev, h->s.part_loss, h->s.part_loss2);
+                                                        W, k, h->loss_f, h->s.part_loss, h->s.part_loss2);
     };
     if (vec) go(cand_pass_kernel<K, XSTEP, true>);
     else go(cand_pass_kernel<K, XSTEP, false>);
@@ -148,32 +148,30 @@ inline cudaError_t bf16_half_step(glrm_s *h, bool xstep)
     h->launches += 1;
     // gradient: BF16 rows for segments whose last step was accepted, FP32 rows for the others
     tmark(h, xstep ? "bf16_grad_x" : "bf16_grad_y");
-    e = xstep ? dispatch_pass<float, true, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (float *)s.part_grad,
+    e = xstep ? dispatch_pass<float, true, true, __nv_bfloat16>(o, F, Wb, k, h->loss_f, (float *)s.part_grad,
                                                                   s.part_loss, st, acc, 1)
-              : dispatch_pass<float, false, true, __nv_bfloat16>(o, F, Wb, k, h->loss_dev, (float *)s.part_grad,
+              : dispatch_pass<float, false, true, __nv_bfloat16>(o, F, Wb, k, h->loss_f, (float *)s.part_grad,
                                                                    s.part_loss, st, acc, 1);
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "fp32_grad_x" : "fp32_grad_y");
-    e = xstep ? dispatch_pass<float, true, true>(o, F, W, k, h->loss_dev, (float *)s.part_grad, s.part_loss, st, acc, 0)
-              : dispatch_pass<float, false, true>(o, F, W, k, h->loss_dev, (float *)s.part_grad, s.part_loss, st, acc, 0);
+    e = xstep ? dispatch_pass<float, true, true>(o, F, W, k, h->loss_f, (float *)s.part_grad, s.part_loss, st, acc, 0)
+              : dispatch_pass<float, false, true>(o, F, W, k, h->loss_f, (float *)s.part_grad, s.part_loss, st, acc, 0);
     if (e != cudaSuccess) return e;
     h->launches += 2 * (o.nchunks ? 1 : 0);
-    const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
-    prox_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const float *)s.part_grad,
-                                                            s.part_loss, F, alpha, k, rk, rw, (float *)s.cand,
-                                                            s.f_old, s.r_old, s.r_new);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_prox<float>(o.nseg, o.segchunk, (const float *)s.part_grad, s.part_loss, F, alpha, k, rk, rw,
+                           (float *)s.cand, s.f_old, s.r_old, s.r_new, st);
+    if (e != cudaSuccess) return e;
     tmark(h, xstep ? "cand_x" : "cand_y");
     e = xstep ? cand_pass<true>(h, o, F, (const float *)s.cand, W) : cand_pass<false>(h, o, F, (const float *)s.cand, W);
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "decide_x" : "decide_y");
-    decide_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
-        o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F, alpha, k,
-        xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y, acc, s.part_loss);
+    e = launch_decide<float>(o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F,
+                             alpha, k, xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y, acc,
+                             st, s.part_loss);
     tmark(h, nullptr);
     h->launches += 2;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace glrm

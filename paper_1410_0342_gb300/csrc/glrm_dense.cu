@@ -1271,23 +1271,21 @@ cudaError_t dense_half_step(glrm_s *h, bool xstep)
     e = xstep ? launch_dense<true, true>(h, F, (float *)s.part_grad, s.part_loss)
               : launch_dense<false, true>(h, F, (float *)s.part_grad, s.part_loss);
     if (e != cudaSuccess) return e;
-    const unsigned nbs = blocks_for(nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
-    prox_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(nseg, segchunk, (const float *)s.part_grad,
-                                                           s.part_loss, F, alpha, h->k, rk, rw,
-                                                           (float *)s.cand, s.f_old, s.r_old, s.r_new);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_prox<float>(nseg, segchunk, (const float *)s.part_grad, s.part_loss, F, alpha, h->k, rk, rw,
+                           (float *)s.cand, s.f_old, s.r_old, s.r_new, st);
+    if (e != cudaSuccess) return e;
     tmark(h, xstep ? "dense_loss_x" : "dense_loss_y");
     e = xstep ? launch_dense<true, false>(h, (const float *)s.cand, nullptr, s.part_loss2)
               : launch_dense<false, false>(h, (const float *)s.cand, nullptr, s.part_loss2);
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "decide_x" : "decide_y");
-    decide_kernel<float><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
-        nseg, segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F, alpha, h->k,
-        xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y, xstep ? s.acc_x : s.acc_y);
+    e = launch_decide<float>(nseg, segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const float *)s.cand, F,
+                             alpha, h->k, xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y,
+                             xstep ? s.acc_x : s.acc_y, st);
     tmark(h, nullptr);
     h->launches += 2;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, double *out)

@@ -131,6 +131,27 @@ __device__ __forceinline__ T loss_deriv(const LossSpec &s, T u, T a, T &L)
     return loss_deriv_kind<T>(s.kind, u, a, T(s.param), T(s.levels), L);
 }
 
+// A column's loss with its parameters already in FP32.  The FP32 kernels read
+// this form so that no entry converts the FP64 parameter (a conversion that
+// runs on the FP64 pipe, 1/64 of the FP32 rate on this GPU).
+struct __align__(16) LossSpecF {
+    int32_t kind;
+    int32_t levels;
+    float param;
+    float levelsf;
+};
+template <class T> struct LossOfT { using type = LossSpec; };
+template <> struct LossOfT<float> { using type = LossSpecF; };
+// The loss table type the kernels of element type T read.
+template <class T> using LossOf = typename LossOfT<T>::type;
+
+template <class T>
+__device__ __forceinline__ T loss_deriv(const LossSpecF &s, T u, T a, T &L)
+{
+    static_assert(sizeof(T) == sizeof(float), "LossSpecF is read by FP32 kernels");
+    return loss_deriv_kind<T>(s.kind, u, a, s.param, s.levelsf, L);
+}
+
 // argmin_a L(u, a) (Sec. 5.3).  For the ordinal hinge,
 // L(u, a+1) - L(u, a) = (1 + a - u)_+ - (u - a)_+ is <= 0 exactly when
 // u >= a + 1/2, so the minimiser is 1 + #{a in 1..d-1 : u > a + 1/2} with

@@ -122,7 +122,7 @@ template <class T, int K, bool XSTEP, bool VEC, bool GRAD, class WT = T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ order,
             const int32_t *__restrict__ idx, const T *__restrict__ val, const T *__restrict__ F,
-            const WT *__restrict__ W, int k, const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
+            const WT *__restrict__ W, int k, const LossOf<T> *__restrict__ loss, T *__restrict__ part_grad,
             double *__restrict__ part_loss, const int32_t *__restrict__ sel, int want,
             const T *__restrict__ lsc)
 {
@@ -141,47 +141,97 @@ pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__r
 #pragma unroll
     for (int s = 0; s < S; ++s) g[s] = T(0);
     T lsum = T(0);
-    LossSpec sp;
+    LossOf<T> sp;
     T wsc = T(1);
     if constexpr (!XSTEP) {
         sp = loss[ch.x];
         if (lsc) wsc = __ldg(lsc + ch.x);
     }
-    for (int base = ch.y; base < ch.z; base += PER) {
-        const int e = base + grp;
-        const bool ok = e < ch.z;
-        int j = 0;
-        T a = T(0);
-        T w[S];
-        if (ok) {
-            j = __ldg(idx + e);
-            a = __ldg(val + e);
-            load_lane_w<T, S, G, VEC, WT>(w, W + (int64_t)j * k, gl, k);
-        } else {
+    if constexpr (!GRAD) {
+        // loss passes: a software pipeline, the next group of entries' index,
+        // value, loss and gathered row loaded before the current group is
+        // evaluated (two gathers per lane in flight).  The gradient passes
+        // keep one: their gradient registers would cut the occupancy more
+        // than the second gather gains (94 against 73 registers, measured
+        // slower on the k = 64 completion table).
+        int jn = 0;
+        T an = T(0);
+        T wn[S];
+        LossOf<T> spn = sp;
+        T wscn = wsc;
+        auto fetch = [&](int e) {
+            if (e < ch.z) {
+                jn = __ldg(idx + e);
+                an = __ldg(val + e);
+                load_lane_w<T, S, G, VEC, WT>(wn, W + (int64_t)jn * k, gl, k);
+                if constexpr (XSTEP) {
+                    spn = loss[jn];
+                    if (lsc) wscn = __ldg(lsc + jn);
+                }
+            } else {
 #pragma unroll
-            for (int s = 0; s < S; ++s) w[s] = T(0);
-        }
-        T u = T(0);
+                for (int s = 0; s < S; ++s) wn[s] = T(0);
+            }
+        };
+        fetch(ch.y + grp);
+        for (int base = ch.y; base < ch.z; base += PER) {
+            const bool ok = base + grp < ch.z;
+            const T a = an;
+            T w[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) u = fma(f[s], w[s], u);
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) u += shfl_xor(u, o);
-        if (ok) {
+            for (int s = 0; s < S; ++s) w[s] = wn[s];
             if constexpr (XSTEP) {
-                sp = loss[j];
-                if (lsc) wsc = __ldg(lsc + j);
+                sp = spn;
+                wsc = wscn;
             }
-            T L;
-            T d = loss_deriv<T>(sp, u, a, L);
-            if (lsc) {
-                d *= wsc;
-                L *= wsc;
+            fetch(base + PER + grp);
+            T u = T(0);
+#pragma unroll
+            for (int s = 0; s < S; ++s) u = fma(f[s], w[s], u);
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) u += shfl_xor(u, o);
+            if (ok) {
+                T L;
+                loss_deriv<T>(sp, u, a, L);
+                if (lsc) L *= wsc;
+                if (gl == 0) lsum += L;
             }
-            if constexpr (GRAD) {
+        }
+    } else {
+        for (int base = ch.y; base < ch.z; base += PER) {
+            const int e = base + grp;
+            const bool ok = e < ch.z;
+            int j = 0;
+            T a = T(0);
+            T w[S];
+            if (ok) {
+                j = __ldg(idx + e);
+                a = __ldg(val + e);
+                load_lane_w<T, S, G, VEC, WT>(w, W + (int64_t)j * k, gl, k);
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) w[s] = T(0);
+            }
+            T u = T(0);
+#pragma unroll
+            for (int s = 0; s < S; ++s) u = fma(f[s], w[s], u);
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) u += shfl_xor(u, o);
+            if (ok) {
+                if constexpr (XSTEP) {
+                    sp = loss[j];
+                    if (lsc) wsc = __ldg(lsc + j);
+                }
+                T L;
+                T d = loss_deriv<T>(sp, u, a, L);
+                if (lsc) {
+                    d *= wsc;
+                    L *= wsc;
+                }
 #pragma unroll
                 for (int s = 0; s < S; ++s) g[s] = fma(d, w[s], g[s]);
+                if (gl == 0) lsum += L;
             }
-            if (gl == 0) lsum += L;
         }
     }
     if constexpr (GRAD) {
@@ -281,6 +331,138 @@ decide_kernel(int64_t nseg, const int32_t *__restrict__ segchunk,
         kept_reg[s] = acc ? r_new[s] : r_old[s];
         accepted[s] = acc ? 1 : 0;
     }
+}
+
+// The same two steps with LG lanes per segment (32 / LG segments per warp),
+// for half-steps with many segments: a warp per segment leaves most lanes
+// idle at small k and runs as many warps as segments.  Partial gradients are
+// summed per coordinate in slot order as above; the segment's FP64 loss
+// partials in slot order by each lane of the group.
+template <class T, int LG>
+__global__ void __launch_bounds__(256)
+prox_narrow_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const T *__restrict__ part_grad,
+                   const double *__restrict__ part_loss, const T *__restrict__ F, const T *__restrict__ alpha,
+                   int k, int rkind, T rw, T *__restrict__ cand, double *__restrict__ f_old,
+                   double *__restrict__ r_old, double *__restrict__ r_new)
+{
+    const int gl = threadIdx.x % LG;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LG;
+    const bool live = s < nseg;  // whole groups: the shuffles below run on every lane
+    int cb = 0, ce = 0;
+    T al = T(0);
+    if (live) {
+        cb = segchunk[s];
+        ce = segchunk[s + 1];
+        al = alpha[s];
+    }
+    T ro = T(0), rn = T(0);
+    if (live)
+        for (int c = gl; c < k; c += LG) {
+            T g = T(0);
+            for (int q = cb; q < ce; ++q) g += part_grad[(int64_t)q * k + c];
+            const T x = F[s * k + c];
+            const int rkc = reg_kind_at(rkind, c, k);
+            const T xp = prox1<T>(rkc, rw, al, x - al * g);
+            cand[s * k + c] = xp;
+            ro += reg1t<T>(rkc, rw, x);
+            rn += reg1t<T>(rkc, rw, xp);
+        }
+#pragma unroll
+    for (int o = 1; o < LG; o <<= 1) {
+        ro += shfl_xor(ro, o);
+        rn += shfl_xor(rn, o);
+    }
+    if (live && gl == 0) {
+        double ls = 0.0;
+        for (int q = cb; q < ce; ++q) ls += part_loss[q];
+        f_old[s] = ls + ro;
+        r_old[s] = ro;
+        r_new[s] = rn;
+    }
+}
+
+template <class T, int LG>
+__global__ void __launch_bounds__(256)
+decide_narrow_kernel(int64_t nseg, const int32_t *__restrict__ segchunk, const double *__restrict__ part_loss_new,
+                     const double *__restrict__ f_old, const double *__restrict__ r_old,
+                     const double *__restrict__ r_new, const T *__restrict__ cand, T *__restrict__ F,
+                     T *__restrict__ alpha, int k, double *__restrict__ kept_obj, double *__restrict__ kept_reg,
+                     int32_t *__restrict__ accepted, const double *__restrict__ part_loss_old)
+{
+    const int gl = threadIdx.x % LG;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LG;
+    if (s >= nseg) return;  // no shuffles here
+    const int cb = segchunk[s], ce = segchunk[s + 1];
+    double fn = 0.0;
+    for (int q = cb; q < ce; ++q) fn += part_loss_new[q];
+    fn += r_new[s];
+    double fo;
+    if (part_loss_old) {
+        fo = 0.0;
+        for (int q = cb; q < ce; ++q) fo += part_loss_old[q];
+        fo += r_old[s];
+    } else {
+        fo = f_old[s];
+    }
+    const bool acc = fn <= fo;
+    if (acc)
+        for (int c = gl; c < k; c += LG) F[s * k + c] = cand[s * k + c];
+    if (gl == 0) {
+        alpha[s] = alpha[s] * (acc ? T(1.05) : T(0.7));
+        kept_obj[s] = acc ? fn : fo;
+        kept_reg[s] = acc ? r_new[s] : r_old[s];
+        accepted[s] = acc ? 1 : 0;
+    }
+}
+
+inline unsigned blocks_for(int64_t items, int per_block)
+{
+    return (unsigned)((items + per_block - 1) / per_block);
+}
+
+// Segments above which the prox / decide steps run LG lanes per segment.
+constexpr int64_t kNarrowSegments = 32768;
+
+template <class T>
+cudaError_t launch_prox(int64_t nseg, const int32_t *segchunk, const T *part_grad, const double *part_loss,
+                        const T *F, const T *alpha, int k, int rk, T rw, T *cand, double *f_old, double *r_old,
+                        double *r_new, cudaStream_t st)
+{
+    if (nseg >= kNarrowSegments && k <= 64) {
+        if (k <= 16)
+            prox_narrow_kernel<T, 4><<<(unsigned)((nseg * 4 + 255) / 256), 256, 0, st>>>(
+                nseg, segchunk, part_grad, part_loss, F, alpha, k, rk, rw, cand, f_old, r_old, r_new);
+        else
+            prox_narrow_kernel<T, 8><<<(unsigned)((nseg * 8 + 255) / 256), 256, 0, st>>>(
+                nseg, segchunk, part_grad, part_loss, F, alpha, k, rk, rw, cand, f_old, r_old, r_new);
+    } else {
+        prox_kernel<T><<<blocks_for(nseg, kWarpsPerBlock), kWarpsPerBlock * 32, 0, st>>>(
+            nseg, segchunk, part_grad, part_loss, F, alpha, k, rk, rw, cand, f_old, r_old, r_new);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_decide(int64_t nseg, const int32_t *segchunk, const double *part_loss_new, const double *f_old,
+                          const double *r_old, const double *r_new, const T *cand, T *F, T *alpha, int k,
+                          double *kept_obj, double *kept_reg, int32_t *accepted, cudaStream_t st,
+                          const double *part_loss_old = nullptr)
+{
+    if (nseg >= kNarrowSegments && k <= 64) {
+        if (k <= 16)
+            decide_narrow_kernel<T, 4><<<(unsigned)((nseg * 4 + 255) / 256), 256, 0, st>>>(
+                nseg, segchunk, part_loss_new, f_old, r_old, r_new, cand, F, alpha, k, kept_obj, kept_reg, accepted,
+                part_loss_old);
+        else
+            decide_narrow_kernel<T, 8><<<(unsigned)((nseg * 8 + 255) / 256), 256, 0, st>>>(
+                nseg, segchunk, part_loss_new, f_old, r_old, r_new, cand, F, alpha, k, kept_obj, kept_reg, accepted,
+                part_loss_old);
+    } else {
+        decide_kernel<T><<<blocks_for(nseg, kWarpsPerBlock), kWarpsPerBlock * 32, 0, st>>>(
+            nseg, segchunk, part_loss_new, f_old, r_old, r_new, cand, F, alpha, k, kept_obj, kept_reg, accepted,
+            part_loss_old);
+    }
+    return cudaGetLastError();
 }
 
 // Deterministic two-level sums.  Stage 1: block b sums a fixed contiguous
@@ -424,13 +606,9 @@ __global__ void reset_alpha_kernel(const int32_t *__restrict__ ptr, int64_t nseg
 
 // ------------------------------------------------------------------ launchers
 
-inline unsigned blocks_for(int64_t items, int per_block)
-{
-    return (unsigned)((items + per_block - 1) / per_block);
-}
 
 template <class T, int K, bool XSTEP, bool GRAD, class WT>
-cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
+cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const LossOf<T> *loss,
                         T *part_grad, double *part_loss, cudaStream_t st, const int32_t *sel, int want,
                         const T *lsc)
 {
@@ -456,7 +634,7 @@ cudaError_t launch_pass(const Orient &o, const T *F, const WT *W, int k, const L
 
 // Dispatch a runtime k to the smallest padded width K >= k.
 template <class T, bool XSTEP, bool GRAD, class WT = T>
-cudaError_t dispatch_pass(const Orient &o, const T *F, const WT *W, int k, const LossSpec *loss,
+cudaError_t dispatch_pass(const Orient &o, const T *F, const WT *W, int k, const LossOf<T> *loss,
                           T *part_grad, double *part_loss, cudaStream_t st, const int32_t *sel = nullptr,
                           int want = 0, const T *lsc = nullptr)
 {
@@ -494,29 +672,26 @@ cudaError_t Engine<T>::half_step(glrm_s *h, bool xstep)
     }
     tmark(h, xstep ? "pass_grad_x" : "pass_grad_y");
     const T *lsc = (const T *)h->lscale;
-    e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st, nullptr, 0, lsc)
-              : dispatch_pass<T, false, true>(o, F, W, k, h->loss_dev, (T *)s.part_grad, s.part_loss, st, nullptr, 0, lsc);
+    e = xstep ? dispatch_pass<T, true, true>(o, F, W, k, loss_of<T>(h), (T *)s.part_grad, s.part_loss, st, nullptr, 0, lsc)
+              : dispatch_pass<T, false, true>(o, F, W, k, loss_of<T>(h), (T *)s.part_grad, s.part_loss, st, nullptr, 0, lsc);
     if (e != cudaSuccess) return e;
-    const unsigned nbs = blocks_for(o.nseg, kWarpsPerBlock);
     tmark(h, xstep ? "prox_x" : "prox_y");
-    prox_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, st>>>(o.nseg, o.segchunk, (const T *)s.part_grad,
-                                                       s.part_loss, F, alpha, k, rk, rw, (T *)s.cand,
-                                                       s.f_old, s.r_old, s.r_new);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_prox<T>(o.nseg, o.segchunk, (const T *)s.part_grad, s.part_loss, F, alpha, k, rk, rw, (T *)s.cand,
+                       s.f_old, s.r_old, s.r_new, st);
+    if (e != cudaSuccess) return e;
     tmark(h, xstep ? "pass_loss_x" : "pass_loss_y");
-    e = xstep ? dispatch_pass<T, true, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st,
+    e = xstep ? dispatch_pass<T, true, false>(o, (const T *)s.cand, W, k, loss_of<T>(h), nullptr, s.part_loss2, st,
                                               nullptr, 0, lsc)
-              : dispatch_pass<T, false, false>(o, (const T *)s.cand, W, k, h->loss_dev, nullptr, s.part_loss2, st,
+              : dispatch_pass<T, false, false>(o, (const T *)s.cand, W, k, loss_of<T>(h), nullptr, s.part_loss2, st,
                                                nullptr, 0, lsc);
     if (e != cudaSuccess) return e;
     tmark(h, xstep ? "decide_x" : "decide_y");
-    decide_kernel<T><<<nbs, kWarpsPerBlock * 32, 0, st>>>(
-        o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const T *)s.cand, F, alpha, k,
-        xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y,
-        xstep ? s.acc_x : s.acc_y);
+    e = launch_decide<T>(o.nseg, o.segchunk, s.part_loss2, s.f_old, s.r_old, s.r_new, (const T *)s.cand, F, alpha, k,
+                         xstep ? s.kept_obj_x : s.kept_obj_y, xstep ? s.kept_reg_x : s.kept_reg_y,
+                         xstep ? s.acc_x : s.acc_y, st);
     tmark(h, nullptr);
     h->launches += 2 + 2 * pass_launches;
-    return cudaGetLastError();
+    return e;
 }
 
 // Objective after a sweep: the Y-step's kept column objectives hold every
@@ -543,7 +718,7 @@ cudaError_t Engine<T>::objective_at(glrm_s *h, const T *X, const T *Yt, double *
 {
     Scratch &s = h->s;
     tmark(h, "objective_pass");
-    cudaError_t e = dispatch_pass<T, true, false>(h->csr, X, Yt, h->k, h->loss_dev, nullptr,
+    cudaError_t e = dispatch_pass<T, true, false>(h->csr, X, Yt, h->k, loss_of<T>(h), nullptr,
                                                   s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     if (e != cudaSuccess) return e;
     tmark(h, "reduce_stage1");
@@ -578,13 +753,13 @@ cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt
     tmark(h, "grad_pass_x");
     if constexpr (std::is_same<T, float>::value) {
         if (bf16)
-            e = dispatch_pass<T, true, true, __nv_bfloat16>(h->csr, X, s.yt_bf16, h->k, h->loss_dev,
+            e = dispatch_pass<T, true, true, __nv_bfloat16>(h->csr, X, s.yt_bf16, h->k, loss_of<T>(h),
                                                             (T *)s.part_grad, s.part_loss, h->stream);
         else
-            e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev, (T *)s.part_grad,
+            e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, loss_of<T>(h), (T *)s.part_grad,
                                              s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     } else {
-        e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, h->loss_dev, (T *)s.part_grad, s.part_loss,
+        e = dispatch_pass<T, true, true>(h->csr, X, Yt, h->k, loss_of<T>(h), (T *)s.part_grad, s.part_loss,
                                          h->stream, nullptr, 0, (const T *)h->lscale);
     }
     if (e != cudaSuccess) return e;
@@ -595,13 +770,13 @@ cudaError_t Engine<T>::grad_at(glrm_s *h, const T *X, const T *Yt, T *GX, T *GYt
     tmark(h, "grad_pass_y");
     if constexpr (std::is_same<T, float>::value) {
         if (bf16)
-            e = dispatch_pass<T, false, true, __nv_bfloat16>(h->csc, Yt, s.x_bf16, h->k, h->loss_dev,
+            e = dispatch_pass<T, false, true, __nv_bfloat16>(h->csc, Yt, s.x_bf16, h->k, loss_of<T>(h),
                                                              (T *)s.part_grad, s.part_loss, h->stream);
         else
-            e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
+            e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, loss_of<T>(h), (T *)s.part_grad,
                                               s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     } else {
-        e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, h->loss_dev, (T *)s.part_grad,
+        e = dispatch_pass<T, false, true>(h->csc, Yt, X, h->k, loss_of<T>(h), (T *)s.part_grad,
                                           s.part_loss, h->stream, nullptr, 0, (const T *)h->lscale);
     }
     if (e != cudaSuccess) return e;

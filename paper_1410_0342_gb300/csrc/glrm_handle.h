@@ -162,6 +162,7 @@ struct glrm_s {
     cudaStream_t stream = nullptr;
     std::vector<glrm::LossSpec> loss_host;
     glrm::LossSpec *loss_dev = nullptr;
+    glrm::LossSpecF *loss_f = nullptr;  // the same losses with FP32 parameters (FP32 kernels)
     int rx_kind = 0, ry_kind = 0;
     bool offset = false;  // last coordinate of X held at 1, of Y unpenalised (glrm_set_offset)
     void *lscale = nullptr;  // n per-column loss weights, element type (glrm_set_column_scale); null: all 1
@@ -194,6 +195,11 @@ struct glrm_s {
 namespace glrm {
 
 size_t elem_size(int prec);
+
+// The loss table the kernels of element type T read.
+template <class T> inline const LossOf<T> *loss_of(const glrm_s *h);
+template <> inline const LossSpec *loss_of<double>(const glrm_s *h) { return h->loss_dev; }
+template <> inline const LossSpecF *loss_of<float>(const glrm_s *h) { return h->loss_f; }
 
 // The regulariser kind the kernels of one half-step take: the model's kind
 // with the offset role of that factor above it (see reg_kind_at).

@@ -195,13 +195,13 @@ struct Ring {
 };
 
 // Loss and derivative with the kind fixed at compile time when KIND >= 0.
-template <class T, int KIND>
-__device__ __forceinline__ T loss_k(const LossSpec &s, T u, T a, T &L)
+template <class T, int KIND, class LS>
+__device__ __forceinline__ T loss_k(const LS &s, T u, T a, T &L)
 {
     if constexpr (KIND < 0) {
         return loss_deriv<T>(s, u, a, L);
     } else {
-        LossSpec q = s;
+        LS q = s;
         q.kind = KIND;
         return loss_deriv<T>(q, u, a, L);
     }
@@ -213,8 +213,8 @@ __device__ __forceinline__ T loss_k(const LossSpec &s, T u, T a, T &L)
 // q of the batch buffer.
 template <class T, int K, bool XSTEP, bool GRAD, int KIND, bool FULL>
 __device__ __forceinline__ void mt_batch2(int cnt, int myj, uint32_t mym, uint32_t &voff,
-                                          const Ring<T> &rg, const T *rows, const LossSpec *Ls,
-                                          const LossSpec &segspec, const Vec<T, K> &f, Vec<T, K> &g,
+                                          const Ring<T> &rg, const T *rows, const LossOf<T> *Ls,
+                                          const LossOf<T> &segspec, const Vec<T, K> &f, Vec<T, K> &g,
                                           T &lsum)
 {
     const int lane = threadIdx.x & 31;
@@ -273,7 +273,7 @@ __device__ __forceinline__ T mt_pass2(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K>
                                       int64_t vstart, int64_t vend, const int32_t *__restrict__ tidx,
                                       const uint32_t *__restrict__ tmask, const T *__restrict__ tval,
                                       const T *Ws, const T *__restrict__ W, T *gbuf,
-                                      const LossSpec *__restrict__ Lsrc, const LossSpec &segspec)
+                                      const LossOf<T> *__restrict__ Lsrc, const LossOf<T> &segspec)
 {
     const int lane = threadIdx.x & 31;
     T lsum = T(0);
@@ -312,7 +312,7 @@ __device__ __forceinline__ T mt_pass2(Ring<T> &rg, const Vec<T, K> &f, Vec<T, K>
         const uint32_t total = __reduce_add_sync(0xffffffffu, (unsigned)__popc(mym));
         rg.ensure(voff + total);
         int kind = segkind;
-        const LossSpec *Ls = Lsrc;
+        const LossOf<T> *Ls = Lsrc;
         if constexpr (XSTEP) {
             const int j0 = __shfl_sync(0xffffffffu, myj, 0);
             const int kj = Lsrc[lane < cnt ? myj : j0].kind;
@@ -363,7 +363,7 @@ mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile
           const int32_t *__restrict__ ubeg, const int32_t *__restrict__ segptr,
           const int32_t *__restrict__ tidx, const uint32_t *__restrict__ tmask,
           const T *__restrict__ tval, T *__restrict__ F, const T *__restrict__ W, int64_t nother,
-          int k, T *__restrict__ alpha, const LossSpec *__restrict__ loss, int rk, T rw,
+          int k, T *__restrict__ alpha, const LossOf<T> *__restrict__ loss, int rk, T rw,
           double *__restrict__ kept_obj, double *__restrict__ kept_reg,
           int32_t *__restrict__ accepted, T *__restrict__ part_grad, double *__restrict__ part_loss,
           int *__restrict__ err)
@@ -374,12 +374,12 @@ mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     size_t off = 0;
     T *Ws = reinterpret_cast<T *>(dsm);
-    LossSpec *Ls = nullptr;
+    LossOf<T> *Ls = nullptr;
     if constexpr (FULL) {
         off = align16((size_t)nother * K * sizeof(T));
         if constexpr (XSTEP) {
-            Ls = reinterpret_cast<LossSpec *>(dsm + off);
-            off += (size_t)nother * sizeof(LossSpec);
+            Ls = reinterpret_cast<LossOf<T> *>(dsm + off);
+            off += (size_t)nother * sizeof(LossOf<T>);
         }
     }
     constexpr size_t kWarpBytes = (size_t)kRingSlots * kRingBytes + (FULL ? 0 : 2 * 32 * K * sizeof(T));
@@ -395,7 +395,7 @@ mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile
         }
         if (!stage_panel<T>(Ws, W, 0, (int)nother, k, K, &bar_panel, 0, err)) return;
     }
-    const LossSpec *Lsrc = FULL ? Ls : loss;
+    const LossOf<T> *Lsrc = FULL ? Ls : loss;
     Ring<T> vs;
     vs.init(ring, &bar_ring[wid][0]);
     for (int64_t u = (int64_t)blockIdx.x * nwarps + wid; u < nunits; u += (int64_t)gridDim.x * nwarps) {
@@ -412,7 +412,7 @@ mt_kernel(int64_t nseg, int64_t nunits, int P, const int32_t *__restrict__ utile
         if (live) f.load_masked(F + s * k, k);
         else f.zero();
         g.zero();
-        LossSpec sp{};
+        LossOf<T> sp{};
         if constexpr (!XSTEP) {
             if (live) sp = loss[s];
         }
@@ -563,7 +563,7 @@ cudaError_t launch_mt(glrm_s *h, const Orient &o, T *F, const T *W, int64_t noth
     if (e != cudaSuccess) return e;
     kern<<<o.grid, o.warps * 32, o.smem_bytes, h->stream>>>(
         o.nseg, o.nunits, o.P, o.utile, o.tptr, o.uvoff, o.ubeg, o.ptr, o.tidx, o.tmask,
-        (const T *)o.tval, F, W, nother, h->k, alpha, h->loss_dev, rk, rw, kobj, kreg, acc, pg, pl,
+        (const T *)o.tval, F, W, nother, h->k, alpha, loss_of<T>(h), rk, rw, kobj, kreg, acc, pg, pl,
         h->s.err);
     return cudaGetLastError();
 }

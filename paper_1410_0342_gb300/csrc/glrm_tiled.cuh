@@ -351,12 +351,12 @@ struct EntryStream {
 template <class T, int K, bool XSTEP, bool GRAD, bool SM>
 __device__ __forceinline__ T seg_pass(const Vec<T, K> &f, Vec<T, K> &g, int b, int e, int jbase,
                                       const int32_t *__restrict__ ip, const T *__restrict__ vp,
-                                      const T *__restrict__ Ws, const LossSpec *__restrict__ Ls,
-                                      const LossSpec &segspec)
+                                      const T *__restrict__ Ws, const LossOf<T> *__restrict__ Ls,
+                                      const LossOf<T> &segspec)
 {
     const int lane = threadIdx.x & 31;
     T lsum = T(0);
-    LossSpec sp = segspec;
+    LossOf<T> sp = segspec;
     for (int q = b + lane; q < e; q += 32) {
         int j;
         T a;
@@ -384,7 +384,7 @@ template <class T, int K, bool XSTEP, bool GRAD>
 __device__ __forceinline__ T seg_pass_any(const EntryStream<T> &st, int q, const Vec<T, K> &f,
                                           Vec<T, K> &g, int b, int e, int jbase,
                                           const int32_t *__restrict__ idx, const T *__restrict__ val,
-                                          const T *Ws, const LossSpec *Ls, const LossSpec &segspec)
+                                          const T *Ws, const LossOf<T> *Ls, const LossOf<T> &segspec)
 {
     if (st.staged(q))
         return seg_pass<T, K, XSTEP, GRAD, true>(f, g, b, e, jbase, st.ibase(q), st.vbase(q), Ws,
@@ -409,7 +409,7 @@ template <class T, int K, bool XSTEP>
 __global__ void __launch_bounds__(kStreamWarps * 32, 1)
 fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                   const T *__restrict__ val, T *__restrict__ F, const T *__restrict__ W,
-                  int64_t nother, int k, T *__restrict__ alpha, const LossSpec *__restrict__ loss,
+                  int64_t nother, int k, T *__restrict__ alpha, const LossOf<T> *__restrict__ loss,
                   int rk, T rw, double *__restrict__ kept_obj, double *__restrict__ kept_reg,
                   int32_t *__restrict__ accepted, int *__restrict__ err, int cap)
 {
@@ -419,8 +419,8 @@ fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T *Ws = reinterpret_cast<T *>(dsm);
     size_t off = align16((size_t)nother * K * sizeof(T));
-    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
-    if constexpr (XSTEP) off += (size_t)nother * sizeof(LossSpec);
+    LossOf<T> *Ls = reinterpret_cast<LossOf<T> *>(dsm + off);
+    if constexpr (XSTEP) off += (size_t)nother * sizeof(LossOf<T>);
     EntryStream<T> st;
     st.init(dsm + off + (size_t)wid * stream_bytes<T>(cap), &bar_seg[wid][0], cap);
     if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
@@ -450,7 +450,7 @@ fused_half_kernel(int64_t nseg, const int32_t *__restrict__ ptr, const int32_t *
         Vec<T, K> f, g;
         f.load_masked(F + s * k, k);
         g.zero();
-        LossSpec sp;
+        LossOf<T> sp;
         if constexpr (!XSTEP) sp = loss[s];
         // pass 1: gradient and loss at the current factor
         const T lsum = seg_pass_any<T, K, XSTEP, true>(st, cur, f, g, b, e, 0, idx, val, Ws, Ls, sp);
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 1)
 blocked_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
                     const int32_t *__restrict__ runptr, const int32_t *__restrict__ idx,
                     const T *__restrict__ val, const T *__restrict__ F, const T *__restrict__ W,
-                    int k, const LossSpec *__restrict__ loss, T *__restrict__ part_grad,
+                    int k, const LossOf<T> *__restrict__ loss, T *__restrict__ part_grad,
                     double *__restrict__ part_loss, int *__restrict__ err, int cap)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -532,8 +532,8 @@ blocked_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T *Ws = reinterpret_cast<T *>(dsm);
     size_t off = align16((size_t)R * K * sizeof(T));
-    LossSpec *Ls = reinterpret_cast<LossSpec *>(dsm + off);
-    if constexpr (XSTEP) off += (size_t)R * sizeof(LossSpec);
+    LossOf<T> *Ls = reinterpret_cast<LossOf<T> *>(dsm + off);
+    if constexpr (XSTEP) off += (size_t)R * sizeof(LossOf<T>);
     EntryStream<T> st;
     st.init(dsm + off + (size_t)wid * stream_bytes<T>(cap), &bar_seg[wid][0], cap);
     if (threadIdx.x == 0) mbar_init(&bar_panel, 1);
@@ -581,7 +581,7 @@ blocked_pass_kernel(int64_t nseg, int nb, int R, int ngroups, int64_t nother,
             Vec<T, K> f, g;
             f.load_masked(F + s * k, k);
             g.zero();
-            LossSpec sp;
+            LossOf<T> sp;
             if constexpr (!XSTEP) sp = loss[s];
             const T lsum = seg_pass_any<T, K, XSTEP, GRAD>(st, cur, f, g, qb, qe, (int)r0, idx, val,
                                                           Ws, Ls, sp);
@@ -683,7 +683,7 @@ cudaError_t launch_fused(glrm_s *h, const Orient &o, T *F, const T *W, int64_t n
                                          (int)o.smem_bytes);
     if (e != cudaSuccess) return e;
     kern<<<o.grid, kStreamWarps * 32, o.smem_bytes, h->stream>>>(
-        o.nseg, o.ptr, o.idx, (const T *)o.val, F, W, nother, h->k, alpha, h->loss_dev, rk, rw,
+        o.nseg, o.ptr, o.idx, (const T *)o.val, F, W, nother, h->k, alpha, loss_of<T>(h), rk, rw,
         kept_obj, kept_reg, acc, h->s.err, o.cap);
     return cudaGetLastError();
 }
@@ -698,7 +698,7 @@ cudaError_t launch_blocked_pass(glrm_s *h, const Orient &o, const T *F, const T 
     if (e != cudaSuccess) return e;
     kern<<<o.grid, kStreamWarps * 32, o.smem_bytes, h->stream>>>(
         o.nseg, o.nb, o.R, o.ngroups, nother, o.runptr, o.idx, (const T *)o.val, F, W, h->k,
-        h->loss_dev, part_grad, part_loss, h->s.err, o.cap);
+        loss_of<T>(h), part_grad, part_loss, h->s.err, o.cap);
     return cudaGetLastError();
 }
 
