@@ -48,20 +48,30 @@ cand_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
     float lo = 0.f, ln = 0.f;
     LossSpecF sp;
     if constexpr (!XSTEP) sp = loss[ch.x];
-    for (int base = ch.y; base < ch.z; base += PER) {
-        const int e = base + grp;
-        const bool ok = e < ch.z;
-        int j = 0;
-        float a = 0.f;
-        float w[S];
-        if (ok) {
-            j = __ldg(idx + e);
-            a = __ldg(val + e);
-            load_lane<float, S, G, VW, VEC>(w, W + (int64_t)j * k, gl, k);
+    // software pipeline as in the loss passes: the next group's index,
+    // value, loss and row are loaded before the current group is evaluated
+    float an = 0.f, wn[S];
+    LossSpecF spn = sp;
+    auto fetch = [&](int e) {
+        if (e < ch.z) {
+            const int jn = __ldg(idx + e);
+            an = __ldg(val + e);
+            load_lane<float, S, G, VW, VEC>(wn, W + (int64_t)jn * k, gl, k);
+            if constexpr (XSTEP) spn = loss[jn];
         } else {
 #pragma unroll
-            for (int s = 0; s < S; ++s) w[s] = 0.f;
+            for (int s = 0; s < S; ++s) wn[s] = 0.f;
         }
+    };
+    fetch(ch.y + grp);
+    for (int base = ch.y; base < ch.z; base += PER) {
+        const bool ok = base + grp < ch.z;
+        const float a = an;
+        float w[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) w[s] = wn[s];
+        if constexpr (XSTEP) sp = spn;
+        fetch(base + PER + grp);
         float u0 = 0.f, u1 = 0.f;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -74,7 +84,6 @@ cand_pass_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t
             u1 += shfl_xor(u1, o);
         }
         if (ok && gl == 0) {
-            if constexpr (XSTEP) sp = loss[j];
             float L0, L1;
             loss_deriv<float>(sp, u0, a, L0);
             loss_deriv<float>(sp, u1, a, L1);
