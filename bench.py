@@ -66,10 +66,10 @@ def parse():
     ap.add_argument("--count", type=int, default=4096, help="instances of the batched form")
     ap.add_argument("--no-autotune", action="store_true", help="batched form: default work items")
     ap.add_argument("--form", default="sweep",
-                    choices=["sweep", "batched", "autograd", "completion", "dense"],
+                    choices=["sweep", "batched", "autograd", "completion", "dense", "features"],
                     help="sweep: the benchmark line; the others measure the batched, differentiable, "
-                         "matrix-completion and dense (fully observed, tensor-core) forms on their own "
-                         "workloads")
+                         "matrix-completion, dense (fully observed, tensor-core) and feature-table "
+                         "(categorical / ordinal embeddings) forms on their own workloads")
     return ap.parse_args()
 
 
@@ -501,6 +501,19 @@ def run_glrm(args, world, rank, local):
             G.glrm_set_factors_host(ge.h, hX.numpy(), hY.numpy())
             G._check(G._lib.glrm_sweep(ge.h, 1, G._ptr(out)), ge.h)
 
+        # the host link this box gives: the same bytes copied by plain
+        # asynchronous copies from the pinned buffers (context for e2e, which
+        # varies with it between hosts)
+        dbufs = [torch.empty_like(x, device=dev) for x in hb + [hX, hY]]
+        link = []
+        for _ in range(3):
+            torch.cuda.synchronize(dev)
+            c0 = time.perf_counter()
+            for d_, h_ in zip(dbufs, hb + [hX, hY]):
+                d_.copy_(h_, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            link.append(h2d / (time.perf_counter() - c0) / 1e9)
+        del dbufs
         for _ in range(max(3, args.warmup)):  # the pool reaches its steady size
             e2e_step()
         torch.cuda.synchronize(dev)
@@ -513,7 +526,7 @@ def run_glrm(args, world, rank, local):
         dt = max_over_ranks(dt, world, dev)
         e2e = {"value": world * t.nnz * args.e2e_steps / dt, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8,
-               "steps": args.e2e_steps,
+               "steps": args.e2e_steps, "h2d_link_gbs": float(np.median(link)),
                "includes": "set_observed_host (H2D copy + device validation + chunk tables + the "
                            "chosen path's layout), set_factors_host, one sweep, objective D2H"}
         ge.close()
@@ -708,6 +721,41 @@ def run_form(args):
                          "frac": ach / hbm if hbm else None, "peak_source": source,
                          "tensor_tflops": flops_pass / (per[top] / 1e3) / 1e12,
                          "tensor_frac_of_bf16": (flops_pass / (per[top] / 1e3) / 1e12) / tc if tc else None}})
+        g.close()
+    elif args.form == "features":
+        # a census-like table of features (Sec. 6): real, Boolean, categorical
+        # (6 labels) and ordinal (7 levels) features, embedded on the device
+        m = args.form_rows or 100_000
+        t0 = time.time()
+        t = W.features_mixed(m=m, n_real=300, n_bool=200, n_cat=150, n_ord=100, classes=6, levels=7, k=20,
+                             p_obs=0.6, cyclic=False, rx=(W.REG_QUAD, 0.1), ry=(W.REG_QUAD, 0.1))
+        gen_s = time.time() - t0
+        torch.cuda.synchronize(dev)
+        c0 = time.perf_counter()
+        g = G.GLRM.from_feature_table(t, stream=st)
+        torch.cuda.synchronize(dev)
+        setup_ms = (time.perf_counter() - c0) * 1e3
+        paths = G.glrm_get_path(g.h)
+        g.sweep(args.warmup, history=False)
+        ms = _events(torch, st, lambda: g.sweep(args.steps, history=False))
+        hist = g.sweep(1)
+        rng = np.random.default_rng(7)
+        cnt = 1_000_000
+        rows = torch.as_tensor(rng.integers(0, t.m, cnt).astype(np.int32), device=dev)
+        feats = torch.as_tensor(rng.integers(0, t.nf, cnt).astype(np.int32), device=dev)
+        g.decode_features(rows, feats)
+        ms_dec = _events(torch, st, lambda: g.decode_features(rows, feats))
+        D = int(t.widths().sum())
+        ennz = int(np.sum(t.widths()[t.featidx]))
+        line.update({
+            "metric": "observed feature entries/s per alternating prox-grad sweep", "unit": UNIT,
+            "value": t.nnz * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+            "embedded_entries_per_s": ennz * args.steps / (ms / 1e3),
+            "objective_after": float(hist[-1]), "paths": paths,
+            "setup_ms": setup_ms, "decode_1e6_ms": ms_dec,
+            "config": {"workload": f"feature table m={t.m}: 300 Huber, 200 hinge, 150 categorical (6 labels), "
+                                   "100 ordinal (7 levels) features, 60% observed, k=20, gamma=0.1, FP32",
+                       "nnz": t.nnz, "embedded_columns": D, "embedded_nnz": ennz, "generate_s": gen_s}})
         g.close()
     else:
         t = W.completion(m=args.form_rows) if args.form_rows else W.completion()

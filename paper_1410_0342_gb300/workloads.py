@@ -503,8 +503,12 @@ def features_mixed(m=2000, n_real=6, n_bool=4, n_cat=5, n_ord=5, classes=4, leve
     lkind = np.zeros(nf, np.int32)
     lparam = np.zeros(nf)
     llev = np.zeros(nf, np.int32)
+    # the entries of each feature in ascending order (the same set and order
+    # as a boolean mask, without a pass over all entries per feature)
+    by_feat = np.argsort(featidx, kind="stable")
+    starts = np.concatenate([[0], np.cumsum(np.bincount(featidx, minlength=nf))])
     for j, kd in enumerate(kinds):
-        sel = featidx == j
+        sel = by_feat[starts[j]:starts[j + 1]]
         r = rows[sel]
         if kd == 0:
             u = X0[r] @ rng.standard_normal(k)
