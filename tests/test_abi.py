@@ -79,3 +79,56 @@ def test_null_handle_calls_fail_cleanly(lib):
     lib.glrm_objective.restype = ctypes.c_int
     assert lib.glrm_objective(None, None) == -1
     lib.glrm_destroy(None)
+
+
+def test_null_handle_calls_of_the_method_pieces(lib):
+    """Every handle entry point of the method pieces around the sweep rejects
+    a null handle on the host (GLRM_ERR_ARG) without touching a GPU."""
+    p = ctypes.c_void_p
+    calls = [
+        ("glrm_set_offset", [p, ctypes.c_int32], (None, 1)),
+        ("glrm_column_stats", [p, p, p], (None, None, None)),
+        ("glrm_set_column_scale", [p, p], (None, None)),
+        ("glrm_set_reg_weights", [p, ctypes.c_double, ctypes.c_double], (None, 0.1, 0.1)),
+        ("glrm_certificate", [p, ctypes.c_int32, ctypes.c_double, p, p], (None, 10, 1e-9, None, None)),
+        ("glrm_regularization_path", [p, ctypes.c_int32, p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, p, p,
+                                      p, ctypes.c_int32], (None, 1, None, 1, 1e-6, 1, None, None, None, 0)),
+        ("glrm_svd_init", [p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, p], (None, 8, 4, 1, None)),
+        ("glrm_decode_features", [p, ctypes.c_int32, p, ctypes.c_int64, p, p, p], (None, 1, None, 0, None, None, None)),
+        ("glrm_proxprox_sweep", [p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, p], (None, 1, 1.0, 1, None)),
+    ]
+    for name, argtypes, args in calls:
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        f.argtypes = argtypes
+        assert f(*args) == -1, name
+
+
+class _Feature(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32)]
+
+
+class _Loss(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32), ("param", ctypes.c_double)]
+
+
+def test_embed_losses_on_the_host(lib):
+    """Block widths (scalar 1, categorical d, ordinal d - 1), the scalar
+    features' losses kept, the hinge loss on every block column; bad
+    descriptors rejected."""
+    f = lib.glrm_embed_losses
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    feats = (_Feature * 4)(_Feature(0, 0), _Feature(1, 3), _Feature(2, 4), _Feature(0, 0))
+    sl = (_Loss * 4)(_Loss(1, 0, 0.5), _Loss(0, 0, 0.0), _Loss(0, 0, 0.0), _Loss(6, 0, 0.3))
+    D = ctypes.c_int64()
+    assert f(4, ctypes.cast(feats, ctypes.c_void_p), ctypes.cast(sl, ctypes.c_void_p), None, ctypes.byref(D)) == 0
+    assert D.value == 1 + 3 + 3 + 1
+    out = (_Loss * D.value)()
+    assert f(4, ctypes.cast(feats, ctypes.c_void_p), ctypes.cast(sl, ctypes.c_void_p),
+             ctypes.cast(out, ctypes.c_void_p), None) == 0
+    assert [o.kind for o in out] == [1, 2, 2, 2, 2, 2, 2, 6]
+    assert out[0].param == 0.5 and out[7].param == 0.3
+    for bad in ((1, 1), (2, 1), (3, 4), (1, 70000)):
+        fb = (_Feature * 1)(_Feature(*bad))
+        assert f(1, ctypes.cast(fb, ctypes.c_void_p), ctypes.cast(sl, ctypes.c_void_p), None, ctypes.byref(D)) == -1
