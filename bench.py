@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--count", type=int, default=4096, help="instances of the batched form")
     ap.add_argument("--no-autotune", action="store_true", help="batched form: default work items")
     ap.add_argument("--form", default="sweep",
-                    choices=["sweep", "batched", "autograd", "completion", "dense", "features"],
+                    choices=["sweep", "batched", "autograd", "completion", "dense", "features", "pieces"],
                     help="sweep: the benchmark line; the others measure the batched, differentiable, "
                          "matrix-completion, dense (fully observed, tensor-core) and feature-table "
                          "(categorical / ordinal embeddings) forms on their own workloads")
@@ -722,6 +722,51 @@ def run_form(args):
                          "tensor_tflops": flops_pass / (per[top] / 1e3) / 1e12,
                          "tensor_frac_of_bf16": (flops_pass / (per[top] / 1e3) / 1e12) / tc if tc else None}})
         g.close()
+    elif args.form == "pieces":
+        # the method pieces around the sweep, timed on the benchmark's mixed
+        # table (and on quadratic-regularised / quadratic-loss variants of it
+        # where the piece needs one)
+        t = W.mixed(m=args.rows)
+        g = G.GLRM.from_table(t, stream=st)
+        G.glrm_set_path(g.h, 1, 1)  # the sparse observed set (the pieces read CSR / CSC)
+        res = {}
+        mu = torch.empty(t.n, dtype=torch.float64, device=dev)
+        s2 = torch.empty_like(mu)
+        G.glrm_column_stats(g.h, mu, s2)
+        res["column_stats_ms"] = _events(torch, st, lambda: G.glrm_column_stats(g.h, mu, s2))
+        g.set_offset(True)
+        g.svd_init(power_iters=4, offset=True)
+        res["svd_init_ms"] = _events(torch, st, lambda: g.svd_init(power_iters=4, offset=True))
+        g.set_offset(False)
+        g.close()
+        tq = W.Table(t.name, t.m, t.n, t.k, t.rowptr, t.colidx, t.val, t.colptr, t.rowidx, t.cval, t.loss_kind,
+                     t.loss_param, t.loss_levels, (W.REG_QUAD, 0.1), (W.REG_QUAD, 0.1), t.X0, t.Yt0)
+        g = G.GLRM.from_table(tq, stream=st)
+        G.glrm_set_path(g.h, 1, 1)
+        g.sweep(5, history=False)
+        torch.cuda.synchronize(dev)
+        c0 = time.perf_counter()
+        val, its = g.certificate(max_iters=50, tol=0.0)
+        res["certificate_50_iterations_ms"] = (time.perf_counter() - c0) * 1e3
+        res["certificate_value_after_5_sweeps"] = val
+        c0 = time.perf_counter()
+        obj, sw, _ = g.regularization_path([1.0, 0.3, 0.1], max_sweeps=20, rtol=1e-4, window=5)
+        res["regularization_path_3_weights_ms"] = (time.perf_counter() - c0) * 1e3
+        res["regularization_path_sweeps"] = sw.tolist()
+        g.close()
+        tc = W.completion(m=100_000, k=32)
+        gq = G.GLRM.from_table(tc, stream=st)
+        gq.proxprox_sweep(1, 1.0, 3, history=False)
+        res["proxprox_sweep_completion_100k_ms"] = _events(torch, st,
+                                                           lambda: gq.proxprox_sweep(3, 1.0, 3, history=False)) / 3
+        gq.als_sweep(1, history=False)
+        res["als_sweep_completion_100k_ms"] = _events(torch, st, lambda: gq.als_sweep(3, history=False)) / 3
+        gq.close()
+        line.update({"metric": "milliseconds per call", "unit": "ms", "higher_is_better": False,
+                     "config": {"workload": f"mixed table m={t.m} n=1000 k=20 (quadratic-regularised copy for "
+                                            "the certificate and the path); completion m=100000 n=20000 k=32 "
+                                            "(2e7 entries) for prox-prox and ALS", "nnz": t.nnz},
+                     "results": res})
     elif args.form == "features":
         # a census-like table of features (Sec. 6): real, Boolean, categorical
         # (6 labels) and ordinal (7 levels) features, embedded on the device

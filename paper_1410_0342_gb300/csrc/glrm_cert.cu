@@ -24,6 +24,8 @@ namespace {
 constexpr int kCertBlocks = 304;  // partial sums of the reductions (2 x 152 SMs)
 constexpr int kJacobiSweeps = 60;
 constexpr int kSvdMaxL = 96;  // columns of the randomized range finder (k + oversampling)
+// Segments averaging this many entries or more take the chunked products.
+constexpr int64_t kLongSegment = 2048;
 
 // g[e] = w_j L_j'(u, a) with u = x_i . y_j accumulated in FP64 in coordinate
 // order, one warp per segment; the same value in both orders.
@@ -112,6 +114,43 @@ __global__ void cert_apply_kernel(int64_t nseg, const int32_t *__restrict__ ptr,
         lr += __shfl_xor_sync(0xffffffffu, lr, o);
     }
     if (lane == 0) out[s] = scale * acc + lr;
+}
+
+// The same two products over the chunk table of an orientation (chunks of at
+// most 1024 entries), for long segments: one warp per chunk writes a
+// partial, one warp per segment adds its chunks' partials in chunk order.
+__global__ void chunk_apply_kernel(int64_t nchunks, const int4 *__restrict__ chunks, const int32_t *__restrict__ idx,
+                                   const double *__restrict__ g, const double *__restrict__ x,
+                                   double *__restrict__ part)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= nchunks) return;
+    const int4 ch = chunks[c];
+    double acc = 0.0;
+    for (int e = ch.y + lane; e < ch.z; e += 32) acc += g[e] * x[idx[e]];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[c] = acc;
+}
+
+template <class T>
+__global__ void seg_apply_sum_kernel(int64_t nseg, const int32_t *__restrict__ segchunk,
+                                     const double *__restrict__ part, double scale, const T *__restrict__ F, int k,
+                                     const double *__restrict__ kv, double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nseg) return;
+    double lr = 0.0;
+    for (int c = lane; c < k; c += 32) lr += (double)F[s * k + c] * kv[c];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) lr += __shfl_xor_sync(0xffffffffu, lr, o);
+    if (lane == 0) {
+        double acc = 0.0;
+        for (int c = segchunk[s]; c < segchunk[s + 1]; ++c) acc += part[c];
+        out[s] = scale * acc + lr;
+    }
 }
 
 // Partial sums of squares.
@@ -368,6 +407,8 @@ cudaError_t certificate_impl(glrm_s *h, int iters, double tol, double *norm, int
     A(&part, part_len * sizeof(double));
     A(&small, small_len * sizeof(double));
     A(&rank, sizeof(int));
+    double *cpart = nullptr;  // chunk partials of the long-segment products
+    A(&cpart, (size_t)std::max(h->csr.nchunks, h->csc.nchunks) * sizeof(double));
     // small: Ga | Gb | K | t | Kt | scratch (6 k^2 + 2k + 4) | sq
     double *Ga = small, *Gb = Ga + npair, *K = Gb + npair, *t = K + k * k, *kt = t + k, *core = kt + k;
     double *sq = core + 6 * k * k + 2 * k + 4;
@@ -389,6 +430,16 @@ cudaError_t certificate_impl(glrm_s *h, int iters, double tol, double *norm, int
         h->launches += 11;
         e = cudaGetLastError();
     }
+    // out = scale * G_orient x + F (K-vector kt) over one orientation
+    auto apply = [&](const Orient &o, int64_t nseg, const double *g, const double *x, const T *F, double *out) {
+        if (o.nchunks > 0 && nnz >= kLongSegment * nseg) {
+            chunk_apply_kernel<<<nblk(o.nchunks, 8), 256, 0, st>>>(o.nchunks, o.chunks, o.idx, g, x, cpart);
+            seg_apply_sum_kernel<T><<<nblk(nseg, 8), 256, 0, st>>>(nseg, o.segchunk, cpart, scale, F, k, kt, out);
+            h->launches += 1;
+        } else {
+            cert_apply_kernel<T><<<nblk(nseg, 8), 256, 0, st>>>(nseg, o.ptr, o.idx, g, x, scale, F, k, kt, out);
+        }
+    };
     double est = 0.0, prev = -1.0;
     int it = 0;
     for (; e == cudaSuccess && it < iters; ++it) {
@@ -396,12 +447,12 @@ cudaError_t certificate_impl(glrm_s *h, int iters, double tol, double *norm, int
         cert_kvec_kernel<T><<<kCertBlocks, 64, 0, st>>>(n, Yt, k, v, part);
         cert_sum_kernel<<<1, 64, 0, st>>>(part, kCertBlocks, k, t);
         cert_kmat_kernel<<<1, 64, 0, st>>>(K, k, false, t, kt);
-        cert_apply_kernel<T><<<nblk(m, 8), 256, 0, st>>>(m, h->csr.ptr, h->csr.idx, gr, v, scale, X, k, kt, w);
+        apply(h->csr, m, gr, v, X, w);
         // v = M^T w
         cert_kvec_kernel<T><<<kCertBlocks, 64, 0, st>>>(m, X, k, w, part);
         cert_sum_kernel<<<1, 64, 0, st>>>(part, kCertBlocks, k, t);
         cert_kmat_kernel<<<1, 64, 0, st>>>(K, k, true, t, kt);
-        cert_apply_kernel<T><<<nblk(n, 8), 256, 0, st>>>(n, h->csc.ptr, h->csc.idx, gc, w, scale, Yt, k, kt, v);
+        apply(h->csc, n, gc, w, Yt, v);
         // ||M^T M v|| with ||v|| = 1 is the estimate of sigma^2; normalise v
         cert_sq_kernel<<<kCertBlocks, 256, 0, st>>>(n, v, part);
         cert_sum_kernel<<<1, 32, 0, st>>>(part, kCertBlocks, 1, sq);
@@ -419,7 +470,8 @@ cudaError_t certificate_impl(glrm_s *h, int iters, double tol, double *norm, int
         }
         prev = est;
     }
-    for (void *p : {(void *)gr, (void *)gc, (void *)v, (void *)w, (void *)part, (void *)small, (void *)rank})
+    for (void *p : {(void *)gr, (void *)gc, (void *)v, (void *)w, (void *)part, (void *)small, (void *)rank,
+                    (void *)cpart})
         if (p) cudaFreeAsync(p, st);
     *norm = est;
     *done = it;
@@ -476,6 +528,48 @@ __global__ void svd_spmm_kernel(int64_t nseg, const int32_t *__restrict__ ptr, c
     for (int q = 0; q < kSvdMaxL / 32; ++q) {
         const int c = q * 32 + lane;
         if (c < l) out[s * l + c] = acc[q];
+    }
+}
+
+// out rows over the chunk table (see chunk_apply_kernel): partial l-vectors
+// per chunk, then per segment the sum of its chunks' partials in chunk order.
+__global__ void svd_chunk_spmm_kernel(int64_t nchunks, const int4 *__restrict__ chunks,
+                                      const int32_t *__restrict__ idx, const double *__restrict__ a,
+                                      const double *__restrict__ In, int l, double *__restrict__ part)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= nchunks) return;
+    const int4 ch = chunks[c];
+    double acc[kSvdMaxL / 32];
+#pragma unroll
+    for (int q = 0; q < kSvdMaxL / 32; ++q) acc[q] = 0.0;
+    for (int e = ch.y; e < ch.z; ++e) {
+        const double av = a[e];
+        const double *row = In + (int64_t)idx[e] * l;
+#pragma unroll
+        for (int q = 0; q < kSvdMaxL / 32; ++q) {
+            const int col = q * 32 + lane;
+            if (col < l) acc[q] += av * row[col];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSvdMaxL / 32; ++q) {
+        const int col = q * 32 + lane;
+        if (col < l) part[c * l + col] = acc[q];
+    }
+}
+
+__global__ void svd_seg_sum_kernel(int64_t nseg, const int32_t *__restrict__ segchunk,
+                                   const double *__restrict__ part, int l, double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nseg) return;
+    for (int col = lane; col < l; col += 32) {
+        double acc = 0.0;
+        for (int c = segchunk[s]; c < segchunk[s + 1]; ++c) acc += part[(int64_t)c * l + col];
+        out[s * l + col] = acc;
     }
 }
 
@@ -637,9 +731,20 @@ cudaError_t svd_init_impl(glrm_s *h, int oversample, int power_iters, unsigned l
     A(&Qn, (size_t)n * l);
     A(&part, (size_t)kCertBlocks * l * l);
     A(&small, (size_t)6 * l * l + 3 * (size_t)l + 64);
+    double *spart = nullptr;  // chunk partials of the long-segment products
+    A(&spart, (size_t)std::max(h->csr.nchunks, h->csc.nchunks) * l);
     double *G = small, *R = G + l * l, *scratch = R + l * l, *PX = scratch + 2 * l * l + l, *PY = PX + l * kp;
     double *sv = PY + l * kp;
     const int bt = ((l + 31) / 32) * 32;
+    auto spmm = [&](const Orient &o, int64_t nseg, const double *a, const double *In, double *out) {
+        if (o.nchunks > 0 && nnz >= kLongSegment * nseg) {
+            svd_chunk_spmm_kernel<<<nblk(o.nchunks, 8), 256, 0, st>>>(o.nchunks, o.chunks, o.idx, a, In, l, spart);
+            svd_seg_sum_kernel<<<nblk(nseg, 8), 256, 0, st>>>(nseg, o.segchunk, spart, l, out);
+            h->launches += 1;
+        } else {
+            svd_spmm_kernel<<<nblk(nseg, 8), 256, 0, st>>>(nseg, o.ptr, o.idx, a, In, l, out);
+        }
+    };
     auto orth = [&](double *F, int64_t rows) {  // F <- F (V D^-1/2) of its Gram
         svd_gram_kernel<<<kCertBlocks, 256, 0, st>>>(rows, F, l, part);
         cert_sum_kernel<<<1, 256, 0, st>>>(part, kCertBlocks, l * l, G);
@@ -656,18 +761,18 @@ cudaError_t svd_init_impl(glrm_s *h, int oversample, int power_iters, unsigned l
             svd_scale_kernel<T><<<nblk(n, 8), 256, 0, st>>>(n, h->csc.ptr, h->csc.idx, cv, false, m, h->csc.ptr, mu,
                                                             s2, ac);
             svd_random_kernel<<<nblk(n * l, 256), 256, 0, st>>>(n * l, seed, Qn);
-            svd_spmm_kernel<<<nblk(m, 8), 256, 0, st>>>(m, h->csr.ptr, h->csr.idx, ar, Qn, l, Qm);  // A~ Omega
+            spmm(h->csr, m, ar, Qn, Qm);  // A~ Omega
             h->launches += 4;
             orth(Qm, m);
             for (int it = 0; it < power_iters; ++it) {
-                svd_spmm_kernel<<<nblk(n, 8), 256, 0, st>>>(n, h->csc.ptr, h->csc.idx, ac, Qm, l, Qn);  // A~^T Q
+                spmm(h->csc, n, ac, Qm, Qn);  // A~^T Q
                 orth(Qn, n);
-                svd_spmm_kernel<<<nblk(m, 8), 256, 0, st>>>(m, h->csr.ptr, h->csr.idx, ar, Qn, l, Qm);  // A~ Q
+                spmm(h->csr, m, ar, Qn, Qm);  // A~ Q
                 orth(Qm, m);
                 h->launches += 2;
             }
             // B^T = A~^T Q (n x l); its Gram B B^T = W diag(s^2) W^T
-            svd_spmm_kernel<<<nblk(n, 8), 256, 0, st>>>(n, h->csc.ptr, h->csc.idx, ac, Qm, l, Qn);
+            spmm(h->csc, n, ac, Qm, Qn);
             svd_gram_kernel<<<kCertBlocks, 256, 0, st>>>(n, Qn, l, part);
             cert_sum_kernel<<<1, 256, 0, st>>>(part, kCertBlocks, l * l, G);
             svd_top_kernel<<<1, bt, 0, st>>>(G, l, kp, scratch, PX, PY, sv);
@@ -683,7 +788,7 @@ cudaError_t svd_init_impl(glrm_s *h, int oversample, int power_iters, unsigned l
             e = cudaMemcpyAsync(sv_host, sv, kp * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    for (double *p : {mu, s2, ar, ac, Qm, Qn, part, small})
+    for (double *p : {mu, s2, ar, ac, Qm, Qn, part, small, spart})
         if (p) cudaFreeAsync(p, st);
     return e;
 }

@@ -98,6 +98,98 @@ colstats_csc_kernel(int64_t n, const int32_t *__restrict__ ptr, const T *__restr
     }
 }
 
+// Block-wide sums / extrema (256 threads), the result on every thread in a
+// fixed order (warp butterflies, then the 8 warp results in warp order).
+__device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[2])
+{
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();  // the previous use of sh is over
+    if (lane == 0) {
+        sh[w][0] = a;
+        sh[w][1] = b;
+    }
+    __syncthreads();
+    double x = 0.0, y = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+        x += sh[q][0];
+        y += sh[q][1];
+    }
+    a = x;
+    b = y;
+}
+
+__device__ __forceinline__ void block_minmax(double &lo, double &hi, double (*sh)[2])
+{
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        sh[w][0] = lo;
+        sh[w][1] = hi;
+    }
+    __syncthreads();
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+        lo = fmin(lo, sh[q][0]);
+        hi = fmax(hi, sh[q][1]);
+    }
+}
+
+// The same bisection with one CTA (256 threads) per column, for long columns
+// (a tall table has few columns: a warp each would leave most of the GPU idle).
+template <class T>
+__global__ void __launch_bounds__(256)
+colstats_csc_block_kernel(int64_t n, const int32_t *__restrict__ ptr, const T *__restrict__ val,
+                          const LossSpec *__restrict__ loss, double *__restrict__ mu, double *__restrict__ s2)
+{
+    __shared__ double sh[8][2];
+    for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+        const int b = ptr[j], e = ptr[j + 1];
+        if (b == e) {
+            if (threadIdx.x == 0) mu[j] = s2[j] = nan64();
+            continue;
+        }
+        const LossSpec sp = loss[j];
+        double lo = __longlong_as_double(0x7ff0000000000000LL), hi = -lo;
+        for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+            const double a = (double)val[q];
+            lo = fmin(lo, a);
+            hi = fmax(hi, a);
+        }
+        block_minmax(lo, hi, sh);
+        lo -= kStatBracket;
+        hi += kStatBracket;
+        const double tol = (hi - lo) * 0x1p-62;
+        for (int it = 0; it < kStatMaxIters && hi - lo > tol; ++it) {
+            const double mid = lo + 0.5 * (hi - lo);
+            if (!(mid > lo && mid < hi)) break;
+            double g = 0.0, ga = 0.0;
+            for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+                double L;
+                const double d = loss_deriv<double>(sp, mid, (double)val[q], L);
+                g += d;
+                ga += fabs(d);
+            }
+            block_sum2(g, ga, sh);
+            if (g < -kStatTieRel * ga) lo = mid;
+            else hi = mid;
+        }
+        double ls = 0.0, unused = 0.0;
+        for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+            double L;
+            loss_deriv<double>(sp, hi, (double)val[q], L);
+            ls += L;
+        }
+        block_sum2(ls, unused, sh);
+        if (threadIdx.x == 0) {
+            mu[j] = hi;
+            s2[j] = e - b > 1 ? ls / (double)(e - b - 1) : nan64();
+        }
+    }
+}
+
 // Dense, fully observed table (m x lda FP32): one CTA per 32 consecutive
 // columns, lane = column, the warps striding over rows (every load a
 // coalesced 128-byte row segment).  The CTA's columns bisect in lockstep;
@@ -196,6 +288,17 @@ cudaError_t launch_column_stats(glrm_s *h, double *mu, double *s2)
         int sms = 0;
         cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         if (e != cudaSuccess) return e;
+        if (h->nnz >= 2048 * h->n) {  // long columns: a CTA per column
+            const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(h->n, (int64_t)sms * 8));
+            if (h->prec == GLRM_FP64)
+                colstats_csc_block_kernel<double><<<grid, 256, 0, h->stream>>>(
+                    h->n, h->csc.ptr, (const double *)h->csc.val, h->loss_dev, mu, s2);
+            else
+                colstats_csc_block_kernel<float><<<grid, 256, 0, h->stream>>>(
+                    h->n, h->csc.ptr, (const float *)h->csc.val, h->loss_dev, mu, s2);
+            ++h->launches;
+            return cudaGetLastError();
+        }
         const int64_t want = (h->n + 7) / 8;  // 8 warps (columns) per CTA
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
         if (h->prec == GLRM_FP64)

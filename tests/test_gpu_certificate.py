@@ -111,3 +111,24 @@ def test_regularization_path_matches_oracle(G, oracle_mod):
         assert c == pytest.approx(max(s[s <= w]) / w, rel=1e-4)
     Xg, Yg = (a.cpu().numpy() for a in g.factors())
     np.testing.assert_allclose(Xg @ Yg.T, X @ Yt.T, rtol=0, atol=1e-6 * np.abs(X @ Yt.T).max())
+
+
+def test_certificate_tall_table(G, oracle_mod):
+    """6,000 x 24: columns of 6,000 entries take the chunked products (chunk
+    partials summed per column in chunk order); the closed form at the qPCA
+    optimum and the oracle at other factors."""
+    t = _table(W.qpca_dense(m=6000, n=24, k=3, seed=17), 3, 2.0)
+    A = t.val.reshape(t.m, t.n)
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    r = np.sqrt(np.maximum(s[:3] - 2.0, 0.0))
+    g = G.GLRM.from_table(t, precision=G.GLRM_FP64)
+    g.set_factors(torch.as_tensor(U[:, :3] * r, dtype=g.dtype, device="cuda"),
+                  torch.as_tensor(Vt[:3].T * r, dtype=g.dtype, device="cuda"))
+    val, _ = g.certificate(max_iters=5000, tol=1e-14)
+    assert val == pytest.approx(s[3] / 2.0, rel=1e-6)
+    g.set_factors(torch.as_tensor(t.X0, dtype=g.dtype, device="cuda"),
+                  torch.as_tensor(t.Yt0, dtype=g.dtype, device="cuda"))
+    g.sweep(3)
+    X, Yt = (a.cpu().numpy() for a in g.factors())
+    val, _ = g.certificate(max_iters=20000, tol=1e-14)
+    assert val == pytest.approx(oracle_problem(oracle_mod, t).certificate(X, Yt), rel=1e-5)

@@ -96,3 +96,12 @@ def test_svd_init_then_sweeps(G, oracle_mod):
     synced_sweeps(g, oracle_mod, t, 3, offset=True)
     f_svd = g.sweep(7)[-1]
     assert f_svd < f_rand
+
+
+def test_svd_init_tall_table(G, oracle_mod):
+    """8,000 x 30 with 60% observed: the Y-side products take the chunked form
+    (columns of about 4,800 entries)."""
+    from gpu_parity import subset_table
+    t = W.qpca_dense(m=8000, n=30, k=4, seed=18, noise=0.05)
+    t = subset_table(t, np.random.default_rng(18).random(t.nnz) < 0.6)
+    _compare(G, oracle_mod, t, 0, False, 1e-6)
