@@ -30,10 +30,27 @@ Parity status of each function (the pins live in tests/test_oracle_*.py):
   als                                  pinned (normal equations vs numpy.linalg,
                                        qPCA closed form)
   column_stats                         pinned (quadratic: mean and sample variance;
-                                       l1: median; quantile: the alpha-quantile,
-                                       brute force over a grid)
-  offset                               pinned (k = 1: the offset row converges
-                                       to the column statistic mu_j)
+                                       l1: median; quantile: the alpha-quantile;
+                                       logistic log-odds; hinge two-label minimum;
+                                       the smallest point of a flat bottom; brute
+                                       force over a grid)
+  offset                               pinned (objective by hand; k = 1: the
+                                       offset row converges to the column mean)
+  col_scale (weighted losses)          pinned (objective and gradient by hand; the
+                                       sweep's invariance under weights c with
+                                       regulariser weights c and steps alpha / c)
+  mloss / mgrad / mdecode              pinned (hand values, sums of the scalar hinge
+                                       over the block, finite differences, brute-
+                                       force decoding with ties)
+  FeatureProblem objective / proxgrad  pinned (cell-by-cell sum; scalar features
+                                       follow the plain sweep exactly; a block
+                                       follows its Boolean columns' sweep exactly)
+  entry_derivs / certificate           pinned (the qPCA closed forms: s_{k+1} / w
+                                       holding at rank 5 and failing at rank 4;
+                                       invariance under X T, Y T^-T)
+  svd_init                             pinned (an exactly low-rank table plus
+                                       column offsets reproduced; invariance under
+                                       affine encodings of a quadratic column)
   proxprox                             pinned (fixed points: the least-squares
                                        solution for r = 0, the closed form
                                        ((1 + 2 alpha gamma) G + gamma I) x = b
