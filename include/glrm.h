@@ -149,6 +149,18 @@ int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host
                            const int32_t *csc_colptr_host, const int32_t *csc_rowidx_host,
                            const void *csc_val_host);
 
+/* Omega from its CSR arrays alone (device / host pointers, as above): the
+ * CSR arrays are copied and validated as by glrm_set_observed, and the CSC
+ * orientation is then built from them on the device by a stable counting
+ * sort of the entries by column (rows ascending within each column; the
+ * result does not depend on scheduling), so only half the bytes cross from
+ * the host.  Allocates a count table of at most 2^26 int32 for the sort
+ * (freed before returning).  Synchronises. */
+int glrm_set_observed_csr(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_dev, const int32_t *csr_colidx_dev,
+                          const void *csr_val_dev);
+int glrm_set_observed_csr_host(glrm_t h, int64_t nnz, const int32_t *csr_rowptr_host,
+                               const int32_t *csr_colidx_host, const void *csr_val_host);
+
 /* Give the model a fully observed table instead: Omega = every (i, j), the
  * data matrix of Section 2 with nothing missing.  A: m x n, row-major with
  * leading dimension lda >= n (elements), FP32 (GLRM_FP32 and GLRM_BF16

@@ -510,13 +510,16 @@ int configure_paths(glrm_s *h, float *preA = nullptr)
     return GLRM_OK;
 }
 
+// csc_given false: only the CSR arrays are given; the CSC orientation is
+// built from them on the device after they pass validation.
 int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *ci, const void *rv,
-                      const int32_t *cp, const int32_t *ri, const void *cv, cudaMemcpyKind kind)
+                      const int32_t *cp, const int32_t *ri, const void *cv, cudaMemcpyKind kind,
+                      bool csc_given = true)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     DeviceGuard dg(h->device);
     if (nnz < 0 || nnz >= (int64_t)INT32_MAX) return fail(h, GLRM_ERR_RANGE, "nnz must be in [0, 2^31)");
-    if (!rp || !cp || (nnz > 0 && (!ci || !rv || !ri || !cv)))
+    if (!rp || (csc_given && !cp) || (nnz > 0 && (!ci || !rv || (csc_given && (!ri || !cv)))))
         return fail(h, GLRM_ERR_ARG, "null observed-set pointer");
     h->have_omega = false;
     free_orient(h->csr, h->stream);
@@ -567,10 +570,12 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         CK(cudaMemcpyAsync(R.val, rv, (size_t)nnz * es, kind, st));
     }
     CK(cudaEventRecord(h->ev_csr, st));
-    CK(cudaMemcpyAsync(C.ptr, cp, (size_t)(h->n + 1) * sizeof(int32_t), kind, st));
-    if (nnz > 0) {
-        CK(cudaMemcpyAsync(C.idx, ri, (size_t)nnz * sizeof(int32_t), kind, st));
-        CK(cudaMemcpyAsync(C.val, cv, (size_t)nnz * es, kind, st));
+    if (csc_given) {
+        CK(cudaMemcpyAsync(C.ptr, cp, (size_t)(h->n + 1) * sizeof(int32_t), kind, st));
+        if (nnz > 0) {
+            CK(cudaMemcpyAsync(C.idx, ri, (size_t)nnz * sizeof(int32_t), kind, st));
+            CK(cudaMemcpyAsync(C.val, cv, (size_t)nnz * es, kind, st));
+        }
     }
     CK(cudaStreamWaitEvent(au, h->ev_csr, 0));
     // validation, per orientation: pointers first (the index checks rely on
@@ -629,7 +634,15 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
             rc = cuda_fail(h, e, "dense set-up");
         }
     }
-    if (rc == GLRM_OK && hf[0] == 0) {
+    if (rc == GLRM_OK && hf[0] == 0 && !csc_given) {
+        // the CSC orientation from the validated CSR arrays: consistent by
+        // construction, so no CSC checks or digests
+        e = build_csc_from_csr(h, au);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_aux, au);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_aux, 0);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "csc from csr");
+    }
+    if (rc == GLRM_OK && hf[0] == 0 && csc_given) {
         // the CSC side: on the main stream, after its copies
         e = cudaEventRecord(h->ev_aux, au);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_aux, 0);
@@ -1015,6 +1028,16 @@ int glrm_set_observed_host(glrm_t h, int64_t nnz, const int32_t *rp, const int32
                            const void *rv, const int32_t *cp, const int32_t *ri, const void *cv)
 {
     return set_observed_impl(h, nnz, rp, ci, rv, cp, ri, cv, cudaMemcpyHostToDevice);
+}
+
+int glrm_set_observed_csr(glrm_t h, int64_t nnz, const int32_t *rp, const int32_t *ci, const void *rv)
+{
+    return set_observed_impl(h, nnz, rp, ci, rv, nullptr, nullptr, nullptr, cudaMemcpyDeviceToDevice, false);
+}
+
+int glrm_set_observed_csr_host(glrm_t h, int64_t nnz, const int32_t *rp, const int32_t *ci, const void *rv)
+{
+    return set_observed_impl(h, nnz, rp, ci, rv, nullptr, nullptr, nullptr, cudaMemcpyHostToDevice, false);
 }
 
 int glrm_set_dense(glrm_t h, const void *A, int64_t lda)

@@ -54,6 +54,8 @@ def _load():
         "glrm_set_observed": [p, i64, p, p, p, p, p, p],
         "glrm_set_observed_host": [p, i64, p, p, p, p, p, p],
         "glrm_set_dense": [p, p, i64],
+        "glrm_set_observed_csr": [p, i64, p, p, p],
+        "glrm_set_observed_csr_host": [p, i64, p, p, p],
         "glrm_set_dense_host": [p, p, i64],
         "glrm_set_factors": [p, p, p],
         "glrm_get_factors": [p, p, p],
@@ -183,6 +185,14 @@ def glrm_set_observed_host(h, nnz, csr_rowptr, csr_colidx, csr_val, csc_colptr, 
     _check(_lib.glrm_set_observed_host(h, nnz, _ptr(csr_rowptr), _ptr(csr_colidx),
                                        _ptr(csr_val), _ptr(csc_colptr), _ptr(csc_rowidx),
                                        _ptr(csc_val)), h)
+
+
+def glrm_set_observed_csr(h, nnz, csr_rowptr, csr_colidx, csr_val):
+    _check(_lib.glrm_set_observed_csr(h, nnz, _ptr(csr_rowptr), _ptr(csr_colidx), _ptr(csr_val)), h)
+
+
+def glrm_set_observed_csr_host(h, nnz, csr_rowptr, csr_colidx, csr_val):
+    _check(_lib.glrm_set_observed_csr_host(h, nnz, _ptr(csr_rowptr), _ptr(csr_colidx), _ptr(csr_val)), h)
 
 
 def glrm_set_dense(h, A, lda=None):

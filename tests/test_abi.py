@@ -34,7 +34,8 @@ def test_header_declares_entry_points():
               "glrm_get_state", "glrm_set_state", "glrm_last_error", "glrm_destroy",
               "glrm_set_offset", "glrm_column_stats", "glrm_set_column_scale", "glrm_proxprox_sweep",
               "glrm_embed_losses", "glrm_embed_size", "glrm_embed_features", "glrm_decode_features",
-              "glrm_set_reg_weights", "glrm_certificate", "glrm_regularization_path", "glrm_svd_init"):
+              "glrm_set_reg_weights", "glrm_certificate", "glrm_regularization_path", "glrm_svd_init",
+              "glrm_set_observed_csr", "glrm_set_observed_csr_host"):
         assert n in names
 
 
