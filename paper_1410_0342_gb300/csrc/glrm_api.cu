@@ -15,7 +15,7 @@
 #include <string>
 #include <vector>
 
-#include "glrm_handle.h"
+#include "glrm_setup.h"
 
 using namespace glrm;
 
@@ -563,9 +563,12 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     CK(cudaMemsetAsync((char *)R.val + (size_t)nnz * es, 0, kPad * es, st));
     CK(cudaMemsetAsync((char *)C.val + (size_t)nnz * es, 0, kPad * es, st));
     // CSR first: its checks and chunk table run on the auxiliary stream while
-    // the CSC arrays are still being copied
+    // the CSC arrays are still being copied.  From host CSR arrays alone the
+    // entries come over in pieces of whole row blocks, each checked and counted
+    // for the CSC build while the next one is copied (pipe).
+    const bool pipe = !csc_given && kind == cudaMemcpyHostToDevice && nnz > 0;
     CK(cudaMemcpyAsync(R.ptr, rp, (size_t)(h->m + 1) * sizeof(int32_t), kind, st));
-    if (nnz > 0) {
+    if (nnz > 0 && !pipe) {
         CK(cudaMemcpyAsync(R.idx, ci, (size_t)nnz * sizeof(int32_t), kind, st));
         CK(cudaMemcpyAsync(R.val, rv, (size_t)nnz * es, kind, st));
     }
@@ -588,11 +591,16 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (e != cudaSuccess) return cuda_fail(h, e, "validation");
         return GLRM_OK;
     };
-    // chunk table of one orientation, host-built from its validated pointer array
-    auto chunk_table = [&](Orient &o, int64_t nother, cudaStream_t s) -> int {
+    // chunk table of one orientation, host-built from its validated pointer
+    // array (read back, or the host copy when there is one)
+    auto chunk_table = [&](Orient &o, int64_t nother, cudaStream_t s, const int32_t *host_ptr = nullptr) -> int {
         std::vector<int32_t> ptr(o.nseg + 1);
-        CK(cudaMemcpyAsync(ptr.data(), o.ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        if (host_ptr) {
+            std::copy(host_ptr, host_ptr + o.nseg + 1, ptr.begin());
+        } else {
+            CK(cudaMemcpyAsync(ptr.data(), o.ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
         std::vector<int4> chunks;
         std::vector<int32_t> segchunk;
         build_chunks(ptr, chunks, segchunk, o.maxlen);
@@ -616,12 +624,48 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     cudaError_t e = launch_validate_ptr(R.ptr, h->m, nnz, flag, au);
     if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_ptr");
     if (rc == GLRM_OK) rc = check(0, au);
-    if (rc == GLRM_OK && hf[0] == 0) {
+    CscBuild cb;
+    bool cb_live = false;
+    if (rc == GLRM_OK && hf[0] == 0 && pipe) {
+        // the pointers are valid: pieces of row blocks, copied on the main
+        // stream, checked and counted on the auxiliary one as each lands
+        const int32_t *hrp = rp;
+        e = csc_build_begin(h, cb, au);
+        cb_live = e == cudaSuccess;
+        const int64_t pieces = std::max<int64_t>(1, std::min<int64_t>({8, nnz / (8 << 20) + 1, cb.nblk}));
+        const int64_t per = (cb.nblk + pieces - 1) / pieces;
+        std::vector<cudaEvent_t> evs;
+        for (int64_t b0 = 0; e == cudaSuccess && b0 < cb.nblk; b0 += per) {
+            const int64_t b1 = std::min<int64_t>(cb.nblk, b0 + per);
+            const int64_t r0 = b0 * cb.RB, r1 = std::min<int64_t>(h->m, b1 * cb.RB);
+            const int64_t e0 = hrp[r0], e1 = hrp[r1];
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) break;
+            evs.push_back(ev);
+            if (e1 > e0) {
+                e = cudaMemcpyAsync(R.idx + e0, ci + e0, (size_t)(e1 - e0) * sizeof(int32_t), kind, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync((char *)R.val + (size_t)e0 * es, (const char *)rv + (size_t)e0 * es,
+                                        (size_t)(e1 - e0) * es, kind, st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(au, ev, 0);
+            if (e == cudaSuccess)
+                e = launch_check_rows(R.ptr + r0, R.idx, R.val, r1 - r0, e1 - e0, h->prec, h->n, h->loss_dev, flag,
+                                      au);
+            if (e == cudaSuccess) e = csc_build_count(h, cb, b0, b1, au);
+        }
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "csr pieces");
+        if (rc == GLRM_OK) rc = check(0, au);
+        for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    } else if (rc == GLRM_OK && hf[0] == 0) {
         e = launch_check_entries(R, true, h->n, h->n, nnz, h->prec, h->loss_dev, flag, dig, au);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
         if (rc == GLRM_OK) rc = check(0, au);
     }
-    if (rc == GLRM_OK && hf[0] == 0) rc = chunk_table(R, h->n, au);
+    if (rc == GLRM_OK && hf[0] == 0)
+        rc = chunk_table(R, h->n, au, kind == cudaMemcpyHostToDevice ? rp : nullptr);
     // the dense table needs the CSR arrays only: built here too when it will be chosen
     float *preA = nullptr;
     if (rc == GLRM_OK && hf[0] == 0 && dense_choice(h) == 1) {
@@ -634,10 +678,16 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
             rc = cuda_fail(h, e, "dense set-up");
         }
     }
+    std::vector<int32_t> cpost;  // the built CSC's column pointers (host copy)
     if (rc == GLRM_OK && hf[0] == 0 && !csc_given) {
         // the CSC orientation from the validated CSR arrays: consistent by
         // construction, so no CSC checks or digests
-        e = build_csc_from_csr(h, au);
+        if (cb_live) {
+            e = csc_build_finish(h, cb, cpost, au);
+            cb_live = false;
+        } else {
+            e = build_csc_from_csr(h, au);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_aux, au);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_aux, 0);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "csc from csr");
@@ -660,6 +710,10 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
             if (rc == GLRM_OK) rc = check(1, st);
         }
     }
+    if (cb_live) {  // a pipelined build that did not reach its end
+        dfree(cb.cnt, au);
+        dfree(cb.tot, au);
+    }
     dfree(flag, st);
     dfree(dig, st);
     const int hflag = hf[0] | hf[1];
@@ -676,7 +730,8 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         return fail(h, code, (hflag & 8) && !(hflag & ~8) ? "non-finite value in the observed set"
                                                         : flag_message(hflag));
     }
-    if ((rc = chunk_table(C, h->m, st)) != GLRM_OK) {
+    const int32_t *cpost_host = !cpost.empty() ? cpost.data() : (csc_given && kind == cudaMemcpyHostToDevice ? cp : nullptr);
+    if ((rc = chunk_table(C, h->m, st, cpost_host)) != GLRM_OK) {
         if (preA) cudaFreeAsync(preA, st);
         return rc;
     }

@@ -16,21 +16,25 @@
 #include <algorithm>
 #include <climits>
 
-#include "glrm_handle.h"
+#include "glrm_setup.h"
 
 namespace glrm {
 namespace {
 
-__global__ void tr_count_kernel(int64_t m, int64_t n, int RB, int64_t nblk, const int32_t *__restrict__ rowptr,
-                                const int32_t *__restrict__ colidx, int32_t *__restrict__ cnt)
+__global__ void tr_count_kernel(int64_t m, int64_t n, int RB, int64_t b0, int64_t b1,
+                                const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                int32_t *__restrict__ cnt)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= nblk) return;
+    const int64_t b = b0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (b >= b1) return;
     int32_t *c = cnt + b * n;
     const int64_t r1 = std::min<int64_t>(m, (b + 1) * RB);
     for (int64_t i = b * RB; i < r1; ++i) {
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) c[colidx[e]] += 1;
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+            const int32_t j = colidx[e];
+            if (j >= 0 && j < n) c[j] += 1;  // unchecked input: never out of the table
+        }
         __syncwarp();  // the next row may share a column with this one
     }
 }
@@ -104,49 +108,74 @@ __global__ void tr_scatter_kernel(int64_t m, int64_t n, int RB, int64_t nblk, co
 
 }  // namespace
 
-cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st)
+cudaError_t csc_build_begin(glrm_s *h, CscBuild &b, cudaStream_t st)
+{
+    const int64_t m = h->m, n = h->n;
+    const int64_t budget = (int64_t)1 << 26;
+    const int64_t rb = std::max<int64_t>(std::max<int64_t>(1, (m + 4095) / 4096), (m * n + budget - 1) / budget);
+    b.RB = (int)((rb + 31) / 32 * 32);  // whole 32-row groups for the merge walk
+    b.nblk = (m + b.RB - 1) / b.RB;
+    cudaError_t e = dalloc_on(h, &b.cnt, (size_t)std::max<int64_t>(1, n * b.nblk) * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = dalloc_on(h, &b.tot, (size_t)std::max<int64_t>(1, n) * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.cnt, 0, (size_t)n * b.nblk * sizeof(int32_t), st);
+    return e;
+}
+
+cudaError_t csc_build_count(glrm_s *h, const CscBuild &b, int64_t b0, int64_t b1, cudaStream_t st)
+{
+    if (b1 <= b0 || h->nnz == 0) return cudaSuccess;
+    tr_count_kernel<<<(unsigned)((b1 - b0 + 7) / 8), 256, 0, st>>>(h->m, h->n, b.RB, b0, b1, h->csr.ptr, h->csr.idx,
+                                                                    b.cnt);
+    ++h->launches;
+    return cudaGetLastError();
+}
+
+cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, cudaStream_t st)
 {
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     Orient &R = h->csr, &C = h->csc;
-    const int64_t budget = (int64_t)1 << 26;
-    int64_t rb = std::max<int64_t>(std::max<int64_t>(1, (m + 4095) / 4096), (m * n + budget - 1) / budget);
-    const int RB = (int)((rb + 31) / 32 * 32);  // whole 32-row groups for the merge walk
-    const int64_t nblk = (m + RB - 1) / RB;
-    int32_t *cnt = nullptr, *tot = nullptr;
-    cudaError_t e = dalloc_on(h, &cnt, (size_t)std::max<int64_t>(1, n * nblk) * sizeof(int32_t), st);
-    if (e == cudaSuccess) e = dalloc_on(h, &tot, (size_t)std::max<int64_t>(1, n) * sizeof(int32_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)n * nblk * sizeof(int32_t), st);
-    if (e == cudaSuccess && nnz > 0) {
-        const unsigned g = (unsigned)((nblk + 7) / 8);
-        tr_count_kernel<<<g, 256, 0, st>>>(m, n, RB, nblk, R.ptr, R.idx, cnt);
-        tr_scan_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, nblk, cnt, tot);
+    cudaError_t e = cudaSuccess;
+    if (nnz > 0) {
+        tr_scan_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, b.nblk, b.cnt, b.tot);
         e = cudaGetLastError();
-    } else if (e == cudaSuccess) {
-        e = cudaMemsetAsync(tot, 0, (size_t)std::max<int64_t>(1, n) * sizeof(int32_t), st);
+    } else {
+        e = cudaMemsetAsync(b.tot, 0, (size_t)std::max<int64_t>(1, n) * sizeof(int32_t), st);
     }
-    std::vector<int32_t> ht((size_t)n), cp((size_t)n + 1);
+    std::vector<int32_t> ht((size_t)n);
+    cp.assign((size_t)n + 1, 0);
     if (e == cudaSuccess && n > 0)
-        e = cudaMemcpyAsync(ht.data(), tot, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(ht.data(), b.tot, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) {
-        cp[0] = 0;
         for (int64_t j = 0; j < n; ++j) cp[(size_t)j + 1] = cp[(size_t)j] + ht[(size_t)j];
         e = cudaMemcpyAsync(C.ptr, cp.data(), cp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess && nnz > 0) {
-        const unsigned g = (unsigned)((nblk + 7) / 8);
+        const unsigned g = (unsigned)((b.nblk + 7) / 8);
         if (h->prec == GLRM_FP64)
-            tr_scatter_kernel<double><<<g, 256, 0, st>>>(m, n, RB, nblk, R.ptr, R.idx, (const double *)R.val, C.ptr,
-                                                         cnt, C.idx, (double *)C.val);
+            tr_scatter_kernel<double><<<g, 256, 0, st>>>(m, n, b.RB, b.nblk, R.ptr, R.idx, (const double *)R.val,
+                                                         C.ptr, b.cnt, C.idx, (double *)C.val);
         else
-            tr_scatter_kernel<float><<<g, 256, 0, st>>>(m, n, RB, nblk, R.ptr, R.idx, (const float *)R.val, C.ptr,
-                                                        cnt, C.idx, (float *)C.val);
+            tr_scatter_kernel<float><<<g, 256, 0, st>>>(m, n, b.RB, b.nblk, R.ptr, R.idx, (const float *)R.val,
+                                                        C.ptr, b.cnt, C.idx, (float *)C.val);
         e = cudaGetLastError();
     }
-    h->launches += 3;
+    h->launches += 2;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table goes out of scope
-    dfree(cnt, st);
-    dfree(tot, st);
+    dfree(b.cnt, st);
+    dfree(b.tot, st);
+    return e;
+}
+
+cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st)
+{
+    CscBuild b;
+    cudaError_t e = csc_build_begin(h, b, st);
+    if (e == cudaSuccess) e = csc_build_count(h, b, 0, b.nblk, st);
+    std::vector<int32_t> cp;
+    if (e == cudaSuccess) return csc_build_finish(h, b, cp, st);
+    dfree(b.cnt, st);
+    dfree(b.tot, st);
     return e;
 }
 

@@ -4,7 +4,7 @@
 // check ORs a bit into a device flag word; nothing traps.
 #include <algorithm>
 
-#include "glrm_handle.h"
+#include "glrm_setup.h"
 
 namespace glrm {
 namespace {
@@ -151,6 +151,22 @@ cudaError_t launch_check_entries(const Orient &o, bool rows, int64_t other, int6
     else
         check_entries_kernel<float><<<nb, 256, 0, st>>>(o.ptr, o.idx, (const float *)o.val, o.nseg, pc, other,
                                                         rows, n, loss, flag, digest);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_rows(const int32_t *ptr, const int32_t *idx, const void *val, int64_t nseg,
+                              int64_t nnz_part, int prec, int64_t other, const LossSpec *loss, int *flag,
+                              cudaStream_t st)
+{
+    if (nseg == 0) return cudaSuccess;
+    const int pc = seg_pieces(nnz_part, nseg);
+    const unsigned nb = piece_blocks(nseg, pc);
+    if (prec == GLRM_FP64)
+        check_entries_kernel<double><<<nb, 256, 0, st>>>(ptr, idx, (const double *)val, nseg, pc, other, true,
+                                                         other, loss, flag, nullptr);
+    else
+        check_entries_kernel<float><<<nb, 256, 0, st>>>(ptr, idx, (const float *)val, nseg, pc, other, true, other,
+                                                        loss, flag, nullptr);
     return cudaGetLastError();
 }
 
