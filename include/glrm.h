@@ -228,10 +228,11 @@ int glrm_column_stats(glrm_t h, double *mu_dev, double *sigma2_dev);
  * w_host != NULL (n finite doubles > 0, copied) column j's loss becomes
  * w_j L_j everywhere (sweeps, objective, gradients); w_j = 1 / sigma2_j
  * gives the paper's standardised GLRM.  NULL removes them.  Weighted models
- * run every half-step on the chunked path (glrm_get_path reports
- * GLRM_PATH_CHUNKED); GLRM_BF16 models and fully observed dense tables
- * (glrm_set_dense) return GLRM_ERR_ARG / GLRM_ERR_STATE, as do
- * glrm_als_sweep and glrm_proxprox_sweep on a weighted model.  Synchronises. */
+ * run on the dense form when the table is held densely (a fully observed
+ * table, or an observed set on the dense path), else every half-step on the
+ * chunked path (glrm_get_path reports GLRM_PATH_CHUNKED).  GLRM_BF16 models
+ * return GLRM_ERR_ARG, as do glrm_als_sweep and glrm_proxprox_sweep on a
+ * weighted model.  Synchronises. */
 int glrm_set_column_scale(glrm_t h, const double *w_host);
 
 /* Change the regulariser weights (kinds stay).  Takes effect for work

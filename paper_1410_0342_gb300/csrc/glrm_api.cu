@@ -100,9 +100,9 @@ cudaError_t run_half(glrm_s *h, bool xstep) { return Engine<T>::half_step(h, xst
 
 cudaError_t half_step(glrm_s *h, bool xstep)
 {
-    // scaled losses (glrm_set_column_scale) run on the chunked path
-    if (h->lscale) return h->prec == GLRM_FP64 ? run_half<double>(h, xstep) : run_half<float>(h, xstep);
     if (h->dn.on) return dense_half_step(h, xstep);
+    // scaled losses (glrm_set_column_scale) on a sparse table run on the chunked path
+    if (h->lscale) return h->prec == GLRM_FP64 ? run_half<double>(h, xstep) : run_half<float>(h, xstep);
     const Orient &o = xstep ? h->csr : h->csc;
     if (o.mode == kModeMasked)
         return h->prec == GLRM_FP64 ? Engine<double>::masked_half_step(h, xstep)
@@ -1155,8 +1155,6 @@ int glrm_set_column_scale(glrm_t h, const double *w_host)
 {
     if (!h) return fail(nullptr, GLRM_ERR_ARG, "null handle");
     if (h->prec == GLRM_BF16) return fail(h, GLRM_ERR_ARG, "column loss weights need a GLRM_FP32 or GLRM_FP64 model");
-    if (w_host && h->dn.on && !h->dn.missing)
-        return fail(h, GLRM_ERR_STATE, "column loss weights run on an observed set, not on a dense table");
     DeviceGuard dg(h->device);
     drop_conv_graph(h);  // captured sweeps carry the weight pointer
     if (!w_host) {
@@ -1580,7 +1578,7 @@ int glrm_objective_at(glrm_t h, const void *X, const void *Yt, double *out)
     if (!X || !Yt || !out) return fail(h, GLRM_ERR_ARG, "null pointer");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->dn.on && !h->lscale ? dense_objective_at(h, (const float *)X, (const float *)Yt, out)
+    cudaError_t e = h->dn.on ? dense_objective_at(h, (const float *)X, (const float *)Yt, out)
                     : h->prec == GLRM_FP64
                         ? Engine<double>::objective_at(h, (const double *)X, (const double *)Yt, out)
                         : Engine<float>::objective_at(h, (const float *)X, (const float *)Yt, out);
@@ -1608,7 +1606,7 @@ int glrm_grad_at(glrm_t h, const void *X, const void *Yt, void *GX, void *GYt, i
     if (include_reg && (h->rx_kind == kRegNonneg || h->ry_kind == kRegNonneg))
         return fail(h, GLRM_ERR_ARG, "the nonnegativity indicator has no gradient");
     DeviceGuard dg(h->device);
-    cudaError_t e = h->dn.on && !h->lscale ? dense_grad_at(h, (const float *)X, (const float *)Yt, (float *)GX, (float *)GYt,
+    cudaError_t e = h->dn.on ? dense_grad_at(h, (const float *)X, (const float *)Yt, (float *)GX, (float *)GYt,
                                              include_reg != 0, scale)
                     : h->prec == GLRM_FP64
                         ? Engine<double>::grad_at(h, (const double *)X, (const double *)Yt,
@@ -1807,7 +1805,7 @@ int glrm_get_path(glrm_t h, int32_t *paths_host)
 {
     if (!h || !paths_host) return fail(h, GLRM_ERR_ARG, "null argument");
     if (!h->have_omega) return fail(h, GLRM_ERR_STATE, "no observed set");
-    if (h->lscale) {
+    if (h->lscale && !h->dn.on) {
         paths_host[0] = paths_host[1] = GLRM_PATH_CHUNKED;
         return GLRM_OK;
     }

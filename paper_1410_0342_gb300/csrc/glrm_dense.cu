@@ -71,6 +71,7 @@ struct DenseArgs {
     const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid, lo
     int64_t pack_part;        // elements per part
     const LossF *lossf;       // n column losses; w: the kind of the column's 16-column group, else -1
+    const float *wcol;        // n per-column loss weights (the scaled losses of Section 4.3); null: all 1
     const DnItem *items;      // one per CTA
     const int32_t *blocks;    // Y-step: per tile its four 32-column blocks (-1: none)
     const int32_t *segchunk;  // own index -> first partial slot
@@ -226,6 +227,25 @@ __device__ __forceinline__ void dn_block_any(const float (&u)[16], const float (
     }
 }
 
+// The X-step with per-column loss weights: 16 entries of 16 columns, each
+// loss and derivative times its column's weight (wt: the weights of these
+// columns; read only for entries inside the table).
+__device__ __forceinline__ void dn_block_w(const float (&u)[16], const float (&a)[16], const LossF *lf,
+                                           const float *__restrict__ wt, uint32_t valid, float (&rr)[16],
+                                           float &lsum)
+{
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        const LossF sp = lf[w];
+        float L;
+        const float d = loss_deriv_kind<float>(__float_as_int(sp.x), u[w], a[w], sp.y, sp.z, L);
+        const bool v = ((valid >> w) & 1u) && a[w] == a[w];
+        const float c = v ? __ldg(wt + w) : 0.f;
+        lsum += v ? c * L : 0.f;
+        rr[w] = v ? c * d : 0.f;
+    }
+}
+
 // One pass over a (128 own rows) x (range of chunks) block.  GRAD: partial
 // gradient rows and partial losses; otherwise partial losses only.
 // A tiles: X-step, two boxes of 32 columns x 128 own rows with the 128-byte
@@ -303,6 +323,8 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     // Y-step: this thread's column loss, and whether the warp shares one kind
     LossF myspec = make_float4(__int_as_float(kLossQuad), 0.f, 0.f, 0.f);
     if (!XSTEP && own_ok) myspec = p.lossf[own];
+    // Y-step with column weights: this thread's column's weight
+    const float wown = (!XSTEP && p.wcol && own_ok) ? p.wcol[own] : 1.f;
     int wkind = -1;
     if constexpr (!XSTEP) {
         const int kd = __float_as_int(myspec.x);
@@ -553,7 +575,9 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                     prm = l0.y;
                     lev = l0.z;
                 }
-                if (__all_sync(0xffffffffu, valid == 0xffffu)) {
+                if (XSTEP && p.wcol) {
+                    dn_block_w(u, a, lf, p.wcol + t0 + tb, valid, rr, lsum);
+                } else if (__all_sync(0xffffffffu, valid == 0xffffu)) {
                     switch (kind) {
                     case kLossQuad: dn_block<kLossQuad, MISS>(u, a, prm, lev, rr, lsum); break;
                     case kLossHuber: dn_block<kLossHuber, MISS>(u, a, prm, lev, rr, lsum); break;
@@ -564,6 +588,11 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                     }
                 } else {
                     dn_block_any<XSTEP>(u, a, lf, myspec, valid, rr, lsum);
+                }
+                if (!XSTEP && p.wcol) {  // the column's weight on its 16 entries
+                    lsum *= wown;
+#pragma unroll
+                    for (int w = 0; w < 16; ++w) rr[w] *= wown;
                 }
             }
             // compensated FP32 running sum of the chunk sums
@@ -830,6 +859,7 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     a.pt = d.pt;
     a.pack_part = d.pack_part;
     a.lossf = d.lossf;
+    a.wcol = (const float *)h->lscale;
     a.items = XSTEP ? d.items_x : d.items_y;
     a.blocks = XSTEP ? nullptr : d.blocks_y;
     a.segchunk = XSTEP ? d.segchunk_x : d.segchunk_y;

@@ -9,7 +9,8 @@ import torch
 
 from paper_1410_0342_gb300 import workloads as W
 
-from gpu_parity import decode_state, oracle_problem, subset_table, synced_sweeps
+from gpu_parity import (assert_grad_close, decode_state, grad_bounds, oracle_problem, subset_table,
+                        synced_sweeps)
 
 pytestmark = pytest.mark.gpu
 
@@ -182,8 +183,8 @@ def _weights(s2):
 @pytest.mark.parametrize("paths", [(1, 1), (2, 2), (4, 4), (6, 6)])
 def test_scaled_losses_match_oracle(G, oracle_mod, paths):
     """w_j = 1 / sigma2_j from the GPU's own statistics (the standardised GLRM
-    of Sec. 4.3, with the offset); whatever path was asked for, the weighted
-    half-steps run on the chunked path."""
+    of Sec. 4.3, with the offset); the weighted half-steps run on the dense
+    form where it was asked for (6), else on the chunked path."""
     t = W.small_mixed(m=1303, n=140, k=8, p_obs=0.5, seed=620, nkinds=7, rx=(RQ, 0.1), ry=(RQ, 0.1))
     g = G.GLRM.from_table(t)
     G.glrm_set_path(g.h, *paths)
@@ -193,7 +194,8 @@ def test_scaled_losses_match_oracle(G, oracle_mod, paths):
     g.set_factors(torch.as_tensor(t.X0, device=g.device), torch.as_tensor(t.Yt0, device=g.device))
     g.set_offset(True)
     g.set_column_scale(w)
-    assert tuple(G.glrm_get_path(g.h)) == (G.GLRM_PATH_CHUNKED, G.GLRM_PATH_CHUNKED)
+    want = G.GLRM_PATH_DENSE if paths == (6, 6) else G.GLRM_PATH_CHUNKED
+    assert tuple(G.glrm_get_path(g.h)) == (want, want)
     synced_sweeps(g, oracle_mod, t, 6, offset=True, col_scale=w)
     g.set_column_scale(None)
     synced_sweeps(g, oracle_mod, t, 2, offset=True)
@@ -229,6 +231,35 @@ def test_scale_arguments(G):
     b = G.GLRM.from_table(t, precision=G.GLRM_BF16)
     with pytest.raises(G.GLRMError):
         b.set_column_scale(np.ones(t.n))
-    d = G.GLRM.from_dense_table(W.small_mixed(m=64, n=16, k=3, p_obs=1.0, seed=9))
-    with pytest.raises(G.GLRMError):
-        d.set_column_scale(np.ones(16))
+
+
+
+@pytest.mark.parametrize("m,n,k", [(1000, 301, 20), (129, 65, 16)])
+def test_scaled_dense_table_matches_oracle(G, oracle_mod, m, n, k):
+    """Weighted losses on a fully observed table (the tensor-core form, every
+    loss kind, ragged against the 128-row tiles and 64-wide chunks): sweeps
+    from a state shared with the oracle, then objective and gradient at the
+    factors reached.  The oracle's gradient bounds are of the unweighted
+    terms: a row coordinate's terms carry weights up to max w, a column's its
+    own w_j."""
+    t = W.small_mixed(m=m, n=n, k=k, p_obs=1.0, seed=622 + k, nkinds=7, rx=(RQ, 0.1), ry=(RQ, 0.1))
+    w = np.random.default_rng(k).uniform(0.25, 4.0, size=n)
+    g = G.GLRM.from_dense_table(t)
+    g.set_column_scale(w)
+    assert tuple(G.glrm_get_path(g.h)) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    synced_sweeps(g, oracle_mod, t, 6, col_scale=w)
+    X, Yt = g.factors()
+    Xd = X.double().cpu().numpy()
+    Yd = Yt.double().cpu().numpy()
+    p = oracle_problem(oracle_mod, t, col_scale=w)
+    of = p.objective(Xd, Yd)
+    assert abs(g.objective() - of) <= 1e-5 * abs(of), (g.objective(), of)
+    GX = torch.empty_like(X)
+    GY = torch.empty_like(Yt)
+    G.glrm_grad_at(g.h, X, Yt, GX, GY, False)
+    oGX, oGY = p.gradient(Xd, Yd)
+    sX, sY, vX, vY = grad_bounds(oracle_problem(oracle_mod, t), Xd, Yd)
+    assert_grad_close(GX.cpu().numpy(), oGX, sX * w.max(), vX * w.max(), what="GX")
+    assert_grad_close(GY.cpu().numpy(), oGY, sY * w[:, None], vY * w[:, None], what="GYt")
+    g.set_column_scale(None)
+    synced_sweeps(g, oracle_mod, t, 2)
