@@ -71,7 +71,7 @@ struct DenseArgs {
     const __nv_bfloat16 *pt;  // other factor per chunk, K-major over the chunk rows: parts hi, mid, lo
     int64_t pack_part;        // elements per part
     const LossF *lossf;       // n column losses; w: the kind of the column's 16-column group, else -1
-    const float *wcol;        // n per-column loss weights (the scaled losses of Section 4.3); null: all 1
+    const float *wcol;        // WGT kernels: n per-column loss weights (the scaled losses of Section 4.3)
     const DnItem *items;      // one per CTA
     const int32_t *blocks;    // Y-step: per tile its four 32-column blocks (-1: none)
     const int32_t *segchunk;  // own index -> first partial slot
@@ -268,7 +268,7 @@ __device__ __forceinline__ void dn_block_w(const float (&u)[16], const float (&a
 // R's and W's BF16 high parts (FP32 accumulation) and only R's high part is
 // written to tensor memory; GEMM1, the losses, derivatives and objectives
 // keep the six-product FP32 quality.
-template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16 = false>
+template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16 = false, bool WGT = false>
 __global__ void __launch_bounds__(kDnThreads, 1)
 dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
 {
@@ -324,7 +324,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
     LossF myspec = make_float4(__int_as_float(kLossQuad), 0.f, 0.f, 0.f);
     if (!XSTEP && own_ok) myspec = p.lossf[own];
     // Y-step with column weights: this thread's column's weight
-    const float wown = (!XSTEP && p.wcol && own_ok) ? p.wcol[own] : 1.f;
+    const float wown = (!XSTEP && WGT && own_ok) ? p.wcol[own] : 1.f;
     int wkind = -1;
     if constexpr (!XSTEP) {
         const int kd = __float_as_int(myspec.x);
@@ -575,7 +575,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                     prm = l0.y;
                     lev = l0.z;
                 }
-                if (XSTEP && p.wcol) {
+                if constexpr (XSTEP && WGT) {
                     dn_block_w(u, a, lf, p.wcol + t0 + tb, valid, rr, lsum);
                 } else if (__all_sync(0xffffffffu, valid == 0xffffu)) {
                     switch (kind) {
@@ -589,7 +589,7 @@ dense_pass_kernel(const DenseArgs p, const __grid_constant__ CUtensorMap amap)
                 } else {
                     dn_block_any<XSTEP>(u, a, lf, myspec, valid, rr, lsum);
                 }
-                if (!XSTEP && p.wcol) {  // the column's weight on its 16 entries
+                if constexpr (!XSTEP && WGT) {  // the column's weight on its 16 entries
                     lsum *= wown;
 #pragma unroll
                     for (int w = 0; w < 16; ++w) rr[w] *= wown;
@@ -818,27 +818,27 @@ int dense_width(int k)
     return 0;
 }
 
-template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16>
+template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16, bool WGT>
 cudaError_t launch_dense_kp(glrm_s *h, const DenseArgs &a, int nA, unsigned items)
 {
     const size_t smem = DnSmem<XSTEP, GRAD, KP>::bytes(nA);
-    cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16>,
+    cudaError_t e = cudaFuncSetAttribute(dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16, WGT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(XSTEP ? h->dn.tmap_x : h->dn.tmap_y);
-    dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16><<<items, kDnThreads, smem, h->stream>>>(a, *map);
+    dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16, WGT><<<items, kDnThreads, smem, h->stream>>>(a, *map);
     h->launches += 1;
     return cudaGetLastError();
 }
 
 // A stages that fit next to the fixed buffers and the kernel's static shared
 // memory (at most kDnMaxStages; fewer than 2 is refused by the caller).
-template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16>
+template <bool XSTEP, bool GRAD, int KP, bool MISS, bool B16, bool WGT>
 int stages_kp(int optin)
 {
     using SM = DnSmem<XSTEP, GRAD, KP>;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, dense_pass_kernel<XSTEP, GRAD, KP, MISS, B16, WGT>) != cudaSuccess) return 0;
     if ((size_t)optin < fa.sharedSizeBytes) return 0;
     const size_t room = (size_t)optin - fa.sharedSizeBytes;
     if (room < SM::bytes(0)) return 0;
@@ -872,22 +872,25 @@ cudaError_t launch_dense(glrm_s *h, const float *F, float *part_grad, double *pa
     if (e != cudaSuccess) return e;
     // the BF16 form's gradient passes take the single-product GEMM2
     const bool b16 = GRAD && h->prec == GLRM_BF16;
-#define GLRM_DENSE_GO(KK, MS, B)                                                   \
+#define GLRM_DENSE_GO(KK, MS, B, WG)                                               \
     {                                                                              \
-        a.nA = stages_kp<XSTEP, GRAD, KK, MS, B>(optin);                           \
+        a.nA = stages_kp<XSTEP, GRAD, KK, MS, B, WG>(optin);                       \
         if (a.nA < 2) return cudaErrorInvalidConfiguration;                        \
-        return launch_dense_kp<XSTEP, GRAD, KK, MS, B>(h, a, a.nA, tiles);         \
+        return launch_dense_kp<XSTEP, GRAD, KK, MS, B, WG>(h, a, a.nA, tiles);     \
     }
+    // weighted losses (FP32 models only) take the variant that also tests for
+    // missing cells, whatever the table: the test never fires on a full one
 #define GLRM_DENSE_CASE(KK)                                                        \
     if (d.KP == KK) {                                                              \
+        if (a.wcol) GLRM_DENSE_GO(KK, true, false, true)                           \
         if constexpr (GRAD) {                                                      \
             if (b16) {                                                             \
-                if (d.missing) GLRM_DENSE_GO(KK, true, true)                       \
-                GLRM_DENSE_GO(KK, false, true)                                     \
+                if (d.missing) GLRM_DENSE_GO(KK, true, true, false)                \
+                GLRM_DENSE_GO(KK, false, true, false)                              \
             }                                                                      \
         }                                                                          \
-        if (d.missing) GLRM_DENSE_GO(KK, true, false)                              \
-        GLRM_DENSE_GO(KK, false, false)                                            \
+        if (d.missing) GLRM_DENSE_GO(KK, true, false, false)                       \
+        GLRM_DENSE_GO(KK, false, false, false)                                     \
     }
     GLRM_DENSE_CASE(16)
     GLRM_DENSE_CASE(32)
