@@ -626,6 +626,8 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     if (rc == GLRM_OK) rc = check(0, au);
     CscBuild cb;
     bool cb_live = false;
+    float *preA = nullptr;  // the dense table, when the dense form will be chosen
+    const int64_t pre_lda = (h->n + 3) / 4 * 4;
     if (rc == GLRM_OK && hf[0] == 0 && pipe) {
         // the pointers are valid: pieces of row blocks, copied on the main
         // stream, checked and counted on the auxiliary one as each lands
@@ -664,29 +666,29 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
         if (rc == GLRM_OK) rc = check(0, au);
     }
-    if (rc == GLRM_OK && hf[0] == 0)
-        rc = chunk_table(R, h->n, au, kind == cudaMemcpyHostToDevice ? rp : nullptr);
     // the dense table needs the CSR arrays only: built here too when it will be chosen
-    float *preA = nullptr;
+    // (queued before the CSR chunk table, whose host build overlaps it)
     if (rc == GLRM_OK && hf[0] == 0 && dense_choice(h) == 1) {
-        const int64_t lda = (h->n + 3) / 4 * 4;
-        e = dalloc_on(h, &preA, std::max<size_t>((size_t)h->m * lda * sizeof(float), 16), au);
-        if (e == cudaSuccess) e = launch_dense_scatter(h, preA, lda, au);
+        e = dalloc_on(h, &preA, std::max<size_t>((size_t)h->m * pre_lda * sizeof(float), 16), au);
+        if (e == cudaSuccess) e = launch_dense_scatter(h, preA, pre_lda, au);
         if (e != cudaSuccess) {
             if (preA) cudaFreeAsync(preA, au);
             preA = nullptr;
             rc = cuda_fail(h, e, "dense set-up");
         }
     }
+    if (rc == GLRM_OK && hf[0] == 0)
+        rc = chunk_table(R, h->n, au, kind == cudaMemcpyHostToDevice ? rp : nullptr);
     std::vector<int32_t> cpost;  // the built CSC's column pointers (host copy)
     if (rc == GLRM_OK && hf[0] == 0 && !csc_given) {
         // the CSC orientation from the validated CSR arrays: consistent by
-        // construction, so no CSC checks or digests
+        // construction, so no CSC checks or digests; its entries read from
+        // the dense table's tiles when there is one
         if (cb_live) {
-            e = csc_build_finish(h, cb, cpost, au);
+            e = csc_build_finish(h, cb, cpost, au, preA, pre_lda);
             cb_live = false;
         } else {
-            e = build_csc_from_csr(h, au);
+            e = build_csc_from_csr(h, au, preA, pre_lda);
         }
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_aux, au);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_aux, 0);

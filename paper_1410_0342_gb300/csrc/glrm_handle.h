@@ -278,7 +278,7 @@ cudaError_t certificate_norm(glrm_s *h, int iters, double tol, double *norm, int
 // SVD initialisation of the factors (glrm_cert.cu).
 cudaError_t svd_init(glrm_s *h, int oversample, int power_iters, unsigned long long seed, double *sv_host);
 // The CSC arrays (C.ptr, C.idx, C.val allocated) from validated CSR ones (glrm_transpose.cu).
-cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st);
+cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st, const float *A = nullptr, int64_t lda = 0);
 // Raise *flag when an index lies outside [0, bound).
 cudaError_t launch_check_index(const int32_t *idx, int64_t n, int64_t bound, int *flag, cudaStream_t st);
 cudaError_t launch_embed_rowcount(int64_t m, const int32_t *rowptr, const int32_t *featidx, const FeatDev *F,

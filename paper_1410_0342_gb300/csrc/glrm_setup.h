@@ -20,6 +20,8 @@ cudaError_t launch_check_rows(const int32_t *ptr, const int32_t *idx, const void
 // count over row blocks [b0, b1) (entries outside the column range are
 // skipped, so it is safe before the checks' verdict), finish (prefixes,
 // column pointers into h->csc.ptr and colptr_host, the placement, release).
+// With A (FP32 / BF16 models: the set's dense table, lda floats per row, NaN
+// outside the set) the placement reads the entries from its tiles.
 struct CscBuild {
     int RB = 0;        // rows per block (a multiple of 32)
     int64_t nblk = 0;  // row blocks
@@ -27,6 +29,7 @@ struct CscBuild {
 };
 cudaError_t csc_build_begin(glrm_s *h, CscBuild &b, cudaStream_t st);
 cudaError_t csc_build_count(glrm_s *h, const CscBuild &b, int64_t b0, int64_t b1, cudaStream_t st);
-cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &colptr_host, cudaStream_t st);
+cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &colptr_host, cudaStream_t st,
+                             const float *A = nullptr, int64_t lda = 0);
 
 }  // namespace glrm

@@ -5,14 +5,16 @@
 //
 // Rows are cut into nblk blocks of RB consecutive rows (at most about 4,096
 // blocks, and n x nblk <= 2^26 counters).  Pass 1: per row block, the count
-// of its entries in every column (one warp per row block, its rows in order;
-// the columns of a row are distinct, so no two lanes touch the same counter;
-// the block's n counters are contiguous).  Pass 2: per column, the exclusive
-// prefix of its counts over the row blocks (one warp per column) and the
-// column's total.  The column pointers are the exclusive prefix of the totals
-// (host).  Pass 3: per row block, its rows in order, every entry placed at
-// colptr[j] + the running count of column j in the block (32 rows merged at a
-// time, so the stores for one column are coalesced).
+// of its entries in every column (the block's n counters are contiguous).
+// Pass 2: per column, the exclusive prefix of its counts over the row blocks
+// (one warp per column) and the column's total.  The column pointers are the
+// exclusive prefix of the totals (host).  Pass 3: per row block, its rows in
+// order, every entry placed at colptr[j] + the running count of column j in
+// the block (32 rows merged at a time, so the stores for one column are
+// coalesced).  Where n counters fit in shared memory, passes 1 and 3 keep a
+// block's counters there (pass 1: one CTA per row block over the block's
+// contiguous entries with shared-memory atomics; pass 3: a warp's running
+// slots), so no step waits on a global read-modify-write.
 #include <algorithm>
 #include <climits>
 
@@ -37,6 +39,29 @@ __global__ void tr_count_kernel(int64_t m, int64_t n, int RB, int64_t b0, int64_
         }
         __syncwarp();  // the next row may share a column with this one
     }
+}
+
+// Pass 1 with the counters in shared memory: one CTA per row block, its
+// entries (contiguous in the CSR arrays) taken in any order, since a count
+// does not depend on it; the n counts are written out whole, zeros included.
+__global__ void tr_count_smem_kernel(int64_t m, int64_t n, int RB, int64_t b0, int64_t b1,
+                                     const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                     int32_t *__restrict__ cnt)
+{
+    extern __shared__ int32_t sc[];
+    const int64_t b = b0 + blockIdx.x;
+    if (b >= b1) return;  // the same on every thread of the CTA
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) sc[j] = 0;
+    __syncthreads();
+    const int64_t r0 = b * RB, r1 = std::min<int64_t>(m, (b + 1) * RB);
+    const int64_t e0 = rowptr[r0], e1 = rowptr[r1];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int32_t j = __ldg(colidx + e);
+        if (j >= 0 && j < n) atomicAdd(&sc[j], 1);  // unchecked input: never out of the table
+    }
+    __syncthreads();
+    int32_t *c = cnt + b * n;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) c[j] = sc[j];
 }
 
 // Exclusive prefix over the row blocks of one column's counts (in place), one
@@ -106,6 +131,55 @@ __global__ void tr_scatter_kernel(int64_t m, int64_t n, int RB, int64_t nblk, co
     }
 }
 
+// Pass 3 from the dense table of the same set (NaN at the cells outside it),
+// when the dense form holds one: one warp per tile of 32 rows x 32 columns,
+// staged in shared memory; per column, the rows holding an entry (a ballot
+// over the column's 32 cells) go to consecutive slots colptr[j] + off[b][j] +
+// rank, so the stores of a column are coalesced and its rows ascend.  Every
+// read is a whole 128-byte row segment, so the pass streams the table once.
+constexpr int kFillWarps = 8;
+__global__ void __launch_bounds__(kFillWarps * 32)
+tr_fill_dense_kernel(int64_t m, int64_t n, int RB, int64_t nblk, const float *__restrict__ A, int64_t lda,
+                     const int32_t *__restrict__ colptr, const int32_t *__restrict__ off,
+                     int32_t *__restrict__ rowidx, float *__restrict__ cval)
+{
+    __shared__ float tile[kFillWarps][32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t nch = (n + 31) / 32;
+    const int64_t gw = (int64_t)blockIdx.x * kFillWarps + w;
+    if (gw >= nblk * nch) return;  // whole warps
+    const int64_t b = gw / nch, c0 = (gw - b * nch) * 32, j = c0 + lane;
+    const int cols = (int)std::min<int64_t>(32, n - c0);
+    int32_t slot = j < n ? colptr[j] + off[b * n + j] : 0;  // lane: column j's next slot
+    const int64_t r1 = std::min<int64_t>(m, (b + 1) * RB);
+    for (int64_t i0 = b * RB; i0 < r1; i0 += 32) {
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const int64_t i = i0 + r;
+            tile[w][r][lane] = (i < r1 && j < n) ? A[i * lda + j] : __int_as_float(0x7fffffff);
+        }
+        __syncwarp();
+        for (int c = 0; c < cols; ++c) {  // lane: row i0 + lane
+            const float v = tile[w][lane][c];
+            const bool has = v == v;
+            const uint32_t mask = __ballot_sync(0xffffffffu, has);
+            const int32_t base = __shfl_sync(0xffffffffu, slot, c);
+            if (has) {
+                const int32_t p = base + __popc(mask & lt);
+                rowidx[p] = (int32_t)(i0 + lane);
+                cval[p] = v;
+            }
+            if (lane == c) slot += __popc(mask);
+        }
+        __syncwarp();
+    }
+}
+
+// Shared memory for pass 1's n counters per CTA, at most; wider tables count
+// on global counters.
+constexpr size_t kTrSmemMax = 160 * 1024;
+
 }  // namespace
 
 cudaError_t csc_build_begin(glrm_s *h, CscBuild &b, cudaStream_t st)
@@ -124,13 +198,25 @@ cudaError_t csc_build_begin(glrm_s *h, CscBuild &b, cudaStream_t st)
 cudaError_t csc_build_count(glrm_s *h, const CscBuild &b, int64_t b0, int64_t b1, cudaStream_t st)
 {
     if (b1 <= b0 || h->nnz == 0) return cudaSuccess;
-    tr_count_kernel<<<(unsigned)((b1 - b0 + 7) / 8), 256, 0, st>>>(h->m, h->n, b.RB, b0, b1, h->csr.ptr, h->csr.idx,
-                                                                    b.cnt);
+    const size_t sm = (size_t)h->n * sizeof(int32_t);
+    if (sm <= kTrSmemMax) {
+        if (sm > 48 * 1024) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(tr_count_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        tr_count_smem_kernel<<<(unsigned)(b1 - b0), 256, sm, st>>>(h->m, h->n, b.RB, b0, b1, h->csr.ptr,
+                                                                   h->csr.idx, b.cnt);
+    } else {
+        tr_count_kernel<<<(unsigned)((b1 - b0 + 7) / 8), 256, 0, st>>>(h->m, h->n, b.RB, b0, b1, h->csr.ptr,
+                                                                        h->csr.idx, b.cnt);
+    }
     ++h->launches;
     return cudaGetLastError();
 }
 
-cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, cudaStream_t st)
+cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, cudaStream_t st, const float *A,
+                             int64_t lda)
 {
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     Orient &R = h->csr, &C = h->csc;
@@ -150,7 +236,12 @@ cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, c
         for (int64_t j = 0; j < n; ++j) cp[(size_t)j + 1] = cp[(size_t)j] + ht[(size_t)j];
         e = cudaMemcpyAsync(C.ptr, cp.data(), cp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess && nnz > 0) {
+    if (e == cudaSuccess && nnz > 0 && A && h->prec != GLRM_FP64) {
+        const int64_t warps = b.nblk * ((n + 31) / 32);
+        tr_fill_dense_kernel<<<(unsigned)((warps + kFillWarps - 1) / kFillWarps), kFillWarps * 32, 0, st>>>(
+            m, n, b.RB, b.nblk, A, lda, C.ptr, b.cnt, C.idx, (float *)C.val);
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess && nnz > 0) {
         const unsigned g = (unsigned)((b.nblk + 7) / 8);
         if (h->prec == GLRM_FP64)
             tr_scatter_kernel<double><<<g, 256, 0, st>>>(m, n, b.RB, b.nblk, R.ptr, R.idx, (const double *)R.val,
@@ -167,13 +258,13 @@ cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, c
     return e;
 }
 
-cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st)
+cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st, const float *A, int64_t lda)
 {
     CscBuild b;
     cudaError_t e = csc_build_begin(h, b, st);
     if (e == cudaSuccess) e = csc_build_count(h, b, 0, b.nblk, st);
     std::vector<int32_t> cp;
-    if (e == cudaSuccess) return csc_build_finish(h, b, cp, st);
+    if (e == cudaSuccess) return csc_build_finish(h, b, cp, st, A, lda);
     dfree(b.cnt, st);
     dfree(b.tot, st);
     return e;

@@ -70,6 +70,43 @@ def test_csr_only_dense_form_and_row_blocks(G):
     np.testing.assert_array_equal(a.sweep(2), b.sweep(2))
 
 
+@pytest.mark.parametrize("host", [True, False])
+def test_csr_only_dense_form_csc(G, host):
+    """On the dense form the CSC entries are read from the dense table's
+    tiles; the dense sweeps never read them, so they are checked through what
+    does: the column statistics and sweeps on the sparse paths after a path
+    switch, bitwise against a handle given both orientations (ragged rows and
+    columns, an empty row and an empty column)."""
+    t = W.small_mixed(m=3001, n=301, k=8, p_obs=0.6, seed=903, nkinds=7)
+    rows = t.rows()
+    t = subset_table(t, ~((rows == 11) | (t.colidx == 300)))
+    a, b = _twins(G, t, 1, host)
+    assert tuple(G.glrm_get_path(b.h)) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
+    np.testing.assert_array_equal(a.sweep(2), b.sweep(2))
+    for x, y in zip(a.column_stats(), b.column_stats()):
+        assert torch.equal(x.nan_to_num(-7.0), y.nan_to_num(-7.0))
+    for paths in ((1, 1), (2, 3)):
+        G.glrm_set_path(a.h, *paths)
+        G.glrm_set_path(b.h, *paths)
+        np.testing.assert_array_equal(a.sweep(2), b.sweep(2))
+    Xa, Ya = a.factors()
+    Xb, Yb = b.factors()
+    assert torch.equal(Xa, Xb) and torch.equal(Ya, Yb)
+
+
+def test_csr_only_wide_tables(G):
+    """Column counts beyond what shared memory holds (n = 50,000: the count and
+    scatter passes on global counters) and a host-piped build of a table whose
+    counters take the opt-in shared memory (n = 20,000) with a ragged last row
+    block."""
+    tw = W.completion(m=3000, n=50_000, k=8, per_row=40)
+    a, b = _twins(G, tw, 1, True)
+    np.testing.assert_array_equal(a.sweep(2), b.sweep(2))
+    tc = W.completion(m=70_001, n=20_000, k=8, per_row=30)
+    a, b = _twins(G, tc, 1, True)
+    np.testing.assert_array_equal(a.sweep(2), b.sweep(2))
+
+
 def test_csr_only_rejects_bad_arrays(G):
     t = W.small_mixed(m=200, n=40, k=4, seed=902)
     b = G.GLRM(t.m, t.n, t.k, (t.loss_kind, t.loss_param, t.loss_levels), t.rx, t.ry, G.GLRM_FP32)
