@@ -540,6 +540,9 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         CK(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming));
     }
     cudaStream_t au = h->aux;
+    // the built CSC's column pointers (host copy; an upload source on the
+    // auxiliary stream, so declared before the drain below)
+    std::vector<int32_t> cpost;
     // every return below waits for the work queued on the auxiliary stream
     struct AuxDrain {
         cudaStream_t s;
@@ -628,12 +631,17 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     bool cb_live = false;
     float *preA = nullptr;  // the dense table, when the dense form will be chosen
     const int64_t pre_lda = (h->n + 3) / 4 * 4;
+    bool r_chunked = false;  // the CSR chunk table is built
+    cudaEvent_t a_ready = nullptr;  // the dense table is written
     if (rc == GLRM_OK && hf[0] == 0 && pipe) {
         // the pointers are valid: pieces of row blocks, copied on the main
         // stream, checked and counted on the auxiliary one as each lands
         const int32_t *hrp = rp;
         e = csc_build_begin(h, cb, au);
         cb_live = e == cudaSuccess;
+        // the dense table, when it will be chosen, is scattered piece by piece too
+        if (e == cudaSuccess && dense_choice(h) == 1)
+            e = dalloc_on(h, &preA, std::max<size_t>((size_t)h->m * pre_lda * sizeof(float), 16), au);
         const int64_t pieces = std::max<int64_t>(1, std::min<int64_t>({8, nnz / (8 << 20) + 1, cb.nblk}));
         const int64_t per = (cb.nblk + pieces - 1) / pieces;
         std::vector<cudaEvent_t> evs;
@@ -657,8 +665,13 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
                 e = launch_check_rows(R.ptr + r0, R.idx, R.val, r1 - r0, e1 - e0, h->prec, h->n, h->loss_dev, flag,
                                       au);
             if (e == cudaSuccess) e = csc_build_count(h, cb, b0, b1, au);
+            if (e == cudaSuccess && preA) e = launch_dense_scatter(h, preA, pre_lda, au, r0, r1);
         }
         if (e != cudaSuccess) rc = cuda_fail(h, e, "csr pieces");
+        // the CSR chunk table from the host's (validated) pointers while the
+        // pieces are copied; its upload queues behind them
+        if (rc == GLRM_OK) rc = chunk_table(R, h->n, st, rp);
+        r_chunked = rc == GLRM_OK;
         if (rc == GLRM_OK) rc = check(0, au);
         for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
     } else if (rc == GLRM_OK && hf[0] == 0) {
@@ -666,29 +679,33 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (e != cudaSuccess) rc = cuda_fail(h, e, "validate_idx");
         if (rc == GLRM_OK) rc = check(0, au);
     }
-    // the dense table needs the CSR arrays only: built here too when it will be chosen
-    // (queued before the CSR chunk table, whose host build overlaps it)
-    if (rc == GLRM_OK && hf[0] == 0 && dense_choice(h) == 1) {
-        e = dalloc_on(h, &preA, std::max<size_t>((size_t)h->m * pre_lda * sizeof(float), 16), au);
-        if (e == cudaSuccess) e = launch_dense_scatter(h, preA, pre_lda, au);
+    // the dense table needs the CSR arrays only: built here too when it will
+    // be chosen (queued before the CSR chunk table, whose host build overlaps
+    // it); when the CSC is built here, on the main stream beside the CSC
+    // build's prefix pass, which then reads its entries from it
+    cudaStream_t ds = csc_given ? au : st;
+    if (rc == GLRM_OK && hf[0] == 0 && !preA && dense_choice(h) == 1) {
+        e = dalloc_on(h, &preA, std::max<size_t>((size_t)h->m * pre_lda * sizeof(float), 16), ds);
+        if (e == cudaSuccess) e = launch_dense_scatter(h, preA, pre_lda, ds);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a_ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(a_ready, ds);
         if (e != cudaSuccess) {
-            if (preA) cudaFreeAsync(preA, au);
+            if (preA) cudaFreeAsync(preA, ds);
             preA = nullptr;
             rc = cuda_fail(h, e, "dense set-up");
         }
     }
-    if (rc == GLRM_OK && hf[0] == 0)
+    if (rc == GLRM_OK && hf[0] == 0 && !r_chunked)
         rc = chunk_table(R, h->n, au, kind == cudaMemcpyHostToDevice ? rp : nullptr);
-    std::vector<int32_t> cpost;  // the built CSC's column pointers (host copy)
     if (rc == GLRM_OK && hf[0] == 0 && !csc_given) {
         // the CSC orientation from the validated CSR arrays: consistent by
         // construction, so no CSC checks or digests; its entries read from
         // the dense table's tiles when there is one
         if (cb_live) {
-            e = csc_build_finish(h, cb, cpost, au, preA, pre_lda);
+            e = csc_build_finish(h, cb, cpost, au, preA, pre_lda, a_ready);
             cb_live = false;
         } else {
-            e = build_csc_from_csr(h, au, preA, pre_lda);
+            e = build_csc_from_csr(h, au, preA, pre_lda, a_ready);
         }
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_aux, au);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_aux, 0);
@@ -718,6 +735,7 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     }
     dfree(flag, st);
     dfree(dig, st);
+    if (a_ready) cudaEventDestroy(a_ready);  // released once its waits are done
     const int hflag = hf[0] | hf[1];
     if (preA && (rc != GLRM_OK || hflag)) {
         cudaStreamSynchronize(au);

@@ -777,8 +777,11 @@ static __global__ void dense_validate_kernel(const float *__restrict__ A, int64_
 
 // Omega's values (CSR) into a dense table that holds NaN everywhere else:
 // one warp per row writes the row's NaN fill, then its entries.
+// Rows 0 .. m - 1 of rowptr (which may point into the middle of a pointer
+// array: entry indices are absolute) into rows of A; a column index outside
+// [0, n) is skipped, so rows whose checks are still running may be scattered.
 static __global__ void dense_scatter_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                            const float *__restrict__ val, int64_t m, int64_t lda,
+                                            const float *__restrict__ val, int64_t m, int64_t n, int64_t lda,
                                             float *__restrict__ A)
 {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -786,7 +789,10 @@ static __global__ void dense_scatter_kernel(const int32_t *__restrict__ rowptr, 
     float *row = A + i * lda;
     for (int64_t c = threadIdx.x & 31; c < lda; c += 32) row[c] = __int_as_float(0x7fffffff);
     __syncwarp();
-    for (int e = rowptr[i] + (threadIdx.x & 31); e < rowptr[i + 1]; e += 32) row[colidx[e]] = val[e];
+    for (int e = rowptr[i] + (threadIdx.x & 31); e < rowptr[i + 1]; e += 32) {
+        const int32_t j = colidx[e];
+        if (j >= 0 && j < n) row[j] = val[e];
+    }
 }
 
 static __global__ void dense_alpha_kernel(float *__restrict__ alpha, int64_t nseg, float value)
@@ -1259,10 +1265,12 @@ cudaError_t dense_prepare(glrm_s *h)
     return e;
 }
 
-cudaError_t launch_dense_scatter(glrm_s *h, float *A, int64_t lda, cudaStream_t st)
+cudaError_t launch_dense_scatter(glrm_s *h, float *A, int64_t lda, cudaStream_t st, int64_t r0, int64_t r1)
 {
-    dense_scatter_kernel<<<(unsigned)((h->m + 7) / 8), 256, 0, st>>>(h->csr.ptr, h->csr.idx,
-                                                                   (const float *)h->csr.val, h->m, lda, A);
+    if (r1 < 0) r1 = h->m;
+    if (r1 <= r0) return cudaSuccess;
+    dense_scatter_kernel<<<(unsigned)((r1 - r0 + 7) / 8), 256, 0, st>>>(
+        h->csr.ptr + r0, h->csr.idx, (const float *)h->csr.val, r1 - r0, h->n, lda, A + r0 * lda);
     h->launches += 1;
     return cudaGetLastError();
 }

@@ -278,7 +278,8 @@ cudaError_t certificate_norm(glrm_s *h, int iters, double tol, double *norm, int
 // SVD initialisation of the factors (glrm_cert.cu).
 cudaError_t svd_init(glrm_s *h, int oversample, int power_iters, unsigned long long seed, double *sv_host);
 // The CSC arrays (C.ptr, C.idx, C.val allocated) from validated CSR ones (glrm_transpose.cu).
-cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st, const float *A = nullptr, int64_t lda = 0);
+cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st, const float *A = nullptr, int64_t lda = 0,
+                               cudaEvent_t a_ready = nullptr);
 // Raise *flag when an index lies outside [0, bound).
 cudaError_t launch_check_index(const int32_t *idx, int64_t n, int64_t bound, int *flag, cudaStream_t st);
 cudaError_t launch_embed_rowcount(int64_t m, const int32_t *rowptr, const int32_t *featidx, const FeatDev *F,
@@ -295,8 +296,11 @@ void dense_free(glrm_s *h);
 cudaError_t dense_prepare(glrm_s *h);
 cudaError_t launch_dense_validate(const float *A, int64_t lda, int64_t m, int64_t n, const LossSpec *loss,
                                   int *flag, cudaStream_t st);
-// The CSR entries into a dense m x lda table A, NaN at every other cell (on st).
-cudaError_t launch_dense_scatter(glrm_s *h, float *A, int64_t lda, cudaStream_t st);
+// The CSR entries of rows r0 .. r1 - 1 (r1 < 0: all rows) into those rows of
+// a dense m x lda table A, NaN at every other cell (on st); column indices
+// outside [0, n) are skipped.
+cudaError_t launch_dense_scatter(glrm_s *h, float *A, int64_t lda, cudaStream_t st, int64_t r0 = 0,
+                                 int64_t r1 = -1);
 cudaError_t dense_reset_steps(glrm_s *h);
 cudaError_t dense_half_step(glrm_s *h, bool xstep);
 cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, double *out);

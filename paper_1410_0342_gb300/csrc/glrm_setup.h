@@ -21,7 +21,9 @@ cudaError_t launch_check_rows(const int32_t *ptr, const int32_t *idx, const void
 // skipped, so it is safe before the checks' verdict), finish (prefixes,
 // column pointers into h->csc.ptr and colptr_host, the placement, release).
 // With A (FP32 / BF16 models: the set's dense table, lda floats per row, NaN
-// outside the set) the placement reads the entries from its tiles.
+// outside the set) the placement reads the entries from its tiles, after
+// a_ready (if given) on st.  colptr_host must live until st has passed the
+// upload of the column pointers from it.
 struct CscBuild {
     int RB = 0;        // rows per block (a multiple of 32)
     int64_t nblk = 0;  // row blocks
@@ -30,6 +32,6 @@ struct CscBuild {
 cudaError_t csc_build_begin(glrm_s *h, CscBuild &b, cudaStream_t st);
 cudaError_t csc_build_count(glrm_s *h, const CscBuild &b, int64_t b0, int64_t b1, cudaStream_t st);
 cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &colptr_host, cudaStream_t st,
-                             const float *A = nullptr, int64_t lda = 0);
+                             const float *A = nullptr, int64_t lda = 0, cudaEvent_t a_ready = nullptr);
 
 }  // namespace glrm

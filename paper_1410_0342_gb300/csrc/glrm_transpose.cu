@@ -7,7 +7,7 @@
 // blocks, and n x nblk <= 2^26 counters).  Pass 1: per row block, the count
 // of its entries in every column (the block's n counters are contiguous).
 // Pass 2: per column, the exclusive prefix of its counts over the row blocks
-// (one warp per column) and the column's total.  The column pointers are the
+// (in two levels over segments of row blocks) and the column's total.  The column pointers are the
 // exclusive prefix of the totals (host).  Pass 3: per row block, its rows in
 // order, every entry placed at colptr[j] + the running count of column j in
 // the block (32 rows merged at a time, so the stores for one column are
@@ -64,28 +64,41 @@ __global__ void tr_count_smem_kernel(int64_t m, int64_t n, int RB, int64_t b0, i
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) c[j] = sc[j];
 }
 
-// Exclusive prefix over the row blocks of one column's counts (in place), one
-// warp per column, 32 blocks at a time with a carried total; tot[j] receives
-// the column's count.
-__global__ void tr_scan_kernel(int64_t n, int64_t nblk, int32_t *__restrict__ cnt, int32_t *__restrict__ tot)
+// Pass 2 in two levels over S segments of L consecutive row blocks, one
+// thread per (segment, column), so consecutive threads read consecutive
+// counters: first each segment's sum per column; then each segment's start
+// (the sum of the segments before it) carried through its blocks, the counts
+// replaced in place by their exclusive prefix; the last segment's thread
+// writes the column's total.
+__global__ void tr_segsum_kernel(int64_t n, int64_t nblk, int64_t S, int64_t L, const int32_t *__restrict__ cnt,
+                                 int32_t *__restrict__ seg)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (j >= n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S * n) return;
+    const int64_t s = t / n, j = t - s * n;
+    const int64_t b0 = s * L, b1 = std::min<int64_t>(nblk, b0 + L);
+    int32_t acc = 0;
+#pragma unroll 4
+    for (int64_t b = b0; b < b1; ++b) acc += cnt[b * n + j];
+    seg[t] = acc;
+}
+
+__global__ void tr_segscan_kernel(int64_t n, int64_t nblk, int64_t S, int64_t L, int32_t *__restrict__ cnt,
+                                  const int32_t *__restrict__ seg, int32_t *__restrict__ tot)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S * n) return;
+    const int64_t s = t / n, j = t - s * n;
     int32_t carry = 0;
-    for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
-        const int64_t b = b0 + lane;
-        const int32_t v = b < nblk ? cnt[b * n + j] : 0;
-        int32_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (b < nblk) cnt[b * n + j] = carry + incl - v;
-        carry += __shfl_sync(0xffffffffu, incl, 31);
+    for (int64_t q = 0; q < s; ++q) carry += seg[q * n + j];
+    if (s == S - 1) tot[j] = carry + seg[t];
+    const int64_t b0 = s * L, b1 = std::min<int64_t>(nblk, b0 + L);
+#pragma unroll 4
+    for (int64_t b = b0; b < b1; ++b) {
+        const int32_t v = cnt[b * n + j];
+        cnt[b * n + j] = carry;
+        carry += v;
     }
-    if (lane == 0) tot[j] = carry;
 }
 
 // Pass 3 walks 32 rows at a time (lane = row) and merges their sorted column
@@ -216,14 +229,25 @@ cudaError_t csc_build_count(glrm_s *h, const CscBuild &b, int64_t b0, int64_t b1
 }
 
 cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, cudaStream_t st, const float *A,
-                             int64_t lda)
+                             int64_t lda, cudaEvent_t a_ready)
 {
     const int64_t m = h->m, n = h->n, nnz = h->nnz;
     Orient &R = h->csr, &C = h->csc;
     cudaError_t e = cudaSuccess;
     if (nnz > 0) {
-        tr_scan_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, b.nblk, b.cnt, b.tot);
-        e = cudaGetLastError();
+        // segments: at most 64, at most 2^22 segment sums
+        const int64_t S = std::max<int64_t>(1, std::min<int64_t>({64, b.nblk, ((int64_t)1 << 22) / std::max<int64_t>(1, n)}));
+        const int64_t L = (b.nblk + S - 1) / S;
+        int32_t *seg = nullptr;
+        e = dalloc_on(h, &seg, (size_t)(S * n) * sizeof(int32_t), st);
+        if (e == cudaSuccess) {
+            const unsigned g = (unsigned)((S * n + 255) / 256);
+            tr_segsum_kernel<<<g, 256, 0, st>>>(n, b.nblk, S, L, b.cnt, seg);
+            tr_segscan_kernel<<<g, 256, 0, st>>>(n, b.nblk, S, L, b.cnt, seg, b.tot);
+            e = cudaGetLastError();
+            dfree(seg, st);
+            h->launches += 1;
+        }
     } else {
         e = cudaMemsetAsync(b.tot, 0, (size_t)std::max<int64_t>(1, n) * sizeof(int32_t), st);
     }
@@ -237,6 +261,7 @@ cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, c
         e = cudaMemcpyAsync(C.ptr, cp.data(), cp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess && nnz > 0 && A && h->prec != GLRM_FP64) {
+        if (a_ready) e = cudaStreamWaitEvent(st, a_ready, 0);
         const int64_t warps = b.nblk * ((n + 31) / 32);
         tr_fill_dense_kernel<<<(unsigned)((warps + kFillWarps - 1) / kFillWarps), kFillWarps * 32, 0, st>>>(
             m, n, b.RB, b.nblk, A, lda, C.ptr, b.cnt, C.idx, (float *)C.val);
@@ -252,19 +277,24 @@ cudaError_t csc_build_finish(glrm_s *h, CscBuild &b, std::vector<int32_t> &cp, c
         e = cudaGetLastError();
     }
     h->launches += 2;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table goes out of scope
+    // the column pointers went out from cp (the caller's) before this
+    // returns; the tables are released in stream order
     dfree(b.cnt, st);
     dfree(b.tot, st);
     return e;
 }
 
-cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st, const float *A, int64_t lda)
+cudaError_t build_csc_from_csr(glrm_s *h, cudaStream_t st, const float *A, int64_t lda, cudaEvent_t a_ready)
 {
     CscBuild b;
     cudaError_t e = csc_build_begin(h, b, st);
     if (e == cudaSuccess) e = csc_build_count(h, b, 0, b.nblk, st);
     std::vector<int32_t> cp;
-    if (e == cudaSuccess) return csc_build_finish(h, b, cp, st, A, lda);
+    if (e == cudaSuccess) {
+        e = csc_build_finish(h, b, cp, st, A, lda, a_ready);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // cp goes out of scope
+        return e;
+    }
     dfree(b.cnt, st);
     dfree(b.tot, st);
     return e;

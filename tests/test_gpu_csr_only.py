@@ -70,16 +70,20 @@ def test_csr_only_dense_form_and_row_blocks(G):
     np.testing.assert_array_equal(a.sweep(2), b.sweep(2))
 
 
-@pytest.mark.parametrize("host", [True, False])
-def test_csr_only_dense_form_csc(G, host):
+@pytest.mark.parametrize("table,host", [("small", True), ("small", False), ("mixed20k", True)])
+def test_csr_only_dense_form_csc(G, table, host):
     """On the dense form the CSC entries are read from the dense table's
     tiles; the dense sweeps never read them, so they are checked through what
     does: the column statistics and sweeps on the sparse paths after a path
     switch, bitwise against a handle given both orientations (ragged rows and
-    columns, an empty row and an empty column)."""
-    t = W.small_mixed(m=3001, n=301, k=8, p_obs=0.6, seed=903, nkinds=7)
-    rows = t.rows()
-    t = subset_table(t, ~((rows == 11) | (t.colidx == 300)))
+    columns, an empty row and an empty column; the 20,000-row table comes
+    over from the host in two pieces, its dense table scattered per piece)."""
+    if table == "small":
+        t = W.small_mixed(m=3001, n=301, k=8, p_obs=0.6, seed=903, nkinds=7)
+        rows = t.rows()
+        t = subset_table(t, ~((rows == 11) | (t.colidx == 300)))
+    else:
+        t = W.mixed(m=20000)
     a, b = _twins(G, t, 1, host)
     assert tuple(G.glrm_get_path(b.h)) == (G.GLRM_PATH_DENSE, G.GLRM_PATH_DENSE)
     np.testing.assert_array_equal(a.sweep(2), b.sweep(2))
