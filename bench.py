@@ -507,13 +507,14 @@ def run_glrm(args, world, rank, local):
         # varies with it between hosts)
         dbufs = [torch.empty_like(x, device=dev) for x in hb + [hX, hY]]
         link = []
-        for _ in range(3):
+        for rep in range(6):  # the first is a warm-up, not recorded
             torch.cuda.synchronize(dev)
             c0 = time.perf_counter()
             for d_, h_ in zip(dbufs, hb + [hX, hY]):
                 d_.copy_(h_, non_blocking=True)
             torch.cuda.synchronize(dev)
-            link.append(h2d / (time.perf_counter() - c0) / 1e9)
+            if rep:
+                link.append(h2d / (time.perf_counter() - c0) / 1e9)
         del dbufs
         for _ in range(max(3, args.warmup)):  # the pool reaches its steady size
             e2e_step()
