@@ -137,7 +137,7 @@ int plan_masked(glrm_s *h, Orient &o, bool xstep, int force, int K, int sms, siz
     const int64_t ntiles = (o.nseg + 31) / 32;
     const bool forced = force != GLRM_PATH_AUTO;
     CK(dalloc(h, &o.tptr, (size_t)(ntiles + 1) * sizeof(int32_t)));
-    CK(launch_mt_count(o, o.tptr, h->stream));
+    CK(launch_mt_count(o, nother, o.tptr, h->stream));
     std::vector<int32_t> cnt((size_t)ntiles);
     CK(cudaMemcpyAsync(cnt.data(), o.tptr, (size_t)ntiles * sizeof(int32_t), cudaMemcpyDeviceToHost,
                        h->stream));

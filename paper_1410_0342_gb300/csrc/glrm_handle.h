@@ -307,7 +307,7 @@ cudaError_t dense_objective_at(glrm_s *h, const float *X, const float *Yt, doubl
 cudaError_t dense_grad_at(glrm_s *h, const float *X, const float *Yt, float *GX, float *GYt, bool reg,
                           const double *scale);
 cudaError_t launch_build_runptr(const Orient &o, cudaStream_t st);
-cudaError_t launch_mt_count(const Orient &o, int32_t *cnt, cudaStream_t st);
+cudaError_t launch_mt_count(const Orient &o, int64_t nother, int32_t *cnt, cudaStream_t st);
 cudaError_t launch_mt_build(const Orient &o, int prec, cudaStream_t st);
 
 }  // namespace glrm

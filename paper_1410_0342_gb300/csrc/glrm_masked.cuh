@@ -56,6 +56,41 @@ static __global__ void mt_count_kernel(int64_t nseg, const int32_t *__restrict__
     if (lane == 0) cnt[t] = c;
 }
 
+// The same count from a bitmap of the other dimension in shared memory (one
+// CTA per tile, nother bits): every entry of the tile's 32 segments (one
+// contiguous range) sets its index's bit, the count is the number of bits
+// set.  Its cost is the tile's entries plus nother / 32 words, where the
+// merge above takes one dependent step per distinct index.  Indices were
+// validated to lie in [0, nother); any other is skipped so the bitmap is never
+// left.
+static __global__ void mt_count_bitmap_kernel(int64_t nseg, int64_t nother, const int32_t *__restrict__ ptr,
+                                              const int32_t *__restrict__ idx, int32_t *__restrict__ cnt)
+{
+    extern __shared__ uint32_t bits[];
+    const int64_t t = blockIdx.x;
+    const int64_t words = (nother + 31) / 32;
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+    __syncthreads();
+    const int64_t s0 = t * 32, s1 = std::min<int64_t>(nseg, s0 + 32);
+    const int64_t e0 = ptr[s0], e1 = ptr[s1];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int32_t j = __ldg(idx + e);
+        if (j >= 0 && j < nother) atomicOr(&bits[j >> 5], 1u << (j & 31));
+    }
+    __syncthreads();
+    int c = 0;
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) c += __popc(bits[w]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ int part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
+        cnt[t] = tot;
+    }
+}
+
 // Emit pairs and tile-ordered values.  A tile's pair list is cut into units
 // of at most P pairs (unit q of tile t starts at pair tptr[t] + q P); the
 // value offset where each unit starts goes to uvoff[ubeg[t] + q].
@@ -653,10 +688,20 @@ cudaError_t mt_build(const Orient &o, cudaStream_t st)
     return cudaGetLastError();
 }
 
-inline cudaError_t mt_count(const Orient &o, int32_t *cnt, cudaStream_t st)
+inline cudaError_t mt_count(const Orient &o, int64_t nother, int32_t *cnt, cudaStream_t st)
 {
     const int64_t ntiles = (o.nseg + 31) / 32;
-    mt_count_kernel<<<blocks_for(ntiles, 8), 256, 0, st>>>(o.nseg, o.ptr, o.idx, cnt);
+    const size_t bitmap = (size_t)((nother + 31) / 32) * sizeof(uint32_t);
+    if (ntiles > 0 && bitmap <= 160 * 1024) {
+        if (bitmap > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(mt_count_bitmap_kernel,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bitmap);
+            if (e != cudaSuccess) return e;
+        }
+        mt_count_bitmap_kernel<<<(unsigned)ntiles, 256, bitmap, st>>>(o.nseg, nother, o.ptr, o.idx, cnt);
+    } else {
+        mt_count_kernel<<<blocks_for(ntiles, 8), 256, 0, st>>>(o.nseg, o.ptr, o.idx, cnt);
+    }
     return cudaGetLastError();
 }
 

@@ -93,11 +93,19 @@ __global__ void tr_segscan_kernel(int64_t n, int64_t nblk, int64_t S, int64_t L,
     for (int64_t q = 0; q < s; ++q) carry += seg[q * n + j];
     if (s == S - 1) tot[j] = carry + seg[t];
     const int64_t b0 = s * L, b1 = std::min<int64_t>(nblk, b0 + L);
-#pragma unroll 4
-    for (int64_t b = b0; b < b1; ++b) {
-        const int32_t v = cnt[b * n + j];
-        cnt[b * n + j] = carry;
-        carry += v;
+    // a batch of counts is loaded before any of it is overwritten, so the
+    // loads are in flight together instead of each waiting for the last store
+    constexpr int kBatch = 16;
+    for (int64_t b = b0; b < b1; b += kBatch) {
+        int32_t v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) v[u] = b + u < b1 ? cnt[(b + u) * n + j] : 0;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (b + u < b1) {
+                cnt[(b + u) * n + j] = carry;
+                carry += v[u];
+            }
     }
 }
 

@@ -103,6 +103,19 @@ def test_sparse_chunked_matches_oracle(G, oracle_mod):
     synced_sweeps(g, oracle_mod, t, 6)
 
 
+@pytest.mark.parametrize("paths", [(4, 4), (5, 5)])
+def test_masked_tiles_of_a_tall_table(G, oracle_mod, paths):
+    """Masked tiles whose other dimension takes more than 48 KB of bitmap to
+    count (the Y-step's 400,003 rows: the pair counts of its tiles from a
+    bitmap in opt-in shared memory), against the oracle."""
+    t = W.completion(m=400_003, n=700, k=8, per_row=6)
+    g = G.GLRM.from_table(t)
+    G.glrm_set_path(g.h, *paths)
+    # the Y-step's 22 tiles are too few for the GPU's warps: split either way
+    assert tuple(G.glrm_get_path(g.h)) == (paths[0], G.GLRM_PATH_MASKED_SPLIT)
+    synced_sweeps(g, oracle_mod, t, 3)
+
+
 @pytest.mark.parametrize("p_obs,k", [(0.55, 12), (0.45, 33), (0.9, 5)])
 def test_dense_path_with_missing_cells(G, oracle_mod, p_obs, k):
     """An observed set stored densely (NaN at the missing cells): synced
