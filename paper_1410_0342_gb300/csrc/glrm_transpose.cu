@@ -5,16 +5,16 @@
 //
 // Rows are cut into nblk blocks of RB consecutive rows (at most about 4,096
 // blocks, and n x nblk <= 2^26 counters).  Pass 1: per row block, the count
-// of its entries in every column (the block's n counters are contiguous).
-// Pass 2: per column, the exclusive prefix of its counts over the row blocks
-// (in two levels over segments of row blocks) and the column's total.  The column pointers are the
-// exclusive prefix of the totals (host).  Pass 3: per row block, its rows in
-// order, every entry placed at colptr[j] + the running count of column j in
-// the block (32 rows merged at a time, so the stores for one column are
-// coalesced).  Where n counters fit in shared memory, passes 1 and 3 keep a
-// block's counters there (pass 1: one CTA per row block over the block's
-// contiguous entries with shared-memory atomics; pass 3: a warp's running
-// slots), so no step waits on a global read-modify-write.
+// of its entries in every column (the block's n counters are contiguous; one
+// CTA per row block with the counters in shared memory where n of them fit,
+// else one warp per row block on global counters).  Pass 2: per column, the
+// exclusive prefix of its counts over the row blocks (two levels over
+// segments of row blocks) and the column's total.  The column pointers are
+// the exclusive prefix of the totals (host).  Pass 3: per row block, its rows
+// in order, every entry placed at colptr[j] + the running count of column j
+// in the block: read from the set's dense table tile by tile when the dense
+// form holds one, else 32 rows merged at a time; either way the stores for
+// one column are coalesced.
 #include <algorithm>
 #include <climits>
 
