@@ -543,11 +543,17 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
     // the built CSC's column pointers (host copy; an upload source on the
     // auxiliary stream, so declared before the drain below)
     std::vector<int32_t> cpost;
-    // every return below waits for the work queued on the auxiliary stream
-    struct AuxDrain {
-        cudaStream_t s;
-        ~AuxDrain() { cudaStreamSynchronize(s); }
-    } drain{au};
+    // every return below waits for the work queued on both streams, so no
+    // copy from the caller's arrays is still running when the call returns
+    // (an early return on invalid CSR arrays may leave CSC copies queued)
+    struct Drain {
+        cudaStream_t a, s;
+        ~Drain()
+        {
+            cudaStreamSynchronize(a);
+            cudaStreamSynchronize(s);
+        }
+    } drain{au, st};
     CK(dalloc(h, &R.ptr, (size_t)(h->m + 1) * sizeof(int32_t)));
     CK(dalloc(h, &C.ptr, (size_t)(h->n + 1) * sizeof(int32_t)));
     CK(dalloc(h, &R.idx, nz * sizeof(int32_t)));
@@ -680,9 +686,10 @@ int set_observed_impl(glrm_s *h, int64_t nnz, const int32_t *rp, const int32_t *
         if (rc == GLRM_OK) rc = check(0, au);
     }
     // the dense table needs the CSR arrays only: built here too when it will
-    // be chosen (queued before the CSR chunk table, whose host build overlaps
-    // it); when the CSC is built here, on the main stream beside the CSC
-    // build's prefix pass, which then reads its entries from it
+    // be chosen and was not scattered piece by piece above (queued before the
+    // CSR chunk table, whose host build overlaps it); when the CSC is built
+    // here, on the main stream beside the CSC build's prefix pass, which then
+    // reads its entries from it
     cudaStream_t ds = csc_given ? au : st;
     if (rc == GLRM_OK && hf[0] == 0 && !preA && dense_choice(h) == 1) {
         e = dalloc_on(h, &preA, std::max<size_t>((size_t)h->m * pre_lda * sizeof(float), 16), ds);
